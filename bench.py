@@ -1,0 +1,352 @@
+"""Benchmark of the SM hot path (rows a1-a4: emission, sweep, fused moments,
+closures) on the 2D multigroup workload: 256x256 cells, 128 directions,
+64 groups, FP32 sweep arithmetic with FP64 Planck and FP64 moment sums.
+
+Prints one JSON line (rank 0).  Metric: cell-direction-group updates/s of
+whole hot-path passes, with the intensity resident in HBM (inputs far larger
+than L2: 8.6 GB per intensity copy, so no L2 flush is needed).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per GPU, launched by torchrun; the
+single-GPU method has no exchange step), timed with a barrier on both sides
+and the maximum over ranks.  --impl reference times the FP64 CPU oracle on
+the host cores instead (bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_FP32 = 4
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nx", type=int, default=0, help="override cells per axis (profiling cases)")
+    ap.add_argument("--groups", type=int, default=0, help="override the group count")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2504_21784_gb300 import workloads as W
+    cfg = W.multigroup_2d()
+    if args.nx or args.groups:
+        cfg = cfg.resized(args.nx or cfg.nx, n_groups=args.groups or None)
+        cfg.name = f"multigroup2d_{cfg.nx}x{cfg.ny}x{cfg.n_dir}x{cfg.n_groups}"
+    return cfg
+
+
+def algorithmic_bytes(cfg, prec: int) -> dict:
+    """Minimal HBM traffic of one sweep-kernel launch: read I^k and write I
+    (4 nodes each per update), read the emission (4 nodes) and sigma~, sigma
+    once per (cell, group), write the 36 per-cell moment sums once."""
+    rs = prec // 8
+    upd = cfg.updates
+    per_update = 2 * 4 * rs
+    src = cfg.n_cells * cfg.n_groups * (4 + 2) * rs
+    mom = cfg.n_cells * 36 * rs
+    total = upd * per_update + src + mom
+    return {"per_update": total / upd, "per_launch": total, "updates": upd}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic(prec: int, cfg=None):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"sweep2d_multigroup2d_fp{prec}_traffic.json")
+    src = os.path.join(ROOT, "paper_2504_21784_gb300", "csrc", "sm_sweep.cu")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if rec.get("sm_sweep_cu_sha256") != h:
+        return None
+    if cfg is not None and rec.get("workload") not in (None, cfg.name):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(cfg, budget_s: float = 8.0):
+    """Time the FP64 oracle sweep, as it stands, on the host cores over a
+    bounded sample of (direction, group) pairs of the same workload."""
+    import numpy as np
+    import oracle as O
+    from paper_2504_21784_gb300 import workloads as W
+    T = W.temperature_wave(cfg)
+    s = W.scale_field(cfg)
+    sig = O.opacity(cfg.opacity_kind, cfg.opacity_alpha, cfg.edges, T, s)
+    q = O.emission(cfg.edges, cfg.a, cfg.c, T, sig)
+    omx, omy, w = O.quadrature(2, cfg.n_polar, cfg.n_azim)
+    infl = O.inflow(cfg.edges, cfg.a, cfg.c, cfg.T_bdr)
+    inv = 1.0 / (cfg.c * cfg.dt)
+    rng = np.random.default_rng(0)
+    allpairs = [(d, g) for d in range(cfg.n_dir) for g in range(cfg.n_groups)]
+    cores = O.num_threads()
+    cal = [allpairs[i] for i in rng.choice(len(allpairs), size=min(2 * cores, 64), replace=False)]
+    t0 = time.perf_counter()
+    O.sweep_pairs(2, cfg.nx, cfg.ny, cfg.extent, omx, omy, sig, inv, q, None, infl, cal)
+    t_cal = time.perf_counter() - t0
+    n = int(max(len(cal), min(len(allpairs), len(cal) * budget_s / max(t_cal, 1e-3))))
+    n = max(cores, (n // cores) * cores)
+    sample = [allpairs[i] for i in rng.choice(len(allpairs), size=n, replace=False)]
+    t0 = time.perf_counter()
+    O.sweep_pairs(2, cfg.nx, cfg.ny, cfg.extent, omx, omy, sig, inv, q, None, infl, sample)
+    dt = time.perf_counter() - t0
+    upd = n * cfg.n_cells
+    return {"value": upd / dt, "unit": "cell-dir-group updates/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{n} random (direction, group) sweeps of the full {cfg.nx}x{cfg.ny} mesh "
+                      f"({upd} updates, {dt:.1f} s), FP64 oracle sweep only, OpenMP over pairs"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle on the host cores, same metric and workload."""
+    from paper_2504_21784_gb300 import workloads as W
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cfg = workload(args)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(cfg, budget_s=3.0)
+        if i >= args.warmup:
+            vals.append(r["value"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": "sweep cell-dir-group updates/s", "value": v,
+            "unit": "cell-dir-group updates/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": cfg.updates / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": cfg.name, "step": "bounded sample of oracle sweeps"},
+            "cpu_baseline": {"value": v, "unit": r["unit"], "cores": r["cores"],
+                             "kind": "oracle", "sample": r["sample"]},
+            "e2e": {"value": v, "unit": "cell-dir-group updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    import paper_2504_21784_gb300 as sm
+    from paper_2504_21784_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    cfg = workload(args)
+    prec = args.precision
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        prob = sm.Problem.from_config(cfg, prec, stream=stream)
+        T = torch.from_numpy(W.temperature_wave(cfg)).cuda()
+        scale = torch.from_numpy(W.scale_field(cfg)).cuda()
+        sigma = prob.opacity(T, scale)
+        I = [prob.empty_intensity(), prob.empty_intensity()]
+        mom = prob.new_moments()
+        clo = prob.new_closures()
+        prob.sweep(T, sigma, None, I[0], mom, clo)  # realistic I^k: one step of history
+        prob.synchronize()
+
+        def step(i):
+            prob.sweep(T, sigma, I[i % 2], I[(i + 1) % 2], mom, clo)
+
+        for i in range(args.warmup):
+            step(i)
+        prob.synchronize()
+        barrier()
+        prob.set_profiling(True)
+        n0 = prob.launch_count()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            time.sleep(0.3)
+            ev0.record(stream)
+            for i in range(args.steps):
+                step(i + args.warmup)
+            ev1.record(stream)
+            ev1.synchronize()
+        prob.synchronize()
+        barrier()
+        launches = prob.launch_count() - n0
+        ktimes = prob.kernel_times()
+        prob.set_profiling(False)
+        ms = ev0.elapsed_time(ev1) / args.steps
+        t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        ms = float(t_max.item())
+
+        # end to end through the host-buffer entry point
+        T_h = torch.from_numpy(W.temperature_wave(cfg)).pin_memory().numpy()
+        S_h = sigma.cpu().pin_memory().numpy()
+        M_h = torch.zeros(tuple(mom.shape), dtype=torch.float64).pin_memory().numpy()
+        C_h = torch.zeros(tuple(clo.shape), dtype=torch.float64).pin_memory().numpy()
+        e2e_steps = max(3, args.steps // 2)
+        prob.sweep_host(T_h, S_h, I[0], I[1], M_h, C_h)
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            prob.sweep_host(T_h, S_h, I[i % 2], I[(i + 1) % 2], M_h, C_h)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        t_e = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
+        e2e_s = float(t_e.item())
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    upd = cfg.updates
+    value = world * upd / (ms * 1e-3)
+    alg = algorithmic_bytes(cfg, prec)
+    sweep_ms = ktimes["sweep_ms"] / max(ktimes["count"], 1)
+    peak, peak_kind = measured_peaks()
+    achieved = alg["per_launch"] / (sweep_ms * 1e-3) / 1e9
+    clocks = clk.summary()
+    line = {
+        "metric": "sweep cell-dir-group updates/s",
+        "value": value,
+        "unit": "cell-dir-group updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec == 32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": cfg.name, "cells": cfg.n_cells, "directions": cfg.n_dir,
+                   "groups": cfg.n_groups,
+                   "step": "emission (FP64 Planck) + sweep with fused moments + FP64 "
+                           "moment reduction + closures",
+                   "sweep_precision": f"fp{prec}", "l2": "inputs larger than L2 "
+                   f"({prob.info['intensity_bytes'] / 1e9:.1f} GB per intensity copy)",
+                   "tiling": {k: prob.info[k] for k in ("tile_x", "warps_per_cta",
+                                                        "groups_per_warp", "n_chains",
+                                                        "n_strips")},
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "kernel_ms": {"emission": ktimes["emission_ms"] / max(ktimes["count"], 1),
+                      "sweep": sweep_ms,
+                      "reduce_closures": ktimes["reduce_ms"] / max(ktimes["count"], 1)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": recorded_traffic(prec, cfg),
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_per_update": alg["per_update"],
+                     "kernel": "sweep2d_kernel"},
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "e2e": {"value": world * upd / e2e_s, "unit": "cell-dir-group updates/s",
+                "h2d_bytes_per_step": int(T_h.nbytes + S_h.nbytes),
+                "d2h_bytes_per_step": int(M_h.nbytes + C_h.nbytes),
+                "api": "sm_sweep_host (host T, sigma in; moments, closures out)"},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

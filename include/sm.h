@@ -1,0 +1,213 @@
+/*
+ * sm.h -- C ABI of the GB300 (sm_103a) Second Moment thermal-radiative-transfer
+ * hot path: the lumped upwind-DG discrete-ordinates transport sweep over every
+ * direction and group, fused with the angular-moment reductions and the gray
+ * low-order closures of Olivier, Warsa & Park, "Efficient, Nonlinear Second
+ * Moment Methods for Multigroup Thermal Radiative Transfer" (arXiv 2504.21784).
+ *
+ * Conventions for every entry point
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *    library never frees them.  Pointers named *_host are host pointers.
+ *  - Every call is asynchronous on the problem's CUDA stream unless stated.
+ *    Device-side conditions (a wavefront wait that ran out of time) are
+ *    reported by sm_synchronize().
+ *  - No exception crosses the ABI.  A non-zero sm_status is returned and a
+ *    thread-local message is available from sm_last_error().
+ *  - All arrays are dense and C-ordered:
+ *      cell  = iy*nx + ix                      (1D: ny = 1)
+ *      node  = a + 2*b  (2D; a = x side, b = y side, 0 = low), node = a (1D);
+ *              nodes are the corners (Gauss-Lobatto points) of each cell
+ *      T_nodal[cell][node], sigma[g][cell], q[g][cell][node],
+ *      canonical intensity I[d][g][cell][node]
+ *    Direction order: 1D ascending Gauss-Legendre mu; 2D quadrant-major
+ *    (signs of (Omega_x, Omega_y): (+,+), (-,+), (-,-), (+,-)), then polar
+ *    cosine ascending, then azimuth.
+ *  - The intensity that persists between calls (I^k and the new I) lives in
+ *    an opaque packed layout of sm_problem_info.intensity_bytes bytes in the
+ *    sweep precision; convert with sm_pack_intensity / sm_unpack_intensity.
+ */
+#ifndef SM_TRT_H
+#define SM_TRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SM_OK = 0,
+    SM_ERR_INVALID_ARG = 1,    /* bad descriptor, size or pointer */
+    SM_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    SM_ERR_OOM = 3,            /* device allocation failed */
+    SM_ERR_NO_CONVERGENCE = 4, /* reserved for the iterative low-order solve */
+    SM_ERR_NONPHYSICAL = 5,    /* non-positive temperature or NaN input */
+    SM_ERR_TIMEOUT = 6,        /* a device wavefront wait exceeded its time limit */
+    SM_ERR_UNSUPPORTED = 7     /* valid but not implemented (e.g. a tile shape) */
+} sm_status;
+
+/* opacity models (Sec. 6.1 power law; Sec. 6.2 form alpha (1 - e^{-nu/T}) / nu^3) */
+enum { SM_OPACITY_POWER = 0, SM_OPACITY_LARSEN = 1 };
+
+typedef struct sm_problem sm_problem; /* opaque, owned by the library */
+
+/* Problem descriptor; every field is copied by sm_create_problem. */
+typedef struct {
+    int dim;                   /* 1 or 2 */
+    int nx, ny;                /* cells per axis (ny ignored in 1D) */
+    double x0, x1, y0, y1;     /* uniform structured mesh on [x0,x1] x [y0,y1] */
+    int n_groups;              /* G >= 1 */
+    const double *group_edges; /* host, G+1 ascending positive edges nu_1..nu_{G+1} */
+    int n_polar;               /* 1D: Gauss-Legendre order (even); 2D: polar cosines per octant */
+    int n_azim;                /* 2D: azimuths per octant (ignored in 1D) */
+    double a, c;               /* radiation constant, speed of light */
+    double dt;                 /* time step; <= 0 selects the steady operator (no 1/(c dt)) */
+    int opacity_kind;          /* SM_OPACITY_POWER or SM_OPACITY_LARSEN */
+    double opacity_alpha;      /* alpha of SM_OPACITY_LARSEN */
+    double T_bdr[4];           /* boundary temperature per side: left, right, bottom, top;
+                                  <= 0 means vacuum (zero inflow) */
+    int precision;             /* sweep arithmetic: 32 (FP32) or 64 (FP64) */
+    int groups_per_warp;       /* (d,g) slots per lane of a warp task: 1, 2, 4; 0 = auto */
+    int tile_x;                /* wavefront strip width in cells: 4, 8, 16, 32; 0 = auto */
+    int warps_per_cta;         /* warp tasks sharing one strip CTA: 1..16; 0 = auto */
+} sm_problem_desc;
+
+typedef struct {
+    int dim, nx, ny;
+    int n_dir, n_groups, n_cells, n_nodes;
+    int n_moments;             /* 9 in 2D, 5 in 1D (per node) */
+    int n_closures;            /* 11 in 2D, 7 in 1D (per node) */
+    int precision;
+    int dirs_per_quadrant;     /* padded to the lane mapping */
+    int groups_per_lane_row;   /* groups interleaved across the 32 lanes */
+    int groups_per_warp;       /* (d,g) slots per lane */
+    int n_groups_padded;
+    int n_warp_tasks;          /* per quadrant */
+    int tile_x, warps_per_cta, n_chains, n_strips;
+    size_t intensity_elems;    /* packed intensity elements (padding included) */
+    size_t intensity_bytes;
+    size_t workspace_bytes;    /* device scratch the library owns */
+    double alpha;              /* Eq. alpha: sum w |Omega.n| / sum w with S_N quadrature */
+} sm_problem_info;
+
+/* Create a problem: builds the S_N set (Sec. 2; Gauss-Legendre in 1D,
+ * square product set in 2D, weights summing to 4 pi), the group-edge tables
+ * and the lane mapping, and allocates the device workspace.  stream is a
+ * cudaStream_t (NULL = legacy default stream).  Errors: INVALID_ARG for an
+ * empty mesh, G < 1, non-ascending edges, an odd 1D order or an unsupported
+ * tile; OOM; CUDA. */
+sm_status sm_create_problem(const sm_problem_desc *desc, void *stream, sm_problem **out);
+
+/* Free the workspace and the problem.  NULL is accepted. */
+sm_status sm_destroy_problem(sm_problem *p);
+
+sm_status sm_get_info(const sm_problem *p, sm_problem_info *out);
+
+/* Rebind the CUDA stream used by subsequent calls. */
+sm_status sm_set_stream(sm_problem *p, void *stream);
+
+/* Change the wavefront strip width and warps per CTA (the packed intensity
+ * layout does not depend on them).  0 keeps the current value. */
+sm_status sm_set_tiling(sm_problem *p, int tile_x, int warps_per_cta);
+
+/* Copy the discrete ordinates {Omega_d, w_d} (Sec. 2) to host arrays of
+ * n_dir entries each in the canonical order (omy is all zero in 1D). */
+sm_status sm_get_quadrature(const sm_problem *p, double *omx_host, double *omy_host,
+                            double *w_host);
+
+/* Multigroup opacity sigma_{g,K} from the element-average temperature
+ * (Sec. 3, Rem. opacity): POWER: s_K Tbar^-3; LARSEN: s_K alpha
+ * (1 - e^{-E_g/Tbar}) / E_g^3 with E_g the geometric mean of the group's
+ * edges (Sec. 6.2).  T_nodal_dev[cell][node], scale_dev[cell] (s_K),
+ * sigma_dev[g][cell] out, all FP64. */
+sm_status sm_opacity(sm_problem *p, const double *T_nodal_dev, const double *scale_dev,
+                     double *sigma_dev);
+
+/* a1. Emission source q_{g,n} = sigma_g a c T_n^4 b_g(T_n) / 4 pi at every
+ * node (Eq. smm_be_transport, Eq. planck, lumped), b_g by the Planck series
+ * in FP64 with the lowest edge taken to 0 and the highest to infinity
+ * (sum_g b_g = 1).  Fills the internal source buffer used by the next sweep
+ * and the nodal Planck- and Rosseland-collapsed opacities sigma_P, sigma_F
+ * (Sec. 2) used by the closures.  q_dev[g][cell][node] (FP64) receives a
+ * copy when non-NULL.  A non-positive or non-finite temperature is recorded
+ * in the device status and reported by sm_synchronize() as NONPHYSICAL. */
+sm_status sm_emission(sm_problem *p, const double *T_nodal_dev, const double *sigma_dev,
+                      double *q_dev);
+
+/* One pass of the hot path (rows a1-a4):
+ *   a1 emission from T_nodal (as sm_emission);
+ *   a2 the lumped upwind DG cell solves of Eq. dgsn_transport for every
+ *      (direction, group) in wavefront order, sigma~ = sigma + 1/(c dt) and
+ *      the time-edge source I^k/(c dt) of Eq. smm_be_transport, isotropic
+ *      inflow B_g(T_bdr)/4 pi (Eq. transport BC);
+ *   a3 fused per-node moments summed over all (d,g):
+ *      2D [phi, Fx, Fy, Txx, Txy, Tyy, SE, SFx, SFy], 1D [phi, F, T, SE, SF]
+ *      with phi = sum w I (= c E), F = sum w Omega I, T = sum w (Omega Omega
+ *      - I/3) I (in-plane block), SE = sum_g sigma_g sum_d w I,
+ *      SF = sum_g sigma_g sum_d w Omega I (Sec. 2, Eqs. sigmaE and
+ *      additive_mg_correction numerators);
+ *   a4 closures (as sm_closures) when closures_dev is non-NULL.
+ * I_prev_dev: packed I^k (NULL: zero, i.e. no time-edge source).
+ * I_out_dev: packed new intensity (required; must not alias I_prev_dev).
+ * moments_dev[cell][node][n_moments] FP64 (may be NULL).
+ * closures_dev[cell][node][n_closures] FP64 (may be NULL). */
+sm_status sm_sweep(sm_problem *p, const double *T_nodal_dev, const double *sigma_dev,
+                   const void *I_prev_dev, void *I_out_dev, double *moments_dev,
+                   double *closures_dev);
+
+/* a4. Closures of the gray low-order system from moments (Sec. 2):
+ * sigma_E = SE/phi (Eq. sigmaE; sigma_P where phi = 0), sigma_F =
+ * sum r_g sigma_g / sum r_g (Eq. sigmaF), sigma_P = sum b_g sigma_g / sum b_g,
+ * additive correction sum_g (sigma_F - sigma_g) F_g = sigma_F F - SF
+ * (Eq. additive_mg_correction), with nodal spectra at T_nodal.
+ * Output per node: 2D [E, Fx, Fy, Txx, Txy, Tyy, sigE, sigF, sigP, Cx, Cy],
+ * 1D [E, F, T, sigE, sigF, sigP, C];  E = phi / c. */
+sm_status sm_closures(sm_problem *p, const double *moments_dev, const double *T_nodal_dev,
+                      const double *sigma_dev, double *closures_dev);
+
+/* End-to-end variant of sm_sweep for callers holding host buffers: copies
+ * T_nodal_host and sigma_host to the device, runs sm_sweep, copies moments
+ * and closures back to the host arrays (either may be NULL) and waits for
+ * completion.  Host buffers should be pinned for full copy bandwidth.  The
+ * intensity stays device resident (I_prev_dev, I_out_dev as in sm_sweep). */
+sm_status sm_sweep_host(sm_problem *p, const double *T_nodal_host, const double *sigma_host,
+                        const void *I_prev_dev, void *I_out_dev, double *moments_host,
+                        double *closures_host);
+
+/* Convert between the canonical FP64 layout I[d][g][cell][node] and the
+ * packed sweep layout (rounded to the sweep precision; padding slots are
+ * zeroed by pack and skipped by unpack). */
+sm_status sm_pack_intensity(sm_problem *p, const double *I_canon_dev, void *I_packed_dev);
+sm_status sm_unpack_intensity(sm_problem *p, const void *I_packed_dev, double *I_canon_dev);
+
+/* Wait for the problem's stream and report device-side status: SM_OK, or
+ * SM_ERR_TIMEOUT when a wavefront wait gave up (the sweep output is then
+ * invalid).  Clears the device status word. */
+sm_status sm_synchronize(sm_problem *p);
+
+/* Pick tile_x and warps_per_cta by timing each candidate on the given
+ * inputs with CUDA events (reps timed sweeps each after one warm-up); the
+ * fastest is kept.  Overwrites I_out_dev.  Synchronous. */
+sm_status sm_autotune(sm_problem *p, const double *T_nodal_dev, const double *sigma_dev,
+                      const void *I_prev_dev, void *I_out_dev, int reps);
+
+/* Kernel timing with CUDA events on the problem's stream.  While enabled,
+ * each sweep records (without any synchronization) events around its
+ * emission, sweep and reduction kernels, for up to 4096 sweeps;
+ * sm_get_kernel_times synchronizes and returns the summed milliseconds and
+ * the number of sweeps timed, then resets them.
+ * ms_host[0] = emission, [1] = sweep kernel, [2] = moment reduction/closures. */
+sm_status sm_set_profiling(sm_problem *p, int enable);
+sm_status sm_get_kernel_times(sm_problem *p, double *ms_host, int *count_host);
+
+/* Number of kernels this problem has launched since creation. */
+int64_t sm_launch_count(const sm_problem *p);
+
+const char *sm_last_error(void);
+const char *sm_status_string(sm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SM_TRT_H */

@@ -1,0 +1,30 @@
+/*
+ * sm_debug.h -- test hooks of the library (not needed by normal callers).
+ *
+ * They let a test drive the bounded-wait path of the wavefront sweep without
+ * any GPU fault: with skip_publish enabled, the first strip of every chain
+ * never releases its row counters, so every downstream wait runs into its
+ * time limit, records SM_ERR_TIMEOUT in the device status word and returns;
+ * sm_synchronize() then reports SM_ERR_TIMEOUT and the problem stays usable.
+ * The paper has no counterpart (its sweeps run on CPUs without such waits).
+ */
+#ifndef SM_TRT_DEBUG_H
+#define SM_TRT_DEBUG_H
+
+#include "sm.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Time limit of every wavefront wait of this problem, in nanoseconds
+ * (default 2e9).  INVALID_ARG for ns <= 0. */
+sm_status sm_debug_set_wait_limit_ns(sm_problem *p, long long ns);
+
+/* Non-zero: strip 0 of each chain withholds its row counters (see above). */
+sm_status sm_debug_skip_publish(sm_problem *p, int enable);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SM_TRT_DEBUG_H */

@@ -84,7 +84,7 @@ def _load():
             "orc_emission": (None, [_I, _PD, _D, _D, _I, _I, _PD, _PD, _PD]),
             "orc_inflow": (None, [_I, _PD, _D, _D, _PD, _PD]),
             "orc_sweep_pairs": (_I, [_I, _I, _I, _D, _D, _D, _D, _I, _PD, _PD, _I, _PD, _D,
-                                     _PD, _PD, _PD, _I, _PI, _PD, _I]),
+                                     _PD, _PD, _I, _PD, _I, _PI, _PD, _I]),
             "orc_moments": (None, [_I, _I, _I, _PD, _PD, _PD, _I, _PD, _PD, _PD]),
             "orc_closures": (None, [_I, _I, _I, _PD, _D, _PD, _PD, _PD, _PD]),
             "orc_alpha": (_D, [_I, _PD, _PD]),
@@ -207,19 +207,14 @@ def sweep_pairs(dim, nx, ny, extent, omx, omy, sigma, inv_cdt, q, I_prev, inflow
                 nthreads: int = 0):
     """Sweep the listed (d, g) pairs (all when ``pairs`` is None).
 
-    Returns I[pair][cell][node] (all: reshaped to [d][g][cell][node])."""
+    ``I_prev`` is [d][g][cell][node], or [pair][cell][node] for just the listed
+    pairs.  Returns I[pair][cell][node] (all: reshaped to [d][g][cell][node])."""
     lib = _load()
     omx, omy, sigma, q, inflow_ = map(_f64, (omx, omy, sigma, q, inflow_))
     G = sigma.shape[0]
     ncell = sigma.shape[1]
     nn = 2 if dim == 1 else 4
     nd = len(omx)
-    if I_prev is not None:
-        I_prev = _f64(I_prev)
-        assert I_prev.size == nd * G * ncell * nn
-        pprev = _p(I_prev)
-    else:
-        pprev = None
     if pairs is None:
         npair = nd * G
         ppairs = None
@@ -227,11 +222,21 @@ def sweep_pairs(dim, nx, ny, extent, omx, omy, sigma, inv_cdt, q, I_prev, inflow
         pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
         npair = pr.shape[0]
         ppairs = pr.ctypes.data_as(_PI)
+    per_pair = 0
+    if I_prev is not None:
+        I_prev = _f64(I_prev)
+        if pairs is not None and I_prev.size == npair * ncell * nn:
+            per_pair = 1  # I^k given only for the listed pairs
+        else:
+            assert I_prev.size == nd * G * ncell * nn
+        pprev = _p(I_prev)
+    else:
+        pprev = None
     out = np.zeros((npair, ncell, nn))
     x0, x1, y0, y1 = extent
     rc = lib.orc_sweep_pairs(dim, nx, ny if dim == 2 else 1, x0, x1, y0, y1, nd, _p(omx),
-                             _p(omy), G, _p(sigma), float(inv_cdt), _p(q), pprev, _p(inflow_),
-                             npair, ppairs, _p(out), int(nthreads))
+                             _p(omy), G, _p(sigma), float(inv_cdt), _p(q), pprev, per_pair,
+                             _p(inflow_), npair, ppairs, _p(out), int(nthreads))
     if rc:
         raise FloatingPointError("singular local system in oracle sweep")
     if pairs is None:

@@ -305,7 +305,14 @@ void orc_opacity(int kind, double alpha, int G, const double *edges, int ncell, 
 void orc_emission(int G, const double *edges, double a, double c, int ncell, int nnode,
                   const double *T_nodal, const double *sigma, double *q)
 {
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+    {
     double *b = (double *)malloc(sizeof(double) * (G > 0 ? G : 1));
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
     for (int k = 0; k < ncell; ++k) {
         for (int n = 0; n < nnode; ++n) {
             double T = T_nodal[k * nnode + n];
@@ -317,6 +324,7 @@ void orc_emission(int G, const double *edges, double a, double c, int ncell, int
         }
     }
     free(b);
+    }
 }
 
 /* Isotropic boundary inflow B_g(T_bdr)/4pi per side (Eq. transport BC);
@@ -522,15 +530,17 @@ static int orc_sweep_one(const orc_mesh *m, double Ox, double Oy, const double *
  *   sigma[g][cell]       multigroup opacity sigma_g (not sigma~)
  *   inv_cdt              1/(c dt); 0 gives the steady-state operator
  *   q[g][cell][node]     emission density
- *   I_prev[d][g][cell][node]  previous-time intensity I^k (NULL: zero)
+ *   I_prev               previous-time intensity I^k (NULL: zero), laid out
+ *                        [d][g][cell][node], or [pair][cell][node] when
+ *                        prev_per_pair is non-zero
  *   inflow[4][G]         boundary inflow per side and group
  *   out[pair][cell][node]
  * The time-edge source I^k/(c dt) and sigma~ = sigma + 1/(c dt) follow
  * Eq. smm_be_transport.  Returns 0, or -1 on a singular local system. */
 int orc_sweep_pairs(int dim, int nx, int ny, double x0, double x1, double y0, double y1,
                     int ndir, const double *omx, const double *omy, int G, const double *sigma,
-                    double inv_cdt, const double *q, const double *I_prev, const double *inflow,
-                    int npairs, const int *pairs, double *out, int nthreads)
+                    double inv_cdt, const double *q, const double *I_prev, int prev_per_pair,
+                    const double *inflow, int npairs, const int *pairs, double *out, int nthreads)
 {
     orc_mesh m;
     m.dim = dim;
@@ -554,7 +564,11 @@ int orc_sweep_pairs(int dim, int nx, int ny, double x0, double x1, double y0, do
         for (size_t k = 0; k < ncell; ++k) {
             sig_t[k] = sigma[(size_t)g * ncell + k] + inv_cdt;
             for (int n = 0; n < nn; ++n) {
-                double ip = I_prev ? I_prev[(((size_t)d * G + g) * ncell + k) * nn + n] : 0.0;
+                double ip = 0.0;
+                if (I_prev && prev_per_pair)
+                    ip = I_prev[((size_t)pi * ncell + k) * nn + n];
+                else if (I_prev)
+                    ip = I_prev[(((size_t)d * G + g) * ncell + k) * nn + n];
                 src[k * nn + n] = q[((size_t)g * ncell + k) * nn + n] + inv_cdt * ip;
             }
         }

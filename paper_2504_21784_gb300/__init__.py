@@ -1,0 +1,300 @@
+"""GB300 (sm_103a) Second Moment TRT hot path: Python binding of libsmtrt.so.
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels (``csrc/``), reached through the C ABI of ``include/sm.h``.  PyTorch
+supplies device memory and the CUDA stream.  There is no CPU fallback: if the
+library has not been built (``python -m paper_2504_21784_gb300.build`` or
+``__graft_entry__.build()``) every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsmtrt.so")
+
+SM_OK = 0
+STATUS = {0: "SM_OK", 1: "SM_ERR_INVALID_ARG", 2: "SM_ERR_CUDA", 3: "SM_ERR_OOM",
+          4: "SM_ERR_NO_CONVERGENCE", 5: "SM_ERR_NONPHYSICAL", 6: "SM_ERR_TIMEOUT",
+          7: "SM_ERR_UNSUPPORTED"}
+
+#: every symbol declared in include/sm.h and include/sm_debug.h
+EXPORTED = ["sm_create_problem", "sm_destroy_problem", "sm_get_info", "sm_set_stream",
+            "sm_set_tiling", "sm_get_quadrature", "sm_opacity", "sm_emission", "sm_sweep",
+            "sm_closures", "sm_sweep_host", "sm_pack_intensity", "sm_unpack_intensity",
+            "sm_synchronize", "sm_autotune", "sm_set_profiling", "sm_get_kernel_times",
+            "sm_launch_count", "sm_last_error", "sm_status_string",
+            "sm_debug_set_wait_limit_ns", "sm_debug_skip_publish"]
+
+
+class SMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double),
+                ("y1", ctypes.c_double), ("n_groups", ctypes.c_int),
+                ("group_edges", ctypes.POINTER(ctypes.c_double)), ("n_polar", ctypes.c_int),
+                ("n_azim", ctypes.c_int), ("a", ctypes.c_double), ("c", ctypes.c_double),
+                ("dt", ctypes.c_double), ("opacity_kind", ctypes.c_int),
+                ("opacity_alpha", ctypes.c_double), ("T_bdr", ctypes.c_double * 4),
+                ("precision", ctypes.c_int), ("groups_per_warp", ctypes.c_int),
+                ("tile_x", ctypes.c_int), ("warps_per_cta", ctypes.c_int)]
+
+
+class ProblemInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in (
+        "dim", "nx", "ny", "n_dir", "n_groups", "n_cells", "n_nodes", "n_moments", "n_closures",
+        "precision", "dirs_per_quadrant", "groups_per_lane_row", "groups_per_warp",
+        "n_groups_padded", "n_warp_tasks", "tile_x", "warps_per_cta", "n_chains", "n_strips")] + [
+        ("intensity_elems", ctypes.c_size_t), ("intensity_bytes", ctypes.c_size_t),
+        ("workspace_bytes", ctypes.c_size_t), ("alpha", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Load libsmtrt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
+                          "(python -m paper_2504_21784_gb300.build)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    D = ctypes.c_double
+    PD = ctypes.POINTER(ctypes.c_double)
+    sigs = {
+        "sm_create_problem": [ctypes.POINTER(ProblemDesc), P, ctypes.POINTER(P)],
+        "sm_destroy_problem": [P],
+        "sm_get_info": [P, ctypes.POINTER(ProblemInfo)],
+        "sm_set_stream": [P, P],
+        "sm_set_tiling": [P, I, I],
+        "sm_get_quadrature": [P, PD, PD, PD],
+        "sm_opacity": [P, P, P, P],
+        "sm_emission": [P, P, P, P],
+        "sm_sweep": [P, P, P, P, P, P, P],
+        "sm_closures": [P, P, P, P, P],
+        "sm_sweep_host": [P, P, P, P, P, P, P],
+        "sm_pack_intensity": [P, P, P],
+        "sm_unpack_intensity": [P, P, P],
+        "sm_synchronize": [P],
+        "sm_autotune": [P, P, P, P, P, I],
+        "sm_set_profiling": [P, I],
+        "sm_get_kernel_times": [P, PD, ctypes.POINTER(ctypes.c_int)],
+        "sm_debug_set_wait_limit_ns": [P, ctypes.c_longlong],
+        "sm_debug_skip_publish": [P, I],
+    }
+    for name, args in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.sm_launch_count.argtypes = [P]
+    lib.sm_launch_count.restype = ctypes.c_int64
+    lib.sm_last_error.argtypes = []
+    lib.sm_last_error.restype = ctypes.c_char_p
+    lib.sm_status_string.argtypes = [ctypes.c_int]
+    lib.sm_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != SM_OK:
+        raise SMError(code, load().sm_last_error().decode())
+
+
+def _ptr(t) -> Optional[int]:
+    """Device pointer of a torch tensor (None passes NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _hptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data
+
+
+class Problem:
+    """One SM transport problem on the current CUDA device."""
+
+    def __init__(self, dim: int, nx: int, ny: int, extent: Sequence[float], edges,
+                 n_polar: int, n_azim: int = 0, a: float = 1.0, c: float = 1.0,
+                 dt: float = 0.01, opacity_kind: int = 0, opacity_alpha: float = 0.0,
+                 T_bdr: Sequence[float] = (0.0, 0.0, 0.0, 0.0), precision: int = 32,
+                 groups_per_warp: int = 0, tile_x: int = 0, warps_per_cta: int = 0,
+                 stream=None):
+        import torch
+        lib = load()
+        self._torch = torch
+        self._edges = np.ascontiguousarray(np.asarray(edges, dtype=np.float64))
+        d = ProblemDesc()
+        d.dim, d.nx, d.ny = dim, nx, ny
+        d.x0, d.x1, d.y0, d.y1 = [float(v) for v in extent]
+        d.n_groups = len(self._edges) - 1
+        d.group_edges = self._edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.n_polar, d.n_azim = n_polar, n_azim
+        d.a, d.c, d.dt = a, c, dt
+        d.opacity_kind, d.opacity_alpha = opacity_kind, opacity_alpha
+        for i in range(4):
+            d.T_bdr[i] = float(T_bdr[i])
+        d.precision = precision
+        d.groups_per_warp, d.tile_x, d.warps_per_cta = groups_per_warp, tile_x, warps_per_cta
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        h = ctypes.c_void_p()
+        _check(lib.sm_create_problem(ctypes.byref(d), ctypes.c_void_p(stream.cuda_stream),
+                                     ctypes.byref(h)))
+        self._h = h
+        self.refresh_info()
+
+    @classmethod
+    def from_config(cls, cfg, precision: int = 32, **kw) -> "Problem":
+        return cls(cfg.dim, cfg.nx, cfg.ny, cfg.extent, cfg.edges, cfg.n_polar, cfg.n_azim,
+                   cfg.a, cfg.c, cfg.dt, cfg.opacity_kind, cfg.opacity_alpha, cfg.T_bdr,
+                   precision, **kw)
+
+    # ---------------------------------------------------------------- basics
+    def refresh_info(self):
+        info = ProblemInfo()
+        _check(load().sm_get_info(self._h, ctypes.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in ProblemInfo._fields_}
+        return self.info
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sm_destroy_problem(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def quadrature(self):
+        n = self.info["n_dir"]
+        ox, oy, w = np.zeros(n), np.zeros(n), np.zeros(n)
+        PD = ctypes.POINTER(ctypes.c_double)
+        _check(load().sm_get_quadrature(self._h, ox.ctypes.data_as(PD), oy.ctypes.data_as(PD),
+                                        w.ctypes.data_as(PD)))
+        return ox, oy, w
+
+    def set_tiling(self, tile_x: int = 0, warps_per_cta: int = 0):
+        _check(load().sm_set_tiling(self._h, tile_x, warps_per_cta))
+        self.refresh_info()
+
+    def set_stream(self, stream):
+        self._stream = stream
+        _check(load().sm_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)))
+
+    # ---------------------------------------------------------------- buffers
+    def empty_intensity(self):
+        """Device buffer for a packed intensity (I^k or the new I)."""
+        dt = self._torch.float32 if self.info["precision"] == 32 else self._torch.float64
+        return self._torch.zeros(self.info["intensity_elems"], dtype=dt, device="cuda")
+
+    def pack(self, I_canon):
+        out = self.empty_intensity()
+        _check(load().sm_pack_intensity(self._h, _ptr(I_canon), _ptr(out)))
+        return out
+
+    def unpack(self, I_packed):
+        i = self.info
+        out = self._torch.zeros((i["n_dir"], i["n_groups"], i["n_cells"], i["n_nodes"]),
+                                dtype=self._torch.float64, device="cuda")
+        _check(load().sm_unpack_intensity(self._h, _ptr(I_packed), _ptr(out)))
+        return out
+
+    # ---------------------------------------------------------------- hot path
+    def opacity(self, T, scale, out=None):
+        i = self.info
+        if out is None:
+            out = self._torch.empty((i["n_groups"], i["n_cells"]), dtype=self._torch.float64,
+                                    device="cuda")
+        _check(load().sm_opacity(self._h, _ptr(T), _ptr(scale), _ptr(out)))
+        return out
+
+    def emission(self, T, sigma, want_q: bool = True):
+        i = self.info
+        q = None
+        if want_q:
+            q = self._torch.empty((i["n_groups"], i["n_cells"], i["n_nodes"]),
+                                  dtype=self._torch.float64, device="cuda")
+        _check(load().sm_emission(self._h, _ptr(T), _ptr(sigma), _ptr(q)))
+        return q
+
+    def sweep(self, T, sigma, I_prev, I_out, moments=None, closures=None):
+        _check(load().sm_sweep(self._h, _ptr(T), _ptr(sigma), _ptr(I_prev), _ptr(I_out),
+                               _ptr(moments), _ptr(closures)))
+
+    def new_moments(self):
+        i = self.info
+        return self._torch.empty((i["n_cells"], i["n_nodes"], i["n_moments"]),
+                                 dtype=self._torch.float64, device="cuda")
+
+    def new_closures(self):
+        i = self.info
+        return self._torch.empty((i["n_cells"], i["n_nodes"], i["n_closures"]),
+                                 dtype=self._torch.float64, device="cuda")
+
+    def closures(self, moments, T, sigma, out=None):
+        if out is None:
+            out = self.new_closures()
+        _check(load().sm_closures(self._h, _ptr(moments), _ptr(T), _ptr(sigma), _ptr(out)))
+        return out
+
+    def sweep_host(self, T_host: np.ndarray, sigma_host: np.ndarray, I_prev, I_out,
+                   moments_host: Optional[np.ndarray], closures_host: Optional[np.ndarray]):
+        """End-to-end call with host input/output buffers (copies inside)."""
+        mp = _hptr(moments_host) if moments_host is not None else None
+        cp = _hptr(closures_host) if closures_host is not None else None
+        _check(load().sm_sweep_host(self._h, _hptr(T_host), _hptr(sigma_host), _ptr(I_prev),
+                                    _ptr(I_out), mp, cp))
+
+    def synchronize(self):
+        _check(load().sm_synchronize(self._h))
+
+    def autotune(self, T, sigma, I_prev, I_out, reps: int = 3):
+        _check(load().sm_autotune(self._h, _ptr(T), _ptr(sigma), _ptr(I_prev), _ptr(I_out),
+                                  reps))
+        self.refresh_info()
+
+    def set_profiling(self, on: bool):
+        _check(load().sm_set_profiling(self._h, 1 if on else 0))
+
+    def kernel_times(self):
+        ms = (ctypes.c_double * 3)()
+        n = ctypes.c_int()
+        _check(load().sm_get_kernel_times(self._h, ms, ctypes.byref(n)))
+        return {"emission_ms": ms[0], "sweep_ms": ms[1], "reduce_ms": ms[2], "count": n.value}
+
+    def launch_count(self) -> int:
+        return int(load().sm_launch_count(self._h))
+
+    # ---------------------------------------------------------------- test hooks
+    def debug_wait_limit_ns(self, ns: int):
+        _check(load().sm_debug_set_wait_limit_ns(self._h, int(ns)))
+
+    def debug_skip_publish(self, on: bool):
+        _check(load().sm_debug_skip_publish(self._h, 1 if on else 0))

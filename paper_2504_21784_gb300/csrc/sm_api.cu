@@ -1,0 +1,743 @@
+// Host implementation of the C ABI declared in include/sm.h: problem set-up
+// (S_N quadrature, lane mapping, workspace), launch orchestration of the hot
+// path (emission -> sweep -> reduction/closures), timing and status.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sm_internal.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+sm_status fail(sm_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+#define SM_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? SM_ERR_OOM : SM_ERR_CUDA,        \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));               \
+        }                                                                                  \
+    } while (0)
+
+// n-point Gauss-Legendre rule on [-1, 1] (ascending nodes): Newton's method on
+// P_n from the asymptotic initial guess cos(pi (4i+3)/(4n+2)), with P_n and
+// P_n' from the three-term recurrence in long double.
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int i = 0; i < n; ++i) {
+        long double z = cosl(pi * (4.0L * i + 3.0L) / (4.0L * n + 2.0L));
+        long double dp = 1.0L;
+        for (int it = 0; it < 60; ++it) {
+            long double p0 = 1.0L, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                long double p2 = ((2.0L * k - 1.0L) * z * p1 - (k - 1.0L) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) {
+                p1 = z;
+                p0 = 1.0L;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0L);
+            long double dz = p1 / dp;
+            z -= dz;
+            if (fabsl(dz) < 1e-19L) break;
+        }
+        long double p0 = 1.0L, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            long double p2 = ((2.0L * k - 1.0L) * z * p1 - (k - 1.0L) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        if (n == 1) {
+            p1 = z;
+            p0 = 1.0L;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0L);
+        x[n - 1 - i] = (double)z;
+        w[n - 1 - i] = (double)(2.0L / ((1.0L - z * z) * dp * dp));
+    }
+}
+
+int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+template <typename T>
+sm_status dev_alloc(T **ptr, size_t bytes, size_t *acc) {
+    if (*ptr) {
+        cudaFree(*ptr);
+        *ptr = nullptr;
+    }
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc((void **)ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? SM_ERR_OOM : SM_ERR_CUDA,
+                    std::string("cudaMalloc(") + std::to_string(bytes) + "): " +
+                        cudaGetErrorString(e));
+    }
+    if (acc) *acc += bytes;
+    return SM_OK;
+}
+
+void free_all(sm_problem *p) {
+    void *bufs[] = {p->d_edges, p->d_inflow, p->d_lanes, p->d_dir_of, p->d_Q,
+                    p->d_SG, p->d_gray, p->d_part, p->d_face, p->d_flags,
+                    p->d_ctrl, p->d_mom_tmp, p->d_T_tmp, p->d_sig_tmp, p->d_clo_tmp};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    for (auto &e : p->ev_pool)
+        if (e) cudaEventDestroy(e);
+    p->ev_pool.clear();
+}
+
+constexpr int MAX_TIMED_SWEEPS = 4096;
+
+// Events of the n-th timed sweep (created on first use).
+cudaEvent_t *timing_events(sm_problem *p, int n) {
+    if (n >= MAX_TIMED_SWEEPS) return nullptr;
+    while ((int)p->ev_pool.size() < 4 * (n + 1)) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        p->ev_pool.push_back(e);
+    }
+    return &p->ev_pool[4 * n];
+}
+
+size_t n_part_sets(const sm_problem *p) {
+    return p->dim == 1 ? (size_t)p->NQ * p->NWT : (size_t)p->NCH;
+}
+
+// (Re)allocate the tiling-dependent workspace for tile_x / warps_per_cta.
+sm_status apply_tiling(sm_problem *p, int TX, int W) {
+    if (p->dim == 1) {
+        p->TX = p->nx;
+        p->W = 1;
+        p->NS = 1;
+        p->CPQ = p->NWT;
+        p->NCH = p->NQ * p->NWT;
+    } else {
+        if (TX < 1 || TX > 64) return fail(SM_ERR_INVALID_ARG, "tile_x must be in 1..64");
+        if (W < 1 || W > 16) return fail(SM_ERR_INVALID_ARG, "warps_per_cta must be in 1..16");
+        W = std::min(W, p->NWT);
+        const int old_TX = p->TX, old_W = p->W;
+        p->TX = TX;
+        p->W = W;
+        size_t smem = 0;
+        if (smk::sweep2d_max_resident(p, W, &smem) <= 0) {
+            p->TX = old_TX;
+            p->W = old_W;
+            return fail(SM_ERR_UNSUPPORTED, "tiling needs " + std::to_string(smem) +
+                                                " B of shared memory per CTA (too much)");
+        }
+        p->NS = (p->nx + TX - 1) / TX;
+        p->CPQ = (p->NWT + W - 1) / W;
+        p->NCH = p->NQ * p->CPQ;
+    }
+    const size_t nsets = n_part_sets(p);
+    const size_t part_bytes = nsets * (size_t)p->ncell * p->nn * p->nm * p->rsize;
+    if (nsets != p->part_sets || !p->d_part) {
+        sm_status st = dev_alloc(&p->d_part, part_bytes, nullptr);
+        if (st) return st;
+        p->part_sets = nsets;
+    }
+    if (p->dim == 2) {
+        const size_t fb = (size_t)p->NCH * p->NS * p->ny * p->W * p->GW * 32 * 2 * p->rsize;
+        if (fb != p->face_bytes || !p->d_face) {
+            sm_status st = dev_alloc(&p->d_face, fb, nullptr);
+            if (st) return st;
+            p->face_bytes = fb;
+        }
+        const size_t nf = (size_t)p->NCH * p->NS;
+        if (nf != p->flags_count || !p->d_flags) {
+            sm_status st = dev_alloc(&p->d_flags, nf * sizeof(unsigned long long), nullptr);
+            if (st) return st;
+            SM_CUDA(cudaMemset(p->d_flags, 0, nf * sizeof(unsigned long long)));
+            p->flags_count = nf;
+        }
+    }
+    p->workspace_bytes = (size_t)p->Gp * p->ncell * p->nn * p->rsize +      // Q
+                         (size_t)p->Gp * p->ncell * 2 * p->rsize +          // SG
+                         (size_t)p->ncell * p->nn * 2 * 8 +                 // gray
+                         part_bytes + p->face_bytes + p->flags_count * 8 +  // sweep scratch
+                         (size_t)p->ncell * p->nn * (p->nm + p->nc + 1) * 8 +  // staging
+                         (size_t)p->G * p->ncell * 8;
+    return SM_OK;
+}
+
+smk::SweepArgs make_args(const sm_problem *p, const void *I_prev, void *I_out) {
+    smk::SweepArgs a;
+    a.nx = p->nx;
+    a.ny = p->ny;
+    a.ncell = p->ncell;
+    a.NQ = p->NQ;
+    a.NWT = p->NWT;
+    a.NGB = p->NGB;
+    a.DB = p->DB;
+    a.LG = p->LG;
+    a.GW = p->GW;
+    a.Gp = p->Gp;
+    a.W = p->W;
+    a.NS = p->NS;
+    a.TX = p->TX;
+    a.CPQ = p->CPQ;
+    a.NCH = p->NCH;
+    a.n_tasks = p->NS * p->NCH;
+    a.inv_cdt = p->inv_cdt;
+    a.lanes = p->d_lanes;
+    a.Q = p->d_Q;
+    a.SG = p->d_SG;
+    a.inflow = p->d_inflow;
+    a.I_prev = I_prev;
+    a.I_out = I_out;
+    a.part = p->d_part;
+    a.face = p->d_face;
+    a.flags = p->d_flags;
+    a.ctrl = p->d_ctrl;
+    a.epoch = p->epoch;
+    a.timeout_ns = p->timeout_ns;
+    a.fault_skip_publish = p->fault_skip_publish;
+    return a;
+}
+
+sm_status check_ptr(const void *ptr, const char *name) {
+    if (!ptr) return fail(SM_ERR_INVALID_ARG, std::string(name) + " is NULL");
+    return SM_OK;
+}
+
+// The hot path without argument checks: emission, sweep, reduction.
+sm_status run_sweep(sm_problem *p, const double *T, const double *sigma, const void *I_prev,
+                    void *I_out, double *mom, double *clo) {
+    cudaStream_t s = p->stream;
+    cudaEvent_t *ev = p->profiling ? timing_events(p, p->n_timed) : nullptr;
+    if (ev) SM_CUDA(cudaEventRecord(ev[0], s));
+    SM_CUDA(smk::launch_emission(p, T, sigma, nullptr, s));
+    p->launches++;
+    if (ev) SM_CUDA(cudaEventRecord(ev[1], s));
+    ++p->epoch;
+    smk::SweepArgs a = make_args(p, I_prev, I_out);
+    if (p->dim == 2) {
+        SM_CUDA(cudaMemsetAsync(p->d_ctrl, 0, 2 * sizeof(unsigned int), s));
+        size_t smem = 0;
+        const int resident = smk::sweep2d_max_resident(p, p->W, &smem);
+        if (resident <= 0) return fail(SM_ERR_UNSUPPORTED, "sweep tiling does not fit");
+        const int grid = std::min(a.n_tasks, resident);
+        SM_CUDA(smk::launch_sweep2d(p, a, grid, s));
+    } else {
+        SM_CUDA(smk::launch_sweep1d(p, a, s));
+    }
+    p->launches++;
+    if (ev) SM_CUDA(cudaEventRecord(ev[2], s));
+    double *m = mom ? mom : p->d_mom_tmp;
+    SM_CUDA(smk::launch_reduce(p, (int)n_part_sets(p), m, clo, s));
+    p->launches++;
+    if (ev) {
+        SM_CUDA(cudaEventRecord(ev[3], s));
+        p->n_timed++;
+    }
+    return SM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sm_last_error(void) { return g_err.c_str(); }
+
+const char *sm_status_string(sm_status s) {
+    switch (s) {
+        case SM_OK: return "SM_OK";
+        case SM_ERR_INVALID_ARG: return "SM_ERR_INVALID_ARG";
+        case SM_ERR_CUDA: return "SM_ERR_CUDA";
+        case SM_ERR_OOM: return "SM_ERR_OOM";
+        case SM_ERR_NO_CONVERGENCE: return "SM_ERR_NO_CONVERGENCE";
+        case SM_ERR_NONPHYSICAL: return "SM_ERR_NONPHYSICAL";
+        case SM_ERR_TIMEOUT: return "SM_ERR_TIMEOUT";
+        case SM_ERR_UNSUPPORTED: return "SM_ERR_UNSUPPORTED";
+    }
+    return "SM_ERR_UNKNOWN";
+}
+
+sm_status sm_create_problem(const sm_problem_desc *d, void *stream, sm_problem **out) {
+    if (!d || !out) return fail(SM_ERR_INVALID_ARG, "desc and out must be non-NULL");
+    *out = nullptr;
+    if (d->dim != 1 && d->dim != 2) return fail(SM_ERR_INVALID_ARG, "dim must be 1 or 2");
+    if (d->nx < 1 || (d->dim == 2 && d->ny < 1))
+        return fail(SM_ERR_INVALID_ARG, "empty mesh: nx and ny must be >= 1");
+    if ((long long)d->nx * (d->dim == 2 ? d->ny : 1) > (1LL << 30))
+        return fail(SM_ERR_INVALID_ARG, "mesh too large (more than 2^30 cells)");
+    if (!(d->x1 > d->x0) || (d->dim == 2 && !(d->y1 > d->y0)))
+        return fail(SM_ERR_INVALID_ARG, "domain extent must be positive");
+    if (d->n_groups < 1 || !d->group_edges)
+        return fail(SM_ERR_INVALID_ARG, "n_groups must be >= 1 with group_edges");
+    for (int g = 0; g <= d->n_groups; ++g) {
+        if (!(d->group_edges[g] > 0.0) || !std::isfinite(d->group_edges[g]))
+            return fail(SM_ERR_INVALID_ARG, "group edges must be positive and finite");
+        if (g > 0 && !(d->group_edges[g] > d->group_edges[g - 1]))
+            return fail(SM_ERR_INVALID_ARG, "group edges must be ascending");
+    }
+    if (d->dim == 1 && (d->n_polar < 2 || d->n_polar % 2))
+        return fail(SM_ERR_INVALID_ARG, "1D quadrature order must be even and >= 2");
+    if (d->dim == 2 && (d->n_polar < 1 || d->n_azim < 1))
+        return fail(SM_ERR_INVALID_ARG, "2D quadrature needs n_polar, n_azim >= 1");
+    if (!(d->a > 0.0) || !(d->c > 0.0)) return fail(SM_ERR_INVALID_ARG, "a and c must be > 0");
+    if (d->precision != 32 && d->precision != 64)
+        return fail(SM_ERR_INVALID_ARG, "precision must be 32 or 64");
+    if (d->opacity_kind != SM_OPACITY_POWER && d->opacity_kind != SM_OPACITY_LARSEN)
+        return fail(SM_ERR_INVALID_ARG, "unknown opacity_kind");
+    if (d->groups_per_warp != 0 && d->groups_per_warp != 1 && d->groups_per_warp != 2 &&
+        d->groups_per_warp != 4)
+        return fail(SM_ERR_INVALID_ARG, "groups_per_warp must be 0, 1, 2 or 4");
+    if (d->tile_x < 0 || d->tile_x > 64) return fail(SM_ERR_INVALID_ARG, "tile_x out of range");
+    if (d->warps_per_cta < 0 || d->warps_per_cta > 16)
+        return fail(SM_ERR_INVALID_ARG, "warps_per_cta out of range");
+
+    smk::planck_upload_tables();
+    sm_problem *p = new sm_problem();
+    p->desc = *d;
+    p->edges.assign(d->group_edges, d->group_edges + d->n_groups + 1);
+    p->desc.group_edges = p->edges.data();
+    p->dim = d->dim;
+    p->nx = d->nx;
+    p->ny = d->dim == 2 ? d->ny : 1;
+    p->ncell = p->nx * p->ny;
+    p->nn = d->dim == 2 ? 4 : 2;
+    p->nm = d->dim == 2 ? 9 : 5;
+    p->nc = d->dim == 2 ? 11 : 7;
+    p->G = d->n_groups;
+    p->NQ = d->dim == 2 ? 4 : 2;
+    p->hx = (d->x1 - d->x0) / p->nx;
+    p->hy = d->dim == 2 ? (d->y1 - d->y0) / p->ny : 1.0;
+    p->inv_cdt = d->dt > 0.0 ? 1.0 / (d->c * d->dt) : 0.0;
+    p->prec = d->precision;
+    p->rsize = p->prec == 32 ? 4 : 8;
+    p->stream = (cudaStream_t)stream;
+
+    // ---- quadrature in canonical order
+    const double PI = 3.14159265358979323846;
+    if (p->dim == 1) {
+        std::vector<double> x, w;
+        gauss_legendre(d->n_polar, x, w);
+        p->nd = d->n_polar;
+        p->omx = x;
+        p->omy.assign(p->nd, 0.0);
+        p->w.resize(p->nd);
+        for (int i = 0; i < p->nd; ++i) p->w[i] = 2.0 * PI * w[i];
+        p->DQ = p->nd / 2;
+    } else {
+        std::vector<double> x, w;
+        gauss_legendre(2 * d->n_polar, x, w);
+        const int np = d->n_polar, na = d->n_azim;
+        p->nd = 4 * np * na;
+        p->DQ = np * na;
+        const int sgx[4] = {1, -1, -1, 1}, sgy[4] = {1, 1, -1, -1};
+        for (int q = 0; q < 4; ++q)
+            for (int ip = 0; ip < np; ++ip) {
+                const double xi = x[np + ip], wp = w[np + ip];
+                const double st = std::sqrt(1.0 - xi * xi);
+                for (int ia = 0; ia < na; ++ia) {
+                    const double phi = (ia + 0.5) * (0.5 * PI) / na;
+                    p->omx.push_back(sgx[q] * st * std::cos(phi));
+                    p->omy.push_back(sgy[q] * st * std::sin(phi));
+                    p->w.push_back(2.0 * wp * (0.5 * PI) / na);
+                }
+            }
+    }
+    {
+        double sa = 0, sw = 0;
+        for (int i = 0; i < p->nd; ++i) {
+            sa += p->w[i] * std::fabs(p->omx[i]);
+            sw += p->w[i];
+        }
+        p->alpha = sa / sw;
+    }
+
+    // ---- lane mapping
+    p->DQP = p->DQ <= 32 ? next_pow2(p->DQ) : ((p->DQ + 31) / 32) * 32;
+    p->DQL = std::min(p->DQP, 32);
+    p->LG = 32 / p->DQL;
+    p->DB = p->DQP / p->DQL;
+    int GW = d->groups_per_warp;
+    if (GW == 0) {
+        const int gpl = (p->G + p->LG - 1) / p->LG;  // slots per lane if GW were unlimited
+        GW = gpl >= 16 ? 2 : 1;
+    }
+    p->GW = GW;
+    p->GSLOT = GW * p->LG;
+    p->Gp = ((p->G + p->GSLOT - 1) / p->GSLOT) * p->GSLOT;
+    p->NGB = p->Gp / p->GSLOT;
+    p->NWT = p->DB * p->NGB;
+
+    std::vector<smk::LaneConst> lanes((size_t)p->NQ * p->DB * 32);
+    std::vector<int> dir_of(lanes.size(), -1);
+    for (int q = 0; q < p->NQ; ++q)
+        for (int db = 0; db < p->DB; ++db)
+            for (int lane = 0; lane < 32; ++lane) {
+                smk::LaneConst &L = lanes[(q * p->DB + db) * 32 + lane];
+                std::memset(&L, 0, sizeof(L));
+                const int dq = db * p->DQL + (lane % p->DQL);  // direction inside the quadrant
+                L.g_lo = lane / p->DQL;
+                int d_can = -1;
+                if (dq < p->DQ) {
+                    if (p->dim == 2) {
+                        d_can = q * p->DQ + dq;
+                    } else {
+                        // 1D "quadrants": q = 0 -> mu > 0 (upper half of the GL nodes),
+                        // q = 1 -> mu < 0 (lower half)
+                        d_can = (q == 0) ? p->DQ + dq : dq;
+                    }
+                }
+                // padding lanes reuse a valid direction with zero weight
+                const int ds = d_can >= 0 ? d_can : (p->dim == 2 ? q * p->DQ : (q == 0 ? p->DQ : 0));
+                const double ox = p->omx[ds], oy = p->omy[ds];
+                const double wt = d_can >= 0 ? p->w[ds] : 0.0;
+                L.mu = std::fabs(ox) / p->hx;
+                L.eta = p->dim == 2 ? std::fabs(oy) / p->hy : 0.0;
+                if (p->dim == 2) {
+                    L.wm[0] = wt;
+                    L.wm[1] = wt * ox;
+                    L.wm[2] = wt * oy;
+                    L.wm[3] = wt * (ox * ox - 1.0 / 3.0);
+                    L.wm[4] = wt * ox * oy;
+                    L.wm[5] = wt * (oy * oy - 1.0 / 3.0);
+                } else {
+                    L.wm[0] = wt;
+                    L.wm[1] = wt * ox;
+                    L.wm[2] = wt * (ox * ox - 1.0 / 3.0);
+                }
+                L.valid = d_can >= 0;
+                dir_of[(q * p->DB + db) * 32 + lane] = d_can;
+            }
+
+    // ---- allocations
+    sm_status st;
+    size_t acc = 0;
+#define SM_TRY(x)            \
+    do {                     \
+        st = (x);            \
+        if (st) {            \
+            free_all(p);     \
+            delete p;        \
+            return st;       \
+        }                    \
+    } while (0)
+    SM_TRY(dev_alloc(&p->d_edges, sizeof(double) * (p->G + 1), &acc));
+    SM_TRY(dev_alloc(&p->d_inflow, 4 * (size_t)p->Gp * p->rsize, &acc));
+    SM_TRY(dev_alloc(&p->d_lanes, sizeof(smk::LaneConst) * lanes.size(), &acc));
+    SM_TRY(dev_alloc(&p->d_dir_of, sizeof(int) * dir_of.size(), &acc));
+    SM_TRY(dev_alloc(&p->d_Q, (size_t)p->Gp * p->ncell * p->nn * p->rsize, &acc));
+    SM_TRY(dev_alloc(&p->d_SG, (size_t)p->Gp * p->ncell * 2 * p->rsize, &acc));
+    SM_TRY(dev_alloc(&p->d_gray, (size_t)p->ncell * p->nn * 2 * sizeof(double), &acc));
+    SM_TRY(dev_alloc(&p->d_ctrl, smk::CTRL_WORDS * sizeof(unsigned int), &acc));
+    SM_TRY(dev_alloc(&p->d_mom_tmp, (size_t)p->ncell * p->nn * p->nm * sizeof(double), &acc));
+    SM_TRY(dev_alloc(&p->d_clo_tmp, (size_t)p->ncell * p->nn * p->nc * sizeof(double), &acc));
+    SM_TRY(dev_alloc(&p->d_T_tmp, (size_t)p->ncell * p->nn * sizeof(double), &acc));
+    SM_TRY(dev_alloc(&p->d_sig_tmp, (size_t)p->G * p->ncell * sizeof(double), &acc));
+    auto cuda_try = [&](cudaError_t e, const char *what) -> sm_status {
+        if (e == cudaSuccess) return SM_OK;
+        return fail(SM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    SM_TRY(cuda_try(cudaMemcpy(p->d_edges, p->edges.data(), sizeof(double) * (p->G + 1),
+                               cudaMemcpyHostToDevice), "edges"));
+    SM_TRY(cuda_try(cudaMemcpy(p->d_lanes, lanes.data(), sizeof(smk::LaneConst) * lanes.size(),
+                               cudaMemcpyHostToDevice), "lanes"));
+    SM_TRY(cuda_try(cudaMemcpy(p->d_dir_of, dir_of.data(), sizeof(int) * dir_of.size(),
+                               cudaMemcpyHostToDevice), "dir_of"));
+    SM_TRY(cuda_try(cudaMemset(p->d_ctrl, 0, smk::CTRL_WORDS * sizeof(unsigned int)), "ctrl"));
+    SM_TRY(cuda_try(smk::launch_inflow(p, p->stream), "inflow"));
+    p->launches++;
+
+    // ---- tiling
+    if (p->dim == 2) {
+        int TX = d->tile_x, W = d->warps_per_cta;
+        if (W == 0) W = std::min(p->prec == 32 ? 8 : 4, p->NWT);
+        if (TX == 0) TX = p->nx >= 128 ? 16 : 8;
+        st = apply_tiling(p, TX, W);
+        if (st && d->tile_x == 0 && d->warps_per_cta == 0) {
+            // fall back to the smallest footprint before giving up
+            st = apply_tiling(p, 4, 1);
+        }
+        if (st) {
+            free_all(p);
+            delete p;
+            return st;
+        }
+    } else {
+        SM_TRY(apply_tiling(p, 0, 0));
+    }
+    SM_TRY(cuda_try(cudaStreamSynchronize(p->stream), "create sync"));
+#undef SM_TRY
+    *out = p;
+    return SM_OK;
+}
+
+sm_status sm_destroy_problem(sm_problem *p) {
+    if (!p) return SM_OK;
+    cudaStreamSynchronize(p->stream);
+    free_all(p);
+    delete p;
+    return SM_OK;
+}
+
+sm_status sm_get_info(const sm_problem *p, sm_problem_info *o) {
+    if (!p || !o) return fail(SM_ERR_INVALID_ARG, "NULL argument");
+    std::memset(o, 0, sizeof(*o));
+    o->dim = p->dim;
+    o->nx = p->nx;
+    o->ny = p->ny;
+    o->n_dir = p->nd;
+    o->n_groups = p->G;
+    o->n_cells = p->ncell;
+    o->n_nodes = p->nn;
+    o->n_moments = p->nm;
+    o->n_closures = p->nc;
+    o->precision = p->prec;
+    o->dirs_per_quadrant = p->DQP;
+    o->groups_per_lane_row = p->LG;
+    o->groups_per_warp = p->GW;
+    o->n_groups_padded = p->Gp;
+    o->n_warp_tasks = p->NWT;
+    o->tile_x = p->TX;
+    o->warps_per_cta = p->W;
+    o->n_chains = p->NCH;
+    o->n_strips = p->NS;
+    o->intensity_elems = (size_t)p->NQ * p->NWT * p->ncell * p->GW * 32 * p->nn;
+    o->intensity_bytes = o->intensity_elems * p->rsize;
+    o->workspace_bytes = p->workspace_bytes;
+    o->alpha = p->alpha;
+    return SM_OK;
+}
+
+sm_status sm_set_stream(sm_problem *p, void *stream) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    p->stream = (cudaStream_t)stream;
+    return SM_OK;
+}
+
+sm_status sm_set_tiling(sm_problem *p, int tile_x, int warps_per_cta) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    if (p->dim == 1) return SM_OK;
+    SM_CUDA(cudaStreamSynchronize(p->stream));
+    return apply_tiling(p, tile_x > 0 ? tile_x : p->TX, warps_per_cta > 0 ? warps_per_cta : p->W);
+}
+
+sm_status sm_get_quadrature(const sm_problem *p, double *omx, double *omy, double *w) {
+    if (!p || !omx || !omy || !w) return fail(SM_ERR_INVALID_ARG, "NULL argument");
+    std::copy(p->omx.begin(), p->omx.end(), omx);
+    std::copy(p->omy.begin(), p->omy.end(), omy);
+    std::copy(p->w.begin(), p->w.end(), w);
+    return SM_OK;
+}
+
+sm_status sm_opacity(sm_problem *p, const double *T, const double *scale, double *sigma) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    sm_status st;
+    if ((st = check_ptr(T, "T_nodal_dev")) || (st = check_ptr(scale, "scale_dev")) ||
+        (st = check_ptr(sigma, "sigma_dev")))
+        return st;
+    SM_CUDA(smk::launch_opacity(p, T, scale, sigma, p->stream));
+    p->launches++;
+    return SM_OK;
+}
+
+sm_status sm_emission(sm_problem *p, const double *T, const double *sigma, double *q) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    sm_status st;
+    if ((st = check_ptr(T, "T_nodal_dev")) || (st = check_ptr(sigma, "sigma_dev"))) return st;
+    SM_CUDA(smk::launch_emission(p, T, sigma, q, p->stream));
+    p->launches++;
+    return SM_OK;
+}
+
+sm_status sm_sweep(sm_problem *p, const double *T, const double *sigma, const void *I_prev,
+                   void *I_out, double *mom, double *clo) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    sm_status st;
+    if ((st = check_ptr(T, "T_nodal_dev")) || (st = check_ptr(sigma, "sigma_dev")) ||
+        (st = check_ptr(I_out, "I_out_dev")))
+        return st;
+    if (I_prev == I_out) return fail(SM_ERR_INVALID_ARG, "I_prev_dev must not alias I_out_dev");
+    return run_sweep(p, T, sigma, I_prev, I_out, mom, clo);
+}
+
+sm_status sm_closures(sm_problem *p, const double *mom, const double *T, const double *sigma,
+                      double *clo) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    sm_status st;
+    if ((st = check_ptr(mom, "moments_dev")) || (st = check_ptr(T, "T_nodal_dev")) ||
+        (st = check_ptr(sigma, "sigma_dev")) || (st = check_ptr(clo, "closures_dev")))
+        return st;
+    SM_CUDA(smk::launch_closures_from_T(p, mom, T, sigma, clo, p->stream));
+    p->launches++;
+    return SM_OK;
+}
+
+sm_status sm_sweep_host(sm_problem *p, const double *T_host, const double *sigma_host,
+                        const void *I_prev, void *I_out, double *mom_host, double *clo_host) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    sm_status st;
+    if ((st = check_ptr(T_host, "T_nodal_host")) || (st = check_ptr(sigma_host, "sigma_host")) ||
+        (st = check_ptr(I_out, "I_out_dev")))
+        return st;
+    if (I_prev == I_out) return fail(SM_ERR_INVALID_ARG, "I_prev_dev must not alias I_out_dev");
+    cudaStream_t s = p->stream;
+    const size_t tb = (size_t)p->ncell * p->nn * sizeof(double);
+    const size_t sb = (size_t)p->G * p->ncell * sizeof(double);
+    SM_CUDA(cudaMemcpyAsync(p->d_T_tmp, T_host, tb, cudaMemcpyHostToDevice, s));
+    SM_CUDA(cudaMemcpyAsync(p->d_sig_tmp, sigma_host, sb, cudaMemcpyHostToDevice, s));
+    st = run_sweep(p, p->d_T_tmp, p->d_sig_tmp, I_prev, I_out, p->d_mom_tmp,
+                   clo_host ? p->d_clo_tmp : nullptr);
+    if (st) return st;
+    if (mom_host)
+        SM_CUDA(cudaMemcpyAsync(mom_host, p->d_mom_tmp,
+                                (size_t)p->ncell * p->nn * p->nm * sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+    if (clo_host)
+        SM_CUDA(cudaMemcpyAsync(clo_host, p->d_clo_tmp,
+                                (size_t)p->ncell * p->nn * p->nc * sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+    return sm_synchronize(p);
+}
+
+sm_status sm_pack_intensity(sm_problem *p, const double *canon, void *packed) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    sm_status st;
+    if ((st = check_ptr(canon, "I_canon_dev")) || (st = check_ptr(packed, "I_packed_dev")))
+        return st;
+    SM_CUDA(smk::launch_pack(p, canon, packed, 0, p->stream));
+    p->launches++;
+    return SM_OK;
+}
+
+sm_status sm_unpack_intensity(sm_problem *p, const void *packed, double *canon) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    sm_status st;
+    if ((st = check_ptr(canon, "I_canon_dev")) || (st = check_ptr(packed, "I_packed_dev")))
+        return st;
+    SM_CUDA(smk::launch_pack(p, canon, const_cast<void *>(packed), 1, p->stream));
+    p->launches++;
+    return SM_OK;
+}
+
+sm_status sm_synchronize(sm_problem *p) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    SM_CUDA(cudaStreamSynchronize(p->stream));
+    unsigned int ctrl[smk::CTRL_WORDS];
+    SM_CUDA(cudaMemcpy(ctrl, p->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost));
+    const unsigned int status = ctrl[smk::CTRL_STATUS];
+    if (status) {
+        SM_CUDA(cudaMemset(p->d_ctrl + smk::CTRL_STATUS, 0, sizeof(unsigned int)));
+        if (status & smk::ST_TIMEOUT)
+            return fail(SM_ERR_TIMEOUT, "a wavefront wait exceeded its time limit");
+        return fail(SM_ERR_NONPHYSICAL, "non-positive or non-finite temperature");
+    }
+    return SM_OK;
+}
+
+sm_status sm_set_profiling(sm_problem *p, int enable) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    SM_CUDA(cudaStreamSynchronize(p->stream));
+    p->profiling = enable != 0;
+    p->n_timed = 0;
+    return SM_OK;
+}
+
+sm_status sm_get_kernel_times(sm_problem *p, double *ms, int *count) {
+    if (!p || !ms || !count) return fail(SM_ERR_INVALID_ARG, "NULL argument");
+    SM_CUDA(cudaStreamSynchronize(p->stream));
+    ms[0] = ms[1] = ms[2] = 0.0;
+    for (int n = 0; n < p->n_timed; ++n) {
+        cudaEvent_t *ev = &p->ev_pool[4 * n];
+        for (int k = 0; k < 3; ++k) {
+            float t = 0.f;
+            SM_CUDA(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+            ms[k] += t;
+        }
+    }
+    *count = p->n_timed;
+    p->n_timed = 0;
+    return SM_OK;
+}
+
+int64_t sm_launch_count(const sm_problem *p) { return p ? p->launches : 0; }
+
+sm_status sm_autotune(sm_problem *p, const double *T, const double *sigma, const void *I_prev,
+                      void *I_out, int reps) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    sm_status st;
+    if ((st = check_ptr(T, "T_nodal_dev")) || (st = check_ptr(sigma, "sigma_dev")) ||
+        (st = check_ptr(I_out, "I_out_dev")))
+        return st;
+    if (p->dim == 1) return SM_OK;
+    if (reps < 1) reps = 3;
+    const int tx_c[] = {4, 8, 16, 32};
+    const int w_c[] = {1, 2, 4, 8, 16};
+    const int best0_tx = p->TX, best0_w = p->W;
+    int best_tx = best0_tx, best_w = best0_w;
+    float best_ms = 1e30f;
+    const bool prof = p->profiling;
+    p->profiling = false;
+    cudaEvent_t a, b;
+    SM_CUDA(cudaEventCreate(&a));
+    SM_CUDA(cudaEventCreate(&b));
+    for (int tx : tx_c) {
+        if (tx > 2 * p->nx && tx != 4) continue;
+        for (int w : w_c) {
+            if (w > p->NWT && w != 1) continue;
+            if (apply_tiling(p, tx, w) != SM_OK) continue;
+            st = run_sweep(p, T, sigma, I_prev, I_out, nullptr, nullptr);  // warm-up
+            if (st) break;
+            SM_CUDA(cudaEventRecord(a, p->stream));
+            for (int r = 0; r < reps && !st; ++r)
+                st = run_sweep(p, T, sigma, I_prev, I_out, nullptr, nullptr);
+            SM_CUDA(cudaEventRecord(b, p->stream));
+            SM_CUDA(cudaEventSynchronize(b));
+            float ms = 0;
+            SM_CUDA(cudaEventElapsedTime(&ms, a, b));
+            if (st == SM_OK && ms < best_ms) {
+                best_ms = ms;
+                best_tx = p->TX;
+                best_w = p->W;
+            }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    p->profiling = prof;
+    sm_status sync = sm_synchronize(p);
+    sm_status fin = apply_tiling(p, best_tx, best_w);
+    if (st) return st;
+    if (sync) return sync;
+    return fin;
+}
+
+// Test hooks (not part of the public header): shorten the wavefront wait
+// limit and make the first strip of every chain withhold its row counters,
+// so that a test can exercise the bounded-wait / status path without any
+// fault.  Both are host-side settings of this problem only.
+sm_status sm_debug_set_wait_limit_ns(sm_problem *p, long long ns) {
+    if (!p || ns <= 0) return fail(SM_ERR_INVALID_ARG, "bad argument");
+    p->timeout_ns = ns;
+    return SM_OK;
+}
+sm_status sm_debug_skip_publish(sm_problem *p, int enable) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    p->fault_skip_publish = enable != 0;
+    return SM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,120 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sm.h"
+#include "../../include/sm_debug.h"
+
+namespace smk {
+
+// ---------------------------------------------------------------------------
+// Per-lane direction constants of one warp task (quadrant, direction block).
+// mu = |Omega_x|/hx, eta = |Omega_y|/hy; wm = w * {1, Ox, Oy, Ox^2-1/3,
+// Ox*Oy, Oy^2-1/3} (1D: w * {1, mu, mu^2-1/3}); g_lo = group offset of the
+// lane inside a lane row; valid = 0 for padding lanes.
+struct LaneConst {
+    double mu, eta;
+    double wm[6];
+    int g_lo;
+    int valid;
+};
+
+// Device control block: [0] work-queue counter, [1] abort flag (both reset per
+// sweep launch), [2] sticky status bits (cleared by sm_synchronize).
+enum { CTRL_QUEUE = 0, CTRL_ABORT = 1, CTRL_STATUS = 2, CTRL_WORDS = 4 };
+// status bits written by kernels
+enum { ST_TIMEOUT = 1u, ST_NONPHYSICAL = 2u };
+
+struct SweepArgs {
+    int nx, ny, ncell;
+    int NQ, NWT, NGB, DB, LG, GW, Gp;
+    int W;            // warps per CTA
+    int NS, TX;       // strips, strip width
+    int CPQ, NCH;     // chains per quadrant, chains
+    int n_tasks;
+    double inv_cdt;
+    const LaneConst *lanes;  // [NQ][DB][32]
+    const void *Q;           // [Gp][cell][nn]  sweep precision
+    const void *SG;          // [Gp][cell][2]   {sigma~, sigma}
+    const void *inflow;      // [4][Gp]
+    const void *I_prev;      // packed or null
+    void *I_out;             // packed
+    void *part;              // [n_part][cell][nn*nm]
+    void *face;              // [NCH][NS][ny][W][GW][32][2]
+    unsigned long long *flags;  // [NCH][NS]
+    unsigned int *ctrl;
+    unsigned long long epoch;
+    long long timeout_ns;
+    int fault_skip_publish;  // test hook: strip 0 never publishes
+};
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_opacity(const sm_problem *p, const double *T, const double *scale,
+                           double *sigma, cudaStream_t s);
+cudaError_t launch_emission(const sm_problem *p, const double *T, const double *sigma,
+                            double *q_canon, cudaStream_t s);
+cudaError_t launch_inflow(const sm_problem *p, cudaStream_t s);
+cudaError_t launch_closures_from_T(const sm_problem *p, const double *mom, const double *T,
+                                   const double *sigma, double *out, cudaStream_t s);
+cudaError_t launch_sweep2d(const sm_problem *p, const SweepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_sweep1d(const sm_problem *p, const SweepArgs &a, cudaStream_t s);
+cudaError_t launch_reduce(const sm_problem *p, int n_part, double *mom, double *clo,
+                          cudaStream_t s);
+cudaError_t launch_pack(const sm_problem *p, const double *canon, void *packed, int unpack,
+                        cudaStream_t s);
+int sweep2d_max_resident(const sm_problem *p, int W, size_t *smem_out);
+size_t sweep2d_smem_bytes(int prec, int W, int GW, int TX);
+void planck_upload_tables(void);
+
+}  // namespace smk
+
+struct sm_problem {
+    // descriptor copy
+    sm_problem_desc desc;
+    std::vector<double> edges;
+    int dim, nx, ny, ncell, nn, nm, nc, G, nd, NQ;
+    double hx, hy, inv_cdt;
+    int prec;  // 32 or 64
+    size_t rsize;
+    // quadrature (canonical order)
+    std::vector<double> omx, omy, w;
+    double alpha;
+    // lane mapping
+    int DQ, DQP, DQL, LG, DB, GW, GSLOT, Gp, NGB, NWT;
+    // tiling
+    int TX, W, NS, CPQ, NCH;
+    // device buffers
+    double *d_edges = nullptr;      // [G+1]
+    void *d_inflow = nullptr;       // [4][Gp] sweep precision
+    smk::LaneConst *d_lanes = nullptr;
+    int *d_dir_of = nullptr;        // [NQ][DB][32] canonical direction (or -1)
+    void *d_Q = nullptr;
+    void *d_SG = nullptr;
+    double *d_gray = nullptr;       // [cell][node][2] sigma_P, sigma_F
+    void *d_part = nullptr;
+    size_t part_sets = 0;
+    void *d_face = nullptr;
+    size_t face_bytes = 0;
+    unsigned long long *d_flags = nullptr;
+    size_t flags_count = 0;
+    unsigned int *d_ctrl = nullptr;
+    double *d_mom_tmp = nullptr;
+    double *d_T_tmp = nullptr;      // host-input staging for sm_sweep_host
+    double *d_sig_tmp = nullptr;
+    double *d_clo_tmp = nullptr;
+    unsigned long long epoch = 0;
+    long long timeout_ns = 2000000000LL;
+    int fault_skip_publish = 0;
+    cudaStream_t stream = nullptr;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;  // 4 events per timed sweep, read back lazily
+    int n_timed = 0;
+    int64_t launches = 0;
+    size_t workspace_bytes = 0;
+};
+

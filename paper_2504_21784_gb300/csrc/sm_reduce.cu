@@ -1,0 +1,126 @@
+// Row a3 (final stage) and a4: sum the per-chain partial moments in FP64 in a
+// fixed order (deterministic) and form the gray low-order closures of Sec. 2
+// (Eqs. sigmaE, sigmaF, sigma_P, additive_mg_correction) from them and the
+// nodal spectra left by the emission pass.  Also the pack / unpack kernels
+// between the canonical intensity I[d][g][cell][node] and the sweep layout
+// [quadrant][warp task][cell][slot][lane][node].
+#include <algorithm>
+
+#include "sm_internal.cuh"
+
+namespace smk {
+
+template <typename RT>
+__global__ void reduce_kernel(int dim, int nnodes_total, int nm, int nsets, size_t set_stride,
+                              double inv_c, const RT *__restrict__ part,
+                              const double *__restrict__ gray, double *__restrict__ mom,
+                              double *__restrict__ clo) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;  // (cell, node)
+    if (t >= nnodes_total) return;
+    double acc[9];
+#pragma unroll
+    for (int m = 0; m < 9; ++m) acc[m] = 0.0;
+    const RT *pp = part + (size_t)t * nm;
+    for (int s = 0; s < nsets; ++s) {
+        const RT *ps = pp + (size_t)s * set_stride;
+        for (int m = 0; m < nm; ++m) acc[m] += (double)ps[m];
+    }
+    if (mom) {
+        for (int m = 0; m < nm; ++m) mom[(size_t)t * nm + m] = acc[m];
+    }
+    if (clo) {
+        const double sP = gray[(size_t)t * 2 + 0], sF = gray[(size_t)t * 2 + 1];
+        const double phi = acc[0];
+        if (dim == 1) {
+            double *o = clo + (size_t)t * 7;
+            o[0] = phi * inv_c;
+            o[1] = acc[1];
+            o[2] = acc[2];
+            o[3] = (phi != 0.0) ? acc[3] / phi : sP;
+            o[4] = sF;
+            o[5] = sP;
+            o[6] = sF * acc[1] - acc[4];
+        } else {
+            double *o = clo + (size_t)t * 11;
+            o[0] = phi * inv_c;
+            o[1] = acc[1];
+            o[2] = acc[2];
+            o[3] = acc[3];
+            o[4] = acc[4];
+            o[5] = acc[5];
+            o[6] = (phi != 0.0) ? acc[6] / phi : sP;
+            o[7] = sF;
+            o[8] = sP;
+            o[9] = sF * acc[1] - acc[7];
+            o[10] = sF * acc[2] - acc[8];
+        }
+    }
+}
+
+cudaError_t launch_reduce(const sm_problem *p, int n_part, double *mom, double *clo,
+                          cudaStream_t s) {
+    const int n = p->ncell * p->nn;
+    const int threads = 128;
+    const size_t stride = (size_t)n * p->nm;
+    const double inv_c = 1.0 / p->desc.c;
+    if (p->prec == 32)
+        reduce_kernel<float><<<(n + threads - 1) / threads, threads, 0, s>>>(
+            p->dim, n, p->nm, n_part, stride, inv_c, (const float *)p->d_part, p->d_gray, mom, clo);
+    else
+        reduce_kernel<double><<<(n + threads - 1) / threads, threads, 0, s>>>(
+            p->dim, n, p->nm, n_part, stride, inv_c, (const double *)p->d_part, p->d_gray, mom,
+            clo);
+    return cudaGetLastError();
+}
+
+template <typename RT>
+__global__ void pack_kernel(size_t total, int nn, int ncell, int GW, int NWT, int NGB, int LG,
+                            int DB, int G, const int *__restrict__ dir_of,
+                            const LaneConst *__restrict__ lanes, double *__restrict__ canon,
+                            RT *__restrict__ packed, int unpack) {
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        size_t e = idx;
+        const int node = (int)(e % nn);
+        e /= nn;
+        const int lane = (int)(e % 32);
+        e /= 32;
+        const int gw = (int)(e % GW);
+        e /= GW;
+        const int cell = (int)(e % ncell);
+        e /= ncell;
+        const int wt = (int)(e % NWT);
+        const int q = (int)(e / NWT);
+        const int db = wt / NGB, gb = wt - db * NGB;
+        const int li = (q * DB + db) * 32 + lane;
+        const int d = dir_of[li];
+        const int g = gb * GW * LG + gw * LG + lanes[li].g_lo;
+        const bool valid = d >= 0 && g < G;
+        const size_t ci = (((size_t)d * G + g) * ncell + cell) * nn + node;
+        if (!unpack) {
+            packed[idx] = valid ? (RT)canon[ci] : (RT)0;
+        } else if (valid) {
+            canon[ci] = (double)packed[idx];
+        }
+    }
+}
+
+cudaError_t launch_pack(const sm_problem *p, const double *canon, void *packed, int unpack,
+                        cudaStream_t s) {
+    const size_t total = (size_t)p->NQ * p->NWT * p->ncell * p->GW * 32 * p->nn;
+    const int threads = 256;
+    const int blocks = (int)std::min<size_t>((total + threads - 1) / threads, 65535 * 8);
+    if (p->prec == 32)
+        pack_kernel<float><<<blocks, threads, 0, s>>>(total, p->nn, p->ncell, p->GW, p->NWT, p->NGB,
+                                                      p->LG, p->DB, p->G, p->d_dir_of, p->d_lanes,
+                                                      const_cast<double *>(canon), (float *)packed,
+                                                      unpack);
+    else
+        pack_kernel<double><<<blocks, threads, 0, s>>>(total, p->nn, p->ncell, p->GW, p->NWT,
+                                                       p->NGB, p->LG, p->DB, p->G, p->d_dir_of,
+                                                       p->d_lanes, const_cast<double *>(canon),
+                                                       (double *)packed, unpack);
+    return cudaGetLastError();
+}
+
+}  // namespace smk

@@ -1,0 +1,90 @@
+"""Shared helpers for the GPU parity tests: build one case on both sides.
+
+The library gets its inputs as torch tensors; the oracle gets the same values
+as numpy arrays.  Nothing here computes any part of the method: the oracle
+computes every expected value."""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+import oracle as O
+from paper_2504_21784_gb300 import workloads as W
+
+
+def config(dim, nx, ny, G, npol, naz=0, kind=W.OPACITY_LARSEN, T_bdr=(1.0, 0.0, 0.0, 0.0),
+           dt=0.01, extent=(0.0, 1.0, 0.0, 1.0), name="case") -> W.Config:
+    edges = W.log_edges(G) if G > 1 else W.GRAY_EDGES.copy()
+    return W.Config(name, dim, nx, ny if dim == 2 else 1, extent, edges, npol, naz, kind,
+                    10.0 if kind == W.OPACITY_LARSEN else 0.0, T_bdr, dt=dt)
+
+
+def rel_err(got, ref, floor_frac):
+    """max |got - ref| / (|ref| + floor_frac * max|ref|)."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = np.abs(ref) + floor_frac * np.max(np.abs(ref))
+    return float(np.max(np.abs(got - ref) / scale))
+
+
+@dataclasses.dataclass
+class Case:
+    cfg: W.Config
+    prob: object
+    T: np.ndarray
+    scale: np.ndarray
+    sigma: np.ndarray        # oracle opacity, fed to both sides
+    I_prev: np.ndarray       # canonical, already rounded to the sweep precision
+    q: np.ndarray            # oracle emission
+    inflow: np.ndarray       # oracle inflow
+    omx: np.ndarray
+    omy: np.ndarray
+    w: np.ndarray
+
+
+def build_case(sm, cfg: W.Config, precision: int, seed: int = 0, with_prev: bool = True,
+               **tiling) -> Case:
+    import torch
+    prob = sm.Problem.from_config(cfg, precision, **tiling)
+    nn = cfg.n_nodes
+    T = W.temperature_wave(cfg, seed=seed + 1)
+    scale = W.scale_field(cfg, seed=seed + 7)
+    sigma = O.opacity(cfg.opacity_kind, cfg.opacity_alpha, cfg.edges, T, scale)
+    omx, omy, w = O.quadrature(cfg.dim, cfg.n_polar, cfg.n_azim)
+    I_prev = None
+    if with_prev:
+        Ic = W.intensity_random(cfg.n_dir, cfg.n_groups, cfg.n_cells, nn, seed=seed + 3,
+                                scale=0.05)
+        packed = prob.pack(torch.from_numpy(Ic).cuda())
+        I_prev = prob.unpack(packed).cpu().numpy()  # what the sweep really reads
+    q = O.emission(cfg.edges, cfg.a, cfg.c, T, sigma)
+    infl = O.inflow(cfg.edges, cfg.a, cfg.c, cfg.T_bdr)
+    return Case(cfg, prob, T, scale, sigma, I_prev, q, infl, omx, omy, w)
+
+
+def run_gpu(case: Case, want_closures=True):
+    import torch
+    prob = case.prob
+    Td = torch.from_numpy(case.T).cuda()
+    Sd = torch.from_numpy(case.sigma).cuda()
+    Ip = None
+    if case.I_prev is not None:
+        Ip = prob.pack(torch.from_numpy(case.I_prev).cuda())
+    Io = prob.empty_intensity()
+    mom = prob.new_moments()
+    clo = prob.new_closures() if want_closures else None
+    prob.sweep(Td, Sd, Ip, Io, mom, clo)
+    prob.synchronize()
+    I = prob.unpack(Io).cpu().numpy()
+    return I, mom.cpu().numpy(), (clo.cpu().numpy() if clo is not None else None), Io
+
+
+def run_oracle(case: Case):
+    cfg = case.cfg
+    inv_cdt = 1.0 / (cfg.c * cfg.dt) if cfg.dt > 0 else 0.0
+    I = O.sweep(cfg.dim, cfg.nx, cfg.ny, cfg.extent, case.omx, case.omy, case.sigma, inv_cdt,
+                case.q, case.I_prev, case.inflow)
+    mom = O.moments(cfg.dim, case.omx, case.omy, case.w, case.sigma, I)
+    clo = O.closures(cfg.dim, cfg.edges, cfg.c, case.sigma, case.T, mom)
+    return I, mom, clo

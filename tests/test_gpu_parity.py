@@ -1,0 +1,236 @@
+"""GPU parity: the CUDA hot path (through the C ABI) against the FP64 oracle,
+element by element, on seeded inputs that span several strips, several warp
+tasks, padded lanes and groups, and ragged strip tails.
+
+Tolerances (spec contract; derivation in the design doc):
+  FP64 sweep:  1e-11 relative      FP32 sweep:  1e-5 relative
+"Relative" is taken per field, as the paper reports errors relative to the
+magnitude of the reference: every element's error is divided by the largest
+magnitude of its field -- one (direction, group) slice of the intensity, one
+moment component (F and T are measured against phi, SF against SE, as they
+vanish near equilibrium).  Dividing by the element itself is meaningless at
+the nodes where the lumped-DG solution (no positivity fix-up) passes through
+zero.  sigma_E = SE/phi is compared weighted by phi for the same reason, the
+additive correction against sigma_F * phi.  Elementwise ratios are printed.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2504_21784_gb300 import workloads as W
+
+from _cases import build_case, config, rel_err, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = {64: 1e-11, 32: 1e-5}
+
+CASES_2D = {
+    # name: (config kwargs, tiling kwargs)
+    "ragged_lanes": (dict(nx=37, ny=21, G=5, npol=2, naz=3),
+                     dict(tile_x=8, warps_per_cta=2, groups_per_warp=1)),
+    "gw2_32dirs": (dict(nx=24, ny=19, G=12, npol=4, naz=8),
+                   dict(tile_x=8, warps_per_cta=4, groups_per_warp=2)),
+    "gw4_dirblocks": (dict(nx=17, ny=9, G=6, npol=4, naz=16),
+                      dict(tile_x=4, warps_per_cta=3, groups_per_warp=4)),
+    "gray_channel": (dict(nx=32, ny=32, G=1, npol=4, naz=8, kind=W.OPACITY_POWER),
+                     dict(tile_x=8, warps_per_cta=1, groups_per_warp=1)),
+    "single_cell": (dict(nx=1, ny=1, G=3, npol=1, naz=2, T_bdr=(1.0, 0.3, 0.5, 0.7)),
+                    dict(tile_x=4, warps_per_cta=1, groups_per_warp=1)),
+    "steady_allsides": (dict(nx=9, ny=14, G=4, npol=2, naz=4, dt=0.0,
+                             T_bdr=(1.0, 0.5, 0.25, 0.8)),
+                        dict(tile_x=4, warps_per_cta=2, groups_per_warp=2)),
+}
+
+CASES_1D = {
+    "marshak_s8": (dict(nx=200, ny=1, G=1, npol=8, kind=W.OPACITY_POWER), dict()),
+    "mg_s6_gw2": (dict(nx=53, ny=1, G=11, npol=6, T_bdr=(1.0, 0.4, 0, 0)),
+                  dict(groups_per_warp=2)),
+}
+
+
+def _field_err(got, ref, scale_field=None, axis=None):
+    """max |got - ref| / max|scale| (per slice along leading axes when axis given)."""
+    sc = ref if scale_field is None else scale_field
+    d = np.abs(np.asarray(got) - np.asarray(ref))
+    if axis is None:
+        return float(d.max() / max(np.abs(sc).max(), 1e-300))
+    red = tuple(range(axis, d.ndim))
+    return float(np.max(d.max(axis=red) / np.maximum(np.abs(sc).max(axis=red), 1e-300)))
+
+
+def parity_errors(case, gpu, ref):
+    Ig, mg, cg = gpu
+    Io, mo, co = ref
+    dim = case.cfg.dim
+    e = {}
+    e["I"] = _field_err(Ig, Io, axis=2)  # per (d, g) slice
+    e["I_elem"] = rel_err(Ig, Io, 1e-12)
+    if dim == 2:
+        phi, se = 0, 6
+        groups = {"phi": [0], "F,T": [1, 2, 3, 4, 5], "SE": [6], "SF": [7, 8]}
+        scale_of = {"phi": 0, "F,T": 0, "SE": 6, "SF": 6}
+        sE, sF, sP, corr, E_, vec = 6, 7, 8, [9, 10], 0, [1, 2, 3, 4, 5]
+    else:
+        phi, se = 0, 3
+        groups = {"phi": [0], "F,T": [1, 2], "SE": [3], "SF": [4]}
+        scale_of = {"phi": 0, "F,T": 0, "SE": 3, "SF": 3}
+        sE, sF, sP, corr, E_, vec = 3, 4, 5, [6], 0, [1, 2]
+    for name, ms in groups.items():
+        e["mom_" + name] = max(_field_err(mg[..., m], mo[..., m], mo[..., scale_of[name]])
+                               for m in ms)
+    e["clo_E"] = _field_err(cg[..., E_], co[..., E_])
+    e["clo_F,T"] = max(_field_err(cg[..., j], co[..., j], co[..., E_] * case.cfg.c) for j in vec)
+    e["clo_sigE"] = _field_err(cg[..., sE] * mo[..., phi], co[..., sE] * mo[..., phi],
+                               mo[..., se])
+    e["clo_sigF,P"] = max(rel_err(cg[..., j], co[..., j], 0.0) for j in (sF, sP))
+    e["clo_corr"] = max(_field_err(cg[..., j], co[..., j], co[..., sF] * mo[..., phi])
+                        for j in corr)
+    return e
+
+
+def _check_all(case, precision, label):
+    rtol = TOL[precision]
+    Ig, mg, cg, _ = run_gpu(case)
+    ref = run_oracle(case)
+    e = parity_errors(case, (Ig, mg, cg), ref)
+    print(f"[{label} fp{precision}] " + "  ".join(f"{k} {v:.2e}" for k, v in e.items()) +
+          f"  ({case.prob.info['n_chains']} chains x {case.prob.info['n_strips']} strips)")
+    bad = {k: v for k, v in e.items() if k != "I_elem" and not v <= rtol}
+    assert not bad, f"parity above {rtol}: {bad}"
+    return Ig
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("name", sorted(CASES_2D))
+def test_sweep_2d_parity(gpu_lib, name, precision):
+    ck, tk = CASES_2D[name]
+    cfg = config(2, **ck)
+    case = build_case(gpu_lib, cfg, precision, seed=sum(map(ord, name)) % 1000, **tk)
+    _check_all(case, precision, name)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("name", sorted(CASES_1D))
+def test_sweep_1d_parity(gpu_lib, name, precision):
+    ck, tk = CASES_1D[name]
+    cfg = config(1, **ck)
+    case = build_case(gpu_lib, cfg, precision, seed=5, **tk)
+    _check_all(case, precision, name)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_no_previous_intensity(gpu_lib, precision):
+    cfg = config(2, 20, 12, 3, 2, 4)
+    case = build_case(gpu_lib, cfg, precision, seed=9, with_prev=False, tile_x=8,
+                      warps_per_cta=2)
+    _check_all(case, precision, "no_prev")
+
+
+def test_quadrature_matches_oracle(gpu_lib):
+    for dim, npol, naz in [(1, 8, 0), (1, 6, 0), (2, 4, 8), (2, 2, 3), (2, 4, 16)]:
+        cfg = config(dim, 8, 8, 2, npol, naz)
+        prob = gpu_lib.Problem.from_config(cfg, 64)
+        ox, oy, w = prob.quadrature()
+        rx, ry, rw = O.quadrature(dim, npol, naz)
+        assert np.max(np.abs(ox - rx)) < 1e-15
+        assert np.max(np.abs(oy - ry)) < 1e-15
+        assert np.max(np.abs(w - rw)) < 1e-14
+        assert abs(prob.info["alpha"] - O.alpha(rx, rw)) < 1e-15
+
+
+@pytest.mark.parametrize("kind", [W.OPACITY_POWER, W.OPACITY_LARSEN])
+def test_opacity_matches_oracle(gpu_lib, kind):
+    import torch
+    cfg = config(2, 19, 7, 9, 2, 2, kind=kind)
+    prob = gpu_lib.Problem.from_config(cfg, 64)
+    T = W.temperature_random(cfg.n_cells, 4, seed=2)
+    s = W.scale_field(cfg, seed=3)
+    ref = O.opacity(kind, cfg.opacity_alpha, cfg.edges, T, s)
+    got = prob.opacity(torch.from_numpy(T).cuda(), torch.from_numpy(s).cuda()).cpu().numpy()
+    prob.synchronize()
+    assert rel_err(got, ref, 0.0) < 1e-13
+
+
+@pytest.mark.parametrize("G", [1, 7, 64])
+def test_emission_matches_oracle(gpu_lib, G):
+    import torch
+    cfg = config(2, 13, 11, G, 1, 1)
+    prob = gpu_lib.Problem.from_config(cfg, 64)
+    T = W.temperature_random(cfg.n_cells, 4, seed=G, lo=0.01, hi=3.0)
+    sig = O.opacity(cfg.opacity_kind, cfg.opacity_alpha, cfg.edges, T, np.ones(cfg.n_cells))
+    ref = O.emission(cfg.edges, cfg.a, cfg.c, T, sig)
+    got = prob.emission(torch.from_numpy(T).cuda(), torch.from_numpy(sig).cuda()).cpu().numpy()
+    prob.synchronize()
+    e = rel_err(got, ref, 1e-300)
+    print(f"emission G={G}: {e:.3e}")
+    assert e < 1e-12
+
+
+def test_tiling_does_not_change_intensity(gpu_lib):
+    """The per-(d,g) arithmetic is independent of the strip width and of the
+    warps per CTA: the intensity is bitwise identical, moments agree to the
+    reassociation of their sums."""
+    cfg = config(2, 40, 23, 8, 4, 8)
+    case = build_case(gpu_lib, cfg, 32, seed=4, tile_x=8, warps_per_cta=2, groups_per_warp=2)
+    I1, m1, _, _ = run_gpu(case)
+    for tx, wpc in [(4, 1), (16, 4), (32, 3)]:
+        case.prob.set_tiling(tx, wpc)
+        I2, m2, _, _ = run_gpu(case)
+        assert np.array_equal(I1, I2)
+        assert rel_err(m2[..., 0], m1[..., 0], 1e-6) < 1e-6
+
+
+def test_sweep_host_matches_device(gpu_lib):
+    import torch
+    cfg = config(2, 21, 17, 6, 2, 4)
+    case = build_case(gpu_lib, cfg, 32, seed=8, tile_x=8, warps_per_cta=2)
+    Ig, mg, cg, _ = run_gpu(case)
+    prob = case.prob
+    Ip = prob.pack(torch.from_numpy(case.I_prev).cuda())
+    Io = prob.empty_intensity()
+    mh = np.zeros((cfg.n_cells, 4, 9))
+    ch = np.zeros((cfg.n_cells, 4, 11))
+    prob.sweep_host(np.ascontiguousarray(case.T), np.ascontiguousarray(case.sigma), Ip, Io, mh, ch)
+    assert np.array_equal(mh, mg)
+    assert np.array_equal(ch, cg)
+    assert np.array_equal(prob.unpack(Io).cpu().numpy(), Ig)
+
+
+def test_pack_unpack_roundtrip(gpu_lib):
+    import torch
+    for prec in (32, 64):
+        cfg = config(2, 9, 5, 5, 2, 3)
+        prob = gpu_lib.Problem.from_config(cfg, prec, groups_per_warp=2)
+        I = W.intensity_random(cfg.n_dir, cfg.n_groups, cfg.n_cells, 4, seed=1)
+        back = prob.unpack(prob.pack(torch.from_numpy(I).cuda())).cpu().numpy()
+        if prec == 64:
+            assert np.array_equal(back, I)
+        else:
+            assert np.array_equal(back, I.astype(np.float32).astype(np.float64))
+
+
+def test_autotune_keeps_results(gpu_lib):
+    import torch
+    cfg = config(2, 48, 40, 8, 4, 8)
+    case = build_case(gpu_lib, cfg, 32, seed=6)
+    I1, m1, _, _ = run_gpu(case)
+    prob = case.prob
+    Td = torch.from_numpy(case.T).cuda()
+    Sd = torch.from_numpy(case.sigma).cuda()
+    Ip = prob.pack(torch.from_numpy(case.I_prev).cuda())
+    prob.autotune(Td, Sd, Ip, prob.empty_intensity(), reps=1)
+    I2, m2, _, _ = run_gpu(case)
+    assert np.array_equal(I1, I2)
+    assert rel_err(m2[..., 0], m1[..., 0], 1e-6) < 1e-6
+
+
+def test_launch_count_and_kernel_times(gpu_lib):
+    cfg = config(2, 16, 16, 4, 2, 2)
+    case = build_case(gpu_lib, cfg, 32, seed=2)
+    n0 = case.prob.launch_count()
+    case.prob.set_profiling(True)
+    run_gpu(case)
+    t = case.prob.kernel_times()
+    assert t["count"] == 1 and t["sweep_ms"] > 0
+    assert case.prob.launch_count() - n0 >= 3
