@@ -201,6 +201,39 @@ sm_status sm_autotune(sm_problem *p, const double *T_nodal_dev, const double *si
 sm_status sm_set_profiling(sm_problem *p, int enable);
 sm_status sm_get_kernel_times(sm_problem *p, double *ms_host, int *count_host);
 
+/* Allocation-free variant of sm_sweep for small 2D problems (the paper has
+ * no counterpart: it is a service to callers of this library).
+ *
+ * For callers that cannot call cudaMalloc -- a thread that must not block on
+ * the allocator or synchronize the device, a process whose device memory is
+ * fully reserved by another allocator, or an embedding with a fixed memory
+ * budget -- and therefore cannot use sm_create_problem, which allocates a
+ * workspace.  It runs the same pass as sm_sweep (emission, sweep with fused
+ * moments, moment sums and closures) for the problem described by desc
+ * (dim must be 2; tile fields are chosen internally), with every
+ * intermediate buffer in one static device array of 16 MiB that the library
+ * holds on every GPU that loads it, until the process exits.  It allocates
+ * nothing: no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Inputs and outputs are caller-owned device arrays in the canonical
+ * layouts: T_nodal_dev[cell][4], sigma_dev[g][cell], I_prev_canon_dev and
+ * I_out_canon_dev [d][g][cell][4] (FP64; I_prev may be NULL),
+ * moments_dev[cell][4][9] and closures_dev[cell][4][11] (either may be NULL).
+ * A problem whose scratch would exceed 16 MiB is rejected with
+ * SM_ERR_INVALID_ARG and a message giving the size it needs (for example,
+ * 32x32 cells x 32 directions x 8 groups in FP32 fits).
+ *
+ * The first call on a device (with that device current) looks up the
+ * array's device address with cudaGetSymbolAddress; make it before any
+ * stream capture.  The call is synchronous on stream (a cudaStream_t, NULL
+ * for the legacy default stream) and returns SM_ERR_TIMEOUT or
+ * SM_ERR_NONPHYSICAL like sm_synchronize.  All calls share the one array,
+ * which keeps the previous call's contents (the parts that must start at
+ * zero are cleared by each call): calls that overlap on the GPU race. */
+sm_status sm_sweep_static(const sm_problem_desc *desc, void *stream, const double *T_nodal_dev,
+                          const double *sigma_dev, const double *I_prev_canon_dev,
+                          double *I_out_canon_dev, double *moments_dev, double *closures_dev);
+
 /* Number of kernels this problem has launched since creation. */
 int64_t sm_launch_count(const sm_problem *p);
 

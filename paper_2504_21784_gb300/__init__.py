@@ -28,7 +28,7 @@ EXPORTED = ["sm_create_problem", "sm_destroy_problem", "sm_get_info", "sm_set_st
             "sm_closures", "sm_sweep_host", "sm_pack_intensity", "sm_unpack_intensity",
             "sm_synchronize", "sm_autotune", "sm_set_profiling", "sm_get_kernel_times",
             "sm_launch_count", "sm_last_error", "sm_status_string",
-            "sm_debug_set_wait_limit_ns", "sm_debug_skip_publish"]
+            "sm_debug_set_wait_limit_ns", "sm_debug_skip_publish", "sm_sweep_static"]
 
 
 class SMError(RuntimeError):
@@ -94,6 +94,7 @@ def load():
         "sm_get_kernel_times": [P, PD, ctypes.POINTER(ctypes.c_int)],
         "sm_debug_set_wait_limit_ns": [P, ctypes.c_longlong],
         "sm_debug_skip_publish": [P, I],
+        "sm_sweep_static": [ctypes.POINTER(ProblemDesc), P, P, P, P, P, P, P],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -298,3 +299,30 @@ class Problem:
 
     def debug_skip_publish(self, on: bool):
         _check(load().sm_debug_skip_publish(self._h, 1 if on else 0))
+
+
+def sweep_static(cfg, precision: int, T, sigma, I_prev, I_out, moments=None, closures=None,
+                 groups_per_warp: int = 0, stream=None):
+    """Allocation-free pass of the hot path (``sm_sweep_static``) for small 2D
+    problems: for callers that cannot allocate device memory.  All tensors are
+    caller-owned CUDA tensors in the canonical FP64 layouts (I_prev may be
+    None); the library uses its fixed 16 MiB device scratch array."""
+    import torch
+    edges = np.ascontiguousarray(np.asarray(cfg.edges, dtype=np.float64))
+    d = ProblemDesc()
+    d.dim, d.nx, d.ny = cfg.dim, cfg.nx, cfg.ny
+    d.x0, d.x1, d.y0, d.y1 = [float(v) for v in cfg.extent]
+    d.n_groups = len(edges) - 1
+    d.group_edges = edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.n_polar, d.n_azim = cfg.n_polar, cfg.n_azim
+    d.a, d.c, d.dt = cfg.a, cfg.c, cfg.dt
+    d.opacity_kind, d.opacity_alpha = cfg.opacity_kind, cfg.opacity_alpha
+    for i in range(4):
+        d.T_bdr[i] = float(cfg.T_bdr[i])
+    d.precision = precision
+    d.groups_per_warp = groups_per_warp
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(load().sm_sweep_static(ctypes.byref(d), ctypes.c_void_p(stream.cuda_stream), _ptr(T),
+                                  _ptr(sigma), _ptr(I_prev), _ptr(I_out), _ptr(moments),
+                                  _ptr(closures)))

@@ -254,6 +254,10 @@ sm_status run_sweep(sm_problem *p, const double *T, const double *sigma, const v
 
 }  // namespace
 
+namespace smk {
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace smk
+
 extern "C" {
 
 const char *sm_last_error(void) { return g_err.c_str(); }

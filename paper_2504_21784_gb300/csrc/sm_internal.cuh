@@ -70,6 +70,9 @@ cudaError_t launch_pack(const sm_problem *p, const double *canon, void *packed, 
 int sweep2d_max_resident(const sm_problem *p, int W, size_t *smem_out);
 size_t sweep2d_smem_bytes(int prec, int W, int GW, int TX);
 void planck_upload_tables(void);
+// Set the thread-local message returned by sm_last_error() (no allocation
+// beyond the message string of at most 255 characters).
+void set_last_error(const char *msg);
 
 }  // namespace smk
 
