@@ -321,8 +321,8 @@ def main():
                            "moment reduction + closures",
                    "sweep_precision": f"fp{prec}", "l2": "inputs larger than L2 "
                    f"({prob.info['intensity_bytes'] / 1e9:.1f} GB per intensity copy)",
-                   "tiling": {k: prob.info[k] for k in ("tile_x", "warps_per_cta",
-                                                        "groups_per_warp", "n_chains",
+                   "tiling": {k: prob.info[k] for k in ("strip_width", "prefetch_rows",
+                                                        "groups_per_warp", "n_tasks",
                                                         "n_strips")},
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "kernel_ms": {"emission": ktimes["emission_ms"] / max(ktimes["count"], 1),

@@ -69,8 +69,8 @@ typedef struct {
                                   <= 0 means vacuum (zero inflow) */
     int precision;             /* sweep arithmetic: 32 (FP32) or 64 (FP64) */
     int groups_per_warp;       /* (d,g) slots per lane of a warp task: 1, 2, 4; 0 = auto */
-    int tile_x;                /* wavefront strip width in cells: 4, 8, 16, 32; 0 = auto */
-    int warps_per_cta;         /* warp tasks sharing one strip CTA: 1..16; 0 = auto */
+    int strip_width;           /* 2D: cell columns per CTA, one warp per column, 1..16; 0 = auto */
+    int prefetch_rows;         /* 2D: rows each warp prefetches by TMA, 2..8; 0 = auto */
 } sm_problem_desc;
 
 typedef struct {
@@ -84,7 +84,7 @@ typedef struct {
     int groups_per_warp;       /* (d,g) slots per lane */
     int n_groups_padded;
     int n_warp_tasks;          /* per quadrant */
-    int tile_x, warps_per_cta, n_chains, n_strips;
+    int strip_width, prefetch_rows, n_tasks, n_strips;
     size_t intensity_elems;    /* packed intensity elements (padding included) */
     size_t intensity_bytes;
     size_t workspace_bytes;    /* device scratch the library owns */
@@ -107,9 +107,10 @@ sm_status sm_get_info(const sm_problem *p, sm_problem_info *out);
 /* Rebind the CUDA stream used by subsequent calls. */
 sm_status sm_set_stream(sm_problem *p, void *stream);
 
-/* Change the wavefront strip width and warps per CTA (the packed intensity
- * layout does not depend on them).  0 keeps the current value. */
-sm_status sm_set_tiling(sm_problem *p, int tile_x, int warps_per_cta);
+/* Change the 2D wavefront strip width (cell columns, one warp each, per CTA)
+ * and the TMA prefetch depth in rows (the packed intensity layout does not
+ * depend on them).  0 keeps the current value. */
+sm_status sm_set_tiling(sm_problem *p, int strip_width, int prefetch_rows);
 
 /* Copy the discrete ordinates {Omega_d, w_d} (Sec. 2) to host arrays of
  * n_dir entries each in the canonical order (omy is all zero in 1D). */
@@ -186,7 +187,7 @@ sm_status sm_unpack_intensity(sm_problem *p, const void *I_packed_dev, double *I
  * invalid).  Clears the device status word. */
 sm_status sm_synchronize(sm_problem *p);
 
-/* Pick tile_x and warps_per_cta by timing each candidate on the given
+/* Pick strip_width and prefetch_rows by timing each candidate on the given
  * inputs with CUDA events (reps timed sweeps each after one warm-up); the
  * fastest is kept.  Overwrites I_out_dev.  Synchronous. */
 sm_status sm_autotune(sm_problem *p, const double *T_nodal_dev, const double *sigma_dev,

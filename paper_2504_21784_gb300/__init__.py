@@ -46,14 +46,14 @@ class ProblemDesc(ctypes.Structure):
                 ("dt", ctypes.c_double), ("opacity_kind", ctypes.c_int),
                 ("opacity_alpha", ctypes.c_double), ("T_bdr", ctypes.c_double * 4),
                 ("precision", ctypes.c_int), ("groups_per_warp", ctypes.c_int),
-                ("tile_x", ctypes.c_int), ("warps_per_cta", ctypes.c_int)]
+                ("strip_width", ctypes.c_int), ("prefetch_rows", ctypes.c_int)]
 
 
 class ProblemInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in (
         "dim", "nx", "ny", "n_dir", "n_groups", "n_cells", "n_nodes", "n_moments", "n_closures",
         "precision", "dirs_per_quadrant", "groups_per_lane_row", "groups_per_warp",
-        "n_groups_padded", "n_warp_tasks", "tile_x", "warps_per_cta", "n_chains", "n_strips")] + [
+        "n_groups_padded", "n_warp_tasks", "strip_width", "prefetch_rows", "n_tasks", "n_strips")] + [
         ("intensity_elems", ctypes.c_size_t), ("intensity_bytes", ctypes.c_size_t),
         ("workspace_bytes", ctypes.c_size_t), ("alpha", ctypes.c_double)]
 
@@ -138,7 +138,7 @@ class Problem:
                  n_polar: int, n_azim: int = 0, a: float = 1.0, c: float = 1.0,
                  dt: float = 0.01, opacity_kind: int = 0, opacity_alpha: float = 0.0,
                  T_bdr: Sequence[float] = (0.0, 0.0, 0.0, 0.0), precision: int = 32,
-                 groups_per_warp: int = 0, tile_x: int = 0, warps_per_cta: int = 0,
+                 groups_per_warp: int = 0, strip_width: int = 0, prefetch_rows: int = 0,
                  stream=None):
         import torch
         lib = load()
@@ -155,7 +155,7 @@ class Problem:
         for i in range(4):
             d.T_bdr[i] = float(T_bdr[i])
         d.precision = precision
-        d.groups_per_warp, d.tile_x, d.warps_per_cta = groups_per_warp, tile_x, warps_per_cta
+        d.groups_per_warp, d.strip_width, d.prefetch_rows = groups_per_warp, strip_width, prefetch_rows
         if stream is None:
             stream = torch.cuda.current_stream()
         self._stream = stream
@@ -201,8 +201,8 @@ class Problem:
                                         w.ctypes.data_as(PD)))
         return ox, oy, w
 
-    def set_tiling(self, tile_x: int = 0, warps_per_cta: int = 0):
-        _check(load().sm_set_tiling(self._h, tile_x, warps_per_cta))
+    def set_tiling(self, strip_width: int = 0, prefetch_rows: int = 0):
+        _check(load().sm_set_tiling(self._h, strip_width, prefetch_rows))
         self.refresh_info()
 
     def set_stream(self, stream):

@@ -95,8 +95,8 @@ sm_status dev_alloc(T **ptr, size_t bytes, size_t *acc) {
 }
 
 void free_all(sm_problem *p) {
-    void *bufs[] = {p->d_edges, p->d_inflow, p->d_lanes, p->d_dir_of, p->d_Q,
-                    p->d_SG, p->d_gray, p->d_part, p->d_face, p->d_flags,
+    void *bufs[] = {p->d_edges, p->d_inflow, p->d_lanes, p->d_dir_of, p->d_src,
+                    p->d_mom_acc, p->d_gray, p->d_part, p->d_face, p->d_flags,
                     p->d_ctrl, p->d_mom_tmp, p->d_T_tmp, p->d_sig_tmp, p->d_clo_tmp};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -118,51 +118,42 @@ cudaEvent_t *timing_events(sm_problem *p, int n) {
     return &p->ev_pool[4 * n];
 }
 
-size_t n_part_sets(const sm_problem *p) {
-    return p->dim == 1 ? (size_t)p->NQ * p->NWT : (size_t)p->NCH;
-}
-
-// (Re)allocate the tiling-dependent workspace for tile_x / warps_per_cta.
-sm_status apply_tiling(sm_problem *p, int TX, int W) {
+// (Re)allocate the tiling-dependent workspace: W cell columns (= warps) per
+// CTA and S prefetched rows per warp for the 2D sweep.
+sm_status apply_tiling(sm_problem *p, int W, int S) {
     if (p->dim == 1) {
-        p->TX = p->nx;
         p->W = 1;
+        p->S = 0;
         p->NS = 1;
-        p->CPQ = p->NWT;
-        p->NCH = p->NQ * p->NWT;
+        const size_t pb = (size_t)p->NQ * p->NWT * p->ncell * p->nn * p->nm * p->rsize;
+        if (!p->d_part) {
+            sm_status st = dev_alloc(&p->d_part, pb, nullptr);
+            if (st) return st;
+        }
     } else {
-        if (TX < 1 || TX > 64) return fail(SM_ERR_INVALID_ARG, "tile_x must be in 1..64");
-        if (W < 1 || W > 16) return fail(SM_ERR_INVALID_ARG, "warps_per_cta must be in 1..16");
-        W = std::min(W, p->NWT);
-        const int old_TX = p->TX, old_W = p->W;
-        p->TX = TX;
+        if (W < 1 || W > 16) return fail(SM_ERR_INVALID_ARG, "strip_width must be in 1..16");
+        if (S < 2 || S > 8) return fail(SM_ERR_INVALID_ARG, "prefetch_rows must be in 2..8");
+        const int old_W = p->W, old_S = p->S;
         p->W = W;
+        p->S = S;
         size_t smem = 0;
-        if (smk::sweep2d_max_resident(p, W, &smem) <= 0) {
-            p->TX = old_TX;
+        const int resident = smk::sweep2d_max_resident(p, W, S, &smem);
+        if (resident <= 0) {
             p->W = old_W;
+            p->S = old_S;
             return fail(SM_ERR_UNSUPPORTED, "tiling needs " + std::to_string(smem) +
                                                 " B of shared memory per CTA (too much)");
         }
-        p->NS = (p->nx + TX - 1) / TX;
-        p->CPQ = (p->NWT + W - 1) / W;
-        p->NCH = p->NQ * p->CPQ;
-    }
-    const size_t nsets = n_part_sets(p);
-    const size_t part_bytes = nsets * (size_t)p->ncell * p->nn * p->nm * p->rsize;
-    if (nsets != p->part_sets || !p->d_part) {
-        sm_status st = dev_alloc(&p->d_part, part_bytes, nullptr);
-        if (st) return st;
-        p->part_sets = nsets;
-    }
-    if (p->dim == 2) {
-        const size_t fb = (size_t)p->NCH * p->NS * p->ny * p->W * p->GW * 32 * 2 * p->rsize;
+        p->resident = resident;
+        p->NS = (p->nx + W - 1) / W;
+        const size_t nwg = (size_t)p->NQ * p->NWT;
+        const size_t fb = nwg * p->NS * p->ny * p->GW * 32 * 2 * p->rsize;
         if (fb != p->face_bytes || !p->d_face) {
             sm_status st = dev_alloc(&p->d_face, fb, nullptr);
             if (st) return st;
             p->face_bytes = fb;
         }
-        const size_t nf = (size_t)p->NCH * p->NS;
+        const size_t nf = nwg * p->NS;
         if (nf != p->flags_count || !p->d_flags) {
             sm_status st = dev_alloc(&p->d_flags, nf * sizeof(unsigned long long), nullptr);
             if (st) return st;
@@ -170,10 +161,12 @@ sm_status apply_tiling(sm_problem *p, int TX, int W) {
             p->flags_count = nf;
         }
     }
-    p->workspace_bytes = (size_t)p->Gp * p->ncell * p->nn * p->rsize +      // Q
-                         (size_t)p->Gp * p->ncell * 2 * p->rsize +          // SG
-                         (size_t)p->ncell * p->nn * 2 * 8 +                 // gray
-                         part_bytes + p->face_bytes + p->flags_count * 8 +  // sweep scratch
+    const size_t mom_scratch = p->dim == 2
+                                   ? (size_t)p->ncell * 36 * p->rsize
+                                   : (size_t)p->NQ * p->NWT * p->ncell * p->nn * p->nm * p->rsize;
+    p->workspace_bytes = (size_t)p->Gp * p->ncell * 8 * p->rsize +         // source records
+                         (size_t)p->ncell * p->nn * 2 * 8 +                 // gray spectra
+                         mom_scratch + p->face_bytes + p->flags_count * 8 +  // sweep scratch
                          (size_t)p->ncell * p->nn * (p->nm + p->nc + 1) * 8 +  // staging
                          (size_t)p->G * p->ncell * 8;
     return SM_OK;
@@ -181,6 +174,7 @@ sm_status apply_tiling(sm_problem *p, int TX, int W) {
 
 smk::SweepArgs make_args(const sm_problem *p, const void *I_prev, void *I_out) {
     smk::SweepArgs a;
+    std::memset(&a, 0, sizeof(a));
     a.nx = p->nx;
     a.ny = p->ny;
     a.ncell = p->ncell;
@@ -192,19 +186,17 @@ smk::SweepArgs make_args(const sm_problem *p, const void *I_prev, void *I_out) {
     a.GW = p->GW;
     a.Gp = p->Gp;
     a.W = p->W;
+    a.S = p->S;
     a.NS = p->NS;
-    a.TX = p->TX;
-    a.CPQ = p->CPQ;
-    a.NCH = p->NCH;
-    a.n_tasks = p->NS * p->NCH;
+    a.n_tasks = p->NS * p->NQ * p->NWT;
     a.inv_cdt = p->inv_cdt;
     a.lanes = p->d_lanes;
-    a.Q = p->d_Q;
-    a.SG = p->d_SG;
+    a.src = p->d_src;
     a.inflow = p->d_inflow;
     a.I_prev = I_prev;
     a.I_out = I_out;
     a.part = p->d_part;
+    a.mom_acc = p->d_mom_acc;
     a.face = p->d_face;
     a.flags = p->d_flags;
     a.ctrl = p->d_ctrl;
@@ -216,6 +208,14 @@ smk::SweepArgs make_args(const sm_problem *p, const void *I_prev, void *I_out) {
 
 sm_status check_ptr(const void *ptr, const char *name) {
     if (!ptr) return fail(SM_ERR_INVALID_ARG, std::string(name) + " is NULL");
+    return SM_OK;
+}
+
+// The packed intensity is read by TMA bulk copies and written with 16-byte
+// vector stores: both buffers must start on a 16-byte boundary.
+sm_status check_intensity_align(const void *I_prev, const void *I_out) {
+    if ((reinterpret_cast<uintptr_t>(I_prev) & 15u) || (reinterpret_cast<uintptr_t>(I_out) & 15u))
+        return fail(SM_ERR_INVALID_ARG, "packed intensity buffers must be 16-byte aligned");
     return SM_OK;
 }
 
@@ -232,10 +232,8 @@ sm_status run_sweep(sm_problem *p, const double *T, const double *sigma, const v
     smk::SweepArgs a = make_args(p, I_prev, I_out);
     if (p->dim == 2) {
         SM_CUDA(cudaMemsetAsync(p->d_ctrl, 0, 2 * sizeof(unsigned int), s));
-        size_t smem = 0;
-        const int resident = smk::sweep2d_max_resident(p, p->W, &smem);
-        if (resident <= 0) return fail(SM_ERR_UNSUPPORTED, "sweep tiling does not fit");
-        const int grid = std::min(a.n_tasks, resident);
+        SM_CUDA(cudaMemsetAsync(p->d_mom_acc, 0, (size_t)p->ncell * 36 * p->rsize, s));
+        const int grid = std::min(a.n_tasks, p->resident);
         SM_CUDA(smk::launch_sweep2d(p, a, grid, s));
     } else {
         SM_CUDA(smk::launch_sweep1d(p, a, s));
@@ -243,7 +241,10 @@ sm_status run_sweep(sm_problem *p, const double *T, const double *sigma, const v
     p->launches++;
     if (ev) SM_CUDA(cudaEventRecord(ev[2], s));
     double *m = mom ? mom : p->d_mom_tmp;
-    SM_CUDA(smk::launch_reduce(p, (int)n_part_sets(p), m, clo, s));
+    if (p->dim == 2)
+        SM_CUDA(smk::launch_reduce(p, p->d_mom_acc, 1, m, clo, s));
+    else
+        SM_CUDA(smk::launch_reduce(p, p->d_part, p->NQ * p->NWT, m, clo, s));
     p->launches++;
     if (ev) {
         SM_CUDA(cudaEventRecord(ev[3], s));
@@ -306,9 +307,10 @@ sm_status sm_create_problem(const sm_problem_desc *d, void *stream, sm_problem *
     if (d->groups_per_warp != 0 && d->groups_per_warp != 1 && d->groups_per_warp != 2 &&
         d->groups_per_warp != 4)
         return fail(SM_ERR_INVALID_ARG, "groups_per_warp must be 0, 1, 2 or 4");
-    if (d->tile_x < 0 || d->tile_x > 64) return fail(SM_ERR_INVALID_ARG, "tile_x out of range");
-    if (d->warps_per_cta < 0 || d->warps_per_cta > 16)
-        return fail(SM_ERR_INVALID_ARG, "warps_per_cta out of range");
+    if (d->strip_width < 0 || d->strip_width > 16)
+        return fail(SM_ERR_INVALID_ARG, "strip_width out of range (0..16)");
+    if (d->prefetch_rows < 0 || d->prefetch_rows > 8 || d->prefetch_rows == 1)
+        return fail(SM_ERR_INVALID_ARG, "prefetch_rows must be 0 or 2..8");
 
     smk::planck_upload_tables();
     sm_problem *p = new sm_problem();
@@ -378,7 +380,7 @@ sm_status sm_create_problem(const sm_problem_desc *d, void *stream, sm_problem *
     int GW = d->groups_per_warp;
     if (GW == 0) {
         const int gpl = (p->G + p->LG - 1) / p->LG;  // slots per lane if GW were unlimited
-        GW = gpl >= 16 ? 2 : 1;
+        GW = gpl >= 4 ? 4 : (gpl >= 2 ? 2 : 1);
     }
     p->GW = GW;
     p->GSLOT = GW * p->LG;
@@ -443,8 +445,8 @@ sm_status sm_create_problem(const sm_problem_desc *d, void *stream, sm_problem *
     SM_TRY(dev_alloc(&p->d_inflow, 4 * (size_t)p->Gp * p->rsize, &acc));
     SM_TRY(dev_alloc(&p->d_lanes, sizeof(smk::LaneConst) * lanes.size(), &acc));
     SM_TRY(dev_alloc(&p->d_dir_of, sizeof(int) * dir_of.size(), &acc));
-    SM_TRY(dev_alloc(&p->d_Q, (size_t)p->Gp * p->ncell * p->nn * p->rsize, &acc));
-    SM_TRY(dev_alloc(&p->d_SG, (size_t)p->Gp * p->ncell * 2 * p->rsize, &acc));
+    SM_TRY(dev_alloc(&p->d_src, (size_t)p->Gp * p->ncell * 8 * p->rsize, &acc));
+    if (p->dim == 2) SM_TRY(dev_alloc(&p->d_mom_acc, (size_t)p->ncell * 36 * p->rsize, &acc));
     SM_TRY(dev_alloc(&p->d_gray, (size_t)p->ncell * p->nn * 2 * sizeof(double), &acc));
     SM_TRY(dev_alloc(&p->d_ctrl, smk::CTRL_WORDS * sizeof(unsigned int), &acc));
     SM_TRY(dev_alloc(&p->d_mom_tmp, (size_t)p->ncell * p->nn * p->nm * sizeof(double), &acc));
@@ -467,14 +469,11 @@ sm_status sm_create_problem(const sm_problem_desc *d, void *stream, sm_problem *
 
     // ---- tiling
     if (p->dim == 2) {
-        int TX = d->tile_x, W = d->warps_per_cta;
-        if (W == 0) W = std::min(p->prec == 32 ? 8 : 4, p->NWT);
-        if (TX == 0) TX = p->nx >= 128 ? 16 : 8;
-        st = apply_tiling(p, TX, W);
-        if (st && d->tile_x == 0 && d->warps_per_cta == 0) {
-            // fall back to the smallest footprint before giving up
-            st = apply_tiling(p, 4, 1);
-        }
+        int W = d->strip_width, S = d->prefetch_rows;
+        if (W == 0) W = 8;
+        if (S == 0) S = p->prec == 32 ? 4 : 3;
+        st = apply_tiling(p, W, S);
+        if (st && d->strip_width == 0 && d->prefetch_rows == 0) st = apply_tiling(p, 2, 2);
         if (st) {
             free_all(p);
             delete p;
@@ -515,9 +514,9 @@ sm_status sm_get_info(const sm_problem *p, sm_problem_info *o) {
     o->groups_per_warp = p->GW;
     o->n_groups_padded = p->Gp;
     o->n_warp_tasks = p->NWT;
-    o->tile_x = p->TX;
-    o->warps_per_cta = p->W;
-    o->n_chains = p->NCH;
+    o->strip_width = p->W;
+    o->prefetch_rows = p->S;
+    o->n_tasks = p->dim == 2 ? p->NS * p->NQ * p->NWT : p->NQ * p->NWT;
     o->n_strips = p->NS;
     o->intensity_elems = (size_t)p->NQ * p->NWT * p->ncell * p->GW * 32 * p->nn;
     o->intensity_bytes = o->intensity_elems * p->rsize;
@@ -532,11 +531,12 @@ sm_status sm_set_stream(sm_problem *p, void *stream) {
     return SM_OK;
 }
 
-sm_status sm_set_tiling(sm_problem *p, int tile_x, int warps_per_cta) {
+sm_status sm_set_tiling(sm_problem *p, int strip_width, int prefetch_rows) {
     if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
     if (p->dim == 1) return SM_OK;
     SM_CUDA(cudaStreamSynchronize(p->stream));
-    return apply_tiling(p, tile_x > 0 ? tile_x : p->TX, warps_per_cta > 0 ? warps_per_cta : p->W);
+    return apply_tiling(p, strip_width > 0 ? strip_width : p->W,
+                        prefetch_rows > 0 ? prefetch_rows : p->S);
 }
 
 sm_status sm_get_quadrature(const sm_problem *p, double *omx, double *omy, double *w) {
@@ -575,6 +575,7 @@ sm_status sm_sweep(sm_problem *p, const double *T, const double *sigma, const vo
         (st = check_ptr(I_out, "I_out_dev")))
         return st;
     if (I_prev == I_out) return fail(SM_ERR_INVALID_ARG, "I_prev_dev must not alias I_out_dev");
+    if ((st = check_intensity_align(I_prev, I_out))) return st;
     return run_sweep(p, T, sigma, I_prev, I_out, mom, clo);
 }
 
@@ -598,6 +599,7 @@ sm_status sm_sweep_host(sm_problem *p, const double *T_host, const double *sigma
         (st = check_ptr(I_out, "I_out_dev")))
         return st;
     if (I_prev == I_out) return fail(SM_ERR_INVALID_ARG, "I_prev_dev must not alias I_out_dev");
+    if ((st = check_intensity_align(I_prev, I_out))) return st;
     cudaStream_t s = p->stream;
     const size_t tb = (size_t)p->ncell * p->nn * sizeof(double);
     const size_t sb = (size_t)p->G * p->ncell * sizeof(double);
@@ -687,22 +689,22 @@ sm_status sm_autotune(sm_problem *p, const double *T, const double *sigma, const
         (st = check_ptr(I_out, "I_out_dev")))
         return st;
     if (p->dim == 1) return SM_OK;
+    if (I_prev == I_out) return fail(SM_ERR_INVALID_ARG, "I_prev_dev must not alias I_out_dev");
+    if ((st = check_intensity_align(I_prev, I_out))) return st;
     if (reps < 1) reps = 3;
-    const int tx_c[] = {4, 8, 16, 32};
-    const int w_c[] = {1, 2, 4, 8, 16};
-    const int best0_tx = p->TX, best0_w = p->W;
-    int best_tx = best0_tx, best_w = best0_w;
+    const int w_c[] = {2, 4, 8, 16};
+    const int s_c[] = {2, 3, 4, 6};
+    int best_w = p->W, best_s = p->S;
     float best_ms = 1e30f;
     const bool prof = p->profiling;
     p->profiling = false;
     cudaEvent_t a, b;
     SM_CUDA(cudaEventCreate(&a));
     SM_CUDA(cudaEventCreate(&b));
-    for (int tx : tx_c) {
-        if (tx > 2 * p->nx && tx != 4) continue;
-        for (int w : w_c) {
-            if (w > p->NWT && w != 1) continue;
-            if (apply_tiling(p, tx, w) != SM_OK) continue;
+    for (int wc : w_c) {
+        if (wc > p->nx && wc != 2) continue;
+        for (int sc : s_c) {
+            if (apply_tiling(p, wc, sc) != SM_OK) continue;
             st = run_sweep(p, T, sigma, I_prev, I_out, nullptr, nullptr);  // warm-up
             if (st) break;
             SM_CUDA(cudaEventRecord(a, p->stream));
@@ -714,16 +716,17 @@ sm_status sm_autotune(sm_problem *p, const double *T, const double *sigma, const
             SM_CUDA(cudaEventElapsedTime(&ms, a, b));
             if (st == SM_OK && ms < best_ms) {
                 best_ms = ms;
-                best_tx = p->TX;
                 best_w = p->W;
+                best_s = p->S;
             }
         }
+        if (st) break;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     p->profiling = prof;
     sm_status sync = sm_synchronize(p);
-    sm_status fin = apply_tiling(p, best_tx, best_w);
+    sm_status fin = apply_tiling(p, best_w, best_s);
     if (st) return st;
     if (sync) return sync;
     return fin;

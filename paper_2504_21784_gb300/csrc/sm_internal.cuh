@@ -33,20 +33,20 @@ enum { ST_TIMEOUT = 1u, ST_NONPHYSICAL = 2u };
 struct SweepArgs {
     int nx, ny, ncell;
     int NQ, NWT, NGB, DB, LG, GW, Gp;
-    int W;            // warps per CTA
-    int NS, TX;       // strips, strip width
-    int CPQ, NCH;     // chains per quadrant, chains
-    int n_tasks;
+    int W;            // 2D: cell columns per CTA = warps per CTA (1D: unused)
+    int S;            // 2D: rows prefetched per warp (TMA stages)
+    int NS;           // 2D: strips
+    int n_tasks;      // 2D: NS * NQ * NWT
     double inv_cdt;
     const LaneConst *lanes;  // [NQ][DB][32]
-    const void *Q;           // [Gp][cell][nn]  sweep precision
-    const void *SG;          // [Gp][cell][2]   {sigma~, sigma}
+    const void *src;         // [cell][Gp][8] sweep precision: q at 4 nodes, sigma~, sigma, 0, 0
     const void *inflow;      // [4][Gp]
     const void *I_prev;      // packed or null
     void *I_out;             // packed
-    void *part;              // [n_part][cell][nn*nm]
-    void *face;              // [NCH][NS][ny][W][GW][32][2]
-    unsigned long long *flags;  // [NCH][NS]
+    void *part;              // 1D: [NQ*NWT][cell][10] per-warp partial moments
+    void *mom_acc;           // 2D: [cell][36] moment accumulator (zeroed per sweep)
+    void *face;              // 2D: [NQ*NWT][NS][ny][GW][32][2]
+    unsigned long long *flags;  // 2D: [NQ*NWT][NS]
     unsigned int *ctrl;
     unsigned long long epoch;
     long long timeout_ns;
@@ -63,12 +63,12 @@ cudaError_t launch_closures_from_T(const sm_problem *p, const double *mom, const
                                    const double *sigma, double *out, cudaStream_t s);
 cudaError_t launch_sweep2d(const sm_problem *p, const SweepArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_sweep1d(const sm_problem *p, const SweepArgs &a, cudaStream_t s);
-cudaError_t launch_reduce(const sm_problem *p, int n_part, double *mom, double *clo,
-                          cudaStream_t s);
+cudaError_t launch_reduce(const sm_problem *p, const void *part, int n_part, double *mom,
+                          double *clo, cudaStream_t s);
 cudaError_t launch_pack(const sm_problem *p, const double *canon, void *packed, int unpack,
                         cudaStream_t s);
-int sweep2d_max_resident(const sm_problem *p, int W, size_t *smem_out);
-size_t sweep2d_smem_bytes(int prec, int W, int GW, int TX);
+int sweep2d_max_resident(const sm_problem *p, int W, int S, size_t *smem_out);
+size_t sweep2d_smem_bytes(int prec, int W, int GW, int S, int GSLOT);
 void planck_upload_tables(void);
 // Set the thread-local message returned by sm_last_error() (no allocation
 // beyond the message string of at most 255 characters).
@@ -89,18 +89,18 @@ struct sm_problem {
     double alpha;
     // lane mapping
     int DQ, DQP, DQL, LG, DB, GW, GSLOT, Gp, NGB, NWT;
-    // tiling
-    int TX, W, NS, CPQ, NCH;
+    // tiling (2D): W cell columns (= warps) per CTA, S prefetched rows per warp
+    int W, S, NS;
+    int resident = 0;  // 2D sweep CTAs that fit on the GPU for (W, S)
     // device buffers
     double *d_edges = nullptr;      // [G+1]
     void *d_inflow = nullptr;       // [4][Gp] sweep precision
     smk::LaneConst *d_lanes = nullptr;
     int *d_dir_of = nullptr;        // [NQ][DB][32] canonical direction (or -1)
-    void *d_Q = nullptr;
-    void *d_SG = nullptr;
+    void *d_src = nullptr;          // [cell][Gp][8] source records
+    void *d_mom_acc = nullptr;      // 2D: [cell][36] moment accumulator
     double *d_gray = nullptr;       // [cell][node][2] sigma_P, sigma_F
-    void *d_part = nullptr;
-    size_t part_sets = 0;
+    void *d_part = nullptr;         // 1D: per-warp partial moments
     void *d_face = nullptr;
     size_t face_bytes = 0;
     unsigned long long *d_flags = nullptr;

@@ -156,12 +156,15 @@ __global__ void opacity_kernel(int ncell, int nn, int G, int kind, double alpha,
 
 // ---------------------------------------------------------------------------
 // Emission (row a1): one thread per (cell, node), walking the group edges once.
+// Writes the sweep's source records src[cell][g][8] = {q at the nodes (unused
+// node slots 0), sigma~, sigma, 0, 0} in the sweep precision; padding groups
+// get no source and sigma~ = 1.
 template <typename RT>
 __global__ void emission_kernel(int ncell, int nn, int G, int Gp, const double *__restrict__ edges,
                                 double acT4_scale, double inv_cdt, const double *__restrict__ T,
-                                const double *__restrict__ sigma, RT *__restrict__ Q,
-                                RT *__restrict__ SG, double *__restrict__ gray,
-                                double *__restrict__ qcanon, unsigned int *ctrl) {
+                                const double *__restrict__ sigma, RT *__restrict__ src,
+                                double *__restrict__ gray, double *__restrict__ qcanon,
+                                unsigned int *ctrl) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ncell * nn) return;
     const int cell = t / nn, node = t - cell * nn;
@@ -173,6 +176,7 @@ __global__ void emission_kernel(int ncell, int nn, int G, int Gp, const double *
     const double invT = 1.0 / Tn;
     EdgeVals lo = edge_vals(0.0);
     double nb = 0.0, db = 0.0, nr = 0.0, dr = 0.0;
+    RT *rec0 = src + (size_t)cell * Gp * 8;
     for (int g = 0; g < G; ++g) {
         const double xhi = (g == G - 1) ? INFINITY : edges[g + 1] * invT;
         const EdgeVals hi = edge_vals(xhi);
@@ -184,20 +188,27 @@ __global__ void emission_kernel(int ncell, int nn, int G, int Gp, const double *
         nr = fma(r, sg, nr);
         dr += r;
         const double qv = sg * b * B4;
-        const size_t qi = ((size_t)g * ncell + cell) * nn + node;
-        Q[qi] = (RT)qv;
-        if (qcanon) qcanon[qi] = qv;
+        RT *rec = rec0 + (size_t)g * 8;
+        rec[node] = (RT)qv;
+        if (qcanon) qcanon[((size_t)g * ncell + cell) * nn + node] = qv;
         if (node == 0) {
-            SG[((size_t)g * ncell + cell) * 2 + 0] = (RT)(sg + inv_cdt);
-            SG[((size_t)g * ncell + cell) * 2 + 1] = (RT)sg;
+            for (int n = nn; n < 4; ++n) rec[n] = (RT)0;
+            rec[4] = (RT)(sg + inv_cdt);
+            rec[5] = (RT)sg;
+            rec[6] = (RT)0;
+            rec[7] = (RT)0;
         }
         lo = hi;
     }
     for (int g = G; g < Gp; ++g) {  // padding groups: no source, unit sigma~
-        Q[((size_t)g * ncell + cell) * nn + node] = (RT)0;
+        RT *rec = rec0 + (size_t)g * 8;
+        rec[node] = (RT)0;
         if (node == 0) {
-            SG[((size_t)g * ncell + cell) * 2 + 0] = (RT)1;
-            SG[((size_t)g * ncell + cell) * 2 + 1] = (RT)0;
+            for (int n = nn; n < 4; ++n) rec[n] = (RT)0;
+            rec[4] = (RT)1;
+            rec[5] = (RT)0;
+            rec[6] = (RT)0;
+            rec[7] = (RT)0;
         }
     }
     gray[(size_t)t * 2 + 0] = nb / db;
@@ -302,11 +313,11 @@ cudaError_t launch_emission(const sm_problem *p, const double *T, const double *
     if (p->prec == 32)
         emission_kernel<float><<<blocks, threads, 0, s>>>(
             p->ncell, p->nn, p->G, p->Gp, p->d_edges, scale, p->inv_cdt, T, sigma,
-            (float *)p->d_Q, (float *)p->d_SG, p->d_gray, q_canon, p->d_ctrl);
+            (float *)p->d_src, p->d_gray, q_canon, p->d_ctrl);
     else
         emission_kernel<double><<<blocks, threads, 0, s>>>(
             p->ncell, p->nn, p->G, p->Gp, p->d_edges, scale, p->inv_cdt, T, sigma,
-            (double *)p->d_Q, (double *)p->d_SG, p->d_gray, q_canon, p->d_ctrl);
+            (double *)p->d_src, p->d_gray, q_canon, p->d_ctrl);
     return cudaGetLastError();
 }
 

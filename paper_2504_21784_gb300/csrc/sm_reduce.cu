@@ -1,5 +1,6 @@
-// Row a3 (final stage) and a4: sum the per-chain partial moments in FP64 in a
-// fixed order (deterministic) and form the gray low-order closures of Sec. 2
+// Row a3 (final stage) and a4: sum the partial moments (the 2D sweep's single
+// accumulator, or the 1D sweep's per-warp partials in a fixed order) in FP64
+// and form the gray low-order closures of Sec. 2
 // (Eqs. sigmaE, sigmaF, sigma_P, additive_mg_correction) from them and the
 // nodal spectra left by the emission pass.  Also the pack / unpack kernels
 // between the canonical intensity I[d][g][cell][node] and the sweep layout
@@ -57,19 +58,18 @@ __global__ void reduce_kernel(int dim, int nnodes_total, int nm, int nsets, size
     }
 }
 
-cudaError_t launch_reduce(const sm_problem *p, int n_part, double *mom, double *clo,
-                          cudaStream_t s) {
+cudaError_t launch_reduce(const sm_problem *p, const void *part, int n_part, double *mom,
+                          double *clo, cudaStream_t s) {
     const int n = p->ncell * p->nn;
     const int threads = 128;
     const size_t stride = (size_t)n * p->nm;
     const double inv_c = 1.0 / p->desc.c;
     if (p->prec == 32)
         reduce_kernel<float><<<(n + threads - 1) / threads, threads, 0, s>>>(
-            p->dim, n, p->nm, n_part, stride, inv_c, (const float *)p->d_part, p->d_gray, mom, clo);
+            p->dim, n, p->nm, n_part, stride, inv_c, (const float *)part, p->d_gray, mom, clo);
     else
         reduce_kernel<double><<<(n + threads - 1) / threads, threads, 0, s>>>(
-            p->dim, n, p->nm, n_part, stride, inv_c, (const double *)p->d_part, p->d_gray, mom,
-            clo);
+            p->dim, n, p->nm, n_part, stride, inv_c, (const double *)part, p->d_gray, mom, clo);
     return cudaGetLastError();
 }
 

@@ -202,15 +202,15 @@ sm_status sm_sweep_static(const sm_problem_desc *d, void *stream, const double *
     const int nlanes = p.NQ * p.DB * 32;
 
     // tiling: the first shape whose shared memory fits
-    const int tx_try[] = {16, 8, 4};
-    const int w_try[] = {4, 2, 1};
+    const int w_try[] = {8, 4, 2, 1};
+    const int s_try[] = {3, 2};
     bool tiled = false;
-    for (int tx : tx_try) {
-        for (int w : w_try) {
-            p.TX = tx;
-            p.W = std::min(w, p.NWT);
+    for (int w : w_try) {
+        for (int st : s_try) {
+            p.W = w;
+            p.S = st;
             size_t smem = 0;
-            if (smk::sweep2d_max_resident(&p, p.W, &smem) > 0) {
+            if (smk::sweep2d_max_resident(&p, p.W, p.S, &smem) > 0) {
                 tiled = true;
                 break;
             }
@@ -218,9 +218,8 @@ sm_status sm_sweep_static(const sm_problem_desc *d, void *stream, const double *
         if (tiled) break;
     }
     if (!tiled) return static_fail(SM_ERR_UNSUPPORTED, "no sweep tiling fits");
-    p.NS = (p.nx + p.TX - 1) / p.TX;
-    p.CPQ = (p.NWT + p.W - 1) / p.W;
-    p.NCH = p.NQ * p.CPQ;
+    p.NS = (p.nx + p.W - 1) / p.W;
+    const size_t nwg = (size_t)p.NQ * p.NWT;
 
     // carve the scratch
     const size_t ielems = (size_t)p.NQ * p.NWT * p.ncell * p.GW * 32 * p.nn;
@@ -231,16 +230,15 @@ sm_status sm_sweep_static(const sm_problem_desc *d, void *stream, const double *
         return o;
     };
     const size_t o_ctrl = take(smk::CTRL_WORDS * sizeof(unsigned int));
-    const size_t o_flags = take((size_t)p.NCH * p.NS * sizeof(unsigned long long));
+    const size_t o_flags = take(nwg * p.NS * sizeof(unsigned long long));
     const size_t o_edges = take(sizeof(double) * (p.G + 1));
     const size_t o_inflow = take(4 * (size_t)p.Gp * p.rsize);
     const size_t o_lanes = take(sizeof(smk::LaneConst) * nlanes);
     const size_t o_dir = take(sizeof(int) * nlanes);
-    const size_t o_Q = take((size_t)p.Gp * p.ncell * p.nn * p.rsize);
-    const size_t o_SG = take((size_t)p.Gp * p.ncell * 2 * p.rsize);
+    const size_t o_src = take((size_t)p.ncell * p.Gp * 8 * p.rsize);
     const size_t o_gray = take((size_t)p.ncell * p.nn * 2 * sizeof(double));
-    const size_t o_part = take((size_t)p.NCH * p.ncell * p.nn * p.nm * p.rsize);
-    const size_t o_face = take((size_t)p.NCH * p.NS * p.ny * p.W * p.GW * 32 * 2 * p.rsize);
+    const size_t o_acc = take((size_t)p.ncell * 36 * p.rsize);
+    const size_t o_face = take(nwg * p.NS * p.ny * p.GW * 32 * 2 * p.rsize);
     const size_t o_mom = take((size_t)p.ncell * p.nn * p.nm * sizeof(double));
     const size_t o_Ip = take(ielems * p.rsize);
     const size_t o_Io = take(ielems * p.rsize);
@@ -253,15 +251,14 @@ sm_status sm_sweep_static(const sm_problem_desc *d, void *stream, const double *
     }
     p.d_ctrl = reinterpret_cast<unsigned int *>(base + o_ctrl);
     p.d_flags = reinterpret_cast<unsigned long long *>(base + o_flags);
-    p.flags_count = (size_t)p.NCH * p.NS;
+    p.flags_count = nwg * p.NS;
     p.d_edges = reinterpret_cast<double *>(base + o_edges);
     p.d_inflow = base + o_inflow;
     p.d_lanes = reinterpret_cast<smk::LaneConst *>(base + o_lanes);
     p.d_dir_of = reinterpret_cast<int *>(base + o_dir);
-    p.d_Q = base + o_Q;
-    p.d_SG = base + o_SG;
+    p.d_src = base + o_src;
     p.d_gray = reinterpret_cast<double *>(base + o_gray);
-    p.d_part = base + o_part;
+    p.d_mom_acc = base + o_acc;
     p.d_face = base + o_face;
     p.d_mom_tmp = reinterpret_cast<double *>(base + o_mom);
     void *Ip = base + o_Ip;
@@ -272,10 +269,11 @@ sm_status sm_sweep_static(const sm_problem_desc *d, void *stream, const double *
     do {                                                                    \
         if ((x) != cudaSuccess) return static_fail(SM_ERR_CUDA, #x " failed"); \
     } while (0)
-    // what must start at zero: control words (queue, abort, status) and the
-    // wavefront row counters (epoch 1 below)
+    // what must start at zero: control words (queue, abort, status), the
+    // wavefront row counters (epoch 1 below) and the moment accumulator
     ST_CUDA(cudaMemsetAsync(base + o_ctrl, 0, smk::CTRL_WORDS * sizeof(unsigned int), s));
-    ST_CUDA(cudaMemsetAsync(base + o_flags, 0, (size_t)p.NCH * p.NS * 8, s));
+    ST_CUDA(cudaMemsetAsync(base + o_flags, 0, nwg * p.NS * 8, s));
+    ST_CUDA(cudaMemsetAsync(base + o_acc, 0, (size_t)p.ncell * 36 * p.rsize, s));
     ST_CUDA(cudaMemcpyAsync(p.d_edges, d->group_edges, sizeof(double) * (p.G + 1),
                             cudaMemcpyHostToDevice, s));
     ST_CUDA(cudaMemcpyAsync(p.d_lanes, lanes, sizeof(smk::LaneConst) * nlanes,
@@ -287,17 +285,18 @@ sm_status sm_sweep_static(const sm_problem_desc *d, void *stream, const double *
     smk::SweepArgs a;
     std::memset(&a, 0, sizeof(a));
     a.nx = p.nx; a.ny = p.ny; a.ncell = p.ncell; a.NQ = p.NQ; a.NWT = p.NWT; a.NGB = p.NGB;
-    a.DB = p.DB; a.LG = p.LG; a.GW = p.GW; a.Gp = p.Gp; a.W = p.W; a.NS = p.NS; a.TX = p.TX;
-    a.CPQ = p.CPQ; a.NCH = p.NCH; a.n_tasks = p.NS * p.NCH; a.inv_cdt = p.inv_cdt;
-    a.lanes = p.d_lanes; a.Q = p.d_Q; a.SG = p.d_SG; a.inflow = p.d_inflow;
-    a.I_prev = I_prev_canon ? Ip : nullptr; a.I_out = Io; a.part = p.d_part; a.face = p.d_face;
-    a.flags = p.d_flags; a.ctrl = p.d_ctrl; a.epoch = 1; a.timeout_ns = 2000000000LL;
+    a.DB = p.DB; a.LG = p.LG; a.GW = p.GW; a.Gp = p.Gp; a.W = p.W; a.S = p.S; a.NS = p.NS;
+    a.n_tasks = p.NS * p.NQ * p.NWT; a.inv_cdt = p.inv_cdt;
+    a.lanes = p.d_lanes; a.src = p.d_src; a.inflow = p.d_inflow;
+    a.I_prev = I_prev_canon ? Ip : nullptr; a.I_out = Io; a.mom_acc = p.d_mom_acc;
+    a.face = p.d_face; a.flags = p.d_flags; a.ctrl = p.d_ctrl; a.epoch = 1;
+    a.timeout_ns = 2000000000LL;
     a.fault_skip_publish = 0;
     size_t smem = 0;
-    const int resident = smk::sweep2d_max_resident(&p, p.W, &smem);
+    const int resident = smk::sweep2d_max_resident(&p, p.W, p.S, &smem);
     if (resident <= 0) return static_fail(SM_ERR_UNSUPPORTED, "sweep tiling does not fit");
     ST_CUDA(smk::launch_sweep2d(&p, a, std::min(a.n_tasks, resident), s));
-    ST_CUDA(smk::launch_reduce(&p, p.NCH, moments ? moments : p.d_mom_tmp, closures, s));
+    ST_CUDA(smk::launch_reduce(&p, p.d_mom_acc, 1, moments ? moments : p.d_mom_tmp, closures, s));
     ST_CUDA(smk::launch_pack(&p, I_out_canon, Io, 1, s));
     ST_CUDA(cudaStreamSynchronize(s));
     unsigned int ctrl[smk::CTRL_WORDS];

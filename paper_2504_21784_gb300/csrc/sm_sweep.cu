@@ -18,20 +18,27 @@
 // The kernel evaluates this after scaling by 1/A (no overflow in FP32 for
 // optical depths up to ~1e9).  1D: [[A, mu], [-mu, A]] with A = sigma~ + mu.
 //
-// Parallel layout.  A warp task owns 32 lanes x GW slots of (direction, group)
-// pairs of one quadrant (lane = direction inside the quadrant, or direction x
-// group when a quadrant has fewer than 32 directions).  W warp tasks of the
-// same quadrant form a chain; a chain's mesh is cut into column strips of
-// TX cells, one CTA per (chain, strip).  A CTA sweeps its strip row by row in
-// upwind order; the x-inflow of each row comes from the upwind strip through
-// an L2-resident face buffer and a per-(chain, strip) row counter (release /
-// acquire), the y-inflow is carried in shared memory.  Tasks are handed out
-// by an atomic queue in upwind-strip order, so every awaited producer is
-// already running (no deadlock for any grid size), and every wait is bounded
-// in time (status word + abort flag, never a trap).  Per cell, each lane sums
-// its GW intensities, forms the 36 (2D) weighted moments, and the warp
-// reduces them by a transpose-butterfly; the W warps are summed in shared
-// memory and written as one partial per (chain, cell).
+// 2D parallel layout (diagonal wavefront).  A warp task owns 32 lanes x GW
+// slots of (direction, group) pairs of one quadrant (lane = direction inside
+// the quadrant, or direction x group when a quadrant has fewer than 32
+// directions).  A CTA takes one warp task over a strip of W cell columns,
+// one warp per column; each warp walks its column in upwind row order with
+// the y-inflow carried in registers.  The x-inflow of a row comes from the
+// warp of the upwind column through a shared-memory ring (pairwise row
+// counters, back-pressure of R rows), and across strips from the upwind CTA
+// through an L2-resident face buffer and a per-(warp task, strip) row counter
+// (release / acquire).  So the W warps of a CTA run one row apart, a staircase
+// wavefront with no CTA-wide barrier inside a task.  Each warp prefetches
+// the I^k and source records of its next S rows with TMA bulk copies
+// (cp.async.bulk, mbarrier completion) into shared memory.  Tasks come from an
+// atomic queue in upwind-strip order, so every awaited producer is already
+// running (no deadlock for any grid size), and every wait is bounded in time
+// (status word + abort flag, never a trap).  Per cell, each lane sums its GW
+// intensities, forms the 36 weighted moments, the warp reduces them by a
+// transpose-butterfly and adds them with vector atomics to an L2-resident
+// per-cell accumulator.
+#include <stdint.h>
+
 #include "sm_internal.cuh"
 
 namespace smk {
@@ -43,15 +50,6 @@ template <> struct V2<double> { using t = double2; };
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
 
-__device__ __forceinline__ void ld4_stream(const float *p, float (&v)[4]) {
-    const float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
-    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-}
-__device__ __forceinline__ void ld4_stream(const double *p, double (&v)[4]) {
-    const double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
-    const double2 b = __ldcs(reinterpret_cast<const double2 *>(p + 2));
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-}
 __device__ __forceinline__ void st4_stream(float *p, const float (&v)[4]) {
     __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
 }
@@ -59,13 +57,13 @@ __device__ __forceinline__ void st4_stream(double *p, const double (&v)[4]) {
     __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
     __stcs(reinterpret_cast<double2 *>(p + 2), make_double2(v[2], v[3]));
 }
-__device__ __forceinline__ void ld4_ro(const float *p, float (&v)[4]) {
-    const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+__device__ __forceinline__ void lds4(const float *p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
 }
-__device__ __forceinline__ void ld4_ro(const double *p, double (&v)[4]) {
-    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
-    const double2 b = __ldg(reinterpret_cast<const double2 *>(p + 2));
+__device__ __forceinline__ void lds4(const double *p, double (&v)[4]) {
+    const double2 a = *reinterpret_cast<const double2 *>(p);
+    const double2 b = *reinterpret_cast<const double2 *>(p + 2);
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
@@ -88,29 +86,116 @@ __device__ __forceinline__ long long global_ns() {
     return t;
 }
 
-// Bounded wait for a producer row counter.  Returns 0 when the counter reached
-// target, 1 when the wait gave up (time limit: records ST_TIMEOUT and raises
-// the abort flag) or another CTA aborted.
-__device__ int wait_flag(const unsigned long long *f, unsigned long long target,
-                         unsigned int *ctrl, long long timeout_ns) {
-    if (ld_acquire(f) >= target) return 0;
+// ---- mbarrier / TMA bulk-copy helpers (inline PTX) ----------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// global -> shared bulk copy; bytes and both addresses multiples of 16
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Records a timeout in the status word, raises the global and CTA abort flags.
+__device__ __forceinline__ void raise_timeout(unsigned int *ctrl, volatile int *s_abort) {
+    atomicOr(ctrl + CTRL_STATUS, (unsigned)ST_TIMEOUT);
+    atomicExch(ctrl + CTRL_ABORT, 1u);
+    *s_abort = 1;
+}
+
+// Bounded wait (every lane) for a TMA stage.  false: timed out or aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned int *ctrl,
+                                          long long timeout_ns, volatile int *s_abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 31) == 0) {
+            if (*s_abort) return false;
+            if (global_ns() - t0 > timeout_ns) {
+                raise_timeout(ctrl, s_abort);
+                return false;
+            }
+        }
+    }
+}
+
+// Bounded wait (every lane) until a shared counter reaches target.
+__device__ __forceinline__ bool smem_wait_geq(volatile int *cnt, int target, unsigned int *ctrl,
+                                              long long timeout_ns, volatile int *s_abort) {
+    if (*cnt >= target) return true;
+    const long long t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+        __nanosleep(20);
+        if (*cnt >= target) return true;
+        if ((it & 15) == 0) {
+            if (*s_abort) return false;
+            if (global_ns() - t0 > timeout_ns) {
+                raise_timeout(ctrl, s_abort);
+                return false;
+            }
+        }
+    }
+}
+
+// Bounded wait (every lane) for a producer row counter in global memory.
+__device__ __forceinline__ bool flag_wait_geq(const unsigned long long *f,
+                                              unsigned long long target, unsigned long long &seen,
+                                              unsigned int *ctrl, long long timeout_ns,
+                                              volatile int *s_abort) {
+    if (seen >= target) return true;
+    seen = ld_acquire(f);
+    if (seen >= target) return true;
     const long long t0 = global_ns();
     unsigned ns = 32;
     for (;;) {
         __nanosleep(ns);
-        if (ns < 512) ns <<= 1;
-        if (ld_acquire(f) >= target) return 0;
-        if (ld_relaxed(ctrl + CTRL_ABORT)) return 1;
+        if (ns < 256) ns <<= 1;
+        seen = ld_acquire(f);
+        if (seen >= target) return true;
+        if (*s_abort || ld_relaxed(ctrl + CTRL_ABORT)) {
+            *s_abort = 1;
+            return false;
+        }
         if (global_ns() - t0 > timeout_ns) {
-            atomicOr(ctrl + CTRL_STATUS, (unsigned)ST_TIMEOUT);
-            atomicExch(ctrl + CTRL_ABORT, 1u);
-            return 1;
+            raise_timeout(ctrl, s_abort);
+            return false;
         }
     }
 }
 
 // Transpose-butterfly warp reduction of CNT values per lane: afterwards v[0]
-// of lane L holds the warp sum of value index L >> (5 - log2 CNT).
+// of lane L holds the warp sum of value index L >> (5 - log2 CNT).  Steps stop
+// at offset STOP (exclusive of smaller offsets) when STOP > 0.
 template <int OFF, int CNT, typename RT> struct TRed {
     static __device__ __forceinline__ void run(RT *v, int lane) {
         if constexpr (CNT > 1) {
@@ -130,198 +215,331 @@ template <int OFF, int CNT, typename RT> struct TRed {
     }
 };
 
-size_t sweep2d_smem_bytes(int prec, int W, int GW, int TX) {
-    const size_t rs = (prec == 32) ? 4 : 8;
-    return (size_t)W * GW * TX * 32 * 2 * rs + (size_t)2 * W * TX * 36 * rs;
+// Reduce 36 per-lane values over the warp and add them to acc[0..35].
+// FP32: lanes end with 4 consecutive sums and use 16-byte vector atomics.
+__device__ __forceinline__ void warp_moments_add(float *v, int lane, float *acc) {
+    // first 32 values: transpose over offsets 16, 8, 4 -> 4 values per lane
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const int off = 16 >> s;
+        const int H = 16 >> s;
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if (i < H) {
+                const float send = up ? v[i] : v[i + H];
+                const float keep = up ? v[i + H] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        v[i] += __shfl_xor_sync(0xffffffffu, v[i], 2);
+        v[i] += __shfl_xor_sync(0xffffffffu, v[i], 1);
+    }
+    if ((lane & 3) == 0)
+        atomicAdd(reinterpret_cast<float4 *>(acc + lane), make_float4(v[0], v[1], v[2], v[3]));
+    // last 4 values: full butterfly, lane 0 adds them
+    float *t = v + 32;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) t[i] += __shfl_xor_sync(0xffffffffu, t[i], off);
+    }
+    if (lane == 0) atomicAdd(reinterpret_cast<float4 *>(acc + 32), make_float4(t[0], t[1], t[2], t[3]));
+}
+__device__ __forceinline__ void warp_moments_add(double *v, int lane, double *acc) {
+    TRed<16, 32, double>::run(v, lane);
+    TRed<16, 4, double>::run(v + 32, lane);
+    atomicAdd(acc + lane, v[0]);
+    if ((lane & 7) == 0) atomicAdd(acc + 32 + (lane >> 3), v[32]);
+}
+
+constexpr int RING = 4;  // rows of x-face buffering between neighbouring warps
+constexpr int SREC = 8;  // source record: q at 4 nodes, sigma~, sigma, 2 pad
+
+__host__ __device__ inline size_t stage_bytes(int rsize, int GW, int GSLOT) {
+    return (size_t)GW * 32 * 4 * rsize + (size_t)GSLOT * SREC * rsize;
+}
+
+size_t sweep2d_smem_bytes(int prec, int W, int GW, int S, int GSLOT) {
+    const int rs = prec == 32 ? 4 : 8;
+    const size_t per_warp = (size_t)S * stage_bytes(rs, GW, GSLOT) + (size_t)RING * GW * 32 * 2 * rs;
+    return (size_t)W * per_warp + (size_t)W * S * 8 + 2 * W * sizeof(int) + 64;
 }
 
 // ---------------------------------------------------------------------------
 template <typename RT, int GW>
 __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs A) {
     using R2 = typename V2<RT>::t;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_task;
-    __shared__ int s_abort;
+    __shared__ volatile int s_abort;
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
-    const int W = A.W, TX = A.TX;
-    const int nx = A.nx, ny = A.ny, ncell = A.ncell;
-    R2 *ycar = reinterpret_cast<R2 *>(smem_raw);                     // [W][GW][TX][32]
-    RT *msm = reinterpret_cast<RT *>(ycar + (size_t)W * GW * TX * 32);  // [2][W][TX][36]
-    const RT *Qp = static_cast<const RT *>(A.Q);
-    const R2 *SGp = static_cast<const R2 *>(A.SG);
+    const int W = A.W, S = A.S;
+    const int nx = A.nx, ny = A.ny;
+    const int GSLOT = GW * A.LG;
+    const size_t stg = stage_bytes((int)sizeof(RT), GW, GSLOT);
+    const size_t ring_bytes = (size_t)RING * GW * 32 * sizeof(R2);
+    unsigned char *wbase = smem_raw + (size_t)w * (S * stg + ring_bytes);
+    R2 *ring_all = reinterpret_cast<R2 *>(smem_raw + S * stg);  // + w * (S*stg + ring_bytes)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)W * (S * stg + ring_bytes));
+    volatile int *rows_done = reinterpret_cast<volatile int *>(bars + (size_t)W * S);
+    volatile int *cons = rows_done + W;
+    uint64_t *mybars = bars + (size_t)w * S;
+    auto ring_of = [&](int ww) {
+        return reinterpret_cast<R2 *>(reinterpret_cast<unsigned char *>(ring_all) +
+                                      (size_t)ww * (S * stg + ring_bytes));
+    };
+    const RT *src = static_cast<const RT *>(A.src);
     const RT *inflow = static_cast<const RT *>(A.inflow);
     const RT *Ip = static_cast<const RT *>(A.I_prev);
     RT *Io = static_cast<RT *>(A.I_out);
-    RT *part = static_cast<RT *>(A.part);
+    RT *acc = static_cast<RT *>(A.mom_acc);
     R2 *face = static_cast<R2 *>(A.face);
     const RT inv_cdt = (RT)A.inv_cdt;
     const RT two = (RT)2;
+    const uint32_t bytes_I = Ip ? (uint32_t)(GW * 32 * 4 * sizeof(RT)) : 0u;
+    const uint32_t bytes_S = (uint32_t)(GSLOT * SREC * sizeof(RT));
+
+    if (threadIdx.x < W * S) mbar_init(bars + threadIdx.x, 1);
+    if (threadIdx.x == 0) s_abort = 0;
+    fence_mbar_init();
+    uint32_t phase = 0;  // parity bit per stage of this warp
 
     for (;;) {
+        __syncthreads();
         if (threadIdx.x == 0) s_task = (int)atomicAdd(A.ctrl + CTRL_QUEUE, 1u);
+        if (threadIdx.x < W) {
+            rows_done[threadIdx.x] = 0;
+            cons[threadIdx.x] = 0;
+        }
         __syncthreads();
         const int task = s_task;
-        if (task >= A.n_tasks) return;
-        const int sr = task / A.NCH, ch = task - sr * A.NCH;
-        const int q = ch / A.CPQ, cq = ch - q * A.CPQ;
+        if (task >= A.n_tasks || s_abort) return;
+        const int NWG = A.NQ * A.NWT;
+        const int sr = task / NWG, wg = task - sr * NWG;
+        const int q = wg / A.NWT, wt = wg - q * A.NWT;
         const int sx = (q == 0 || q == 3) ? 1 : -1;
         const int sy = (q < 2) ? 1 : -1;
         const int strip = sx > 0 ? sr : A.NS - 1 - sr;
-        const int x0 = strip * TX;
-        const int ws = min(TX, nx - x0);
-        const int wt = cq * W + w;
-        const bool wvalid = wt < A.NWT;
-        const int nvalid = min(W, A.NWT - cq * W);
-        const int wtc = wvalid ? wt : 0;
-        const int db = wtc / A.NGB, gb = wtc - db * A.NGB;
+        const int x0 = strip * W;
+        const int ws = min(W, nx - x0);
+        if (w >= ws) continue;  // idle column of a ragged strip
+        const int xw = sx > 0 ? x0 + w : x0 + ws - 1 - w;
+        const int db = wt / A.NGB, gb = wt - db * A.NGB;
         const LaneConst &L = A.lanes[(q * A.DB + db) * 32 + lane];
         const RT mu = (RT)L.mu, eta = (RT)L.eta;
         RT wm[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) wm[k] = (RT)L.wm[k];
+        const int g_lo = L.g_lo;
         const int side_x = sx > 0 ? 0 : 1, side_y = sy > 0 ? 2 : 3;
-        int gidx[GW];
-        RT bx[GW], by[GW];
+        RT X0[GW], X1[GW], Y0[GW], Y1[GW];  // x-inflow (rows u,d), y-inflow (columns u,d)
+        RT bx[GW];                          // boundary x-inflow (first column of strip 0)
 #pragma unroll
         for (int gw = 0; gw < GW; ++gw) {
-            gidx[gw] = gb * (GW * A.LG) + gw * A.LG + L.g_lo;
-            bx[gw] = inflow[side_x * A.Gp + gidx[gw]];
-            by[gw] = inflow[side_y * A.Gp + gidx[gw]];
+            const int g = gb * GSLOT + gw * A.LG + g_lo;
+            const RT by = inflow[side_y * A.Gp + g];
+            Y0[gw] = by;
+            Y1[gw] = by;
+            bx[gw] = inflow[side_x * A.Gp + g];
         }
         const int au = sx > 0 ? 0 : 1, bu = sy > 0 ? 0 : 1;
         const int nuu = au + 2 * bu, ndu = (1 - au) + 2 * bu;
         const int nud = au + 2 * (1 - bu), ndd = (1 - au) + 2 * (1 - bu);
-        const size_t wtbase = (size_t)(q * A.NWT + wtc) * ncell;
-        const bool publish = sr < A.NS - 1;
-        unsigned long long *myflag = A.flags + (size_t)ch * A.NS + strip;
-        const unsigned long long *upflag = A.flags + (size_t)ch * A.NS + (sr > 0 ? strip - sx : strip);
-        // face buffer [chain][strip][row][warp][slot][lane]
-        R2 *face_out = face + ((size_t)ch * A.NS + strip) * ny * W * GW * 32;
-        const R2 *face_in =
-            face + ((size_t)ch * A.NS + (sr > 0 ? strip - sx : strip)) * ny * W * GW * 32;
+        const size_t wtbase = (size_t)wg * A.ncell;
+        const bool global_in = (w == 0) && sr > 0;
+        const bool global_out = (w == ws - 1) && sr < A.NS - 1;
+        const size_t fidx_out = ((size_t)wg * A.NS + strip) * ny;
+        const size_t fidx_in = ((size_t)wg * A.NS + (sr > 0 ? strip - sx : strip)) * ny;
+        unsigned long long *myflag = A.flags + (size_t)wg * A.NS + strip;
+        const unsigned long long *upflag =
+            A.flags + (size_t)wg * A.NS + (sr > 0 ? strip - sx : strip);
         const unsigned long long ep = A.epoch << 32;
+        unsigned long long seen = 0;
+        R2 *ring_in = w > 0 ? ring_of(w - 1) : nullptr;
+        R2 *ring_out = ring_of(w);
 
-        for (int jj = 0; jj < ny; ++jj) {
-            const int y = sy > 0 ? jj : ny - 1 - jj;
-            const int buf = jj & 1;
-            if (sr > 0) {
-                if (threadIdx.x == 0)
-                    s_abort = wait_flag(upflag, ep | (unsigned long long)(jj + 1), A.ctrl,
-                                        A.timeout_ns);
-                __syncthreads();
-                if (s_abort) return;
-            }
-            if (wvalid) {
-                RT Xu[GW], Xd[GW];
+        auto row_y = [&](int jj) { return sy > 0 ? jj : ny - 1 - jj; };
+        auto issue = [&](int jj) {  // lane 0: TMA for row jj into stage jj % S
+            const int st = jj % S;
+            unsigned char *dst = wbase + (size_t)st * stg;
+            const int cell = row_y(jj) * nx + xw;
+            mbar_arrive_expect_tx(mybars + st, bytes_I + bytes_S);
+            if (Ip) bulk_g2s(dst, Ip + ((wtbase + cell) * GW) * 32 * 4, bytes_I, mybars + st);
+            bulk_g2s(dst + bytes_I, src + ((size_t)cell * A.Gp + (size_t)gb * GSLOT) * SREC,
+                     bytes_S, mybars + st);
+        };
+        int issued = -1;    // highest row whose copy was issued
+        int consumed = 0;   // rows whose stage has been waited for
+        if (lane == 0) {
+            fence_proxy_async_smem();
+            for (int jj = 0; jj < min(S, ny); ++jj) issue(jj);
+        }
+        issued = min(S, ny) - 1;
+        bool ok = true;
+        int jj = 0;
+        for (; jj < ny && ok; ++jj) {
+            const int y = row_y(jj);
+            const int st = jj % S;
+            const int slot = jj % RING;
+            // (a) x-inflow
+            if (w == 0 && sr == 0) {
 #pragma unroll
                 for (int gw = 0; gw < GW; ++gw) {
-                    if (sr == 0) {
-                        Xu[gw] = bx[gw];
-                        Xd[gw] = bx[gw];
-                    } else {
-                        const R2 f = __ldcg(face_in + (((size_t)y * W + w) * GW + gw) * 32 + lane);
-                        Xu[gw] = f.x;
-                        Xd[gw] = f.y;
-                    }
+                    X0[gw] = bx[gw];
+                    X1[gw] = bx[gw];
                 }
-                for (int i = 0; i < ws; ++i) {
-                    const int xo = sx > 0 ? i : ws - 1 - i;
-                    const int cell = y * nx + x0 + xo;
-                    RT s[4] = {0, 0, 0, 0}, ss[4] = {0, 0, 0, 0};
+            } else if (global_in) {
+                ok = flag_wait_geq(upflag, ep | (unsigned long long)(jj + 1), seen, A.ctrl,
+                                   A.timeout_ns, &s_abort);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
 #pragma unroll
-                    for (int gw = 0; gw < GW; ++gw) {
-                        const int g = gidx[gw];
-                        RT S[4];
-                        ld4_ro(Qp + ((size_t)g * ncell + cell) * 4, S);
-                        const R2 sg = __ldg(SGp + (size_t)g * ncell + cell);
-                        const size_t ioff = (((wtbase + cell) * GW + gw) * 32 + lane) * 4;
-                        if (Ip) {
-                            RT Ik[4];
-                            ld4_stream(Ip + ioff, Ik);
-#pragma unroll
-                            for (int n = 0; n < 4; ++n) S[n] = fma(inv_cdt, Ik[n], S[n]);
-                        }
-                        R2 *yc = ycar + (((size_t)w * GW + gw) * TX + xo) * 32 + lane;
-                        RT Yu, Yd;
-                        if (jj == 0) {
-                            Yu = by[gw];
-                            Yd = by[gw];
-                        } else {
-                            const R2 t = *yc;
-                            Yu = t.x;
-                            Yd = t.y;
-                        }
-                        const RT iA = rcp(sg.x + mu + eta);
-                        const RT m = mu * iA, e = eta * iA;
-                        const RT ruu = (S[nuu] + two * (mu * Xu[gw] + eta * Yu)) * iA;
-                        const RT rdu = fma(two * eta, Yd, S[ndu]) * iA;
-                        const RT rud = fma(two * mu, Xd[gw], S[nud]) * iA;
-                        const RT rdd = S[ndd] * iA;
-                        const RT P = fma(m, m, fma(e, e, (RT)1));
-                        const RT z = two * m * e;
-                        const RT iD = rcp(fma(P, P, -z * z));
-                        const RT wuu = fma(P, ruu, z * rdd);
-                        const RT wdu = fma(P, rdu, -z * rud);
-                        const RT wud = fma(P, rud, -z * rdu);
-                        const RT wdd = fma(P, rdd, z * ruu);
-                        RT I4[4];
-                        I4[nuu] = (wuu - m * wdu - e * wud) * iD;
-                        I4[ndu] = (wdu + m * wuu - e * wdd) * iD;
-                        I4[nud] = (wud - m * wdd + e * wuu) * iD;
-                        I4[ndd] = (wdd + m * wud + e * wdu) * iD;
-                        st4_stream(Io + ioff, I4);
-                        R2 yo;
-                        yo.x = I4[nud];
-                        yo.y = I4[ndd];
-                        *yc = yo;
-                        Xu[gw] = I4[ndu];
-                        Xd[gw] = I4[ndd];
-#pragma unroll
-                        for (int n = 0; n < 4; ++n) {
-                            s[n] += I4[n];
-                            ss[n] = fma(sg.y, I4[n], ss[n]);
-                        }
-                    }
-                    RT v[36];
-#pragma unroll
-                    for (int n = 0; n < 4; ++n) {
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) v[n * 9 + k] = wm[k] * s[n];
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) v[n * 9 + 6 + k] = wm[k] * ss[n];
-                    }
-                    TRed<16, 32, RT>::run(v, lane);
-                    TRed<16, 4, RT>::run(v + 32, lane);
-                    RT *ms = msm + (((size_t)buf * W + w) * TX + xo) * 36;
-                    ms[lane] = v[0];
-                    if ((lane & 7) == 0) ms[32 + (lane >> 3)] = v[32];
+                for (int gw = 0; gw < GW; ++gw) {
+                    const R2 f = __ldcg(face + ((fidx_in + y) * GW + gw) * 32 + lane);
+                    X0[gw] = f.x;
+                    X1[gw] = f.y;
                 }
-                if (publish) {
+            } else if (w > 0) {
+                ok = smem_wait_geq(rows_done + (w - 1), jj + 1, A.ctrl, A.timeout_ns, &s_abort);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                __threadfence_block();
 #pragma unroll
-                    for (int gw = 0; gw < GW; ++gw) {
-                        R2 f;
-                        f.x = Xu[gw];
-                        f.y = Xd[gw];
-                        __stcg(face_out + (((size_t)y * W + w) * GW + gw) * 32 + lane, f);
-                    }
+                for (int gw = 0; gw < GW; ++gw) {
+                    const R2 f = ring_in[(slot * GW + gw) * 32 + lane];
+                    X0[gw] = f.x;
+                    X1[gw] = f.y;
                 }
             }
-            __syncthreads();
-            if (threadIdx.x == 0 && publish && !(A.fault_skip_publish && sr == 0)) {
-                __threadfence();
-                st_release(myflag, ep | (unsigned long long)(jj + 1));
+            // (b) this row's prefetched I^k and sources
+            ok = mbar_wait(mybars + st, (phase >> st) & 1u, A.ctrl, A.timeout_ns, &s_abort);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            phase ^= 1u << st;
+            consumed = jj + 1;
+            const unsigned char *sb = wbase + (size_t)st * stg;
+            RT Ik[GW][4], Sr[GW][4], sgt[GW], sgm[GW];
+#pragma unroll
+            for (int gw = 0; gw < GW; ++gw) {
+                if (Ip) {
+                    lds4(reinterpret_cast<const RT *>(sb) + ((size_t)gw * 32 + lane) * 4, Ik[gw]);
+                } else {
+                    Ik[gw][0] = Ik[gw][1] = Ik[gw][2] = Ik[gw][3] = (RT)0;
+                }
+                const RT *rec = reinterpret_cast<const RT *>(sb + bytes_I) +
+                                (size_t)(gw * A.LG + g_lo) * SREC;
+                lds4(rec, Sr[gw]);
+                sgt[gw] = rec[4];
+                sgm[gw] = rec[5];
             }
-            RT *pdst = part + ((size_t)ch * ncell + (size_t)y * nx + x0) * 36;
-            for (int e = threadIdx.x; e < ws * 36; e += blockDim.x) {
-                const int xo = e / 36, k = e - xo * 36;
-                RT acc = 0;
-                for (int w2 = 0; w2 < nvalid; ++w2)
-                    acc += msm[(((size_t)buf * W + w2) * TX + xo) * 36 + k];
-                pdst[e] = acc;
+            __syncwarp();
+            if (lane == 0) {
+                if (w > 0) {
+                    __threadfence_block();
+                    cons[w - 1] = jj + 1;  // ring slot of the upwind column is free again
+                }
+                if (jj + S < ny) {
+                    fence_proxy_async_smem();
+                    issue(jj + S);
+                }
             }
+            if (jj + S < ny) issued = jj + S;
+            // (c) cell solves
+            RT s4[4] = {0, 0, 0, 0}, ss4[4] = {0, 0, 0, 0};
+            const int cell = y * nx + xw;
+#pragma unroll
+            for (int gw = 0; gw < GW; ++gw) {
+                RT Sn[4];
+#pragma unroll
+                for (int n = 0; n < 4; ++n) Sn[n] = fma(inv_cdt, Ik[gw][n], Sr[gw][n]);
+                const RT iA = rcp(sgt[gw] + mu + eta);
+                const RT m = mu * iA, e = eta * iA;
+                const RT ruu = (Sn[nuu] + two * (mu * X0[gw] + eta * Y0[gw])) * iA;
+                const RT rdu = fma(two * eta, Y1[gw], Sn[ndu]) * iA;
+                const RT rud = fma(two * mu, X1[gw], Sn[nud]) * iA;
+                const RT rdd = Sn[ndd] * iA;
+                const RT P = fma(m, m, fma(e, e, (RT)1));
+                const RT z = two * m * e;
+                const RT iD = rcp(fma(P, P, -z * z));
+                const RT wuu = fma(P, ruu, z * rdd);
+                const RT wdu = fma(P, rdu, -z * rud);
+                const RT wud = fma(P, rud, -z * rdu);
+                const RT wdd = fma(P, rdd, z * ruu);
+                RT I4[4];
+                I4[nuu] = (wuu - m * wdu - e * wud) * iD;
+                I4[ndu] = (wdu + m * wuu - e * wdd) * iD;
+                I4[nud] = (wud - m * wdd + e * wuu) * iD;
+                I4[ndd] = (wdd + m * wud + e * wdu) * iD;
+                st4_stream(Io + (((wtbase + cell) * GW + gw) * 32 + lane) * 4, I4);
+                X0[gw] = I4[ndu];  // x-outflow -> next column
+                X1[gw] = I4[ndd];
+                Y0[gw] = I4[nud];  // y-outflow -> next row
+                Y1[gw] = I4[ndd];
+#pragma unroll
+                for (int n = 0; n < 4; ++n) {
+                    s4[n] += I4[n];
+                    ss4[n] = fma(sgm[gw], I4[n], ss4[n]);
+                }
+            }
+            // (d) hand the x-outflow downwind
+            if (w < ws - 1) {
+                ok = smem_wait_geq(cons + w, jj + 1 - RING, A.ctrl, A.timeout_ns, &s_abort);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+#pragma unroll
+                for (int gw = 0; gw < GW; ++gw) {
+                    R2 f;
+                    f.x = X0[gw];
+                    f.y = X1[gw];
+                    ring_out[(slot * GW + gw) * 32 + lane] = f;
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence_block();
+                    rows_done[w] = jj + 1;
+                }
+            } else if (global_out) {
+#pragma unroll
+                for (int gw = 0; gw < GW; ++gw) {
+                    R2 f;
+                    f.x = X0[gw];
+                    f.y = X1[gw];
+                    __stcg(face + ((fidx_out + y) * GW + gw) * 32 + lane, f);
+                }
+                __syncwarp();
+                if (lane == 0 && !(A.fault_skip_publish && sr == 0)) {
+                    __threadfence();
+                    st_release(myflag, ep | (unsigned long long)(jj + 1));
+                }
+            }
+            // (e) moments of this cell
+            RT v[36];
+#pragma unroll
+            for (int n = 0; n < 4; ++n) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) v[n * 9 + k] = wm[k] * s4[n];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) v[n * 9 + 6 + k] = wm[k] * ss4[n];
+            }
+            warp_moments_add(v, lane, acc + (size_t)cell * 36);
         }
-        __syncthreads();
+        if (!ok) {
+            // wait (bounded) for this warp's copies still in flight, then leave
+            const long long t0 = global_ns();
+            for (int r = consumed; r <= issued; ++r) {
+                const int st = r % S;
+                while (!mbar_try_wait(mybars + st, (phase >> st) & 1u)) {
+                    if (global_ns() - t0 > A.timeout_ns) break;
+                }
+                phase ^= 1u << st;
+            }
+            s_abort = 1;
+        }
     }
 }
 
@@ -341,9 +559,7 @@ __global__ void __launch_bounds__(256) sweep1d_kernel(const SweepArgs A) {
     const LaneConst &L = A.lanes[(q * A.DB + db) * 32 + lane];
     const RT mu = (RT)L.mu;
     const RT w0 = (RT)L.wm[0], w1 = (RT)L.wm[1], w2 = (RT)L.wm[2];
-    const RT *Qp = static_cast<const RT *>(A.Q);
-    const R2 *Qv = reinterpret_cast<const R2 *>(Qp);
-    const R2 *SGp = static_cast<const R2 *>(A.SG);
+    const RT *src = static_cast<const RT *>(A.src);
     const RT *inflow = static_cast<const RT *>(A.inflow);
     const R2 *Ip = static_cast<const R2 *>(A.I_prev);
     R2 *Io = static_cast<R2 *>(A.I_out);
@@ -365,9 +581,9 @@ __global__ void __launch_bounds__(256) sweep1d_kernel(const SweepArgs A) {
         RT s[2] = {0, 0}, ss[2] = {0, 0};
 #pragma unroll
         for (int gw = 0; gw < GW; ++gw) {
-            const int g = gidx[gw];
-            const R2 qv = __ldg(Qv + (size_t)g * ncell + cell);
-            const R2 sg = __ldg(SGp + (size_t)g * ncell + cell);
+            const RT *rec = src + ((size_t)cell * A.Gp + gidx[gw]) * SREC;
+            const R2 qv = __ldg(reinterpret_cast<const R2 *>(rec));
+            const RT sgt = __ldg(rec + 4), sgm = __ldg(rec + 5);
             RT S[2] = {qv.x, qv.y};
             const size_t ioff = ((wtbase + cell) * GW + gw) * 32 + lane;
             if (Ip) {
@@ -375,7 +591,7 @@ __global__ void __launch_bounds__(256) sweep1d_kernel(const SweepArgs A) {
                 S[0] = fma(inv_cdt, ik.x, S[0]);
                 S[1] = fma(inv_cdt, ik.y, S[1]);
             }
-            const RT iA = rcp(sg.x + mu);
+            const RT iA = rcp(sgt + mu);
             const RT m = mu * iA;
             const RT r1 = fma(two * mu, X[gw], S[au]) * iA;
             const RT r2 = S[1 - au] * iA;
@@ -391,7 +607,7 @@ __global__ void __launch_bounds__(256) sweep1d_kernel(const SweepArgs A) {
 #pragma unroll
             for (int n = 0; n < 2; ++n) {
                 s[n] += I2[n];
-                ss[n] = fma(sg.y, I2[n], ss[n]);
+                ss[n] = fma(sgm, I2[n], ss[n]);
             }
         }
         RT v[10];
@@ -412,12 +628,6 @@ __global__ void __launch_bounds__(256) sweep1d_kernel(const SweepArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-template <typename RT, int GW>
-static cudaError_t launch2d_t(const SweepArgs &a, int grid, size_t smem, cudaStream_t s) {
-    sweep2d_kernel<RT, GW><<<grid, a.W * 32, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
 template <typename RT>
 static const void *kernel2d_ptr(int GW) {
     switch (GW) {
@@ -428,29 +638,21 @@ static const void *kernel2d_ptr(int GW) {
 }
 
 cudaError_t launch_sweep2d(const sm_problem *p, const SweepArgs &a, int grid, cudaStream_t s) {
-    const size_t smem = sweep2d_smem_bytes(p->prec, a.W, a.GW, a.TX);
-    if (p->prec == 32) {
-        switch (a.GW) {
-            case 1: return launch2d_t<float, 1>(a, grid, smem, s);
-            case 2: return launch2d_t<float, 2>(a, grid, smem, s);
-            default: return launch2d_t<float, 4>(a, grid, smem, s);
-        }
-    }
-    switch (a.GW) {
-        case 1: return launch2d_t<double, 1>(a, grid, smem, s);
-        case 2: return launch2d_t<double, 2>(a, grid, smem, s);
-        default: return launch2d_t<double, 4>(a, grid, smem, s);
-    }
+    const size_t smem = sweep2d_smem_bytes(p->prec, a.W, a.GW, a.S, a.GW * a.LG);
+    const void *k = (p->prec == 32) ? kernel2d_ptr<float>(a.GW) : kernel2d_ptr<double>(a.GW);
+    SweepArgs args = a;
+    void *params[] = {&args};
+    return cudaLaunchKernel(k, dim3(grid), dim3(a.W * 32), params, smem, s);
 }
 
-// Configures the shared-memory limit of the 2D kernel for (W, current GW,
-// TX) and returns how many CTAs fit on the whole GPU (0 if none).
-int sweep2d_max_resident(const sm_problem *p, int W, size_t *smem_out) {
-    const size_t smem = sweep2d_smem_bytes(p->prec, W, p->GW, p->TX);
+// Configures the shared-memory limit of the 2D kernel for (W, S) and returns
+// how many CTAs fit on the whole GPU (0 if none).
+int sweep2d_max_resident(const sm_problem *p, int W, int S, size_t *smem_out) {
+    const size_t smem = sweep2d_smem_bytes(p->prec, W, p->GW, S, p->GSLOT);
     if (smem_out) *smem_out = smem;
     const void *k = (p->prec == 32) ? kernel2d_ptr<float>(p->GW) : kernel2d_ptr<double>(p->GW);
     int dev = 0, nsm = 0, maxopt = 0;
-    cudaGetDevice(&dev);
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (smem + 64 > (size_t)maxopt) return 0;

@@ -70,8 +70,8 @@ def test_invalid_descriptors_rejected_before_cuda(lib):
         return rc, so.sm_last_error().decode()
 
     for kw in (dict(nx=0), dict(ny=0), dict(dim=3), dict(n_groups=0), dict(precision=16),
-               dict(x1=0.0), dict(n_polar=0), dict(groups_per_warp=3), dict(tile_x=65),
-               dict(warps_per_cta=17), dict(a=0.0), dict(opacity_kind=7)):
+               dict(x1=0.0), dict(n_polar=0), dict(groups_per_warp=3), dict(strip_width=17),
+               dict(prefetch_rows=9), dict(a=0.0), dict(opacity_kind=7)):
         rc, msg = create(**kw)
         assert rc == 1, (kw, rc, msg)
         assert msg
