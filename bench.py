@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--nx", type=int, default=0, help="override cells per axis (profiling cases)")
     ap.add_argument("--groups", type=int, default=0, help="override the group count")
     return ap.parse_args()
@@ -243,6 +244,10 @@ def main():
         clo = prob.new_closures()
         prob.sweep(T, sigma, None, I[0], mom, clo)  # realistic I^k: one step of history
         prob.synchronize()
+        if not args.no_autotune:  # pick the strip width / prefetch depth (outside timing)
+            prob.autotune(T, sigma, I[0], I[1], reps=2)
+            prob.sweep(T, sigma, None, I[0], mom, clo)
+            prob.synchronize()
 
         def step(i):
             prob.sweep(T, sigma, I[i % 2], I[(i + 1) % 2], mom, clo)

@@ -68,7 +68,7 @@ typedef struct {
     double T_bdr[4];           /* boundary temperature per side: left, right, bottom, top;
                                   <= 0 means vacuum (zero inflow) */
     int precision;             /* sweep arithmetic: 32 (FP32) or 64 (FP64) */
-    int groups_per_warp;       /* (d,g) slots per lane of a warp task: 1, 2, 4; 0 = auto */
+    int groups_per_warp;       /* (d,g) slots per lane of a warp task: 1, 2, 4, 8; 0 = auto */
     int strip_width;           /* 2D: cell columns per CTA, one warp per column, 1..16; 0 = auto */
     int prefetch_rows;         /* 2D: rows each warp prefetches by TMA, 2..8; 0 = auto */
 } sm_problem_desc;

@@ -305,8 +305,8 @@ sm_status sm_create_problem(const sm_problem_desc *d, void *stream, sm_problem *
     if (d->opacity_kind != SM_OPACITY_POWER && d->opacity_kind != SM_OPACITY_LARSEN)
         return fail(SM_ERR_INVALID_ARG, "unknown opacity_kind");
     if (d->groups_per_warp != 0 && d->groups_per_warp != 1 && d->groups_per_warp != 2 &&
-        d->groups_per_warp != 4)
-        return fail(SM_ERR_INVALID_ARG, "groups_per_warp must be 0, 1, 2 or 4");
+        d->groups_per_warp != 4 && d->groups_per_warp != 8)
+        return fail(SM_ERR_INVALID_ARG, "groups_per_warp must be 0, 1, 2, 4 or 8");
     if (d->strip_width < 0 || d->strip_width > 16)
         return fail(SM_ERR_INVALID_ARG, "strip_width out of range (0..16)");
     if (d->prefetch_rows < 0 || d->prefetch_rows > 8 || d->prefetch_rows == 1)
@@ -380,7 +380,9 @@ sm_status sm_create_problem(const sm_problem_desc *d, void *stream, sm_problem *
     int GW = d->groups_per_warp;
     if (GW == 0) {
         const int gpl = (p->G + p->LG - 1) / p->LG;  // slots per lane if GW were unlimited
-        GW = gpl >= 4 ? 4 : (gpl >= 2 ? 2 : 1);
+        const int gmax = d->precision == 32 ? 8 : 4;
+        GW = 1;
+        while (GW < gmax && gpl >= 2 * GW) GW *= 2;
     }
     p->GW = GW;
     p->GSLOT = GW * p->LG;
@@ -471,7 +473,7 @@ sm_status sm_create_problem(const sm_problem_desc *d, void *stream, sm_problem *
     if (p->dim == 2) {
         int W = d->strip_width, S = d->prefetch_rows;
         if (W == 0) W = 8;
-        if (S == 0) S = p->prec == 32 ? 4 : 3;
+        if (S == 0) S = 2;
         st = apply_tiling(p, W, S);
         if (st && d->strip_width == 0 && d->prefetch_rows == 0) st = apply_tiling(p, 2, 2);
         if (st) {
@@ -692,8 +694,8 @@ sm_status sm_autotune(sm_problem *p, const double *T, const double *sigma, const
     if (I_prev == I_out) return fail(SM_ERR_INVALID_ARG, "I_prev_dev must not alias I_out_dev");
     if ((st = check_intensity_align(I_prev, I_out))) return st;
     if (reps < 1) reps = 3;
-    const int w_c[] = {2, 4, 8, 16};
-    const int s_c[] = {2, 3, 4, 6};
+    const int w_c[] = {2, 4, 6, 8, 12, 16};
+    const int s_c[] = {2, 3, 4};
     int best_w = p->W, best_s = p->S;
     float best_ms = 1e30f;
     const bool prof = p->profiling;

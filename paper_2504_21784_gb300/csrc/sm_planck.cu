@@ -7,7 +7,8 @@
 //   x <  2: x^3/3 - x^4/8 + sum_k B_2k x^(2k+3) / ((2k)! (2k+3))
 //   x >= 2: 1 - (15/pi^4) sum_n e^{-nx} (x^3/n + 3x^2/n^2 + 6x/n^3 + 6/n^4)
 // and the Rosseland integral by parts, R(x) = P(x) - (15/4pi^4) x^4/(e^x-1),
-// which gives r_g with dB_g/dT = 4 a c T^3 r_g (Sec. 2).  A group whose lower
+// which gives r_g with dB_g/dT = 4 a c T^3 r_g (Sec. 2); for x < 2 the factor
+// x/(e^x-1) is the Bernoulli generating series itself.  A group whose lower
 // reduced edge is in the tail branch is differenced in tails (1 - P) to keep
 // relative accuracy; the lowest edge is 0 and the highest infinity so that
 // sum_g b_g = 1.
@@ -27,6 +28,7 @@ constexpr double C15 = 15.0 / (PI_D * PI_D * PI_D * PI_D);
 // (-1)^(k+1) 2 zeta(2k) / (2 pi)^(2k); zeta(2k) summed directly with an
 // Euler-Maclaurin tail (k >= 2) and zeta(2) = pi^2/6.
 __constant__ double c_head[NBERN];
+__constant__ double c_bern[NBERN];   // B_2k/(2k)!, k = 1..NBERN
 __constant__ double c_inv_n[NTAIL][4];
 
 static bool g_tables_ready[128] = {false};
@@ -35,7 +37,7 @@ void planck_upload_tables(void) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return;
     if (g_tables_ready[dev]) return;
-    double head[NBERN];
+    double head[NBERN], bern[NBERN];
     for (int k = 1; k <= NBERN; ++k) {
         const int s = 2 * k;
         double zeta;
@@ -53,6 +55,7 @@ void planck_upload_tables(void) {
         double bk = 2.0 * zeta / pow(2.0 * PI_D, s);
         if (k % 2 == 0) bk = -bk;
         head[k - 1] = bk / (2.0 * k + 3.0);
+        bern[k - 1] = bk;
     }
     double invn[NTAIL][4];
     for (int n = 1; n <= NTAIL; ++n) {
@@ -63,6 +66,7 @@ void planck_upload_tables(void) {
         invn[n - 1][3] = r * r * r * r;
     }
     if (cudaMemcpyToSymbol(c_head, head, sizeof(head)) == cudaSuccess &&
+        cudaMemcpyToSymbol(c_bern, bern, sizeof(bern)) == cudaSuccess &&
         cudaMemcpyToSymbol(c_inv_n, invn, sizeof(invn)) == cudaSuccess)
         g_tables_ready[dev] = true;
 }
@@ -86,14 +90,20 @@ __device__ __forceinline__ EdgeVals edge_vals(double x) {
     }
     if (x < XSWITCH) {
         const double y = x * x;
-        double poly = c_head[NBERN - 1];
+        double poly = c_head[NBERN - 1], pb = c_bern[NBERN - 1];
 #pragma unroll
-        for (int k = NBERN - 2; k >= 0; --k) poly = fma(poly, y, c_head[k]);
+        for (int k = NBERN - 2; k >= 0; --k) {
+            poly = fma(poly, y, c_head[k]);
+            pb = fma(pb, y, c_bern[k]);
+        }
         poly *= y;
-        const double s = x * x * x * ((1.0 / 3.0) - 0.125 * x + poly);
+        pb *= y;
+        const double x3 = y * x;
+        const double s = x3 * ((1.0 / 3.0) - 0.125 * x + poly);
         e.P = C15 * s;
         e.Q = 1.0 - e.P;
-        const double rx = 0.25 * C15 * (y * y) / expm1(x);
+        // x^4/(e^x - 1) = x^3 * x/(e^x - 1), with x/(e^x - 1) = 1 - x/2 + sum B_2k x^2k/(2k)!
+        const double rx = 0.25 * C15 * x3 * (1.0 - 0.5 * x + pb);
         e.R = e.P - rx;
         e.RQ = e.Q + rx;
         e.tail = false;
@@ -102,11 +112,11 @@ __device__ __forceinline__ EdgeVals edge_vals(double x) {
     const double e1 = exp(-x);
     const int nmax = min(NTAIL, (int)(40.0 / x) + 2);
     double en = 1.0, sum = 0.0;
-    const double x2 = x * x, x3 = x2 * x;
+    const double x2 = x * x, x3 = x2 * x, x2_3 = 3.0 * x2, x_6 = 6.0 * x;
     for (int n = 0; n < nmax; ++n) {
         en *= e1;
-        const double t = x3 * c_inv_n[n][0] + 3.0 * x2 * c_inv_n[n][1] + 6.0 * x * c_inv_n[n][2] +
-                         6.0 * c_inv_n[n][3];
+        const double t = fma(x3, c_inv_n[n][0],
+                             fma(x2_3, c_inv_n[n][1], fma(x_6, c_inv_n[n][2], 6.0 * c_inv_n[n][3])));
         sum = fma(en, t, sum);
     }
     e.Q = C15 * sum;
@@ -179,7 +189,9 @@ __global__ void emission_kernel(int ncell, int nn, int G, int Gp, const double *
     RT *rec0 = src + (size_t)cell * Gp * 8;
     for (int g = 0; g < G; ++g) {
         const double xhi = (g == G - 1) ? INFINITY : edges[g + 1] * invT;
-        const EdgeVals hi = edge_vals(xhi);
+        // beyond x ~ 745 the tails 1 - P and 1 - R underflow to exactly 0, so
+        // every higher group has b = r = 0: skip their series
+        const EdgeVals hi = (lo.tail && lo.Q == 0.0 && lo.RQ == 0.0) ? lo : edge_vals(xhi);
         double b, r;
         group_br(lo, hi, b, r);
         const double sg = sigma[(size_t)g * ncell + cell];

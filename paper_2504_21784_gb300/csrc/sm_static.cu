@@ -106,8 +106,9 @@ sm_status sm_sweep_static(const sm_problem_desc *d, void *stream, const double *
         return static_fail(SM_ERR_INVALID_ARG, "precision must be 32 or 64");
     if (d->opacity_kind != SM_OPACITY_POWER && d->opacity_kind != SM_OPACITY_LARSEN)
         return static_fail(SM_ERR_INVALID_ARG, "unknown opacity_kind");
-    if (d->groups_per_warp < 0 || d->groups_per_warp > 4 || d->groups_per_warp == 3)
-        return static_fail(SM_ERR_INVALID_ARG, "groups_per_warp must be 0, 1, 2 or 4");
+    if (d->groups_per_warp != 0 && d->groups_per_warp != 1 && d->groups_per_warp != 2 &&
+        d->groups_per_warp != 4 && d->groups_per_warp != 8)
+        return static_fail(SM_ERR_INVALID_ARG, "groups_per_warp must be 0, 1, 2, 4 or 8");
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)

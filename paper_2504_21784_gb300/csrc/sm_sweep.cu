@@ -149,13 +149,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsign
     }
 }
 
-// Bounded wait (every lane) until a shared counter reaches target.
+// Bounded wait (every lane) until a shared counter reaches target.  The
+// neighbouring warp usually publishes within a few hundred cycles, so the
+// wait spins on the shared counter first and only then backs off with
+// __nanosleep (a sleeping warp can oversleep by about a microsecond).
 __device__ __forceinline__ bool smem_wait_geq(volatile int *cnt, int target, unsigned int *ctrl,
                                               long long timeout_ns, volatile int *s_abort) {
     if (*cnt >= target) return true;
+#pragma unroll 1
+    for (int spin = 0; spin < 256; ++spin)
+        if (*cnt >= target) return true;
     const long long t0 = global_ns();
     for (unsigned it = 1;; ++it) {
-        __nanosleep(20);
+        __nanosleep(32);
         if (*cnt >= target) return true;
         if ((it & 15) == 0) {
             if (*s_abort) return false;
@@ -215,58 +221,34 @@ template <int OFF, int CNT, typename RT> struct TRed {
     }
 };
 
-// Reduce 36 per-lane values over the warp and add them to acc[0..35].
-// FP32: lanes end with 4 consecutive sums and use 16-byte vector atomics.
-__device__ __forceinline__ void warp_moments_add(float *v, int lane, float *acc) {
-    // first 32 values: transpose over offsets 16, 8, 4 -> 4 values per lane
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        const int off = 16 >> s;
-        const int H = 16 >> s;
-        const bool up = (lane & off) != 0;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            if (i < H) {
-                const float send = up ? v[i] : v[i + H];
-                const float keep = up ? v[i + H] : v[i];
-                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-            }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        v[i] += __shfl_xor_sync(0xffffffffu, v[i], 2);
-        v[i] += __shfl_xor_sync(0xffffffffu, v[i], 1);
-    }
-    if ((lane & 3) == 0)
-        atomicAdd(reinterpret_cast<float4 *>(acc + lane), make_float4(v[0], v[1], v[2], v[3]));
-    // last 4 values: full butterfly, lane 0 adds them
-    float *t = v + 32;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) t[i] += __shfl_xor_sync(0xffffffffu, t[i], off);
-    }
-    if (lane == 0) atomicAdd(reinterpret_cast<float4 *>(acc + 32), make_float4(t[0], t[1], t[2], t[3]));
-}
-__device__ __forceinline__ void warp_moments_add(double *v, int lane, double *acc) {
-    TRed<16, 32, double>::run(v, lane);
-    TRed<16, 4, double>::run(v + 32, lane);
-    atomicAdd(acc + lane, v[0]);
-    if ((lane & 7) == 0) atomicAdd(acc + 32 + (lane >> 3), v[32]);
-}
+constexpr int RING = 2;   // rows of x-face buffering between neighbouring warps
+constexpr int SREC = 8;   // source record: q at 4 nodes, sigma~, sigma, 2 pad
+constexpr int MROW = 36;  // padded row length of the moment transpose buffers
+constexpr int PUBLISH_ROWS = 8;  // rows per release of a strip's x-faces to the next strip
 
-constexpr int RING = 4;  // rows of x-face buffering between neighbouring warps
-constexpr int SREC = 8;  // source record: q at 4 nodes, sigma~, sigma, 2 pad
+// Reciprocal: the FP32 path uses the hardware approximation (relative error
+// below 2^-22, far inside the FP32 sweep's tolerance); FP64 stays IEEE.
+__device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp_fast(double x) { return __drcp_rn(x); }
 
 __host__ __device__ inline size_t stage_bytes(int rsize, int GW, int GSLOT) {
     return (size_t)GW * 32 * 4 * rsize + (size_t)GSLOT * SREC * rsize;
 }
+// per warp: S stages, the x-face ring, the moment transpose buffer [8][MROW]
+// and the direction weights [6][MROW]
+__host__ __device__ inline size_t warp_smem_bytes(int rsize, int GW, int GSLOT, int S) {
+    return (size_t)S * stage_bytes(rsize, GW, GSLOT) + (size_t)RING * GW * 32 * 2 * rsize +
+           (size_t)(8 + 6) * MROW * rsize;
+}
 
 size_t sweep2d_smem_bytes(int prec, int W, int GW, int S, int GSLOT) {
     const int rs = prec == 32 ? 4 : 8;
-    const size_t per_warp = (size_t)S * stage_bytes(rs, GW, GSLOT) + (size_t)RING * GW * 32 * 2 * rs;
-    return (size_t)W * per_warp + (size_t)W * S * 8 + 2 * W * sizeof(int) + 64;
+    return (size_t)W * warp_smem_bytes(rs, GW, GSLOT, S) + (size_t)W * S * 8 + 2 * W * sizeof(int) +
+           64;
 }
 
 // ---------------------------------------------------------------------------
@@ -282,17 +264,16 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs A) {
     const int nx = A.nx, ny = A.ny;
     const int GSLOT = GW * A.LG;
     const size_t stg = stage_bytes((int)sizeof(RT), GW, GSLOT);
-    const size_t ring_bytes = (size_t)RING * GW * 32 * sizeof(R2);
-    unsigned char *wbase = smem_raw + (size_t)w * (S * stg + ring_bytes);
-    R2 *ring_all = reinterpret_cast<R2 *>(smem_raw + S * stg);  // + w * (S*stg + ring_bytes)
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)W * (S * stg + ring_bytes));
+    const size_t wsz = warp_smem_bytes((int)sizeof(RT), GW, GSLOT, S);
+    const size_t ring_off = (size_t)S * stg;
+    const size_t mb_off = ring_off + (size_t)RING * GW * 32 * sizeof(R2);
+    unsigned char *wbase = smem_raw + (size_t)w * wsz;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)W * wsz);
     volatile int *rows_done = reinterpret_cast<volatile int *>(bars + (size_t)W * S);
     volatile int *cons = rows_done + W;
     uint64_t *mybars = bars + (size_t)w * S;
-    auto ring_of = [&](int ww) {
-        return reinterpret_cast<R2 *>(reinterpret_cast<unsigned char *>(ring_all) +
-                                      (size_t)ww * (S * stg + ring_bytes));
-    };
+    RT *Mb = reinterpret_cast<RT *>(wbase + mb_off);  // [8][MROW]: s_n, ss_n per lane
+    RT *Wt = Mb + 8 * MROW;                           // [6][MROW]: weights per lane
     const RT *src = static_cast<const RT *>(A.src);
     const RT *inflow = static_cast<const RT *>(A.inflow);
     const RT *Ip = static_cast<const RT *>(A.I_prev);
@@ -303,6 +284,11 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs A) {
     const RT two = (RT)2;
     const uint32_t bytes_I = Ip ? (uint32_t)(GW * 32 * 4 * sizeof(RT)) : 0u;
     const uint32_t bytes_S = (uint32_t)(GSLOT * SREC * sizeof(RT));
+    // moment this lane assembles (and, for lanes 0..3, a second one): m = n*9 + k
+    const int m1 = lane, n1 = m1 / 9, k1 = m1 % 9;
+    const int vrow1 = k1 < 6 ? n1 : 4 + n1, wrow1 = k1 < 6 ? k1 : k1 - 6;
+    const int m2 = 32 + (lane & 3), k2 = m2 % 9;
+    const int vrow2 = k2 < 6 ? 3 : 7, wrow2 = k2 < 6 ? k2 : k2 - 6;
 
     if (threadIdx.x < W * S) mbar_init(bars + threadIdx.x, 1);
     if (threadIdx.x == 0) s_abort = 0;
@@ -332,9 +318,8 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs A) {
         const int db = wt / A.NGB, gb = wt - db * A.NGB;
         const LaneConst &L = A.lanes[(q * A.DB + db) * 32 + lane];
         const RT mu = (RT)L.mu, eta = (RT)L.eta;
-        RT wm[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) wm[k] = (RT)L.wm[k];
+        for (int k = 0; k < 6; ++k) Wt[k * MROW + lane] = (RT)L.wm[k];
         const int g_lo = L.g_lo;
         const int side_x = sx > 0 ? 0 : 1, side_y = sy > 0 ? 2 : 3;
         RT X0[GW], X1[GW], Y0[GW], Y1[GW];  // x-inflow (rows u,d), y-inflow (columns u,d)
@@ -360,8 +345,11 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs A) {
             A.flags + (size_t)wg * A.NS + (sr > 0 ? strip - sx : strip);
         const unsigned long long ep = A.epoch << 32;
         unsigned long long seen = 0;
-        R2 *ring_in = w > 0 ? ring_of(w - 1) : nullptr;
-        R2 *ring_out = ring_of(w);
+        const R2 *ring_in =
+            w > 0 ? reinterpret_cast<const R2 *>(smem_raw + (size_t)(w - 1) * wsz + ring_off)
+                  : nullptr;
+        R2 *ring_out = reinterpret_cast<R2 *>(wbase + ring_off);
+        __syncwarp();  // weights visible to the whole warp
 
         auto row_y = [&](int jj) { return sy > 0 ? jj : ny - 1 - jj; };
         auto issue = [&](int jj) {  // lane 0: TMA for row jj into stage jj % S
@@ -404,7 +392,7 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs A) {
                     X0[gw] = f.x;
                     X1[gw] = f.y;
                 }
-            } else if (w > 0) {
+            } else {
                 ok = smem_wait_geq(rows_done + (w - 1), jj + 1, A.ctrl, A.timeout_ns, &s_abort);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
@@ -415,6 +403,11 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs A) {
                     X0[gw] = f.x;
                     X1[gw] = f.y;
                 }
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence_block();
+                    cons[w - 1] = jj + 1;  // ring slot of the upwind column is free again
+                }
             }
             // (b) this row's prefetched I^k and sources
             ok = mbar_wait(mybars + st, (phase >> st) & 1u, A.ctrl, A.timeout_ns, &s_abort);
@@ -422,42 +415,25 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs A) {
             if (!ok) break;
             phase ^= 1u << st;
             consumed = jj + 1;
-            const unsigned char *sb = wbase + (size_t)st * stg;
-            RT Ik[GW][4], Sr[GW][4], sgt[GW], sgm[GW];
-#pragma unroll
-            for (int gw = 0; gw < GW; ++gw) {
-                if (Ip) {
-                    lds4(reinterpret_cast<const RT *>(sb) + ((size_t)gw * 32 + lane) * 4, Ik[gw]);
-                } else {
-                    Ik[gw][0] = Ik[gw][1] = Ik[gw][2] = Ik[gw][3] = (RT)0;
-                }
-                const RT *rec = reinterpret_cast<const RT *>(sb + bytes_I) +
-                                (size_t)(gw * A.LG + g_lo) * SREC;
-                lds4(rec, Sr[gw]);
-                sgt[gw] = rec[4];
-                sgm[gw] = rec[5];
-            }
-            __syncwarp();
-            if (lane == 0) {
-                if (w > 0) {
-                    __threadfence_block();
-                    cons[w - 1] = jj + 1;  // ring slot of the upwind column is free again
-                }
-                if (jj + S < ny) {
-                    fence_proxy_async_smem();
-                    issue(jj + S);
-                }
-            }
-            if (jj + S < ny) issued = jj + S;
-            // (c) cell solves
+            const RT *sbI = reinterpret_cast<const RT *>(wbase + (size_t)st * stg) + lane * 4;
+            const RT *sbS = reinterpret_cast<const RT *>(wbase + (size_t)st * stg + bytes_I) +
+                            (size_t)g_lo * SREC;
+            // (c) cell solves, reading the stage slot by slot
             RT s4[4] = {0, 0, 0, 0}, ss4[4] = {0, 0, 0, 0};
             const int cell = y * nx + xw;
+            RT *io = Io + (((wtbase + cell) * GW) * 32 + lane) * 4;
 #pragma unroll
             for (int gw = 0; gw < GW; ++gw) {
-                RT Sn[4];
+                RT Sn[4], Ik[4];
+                lds4(sbS + (size_t)gw * A.LG * SREC, Sn);
+                const RT sgt = sbS[(size_t)gw * A.LG * SREC + 4];
+                const RT sgm = sbS[(size_t)gw * A.LG * SREC + 5];
+                if (Ip) {
+                    lds4(sbI + (size_t)gw * 128, Ik);
 #pragma unroll
-                for (int n = 0; n < 4; ++n) Sn[n] = fma(inv_cdt, Ik[gw][n], Sr[gw][n]);
-                const RT iA = rcp(sgt[gw] + mu + eta);
+                    for (int n = 0; n < 4; ++n) Sn[n] = fma(inv_cdt, Ik[n], Sn[n]);
+                }
+                const RT iA = rcp_fast(sgt + mu + eta);
                 const RT m = mu * iA, e = eta * iA;
                 const RT ruu = (Sn[nuu] + two * (mu * X0[gw] + eta * Y0[gw])) * iA;
                 const RT rdu = fma(two * eta, Y1[gw], Sn[ndu]) * iA;
@@ -465,7 +441,7 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs A) {
                 const RT rdd = Sn[ndd] * iA;
                 const RT P = fma(m, m, fma(e, e, (RT)1));
                 const RT z = two * m * e;
-                const RT iD = rcp(fma(P, P, -z * z));
+                const RT iD = rcp_fast(fma(P, P, -z * z));
                 const RT wuu = fma(P, ruu, z * rdd);
                 const RT wdu = fma(P, rdu, -z * rud);
                 const RT wud = fma(P, rud, -z * rdu);
@@ -475,7 +451,7 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs A) {
                 I4[ndu] = (wdu + m * wuu - e * wdd) * iD;
                 I4[nud] = (wud - m * wdd + e * wuu) * iD;
                 I4[ndd] = (wdd + m * wud + e * wdu) * iD;
-                st4_stream(Io + (((wtbase + cell) * GW + gw) * 32 + lane) * 4, I4);
+                st4_stream(io + (size_t)gw * 128, I4);
                 X0[gw] = I4[ndu];  // x-outflow -> next column
                 X1[gw] = I4[ndd];
                 Y0[gw] = I4[nud];  // y-outflow -> next row
@@ -483,9 +459,16 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs A) {
 #pragma unroll
                 for (int n = 0; n < 4; ++n) {
                     s4[n] += I4[n];
-                    ss4[n] = fma(sgm[gw], I4[n], ss4[n]);
+                    ss4[n] = fma(sgm, I4[n], ss4[n]);
                 }
             }
+            // the stage is free: prefetch row jj + S into it
+            __syncwarp();
+            if (lane == 0 && jj + S < ny) {
+                fence_proxy_async_smem();
+                issue(jj + S);
+            }
+            if (jj + S < ny) issued = jj + S;
             // (d) hand the x-outflow downwind
             if (w < ws - 1) {
                 ok = smem_wait_geq(cons + w, jj + 1 - RING, A.ctrl, A.timeout_ns, &s_abort);
@@ -512,21 +495,40 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs A) {
                     __stcg(face + ((fidx_out + y) * GW + gw) * 32 + lane, f);
                 }
                 __syncwarp();
-                if (lane == 0 && !(A.fault_skip_publish && sr == 0)) {
+                // release the rows to the downwind strip in batches of PUBLISH_ROWS:
+                // the gpu-scope fence is paid once per batch
+                if (lane == 0 && !(A.fault_skip_publish && sr == 0) &&
+                    ((jj + 1) % PUBLISH_ROWS == 0 || jj + 1 == ny)) {
                     __threadfence();
                     st_release(myflag, ep | (unsigned long long)(jj + 1));
                 }
             }
-            // (e) moments of this cell
-            RT v[36];
+            // (e) moments of this cell: transpose through shared memory, then
+            // lane m forms moment m = n*9 + k as a dot product over the 32 lanes
 #pragma unroll
             for (int n = 0; n < 4; ++n) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) v[n * 9 + k] = wm[k] * s4[n];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) v[n * 9 + 6 + k] = wm[k] * ss4[n];
+                Mb[n * MROW + lane] = s4[n];
+                Mb[(4 + n) * MROW + lane] = ss4[n];
             }
-            warp_moments_add(v, lane, acc + (size_t)cell * 36);
+            __syncwarp();
+            RT d1 = 0, d2 = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                RT a[4], b[4], c[4], e4[4];
+                lds4(Mb + vrow1 * MROW + 4 * i, a);
+                lds4(Wt + wrow1 * MROW + 4 * i, b);
+                lds4(Mb + vrow2 * MROW + 4 * i, c);
+                lds4(Wt + wrow2 * MROW + 4 * i, e4);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    d1 = fma(a[t], b[t], d1);
+                    d2 = fma(c[t], e4[t], d2);
+                }
+            }
+            RT *ac = acc + (size_t)cell * 36;
+            atomicAdd(ac + m1, d1);
+            if (lane < 4) atomicAdd(ac + m2, d2);
+            __syncwarp();  // Mb is rewritten by the next row
         }
         if (!ok) {
             // wait (bounded) for this warp's copies still in flight, then leave
@@ -633,7 +635,8 @@ static const void *kernel2d_ptr(int GW) {
     switch (GW) {
         case 1: return (const void *)sweep2d_kernel<RT, 1>;
         case 2: return (const void *)sweep2d_kernel<RT, 2>;
-        default: return (const void *)sweep2d_kernel<RT, 4>;
+        case 4: return (const void *)sweep2d_kernel<RT, 4>;
+        default: return (const void *)sweep2d_kernel<RT, 8>;
     }
 }
 
@@ -673,13 +676,15 @@ cudaError_t launch_sweep1d(const sm_problem *p, const SweepArgs &a, cudaStream_t
         switch (a.GW) {
             case 1: sweep1d_kernel<float, 1><<<blocks, threads, 0, s>>>(a); break;
             case 2: sweep1d_kernel<float, 2><<<blocks, threads, 0, s>>>(a); break;
-            default: sweep1d_kernel<float, 4><<<blocks, threads, 0, s>>>(a); break;
+            case 4: sweep1d_kernel<float, 4><<<blocks, threads, 0, s>>>(a); break;
+            default: sweep1d_kernel<float, 8><<<blocks, threads, 0, s>>>(a); break;
         }
     } else {
         switch (a.GW) {
             case 1: sweep1d_kernel<double, 1><<<blocks, threads, 0, s>>>(a); break;
             case 2: sweep1d_kernel<double, 2><<<blocks, threads, 0, s>>>(a); break;
-            default: sweep1d_kernel<double, 4><<<blocks, threads, 0, s>>>(a); break;
+            case 4: sweep1d_kernel<double, 4><<<blocks, threads, 0, s>>>(a); break;
+            default: sweep1d_kernel<double, 8><<<blocks, threads, 0, s>>>(a); break;
         }
     }
     return cudaGetLastError();
