@@ -133,7 +133,7 @@ def measured_peaks():
 def recorded_traffic(prec: int, cfg=None):
     """DRAM bytes per sweep launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"sweep2d_multigroup2d_fp{prec}_traffic.json")
+    path = os.path.join(ROOT, "profiles", f"sweep2d_multigroup2d_fp{prec}_traffic.txt")
     src = os.path.join(ROOT, "paper_2504_21784_gb300", "csrc", "sm_sweep.cu")
     if not os.path.exists(path):
         return None
