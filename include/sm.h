@@ -41,7 +41,7 @@ typedef enum {
     SM_ERR_INVALID_ARG = 1,    /* bad descriptor, size or pointer */
     SM_ERR_CUDA = 2,           /* a CUDA runtime call failed */
     SM_ERR_OOM = 3,            /* device allocation failed */
-    SM_ERR_NO_CONVERGENCE = 4, /* reserved for the iterative low-order solve */
+    SM_ERR_NO_CONVERGENCE = 4, /* conjugate gradients broke down in the low-order solve */
     SM_ERR_NONPHYSICAL = 5,    /* non-positive temperature or NaN input */
     SM_ERR_TIMEOUT = 6,        /* a device wavefront wait exceeded its time limit */
     SM_ERR_UNSUPPORTED = 7     /* valid but not implemented (e.g. a tile shape) */
@@ -166,6 +166,91 @@ sm_status sm_sweep(sm_problem *p, const double *T_nodal_dev, const double *sigma
  * 1D [E, F, T, sigE, sigF, sigP, C];  E = phi / c. */
 sm_status sm_closures(sm_problem *p, const double *moments_dev, const double *T_nodal_dev,
                       const double *sigma_dev, double *closures_dev);
+
+/* ------------------------------------------------------------------------
+ * Gray low-order solve and the full time step (Sec. 4 independent LDG
+ * system, Sec. 5 Newton iteration, Algorithm 1).  All low-order arithmetic
+ * is FP64 on the device; the host only drives the iterations (it reads a
+ * few scalars per conjugate-gradient chunk and per Newton iteration), so
+ * both calls synchronize the problem's stream and cannot be captured into
+ * a CUDA graph.
+ * ---------------------------------------------------------------------- */
+
+/* Iteration controls.  Defaults (sm_default_step_params) are the paper's
+ * (Sec. 6): eps = 1e-3 in Eq. relative_tol for the outer and the Newton
+ * iterations, 1e-10 relative residual for conjugate gradients and for the
+ * pointwise elimination, caps of 100 outer, 30 Newton and 40 elimination
+ * iterations.  The paper preconditions conjugate gradients with algebraic
+ * multigrid and caps it at 50; this library preconditions with the exact
+ * diagonal of the Schur complement (Jacobi), which needs more iterations,
+ * so max_pcg defaults to 5000. */
+typedef struct {
+    double eps_outer;   /* Eq. relative_tol for Algorithm 1's fixed point */
+    double eps_inner;   /* Eq. relative_tol for the low-order Newton iteration */
+    double pcg_rtol;    /* stop when ||b - S E||_2 <= pcg_rtol ||b||_2 */
+    double elim_rtol;   /* pointwise elimination stops when |dT| <= elim_rtol |T| */
+    double T_floor;     /* lower bound imposed on T by the elimination */
+    int max_outer, max_inner, max_pcg, max_elim;
+} sm_step_params;
+
+/* Iteration counts of one call. */
+typedef struct {
+    int outer_iters;        /* Algorithm 1 iterations (0 for sm_loworder_newton) */
+    int newton_iters_total; /* low-order Newton iterations, summed over outer iterations */
+    int newton_iters_max;   /* ... largest in one low-order solve */
+    int pcg_iters_total;    /* conjugate-gradient iterations, summed */
+    int pcg_iters_max;      /* ... largest in one linear solve */
+    int pcg_capped;         /* linear solves that stopped at max_pcg */
+    int elim_iters_max;     /* largest pointwise elimination count at any node */
+    int converged;          /* 1 when the outer iteration met eps_outer within max_outer */
+    double last_change;     /* ||u^{l} - u^{l-1}||_2, u = (T, E), of the last outer iteration */
+} sm_step_stats;
+
+void sm_default_step_params(sm_step_params *params_host);
+
+/* Solve the gray low-order system with fixed closures by the Newton
+ * iteration of Sec. 5: gray opacities frozen, emission linearised about the
+ * current T with the pseudo-fission coefficient of Eq. pseudo_fission, the
+ * linear system reduced to the Schur complement in E (Eq. schur; symmetric
+ * positive definite), solved by Jacobi-preconditioned conjugate gradients,
+ * F recovered by back-substitution and T updated by the pointwise
+ * nonlinear elimination of Eq. nonlinear_T_update; stops by
+ * Eq. relative_tol on u = (T, E).
+ *   closures_dev[cell][node][n_closures]: as produced by sm_closures;
+ *   T_star_dev[cell][node]: temperature at the previous time step (T*);
+ *   cv_dev[cell][node]: heat capacity C_v (> 0);
+ *   moments_star_dev[cell][node][n_moments]: moments of the previous step's
+ *     intensity; E* = phi / c and F* = F are the time-edge sources (Sec. 6.1);
+ *   T_dev, E_dev [cell][node]: initial guesses on entry, solution on exit;
+ *   F_dev[cell][node][dim]: flux of the last linear solve (out).
+ * Boundary: Marshak-type with the gray isotropic inflow of desc.T_bdr.
+ * Needs desc.dt > 0.  Errors: INVALID_ARG, NO_CONVERGENCE (conjugate
+ * gradients broke down), NONPHYSICAL (non-finite iterate), CUDA, OOM (the
+ * low-order workspace is allocated on first use).  A capped iteration is
+ * not an error: see stats.  stats_host may be NULL. */
+sm_status sm_loworder_newton(sm_problem *p, const double *closures_dev, const double *T_star_dev,
+                             const double *cv_dev, const double *moments_star_dev, double *T_dev,
+                             double *E_dev, double *F_dev, const sm_step_params *params_host,
+                             sm_step_stats *stats_host);
+
+/* One time step of Algorithm 1 (semi-implicit backward Euler, Eq. smm_be):
+ * multigroup opacities sigma_g(T^k) from sm_opacity at the step's start
+ * temperature, then repeat { sm_sweep with the current T (emission, sweep,
+ * moments, closures); sm_loworder_newton } until Eq. relative_tol holds for
+ * u = (T, E) or max_outer is reached.  E starts at E* and T at T^k.
+ *   scale_dev[cell]: opacity scale s_K (as sm_opacity);
+ *   cv_dev[cell][node]: C_v;
+ *   T_dev[cell][node]: T^k on entry, T^{k+1} on exit;
+ *   E_dev[cell][node], F_dev[cell][node][dim]: low-order solution (out);
+ *   moments_dev[cell][node][n_moments]: on entry the moments of I_prev (the
+ *     time-edge sources), on exit those of I_next;
+ *   I_prev_dev: packed I^k; I_next_dev: packed I^{k+1} (out; no aliasing);
+ *   closures_dev[cell][node][n_closures]: last closures (out; may be NULL).
+ * Errors as sm_sweep and sm_loworder_newton.  Synchronous. */
+sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, double *T_dev,
+                  double *E_dev, double *F_dev, double *moments_dev, const void *I_prev_dev,
+                  void *I_next_dev, double *closures_dev, const sm_step_params *params_host,
+                  sm_step_stats *stats_host);
 
 /* End-to-end variant of sm_sweep for callers holding host buffers: copies
  * T_nodal_host and sigma_host to the device, runs sm_sweep, copies moments

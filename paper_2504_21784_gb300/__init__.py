@@ -28,7 +28,8 @@ EXPORTED = ["sm_create_problem", "sm_destroy_problem", "sm_get_info", "sm_set_st
             "sm_closures", "sm_sweep_host", "sm_pack_intensity", "sm_unpack_intensity",
             "sm_synchronize", "sm_autotune", "sm_set_profiling", "sm_get_kernel_times",
             "sm_launch_count", "sm_last_error", "sm_status_string",
-            "sm_debug_set_wait_limit_ns", "sm_debug_skip_publish", "sm_sweep_static"]
+            "sm_debug_set_wait_limit_ns", "sm_debug_skip_publish", "sm_sweep_static",
+            "sm_default_step_params", "sm_loworder_newton", "sm_step"]
 
 
 class SMError(RuntimeError):
@@ -56,6 +57,37 @@ class ProblemInfo(ctypes.Structure):
         "n_groups_padded", "n_warp_tasks", "strip_width", "prefetch_rows", "n_tasks", "n_strips")] + [
         ("intensity_elems", ctypes.c_size_t), ("intensity_bytes", ctypes.c_size_t),
         ("workspace_bytes", ctypes.c_size_t), ("alpha", ctypes.c_double)]
+
+
+class StepParams(ctypes.Structure):
+    """Iteration controls of the low-order solve and the step (sm_step_params)."""
+    _fields_ = [("eps_outer", ctypes.c_double), ("eps_inner", ctypes.c_double),
+                ("pcg_rtol", ctypes.c_double), ("elim_rtol", ctypes.c_double),
+                ("T_floor", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("max_inner", ctypes.c_int), ("max_pcg", ctypes.c_int),
+                ("max_elim", ctypes.c_int)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in (
+        "outer_iters", "newton_iters_total", "newton_iters_max", "pcg_iters_total",
+        "pcg_iters_max", "pcg_capped", "elim_iters_max", "converged")] + [
+        ("last_change", ctypes.c_double)]
+
+
+def step_params(**overrides) -> StepParams:
+    """The library's default iteration controls with the given fields replaced."""
+    prm = StepParams()
+    load().sm_default_step_params(ctypes.byref(prm))
+    for k, v in overrides.items():
+        if k not in dict(StepParams._fields_):
+            raise KeyError(k)
+        setattr(prm, k, v)
+    return prm
+
+
+def _stats(st: StepStats) -> dict:
+    return {f: getattr(st, f) for f, _ in StepStats._fields_}
 
 
 _lib = None
@@ -95,11 +127,17 @@ def load():
         "sm_debug_set_wait_limit_ns": [P, ctypes.c_longlong],
         "sm_debug_skip_publish": [P, I],
         "sm_sweep_static": [ctypes.POINTER(ProblemDesc), P, P, P, P, P, P, P],
+        "sm_loworder_newton": [P, P, P, P, P, P, P, P, ctypes.POINTER(StepParams),
+                               ctypes.POINTER(StepStats)],
+        "sm_step": [P, P, P, P, P, P, P, P, P, P, ctypes.POINTER(StepParams),
+                    ctypes.POINTER(StepStats)],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    lib.sm_default_step_params.argtypes = [ctypes.POINTER(StepParams)]
+    lib.sm_default_step_params.restype = None
     lib.sm_launch_count.argtypes = [P]
     lib.sm_launch_count.restype = ctypes.c_int64
     lib.sm_last_error.argtypes = []
@@ -289,6 +327,45 @@ class Problem:
         n = ctypes.c_int()
         _check(load().sm_get_kernel_times(self._h, ms, ctypes.byref(n)))
         return {"emission_ms": ms[0], "sweep_ms": ms[1], "reduce_ms": ms[2], "count": n.value}
+
+    # ---------------------------------------------------------------- low order / step
+    def new_nodal(self):
+        """FP64 [cell][node] device array (T, E, C_v)."""
+        i = self.info
+        return self._torch.zeros((i["n_cells"], i["n_nodes"]), dtype=self._torch.float64,
+                                 device="cuda")
+
+    def new_flux(self):
+        i = self.info
+        return self._torch.zeros((i["n_cells"], i["n_nodes"], i["dim"]),
+                                 dtype=self._torch.float64, device="cuda")
+
+    def loworder_newton(self, closures, T_star, cv, moments_star, T, E, F=None,
+                        params: Optional[StepParams] = None) -> dict:
+        """Gray low-order Newton solve (sm_loworder_newton); T and E are
+        updated in place, F (allocated when None) receives the flux.
+        Returns the iteration counts, with the flux under "F"."""
+        if F is None:
+            F = self.new_flux()
+        st = StepStats()
+        _check(load().sm_loworder_newton(
+            self._h, _ptr(closures), _ptr(T_star), _ptr(cv), _ptr(moments_star), _ptr(T),
+            _ptr(E), _ptr(F), ctypes.byref(params) if params is not None else None,
+            ctypes.byref(st)))
+        out = _stats(st)
+        out["F"] = F
+        return out
+
+    def step(self, scale, cv, T, E, F, moments, I_prev, I_next, closures=None,
+             params: Optional[StepParams] = None) -> dict:
+        """One time step of Algorithm 1 (sm_step): T, E, F, moments, I_next
+        (and closures, when given) are updated in place."""
+        st = StepStats()
+        _check(load().sm_step(self._h, _ptr(scale), _ptr(cv), _ptr(T), _ptr(E), _ptr(F),
+                              _ptr(moments), _ptr(I_prev), _ptr(I_next), _ptr(closures),
+                              ctypes.byref(params) if params is not None else None,
+                              ctypes.byref(st)))
+        return _stats(st)
 
     def launch_count(self) -> int:
         return int(load().sm_launch_count(self._h))

@@ -100,6 +100,7 @@ void free_all(sm_problem *p) {
                     p->d_ctrl, p->d_mom_tmp, p->d_T_tmp, p->d_sig_tmp, p->d_clo_tmp};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    smk::lo_free(p);
     for (auto &e : p->ev_pool)
         if (e) cudaEventDestroy(e);
     p->ev_pool.clear();

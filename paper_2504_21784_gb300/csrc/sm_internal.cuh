@@ -73,8 +73,12 @@ void planck_upload_tables(void);
 // Set the thread-local message returned by sm_last_error() (no allocation
 // beyond the message string of at most 255 characters).
 void set_last_error(const char *msg);
+// Free the low-order workspace (no-op when the low-order solve never ran).
+void lo_free(sm_problem *p);
 
 }  // namespace smk
+
+struct sm_lo_state;  // low-order solve workspace, created on first use
 
 struct sm_problem {
     // descriptor copy
@@ -119,5 +123,6 @@ struct sm_problem {
     int n_timed = 0;
     int64_t launches = 0;
     size_t workspace_bytes = 0;
+    sm_lo_state *lo = nullptr;
 };
 
