@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--nx", type=int, default=0, help="override cells per axis (profiling cases)")
     ap.add_argument("--groups", type=int, default=0, help="override the group count")
+    ap.add_argument("--no-step-metric", action="store_true",
+                    help="skip the seconds-per-converged-step comparison (FP32 vs FP64 sweep)")
+    ap.add_argument("--step-steps", type=int, default=3,
+                    help="time steps timed per path in the step comparison (after 1 warm-up step)")
     return ap.parse_args()
 
 
@@ -178,6 +182,72 @@ def cpu_baseline(cfg, budget_s: float = 8.0):
             "kind": "oracle",
             "sample": f"{n} random (direction, group) sweeps of the full {cfg.nx}x{cfg.ny} mesh "
                       f"({upd} updates, {dt:.1f} s), FP64 oracle sweep only, OpenMP over pairs"}
+
+
+def converged_steps(sm, W, cfg, prec: int, n_steps: int, stream, autotune: bool = True):
+    """Seconds per converged time step (Algorithm 1 through sm_step) from the
+    equilibrium initial state T = T0, I = B_g(T0)/4pi (whose moments are
+    phi = a c T0^4, F = 0), with the paper's iteration controls.  One
+    warm-up step (allocates the low-order workspace), then n_steps timed
+    steps of the same evolution.  sm_step synchronizes internally, so the
+    host clock brackets the device work."""
+    import torch
+    with torch.cuda.stream(stream):
+        prob = sm.Problem.from_config(cfg, prec, stream=stream)
+        nc, nn = cfg.n_cells, cfg.n_nodes
+        T = torch.full((nc, nn), cfg.T0, dtype=torch.float64, device="cuda")
+        scale = torch.from_numpy(W.scale_field(cfg)).cuda()
+        cv = torch.full((nc, nn), cfg.cv, dtype=torch.float64, device="cuda")
+        ones = torch.ones((cfg.n_groups, nc), dtype=torch.float64, device="cuda")
+        b = prob.emission(T, ones)  # unit opacity: B_g(T0)/4pi per node
+        I = [prob.pack(b.unsqueeze(0).expand(cfg.n_dir, -1, -1, -1).contiguous()),
+             prob.empty_intensity()]
+        del b, ones
+        mom = prob.new_moments()
+        mom.zero_()
+        mom[..., 0] = cfg.a * cfg.c * cfg.T0 ** 4
+        E, F = prob.new_nodal(), prob.new_flux()
+        if autotune:
+            sigma = prob.opacity(T, scale)
+            prob.autotune(T, sigma, I[0], I[1], reps=2)
+            del sigma
+        secs, stats = [], []
+        for k in range(1 + n_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = prob.step(scale, cv, T, E, F, mom, I[k % 2], I[(k + 1) % 2])
+            torch.cuda.synchronize()
+            if k >= 1:
+                secs.append(time.perf_counter() - t0)
+                stats.append(st)
+        out = {"s_per_step": sum(secs) / len(secs),
+               "outer_iters": [s["outer_iters"] for s in stats],
+               "newton_iters": [s["newton_iters_total"] for s in stats],
+               "pcg_iters": [s["pcg_iters_total"] for s in stats],
+               "pcg_capped": sum(s["pcg_capped"] for s in stats),
+               "converged": all(s["converged"] for s in stats),
+               "tiling": {k: prob.info[k] for k in ("strip_width", "prefetch_rows",
+                                                    "groups_per_warp")}}
+        Tn = T.cpu().numpy()
+        prob.close()
+        return out, Tn
+
+
+def step_metric(sm, W, cfgs, n_steps: int, stream):
+    """Metric 2: FP32 vs FP64 sweep path, seconds per converged step, with
+    the FP32 path's temperature error against the FP64 path after the same
+    steps (max |dT| / max |T|)."""
+    import numpy as np
+    res = {}
+    for cfg in cfgs:
+        r32, T32 = converged_steps(sm, W, cfg, 32, n_steps, stream)
+        r64, T64 = converged_steps(sm, W, cfg, 64, n_steps, stream)
+        res[cfg.name] = {"fp32": r32, "fp64": r64,
+                         "fp64_over_fp32_time": r64["s_per_step"] / r32["s_per_step"],
+                         "fp32_vs_fp64_T_rel": float(np.abs(T32 - T64).max() / np.abs(T64).max()),
+                         "steps_timed": n_steps, "warmup_steps": 1,
+                         "state": "equilibrium start T0 = %g, steps 2..%d" % (cfg.T0, n_steps + 1)}
+    return res
 
 
 def run_reference(args):
@@ -345,6 +415,11 @@ def main():
                 "d2h_bytes_per_step": int(M_h.nbytes + C_h.nbytes),
                 "api": "sm_sweep_host (host T, sigma in; moments, closures out)"},
     }
+    if not args.no_step_metric and not (args.nx or args.groups):
+        del I, mom, clo, sigma, prob
+        torch.cuda.empty_cache()
+        line["step_metric"] = step_metric(sm, W, [W.multigroup_2d(), W.gray_channel_2d()],
+                                          args.step_steps, stream)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)
     print(json.dumps(line), flush=True)

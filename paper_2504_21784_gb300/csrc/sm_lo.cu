@@ -13,15 +13,27 @@
 // Unknowns are nodal (cell corners): E_n and F_n = (F_x, F_y).  With the
 // interior faces oriented +x / +y, s = +1, so F^.n takes the low-side F and
 // P^ n the high-side E.  The lumped A_FF = m sigma~_F is diagonal, which lets
-// S = A_EE - A_EF A_FF^-1 A_FE be applied matrix-free as a two-hop stencil on
-// the structured mesh; the whole working set of a 256x256 mesh (a few MB)
-// stays in L2, so these kernels are launch- and latency-bound rather than
-// bandwidth-bound.  PCG scalars never leave the device: each kernel's
-// reductions are finished by the last block to arrive (deterministic fixed-
-// order sums, no atomics on floating point), and chunks of iterations are
-// replayed from a CUDA graph; the host only polls a done flag per chunk.
+// S = A_EE - A_EF A_FF^-1 A_FE be applied matrix-free as a stencil over a
+// cell and its four face neighbours.
+//
+// GB300 runs FP64 at about 1/64 of its FP32 rate (roughly two FP64 FMAs per
+// clock per SM), so these kernels are bound by FP64 instruction count, not by
+// memory: the whole working set of a 256x256 mesh is a few MB and stays in
+// L2.  The design therefore minimises FP64 work: one thread per cell (the
+// four nodes of a cell share their stencil loads and partial sums, read as
+// double2 vectors), geometry folded into per-problem coefficients, 1/A_FF and
+// 1/diag(S) precomputed so that conjugate-gradient iterations divide nothing,
+// and the pointwise temperature Newton step taken with an FP32 reciprocal of
+// its derivative (a quasi-Newton step: the root is unchanged).  PCG scalars
+// never leave the device: every grid-wide sum is finished by the last block
+// to arrive (deterministic fixed-order sums, no floating-point atomics), and
+// the iteration runs as a device-side WHILE loop (a conditional node of a
+// CUDA graph) whose condition a one-thread kernel clears when the iteration
+// has converged, broken down or reached its cap -- that kernel also counts
+// loop trips against a hard bound, so the loop always ends.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <string>
 
 #include "sm_internal.cuh"
@@ -29,193 +41,251 @@
 namespace smk {
 namespace lo {
 
-constexpr int BLOCK = 256;
-constexpr int PCG_CHUNK = 16;  // PCG iterations per graph replay (even: p buffers alternate)
+constexpr int BLOCK = 128;
 enum { DONE_NO = 0, DONE_CONVERGED = 1, DONE_BREAKDOWN = 2, DONE_CAPPED = 3 };
 
 struct Scalars {
     double alpha, beta, rz, bnorm, rr, d2, n2, rtol;
     int done, iters, max_iters, elim_max;
+    int body_runs;       // trips of the device loop in the running solve
     unsigned int count;  // arrivals of the running kernel's blocks
-    int pad[3];
+    int pad[2];
 };
 
 struct Geo {
-    int dim, nx, ny, nn, N;
-    double m;         // lumped nodal mass |K| / 2^dim
-    double wfx, wfy;  // Gauss-Lobatto face weights of x- and y-faces
-    double hx, hy;
-    double c, alpha;
+    int dim, nx, ny, ncell, N;
+    double m, c;
+    double wfx, wfy;        // Gauss-Lobatto weights of x- and y-faces
+    double kx, ky, fx, fy;  // A_FE: volume (c/3) m / h, faces (c/3) wf
+    double lx, ly;          // A_EF volume: m / h
+    double px, py, bx, by;  // interior penalty (c alpha / 2) wf, boundary c alpha wf
+    double c3;              // c / 3
 };
 
-struct NodeGeo {
-    int cell, ix, iy, a, b;
+struct Cell {
+    int k, ix, iy;
+    bool L, R, B, T;  // face neighbours present (left, right, bottom, top)
 };
 
-__device__ __forceinline__ NodeGeo node_geo(const Geo &G, int t) {
-    NodeGeo g;
-    g.cell = t / G.nn;
-    const int loc = t - g.cell * G.nn;
-    g.iy = g.cell / G.nx;
-    g.ix = g.cell - g.iy * G.nx;
-    g.a = loc & 1;
-    g.b = G.nn == 4 ? (loc >> 1) : 0;
-    return g;
-}
-__device__ __forceinline__ int nid(const Geo &G, int cell, int a, int b) {
-    return cell * G.nn + (G.nn == 4 ? a + 2 * b : a);
+__device__ __forceinline__ Cell cell_of(const Geo &G, int k) {
+    Cell C;
+    C.k = k;
+    C.iy = k / G.nx;
+    C.ix = k - C.iy * G.nx;
+    C.L = C.ix > 0;
+    C.R = C.ix + 1 < G.nx;
+    C.B = C.iy > 0;
+    C.T = C.iy + 1 < G.ny;
+    return C;
 }
 
-// value accessors for the stencil helpers
+// the NN nodal values of cell k ([cell][node] arrays, 16-byte aligned)
+template <int NN>
+__device__ __forceinline__ void ldc(const double *__restrict__ a, int k, double (&v)[NN]) {
+    const double2 *p = reinterpret_cast<const double2 *>(a + (size_t)k * NN);
+#pragma unroll
+    for (int i = 0; i < NN / 2; ++i) {
+        const double2 t = p[i];
+        v[2 * i] = t.x;
+        v[2 * i + 1] = t.y;
+    }
+}
+template <int NN>
+__device__ __forceinline__ void stc(double *__restrict__ a, int k, const double (&v)[NN]) {
+    double2 *p = reinterpret_cast<double2 *>(a + (size_t)k * NN);
+#pragma unroll
+    for (int i = 0; i < NN / 2; ++i) p[i] = make_double2(v[2 * i], v[2 * i + 1]);
+}
+
+template <int NN>
 struct Vec {
     const double *v;
-    __device__ double operator()(int j) const { return v[j]; }
+    __device__ __forceinline__ void get(int k, double (&o)[NN]) const { ldc<NN>(v, k, o); }
 };
 // PCG search direction formed on the fly: p = z + beta p_old
+template <int NN>
 struct Dir {
-    const double *z, *p_old;
+    const double *z, *p;
     double beta;
-    __device__ double operator()(int j) const { return z[j] + beta * p_old[j]; }
+    __device__ __forceinline__ void get(int k, double (&o)[NN]) const {
+        double a[NN], b[NN];
+        ldc<NN>(z, k, a);
+        ldc<NN>(p, k, b);
+#pragma unroll
+        for (int i = 0; i < NN; ++i) o[i] = fma(beta, b[i], a[i]);
+    }
 };
 
-// Component d of (A_FE e) at node j: first-moment rows, E columns.
-//   volume  -(c/3) int div v E  at the Lobatto points,
-//   faces   (c/3) int [v.n] E^ with E^ the high-side value on interior faces
-//           and the node's own value on the boundary.
-template <class X>
-__device__ __forceinline__ double fe_comp(const Geo &G, const X &e, int j, int d) {
-    const NodeGeo g = node_geo(G, j);
-    const double c3 = G.c / 3.0;
-    if (d == 0) {
-        const double e0 = e(nid(G, g.cell, 0, g.b)), e1 = e(nid(G, g.cell, 1, g.b));
-        double v = -c3 * G.m * (2 * g.a - 1) / G.hx * (e0 + e1);
-        if (g.a == 1)
-            v += c3 * G.wfx * (g.ix + 1 < G.nx ? e(nid(G, g.cell + 1, 0, g.b)) : e1);
-        else
-            v -= c3 * G.wfx * e0;
-        return v;
-    }
-    const double e0 = e(nid(G, g.cell, g.a, 0)), e1 = e(nid(G, g.cell, g.a, 1));
-    double v = -c3 * G.m * (2 * g.b - 1) / G.hy * (e0 + e1);
-    if (g.b == 1)
-        v += c3 * G.wfy * (g.iy + 1 < G.ny ? e(nid(G, g.cell + G.nx, g.a, 0)) : e1);
-    else
-        v -= c3 * G.wfy * e0;
-    return v;
-}
-
-// nodal F values, [node][dim]
-struct FVec {
-    const double *f;
-    int D;
-    __device__ double operator()(int j, int d) const { return f[(size_t)j * D + d]; }
-};
-// F = A_FF^-1 A_FE e formed on the fly (the inner factor of S)
-template <class X>
-struct FOfE {
-    Geo G;
-    X e;
-    const double *aF;
-    __device__ double operator()(int j, int d) const { return fe_comp(G, e, j, d) / aF[j]; }
-};
-
-// (A_EF f) at node t: zeroth-moment rows, F columns.
-//   volume  -int grad u . F,   faces  int [u] F^.n with F^ the low-side F.
-template <class FX>
-__device__ __forceinline__ double ef_at(const Geo &G, const FX &f, int t) {
-    const NodeGeo g = node_geo(G, t);
-    double v = -G.m * (2 * g.a - 1) / G.hx *
-               (f(nid(G, g.cell, 0, g.b), 0) + f(nid(G, g.cell, 1, g.b), 0));
-    if (g.a == 1) {
-        if (g.ix + 1 < G.nx) v += G.wfx * f(t, 0);
-    } else if (g.ix > 0) {
-        v -= G.wfx * f(nid(G, g.cell - 1, 1, g.b), 0);
-    }
-    if (G.dim == 2) {
-        v += -G.m * (2 * g.b - 1) / G.hy *
-             (f(nid(G, g.cell, g.a, 0), 1) + f(nid(G, g.cell, g.a, 1), 1));
-        if (g.b == 1) {
-            if (g.iy + 1 < G.ny) v += G.wfy * f(t, 1);
-        } else if (g.iy > 0) {
-            v -= G.wfy * f(nid(G, g.cell - G.nx, g.a, 1), 1);
-        }
-    }
-    return v;
-}
-
-// (A_EE e) at node t: nodal absorption aE_t e_t, interior penalty
-// (c alpha / 2) int [u][E], boundary c alpha int u E.
-template <class X>
-__device__ __forceinline__ double ee_at(const Geo &G, double aEt, const X &e, int t) {
-    const NodeGeo g = node_geo(G, t);
-    const double pen = 0.5 * G.c * G.alpha, bnd = G.c * G.alpha;
-    const double et = e(t);
-    double v = aEt * et;
-    if (g.a == 1)
-        v += g.ix + 1 < G.nx ? pen * G.wfx * (et - e(nid(G, g.cell + 1, 0, g.b))) : bnd * G.wfx * et;
-    else
-        v += g.ix > 0 ? pen * G.wfx * (et - e(nid(G, g.cell - 1, 1, g.b))) : bnd * G.wfx * et;
-    if (G.dim == 2) {
-        if (g.b == 1)
-            v += g.iy + 1 < G.ny ? pen * G.wfy * (et - e(nid(G, g.cell + G.nx, g.a, 0)))
-                                 : bnd * G.wfy * et;
-        else
-            v += g.iy > 0 ? pen * G.wfy * (et - e(nid(G, g.cell - G.nx, g.a, 1))) : bnd * G.wfy * et;
-    }
-    return v;
-}
-
-// S e at node t
-template <class X>
-__device__ __forceinline__ double schur_at(const Geo &G, double aEt, const double *aF, const X &e,
-                                           int t) {
-    return ee_at(G, aEt, e, t) - ef_at(G, FOfE<X>{G, e, aF}, t);
-}
-
-// Diagonal of S = A_EE + (c/3) A_EF A_FF^-1 A_EF^T (A_FE = -(c/3) A_EF^T):
-// S_tt = (A_EE)_tt + (c/3) sum_j (A_EF)_tj^2 / (A_FF)_jj over the F columns
-// that row t touches.
-__device__ double schur_diag(const Geo &G, double aEt, const double *aF, int t) {
-    const NodeGeo g = node_geo(G, t);
-    const double pen = 0.5 * G.c * G.alpha, bnd = G.c * G.alpha;
-    double dEE = aEt, sum = 0.0;
-    {
-        const double vol = -G.m * (2 * g.a - 1) / G.hx;
-        double c0 = vol, c1 = vol;
-        if (g.a == 1) {
-            if (g.ix + 1 < G.nx) {
-                c1 += G.wfx;
-                dEE += pen * G.wfx;
-            } else {
-                dEE += bnd * G.wfx;
-            }
-        } else if (g.ix > 0) {
-            sum += G.wfx * G.wfx / aF[nid(G, g.cell - 1, 1, g.b)];
-            dEE += pen * G.wfx;
+// Node numbering inside a cell: n = a + 2b (2D), n = a (1D); a, b = 0 on the
+// low x / y side.  x-rows are the node pairs (2b, 2b+1), y-columns (a, a+2).
+//
+// q = S e = A_EE e - A_EF A_FF^-1 A_FE e on the nodes of cell C; e receives
+// the cell's own values.  Per x-row, with s = e_0 + e_1 and ia = 1/A_FF:
+//   u_0 = ((c/3) m/h s - (c/3) wf e_0) ia_0        (first-moment rows, A_FE:
+//   u_1 = ((c/3) wf e^ - (c/3) m/h s) ia_1          volume -(c/3) div v E, face
+//                                                   (c/3)[v.n] E^, E^ the high
+//                                                   side / own value on the
+//                                                   boundary)
+//   (A_EF u)_0 = m/h (u_0 + u_1) - wf u_1^left      (volume -grad u . F, face
+//   (A_EF u)_1 = -m/h (u_0 + u_1) + wf u_1          [u] F^.n, F^ the low side)
+// and A_EE adds aE e, the penalty (c alpha/2) wf (e - e_nb) on interior
+// faces and c alpha wf e on the boundary.  The left neighbour's u_1 needs
+// only its own row and this cell's e_0, so it is recomputed here.
+template <int NN, class Acc>
+__device__ __forceinline__ void schur_cell(const Geo &G, const Cell &C, const Acc &acc,
+                                           const double (&aE)[NN], const double *__restrict__ iaF,
+                                           double (&q)[NN], double (&e)[NN]) {
+    double eL[NN], eR[NN], ia[NN];
+    acc.get(C.k, e);
+    if (C.L) acc.get(C.k - 1, eL);
+    if (C.R) acc.get(C.k + 1, eR);
+    ldc<NN>(iaF, C.k, ia);
+#pragma unroll
+    for (int n = 0; n < NN; ++n) q[n] = aE[n] * e[n];
+#pragma unroll
+    for (int b = 0; b < NN / 2; ++b) {
+        const int n0 = 2 * b, n1 = 2 * b + 1;
+        const double s = e[n0] + e[n1];
+        const double u0 = (G.kx * s - G.fx * e[n0]) * ia[n0];
+        const double u1 = (G.fx * (C.R ? eR[n0] : e[n1]) - G.kx * s) * ia[n1];
+        const double sv = G.lx * (u0 + u1);
+        double v0 = sv, v1 = -sv;
+        if (C.L) {
+            const double uL = (G.fx * e[n0] - G.kx * (eL[n0] + eL[n1])) *
+                              iaF[(size_t)(C.k - 1) * NN + n1];
+            v0 -= G.wfx * uL;
+            q[n0] += G.px * (e[n0] - eL[n1]);
         } else {
-            dEE += bnd * G.wfx;
+            q[n0] += G.bx * e[n0];
         }
-        sum += c0 * c0 / aF[nid(G, g.cell, 0, g.b)] + c1 * c1 / aF[nid(G, g.cell, 1, g.b)];
-    }
-    if (G.dim == 2) {
-        const double vol = -G.m * (2 * g.b - 1) / G.hy;
-        double c0 = vol, c1 = vol;
-        if (g.b == 1) {
-            if (g.iy + 1 < G.ny) {
-                c1 += G.wfy;
-                dEE += pen * G.wfy;
-            } else {
-                dEE += bnd * G.wfy;
-            }
-        } else if (g.iy > 0) {
-            sum += G.wfy * G.wfy / aF[nid(G, g.cell - G.nx, g.a, 1)];
-            dEE += pen * G.wfy;
+        if (C.R) {
+            v1 += G.wfx * u1;
+            q[n1] += G.px * (e[n1] - eR[n0]);
         } else {
-            dEE += bnd * G.wfy;
+            q[n1] += G.bx * e[n1];
         }
-        sum += c0 * c0 / aF[nid(G, g.cell, g.a, 0)] + c1 * c1 / aF[nid(G, g.cell, g.a, 1)];
+        q[n0] -= v0;
+        q[n1] -= v1;
     }
-    return dEE + (G.c / 3.0) * sum;
+    if constexpr (NN == 4) {
+        double eB[NN], eT[NN];
+        if (C.B) acc.get(C.k - G.nx, eB);
+        if (C.T) acc.get(C.k + G.nx, eT);
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int n0 = a, n1 = a + 2;
+            const double s = e[n0] + e[n1];
+            const double u0 = (G.ky * s - G.fy * e[n0]) * ia[n0];
+            const double u1 = (G.fy * (C.T ? eT[n0] : e[n1]) - G.ky * s) * ia[n1];
+            const double sv = G.ly * (u0 + u1);
+            double v0 = sv, v1 = -sv;
+            if (C.B) {
+                const double uB = (G.fy * e[n0] - G.ky * (eB[n0] + eB[n1])) *
+                                  iaF[(size_t)(C.k - G.nx) * NN + n1];
+                v0 -= G.wfy * uB;
+                q[n0] += G.py * (e[n0] - eB[n1]);
+            } else {
+                q[n0] += G.by * e[n0];
+            }
+            if (C.T) {
+                v1 += G.wfy * u1;
+                q[n1] += G.py * (e[n1] - eT[n0]);
+            } else {
+                q[n1] += G.by * e[n1];
+            }
+            q[n0] -= v0;
+            q[n1] -= v1;
+        }
+    }
+}
+
+// A_EF u on the nodes of cell C for a materialised u[node][dim].
+template <int NN>
+__device__ __forceinline__ void ef_cell(const Geo &G, const Cell &C, const double *__restrict__ u,
+                                        double (&out)[NN]) {
+    constexpr int D = NN == 4 ? 2 : 1;
+    const double *uk = u + (size_t)C.k * NN * D;
+#pragma unroll
+    for (int b = 0; b < NN / 2; ++b) {
+        const int n0 = 2 * b, n1 = 2 * b + 1;
+        const double sv = G.lx * (uk[n0 * D] + uk[n1 * D]);
+        out[n0] = sv - (C.L ? G.wfx * u[((size_t)(C.k - 1) * NN + n1) * D] : 0.0);
+        out[n1] = -sv + (C.R ? G.wfx * uk[n1 * D] : 0.0);
+    }
+    if constexpr (NN == 4) {
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int n0 = a, n1 = a + 2;
+            const double sv = G.ly * (uk[n0 * D + 1] + uk[n1 * D + 1]);
+            out[n0] += sv - (C.B ? G.wfy * u[((size_t)(C.k - G.nx) * NN + n1) * D + 1] : 0.0);
+            out[n1] += -sv + (C.T ? G.wfy * uk[n1 * D + 1] : 0.0);
+        }
+    }
+}
+
+// (A_FE e) components on the nodes of cell C (not divided by A_FF).
+template <int NN, class Acc>
+__device__ __forceinline__ void fe_cell(const Geo &G, const Cell &C, const Acc &acc,
+                                        double (&e)[NN], double (&ax)[NN], double (&ay)[NN]) {
+    double eR[NN];
+    acc.get(C.k, e);
+    if (C.R) acc.get(C.k + 1, eR);
+#pragma unroll
+    for (int b = 0; b < NN / 2; ++b) {
+        const int n0 = 2 * b, n1 = 2 * b + 1;
+        const double s = e[n0] + e[n1];
+        ax[n0] = G.kx * s - G.fx * e[n0];
+        ax[n1] = G.fx * (C.R ? eR[n0] : e[n1]) - G.kx * s;
+    }
+    if constexpr (NN == 4) {
+        double eT[NN];
+        if (C.T) acc.get(C.k + G.nx, eT);
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int n0 = a, n1 = a + 2;
+            const double s = e[n0] + e[n1];
+            ay[n0] = G.ky * s - G.fy * e[n0];
+            ay[n1] = G.fy * (C.T ? eT[n0] : e[n1]) - G.ky * s;
+        }
+    }
+}
+
+// diag(S) = diag(A_EE) + (c/3) sum_j (A_EF)_tj^2 / (A_FF)_jj, using
+// A_FE = -(c/3) A_EF^T; the A_EF coefficients of a node are m/h on both
+// nodes of its row (sign of the node's side), plus wf on the right node of
+// the row when the right face is interior and -wf on the left neighbour's
+// right node when the left face is interior.
+template <int NN>
+__device__ __forceinline__ void diag_cell(const Geo &G, const Cell &C, const double (&aE)[NN],
+                                          const double *__restrict__ iaF, double (&d)[NN]) {
+    double ia[NN], sq[NN];
+    ldc<NN>(iaF, C.k, ia);
+    const double lx2 = G.lx * G.lx;
+#pragma unroll
+    for (int b = 0; b < NN / 2; ++b) {
+        const int n0 = 2 * b, n1 = 2 * b + 1;
+        d[n0] = aE[n0] + (C.L ? G.px : G.bx);
+        d[n1] = aE[n1] + (C.R ? G.px : G.bx);
+        sq[n0] = lx2 * (ia[n0] + ia[n1]) +
+                 (C.L ? G.wfx * G.wfx * iaF[(size_t)(C.k - 1) * NN + n1] : 0.0);
+        const double c1 = C.R ? G.wfx - G.lx : -G.lx;
+        sq[n1] = lx2 * ia[n0] + c1 * c1 * ia[n1];
+    }
+    if constexpr (NN == 4) {
+        const double ly2 = G.ly * G.ly;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int n0 = a, n1 = a + 2;
+            d[n0] += C.B ? G.py : G.by;
+            d[n1] += C.T ? G.py : G.by;
+            sq[n0] += ly2 * (ia[n0] + ia[n1]) +
+                      (C.B ? G.wfy * G.wfy * iaF[(size_t)(C.k - G.nx) * NN + n1] : 0.0);
+            const double c1 = C.T ? G.wfy - G.ly : -G.ly;
+            sq[n1] += ly2 * ia[n0] + c1 * c1 * ia[n1];
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < NN; ++n) d[n] += G.c3 * sq[n];
 }
 
 // ---------------------------------------------------------------------------
@@ -274,7 +344,7 @@ __device__ bool grid_sums(double (&v)[K], double *part, unsigned int *count) {
 
 // ---------------------------------------------------------------------------
 // E* = phi / c and F* = F from the moments of the previous step's intensity
-// (the high-order time-edge sources of Sec. 6.1).
+// (the high-order time-edge sources of Sec. 6.1).  One thread per node.
 __global__ void timeedge_kernel(int N, int D, int nm, double inv_c, const double *__restrict__ mom,
                                 double *__restrict__ Estar, double *__restrict__ Fstar) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -283,99 +353,124 @@ __global__ void timeedge_kernel(int N, int D, int nm, double inv_c, const double
     for (int d = 0; d < D; ++d) Fstar[(size_t)t * D + d] = mom[(size_t)t * nm + 1 + d];
 }
 
-// Per low-order solve (closures fixed): aF = m sigma~_F, the first-moment
-// right-hand side b_F = m F*/(c dt) + R1_ind and u_b = A_FF^-1 b_F.
+// Per low-order solve (closures fixed), one thread per node: 1/A_FF with
+// A_FF = m sigma~_F, the first-moment right-hand side b_F = m F*/(c dt) +
+// R1_ind and u_b = A_FF^-1 b_F, where
 // R1_ind(v) = int v . sum_g (sigma_F - sigma_g) F_g + int grad_h v : T
 //             - int_Gamma0 [v] . {T n}   (Sec. 4, independent closures).
-__global__ void prepare_kernel(Geo G, const double *__restrict__ clo, int nc, double inv_cdt,
-                               const double *__restrict__ Fstar, double *__restrict__ aF,
-                               double *__restrict__ bF, double *__restrict__ ub, Scalars *sc) {
+__global__ void __launch_bounds__(BLOCK)
+prepare_kernel(Geo G, const double *__restrict__ clo, int nc, double inv_cdt,
+               const double *__restrict__ Fstar, double *__restrict__ iaF, double *__restrict__ bF,
+               double *__restrict__ ub, Scalars *sc) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) sc->elim_max = 0;
     if (t >= G.N) return;
-    const NodeGeo g = node_geo(G, t);
-    const int D = G.dim;
-    auto Tt = [&](int node, int i, int j) -> double {  // closure tensor component (i, j)
-        const double *cl = clo + (size_t)node * nc;
+    const int D = G.dim, NN = D == 2 ? 4 : 2;
+    const int k = t / NN, n = t - k * NN;
+    const int iy = k / G.nx, ix = k - iy * G.nx;
+    const int a = n & 1, b = n >> 1;
+    auto node = [&](int kk, int aa, int bb) { return kk * NN + aa + 2 * bb; };
+    auto Tt = [&](int nd, int i, int j) -> double {  // closure tensor component (i, j)
+        const double *cl = clo + (size_t)nd * nc;
         if (D == 1) return cl[2];
         return i != j ? cl[4] : (i == 0 ? cl[3] : cl[5]);
     };
     const double *cl = clo + (size_t)t * nc;
     const double sF = D == 1 ? cl[4] : cl[7];
-    const double aFt = G.m * (sF + inv_cdt);
-    aF[t] = aFt;
+    const double ia = 1.0 / (G.m * (sF + inv_cdt));
+    iaF[t] = ia;
     for (int d = 0; d < D; ++d) {
         double r = G.m * (D == 1 ? cl[6] : cl[9 + d]);
-        r += G.m * (2 * g.a - 1) / G.hx *
-             (Tt(nid(G, g.cell, 0, g.b), d, 0) + Tt(nid(G, g.cell, 1, g.b), d, 0));
-        if (D == 2)
-            r += G.m * (2 * g.b - 1) / G.hy *
-                 (Tt(nid(G, g.cell, g.a, 0), d, 1) + Tt(nid(G, g.cell, g.a, 1), d, 1));
-        if (g.a == 1 && g.ix + 1 < G.nx)
-            r -= G.wfx * 0.5 * (Tt(t, d, 0) + Tt(nid(G, g.cell + 1, 0, g.b), d, 0));
-        else if (g.a == 0 && g.ix > 0)
-            r += G.wfx * 0.5 * (Tt(t, d, 0) + Tt(nid(G, g.cell - 1, 1, g.b), d, 0));
+        r += (2 * a - 1) * G.lx * (Tt(node(k, 0, b), d, 0) + Tt(node(k, 1, b), d, 0));
+        if (D == 2) r += (2 * b - 1) * G.ly * (Tt(node(k, a, 0), d, 1) + Tt(node(k, a, 1), d, 1));
+        if (a == 1 && ix + 1 < G.nx)
+            r -= G.wfx * 0.5 * (Tt(t, d, 0) + Tt(node(k + 1, 0, b), d, 0));
+        else if (a == 0 && ix > 0)
+            r += G.wfx * 0.5 * (Tt(t, d, 0) + Tt(node(k - 1, 1, b), d, 0));
         if (D == 2) {
-            if (g.b == 1 && g.iy + 1 < G.ny)
-                r -= G.wfy * 0.5 * (Tt(t, d, 1) + Tt(nid(G, g.cell + G.nx, g.a, 0), d, 1));
-            else if (g.b == 0 && g.iy > 0)
-                r += G.wfy * 0.5 * (Tt(t, d, 1) + Tt(nid(G, g.cell - G.nx, g.a, 1), d, 1));
+            if (b == 1 && iy + 1 < G.ny)
+                r -= G.wfy * 0.5 * (Tt(t, d, 1) + Tt(node(k + G.nx, a, 0), d, 1));
+            else if (b == 0 && iy > 0)
+                r += G.wfy * 0.5 * (Tt(t, d, 1) + Tt(node(k - G.nx, a, 1), d, 1));
         }
-        const double b = G.m * inv_cdt * Fstar[(size_t)t * D + d] + r;
-        bF[(size_t)t * D + d] = b;
-        ub[(size_t)t * D + d] = b / aFt;
+        const double bv = G.m * inv_cdt * Fstar[(size_t)t * D + d] + r;
+        bF[(size_t)t * D + d] = bv;
+        ub[(size_t)t * D + d] = bv * ia;
     }
 }
 
-// Per Newton iteration: linearise about the current T (Sec. 5), form the
-// Schur right-hand side b_E - A_EF u_b, the Jacobi diagonal, and start PCG
-// from x = E: r = rhs - S x, z = r / diag, p = z.
+// Per Newton iteration, one thread per cell: linearise the emission about
+// the current T (Sec. 5), form aE = m c (sigma~_E - nu sigma_E), the Schur
+// right-hand side b_E - A_EF u_b with b_E = m (sigma_P B(T0) + nu q_T0 +
+// E*/dt) + the Marshak inflow, 1/diag(S), and start PCG from x = E:
+// r = rhs - S x, z = r / diag, p = z.
+template <int NN>
 __global__ void __launch_bounds__(BLOCK)
 newton_setup_kernel(Geo G, const double *__restrict__ clo, int nc, double a_rad, double dt,
                     const double *__restrict__ T, const double *__restrict__ Tstar,
                     const double *__restrict__ cv, const double *__restrict__ Estar,
-                    const double *__restrict__ jin2, const double *__restrict__ aF,
+                    const double *__restrict__ jin2, const double *__restrict__ iaF,
                     const double *__restrict__ ub, const double *__restrict__ E,
-                    double *__restrict__ aE, double *__restrict__ diag, double *__restrict__ x,
+                    double *__restrict__ aE_out, double *__restrict__ idiag, double *__restrict__ x,
                     double *__restrict__ r, double *__restrict__ z, double *__restrict__ p0,
                     double rtol, int max_iters, double *part, Scalars *sc) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     double v[3] = {0.0, 0.0, 0.0};
-    if (t < G.N) {
-        const NodeGeo g = node_geo(G, t);
-        const int D = G.dim;
-        const double *cl = clo + (size_t)t * nc;
-        const double sE = D == 1 ? cl[3] : cl[6], sP = D == 1 ? cl[5] : cl[8];
+    if (k < G.ncell) {
+        const Cell C = cell_of(G, k);
+        double T0[NN], Ts[NN], cvv[NN], Es[NN], aE[NN], bE[NN];
+        ldc<NN>(T, k, T0);
+        ldc<NN>(Tstar, k, Ts);
+        ldc<NN>(cv, k, cvv);
+        ldc<NN>(Estar, k, Es);
         const double inv_cdt = 1.0 / (G.c * dt);
-        const double T0 = T[t];
-        const double B0 = a_rad * G.c * T0 * T0 * T0 * T0;
-        const double dB = 4.0 * a_rad * G.c * T0 * T0 * T0;
-        const double cv_dt = cv[t] / dt;
-        const double den = cv_dt + sP * dB;
-        const double nu = den > 0.0 ? sP * dB / den : 0.0;  // pseudo-fission coefficient
-        const double qT0 = cv_dt * (Tstar[t] - T0) - sP * B0;
-        const double aEt = G.m * G.c * (sE + inv_cdt - nu * sE);
-        double bE = G.m * (sP * B0 + nu * qT0 + Estar[t] / dt);
-        // Marshak boundary: -2 int_Gamma_b u F_in with the incoming partial currents
-        if (g.a == 0 && g.ix == 0) bE += G.wfx * jin2[0];
-        if (g.a == 1 && g.ix == G.nx - 1) bE += G.wfx * jin2[1];
-        if (D == 2) {
-            if (g.b == 0 && g.iy == 0) bE += G.wfy * jin2[2];
-            if (g.b == 1 && g.iy == G.ny - 1) bE += G.wfy * jin2[3];
+#pragma unroll
+        for (int n = 0; n < NN; ++n) {
+            const double *cl = clo + ((size_t)k * NN + n) * nc;
+            const double sE = cl[NN == 4 ? 6 : 3], sP = cl[NN == 4 ? 8 : 5];
+            const double Tn = T0[n];
+            const double B0 = a_rad * G.c * (Tn * Tn * Tn * Tn);
+            const double dB = 4.0 * a_rad * G.c * (Tn * Tn * Tn);
+            const double cv_dt = cvv[n] / dt;
+            const double den = cv_dt + sP * dB;
+            const double nu = den > 0.0 ? sP * dB / den : 0.0;  // pseudo-fission coefficient
+            const double qT0 = cv_dt * (Ts[n] - Tn) - sP * B0;
+            aE[n] = G.m * G.c * (sE + inv_cdt - nu * sE);
+            bE[n] = G.m * (sP * B0 + nu * qT0 + Es[n] / dt);
         }
-        const double rhs = bE - ef_at(G, FVec{ub, D}, t);
-        const double dg = schur_diag(G, aEt, aF, t);
-        const double rv = rhs - schur_at(G, aEt, aF, Vec{E}, t);
-        const double zv = rv / dg;
-        aE[t] = aEt;
-        diag[t] = dg;
-        x[t] = E[t];
-        r[t] = rv;
-        z[t] = zv;
-        p0[t] = zv;
-        v[0] = rv * rv;
-        v[1] = rv * zv;
-        v[2] = rhs * rhs;
+        // Marshak boundary: -2 int_Gamma_b u F_in, F_in the incoming partial current
+#pragma unroll
+        for (int b = 0; b < NN / 2; ++b) {
+            if (!C.L) bE[2 * b] += G.wfx * jin2[0];
+            if (!C.R) bE[2 * b + 1] += G.wfx * jin2[1];
+        }
+        if constexpr (NN == 4) {
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                if (!C.B) bE[a] += G.wfy * jin2[2];
+                if (!C.T) bE[a + 2] += G.wfy * jin2[3];
+            }
+        }
+        double efu[NN], dg[NN], q[NN], e[NN], rv[NN], zv[NN], idg[NN];
+        ef_cell<NN>(G, C, ub, efu);
+        diag_cell<NN>(G, C, aE, iaF, dg);
+        schur_cell<NN>(G, C, Vec<NN>{E}, aE, iaF, q, e);
+#pragma unroll
+        for (int n = 0; n < NN; ++n) {
+            const double rhs = bE[n] - efu[n];
+            rv[n] = rhs - q[n];
+            idg[n] = 1.0 / dg[n];
+            zv[n] = rv[n] * idg[n];
+            v[0] += rv[n] * rv[n];
+            v[1] += rv[n] * zv[n];
+            v[2] += rhs * rhs;
+        }
+        stc<NN>(aE_out, k, aE);
+        stc<NN>(idiag, k, idg);
+        stc<NN>(x, k, e);
+        stc<NN>(r, k, rv);
+        stc<NN>(z, k, zv);
+        stc<NN>(p0, k, zv);
     }
     if (grid_sums<3>(v, part, &sc->count)) {
         sc->rr = v[0];
@@ -383,28 +478,32 @@ newton_setup_kernel(Geo G, const double *__restrict__ clo, int nc, double a_rad,
         sc->bnorm = sqrt(v[2]);
         sc->beta = 0.0;
         sc->iters = 0;
+        sc->body_runs = 0;
         sc->rtol = rtol;
         sc->max_iters = max_iters;
         sc->done = sqrt(v[0]) <= rtol * sc->bnorm ? DONE_CONVERGED : DONE_NO;
     }
 }
 
-// PCG, first half of an iteration: p = z + beta p_old (written for this
-// node, formed on the fly for its neighbours), q = S p, alpha = rz / (p.q).
+// PCG, first half of an iteration: p = z + beta p_old (stored for this cell,
+// formed on the fly for its neighbours), q = S p, alpha = rz / (p.q).
+template <int NN>
 __global__ void __launch_bounds__(BLOCK)
-pcg_matvec_kernel(Geo G, const double *__restrict__ aE, const double *__restrict__ aF,
+pcg_matvec_kernel(Geo G, const double *__restrict__ aE, const double *__restrict__ iaF,
                   const double *__restrict__ z, const double *__restrict__ p_old,
                   double *__restrict__ p_new, double *__restrict__ q, double *part, Scalars *sc) {
     if (sc->done) return;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const Dir p{z, p_old, sc->beta};
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     double v[1] = {0.0};
-    if (t < G.N) {
-        const double pt = p(t);
-        const double qt = schur_at(G, aE[t], aF, p, t);
-        p_new[t] = pt;
-        q[t] = qt;
-        v[0] = pt * qt;
+    if (k < G.ncell) {
+        const Cell C = cell_of(G, k);
+        double aEv[NN], qv[NN], pv[NN];
+        ldc<NN>(aE, k, aEv);
+        schur_cell<NN>(G, C, Dir<NN>{z, p_old, sc->beta}, aEv, iaF, qv, pv);
+        stc<NN>(p_new, k, pv);
+        stc<NN>(q, k, qv);
+#pragma unroll
+        for (int n = 0; n < NN; ++n) v[0] += pv[n] * qv[n];
     }
     if (grid_sums<1>(v, part, &sc->count)) {
         if (v[0] > 0.0 && isfinite(v[0]) && isfinite(sc->rz))
@@ -414,24 +513,35 @@ pcg_matvec_kernel(Geo G, const double *__restrict__ aE, const double *__restrict
     }
 }
 
-// PCG, second half: x += alpha p, r -= alpha q, z = r / diag, stopping test
-// ||r|| <= rtol ||b|| and beta = (r.z)_new / (r.z)_old.
+// PCG, second half: x += alpha p, r -= alpha q, z = r / diag, the stopping
+// test ||r|| <= rtol ||b||, the cap, and beta = (r.z)_new / (r.z)_old.
+template <int NN>
 __global__ void __launch_bounds__(BLOCK)
-pcg_update_kernel(int N, const double *__restrict__ p, const double *__restrict__ q,
-                  const double *__restrict__ diag, double *__restrict__ x, double *__restrict__ r,
+pcg_update_kernel(int ncell, const double *__restrict__ p, const double *__restrict__ q,
+                  const double *__restrict__ idiag, double *__restrict__ x, double *__restrict__ r,
                   double *__restrict__ z, double *part, Scalars *sc) {
     if (sc->done) return;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const double alpha = sc->alpha;
     double v[2] = {0.0, 0.0};
-    if (t < N) {
-        x[t] += alpha * p[t];
-        const double rv = r[t] - alpha * q[t];
-        const double zv = rv / diag[t];
-        r[t] = rv;
-        z[t] = zv;
-        v[0] = rv * rv;
-        v[1] = rv * zv;
+    if (k < ncell) {
+        double pv[NN], qv[NN], dv[NN], xv[NN], rv[NN], zv[NN];
+        ldc<NN>(p, k, pv);
+        ldc<NN>(q, k, qv);
+        ldc<NN>(idiag, k, dv);
+        ldc<NN>(x, k, xv);
+        ldc<NN>(r, k, rv);
+#pragma unroll
+        for (int n = 0; n < NN; ++n) {
+            xv[n] = fma(alpha, pv[n], xv[n]);
+            rv[n] = fma(-alpha, qv[n], rv[n]);
+            zv[n] = rv[n] * dv[n];
+            v[0] += rv[n] * rv[n];
+            v[1] += rv[n] * zv[n];
+        }
+        stc<NN>(x, k, xv);
+        stc<NN>(r, k, rv);
+        stc<NN>(z, k, zv);
     }
     if (grid_sums<2>(v, part, &sc->count)) {
         sc->iters += 1;
@@ -447,51 +557,79 @@ pcg_update_kernel(int N, const double *__restrict__ p, const double *__restrict_
     }
 }
 
-// After the linear solve: E = x, back-substitution F = A_FF^-1 (b_F - A_FE E),
-// then the pointwise nonlinear elimination of T (Eq. nonlinear_T_update,
-// lumped): (C_v/dt) T + sigma_P a c T^4 = c sigma_E E + (C_v/dt) T*, Newton
-// from the current T, floored at T_floor.  Sums ||u_new - u_old||^2 and
-// ||u_new||^2 over u = (T, E) for Eq. relative_tol.
+// One thread: ends the device loop when PCG is done, and in any case once
+// the loop has run more trips than the iteration cap allows (two PCG
+// iterations per trip), so the loop ends whatever the reductions report.
+__global__ void pcg_check_kernel(Scalars *sc, cudaGraphConditionalHandle loop) {
+    const int runs = ++sc->body_runs;
+    if (sc->done != DONE_NO || 2 * (long long)runs >= (long long)sc->max_iters + 4)
+        cudaGraphSetConditional(loop, 0);
+}
+
+// After the linear solve, one thread per cell: E = x, back-substitution
+// F = A_FF^-1 (b_F - A_FE E), then the pointwise nonlinear elimination of T
+// (Eq. nonlinear_T_update, lumped): (C_v/dt) T + sigma_P a c T^4 =
+// c sigma_E E + (C_v/dt) T*, iterated from the current T and floored at
+// T_floor.  The step divides f by an FP32 reciprocal of f' (a quasi-Newton
+// step with relative slope error below 1e-7: the root and the stopping test
+// are those of Newton's method; FP64 division is expensive on this GPU).
+// Sums ||u_new - u_old||^2 and ||u_new||^2 over u = (T, E) for
+// Eq. relative_tol.
+template <int NN>
 __global__ void __launch_bounds__(BLOCK)
 newton_finish_kernel(Geo G, const double *__restrict__ clo, int nc, double a_rad, double dt,
-                     const double *__restrict__ x, const double *__restrict__ aF,
+                     const double *__restrict__ x, const double *__restrict__ iaF,
                      const double *__restrict__ bF, const double *__restrict__ Tstar,
                      const double *__restrict__ cv, double *__restrict__ T, double *__restrict__ E,
                      double *__restrict__ F, double rtol, int maxit, double T_floor, double *part,
                      Scalars *sc) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int D = NN == 4 ? 2 : 1;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     double v[2] = {0.0, 0.0};
-    int its = 0;
-    if (t < G.N) {
-        const int D = G.dim;
-        const double En = x[t];
-        const double inv_aF = 1.0 / aF[t];
-        for (int d = 0; d < D; ++d)
-            F[(size_t)t * D + d] = (bF[(size_t)t * D + d] - fe_comp(G, Vec{x}, t, d)) * inv_aF;
-        const double *cl = clo + (size_t)t * nc;
-        const double sE = D == 1 ? cl[3] : cl[6], sP = D == 1 ? cl[5] : cl[8];
-        const double cv_dt = cv[t] / dt;
-        const double k4 = sP * a_rad * G.c;
-        const double rhs = G.c * sE * En + cv_dt * Tstar[t];
-        const double Told = T[t];
-        double y = Told;
-        for (its = 1; its <= maxit; ++its) {
-            const double y3 = y * y * y;
-            const double f = cv_dt * y + k4 * y3 * y - rhs;
-            const double df = cv_dt + 4.0 * k4 * y3;
-            const double yn = fmax(y - f / df, T_floor);
-            const bool conv = fabs(yn - y) <= rtol * fabs(yn);
-            y = yn;
-            if (conv) break;
+    int its_max = 0;
+    if (k < G.ncell) {
+        const Cell C = cell_of(G, k);
+        double e[NN], ax[NN], ay[NN], ia[NN], Told[NN], Ts[NN], cvv[NN], Eold[NN], Tn[NN];
+        fe_cell<NN>(G, C, Vec<NN>{x}, e, ax, ay);
+        ldc<NN>(iaF, k, ia);
+        ldc<NN>(T, k, Told);
+        ldc<NN>(Tstar, k, Ts);
+        ldc<NN>(cv, k, cvv);
+        ldc<NN>(E, k, Eold);
+#pragma unroll
+        for (int n = 0; n < NN; ++n) {
+            const size_t nd = (size_t)k * NN + n;
+            F[nd * D] = (bF[nd * D] - ax[n]) * ia[n];
+            if constexpr (D == 2) F[nd * D + 1] = (bF[nd * D + 1] - ay[n]) * ia[n];
+            const double *cl = clo + nd * nc;
+            const double sE = cl[NN == 4 ? 6 : 3], sP = cl[NN == 4 ? 8 : 5];
+            const double cv_dt = cvv[n] / dt;
+            const double k4 = sP * a_rad * G.c;
+            const double rhs = G.c * sE * e[n] + cv_dt * Ts[n];
+            double y = Told[n];
+            int its;
+            for (its = 1; its <= maxit; ++its) {
+                const double y3 = y * y * y;
+                const double f = cv_dt * y + k4 * y3 * y - rhs;
+                const double df = cv_dt + 4.0 * k4 * y3;
+                const double adf = fabs(df);
+                const double rdf = (adf > 1e-30 && adf < 1e30) ? (double)__frcp_rn((float)df)
+                                                               : 1.0 / df;
+                const double yn = fmax(y - f * rdf, T_floor);
+                const bool conv = fabs(yn - y) <= rtol * fabs(yn);
+                y = yn;
+                if (conv) break;
+            }
+            its_max = max(its_max, min(its, maxit));
+            Tn[n] = y;
+            const double dT = y - Told[n], dE = e[n] - Eold[n];
+            v[0] += dT * dT + dE * dE;
+            v[1] += y * y + e[n] * e[n];
         }
-        its = min(its, maxit);
-        const double dT = y - Told, dE = En - E[t];
-        T[t] = y;
-        E[t] = En;
-        v[0] = dT * dT + dE * dE;
-        v[1] = y * y + En * En;
+        stc<NN>(T, k, Tn);
+        stc<NN>(E, k, e);
     }
-    const int wmax = __reduce_max_sync(0xffffffffu, its);
+    const int wmax = __reduce_max_sync(0xffffffffu, its_max);
     if ((threadIdx.x & 31) == 0 && wmax > 0) atomicMax(&sc->elim_max, wmax);
     if (grid_sums<2>(v, part, &sc->count)) {
         sc->d2 = v[0];
@@ -499,7 +637,8 @@ newton_finish_kernel(Geo G, const double *__restrict__ clo, int nc, double a_rad
     }
 }
 
-// Outer iteration: ||u - u_in||^2 and ||u||^2 for u = (T, E), then u_in <- u.
+// Outer iteration, one thread per node: ||u - u_in||^2 and ||u||^2 for
+// u = (T, E), then u_in <- u.
 __global__ void __launch_bounds__(BLOCK)
 outer_change_kernel(int N, const double *__restrict__ T, const double *__restrict__ E,
                     double *__restrict__ Tin, double *__restrict__ Ein, double *part, Scalars *sc) {
@@ -524,9 +663,9 @@ outer_change_kernel(int N, const double *__restrict__ T, const double *__restric
 // ===========================================================================
 // host side
 struct sm_lo_state {
-    int N = 0, D = 0, nblk = 0;
+    int N = 0, D = 0, NN = 0, nblk_cell = 0, nblk_node = 0;
     double *buf = nullptr;  // every node array in one allocation
-    double *aE, *aF, *bF, *ub, *diag, *x, *r, *z, *pb[2], *q, *Estar, *Fstar, *Tstar, *Tin, *Ein;
+    double *aE, *iaF, *bF, *ub, *idiag, *x, *r, *z, *pb[2], *q, *Estar, *Fstar, *Tstar, *Tin, *Ein;
     double *part = nullptr;
     double *jin2 = nullptr;     // [4] 2 |F_in| per side
     double *sigma = nullptr;    // sigma_g(T^k) of the running step
@@ -534,7 +673,7 @@ struct sm_lo_state {
     smk::lo::Scalars *sc = nullptr;
     smk::lo::Scalars *h_sc = nullptr;  // pinned mirror
     cudaStream_t cap = nullptr;        // private stream for graph capture
-    cudaGraph_t graph = nullptr;
+    cudaGraph_t graph = nullptr;       // PCG: one WHILE node, two iterations per trip
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -542,7 +681,6 @@ namespace {
 
 using smk::lo::BLOCK;
 using smk::lo::Geo;
-using smk::lo::PCG_CHUNK;
 
 sm_status lo_fail(sm_status s, const std::string &m) {
     smk::set_last_error(m.c_str());
@@ -567,34 +705,60 @@ Geo make_geo(const sm_problem *p) {
     G.dim = p->dim;
     G.nx = p->nx;
     G.ny = p->dim == 2 ? p->ny : 1;
-    G.nn = p->nn;
+    G.ncell = p->ncell;
     G.N = p->ncell * p->nn;
-    G.hx = p->hx;
-    G.hy = p->dim == 2 ? p->hy : 1.0;
-    G.m = p->dim == 1 ? 0.5 * p->hx : 0.25 * p->hx * p->hy;
-    G.wfx = p->dim == 1 ? 1.0 : 0.5 * p->hy;
-    G.wfy = 0.5 * p->hx;
+    const double hx = p->hx, hy = p->dim == 2 ? p->hy : 1.0;
+    G.m = p->dim == 1 ? 0.5 * hx : 0.25 * hx * hy;
     G.c = p->desc.c;
-    G.alpha = p->alpha;
+    G.wfx = p->dim == 1 ? 1.0 : 0.5 * hy;
+    G.wfy = 0.5 * hx;
+    G.c3 = G.c / 3.0;
+    G.lx = G.m / hx;
+    G.ly = G.m / hy;
+    G.kx = G.c3 * G.lx;
+    G.ky = G.c3 * G.ly;
+    G.fx = G.c3 * G.wfx;
+    G.fy = G.c3 * G.wfy;
+    const double ca = G.c * p->alpha;
+    G.px = 0.5 * ca * G.wfx;
+    G.py = 0.5 * ca * G.wfy;
+    G.bx = ca * G.wfx;
+    G.by = ca * G.wfy;
     return G;
 }
 
-// Capture PCG_CHUNK iterations (two kernels each) into a graph replayed on
-// the problem's stream; the device buffers it names never move.
+inline bool aligned16(const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
+
+// The PCG loop as a graph: a WHILE node whose body runs two iterations
+// (the search direction alternates between two buffers) and the check
+// kernel that clears the loop condition.
+template <int NN>
 sm_status build_graph(sm_problem *p, sm_lo_state &w) {
     const Geo G = make_geo(p);
     LO_CUDA(cudaStreamCreateWithFlags(&w.cap, cudaStreamNonBlocking));
-    LO_CUDA(cudaStreamBeginCapture(w.cap, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < PCG_CHUNK; ++i) {
-        double *po = w.pb[i & 1], *pn = w.pb[(i + 1) & 1];
-        smk::lo::pcg_matvec_kernel<<<w.nblk, BLOCK, 0, w.cap>>>(G, w.aE, w.aF, w.z, po, pn, w.q,
-                                                                w.part, w.sc);
-        smk::lo::pcg_update_kernel<<<w.nblk, BLOCK, 0, w.cap>>>(G.N, pn, w.q, w.diag, w.x, w.r,
-                                                                w.z, w.part, w.sc);
+    LO_CUDA(cudaGraphCreate(&w.graph, 0));
+    cudaGraphConditionalHandle loop;
+    LO_CUDA(cudaGraphConditionalHandleCreate(&loop, w.graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    LO_CUDA(cudaGraphAddNode(&node, w.graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    LO_CUDA(cudaStreamBeginCaptureToGraph(w.cap, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < 2; ++i) {
+        double *po = w.pb[i], *pn = w.pb[1 - i];
+        smk::lo::pcg_matvec_kernel<NN><<<w.nblk_cell, BLOCK, 0, w.cap>>>(G, w.aE, w.iaF, w.z, po,
+                                                                         pn, w.q, w.part, w.sc);
+        smk::lo::pcg_update_kernel<NN><<<w.nblk_cell, BLOCK, 0, w.cap>>>(
+            G.ncell, pn, w.q, w.idiag, w.x, w.r, w.z, w.part, w.sc);
     }
-    cudaGraph_t g = nullptr;
-    LO_CUDA(cudaStreamEndCapture(w.cap, &g));
-    w.graph = g;
+    smk::lo::pcg_check_kernel<<<1, 1, 0, w.cap>>>(w.sc, loop);
+    cudaGraph_t captured = nullptr;
+    LO_CUDA(cudaStreamEndCapture(w.cap, &captured));
     LO_CUDA(cudaGraphInstantiate(&w.exec, w.graph, 0));
     return SM_OK;
 }
@@ -608,7 +772,9 @@ sm_status lo_ensure(sm_problem *p) {
     const int N = p->ncell * p->nn, D = p->dim;
     w.N = N;
     w.D = D;
-    w.nblk = (N + BLOCK - 1) / BLOCK;
+    w.NN = p->nn;
+    w.nblk_cell = (p->ncell + BLOCK - 1) / BLOCK;
+    w.nblk_node = (N + BLOCK - 1) / BLOCK;
     const size_t nS = 13, nV = 3;  // node arrays and [node][dim] arrays
     const size_t buf_elems = (size_t)N * nS + (size_t)N * D * nV;
     LO_CUDA(cudaMalloc(&w.buf, sizeof(double) * buf_elems));
@@ -622,8 +788,8 @@ sm_status lo_ensure(sm_problem *p) {
     w.ub = take((size_t)N * D);
     w.Fstar = take((size_t)N * D);
     w.aE = take(N);
-    w.aF = take(N);
-    w.diag = take(N);
+    w.iaF = take(N);
+    w.idiag = take(N);
     w.x = take(N);
     w.r = take(N);
     w.z = take(N);
@@ -634,15 +800,16 @@ sm_status lo_ensure(sm_problem *p) {
     w.Tstar = take(N);
     w.Tin = take(N);
     w.Ein = take(N);
-    LO_CUDA(cudaMalloc(&w.part, sizeof(double) * 3 * (size_t)w.nblk));
+    const size_t nblk = (size_t)std::max(w.nblk_cell, w.nblk_node);
+    LO_CUDA(cudaMalloc(&w.part, sizeof(double) * 3 * nblk));
     LO_CUDA(cudaMalloc(&w.jin2, sizeof(double) * 4));
     LO_CUDA(cudaMalloc(&w.sigma, sizeof(double) * (size_t)p->G * p->ncell));
     LO_CUDA(cudaMalloc(&w.clo, sizeof(double) * (size_t)N * p->nc));
     LO_CUDA(cudaMalloc(&w.sc, sizeof(smk::lo::Scalars)));
     LO_CUDA(cudaMemset(w.sc, 0, sizeof(smk::lo::Scalars)));
     LO_CUDA(cudaMallocHost(&w.h_sc, sizeof(smk::lo::Scalars)));
-    p->workspace_bytes += sizeof(double) * (buf_elems + 3 * (size_t)w.nblk + 4 +
-                                            (size_t)p->G * p->ncell + (size_t)N * p->nc) +
+    p->workspace_bytes += sizeof(double) * (buf_elems + 3 * nblk + 4 + (size_t)p->G * p->ncell +
+                                            (size_t)N * p->nc) +
                           sizeof(smk::lo::Scalars);
     // 2 |F_in| per side: 2 sum_{Omega.n<0} w |Omega.n| I_in with the gray
     // isotropic inflow I_in = a c T_bdr^4 / 4 pi (vacuum where T_bdr <= 0)
@@ -660,7 +827,7 @@ sm_status lo_ensure(sm_problem *p) {
         jin2[s] = 2.0 * acc * Iin;
     }
     LO_CUDA(cudaMemcpy(w.jin2, jin2, sizeof(jin2), cudaMemcpyHostToDevice));
-    return build_graph(p, w);
+    return p->dim == 2 ? build_graph<4>(p, w) : build_graph<2>(p, w);
 }
 
 sm_status read_scalars(sm_problem *p) {
@@ -683,7 +850,9 @@ sm_status check_params(const sm_step_params &prm) {
 
 // The Newton iteration of Sec. 5 on the gray system with fixed closures.
 // Time-edge sources in w.Estar / w.Fstar; T, E hold the initial guesses and
-// receive the result, F receives the flux of the last linear solve.
+// receive the result, F receives the flux of the last linear solve.  One
+// host synchronisation per Newton iteration (its stopping test).
+template <int NN>
 sm_status lo_solve(sm_problem *p, const double *clo, const double *Tstar, const double *cv,
                    double *T, double *E, double *F, const sm_step_params &prm,
                    sm_step_stats *st) {
@@ -691,44 +860,35 @@ sm_status lo_solve(sm_problem *p, const double *clo, const double *Tstar, const 
     const Geo G = make_geo(p);
     cudaStream_t s = p->stream;
     const double dt = p->desc.dt, a = p->desc.a;
-    smk::lo::prepare_kernel<<<w.nblk, BLOCK, 0, s>>>(G, clo, p->nc, 1.0 / (G.c * dt), w.Fstar,
-                                                     w.aF, w.bF, w.ub, w.sc);
+    smk::lo::prepare_kernel<<<w.nblk_node, BLOCK, 0, s>>>(G, clo, p->nc, 1.0 / (G.c * dt),
+                                                          w.Fstar, w.iaF, w.bF, w.ub, w.sc);
     LO_CUDA(cudaGetLastError());
     p->launches++;
     double d1 = -1.0;
-    const int max_chunks = prm.max_pcg / PCG_CHUNK + 2;
     for (int it = 1; it <= prm.max_inner; ++it) {
-        smk::lo::newton_setup_kernel<<<w.nblk, BLOCK, 0, s>>>(
-            G, clo, p->nc, a, dt, T, Tstar, cv, w.Estar, w.jin2, w.aF, w.ub, E, w.aE, w.diag, w.x,
-            w.r, w.z, w.pb[0], prm.pcg_rtol, prm.max_pcg, w.part, w.sc);
+        smk::lo::newton_setup_kernel<NN><<<w.nblk_cell, BLOCK, 0, s>>>(
+            G, clo, p->nc, a, dt, T, Tstar, cv, w.Estar, w.jin2, w.iaF, w.ub, E, w.aE, w.idiag,
+            w.x, w.r, w.z, w.pb[0], prm.pcg_rtol, prm.max_pcg, w.part, w.sc);
         LO_CUDA(cudaGetLastError());
-        p->launches++;
+        LO_CUDA(cudaGraphLaunch(w.exec, s));
+        smk::lo::newton_finish_kernel<NN><<<w.nblk_cell, BLOCK, 0, s>>>(
+            G, clo, p->nc, a, dt, w.x, w.iaF, w.bF, Tstar, cv, T, E, F, prm.elim_rtol,
+            prm.max_elim, prm.T_floor, w.part, w.sc);
+        LO_CUDA(cudaGetLastError());
         LO_TRY(read_scalars(p));
-        int chunks = 0;
-        while (!w.h_sc->done && chunks < max_chunks) {
-            LO_CUDA(cudaGraphLaunch(w.exec, s));
-            p->launches += 2 * PCG_CHUNK;
-            ++chunks;
-            LO_TRY(read_scalars(p));
-        }
-        const int done = w.h_sc->done;
-        if (done == smk::lo::DONE_BREAKDOWN)
+        const smk::lo::Scalars &h = *w.h_sc;
+        // kernels that ran: setup, finish, and per loop trip 4 PCG kernels
+        // (they return at once after convergence) plus the check kernel
+        p->launches += 2 + 5LL * h.body_runs;
+        if (h.done == smk::lo::DONE_BREAKDOWN)
             return lo_fail(SM_ERR_NO_CONVERGENCE,
                            "conjugate gradients broke down: the Schur complement is not positive "
                            "definite on the search direction, or the data is not finite");
-        if (done == smk::lo::DONE_NO)
-            return lo_fail(SM_ERR_NO_CONVERGENCE, "conjugate gradients did not stop");
-        st->pcg_iters_total += w.h_sc->iters;
-        st->pcg_iters_max = std::max(st->pcg_iters_max, w.h_sc->iters);
-        if (done == smk::lo::DONE_CAPPED) st->pcg_capped++;
-        smk::lo::newton_finish_kernel<<<w.nblk, BLOCK, 0, s>>>(
-            G, clo, p->nc, a, dt, w.x, w.aF, w.bF, Tstar, cv, T, E, F, prm.elim_rtol, prm.max_elim,
-            prm.T_floor, w.part, w.sc);
-        LO_CUDA(cudaGetLastError());
-        p->launches++;
-        LO_TRY(read_scalars(p));
+        st->pcg_iters_total += h.iters;
+        st->pcg_iters_max = std::max(st->pcg_iters_max, h.iters);
+        if (h.done != smk::lo::DONE_CONVERGED) st->pcg_capped++;
         st->newton_iters_total++;
-        const double dn = std::sqrt(w.h_sc->d2), un = std::sqrt(w.h_sc->n2);
+        const double dn = std::sqrt(h.d2), un = std::sqrt(h.n2);
         if (!std::isfinite(dn))
             return lo_fail(SM_ERR_NONPHYSICAL, "the low-order Newton iterate is not finite");
         if (d1 < 0) d1 = dn;
@@ -739,6 +899,12 @@ sm_status lo_solve(sm_problem *p, const double *clo, const double *Tstar, const 
     }
     st->elim_iters_max = std::max(st->elim_iters_max, w.h_sc->elim_max);
     return SM_OK;
+}
+
+sm_status run_lo(sm_problem *p, const double *clo, const double *Tstar, const double *cv,
+                 double *T, double *E, double *F, const sm_step_params &prm, sm_step_stats *st) {
+    return p->dim == 2 ? lo_solve<4>(p, clo, Tstar, cv, T, E, F, prm, st)
+                       : lo_solve<2>(p, clo, Tstar, cv, T, E, F, prm, st);
 }
 
 sm_status check_lo_problem(sm_problem *p) {
@@ -787,6 +953,8 @@ sm_status sm_loworder_newton(sm_problem *p, const double *closures_dev, const do
     if (!p || !closures_dev || !T_star_dev || !cv_dev || !moments_star_dev || !T_dev || !E_dev ||
         !F_dev)
         return lo_fail(SM_ERR_INVALID_ARG, "NULL argument to sm_loworder_newton");
+    if (!aligned16(T_star_dev) || !aligned16(cv_dev) || !aligned16(T_dev) || !aligned16(E_dev))
+        return lo_fail(SM_ERR_INVALID_ARG, "T, T_star, cv and E must be 16-byte aligned");
     sm_step_params prm;
     if (params)
         prm = *params;
@@ -795,12 +963,12 @@ sm_status sm_loworder_newton(sm_problem *p, const double *closures_dev, const do
     LO_TRY(check_params(prm));
     LO_TRY(check_lo_problem(p));
     sm_lo_state &w = *p->lo;
-    smk::lo::timeedge_kernel<<<w.nblk, BLOCK, 0, p->stream>>>(w.N, w.D, p->nm, 1.0 / p->desc.c,
-                                                             moments_star_dev, w.Estar, w.Fstar);
+    smk::lo::timeedge_kernel<<<w.nblk_node, BLOCK, 0, p->stream>>>(
+        w.N, w.D, p->nm, 1.0 / p->desc.c, moments_star_dev, w.Estar, w.Fstar);
     LO_CUDA(cudaGetLastError());
     p->launches++;
     sm_step_stats st{};
-    LO_TRY(lo_solve(p, closures_dev, T_star_dev, cv_dev, T_dev, E_dev, F_dev, prm, &st));
+    LO_TRY(run_lo(p, closures_dev, T_star_dev, cv_dev, T_dev, E_dev, F_dev, prm, &st));
     st.converged = 1;
     if (stats) *stats = st;
     return SM_OK;
@@ -813,6 +981,8 @@ sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, 
     if (!p || !scale_dev || !cv_dev || !T_dev || !E_dev || !F_dev || !moments_dev || !I_prev_dev ||
         !I_next_dev)
         return lo_fail(SM_ERR_INVALID_ARG, "NULL argument to sm_step");
+    if (!aligned16(cv_dev) || !aligned16(T_dev) || !aligned16(E_dev))
+        return lo_fail(SM_ERR_INVALID_ARG, "T, cv and E must be 16-byte aligned");
     sm_step_params prm;
     if (params)
         prm = *params;
@@ -826,8 +996,8 @@ sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, 
     double *clo = closures_dev ? closures_dev : w.clo;
     // opacities frozen at T^k for the whole step (Sec. 3, Rem. opacity)
     LO_TRY(sm_opacity(p, T_dev, scale_dev, w.sigma));
-    smk::lo::timeedge_kernel<<<w.nblk, BLOCK, 0, s>>>(N, w.D, p->nm, 1.0 / p->desc.c, moments_dev,
-                                                     w.Estar, w.Fstar);
+    smk::lo::timeedge_kernel<<<w.nblk_node, BLOCK, 0, s>>>(N, w.D, p->nm, 1.0 / p->desc.c,
+                                                          moments_dev, w.Estar, w.Fstar);
     LO_CUDA(cudaGetLastError());
     p->launches++;
     LO_CUDA(cudaMemcpyAsync(w.Tstar, T_dev, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
@@ -840,9 +1010,9 @@ sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, 
         // high-order solve with the current T: emission, sweep, moments, closures
         LO_TRY(sm_sweep(p, T_dev, w.sigma, I_prev_dev, I_next_dev, moments_dev, clo));
         LO_TRY(sm_synchronize(p));
-        LO_TRY(lo_solve(p, clo, w.Tstar, cv_dev, T_dev, E_dev, F_dev, prm, &st));
-        smk::lo::outer_change_kernel<<<w.nblk, BLOCK, 0, s>>>(N, T_dev, E_dev, w.Tin, w.Ein,
-                                                             w.part, w.sc);
+        LO_TRY(run_lo(p, clo, w.Tstar, cv_dev, T_dev, E_dev, F_dev, prm, &st));
+        smk::lo::outer_change_kernel<<<w.nblk_node, BLOCK, 0, s>>>(N, T_dev, E_dev, w.Tin, w.Ein,
+                                                                  w.part, w.sc);
         LO_CUDA(cudaGetLastError());
         p->launches++;
         LO_TRY(read_scalars(p));
