@@ -21,6 +21,8 @@ namespace smk {
 constexpr int NBERN = 18;   // head terms: (2/2pi)^36 < 1e-17
 constexpr int NTAIL = 24;   // tail terms: e^{-2*24} ~ 1e-21
 constexpr double XSWITCH = 2.0;
+// from x = 37 on, e^{-x} < 1e-16: the tail series keeps its first term only
+constexpr double XCLOSED = 37.0;
 constexpr double PI_D = 3.14159265358979323846;
 constexpr double C15 = 15.0 / (PI_D * PI_D * PI_D * PI_D);
 
@@ -30,6 +32,11 @@ constexpr double C15 = 15.0 / (PI_D * PI_D * PI_D * PI_D);
 __constant__ double c_head[NBERN];
 __constant__ double c_bern[NBERN];   // B_2k/(2k)!, k = 1..NBERN
 __constant__ double c_inv_n[NTAIL][4];
+// e^{-x} by the table-driven method of Tang (ACM TOMS 15, 1989): 64/ln2, and
+// ln2/64 split into a 32-bit high part (exact products with the step index)
+// and the rounded remainder; the table holds 2^{-j/64}, j = 0..63.
+__constant__ double c_exp[3];
+__device__ double g_exp2_tab[64];
 
 static bool g_tables_ready[128] = {false};
 
@@ -57,6 +64,14 @@ void planck_upload_tables(void) {
         head[k - 1] = bk / (2.0 * k + 3.0);
         bern[k - 1] = bk;
     }
+    const long double ln2 = 0.693147180559945309417232121458176568L;
+    const long double l64 = ln2 / 64.0L;
+    int ex = 0;
+    frexp((double)l64, &ex);
+    const double l64_hi = ldexp(floor(ldexp((double)l64, 32 - ex)), ex - 32);
+    const double cexp[3] = {(double)(64.0L / ln2), l64_hi, (double)(l64 - (long double)l64_hi)};
+    double tab[64];
+    for (int j = 0; j < 64; ++j) tab[j] = (double)exp2l(-(long double)j / 64.0L);
     double invn[NTAIL][4];
     for (int n = 1; n <= NTAIL; ++n) {
         double r = 1.0 / n;
@@ -67,8 +82,21 @@ void planck_upload_tables(void) {
     }
     if (cudaMemcpyToSymbol(c_head, head, sizeof(head)) == cudaSuccess &&
         cudaMemcpyToSymbol(c_bern, bern, sizeof(bern)) == cudaSuccess &&
-        cudaMemcpyToSymbol(c_inv_n, invn, sizeof(invn)) == cudaSuccess)
+        cudaMemcpyToSymbol(c_inv_n, invn, sizeof(invn)) == cudaSuccess &&
+        cudaMemcpyToSymbol(c_exp, cexp, sizeof(cexp)) == cudaSuccess &&
+        cudaMemcpyToSymbol(g_exp2_tab, tab, sizeof(tab)) == cudaSuccess)
         g_tables_ready[dev] = true;
+}
+
+// 1/d for d in [1/2, 1] by the Newton-Raphson reciprocal iteration
+// r <- r (2 - d r) from an FP32 seed (relative error below 2^-23): each step
+// squares the error, so two steps reach double rounding.  Four FMAs, where a
+// correctly rounded FP64 division costs several times more on this GPU.
+__device__ __forceinline__ double recip_nr(double d) {
+    double r = (double)__frcp_rn((float)d);
+    r = fma(r, fma(-d, r, 1.0), r);
+    r = fma(r, fma(-d, r, 1.0), r);
+    return r;
 }
 
 // Values of the cumulative spectra at one reduced edge x = nu/T.
@@ -78,21 +106,55 @@ struct EdgeVals {
     bool tail;     // x in the tail branch
 };
 
-__device__ __forceinline__ EdgeVals edge_vals(double x) {
+// Terms of the head series (x < 2) needed for a truncation error below 2^-56
+// of its leading term, and of the tail series (2 <= x < 37): the first
+// omitted tail term, e^{-N x}/(N+1) of the first, is below 2^-55 for
+// N = ceil(38.2/x).
+// Both are decided in FP32 on xf = (float)x: a count only needs to be large
+// enough, and FP64 compares and divisions are scarce on this GPU.
+__device__ __forceinline__ int head_terms(float xf) {
+    return xf <= 0.25f ? 6 : xf <= 0.5f ? 7 : xf <= 1.0f ? 10 : xf <= 1.5f ? 14 : NBERN;
+}
+__device__ __forceinline__ int tail_terms(float xf) {
+    return min(NTAIL, (int)ceilf(__fdividef(38.25f, xf)));
+}
+
+// e^{-x} for 0 <= x < 708 (normal results): x = N ln2/64 + r with
+// N = round(64 x/ln2) and |r| <= ln2/128, so e^{-x} = 2^{-(N>>6)} 2^{-(N&63)/64}
+// e^{-r}, with e^{-r} by its degree-6 Taylor polynomial (remainder below
+// |r|^7/7! < 2e-20).  About two thirds of the FP64 work of exp() here.
+__device__ __forceinline__ double exp_neg(double x) {
+    const double Nd = rint(x * c_exp[0]);
+    const double s = fma(Nd, c_exp[2], fma(Nd, c_exp[1], -x));  // -r
+    const int n = (int)Nd;
+    double p = fma(s, 1.0 / 720.0, 1.0 / 120.0);
+    p = fma(p, s, 1.0 / 24.0);
+    p = fma(p, s, 1.0 / 6.0);
+    p = fma(p, s, 0.5);
+    p = fma(p, s, 1.0);
+    p = fma(p, s, 1.0);
+    const double scale = __longlong_as_double((long long)(1023 - (n >> 6)) << 52);
+    return __ldg(&g_exp2_tab[n & 63]) * p * scale;
+}
+
+// K, N: head and tail term counts to use (at least head_terms(x) and
+// tail_terms(x)); callers that keep a warp converged pass the warp maximum,
+// so that every lane reads the same coefficient at each step.
+__device__ __forceinline__ EdgeVals edge_vals(double x, int K, int N) {
     EdgeVals e;
-    if (!(x > 0.0)) {
+    const float xf = (float)x;
+    if (!(xf > 0.0f)) {
         e.P = 0.0; e.Q = 1.0; e.R = 0.0; e.RQ = 1.0; e.tail = false;
         return e;
     }
-    if (isinf(x)) {
+    if (isinf(xf)) {
         e.P = 1.0; e.Q = 0.0; e.R = 1.0; e.RQ = 0.0; e.tail = true;
         return e;
     }
-    if (x < XSWITCH) {
+    if (xf < (float)XSWITCH) {
         const double y = x * x;
-        double poly = c_head[NBERN - 1], pb = c_bern[NBERN - 1];
-#pragma unroll
-        for (int k = NBERN - 2; k >= 0; --k) {
+        double poly = c_head[K - 1], pb = c_bern[K - 1];
+        for (int k = K - 2; k >= 0; --k) {
             poly = fma(poly, y, c_head[k]);
             pb = fma(pb, y, c_bern[k]);
         }
@@ -109,23 +171,43 @@ __device__ __forceinline__ EdgeVals edge_vals(double x) {
         e.tail = false;
         return e;
     }
-    const double e1 = exp(-x);
-    const int nmax = min(NTAIL, (int)(40.0 / x) + 2);
-    double en = 1.0, sum = 0.0;
-    const double x2 = x * x, x3 = x2 * x, x2_3 = 3.0 * x2, x_6 = 6.0 * x;
-    for (int n = 0; n < nmax; ++n) {
-        en *= e1;
-        const double t = fma(x3, c_inv_n[n][0],
-                             fma(x2_3, c_inv_n[n][1], fma(x_6, c_inv_n[n][2], 6.0 * c_inv_n[n][3])));
-        sum = fma(en, t, sum);
+    const double e1 = xf < 708.0f ? exp_neg(x) : exp(-x);
+    const double x2 = x * x;
+    if (xf >= (float)XCLOSED) {
+        // only the n = 1 term is above double rounding: 1 - P = (15/pi^4) e^{-x}
+        // (x^3 + 3x^2 + 6x + 6), and 1/(1 - e^{-x}) = 1
+        e.Q = C15 * e1 * fma(fma(x + 3.0, x, 6.0), x, 6.0);
+        e.P = 1.0 - e.Q;
+        const double rx = 0.25 * C15 * (x2 * x2) * e1;
+        e.R = e.P - rx;
+        e.RQ = e.Q + rx;
+        e.tail = true;
+        return e;
     }
+    // sum_n u^n (x^3/n + 3x^2/n^2 + 6x/n^3 + 6/n^4) = x^3 Li_1(u) + 3x^2 Li_2(u)
+    // + 6x Li_3(u) + 6 Li_4(u), u = e^{-x}, each polylogarithm by Horner in u
+    const int nmax = N;
+    double L1 = 0.0, L2 = 0.0, L3 = 0.0, L4 = 0.0;
+    for (int n = nmax - 1; n >= 0; --n) {
+        L1 = fma(L1, e1, c_inv_n[n][0]);
+        L2 = fma(L2, e1, c_inv_n[n][1]);
+        L3 = fma(L3, e1, c_inv_n[n][2]);
+        L4 = fma(L4, e1, c_inv_n[n][3]);
+    }
+    const double sum = e1 * fma(x2 * x, L1, fma(3.0 * x2, L2, fma(6.0 * x, L3, 6.0 * L4)));
     e.Q = C15 * sum;
     e.P = 1.0 - e.Q;
-    const double rx = 0.25 * C15 * (x2 * x2) * e1 / (1.0 - e1);
+    const double rx = 0.25 * C15 * (x2 * x2) * e1 * recip_nr(1.0 - e1);
     e.R = e.P - rx;
     e.RQ = e.Q + rx;
     e.tail = true;
     return e;
+}
+
+__device__ __forceinline__ EdgeVals edge_vals(double x) {
+    const float xf = (float)x;
+    return edge_vals(x, xf < (float)XSWITCH ? head_terms(xf) : NBERN,
+                     xf >= (float)XSWITCH ? tail_terms(xf) : 1);
 }
 
 // b_g and r_g of the group between reduced edges lo < hi
@@ -175,13 +257,16 @@ __global__ void emission_kernel(int ncell, int nn, int G, int Gp, const double *
                                 const double *__restrict__ sigma, RT *__restrict__ src,
                                 double *__restrict__ gray, double *__restrict__ qcanon,
                                 unsigned int *ctrl) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ncell * nn) return;
+    // Lanes past the last node evaluate a copy of it and store nothing, so
+    // that every warp stays converged through the edge loop (the series term
+    // counts below are warp maxima).
+    const int n_nodes = ncell * nn;
+    const int t_raw = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = t_raw < n_nodes;
+    const int t = active ? t_raw : n_nodes - 1;
     const int cell = t / nn, node = t - cell * nn;
     double Tn = T[t];
-    if (!(Tn > 0.0) || !isfinite(Tn)) {
-        atomicOr(ctrl + CTRL_STATUS, ST_NONPHYSICAL);
-    }
+    if (active && (!(Tn > 0.0) || !isfinite(Tn))) atomicOr(ctrl + CTRL_STATUS, ST_NONPHYSICAL);
     const double B4 = acT4_scale * Tn * Tn * Tn * Tn;  // a c T^4 / 4 pi
     const double invT = 1.0 / Tn;
     EdgeVals lo = edge_vals(0.0);
@@ -191,7 +276,14 @@ __global__ void emission_kernel(int ncell, int nn, int G, int Gp, const double *
         const double xhi = (g == G - 1) ? INFINITY : edges[g + 1] * invT;
         // beyond x ~ 745 the tails 1 - P and 1 - R underflow to exactly 0, so
         // every higher group has b = r = 0: skip their series
-        const EdgeVals hi = (lo.tail && lo.Q == 0.0 && lo.RQ == 0.0) ? lo : edge_vals(xhi);
+        const bool skip = lo.tail && lo.Q == 0.0 && lo.RQ == 0.0;
+        const float xf = (float)xhi;
+        const int K = __reduce_max_sync(
+            0xffffffffu, (!skip && xf < (float)XSWITCH) ? head_terms(xf) : 1);
+        const int N = __reduce_max_sync(
+            0xffffffffu,
+            (!skip && xf >= (float)XSWITCH && xf < (float)XCLOSED) ? tail_terms(xf) : 1);
+        const EdgeVals hi = skip ? lo : edge_vals(xhi, K, N);
         double b, r;
         group_br(lo, hi, b, r);
         const double sg = sigma[(size_t)g * ncell + cell];
@@ -200,28 +292,30 @@ __global__ void emission_kernel(int ncell, int nn, int G, int Gp, const double *
         nr = fma(r, sg, nr);
         dr += r;
         const double qv = sg * b * B4;
-        RT *rec = rec0 + (size_t)g * 8;
-        rec[node] = (RT)qv;
-        if (qcanon) qcanon[((size_t)g * ncell + cell) * nn + node] = qv;
-        if (node == 0) {
-            for (int n = nn; n < 4; ++n) rec[n] = (RT)0;
-            rec[4] = (RT)(sg + inv_cdt);
-            rec[5] = (RT)sg;
-            rec[6] = (RT)0;
-            rec[7] = (RT)0;
+        if (active) {
+            rec0[(size_t)g * 8 + node] = (RT)qv;
+            if (qcanon) qcanon[((size_t)g * ncell + cell) * nn + node] = qv;
         }
         lo = hi;
     }
-    for (int g = G; g < Gp; ++g) {  // padding groups: no source, unit sigma~
+    if (!active) return;
+    // the per-cell part of each record (unused node slots, sigma~, sigma), and
+    // the padding groups (no source, unit sigma~), shared out among the nodes
+    // of the cell so that each warp converts a quarter of the opacities
+    for (int g = node; g < Gp; g += nn) {
         RT *rec = rec0 + (size_t)g * 8;
-        rec[node] = (RT)0;
-        if (node == 0) {
-            for (int n = nn; n < 4; ++n) rec[n] = (RT)0;
+        if (g < G) {
+            const double sg = sigma[(size_t)g * ncell + cell];
+            rec[4] = (RT)(sg + inv_cdt);
+            rec[5] = (RT)sg;
+        } else {
+            for (int n = 0; n < nn; ++n) rec[n] = (RT)0;
             rec[4] = (RT)1;
             rec[5] = (RT)0;
-            rec[6] = (RT)0;
-            rec[7] = (RT)0;
         }
+        for (int n = nn; n < 4; ++n) rec[n] = (RT)0;
+        rec[6] = (RT)0;
+        rec[7] = (RT)0;
     }
     gray[(size_t)t * 2 + 0] = nb / db;
     gray[(size_t)t * 2 + 1] = nr / dr;
@@ -318,7 +412,9 @@ cudaError_t launch_opacity(const sm_problem *p, const double *T, const double *s
 
 cudaError_t launch_emission(const sm_problem *p, const double *T, const double *sigma,
                             double *q_canon, cudaStream_t s) {
-    const int threads = 128;
+    // one warp per block: node costs differ by up to ~2x (hot nodes have more
+    // edges below the underflow point), and small blocks keep the last wave short
+    const int threads = 32;
     const int n = p->ncell * p->nn;
     const int blocks = (n + threads - 1) / threads;
     const double scale = p->desc.a * p->desc.c / (4.0 * PI_D);
