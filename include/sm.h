@@ -320,6 +320,72 @@ sm_status sm_sweep_static(const sm_problem_desc *desc, void *stream, const doubl
                           const double *sigma_dev, const double *I_prev_canon_dev,
                           double *I_out_canon_dev, double *moments_dev, double *closures_dev);
 
+/* ------------------------------------------------------------------------
+ * Batched problems: many independent 2D problems -- uneven meshes, group and
+ * direction counts, material layouts -- swept in ONE persistent launch.  The
+ * batch owns one problem per member (created from descs[i]; precision must
+ * be the same for all, dim must be 2, tile fields are ignored: the batch's
+ * strip width and prefetch depth apply to every member).  Every CTA of the
+ * batched sweep takes (member, task) items from one queue, ordered so that
+ * each member keeps its own upwind order.  A call to sm_batch_sweep runs
+ * the whole pass for every member -- emission (a1), sweep with fused
+ * moments (a2, a3), moment sums and closures (a4) -- recorded the first time
+ * as a CUDA graph for that set of buffers and replayed on later calls with
+ * the same buffers (up to 4 buffer sets are kept, e.g. the two roles of the
+ * intensity buffers in a time loop).  The paper runs independent problems
+ * one after another; batching them is this library's addition.
+ * ---------------------------------------------------------------------- */
+typedef struct sm_batch sm_batch; /* opaque, owned by the library */
+
+typedef struct {
+    int n_problems;
+    int n_tasks;        /* queue items of one batched sweep */
+    int strip_width, prefetch_rows;
+    int resident_ctas;  /* persistent grid of the batched sweep */
+    int graphs_cached;
+    size_t smem_bytes;  /* dynamic shared memory per CTA */
+    double updates;     /* sum over members of cells x directions x groups */
+    int64_t launches;   /* kernels launched by batched sweeps so far */
+} sm_batch_info;
+
+/* stream: cudaStream_t (NULL = legacy default stream).  Errors as
+ * sm_create_problem, plus INVALID_ARG for n < 1, a 1D member or mixed
+ * precisions. */
+sm_status sm_create_batch(const sm_problem_desc *descs, int n, void *stream, sm_batch **out);
+/* Destroys the batch and its members.  NULL is accepted. */
+sm_status sm_destroy_batch(sm_batch *b);
+/* Borrowed handle of member i, for sm_get_info, sm_get_quadrature,
+ * sm_opacity, sm_emission, sm_closures, sm_pack_intensity and
+ * sm_unpack_intensity.  sm_sweep, sm_sweep_host, sm_autotune, sm_set_tiling
+ * and sm_destroy_problem refuse batch members (INVALID_ARG): their wavefront
+ * counters belong to the batch. */
+sm_status sm_batch_problem(sm_batch *b, int i, sm_problem **out);
+sm_status sm_batch_get_info(const sm_batch *b, sm_batch_info *out);
+sm_status sm_batch_set_stream(sm_batch *b, void *stream);
+/* Strip width 1..16 and prefetch depth 2..8 for every member (0 keeps the
+ * current value).  Synchronizes the stream; drops the recorded graphs. */
+sm_status sm_batch_set_tiling(sm_batch *b, int strip_width, int prefetch_rows);
+/* One pass for every member.  Each argument is a HOST array of n device
+ * pointers, laid out as for sm_sweep: T_nodal[i], sigma[i], I_prev[i] (the
+ * array or an entry may be NULL: no time-edge source), I_out[i] (required,
+ * 16-byte aligned, not aliasing I_prev[i]), moments[i] and closures[i]
+ * (arrays or entries may be NULL).  Asynchronous on the batch's stream;
+ * sm_batch_synchronize reports device-side status. */
+sm_status sm_batch_sweep(sm_batch *b, const double *const *T_nodal_dev,
+                         const double *const *sigma_dev, const void *const *I_prev_dev,
+                         void *const *I_out_dev, double *const *moments_dev,
+                         double *const *closures_dev);
+/* Waits for the batch's stream; SM_OK, SM_ERR_TIMEOUT or SM_ERR_NONPHYSICAL
+ * (then clears the status). */
+sm_status sm_batch_synchronize(sm_batch *b);
+/* Picks the strip width and prefetch depth of the batch by timing each
+ * candidate (W in 2..16, S in 2..4) on the given buffers with CUDA events,
+ * reps timed passes after one warm-up; keeps the fastest.  Overwrites
+ * I_out.  Synchronous. */
+sm_status sm_batch_autotune(sm_batch *b, const double *const *T_nodal_dev,
+                            const double *const *sigma_dev, const void *const *I_prev_dev,
+                            void *const *I_out_dev, int reps);
+
 /* Number of kernels this problem has launched since creation. */
 int64_t sm_launch_count(const sm_problem *p);
 

@@ -29,7 +29,10 @@ EXPORTED = ["sm_create_problem", "sm_destroy_problem", "sm_get_info", "sm_set_st
             "sm_synchronize", "sm_autotune", "sm_set_profiling", "sm_get_kernel_times",
             "sm_launch_count", "sm_last_error", "sm_status_string",
             "sm_debug_set_wait_limit_ns", "sm_debug_skip_publish", "sm_sweep_static",
-            "sm_default_step_params", "sm_loworder_newton", "sm_step"]
+            "sm_default_step_params", "sm_loworder_newton", "sm_step",
+            "sm_create_batch", "sm_destroy_batch", "sm_batch_problem", "sm_batch_get_info",
+            "sm_batch_set_stream", "sm_batch_set_tiling", "sm_batch_sweep",
+            "sm_batch_synchronize", "sm_batch_autotune"]
 
 
 class SMError(RuntimeError):
@@ -75,6 +78,13 @@ class StepStats(ctypes.Structure):
         ("last_change", ctypes.c_double)]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in (
+        "n_problems", "n_tasks", "strip_width", "prefetch_rows", "resident_ctas",
+        "graphs_cached")] + [("smem_bytes", ctypes.c_size_t), ("updates", ctypes.c_double),
+                              ("launches", ctypes.c_int64)]
+
+
 def step_params(**overrides) -> StepParams:
     """The library's default iteration controls with the given fields replaced."""
     prm = StepParams()
@@ -106,6 +116,7 @@ def load():
     I = ctypes.c_int
     D = ctypes.c_double
     PD = ctypes.POINTER(ctypes.c_double)
+    PP = ctypes.POINTER(ctypes.c_void_p)
     sigs = {
         "sm_create_problem": [ctypes.POINTER(ProblemDesc), P, ctypes.POINTER(P)],
         "sm_destroy_problem": [P],
@@ -131,6 +142,15 @@ def load():
                                ctypes.POINTER(StepStats)],
         "sm_step": [P, P, P, P, P, P, P, P, P, P, ctypes.POINTER(StepParams),
                     ctypes.POINTER(StepStats)],
+        "sm_create_batch": [ctypes.POINTER(ProblemDesc), I, P, ctypes.POINTER(P)],
+        "sm_destroy_batch": [P],
+        "sm_batch_problem": [P, I, ctypes.POINTER(P)],
+        "sm_batch_get_info": [P, ctypes.POINTER(BatchInfo)],
+        "sm_batch_set_stream": [P, P],
+        "sm_batch_set_tiling": [P, I, I],
+        "sm_batch_sweep": [P, PP, PP, PP, PP, PP, PP],
+        "sm_batch_synchronize": [P],
+        "sm_batch_autotune": [P, PP, PP, PP, PP, I],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -376,6 +396,115 @@ class Problem:
 
     def debug_skip_publish(self, on: bool):
         _check(load().sm_debug_skip_publish(self._h, 1 if on else 0))
+
+
+def _desc_of(cfg, precision: int, keep):
+    edges = np.ascontiguousarray(np.asarray(cfg.edges, dtype=np.float64))
+    keep.append(edges)
+    d = ProblemDesc()
+    d.dim, d.nx, d.ny = cfg.dim, cfg.nx, cfg.ny
+    d.x0, d.x1, d.y0, d.y1 = [float(v) for v in cfg.extent]
+    d.n_groups = len(edges) - 1
+    d.group_edges = edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.n_polar, d.n_azim = cfg.n_polar, cfg.n_azim
+    d.a, d.c, d.dt = cfg.a, cfg.c, cfg.dt
+    d.opacity_kind, d.opacity_alpha = cfg.opacity_kind, cfg.opacity_alpha
+    for i in range(4):
+        d.T_bdr[i] = float(cfg.T_bdr[i])
+    d.precision = precision
+    return d
+
+
+class _Member(Problem):
+    """Borrowed handle of a batch member (not destroyed on its own)."""
+
+    def __init__(self, handle, stream):
+        import torch
+        self._torch = torch
+        self._h = handle
+        self._stream = stream
+        self._edges = None
+        self.refresh_info()
+
+    def close(self):
+        self._h = None
+
+
+def _ptr_array(tensors):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = _ptr(t) if t is not None else None
+    return arr
+
+
+class Batch:
+    """Many independent 2D problems swept in one persistent launch
+    (``sm_batch_*``); each pass is recorded once as a CUDA graph per buffer
+    set and replayed afterwards."""
+
+    def __init__(self, cfgs, precision: int = 32, stream=None):
+        import torch
+        lib = load()
+        self._torch = torch
+        keep = []
+        descs = (ProblemDesc * len(cfgs))()
+        for i, cfg in enumerate(cfgs):
+            descs[i] = _desc_of(cfg, precision, keep)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        h = ctypes.c_void_p()
+        _check(lib.sm_create_batch(descs, len(cfgs), ctypes.c_void_p(stream.cuda_stream),
+                                   ctypes.byref(h)))
+        self._h = h
+        self.members = []
+        for i in range(len(cfgs)):
+            ph = ctypes.c_void_p()
+            _check(lib.sm_batch_problem(self._h, i, ctypes.byref(ph)))
+            self.members.append(_Member(ph, stream))
+
+    def info(self) -> dict:
+        bi = BatchInfo()
+        _check(load().sm_batch_get_info(self._h, ctypes.byref(bi)))
+        return {f: getattr(bi, f) for f, _ in BatchInfo._fields_}
+
+    def set_tiling(self, strip_width: int = 0, prefetch_rows: int = 0):
+        _check(load().sm_batch_set_tiling(self._h, strip_width, prefetch_rows))
+        for m in self.members:
+            m.refresh_info()
+
+    def sweep(self, T, sigma, I_prev, I_out, moments=None, closures=None):
+        """Lists of tensors, one per member (I_prev/moments/closures entries may be None)."""
+        n = len(self.members)
+        Ip = _ptr_array(I_prev if I_prev is not None else [None] * n)
+        mo = _ptr_array(moments) if moments is not None else None
+        cl = _ptr_array(closures) if closures is not None else None
+        self._keep = (_ptr_array(T), _ptr_array(sigma), Ip, _ptr_array(I_out), mo, cl)
+        _check(load().sm_batch_sweep(self._h, *self._keep))
+
+    def synchronize(self):
+        _check(load().sm_batch_synchronize(self._h))
+
+    def autotune(self, T, sigma, I_prev, I_out, reps: int = 2):
+        n = len(self.members)
+        Ip = _ptr_array(I_prev if I_prev is not None else [None] * n)
+        _check(load().sm_batch_autotune(self._h, _ptr_array(T), _ptr_array(sigma), Ip,
+                                        _ptr_array(I_out), reps))
+        for m in self.members:
+            m.refresh_info()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for m in self.members:
+                m.close()
+            load().sm_destroy_batch(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sweep_static(cfg, precision: int, T, sigma, I_prev, I_out, moments=None, closures=None,

@@ -97,7 +97,8 @@ sm_status dev_alloc(T **ptr, size_t bytes, size_t *acc) {
 void free_all(sm_problem *p) {
     void *bufs[] = {p->d_edges, p->d_inflow, p->d_lanes, p->d_dir_of, p->d_src,
                     p->d_mom_acc, p->d_gray, p->d_part, p->d_face, p->d_flags,
-                    p->d_ctrl, p->d_mom_tmp, p->d_T_tmp, p->d_sig_tmp, p->d_clo_tmp};
+                    p->ctrl_borrowed ? nullptr : p->d_ctrl, p->d_mom_tmp, p->d_T_tmp,
+                    p->d_sig_tmp, p->d_clo_tmp};
     for (void *b : bufs)
         if (b) cudaFree(b);
     smk::lo_free(p);
@@ -258,6 +259,10 @@ sm_status run_sweep(sm_problem *p, const double *T, const double *sigma, const v
 
 namespace smk {
 void set_last_error(const char *msg) { g_err = msg; }
+sm_status apply_tiling_ext(sm_problem *p, int W, int S) { return apply_tiling(p, W, S); }
+SweepArgs make_sweep_args(const sm_problem *p, const void *I_prev, void *I_out) {
+    return make_args(p, I_prev, I_out);
+}
 }  // namespace smk
 
 extern "C" {
@@ -493,6 +498,8 @@ sm_status sm_create_problem(const sm_problem_desc *d, void *stream, sm_problem *
 
 sm_status sm_destroy_problem(sm_problem *p) {
     if (!p) return SM_OK;
+    if (p->batch_owned)
+        return fail(SM_ERR_INVALID_ARG, "this problem belongs to a batch: destroy the batch");
     cudaStreamSynchronize(p->stream);
     free_all(p);
     delete p;
@@ -536,6 +543,8 @@ sm_status sm_set_stream(sm_problem *p, void *stream) {
 
 sm_status sm_set_tiling(sm_problem *p, int strip_width, int prefetch_rows) {
     if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    if (p->batch_owned)
+        return fail(SM_ERR_INVALID_ARG, "this problem belongs to a batch: sweep it with sm_batch_sweep");
     if (p->dim == 1) return SM_OK;
     SM_CUDA(cudaStreamSynchronize(p->stream));
     return apply_tiling(p, strip_width > 0 ? strip_width : p->W,
@@ -573,6 +582,8 @@ sm_status sm_emission(sm_problem *p, const double *T, const double *sigma, doubl
 sm_status sm_sweep(sm_problem *p, const double *T, const double *sigma, const void *I_prev,
                    void *I_out, double *mom, double *clo) {
     if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    if (p->batch_owned)
+        return fail(SM_ERR_INVALID_ARG, "this problem belongs to a batch: sweep it with sm_batch_sweep");
     sm_status st;
     if ((st = check_ptr(T, "T_nodal_dev")) || (st = check_ptr(sigma, "sigma_dev")) ||
         (st = check_ptr(I_out, "I_out_dev")))
@@ -597,6 +608,8 @@ sm_status sm_closures(sm_problem *p, const double *mom, const double *T, const d
 sm_status sm_sweep_host(sm_problem *p, const double *T_host, const double *sigma_host,
                         const void *I_prev, void *I_out, double *mom_host, double *clo_host) {
     if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    if (p->batch_owned)
+        return fail(SM_ERR_INVALID_ARG, "this problem belongs to a batch: sweep it with sm_batch_sweep");
     sm_status st;
     if ((st = check_ptr(T_host, "T_nodal_host")) || (st = check_ptr(sigma_host, "sigma_host")) ||
         (st = check_ptr(I_out, "I_out_dev")))
@@ -687,6 +700,8 @@ int64_t sm_launch_count(const sm_problem *p) { return p ? p->launches : 0; }
 sm_status sm_autotune(sm_problem *p, const double *T, const double *sigma, const void *I_prev,
                       void *I_out, int reps) {
     if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    if (p->batch_owned)
+        return fail(SM_ERR_INVALID_ARG, "this problem belongs to a batch: sweep it with sm_batch_sweep");
     sm_status st;
     if ((st = check_ptr(T, "T_nodal_dev")) || (st = check_ptr(sigma, "sigma_dev")) ||
         (st = check_ptr(I_out, "I_out_dev")))

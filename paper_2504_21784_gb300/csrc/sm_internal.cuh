@@ -53,6 +53,17 @@ struct SweepArgs {
     int fault_skip_publish;  // test hook: strip 0 never publishes
 };
 
+// Many problems in one persistent 2D sweep launch (sweep2d_batch_kernel).
+struct BatchSweepArgs {
+    const SweepArgs *args;  // [n_problems] (their ctrl is the batch's)
+    const int2 *tasks;      // [n_tasks] (problem, task of that problem)
+    int n_tasks;
+    int W, S, ring_gw;      // CTA width and stages; x-face ring sized for ring_gw slots
+    size_t stg;             // stage bytes: the largest of the batch
+    unsigned int *ctrl;
+    const unsigned long long *epoch;  // advanced by the batch prologue
+};
+
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_opacity(const sm_problem *p, const double *T, const double *scale,
                            double *sigma, cudaStream_t s);
@@ -69,12 +80,20 @@ cudaError_t launch_pack(const sm_problem *p, const double *canon, void *packed, 
                         cudaStream_t s);
 int sweep2d_max_resident(const sm_problem *p, int W, int S, size_t *smem_out);
 size_t sweep2d_smem_bytes(int prec, int W, int GW, int S, int GSLOT);
+size_t sweep2d_stage_bytes(int prec, int GW, int GSLOT);
+size_t sweep2d_batch_smem_bytes(int prec, int W, int S, size_t stg, int ring_gw);
+cudaError_t launch_sweep2d_batch(int prec, const BatchSweepArgs &b, int grid, size_t smem,
+                                 cudaStream_t s);
+int sweep2d_batch_max_resident(int prec, int W, size_t smem);
 void planck_upload_tables(void);
 // Set the thread-local message returned by sm_last_error() (no allocation
 // beyond the message string of at most 255 characters).
 void set_last_error(const char *msg);
 // Free the low-order workspace (no-op when the low-order solve never ran).
 void lo_free(sm_problem *p);
+// Tiling and sweep arguments of one problem (used by the batch object).
+sm_status apply_tiling_ext(sm_problem *p, int W, int S);
+SweepArgs make_sweep_args(const sm_problem *p, const void *I_prev, void *I_out);
 
 }  // namespace smk
 
@@ -124,5 +143,7 @@ struct sm_problem {
     int64_t launches = 0;
     size_t workspace_bytes = 0;
     sm_lo_state *lo = nullptr;
+    bool batch_owned = false;    // member of an sm_batch: swept only by the batch
+    bool ctrl_borrowed = false;  // d_ctrl belongs to the batch
 };
 

@@ -238,42 +238,61 @@ __device__ __forceinline__ double rcp_fast(double x) { return __drcp_rn(x); }
 __host__ __device__ inline size_t stage_bytes(int rsize, int GW, int GSLOT) {
     return (size_t)GW * 32 * 4 * rsize + (size_t)GSLOT * SREC * rsize;
 }
-// per warp: S stages, the x-face ring, the moment transpose buffer [8][MROW]
-// and the direction weights [6][MROW]
-__host__ __device__ inline size_t warp_smem_bytes(int rsize, int GW, int GSLOT, int S) {
-    return (size_t)S * stage_bytes(rsize, GW, GSLOT) + (size_t)RING * GW * 32 * 2 * rsize +
-           (size_t)(8 + 6) * MROW * rsize;
+// ---------------------------------------------------------------------------
+// Shared-memory layout of one 2D sweep CTA: W warps, each owning S stages of
+// stg bytes (prefetched I^k and source records), an x-face ring for ring_gw
+// slots and the moment buffers; after them W*S mbarriers and two row
+// counters per warp.
+struct Layout2D {
+    size_t stg, wsz, ring_off, mb_off;
+};
+
+__host__ __device__ inline Layout2D layout2d(int rsize, int S, size_t stg, int ring_gw) {
+    Layout2D L;
+    L.stg = stg;
+    L.ring_off = (size_t)S * stg;
+    L.mb_off = L.ring_off + (size_t)RING * ring_gw * 32 * 2 * rsize;
+    L.wsz = L.mb_off + (size_t)(8 + 6) * MROW * rsize;
+    return L;
+}
+
+__host__ __device__ inline size_t layout2d_total(const Layout2D &L, int W, int S) {
+    return (size_t)W * L.wsz + (size_t)W * S * 8 + 2 * W * sizeof(int) + 64;
 }
 
 size_t sweep2d_smem_bytes(int prec, int W, int GW, int S, int GSLOT) {
     const int rs = prec == 32 ? 4 : 8;
-    return (size_t)W * warp_smem_bytes(rs, GW, GSLOT, S) + (size_t)W * S * 8 + 2 * W * sizeof(int) +
-           64;
+    return layout2d_total(layout2d(rs, S, stage_bytes(rs, GW, GSLOT), GW), W, S);
 }
 
-// ---------------------------------------------------------------------------
-template <typename RT, int GW>
-__global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs A) {
+size_t sweep2d_batch_smem_bytes(int prec, int W, int S, size_t stg, int ring_gw) {
+    return layout2d_total(layout2d(prec == 32 ? 4 : 8, S, stg, ring_gw), W, S);
+}
+
+size_t sweep2d_stage_bytes(int prec, int GW, int GSLOT) {
+    return stage_bytes(prec == 32 ? 4 : 8, GW, GSLOT);
+}
+
+// One task of the 2D sweep: strip sr of warp task wg (quadrant, direction
+// block, group block) of the problem A, every warp of the CTA sweeping one
+// cell column of the strip from the upwind to the downwind edge.
+template <typename RT, int GW, class Args>
+__device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay, const int task,
+                                             unsigned char *smem_raw, uint64_t *bars,
+                                             volatile int *rows_done, volatile int *cons,
+                                             volatile int *s_abort, uint32_t &phase,
+                                             const unsigned long long epoch) {
     using R2 = typename V2<RT>::t;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ int s_task;
-    __shared__ volatile int s_abort;
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int W = A.W, S = A.S;
     const int nx = A.nx, ny = A.ny;
     const int GSLOT = GW * A.LG;
-    const size_t stg = stage_bytes((int)sizeof(RT), GW, GSLOT);
-    const size_t wsz = warp_smem_bytes((int)sizeof(RT), GW, GSLOT, S);
-    const size_t ring_off = (size_t)S * stg;
-    const size_t mb_off = ring_off + (size_t)RING * GW * 32 * sizeof(R2);
+    const size_t stg = Lay.stg, wsz = Lay.wsz, ring_off = Lay.ring_off;
     unsigned char *wbase = smem_raw + (size_t)w * wsz;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)W * wsz);
-    volatile int *rows_done = reinterpret_cast<volatile int *>(bars + (size_t)W * S);
-    volatile int *cons = rows_done + W;
     uint64_t *mybars = bars + (size_t)w * S;
-    RT *Mb = reinterpret_cast<RT *>(wbase + mb_off);  // [8][MROW]: s_n, ss_n per lane
-    RT *Wt = Mb + 8 * MROW;                           // [6][MROW]: weights per lane
+    RT *Mb = reinterpret_cast<RT *>(wbase + Lay.mb_off);  // [8][MROW]: s_n, ss_n per lane
+    RT *Wt = Mb + 8 * MROW;                               // [6][MROW]: weights per lane
     const RT *src = static_cast<const RT *>(A.src);
     const RT *inflow = static_cast<const RT *>(A.inflow);
     const RT *Ip = static_cast<const RT *>(A.I_prev);
@@ -289,12 +308,259 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs A) {
     const int vrow1 = k1 < 6 ? n1 : 4 + n1, wrow1 = k1 < 6 ? k1 : k1 - 6;
     const int m2 = 32 + (lane & 3), k2 = m2 % 9;
     const int vrow2 = k2 < 6 ? 3 : 7, wrow2 = k2 < 6 ? k2 : k2 - 6;
+    const int NWG = A.NQ * A.NWT;
+    const int sr = task / NWG, wg = task - sr * NWG;
+    const int q = wg / A.NWT, wt = wg - q * A.NWT;
+    const int sx = (q == 0 || q == 3) ? 1 : -1;
+    const int sy = (q < 2) ? 1 : -1;
+    const int strip = sx > 0 ? sr : A.NS - 1 - sr;
+    const int x0 = strip * W;
+    const int ws = min(W, nx - x0);
+    if (w >= ws) return;  // idle column of a ragged strip
+    const int xw = sx > 0 ? x0 + w : x0 + ws - 1 - w;
+    const int db = wt / A.NGB, gb = wt - db * A.NGB;
+    const LaneConst &L = A.lanes[(q * A.DB + db) * 32 + lane];
+    const RT mu = (RT)L.mu, eta = (RT)L.eta;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Wt[k * MROW + lane] = (RT)L.wm[k];
+    const int g_lo = L.g_lo;
+    const int side_x = sx > 0 ? 0 : 1, side_y = sy > 0 ? 2 : 3;
+    RT X0[GW], X1[GW], Y0[GW], Y1[GW];  // x-inflow (rows u,d), y-inflow (columns u,d)
+    RT bx[GW];                          // boundary x-inflow (first column of strip 0)
+#pragma unroll
+    for (int gw = 0; gw < GW; ++gw) {
+        const int g = gb * GSLOT + gw * A.LG + g_lo;
+        const RT by = inflow[side_y * A.Gp + g];
+        Y0[gw] = by;
+        Y1[gw] = by;
+        bx[gw] = inflow[side_x * A.Gp + g];
+    }
+    const int au = sx > 0 ? 0 : 1, bu = sy > 0 ? 0 : 1;
+    const int nuu = au + 2 * bu, ndu = (1 - au) + 2 * bu;
+    const int nud = au + 2 * (1 - bu), ndd = (1 - au) + 2 * (1 - bu);
+    const size_t wtbase = (size_t)wg * A.ncell;
+    const bool global_in = (w == 0) && sr > 0;
+    const bool global_out = (w == ws - 1) && sr < A.NS - 1;
+    const size_t fidx_out = ((size_t)wg * A.NS + strip) * ny;
+    const size_t fidx_in = ((size_t)wg * A.NS + (sr > 0 ? strip - sx : strip)) * ny;
+    unsigned long long *myflag = A.flags + (size_t)wg * A.NS + strip;
+    const unsigned long long *upflag =
+        A.flags + (size_t)wg * A.NS + (sr > 0 ? strip - sx : strip);
+    const unsigned long long ep = epoch << 32;
+    unsigned long long seen = 0;
+    const R2 *ring_in =
+        w > 0 ? reinterpret_cast<const R2 *>(smem_raw + (size_t)(w - 1) * wsz + ring_off)
+              : nullptr;
+    R2 *ring_out = reinterpret_cast<R2 *>(wbase + ring_off);
+    __syncwarp();  // weights visible to the whole warp
 
+    auto row_y = [&](int jj) { return sy > 0 ? jj : ny - 1 - jj; };
+    auto issue = [&](int jj) {  // lane 0: TMA for row jj into stage jj % S
+        const int st = jj % S;
+        unsigned char *dst = wbase + (size_t)st * stg;
+        const int cell = row_y(jj) * nx + xw;
+        mbar_arrive_expect_tx(mybars + st, bytes_I + bytes_S);
+        if (Ip) bulk_g2s(dst, Ip + ((wtbase + cell) * GW) * 32 * 4, bytes_I, mybars + st);
+        bulk_g2s(dst + bytes_I, src + ((size_t)cell * A.Gp + (size_t)gb * GSLOT) * SREC,
+                 bytes_S, mybars + st);
+    };
+    int issued = -1;    // highest row whose copy was issued
+    int consumed = 0;   // rows whose stage has been waited for
+    if (lane == 0) {
+        fence_proxy_async_smem();
+        for (int jj = 0; jj < min(S, ny); ++jj) issue(jj);
+    }
+    issued = min(S, ny) - 1;
+    bool ok = true;
+    int jj = 0;
+    for (; jj < ny && ok; ++jj) {
+        const int y = row_y(jj);
+        const int st = jj % S;
+        const int slot = jj % RING;
+        // (a) x-inflow
+        if (w == 0 && sr == 0) {
+#pragma unroll
+            for (int gw = 0; gw < GW; ++gw) {
+                X0[gw] = bx[gw];
+                X1[gw] = bx[gw];
+            }
+        } else if (global_in) {
+            ok = flag_wait_geq(upflag, ep | (unsigned long long)(jj + 1), seen, A.ctrl,
+                               A.timeout_ns, s_abort);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+#pragma unroll
+            for (int gw = 0; gw < GW; ++gw) {
+                const R2 f = __ldcg(face + ((fidx_in + y) * GW + gw) * 32 + lane);
+                X0[gw] = f.x;
+                X1[gw] = f.y;
+            }
+        } else {
+            ok = smem_wait_geq(rows_done + (w - 1), jj + 1, A.ctrl, A.timeout_ns, s_abort);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            __threadfence_block();
+#pragma unroll
+            for (int gw = 0; gw < GW; ++gw) {
+                const R2 f = ring_in[(slot * GW + gw) * 32 + lane];
+                X0[gw] = f.x;
+                X1[gw] = f.y;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                cons[w - 1] = jj + 1;  // ring slot of the upwind column is free again
+            }
+        }
+        // (b) this row's prefetched I^k and sources
+        ok = mbar_wait(mybars + st, (phase >> st) & 1u, A.ctrl, A.timeout_ns, s_abort);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        phase ^= 1u << st;
+        consumed = jj + 1;
+        const RT *sbI = reinterpret_cast<const RT *>(wbase + (size_t)st * stg) + lane * 4;
+        const RT *sbS = reinterpret_cast<const RT *>(wbase + (size_t)st * stg + bytes_I) +
+                        (size_t)g_lo * SREC;
+        // (c) cell solves, reading the stage slot by slot
+        RT s4[4] = {0, 0, 0, 0}, ss4[4] = {0, 0, 0, 0};
+        const int cell = y * nx + xw;
+        RT *io = Io + (((wtbase + cell) * GW) * 32 + lane) * 4;
+#pragma unroll
+        for (int gw = 0; gw < GW; ++gw) {
+            RT Sn[4], Ik[4];
+            lds4(sbS + (size_t)gw * A.LG * SREC, Sn);
+            const RT sgt = sbS[(size_t)gw * A.LG * SREC + 4];
+            const RT sgm = sbS[(size_t)gw * A.LG * SREC + 5];
+            if (Ip) {
+                lds4(sbI + (size_t)gw * 128, Ik);
+#pragma unroll
+                for (int n = 0; n < 4; ++n) Sn[n] = fma(inv_cdt, Ik[n], Sn[n]);
+            }
+            const RT iA = rcp_fast(sgt + mu + eta);
+            const RT m = mu * iA, e = eta * iA;
+            const RT ruu = (Sn[nuu] + two * (mu * X0[gw] + eta * Y0[gw])) * iA;
+            const RT rdu = fma(two * eta, Y1[gw], Sn[ndu]) * iA;
+            const RT rud = fma(two * mu, X1[gw], Sn[nud]) * iA;
+            const RT rdd = Sn[ndd] * iA;
+            const RT P = fma(m, m, fma(e, e, (RT)1));
+            const RT z = two * m * e;
+            const RT iD = rcp_fast(fma(P, P, -z * z));
+            const RT wuu = fma(P, ruu, z * rdd);
+            const RT wdu = fma(P, rdu, -z * rud);
+            const RT wud = fma(P, rud, -z * rdu);
+            const RT wdd = fma(P, rdd, z * ruu);
+            RT I4[4];
+            I4[nuu] = (wuu - m * wdu - e * wud) * iD;
+            I4[ndu] = (wdu + m * wuu - e * wdd) * iD;
+            I4[nud] = (wud - m * wdd + e * wuu) * iD;
+            I4[ndd] = (wdd + m * wud + e * wdu) * iD;
+            st4_stream(io + (size_t)gw * 128, I4);
+            X0[gw] = I4[ndu];  // x-outflow -> next column
+            X1[gw] = I4[ndd];
+            Y0[gw] = I4[nud];  // y-outflow -> next row
+            Y1[gw] = I4[ndd];
+#pragma unroll
+            for (int n = 0; n < 4; ++n) {
+                s4[n] += I4[n];
+                ss4[n] = fma(sgm, I4[n], ss4[n]);
+            }
+        }
+        // the stage is free: prefetch row jj + S into it
+        __syncwarp();
+        if (lane == 0 && jj + S < ny) {
+            fence_proxy_async_smem();
+            issue(jj + S);
+        }
+        if (jj + S < ny) issued = jj + S;
+        // (d) hand the x-outflow downwind
+        if (w < ws - 1) {
+            ok = smem_wait_geq(cons + w, jj + 1 - RING, A.ctrl, A.timeout_ns, s_abort);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+#pragma unroll
+            for (int gw = 0; gw < GW; ++gw) {
+                R2 f;
+                f.x = X0[gw];
+                f.y = X1[gw];
+                ring_out[(slot * GW + gw) * 32 + lane] = f;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                rows_done[w] = jj + 1;
+            }
+        } else if (global_out) {
+#pragma unroll
+            for (int gw = 0; gw < GW; ++gw) {
+                R2 f;
+                f.x = X0[gw];
+                f.y = X1[gw];
+                __stcg(face + ((fidx_out + y) * GW + gw) * 32 + lane, f);
+            }
+            __syncwarp();
+            // release the rows to the downwind strip in batches of PUBLISH_ROWS:
+            // the gpu-scope fence is paid once per batch
+            if (lane == 0 && !(A.fault_skip_publish && sr == 0) &&
+                ((jj + 1) % PUBLISH_ROWS == 0 || jj + 1 == ny)) {
+                __threadfence();
+                st_release(myflag, ep | (unsigned long long)(jj + 1));
+            }
+        }
+        // (e) moments of this cell: transpose through shared memory, then
+        // lane m forms moment m = n*9 + k as a dot product over the 32 lanes
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            Mb[n * MROW + lane] = s4[n];
+            Mb[(4 + n) * MROW + lane] = ss4[n];
+        }
+        __syncwarp();
+        RT d1 = 0, d2 = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            RT a[4], b[4], c[4], e4[4];
+            lds4(Mb + vrow1 * MROW + 4 * i, a);
+            lds4(Wt + wrow1 * MROW + 4 * i, b);
+            lds4(Mb + vrow2 * MROW + 4 * i, c);
+            lds4(Wt + wrow2 * MROW + 4 * i, e4);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                d1 = fma(a[t], b[t], d1);
+                d2 = fma(c[t], e4[t], d2);
+            }
+        }
+        RT *ac = acc + (size_t)cell * 36;
+        atomicAdd(ac + m1, d1);
+        if (lane < 4) atomicAdd(ac + m2, d2);
+        __syncwarp();  // Mb is rewritten by the next row
+    }
+    if (!ok) {
+        // wait (bounded) for this warp's copies still in flight, then leave
+        const long long t0 = global_ns();
+        for (int r = consumed; r <= issued; ++r) {
+            const int st = r % S;
+            while (!mbar_try_wait(mybars + st, (phase >> st) & 1u)) {
+                if (global_ns() - t0 > A.timeout_ns) break;
+            }
+            phase ^= 1u << st;
+        }
+        *s_abort = 1;
+    }
+}
+
+template <typename RT, int GW>
+__global__ void __launch_bounds__(512) sweep2d_kernel(const __grid_constant__ SweepArgs A) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ int s_task;
+    __shared__ volatile int s_abort;
+    const int W = A.W, S = A.S;
+    const Layout2D Lay = layout2d((int)sizeof(RT), S, stage_bytes((int)sizeof(RT), GW, GW * A.LG), GW);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)W * Lay.wsz);
+    volatile int *rows_done = reinterpret_cast<volatile int *>(bars + (size_t)W * S);
+    volatile int *cons = rows_done + W;
     if (threadIdx.x < W * S) mbar_init(bars + threadIdx.x, 1);
     if (threadIdx.x == 0) s_abort = 0;
     fence_mbar_init();
     uint32_t phase = 0;  // parity bit per stage of this warp
-
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_task = (int)atomicAdd(A.ctrl + CTRL_QUEUE, 1u);
@@ -305,242 +571,72 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const SweepArgs A) {
         __syncthreads();
         const int task = s_task;
         if (task >= A.n_tasks || s_abort) return;
-        const int NWG = A.NQ * A.NWT;
-        const int sr = task / NWG, wg = task - sr * NWG;
-        const int q = wg / A.NWT, wt = wg - q * A.NWT;
-        const int sx = (q == 0 || q == 3) ? 1 : -1;
-        const int sy = (q < 2) ? 1 : -1;
-        const int strip = sx > 0 ? sr : A.NS - 1 - sr;
-        const int x0 = strip * W;
-        const int ws = min(W, nx - x0);
-        if (w >= ws) continue;  // idle column of a ragged strip
-        const int xw = sx > 0 ? x0 + w : x0 + ws - 1 - w;
-        const int db = wt / A.NGB, gb = wt - db * A.NGB;
-        const LaneConst &L = A.lanes[(q * A.DB + db) * 32 + lane];
-        const RT mu = (RT)L.mu, eta = (RT)L.eta;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) Wt[k * MROW + lane] = (RT)L.wm[k];
-        const int g_lo = L.g_lo;
-        const int side_x = sx > 0 ? 0 : 1, side_y = sy > 0 ? 2 : 3;
-        RT X0[GW], X1[GW], Y0[GW], Y1[GW];  // x-inflow (rows u,d), y-inflow (columns u,d)
-        RT bx[GW];                          // boundary x-inflow (first column of strip 0)
-#pragma unroll
-        for (int gw = 0; gw < GW; ++gw) {
-            const int g = gb * GSLOT + gw * A.LG + g_lo;
-            const RT by = inflow[side_y * A.Gp + g];
-            Y0[gw] = by;
-            Y1[gw] = by;
-            bx[gw] = inflow[side_x * A.Gp + g];
-        }
-        const int au = sx > 0 ? 0 : 1, bu = sy > 0 ? 0 : 1;
-        const int nuu = au + 2 * bu, ndu = (1 - au) + 2 * bu;
-        const int nud = au + 2 * (1 - bu), ndd = (1 - au) + 2 * (1 - bu);
-        const size_t wtbase = (size_t)wg * A.ncell;
-        const bool global_in = (w == 0) && sr > 0;
-        const bool global_out = (w == ws - 1) && sr < A.NS - 1;
-        const size_t fidx_out = ((size_t)wg * A.NS + strip) * ny;
-        const size_t fidx_in = ((size_t)wg * A.NS + (sr > 0 ? strip - sx : strip)) * ny;
-        unsigned long long *myflag = A.flags + (size_t)wg * A.NS + strip;
-        const unsigned long long *upflag =
-            A.flags + (size_t)wg * A.NS + (sr > 0 ? strip - sx : strip);
-        const unsigned long long ep = A.epoch << 32;
-        unsigned long long seen = 0;
-        const R2 *ring_in =
-            w > 0 ? reinterpret_cast<const R2 *>(smem_raw + (size_t)(w - 1) * wsz + ring_off)
-                  : nullptr;
-        R2 *ring_out = reinterpret_cast<R2 *>(wbase + ring_off);
-        __syncwarp();  // weights visible to the whole warp
+        sweep2d_task<RT, GW>(A, Lay, task, smem_raw, bars, rows_done, cons, &s_abort, phase,
+                             A.epoch);
+    }
+}
 
-        auto row_y = [&](int jj) { return sy > 0 ? jj : ny - 1 - jj; };
-        auto issue = [&](int jj) {  // lane 0: TMA for row jj into stage jj % S
-            const int st = jj % S;
-            unsigned char *dst = wbase + (size_t)st * stg;
-            const int cell = row_y(jj) * nx + xw;
-            mbar_arrive_expect_tx(mybars + st, bytes_I + bytes_S);
-            if (Ip) bulk_g2s(dst, Ip + ((wtbase + cell) * GW) * 32 * 4, bytes_I, mybars + st);
-            bulk_g2s(dst + bytes_I, src + ((size_t)cell * A.Gp + (size_t)gb * GSLOT) * SREC,
-                     bytes_S, mybars + st);
-        };
-        int issued = -1;    // highest row whose copy was issued
-        int consumed = 0;   // rows whose stage has been waited for
-        if (lane == 0) {
-            fence_proxy_async_smem();
-            for (int jj = 0; jj < min(S, ny); ++jj) issue(jj);
+// Many problems in one persistent launch: the tasks of all problems are taken
+// from one queue, in an order that keeps each problem's own upwind task order
+// (a task waits only on earlier tasks of its problem, which are claimed by
+// running CTAs, so the launch cannot deadlock for any grid size).  Each task's
+// problem arguments are copied to shared memory and the task body is chosen
+// by the problem's slots per lane (GW); the shared-memory layout is sized for
+// the largest stage and ring of the batch.
+
+template <typename RT>
+__global__ void __launch_bounds__(512) sweep2d_batch_kernel(const __grid_constant__ BatchSweepArgs B) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ int2 s_task;
+    __shared__ volatile int s_abort;
+    __shared__ __align__(16) SweepArgs s_args;
+    const int W = B.W, S = B.S;
+    const Layout2D Lay = layout2d((int)sizeof(RT), S, B.stg, B.ring_gw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)W * Lay.wsz);
+    volatile int *rows_done = reinterpret_cast<volatile int *>(bars + (size_t)W * S);
+    volatile int *cons = rows_done + W;
+    if (threadIdx.x < W * S) mbar_init(bars + threadIdx.x, 1);
+    if (threadIdx.x == 0) s_abort = 0;
+    fence_mbar_init();
+    const unsigned long long epoch = *B.epoch;
+    uint32_t phase = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int t = (int)atomicAdd(B.ctrl + CTRL_QUEUE, 1u);
+            s_task = t < B.n_tasks ? B.tasks[t] : make_int2(-1, -1);
         }
-        issued = min(S, ny) - 1;
-        bool ok = true;
-        int jj = 0;
-        for (; jj < ny && ok; ++jj) {
-            const int y = row_y(jj);
-            const int st = jj % S;
-            const int slot = jj % RING;
-            // (a) x-inflow
-            if (w == 0 && sr == 0) {
-#pragma unroll
-                for (int gw = 0; gw < GW; ++gw) {
-                    X0[gw] = bx[gw];
-                    X1[gw] = bx[gw];
-                }
-            } else if (global_in) {
-                ok = flag_wait_geq(upflag, ep | (unsigned long long)(jj + 1), seen, A.ctrl,
-                                   A.timeout_ns, &s_abort);
-                ok = __all_sync(0xffffffffu, ok);
-                if (!ok) break;
-#pragma unroll
-                for (int gw = 0; gw < GW; ++gw) {
-                    const R2 f = __ldcg(face + ((fidx_in + y) * GW + gw) * 32 + lane);
-                    X0[gw] = f.x;
-                    X1[gw] = f.y;
-                }
-            } else {
-                ok = smem_wait_geq(rows_done + (w - 1), jj + 1, A.ctrl, A.timeout_ns, &s_abort);
-                ok = __all_sync(0xffffffffu, ok);
-                if (!ok) break;
-                __threadfence_block();
-#pragma unroll
-                for (int gw = 0; gw < GW; ++gw) {
-                    const R2 f = ring_in[(slot * GW + gw) * 32 + lane];
-                    X0[gw] = f.x;
-                    X1[gw] = f.y;
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    __threadfence_block();
-                    cons[w - 1] = jj + 1;  // ring slot of the upwind column is free again
-                }
-            }
-            // (b) this row's prefetched I^k and sources
-            ok = mbar_wait(mybars + st, (phase >> st) & 1u, A.ctrl, A.timeout_ns, &s_abort);
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) break;
-            phase ^= 1u << st;
-            consumed = jj + 1;
-            const RT *sbI = reinterpret_cast<const RT *>(wbase + (size_t)st * stg) + lane * 4;
-            const RT *sbS = reinterpret_cast<const RT *>(wbase + (size_t)st * stg + bytes_I) +
-                            (size_t)g_lo * SREC;
-            // (c) cell solves, reading the stage slot by slot
-            RT s4[4] = {0, 0, 0, 0}, ss4[4] = {0, 0, 0, 0};
-            const int cell = y * nx + xw;
-            RT *io = Io + (((wtbase + cell) * GW) * 32 + lane) * 4;
-#pragma unroll
-            for (int gw = 0; gw < GW; ++gw) {
-                RT Sn[4], Ik[4];
-                lds4(sbS + (size_t)gw * A.LG * SREC, Sn);
-                const RT sgt = sbS[(size_t)gw * A.LG * SREC + 4];
-                const RT sgm = sbS[(size_t)gw * A.LG * SREC + 5];
-                if (Ip) {
-                    lds4(sbI + (size_t)gw * 128, Ik);
-#pragma unroll
-                    for (int n = 0; n < 4; ++n) Sn[n] = fma(inv_cdt, Ik[n], Sn[n]);
-                }
-                const RT iA = rcp_fast(sgt + mu + eta);
-                const RT m = mu * iA, e = eta * iA;
-                const RT ruu = (Sn[nuu] + two * (mu * X0[gw] + eta * Y0[gw])) * iA;
-                const RT rdu = fma(two * eta, Y1[gw], Sn[ndu]) * iA;
-                const RT rud = fma(two * mu, X1[gw], Sn[nud]) * iA;
-                const RT rdd = Sn[ndd] * iA;
-                const RT P = fma(m, m, fma(e, e, (RT)1));
-                const RT z = two * m * e;
-                const RT iD = rcp_fast(fma(P, P, -z * z));
-                const RT wuu = fma(P, ruu, z * rdd);
-                const RT wdu = fma(P, rdu, -z * rud);
-                const RT wud = fma(P, rud, -z * rdu);
-                const RT wdd = fma(P, rdd, z * ruu);
-                RT I4[4];
-                I4[nuu] = (wuu - m * wdu - e * wud) * iD;
-                I4[ndu] = (wdu + m * wuu - e * wdd) * iD;
-                I4[nud] = (wud - m * wdd + e * wuu) * iD;
-                I4[ndd] = (wdd + m * wud + e * wdu) * iD;
-                st4_stream(io + (size_t)gw * 128, I4);
-                X0[gw] = I4[ndu];  // x-outflow -> next column
-                X1[gw] = I4[ndd];
-                Y0[gw] = I4[nud];  // y-outflow -> next row
-                Y1[gw] = I4[ndd];
-#pragma unroll
-                for (int n = 0; n < 4; ++n) {
-                    s4[n] += I4[n];
-                    ss4[n] = fma(sgm, I4[n], ss4[n]);
-                }
-            }
-            // the stage is free: prefetch row jj + S into it
-            __syncwarp();
-            if (lane == 0 && jj + S < ny) {
-                fence_proxy_async_smem();
-                issue(jj + S);
-            }
-            if (jj + S < ny) issued = jj + S;
-            // (d) hand the x-outflow downwind
-            if (w < ws - 1) {
-                ok = smem_wait_geq(cons + w, jj + 1 - RING, A.ctrl, A.timeout_ns, &s_abort);
-                ok = __all_sync(0xffffffffu, ok);
-                if (!ok) break;
-#pragma unroll
-                for (int gw = 0; gw < GW; ++gw) {
-                    R2 f;
-                    f.x = X0[gw];
-                    f.y = X1[gw];
-                    ring_out[(slot * GW + gw) * 32 + lane] = f;
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    __threadfence_block();
-                    rows_done[w] = jj + 1;
-                }
-            } else if (global_out) {
-#pragma unroll
-                for (int gw = 0; gw < GW; ++gw) {
-                    R2 f;
-                    f.x = X0[gw];
-                    f.y = X1[gw];
-                    __stcg(face + ((fidx_out + y) * GW + gw) * 32 + lane, f);
-                }
-                __syncwarp();
-                // release the rows to the downwind strip in batches of PUBLISH_ROWS:
-                // the gpu-scope fence is paid once per batch
-                if (lane == 0 && !(A.fault_skip_publish && sr == 0) &&
-                    ((jj + 1) % PUBLISH_ROWS == 0 || jj + 1 == ny)) {
-                    __threadfence();
-                    st_release(myflag, ep | (unsigned long long)(jj + 1));
-                }
-            }
-            // (e) moments of this cell: transpose through shared memory, then
-            // lane m forms moment m = n*9 + k as a dot product over the 32 lanes
-#pragma unroll
-            for (int n = 0; n < 4; ++n) {
-                Mb[n * MROW + lane] = s4[n];
-                Mb[(4 + n) * MROW + lane] = ss4[n];
-            }
-            __syncwarp();
-            RT d1 = 0, d2 = 0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                RT a[4], b[4], c[4], e4[4];
-                lds4(Mb + vrow1 * MROW + 4 * i, a);
-                lds4(Wt + wrow1 * MROW + 4 * i, b);
-                lds4(Mb + vrow2 * MROW + 4 * i, c);
-                lds4(Wt + wrow2 * MROW + 4 * i, e4);
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    d1 = fma(a[t], b[t], d1);
-                    d2 = fma(c[t], e4[t], d2);
-                }
-            }
-            RT *ac = acc + (size_t)cell * 36;
-            atomicAdd(ac + m1, d1);
-            if (lane < 4) atomicAdd(ac + m2, d2);
-            __syncwarp();  // Mb is rewritten by the next row
+        if (threadIdx.x < W) {
+            rows_done[threadIdx.x] = 0;
+            cons[threadIdx.x] = 0;
         }
-        if (!ok) {
-            // wait (bounded) for this warp's copies still in flight, then leave
-            const long long t0 = global_ns();
-            for (int r = consumed; r <= issued; ++r) {
-                const int st = r % S;
-                while (!mbar_try_wait(mybars + st, (phase >> st) & 1u)) {
-                    if (global_ns() - t0 > A.timeout_ns) break;
-                }
-                phase ^= 1u << st;
-            }
-            s_abort = 1;
+        __syncthreads();
+        const int2 pt = s_task;
+        if (pt.x < 0 || s_abort) return;
+        {
+            const int *from = reinterpret_cast<const int *>(B.args + pt.x);
+            int *to = reinterpret_cast<int *>(&s_args);
+            for (int i = threadIdx.x; i < (int)(sizeof(SweepArgs) / sizeof(int)); i += blockDim.x)
+                to[i] = from[i];
+        }
+        __syncthreads();
+        switch (s_args.GW) {
+            case 1:
+                sweep2d_task<RT, 1>(s_args, Lay, pt.y, smem_raw, bars, rows_done, cons, &s_abort,
+                                    phase, epoch);
+                break;
+            case 2:
+                sweep2d_task<RT, 2>(s_args, Lay, pt.y, smem_raw, bars, rows_done, cons, &s_abort,
+                                    phase, epoch);
+                break;
+            case 4:
+                sweep2d_task<RT, 4>(s_args, Lay, pt.y, smem_raw, bars, rows_done, cons, &s_abort,
+                                    phase, epoch);
+                break;
+            default:
+                sweep2d_task<RT, 8>(s_args, Lay, pt.y, smem_raw, bars, rows_done, cons, &s_abort,
+                                    phase, epoch);
+                break;
         }
     }
 }
@@ -659,6 +755,32 @@ int sweep2d_max_resident(const sm_problem *p, int W, int S, size_t *smem_out) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (smem + 64 > (size_t)maxopt) return 0;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, W * 32, smem) != cudaSuccess)
+        return 0;
+    return per_sm * nsm;
+}
+
+cudaError_t launch_sweep2d_batch(int prec, const BatchSweepArgs &b, int grid, size_t smem,
+                                 cudaStream_t s) {
+    const void *k = prec == 32 ? (const void *)sweep2d_batch_kernel<float>
+                               : (const void *)sweep2d_batch_kernel<double>;
+    BatchSweepArgs args = b;
+    void *params[] = {&args};
+    return cudaLaunchKernel(k, dim3(grid), dim3(b.W * 32), params, smem, s);
+}
+
+int sweep2d_batch_max_resident(int prec, int W, size_t smem) {
+    const void *k = prec == 32 ? (const void *)sweep2d_batch_kernel<float>
+                               : (const void *)sweep2d_batch_kernel<double>;
+    int dev = 0, nsm = 0, maxopt = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem + 64 + sizeof(SweepArgs) > (size_t)maxopt) return 0;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return 0;

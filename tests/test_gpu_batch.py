@@ -1,0 +1,176 @@
+"""Batched problems in one persistent launch (sm_batch_*): every member's
+result equals a single-problem sweep of the same problem (bit-identical
+intensity; moments and closures up to the order of their atomic sums), the
+FP64 batch matches the oracle per member, graphs are recorded once per buffer
+set, and members refuse single-problem sweeps."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2504_21784_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _cfg(i, n, ny, G, npol, naz, T_bdr=(1.0, 0.0, 0.0, 0.0)):
+    return W.Config(f"m{i}", 2, n, ny, (0.0, 1.0, 0.0, 1.0), W.log_edges(G), npol, naz,
+                    W.OPACITY_LARSEN, 10.0, T_bdr, seed=i)
+
+
+MEMBERS = [  # uneven meshes, 32/64/128 directions, group counts giving GW = 2, 4, 8 and padding
+    _cfg(0, 13, 9, 5, 2, 4),
+    _cfg(1, 24, 31, 12, 4, 4),
+    _cfg(2, 17, 17, 9, 4, 8, T_bdr=(1.0, 0.3, 0.5, 0.0)),
+    _cfg(3, 40, 7, 3, 2, 4),
+    _cfg(4, 8, 21, 20, 4, 8),
+    _cfg(5, 1, 1, 2, 2, 4),
+]
+
+
+def _inputs(sm, prob, cfg, seed):
+    import torch
+    T = torch.from_numpy(W.temperature_wave(cfg, seed=seed)).cuda()
+    scale = torch.from_numpy(W.blocky_two_material(cfg.nx, cfg.ny, seed=100 + seed, block=4,
+                                                   thick=50.0)).cuda()
+    sigma = prob.opacity(T, scale)
+    Ic = W.intensity_random(cfg.n_dir, cfg.n_groups, cfg.n_cells, 4, seed=seed + 3, scale=0.05)
+    Ip = prob.pack(torch.from_numpy(Ic).cuda())
+    return T, sigma, Ip
+
+
+def _run_batch(sm, cfgs, precision, tiling=None):
+    b = sm.Batch(cfgs, precision)
+    if tiling:
+        b.set_tiling(*tiling)
+    T, S, Ip, Io, M, C = [], [], [], [], [], []
+    for i, (cfg, m) in enumerate(zip(cfgs, b.members)):
+        t, s, ip = _inputs(sm, m, cfg, seed=i)
+        T.append(t)
+        S.append(s)
+        Ip.append(ip)
+        Io.append(m.empty_intensity())
+        M.append(m.new_moments())
+        C.append(m.new_closures())
+    b.sweep(T, S, Ip, Io, M, C)
+    b.synchronize()
+    return b, T, S, Ip, Io, M, C
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_batch_equals_single_sweeps(gpu_lib, precision):
+    sm = gpu_lib
+    b, T, S, Ip, Io, M, C = _run_batch(sm, MEMBERS, precision, tiling=(4, 3))
+    tol = 1e-6 if precision == 32 else 1e-13
+    for i, cfg in enumerate(MEMBERS):
+        p = sm.Problem.from_config(cfg, precision, strip_width=4, prefetch_rows=3)
+        assert p.info["groups_per_warp"] == b.members[i].info["groups_per_warp"]
+        Io1 = p.empty_intensity()
+        m1, c1 = p.new_moments(), p.new_closures()
+        p.sweep(T[i], S[i], Ip[i], Io1, m1, c1)
+        p.synchronize()
+        Ib = b.members[i].unpack(Io[i]).cpu().numpy()
+        Is = p.unpack(Io1).cpu().numpy()
+        assert np.array_equal(Ib, Is), f"member {i}: intensity differs"
+        assert _rel(M[i].cpu().numpy()[..., 0], m1.cpu().numpy()[..., 0]) < tol
+        assert _rel(C[i].cpu().numpy()[..., 6], c1.cpu().numpy()[..., 6]) < tol
+
+
+def test_batch_fp64_matches_oracle(gpu_lib):
+    sm = gpu_lib
+    cfgs = MEMBERS[:4]
+    b, T, S, Ip, Io, M, C = _run_batch(sm, cfgs, 64)
+    for i, cfg in enumerate(cfgs):
+        Tn, Sn = T[i].cpu().numpy(), S[i].cpu().numpy()
+        Ipc = b.members[i].unpack(Ip[i]).cpu().numpy()
+        omx, omy, w = O.quadrature(2, cfg.n_polar, cfg.n_azim)
+        q = O.emission(cfg.edges, cfg.a, cfg.c, Tn, Sn)
+        infl = O.inflow(cfg.edges, cfg.a, cfg.c, cfg.T_bdr)
+        Ir = O.sweep(2, cfg.nx, cfg.ny, cfg.extent, omx, omy, Sn, 1.0 / (cfg.c * cfg.dt), q, Ipc,
+                     infl)
+        momr = O.moments(2, omx, omy, w, Sn, Ir)
+        Ig = b.members[i].unpack(Io[i]).cpu().numpy()
+        eI = max(_rel(Ig[d, g], Ir[d, g]) for d in range(cfg.n_dir) for g in range(cfg.n_groups))
+        ephi = _rel(M[i].cpu().numpy()[..., 0], momr[..., 0])
+        print(f"member {i}: I {eI:.2e} phi {ephi:.2e}")
+        assert eI < 1e-11 and ephi < 1e-11
+
+
+def test_batch_graphs_recorded_once_per_buffer_set(gpu_lib):
+    sm = gpu_lib
+    b, T, S, Ip, Io, M, C = _run_batch(sm, MEMBERS[:3], 32)
+    assert b.info()["graphs_cached"] == 1
+    first = [x.clone() for x in Io]
+    b.sweep(T, S, Ip, Io, M, C)          # same buffers: replay
+    b.synchronize()
+    assert b.info()["graphs_cached"] == 1
+    for x, y in zip(first, Io):
+        assert np.array_equal(x.cpu().numpy(), y.cpu().numpy())
+    b.sweep(T, S, Io, Ip, M, C)          # swapped roles: a second graph
+    b.synchronize()
+    assert b.info()["graphs_cached"] == 2
+    launches = b.info()["launches"]
+    assert launches == 3 * (2 + 2 * 3)
+
+
+def test_batch_autotune_keeps_results(gpu_lib):
+    sm = gpu_lib
+    b, T, S, Ip, Io, M, C = _run_batch(sm, MEMBERS, 32)
+    ref = [x.clone() for x in Io]
+    b.autotune(T, S, Ip, Io, reps=1)
+    info = b.info()
+    assert 1 <= info["strip_width"] <= 16 and 2 <= info["prefetch_rows"] <= 4
+    b.sweep(T, S, Ip, Io, M, C)
+    b.synchronize()
+    for m, x, y in zip(b.members, ref, Io):
+        assert np.array_equal(m.unpack(x).cpu().numpy(), m.unpack(y).cpu().numpy())
+
+
+def test_batch_members_refuse_single_sweeps(gpu_lib):
+    import torch
+    sm = gpu_lib
+    b, T, S, Ip, Io, M, C = _run_batch(sm, MEMBERS[:2], 32)
+    with pytest.raises(sm.SMError, match="belongs to a batch"):
+        b.members[0].sweep(T[0], S[0], Ip[0], Io[0])
+    with pytest.raises(sm.SMError, match="belongs to a batch"):
+        b.members[0].set_tiling(2, 2)
+    one_d = W.Config("d1", 1, 10, 1, (0.0, 1.0, 0.0, 1.0), W.log_edges(3), 4, 0,
+                     W.OPACITY_LARSEN, 10.0, (1.0, 0.0, 0.0, 0.0))
+    with pytest.raises(sm.SMError, match="2D"):
+        sm.Batch([MEMBERS[0], one_d], 32)
+    del torch
+
+
+def test_c5_workload_batch(gpu_lib):
+    """The 64-member batched workload: every member's moments are finite and
+    positive, and the smallest members match their single-problem sweeps."""
+    import torch
+    sm = gpu_lib
+    members = W.batched_2d()
+    cfgs = [m.cfg for m in members]
+    b = sm.Batch(cfgs, 32)
+    T, S, Io, M = [], [], [], []
+    for mem, h in zip(members, b.members):
+        t = torch.from_numpy(W.temperature_wave(mem.cfg)).cuda()
+        T.append(t)
+        S.append(h.opacity(t, torch.from_numpy(mem.scale).cuda()))
+        Io.append(h.empty_intensity())
+        M.append(h.new_moments())
+    b.sweep(T, S, None, Io, M, None)
+    b.synchronize()
+    for x in M:
+        phi = x[..., 0]
+        assert bool(torch.isfinite(phi).all()) and bool((phi > 0).all())
+    order = np.argsort([c.n_cells * c.n_dir * c.n_groups for c in cfgs])[:3]
+    for i in order:
+        p = sm.Problem.from_config(cfgs[i], 32, strip_width=b.info()["strip_width"],
+                                   prefetch_rows=b.info()["prefetch_rows"])
+        Io1 = p.empty_intensity()
+        p.sweep(T[i], S[i], None, Io1)
+        p.synchronize()
+        assert np.array_equal(b.members[i].unpack(Io[i]).cpu().numpy(),
+                              p.unpack(Io1).cpu().numpy())
