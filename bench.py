@@ -46,6 +46,8 @@ def parse():
                     help="skip the seconds-per-converged-step comparison (FP32 vs FP64 sweep)")
     ap.add_argument("--step-steps", type=int, default=3,
                     help="time steps timed per path in the step comparison (after 1 warm-up step)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched 64-problem measurement")
     return ap.parse_args()
 
 
@@ -250,6 +252,76 @@ def step_metric(sm, W, cfgs, n_steps: int, stream):
     return res
 
 
+def batched_metric(sm, W, stream, steps: int, warmup: int):
+    """The 64-problem batched workload (uneven 32^2..256^2 meshes, 8-32
+    groups, 32/64/128 directions, blocky two-material layouts), FP32 sweep:
+    whole passes of sm_batch_sweep (prologue, emissions, ONE persistent
+    sweep launch, reductions; replayed from CUDA graphs, the two intensity
+    buffers alternating) after autotuning the batch tiling, against the same
+    problems swept one after another through sm_sweep."""
+    import torch
+    members = W.batched_2d()
+    cfgs = [m.cfg for m in members]
+    upd = float(sum(c.n_cells * c.n_dir * c.n_groups for c in cfgs))
+    out = {"workload": "batched2d_64x(32..256)^2x(32..128)x(8..32)", "problems": len(cfgs),
+           "updates_per_pass": upd}
+    with torch.cuda.stream(stream):
+        b = sm.Batch(cfgs, 32, stream=stream)
+        T, S, I0, I1 = [], [], [], []
+        for mem, h in zip(members, b.members):
+            t = torch.from_numpy(W.temperature_wave(mem.cfg)).cuda()
+            T.append(t)
+            S.append(h.opacity(t, torch.from_numpy(mem.scale).cuda()))
+            I0.append(h.empty_intensity())
+            I1.append(h.empty_intensity())
+        b.sweep(T, S, None, I0, None, None)
+        b.synchronize()
+        b.autotune(T, S, I0, I1, reps=1)
+        bufs = [I0, I1]
+        for i in range(warmup):
+            b.sweep(T, S, bufs[i % 2], bufs[(i + 1) % 2], None, None)
+        b.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for i in range(steps):
+            b.sweep(T, S, bufs[i % 2], bufs[(i + 1) % 2], None, None)
+        ev1.record(stream)
+        ev1.synchronize()
+        b.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        info = b.info()
+        out.update({"value": upd / (ms * 1e-3), "unit": "cell-dir-group updates/s",
+                    "ms_per_pass": ms,
+                    "tiling": {"strip_width": info["strip_width"],
+                               "prefetch_rows": info["prefetch_rows"],
+                               "resident_ctas": info["resident_ctas"],
+                               "queue_items": info["n_tasks"]},
+                    "launches_per_pass": 2 + 2 * len(cfgs), "graph": "replayed"})
+        del I1
+        b.close()
+        # the same problems one after another (single-problem sweeps)
+        probs = [sm.Problem.from_config(c, 32, stream=stream) for c in cfgs]
+        Io = [p.empty_intensity() for p in probs]
+        for p, t, s_, io in zip(probs, T, S, Io):
+            p.sweep(t, s_, None, io)
+        torch.cuda.synchronize()
+        reps = max(1, steps // 2)
+        ev0.record(stream)
+        for _ in range(reps):
+            for p, t, s_, io in zip(probs, T, S, Io):
+                p.sweep(t, s_, None, io)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms_seq = ev0.elapsed_time(ev1) / reps
+        out["sequential_ms_per_pass"] = ms_seq
+        out["batched_speedup"] = ms_seq / ms
+        for p in probs:
+            p.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     """--impl reference: the oracle on the host cores, same metric and workload."""
     from paper_2504_21784_gb300 import workloads as W
@@ -420,6 +492,8 @@ def main():
         torch.cuda.empty_cache()
         line["step_metric"] = step_metric(sm, W, [W.multigroup_2d(), W.gray_channel_2d()],
                                           args.step_steps, stream)
+    if not args.no_batched and not (args.nx or args.groups):
+        line["batched"] = batched_metric(sm, W, stream, max(3, args.steps // 2), 3)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)
     print(json.dumps(line), flush=True)

@@ -726,6 +726,22 @@ __global__ void __launch_bounds__(256) sweep1d_kernel(const SweepArgs A) {
 }
 
 // ---------------------------------------------------------------------------
+// Lets kernel k use up to the device's opt-in shared memory per block (less
+// its static shared memory), so that problems of different sizes sharing one
+// kernel instantiation can all launch; false if smem does not fit.
+static bool allow_dynamic_smem(const void *k, size_t smem, int *nsm) {
+    int dev = 0, maxopt = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    cudaDeviceGetAttribute(nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return false;
+    const size_t limit = (size_t)maxopt - fa.sharedSizeBytes;
+    if (smem > limit) return false;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit) ==
+           cudaSuccess;
+}
+
 template <typename RT>
 static const void *kernel2d_ptr(int GW) {
     switch (GW) {
@@ -750,14 +766,8 @@ int sweep2d_max_resident(const sm_problem *p, int W, int S, size_t *smem_out) {
     const size_t smem = sweep2d_smem_bytes(p->prec, W, p->GW, S, p->GSLOT);
     if (smem_out) *smem_out = smem;
     const void *k = (p->prec == 32) ? kernel2d_ptr<float>(p->GW) : kernel2d_ptr<double>(p->GW);
-    int dev = 0, nsm = 0, maxopt = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (smem + 64 > (size_t)maxopt) return 0;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return 0;
+    int nsm = 0;
+    if (!allow_dynamic_smem(k, smem, &nsm)) return 0;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, W * 32, smem) != cudaSuccess)
         return 0;
@@ -776,14 +786,8 @@ cudaError_t launch_sweep2d_batch(int prec, const BatchSweepArgs &b, int grid, si
 int sweep2d_batch_max_resident(int prec, int W, size_t smem) {
     const void *k = prec == 32 ? (const void *)sweep2d_batch_kernel<float>
                                : (const void *)sweep2d_batch_kernel<double>;
-    int dev = 0, nsm = 0, maxopt = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (smem + 64 + sizeof(SweepArgs) > (size_t)maxopt) return 0;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return 0;
+    int nsm = 0;
+    if (!allow_dynamic_smem(k, smem, &nsm)) return 0;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, W * 32, smem) != cudaSuccess)
         return 0;

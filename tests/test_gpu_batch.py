@@ -174,3 +174,22 @@ def test_c5_workload_batch(gpu_lib):
         p.synchronize()
         assert np.array_equal(b.members[i].unpack(Io[i]).cpu().numpy(),
                               p.unpack(Io1).cpu().numpy())
+
+
+def test_problems_sharing_a_kernel_launch_in_any_order(gpu_lib):
+    """Two problems with the same slots per lane but different stage sizes
+    (32 directions x 32 groups, then 128 directions x 16 groups): the first
+    still launches after the second configured the shared kernel."""
+    import torch
+    sm = gpu_lib
+    big = _cfg(10, 12, 10, 32, 2, 4)
+    small = _cfg(11, 9, 9, 16, 4, 8)
+    pb = sm.Problem.from_config(big, 32, strip_width=8, prefetch_rows=4)
+    ps = sm.Problem.from_config(small, 32, strip_width=2, prefetch_rows=2)
+    assert pb.info["groups_per_warp"] == ps.info["groups_per_warp"] == 8
+    for p, cfg in ((pb, big), (ps, small), (pb, big)):
+        T, S, Ip = _inputs(sm, p, cfg, seed=1)
+        Io = p.empty_intensity()
+        p.sweep(T, S, Ip, Io)
+        p.synchronize()
+        assert bool(torch.isfinite(p.unpack(Io)).all())
