@@ -386,6 +386,56 @@ sm_status sm_batch_autotune(sm_batch *b, const double *const *T_nodal_dev,
                             const double *const *sigma_dev, const void *const *I_prev_dev,
                             void *const *I_out_dev, int reps);
 
+/* ------------------------------------------------------------------------
+ * Time-dependent high-order problem and its discrete adjoint: the gradient
+ * of the time-integrated right-edge leakage with respect to per-cell opacity
+ * scales s_K (sigma_{g,K} = s_K f_g(Tbar_K), opacities frozen at the start of
+ * each step).  The forward being differentiated is the converged high-order
+ * system of each backward-Euler step -- the lumped DG transport of
+ * Eq. dgsn_transport with the time term of Eq. smm_be_transport and the
+ * nodal energy balance C_v (T - T*)/dt = sum_g sigma_g (phi_g - B_g(T))
+ * (Eq. energy_balance) -- which the SM iteration with consistent closures
+ * and the unaccelerated iteration both converge to.  Adjoint differentiation
+ * is this library's addition; the paper does not differentiate.
+ * ---------------------------------------------------------------------- */
+
+/* One backward-Euler step converged by the unaccelerated iteration: a full
+ * pass (emission at the current T, sweep, moments) then one Newton step of
+ * the nodal energy balance, until ||dT|| <= tol ||T||; a final pass makes
+ * I_next the intensity of the converged T.  T_dev[cell][node]: T^n on entry,
+ * T^{n+1} on exit; scale_dev[cell]: s_K; cv_dev[cell][node]; I_prev_dev:
+ * packed I^n (NULL: zero); I_next_dev: packed I^{n+1} (out).  *iters_host
+ * (may be NULL) receives the passes taken.  Needs dt > 0.  Synchronous. */
+sm_status sm_ho_step(sm_problem *p, const double *scale_dev, const double *cv_dev, double *T_dev,
+                     const void *I_prev_dev, void *I_next_dev, double tol, int max_iter,
+                     int *iters_host);
+
+/* Outgoing partial current through the right edge (x = x1) of a packed
+ * intensity, lumped at the face's Gauss-Lobatto points:
+ * sum_{d: Omega_x > 0} w_d Omega_x sum_g sum_{right-edge nodes} (h_y/2) I.
+ * 2D only.  Synchronous. */
+sm_status sm_leakage(sm_problem *p, const void *I_dev, double *out_host);
+
+/* One adjoint step, run backwards in time after sm_ho_step produced
+ * (T_n, T_np1, I_np1): solves the transposed linearised step by source
+ * iteration -- reversed-direction sweeps (the transposed upwind operator of
+ * Omega is that of -Omega: the reversed wavefront), the leakage entering as
+ * the isotropic inflow dt h_x h_y / 4 through the right edge, the energy
+ * multiplier theta per node -- until ||dtheta|| <= tol ||theta||.
+ *   psi_next_dev: packed transport multiplier of step n+1 (NULL for the last
+ *     step); X_next_dev[cell][node]: the later step's dependence on T^{n+1}
+ *     (NULL for the last step);
+ *   psi_out_dev (packed) and X_out_dev[cell][node]: the same for step n;
+ *   grad_dev[cell]: dJ/ds_K of this step is ADDED to it.
+ * The packed multiplier is stored at the original directions' positions
+ * (sm_unpack_intensity gives it in canonical order).  2D only; needs dt > 0.
+ * Synchronous. */
+sm_status sm_adjoint_step(sm_problem *p, const double *scale_dev, const double *cv_dev,
+                          const double *T_n_dev, const double *T_np1_dev, const void *I_np1_dev,
+                          const void *psi_next_dev, const double *X_next_dev, void *psi_out_dev,
+                          double *X_out_dev, double *grad_dev, double tol, int max_iter,
+                          int *iters_host);
+
 /* Number of kernels this problem has launched since creation. */
 int64_t sm_launch_count(const sm_problem *p);
 

@@ -32,7 +32,8 @@ EXPORTED = ["sm_create_problem", "sm_destroy_problem", "sm_get_info", "sm_set_st
             "sm_default_step_params", "sm_loworder_newton", "sm_step",
             "sm_create_batch", "sm_destroy_batch", "sm_batch_problem", "sm_batch_get_info",
             "sm_batch_set_stream", "sm_batch_set_tiling", "sm_batch_sweep",
-            "sm_batch_synchronize", "sm_batch_autotune"]
+            "sm_batch_synchronize", "sm_batch_autotune", "sm_ho_step", "sm_leakage",
+            "sm_adjoint_step"]
 
 
 class SMError(RuntimeError):
@@ -151,6 +152,10 @@ def load():
         "sm_batch_sweep": [P, PP, PP, PP, PP, PP, PP],
         "sm_batch_synchronize": [P],
         "sm_batch_autotune": [P, PP, PP, PP, PP, I],
+        "sm_ho_step": [P, P, P, P, P, P, D, I, ctypes.POINTER(ctypes.c_int)],
+        "sm_leakage": [P, P, PD],
+        "sm_adjoint_step": [P, P, P, P, P, P, P, P, P, P, P, D, I,
+                            ctypes.POINTER(ctypes.c_int)],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -386,6 +391,32 @@ class Problem:
                               ctypes.byref(params) if params is not None else None,
                               ctypes.byref(st)))
         return _stats(st)
+
+    # ---------------------------------------------------------------- time steps / adjoint
+    def ho_step(self, scale, cv, T, I_prev, I_next, tol: float = 1e-13,
+                max_iter: int = 500) -> int:
+        """One backward-Euler step of the high-order problem converged by the
+        unaccelerated iteration (sm_ho_step); T is updated in place.  Returns
+        the number of passes."""
+        it = ctypes.c_int()
+        _check(load().sm_ho_step(self._h, _ptr(scale), _ptr(cv), _ptr(T), _ptr(I_prev),
+                                 _ptr(I_next), float(tol), int(max_iter), ctypes.byref(it)))
+        return it.value
+
+    def leakage(self, I) -> float:
+        out = ctypes.c_double()
+        _check(load().sm_leakage(self._h, _ptr(I), ctypes.byref(out)))
+        return out.value
+
+    def adjoint_step(self, scale, cv, T_n, T_np1, I_np1, psi_next, X_next, psi_out, X_out,
+                     grad, tol: float = 1e-13, max_iter: int = 500) -> int:
+        """One adjoint step (sm_adjoint_step); psi_out, X_out written, grad += dJ/ds."""
+        it = ctypes.c_int()
+        _check(load().sm_adjoint_step(self._h, _ptr(scale), _ptr(cv), _ptr(T_n), _ptr(T_np1),
+                                      _ptr(I_np1), _ptr(psi_next), _ptr(X_next), _ptr(psi_out),
+                                      _ptr(X_out), _ptr(grad), float(tol), int(max_iter),
+                                      ctypes.byref(it)))
+        return it.value
 
     def launch_count(self) -> int:
         return int(load().sm_launch_count(self._h))

@@ -102,6 +102,7 @@ void free_all(sm_problem *p) {
     for (void *b : bufs)
         if (b) cudaFree(b);
     smk::lo_free(p);
+    smk::adjoint_free(p);
     for (auto &e : p->ev_pool)
         if (e) cudaEventDestroy(e);
     p->ev_pool.clear();
@@ -221,17 +222,13 @@ sm_status check_intensity_align(const void *I_prev, const void *I_out) {
     return SM_OK;
 }
 
-// The hot path without argument checks: emission, sweep, reduction.
-sm_status run_sweep(sm_problem *p, const double *T, const double *sigma, const void *I_prev,
-                    void *I_out, double *mom, double *clo) {
+// Sweep kernel and reduction of one pass (the source records are in place).
+sm_status sweep_pass(sm_problem *p, const void *I_prev, void *I_out, double *mom, double *clo,
+                     int reverse, cudaEvent_t *ev) {
     cudaStream_t s = p->stream;
-    cudaEvent_t *ev = p->profiling ? timing_events(p, p->n_timed) : nullptr;
-    if (ev) SM_CUDA(cudaEventRecord(ev[0], s));
-    SM_CUDA(smk::launch_emission(p, T, sigma, nullptr, s));
-    p->launches++;
-    if (ev) SM_CUDA(cudaEventRecord(ev[1], s));
     ++p->epoch;
     smk::SweepArgs a = make_args(p, I_prev, I_out);
+    a.reverse = reverse;
     if (p->dim == 2) {
         SM_CUDA(cudaMemsetAsync(p->d_ctrl, 0, 2 * sizeof(unsigned int), s));
         SM_CUDA(cudaMemsetAsync(p->d_mom_acc, 0, (size_t)p->ncell * 36 * p->rsize, s));
@@ -242,12 +239,29 @@ sm_status run_sweep(sm_problem *p, const double *T, const double *sigma, const v
     }
     p->launches++;
     if (ev) SM_CUDA(cudaEventRecord(ev[2], s));
-    double *m = mom ? mom : p->d_mom_tmp;
-    if (p->dim == 2)
-        SM_CUDA(smk::launch_reduce(p, p->d_mom_acc, 1, m, clo, s));
-    else
-        SM_CUDA(smk::launch_reduce(p, p->d_part, p->NQ * p->NWT, m, clo, s));
+    if (mom || clo) {
+        double *m = mom ? mom : p->d_mom_tmp;
+        if (p->dim == 2)
+            SM_CUDA(smk::launch_reduce(p, p->d_mom_acc, 1, m, clo, s));
+        else
+            SM_CUDA(smk::launch_reduce(p, p->d_part, p->NQ * p->NWT, m, clo, s));
+        p->launches++;
+    }
+    return SM_OK;
+}
+
+// The hot path without argument checks: emission, sweep, reduction.
+sm_status run_sweep(sm_problem *p, const double *T, const double *sigma, const void *I_prev,
+                    void *I_out, double *mom, double *clo) {
+    cudaStream_t s = p->stream;
+    cudaEvent_t *ev = p->profiling ? timing_events(p, p->n_timed) : nullptr;
+    if (ev) SM_CUDA(cudaEventRecord(ev[0], s));
+    SM_CUDA(smk::launch_emission(p, T, sigma, nullptr, s));
     p->launches++;
+    if (ev) SM_CUDA(cudaEventRecord(ev[1], s));
+    // the moments are always summed in a full pass (into scratch when mom is NULL)
+    sm_status st = sweep_pass(p, I_prev, I_out, mom ? mom : p->d_mom_tmp, clo, 0, ev);
+    if (st != SM_OK) return st;
     if (ev) {
         SM_CUDA(cudaEventRecord(ev[3], s));
         p->n_timed++;
@@ -260,6 +274,12 @@ sm_status run_sweep(sm_problem *p, const double *T, const double *sigma, const v
 namespace smk {
 void set_last_error(const char *msg) { g_err = msg; }
 sm_status apply_tiling_ext(sm_problem *p, int W, int S) { return apply_tiling(p, W, S); }
+sm_status sweep_only(sm_problem *p, const void *I_prev, void *I_out, double *mom, double *clo,
+                     int reverse) {
+    if (reverse && p->dim != 2)
+        return fail(SM_ERR_UNSUPPORTED, "reversed (adjoint) sweeps are 2D only");
+    return sweep_pass(p, I_prev, I_out, mom, clo, reverse, nullptr);
+}
 SweepArgs make_sweep_args(const sm_problem *p, const void *I_prev, void *I_out) {
     return make_args(p, I_prev, I_out);
 }

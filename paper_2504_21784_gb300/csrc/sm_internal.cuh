@@ -51,6 +51,8 @@ struct SweepArgs {
     unsigned long long epoch;
     long long timeout_ns;
     int fault_skip_publish;  // test hook: strip 0 never publishes
+    int reverse;             // 2D: sweep -Omega for every direction; I_prev / I_out of
+                             // geometric quadrant q live at quadrant q^2 (adjoint sweeps)
 };
 
 // Many problems in one persistent 2D sweep launch (sweep2d_batch_kernel).
@@ -70,6 +72,10 @@ cudaError_t launch_opacity(const sm_problem *p, const double *T, const double *s
 cudaError_t launch_emission(const sm_problem *p, const double *T, const double *sigma,
                             double *q_canon, cudaStream_t s);
 cudaError_t launch_inflow(const sm_problem *p, cudaStream_t s);
+cudaError_t launch_planck_parts(const sm_problem *p, const double *T, const double *sigma,
+                                double *B4, double *cB, double *sdB, cudaStream_t s);
+cudaError_t launch_opacity_shape(const sm_problem *p, const double *T, double *f, double *df,
+                                 cudaStream_t s);
 cudaError_t launch_closures_from_T(const sm_problem *p, const double *mom, const double *T,
                                    const double *sigma, double *out, cudaStream_t s);
 cudaError_t launch_sweep2d(const sm_problem *p, const SweepArgs &a, int grid, cudaStream_t s);
@@ -91,13 +97,21 @@ void planck_upload_tables(void);
 void set_last_error(const char *msg);
 // Free the low-order workspace (no-op when the low-order solve never ran).
 void lo_free(sm_problem *p);
+// The sweep of one problem without its emission (the caller has written the
+// source records): sweep kernel and, when mom is non-NULL, the moment sums
+// and closures.  reverse = 1 sweeps -Omega (adjoint sweeps, 2D only).
+sm_status sweep_only(sm_problem *p, const void *I_prev, void *I_out, double *mom, double *clo,
+                     int reverse);
+// Free the adjoint workspace (no-op when unused).
+void adjoint_free(sm_problem *p);
 // Tiling and sweep arguments of one problem (used by the batch object).
 sm_status apply_tiling_ext(sm_problem *p, int W, int S);
 SweepArgs make_sweep_args(const sm_problem *p, const void *I_prev, void *I_out);
 
 }  // namespace smk
 
-struct sm_lo_state;  // low-order solve workspace, created on first use
+struct sm_lo_state;   // low-order solve workspace, created on first use
+struct sm_adj_state;  // adjoint workspace, created on first use
 
 struct sm_problem {
     // descriptor copy
@@ -143,6 +157,7 @@ struct sm_problem {
     int64_t launches = 0;
     size_t workspace_bytes = 0;
     sm_lo_state *lo = nullptr;
+    sm_adj_state *adj = nullptr;
     bool batch_owned = false;    // member of an sm_batch: swept only by the batch
     bool ctrl_borrowed = false;  // d_ctrl belongs to the batch
 };

@@ -321,6 +321,65 @@ __global__ void emission_kernel(int ncell, int nn, int G, int Gp, const double *
     gray[(size_t)t * 2 + 1] = nr / dr;
 }
 
+// Group Planck functions and their temperature derivatives at the nodes,
+// for the adjoint (one thread per node): B4[g][cell][node] = B_g(T)/4pi and
+// cB[g][cell][node] = sigma_g dB_g/dT / 4pi with dB_g/dT = 4 a c T^3 r_g
+// (Sec. 2), and sdB[cell][node] = sum_g sigma_g dB_g/dT.
+__global__ void planck_parts_kernel(int ncell, int nn, int G, const double *__restrict__ edges,
+                                    double ac, const double *__restrict__ T,
+                                    const double *__restrict__ sigma, double *__restrict__ B4,
+                                    double *__restrict__ cB, double *__restrict__ sdB) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncell * nn) return;
+    const int cell = t / nn, node = t - cell * nn;
+    const double Tn = T[t];
+    const double invT = 1.0 / Tn;
+    const double inv4pi = 1.0 / (4.0 * PI_D);
+    const double aT4 = ac * Tn * Tn * Tn * Tn, dT = 4.0 * ac * Tn * Tn * Tn;
+    EdgeVals lo = edge_vals(0.0);
+    double s = 0.0;
+    for (int g = 0; g < G; ++g) {
+        const double xhi = (g == G - 1) ? INFINITY : edges[g + 1] * invT;
+        const EdgeVals hi = (lo.tail && lo.Q == 0.0 && lo.RQ == 0.0) ? lo : edge_vals(xhi);
+        double b, r;
+        group_br(lo, hi, b, r);
+        const double sg = sigma[(size_t)g * ncell + cell];
+        const size_t o = ((size_t)g * ncell + cell) * nn + node;
+        B4[o] = aT4 * b * inv4pi;
+        cB[o] = sg * dT * r * inv4pi;
+        s += sg * dT * r;
+        lo = hi;
+    }
+    sdB[t] = s;
+}
+
+// Opacity shape f_g(Tbar) = sigma_g / s and its derivative df_g/dTbar per
+// [g][cell] (POWER: Tbar^-3; LARSEN: alpha (1 - e^{-E_g/Tbar})/E_g^3, E_g the
+// geometric mean of the group's edges), Tbar the cell mean of the nodal T.
+__global__ void opacity_shape_kernel(int ncell, int nn, int G, int kind, double alpha,
+                                     const double *__restrict__ edges,
+                                     const double *__restrict__ T, double *__restrict__ f,
+                                     double *__restrict__ df) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ncell) return;
+    double tb = 0.0;
+    for (int n = 0; n < nn; ++n) tb += T[(size_t)k * nn + n];
+    tb /= nn;
+    for (int g = 0; g < G; ++g) {
+        double fv, dv;
+        if (kind == SM_OPACITY_POWER) {
+            fv = 1.0 / (tb * tb * tb);
+            dv = -3.0 * fv / tb;
+        } else {
+            const double eg = sqrt(edges[g] * edges[g + 1]);
+            fv = alpha * (-expm1(-eg / tb)) / (eg * eg * eg);
+            dv = -alpha * exp(-eg / tb) / (eg * eg * tb * tb);
+        }
+        f[(size_t)g * ncell + k] = fv;
+        df[(size_t)g * ncell + k] = dv;
+    }
+}
+
 // Boundary inflow B_g(T_bdr)/4pi per side (Eq. transport boundary condition).
 template <typename RT>
 __global__ void inflow_kernel(int G, int Gp, const double *__restrict__ edges, double ac4pi,
@@ -426,6 +485,22 @@ cudaError_t launch_emission(const sm_problem *p, const double *T, const double *
         emission_kernel<double><<<blocks, threads, 0, s>>>(
             p->ncell, p->nn, p->G, p->Gp, p->d_edges, scale, p->inv_cdt, T, sigma,
             (double *)p->d_src, p->d_gray, q_canon, p->d_ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_planck_parts(const sm_problem *p, const double *T, const double *sigma,
+                                double *B4, double *cB, double *sdB, cudaStream_t s) {
+    const int n = p->ncell * p->nn;
+    planck_parts_kernel<<<(n + 127) / 128, 128, 0, s>>>(p->ncell, p->nn, p->G, p->d_edges,
+                                                       p->desc.a * p->desc.c, T, sigma, B4, cB,
+                                                       sdB);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_opacity_shape(const sm_problem *p, const double *T, double *f, double *df,
+                                 cudaStream_t s) {
+    opacity_shape_kernel<<<(p->ncell + 127) / 128, 128, 0, s>>>(
+        p->ncell, p->nn, p->G, p->desc.opacity_kind, p->desc.opacity_alpha, p->d_edges, T, f, df);
     return cudaGetLastError();
 }
 

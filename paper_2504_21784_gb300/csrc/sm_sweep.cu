@@ -338,7 +338,9 @@ __device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay,
     const int au = sx > 0 ? 0 : 1, bu = sy > 0 ? 0 : 1;
     const int nuu = au + 2 * bu, ndu = (1 - au) + 2 * bu;
     const int nud = au + 2 * (1 - bu), ndd = (1 - au) + 2 * (1 - bu);
-    const size_t wtbase = (size_t)wg * A.ncell;
+    // memory quadrant of the intensities: the geometric one, or its reverse
+    // for adjoint sweeps (the transposed operator of Omega is that of -Omega)
+    const size_t wtbase = ((size_t)(A.reverse ? (q ^ 2) : q) * A.NWT + wt) * A.ncell;
     const bool global_in = (w == 0) && sr > 0;
     const bool global_out = (w == ws - 1) && sr < A.NS - 1;
     const size_t fidx_out = ((size_t)wg * A.NS + strip) * ny;
