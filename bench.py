@@ -48,6 +48,8 @@ def parse():
                     help="time steps timed per path in the step comparison (after 1 warm-up step)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched 64-problem measurement")
+    ap.add_argument("--adjoint-fd-cells", type=int, default=4,
+                    help="cells of the adjoint finite-difference check (0: skip the adjoint)")
     return ap.parse_args()
 
 
@@ -322,6 +324,59 @@ def batched_metric(sm, W, stream, steps: int, warmup: int):
     return out
 
 
+def adjoint_metric(sm, W, fd_cells: int, warm: bool = False):
+    """The adjoint workload (128^2 cells, 64 directions, 16 groups, 20
+    backward-Euler steps, FP64, each step converged to 1e-13): wall time of
+    the forward (with checkpoints every sqrt(20) steps) and of the backward
+    (segment recomputation + adjoint steps), and central differences
+    (h = 1e-4 s_K) of the time-integrated right-edge leakage on fd_cells
+    cells drawn with seed 21784 among the cells whose adjoint sensitivity is
+    at least 1e-3 of the largest (smaller sensitivities move J by less than
+    its FP64 rounding for a 1e-4 perturbation)."""
+    import numpy as np
+    import torch
+    from paper_2504_21784_gb300 import adjoint as A
+    cfg = W.adjoint_2d_warm() if warm else W.adjoint_2d()
+    prob = sm.Problem.from_config(cfg, 64)
+    T0 = torch.full((cfg.n_cells, 4), cfg.T0, dtype=torch.float64, device="cuda")
+    cv = torch.full((cfg.n_cells, 4), cfg.cv, dtype=torch.float64, device="cuda")
+    s = torch.from_numpy(W.scale_field(cfg)).cuda()
+    st = A.LeakageSetup(prob, cv, T0, A.equilibrium_intensity(prob, T0), cfg.steps, 0,
+                        tol=1e-13, max_iter=5000, dt=cfg.dt)
+    s.requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = A.leakage(s, st)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    J.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    g = s.grad.detach().cpu().numpy()
+    out = {"workload": f"{cfg.name}, T0 = {cfg.T0}, {cfg.steps} steps, FP64", "J": J.item(),
+           "forward_s": t1 - t0, "backward_s": t2 - t1, "checkpoint_every": st.every(),
+           "params": int(g.size), "grad_max_abs": float(np.abs(g).max())}
+    if fd_cells > 0:
+        cand = np.flatnonzero(np.abs(g) >= 1e-3 * np.abs(g).max())
+        rng = np.random.default_rng(21784)
+        cells = rng.choice(cand, min(fd_cells, cand.size), replace=False)
+        errs = []
+        with torch.no_grad():
+            for k in cells:
+                h = 1e-4 * s[k].item()
+                sp, sm_ = s.detach().clone(), s.detach().clone()
+                sp[k] += h
+                sm_[k] -= h
+                fd = (A.leakage(sp, st).item() - A.leakage(sm_, st).item()) / (2 * h)
+                errs.append(abs(fd - g[k]) / abs(g[k]))
+        out.update({"fd_cells": int(len(cells)), "fd_candidates": int(cand.size),
+                    "fd_h": "1e-4 s_K", "fd_max_rel_err": float(max(errs)),
+                    "fd_median_rel_err": float(np.median(errs))})
+    prob.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     """--impl reference: the oracle on the host cores, same metric and workload."""
     from paper_2504_21784_gb300 import workloads as W
@@ -494,6 +549,9 @@ def main():
                                           args.step_steps, stream)
     if not args.no_batched and not (args.nx or args.groups):
         line["batched"] = batched_metric(sm, W, stream, max(3, args.steps // 2), 3)
+    if args.adjoint_fd_cells > 0 and not (args.nx or args.groups):
+        line["adjoint"] = adjoint_metric(sm, W, args.adjoint_fd_cells)
+        line["adjoint_warm"] = adjoint_metric(sm, W, args.adjoint_fd_cells, warm=True)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)
     print(json.dumps(line), flush=True)

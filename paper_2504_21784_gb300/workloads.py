@@ -121,6 +121,14 @@ def adjoint_2d() -> Config:
                   4, 4, OPACITY_LARSEN, 10.0, (1.0, 0.0, 0.0, 0.0), steps=20, seed=21784)
 
 
+def adjoint_2d_warm() -> Config:
+    """The adjoint problem from a warm uniform start T0 = 0.3 (the configuration
+    leaves the initial state open; from T0 = 0.01 the 20-step right-edge leakage
+    depends on a few right-edge cells only, from T0 = 0.3 on ~25 columns)."""
+    c = adjoint_2d()
+    return dataclasses.replace(c, name="adjoint2d_warm_128x128x64x16", T0=0.3)
+
+
 CONFIGS = {
     "c1": marshak_1d,
     "c2": gray_channel_2d,
