@@ -163,7 +163,7 @@ def lo_operators(m: Mesh, c: float, alpha: float):
     return AEF.tocsr(), AFE.tocsr(), P.tocsr()
 
 
-def closure_sources(m: Mesh, clo: np.ndarray):
+def closure_sources(m: Mesh, clo: np.ndarray, face_term: bool = True):
     """R1_ind(v) for every first-moment test function (Sec. 4, independent),
     from nodal closures (2D: [E,Fx,Fy,Txx,Txy,Tyy,sigE,sigF,sigP,Cx,Cy];
     1D: [E,F,T,sigE,sigF,sigP,C])."""
@@ -192,7 +192,7 @@ def closure_sources(m: Mesh, clo: np.ndarray):
                     r[(base + i) * D + d] += mass * sum(g[l] * Tten[base + q, d, l] for l in range(D))
     # - int_Gamma0 [v] . {T n}
     for kind, n, wf, pairs in faces(m):
-        if kind != "int":
+        if kind != "int" or not face_term:
             continue
         for n1, n2 in pairs:
             Tn = 0.5 * (Tten[n1] + Tten[n2]) @ np.array(n[:D])
@@ -256,11 +256,13 @@ def eliminate_T(T0, a, c, cv_dt, sigP, sigE, E, Tstar, rtol, maxit, T_floor):
 
 
 def lo_newton(m: Mesh, ops, c, a, dt, alpha, clo, T_k, cv, Estar, Fstar, jin2, T0, E0,
-              prm: LOParams):
+              prm: LOParams, R1=None, bnd=None):
     """Solve the gray LO system with the energy balance (Eq. absem) by the
     Newton-type iteration of Sec. 5 with nonlinear temperature elimination.
     clo: nodal closures; T_k: previous-step temperature T*; cv: nodal C_v;
-    Estar, Fstar: time-edge sources; T0, E0: initial guesses.
+    Estar, Fstar: time-edge sources; T0, E0: initial guesses.  R1 and bnd
+    replace the first-moment closure source and the zeroth-moment boundary
+    source of the independent method (the consistent method supplies its own).
     Returns (T, E, F, stats)."""
     AEF, AFE, P = ops
     N, D = m.nnode, m.dim
@@ -271,10 +273,12 @@ def lo_newton(m: Mesh, ops, c, a, dt, alpha, clo, T_k, cv, Estar, Fstar, jin2, T
     sEt, sFt = sE + inv_cdt, sF + inv_cdt
     cv_dt = cv.reshape(-1) / dt
     Tk = T_k.reshape(-1)
-    R1 = closure_sources(m, clo)
+    if R1 is None:
+        R1 = closure_sources(m, clo)
     bF = mass * inv_cdt * Fstar.reshape(-1) + R1
     AFF = sp.diags(np.repeat(mass * sFt, D))
-    bnd = boundary_source(m, jin2)
+    if bnd is None:
+        bnd = boundary_source(m, jin2)
     T, E = T0.reshape(-1).copy(), E0.reshape(-1).copy()
     u0 = np.concatenate([T, E])
     d1 = None
@@ -322,6 +326,7 @@ class StepParams:
     eps_outer: float = 1e-3
     max_outer: int = 100
     lo: LOParams = dataclasses.field(default_factory=LOParams)
+    method: str = "independent"   # or "consistent" (Sec. 4)
 
 
 def equilibrium_intensity(cfg, T0, omx):
@@ -362,8 +367,12 @@ def sm_step(cfg, scale, cv, T_k, I_k, mom_k, prm: StepParams):
         I = sweep(cfg.dim, cfg.nx, cfg.ny, cfg.extent, omx, omy, sigma, inv_cdt, q, I_k, infl)
         mom = moments(cfg.dim, omx, omy, w, sigma, I)
         clo = closures(cfg.dim, cfg.edges, c, sigma, T, mom)
+        R1 = bnd = None
+        if prm.method == "consistent":
+            from .consistent import consistent_sources
+            R1, bnd = consistent_sources(m, c, alpha, clo, omx, omy, w, I, I_in_side)
         T, E, F, st = lo_newton(m, ops, c, a, dt, alpha, clo, T_k, cv, Estar, Fstar, jin2, T, E,
-                                prm.lo)
+                                prm.lo, R1=R1, bnd=bnd)
         stats["newton"].append(st["newton"])
         stats["elim_max"] = max(stats["elim_max"], st["elim_max"])
         stats["outer"] = it
