@@ -184,6 +184,12 @@ sm_status sm_closures(sm_problem *p, const double *moments_dev, const double *T_
  * multigrid and caps it at 50; this library preconditions with the exact
  * diagonal of the Schur complement (Jacobi), which needs more iterations,
  * so max_pcg defaults to 5000. */
+/* low-order closures (Sec. 4): independent (first-moment corrections only)
+ * or consistent (face and boundary corrections from the half-range moments
+ * of the high-order intensity, so that the converged low-order solution
+ * equals the high-order moments; 2D) */
+enum { SM_METHOD_INDEPENDENT = 0, SM_METHOD_CONSISTENT = 1 };
+
 typedef struct {
     double eps_outer;   /* Eq. relative_tol for Algorithm 1's fixed point */
     double eps_inner;   /* Eq. relative_tol for the low-order Newton iteration */
@@ -191,6 +197,7 @@ typedef struct {
     double elim_rtol;   /* pointwise elimination stops when |dT| <= elim_rtol |T| */
     double T_floor;     /* lower bound imposed on T by the elimination */
     int max_outer, max_inner, max_pcg, max_elim;
+    int method;         /* SM_METHOD_INDEPENDENT (default) or SM_METHOD_CONSISTENT */
 } sm_step_params;
 
 /* Iteration counts of one call. */
@@ -224,10 +231,21 @@ void sm_default_step_params(sm_step_params *params_host);
  *   T_dev, E_dev [cell][node]: initial guesses on entry, solution on exit;
  *   F_dev[cell][node][dim]: flux of the last linear solve (out).
  * Boundary: Marshak-type with the gray isotropic inflow of desc.T_bdr.
- * Needs desc.dt > 0.  Errors: INVALID_ARG, NO_CONVERGENCE (conjugate
+ * params->method = SM_METHOD_CONSISTENT uses the consistent sources from
+ * the per-quadrant moments of the last sweep (registered with
+ * sm_set_quadrant_moments; 2D).  Needs desc.dt > 0.  Errors: INVALID_ARG, NO_CONVERGENCE (conjugate
  * gradients broke down), NONPHYSICAL (non-finite iterate), CUDA, OOM (the
  * low-order workspace is allocated on first use).  A capped iteration is
  * not an error: see stats.  stats_host may be NULL. */
+/* Register (or, with NULL, drop) a caller buffer qmom_dev[cell][node][4][6]
+ * that every following sweep of p fills with the per-quadrant moments of the
+ * new intensity (quadrants in the canonical order; per quadrant phi, F_x,
+ * F_y, Pi_xx, Pi_xy, Pi_yy with Pi = sum w Omega Omega I, all groups): the
+ * input of the consistent method, from which every half-range current and
+ * second moment on axis-aligned faces follows.  2D only.  The moment
+ * accumulator grows to four quadrants (allocated here).  Synchronizes. */
+sm_status sm_set_quadrant_moments(sm_problem *p, double *qmom_dev);
+
 sm_status sm_loworder_newton(sm_problem *p, const double *closures_dev, const double *T_star_dev,
                              const double *cv_dev, const double *moments_star_dev, double *T_dev,
                              double *E_dev, double *F_dev, const sm_step_params *params_host,
@@ -246,6 +264,11 @@ sm_status sm_loworder_newton(sm_problem *p, const double *closures_dev, const do
  *     time-edge sources), on exit those of I_next;
  *   I_prev_dev: packed I^k; I_next_dev: packed I^{k+1} (out; no aliasing);
  *   closures_dev[cell][node][n_closures]: last closures (out; may be NULL).
+ * With params->method = SM_METHOD_CONSISTENT (2D) the sweeps also form
+ * per-quadrant moments (in the buffer registered with
+ * sm_set_quadrant_moments, else in the library's own) and the low-order
+ * solves use the consistent sources; the step then converges to the
+ * converged high-order step of sm_ho_step.
  * Errors as sm_sweep and sm_loworder_newton.  Synchronous. */
 sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, double *T_dev,
                   double *E_dev, double *F_dev, double *moments_dev, const void *I_prev_dev,

@@ -18,6 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsmtrt.so")
 
 SM_OK = 0
+METHOD_INDEPENDENT, METHOD_CONSISTENT = 0, 1
 STATUS = {0: "SM_OK", 1: "SM_ERR_INVALID_ARG", 2: "SM_ERR_CUDA", 3: "SM_ERR_OOM",
           4: "SM_ERR_NO_CONVERGENCE", 5: "SM_ERR_NONPHYSICAL", 6: "SM_ERR_TIMEOUT",
           7: "SM_ERR_UNSUPPORTED"}
@@ -33,7 +34,7 @@ EXPORTED = ["sm_create_problem", "sm_destroy_problem", "sm_get_info", "sm_set_st
             "sm_create_batch", "sm_destroy_batch", "sm_batch_problem", "sm_batch_get_info",
             "sm_batch_set_stream", "sm_batch_set_tiling", "sm_batch_sweep",
             "sm_batch_synchronize", "sm_batch_autotune", "sm_ho_step", "sm_leakage",
-            "sm_adjoint_step"]
+            "sm_adjoint_step", "sm_set_quadrant_moments"]
 
 
 class SMError(RuntimeError):
@@ -69,7 +70,7 @@ class StepParams(ctypes.Structure):
                 ("pcg_rtol", ctypes.c_double), ("elim_rtol", ctypes.c_double),
                 ("T_floor", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("max_inner", ctypes.c_int), ("max_pcg", ctypes.c_int),
-                ("max_elim", ctypes.c_int)]
+                ("max_elim", ctypes.c_int), ("method", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
@@ -153,6 +154,7 @@ def load():
         "sm_batch_synchronize": [P],
         "sm_batch_autotune": [P, PP, PP, PP, PP, I],
         "sm_ho_step": [P, P, P, P, P, P, D, I, ctypes.POINTER(ctypes.c_int)],
+        "sm_set_quadrant_moments": [P, P],
         "sm_leakage": [P, P, PD],
         "sm_adjoint_step": [P, P, P, P, P, P, P, P, P, P, P, D, I,
                             ctypes.POINTER(ctypes.c_int)],
@@ -391,6 +393,16 @@ class Problem:
                               ctypes.byref(params) if params is not None else None,
                               ctypes.byref(st)))
         return _stats(st)
+
+    def set_quadrant_moments(self, qmom):
+        """Register a [cell][node][4][6] FP64 buffer filled by every later
+        sweep with per-quadrant moments (None drops it)."""
+        _check(load().sm_set_quadrant_moments(self._h, _ptr(qmom)))
+
+    def new_quadrant_moments(self):
+        i = self.info
+        return self._torch.zeros((i["n_cells"], i["n_nodes"], 4, 6), dtype=self._torch.float64,
+                                 device="cuda")
 
     # ---------------------------------------------------------------- time steps / adjoint
     def ho_step(self, scale, cv, T, I_prev, I_next, tol: float = 1e-13,

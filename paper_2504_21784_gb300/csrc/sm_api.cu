@@ -229,9 +229,12 @@ sm_status sweep_pass(sm_problem *p, const void *I_prev, void *I_out, double *mom
     ++p->epoch;
     smk::SweepArgs a = make_args(p, I_prev, I_out);
     a.reverse = reverse;
+    const bool qm = p->qmom_dev != nullptr && p->dim == 2 && !reverse;
+    a.qmom = qm ? 1 : 0;
     if (p->dim == 2) {
         SM_CUDA(cudaMemsetAsync(p->d_ctrl, 0, 2 * sizeof(unsigned int), s));
-        SM_CUDA(cudaMemsetAsync(p->d_mom_acc, 0, (size_t)p->ncell * 36 * p->rsize, s));
+        SM_CUDA(cudaMemsetAsync(p->d_mom_acc, 0, (size_t)(qm ? 4 : 1) * p->ncell * 36 * p->rsize,
+                                s));
         const int grid = std::min(a.n_tasks, p->resident);
         SM_CUDA(smk::launch_sweep2d(p, a, grid, s));
     } else {
@@ -242,7 +245,8 @@ sm_status sweep_pass(sm_problem *p, const void *I_prev, void *I_out, double *mom
     if (mom || clo) {
         double *m = mom ? mom : p->d_mom_tmp;
         if (p->dim == 2)
-            SM_CUDA(smk::launch_reduce(p, p->d_mom_acc, 1, m, clo, s));
+            SM_CUDA(smk::launch_reduce(p, p->d_mom_acc, qm ? 4 : 1, m, clo, s,
+                                       qm ? p->qmom_dev : nullptr));
         else
             SM_CUDA(smk::launch_reduce(p, p->d_part, p->NQ * p->NWT, m, clo, s));
         p->launches++;
@@ -687,6 +691,21 @@ sm_status sm_synchronize(sm_problem *p) {
             return fail(SM_ERR_TIMEOUT, "a wavefront wait exceeded its time limit");
         return fail(SM_ERR_NONPHYSICAL, "non-positive or non-finite temperature");
     }
+    return SM_OK;
+}
+
+sm_status sm_set_quadrant_moments(sm_problem *p, double *qmom_dev) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    if (p->dim != 2) return fail(SM_ERR_UNSUPPORTED, "quadrant moments are 2D only");
+    if (p->batch_owned) return fail(SM_ERR_INVALID_ARG, "this problem belongs to a batch");
+    SM_CUDA(cudaStreamSynchronize(p->stream));
+    if (qmom_dev && !p->qmom_acc4) {
+        // the moment accumulator becomes [quadrant][cell][36]
+        sm_status st = dev_alloc(&p->d_mom_acc, (size_t)4 * p->ncell * 36 * p->rsize, nullptr);
+        if (st) return st;
+        p->qmom_acc4 = true;
+    }
+    p->qmom_dev = qmom_dev;
     return SM_OK;
 }
 

@@ -53,6 +53,7 @@ struct SweepArgs {
     int fault_skip_publish;  // test hook: strip 0 never publishes
     int reverse;             // 2D: sweep -Omega for every direction; I_prev / I_out of
                              // geometric quadrant q live at quadrant q^2 (adjoint sweeps)
+    int qmom;                // 2D: accumulate moments per quadrant, [q][cell][36]
 };
 
 // Many problems in one persistent 2D sweep launch (sweep2d_batch_kernel).
@@ -81,7 +82,7 @@ cudaError_t launch_closures_from_T(const sm_problem *p, const double *mom, const
 cudaError_t launch_sweep2d(const sm_problem *p, const SweepArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_sweep1d(const sm_problem *p, const SweepArgs &a, cudaStream_t s);
 cudaError_t launch_reduce(const sm_problem *p, const void *part, int n_part, double *mom,
-                          double *clo, cudaStream_t s);
+                          double *clo, cudaStream_t s, double *qmom = nullptr);
 cudaError_t launch_pack(const sm_problem *p, const double *canon, void *packed, int unpack,
                         cudaStream_t s);
 int sweep2d_max_resident(const sm_problem *p, int W, int S, size_t *smem_out);
@@ -158,6 +159,8 @@ struct sm_problem {
     size_t workspace_bytes = 0;
     sm_lo_state *lo = nullptr;
     sm_adj_state *adj = nullptr;
+    double *qmom_dev = nullptr;  // per-quadrant moments [cell][node][4][6] filled by each sweep
+    bool qmom_acc4 = false;      // moment accumulator sized for four quadrants
     bool batch_owned = false;    // member of an sm_batch: swept only by the batch
     bool ctrl_borrowed = false;  // d_ctrl belongs to the batch
 };

@@ -60,6 +60,7 @@ struct Geo {
     double lx, ly;          // A_EF volume: m / h
     double px, py, bx, by;  // interior penalty (c alpha / 2) wf, boundary c alpha wf
     double c3;              // c / 3
+    double alpha;           // Eq. alpha of the S_N set
 };
 
 struct Cell {
@@ -343,6 +344,102 @@ __device__ bool grid_sums(double (&v)[K], double *part, unsigned int *count) {
 }
 
 // ---------------------------------------------------------------------------
+// Consistent-method sources (Sec. 4, consistent; the discrete residual
+// approach applied to the lumped upwind DG transport): for each node, the
+// difference between the LDG face terms evaluated with the high-order moments
+// and the moments of the upwind face terms of the transport discretization.
+// With F^pm_n = sum_{Omega.n >< 0} w (Omega.n) I and Pi^pm_n = sum_{Omega.n >< 0}
+// w Omega (Omega.n) I from the per-quadrant moments qm[node][q][phi, F_x, F_y,
+// Pi_xx, Pi_xy, Pi_yy], and K1 / K2 the low / high side of an interior face:
+//   R0(K1 node) = w_f [F.n(K1) + (c alpha/2)(E_K1 - E_K2) - F^+_n(K1) - F^-_n(K2)],
+//   R0(K2 node) = -R0(K1 node),
+//   R1(K1 node) = w_f [(c/3) n E_K2 - Pi^+_n(K1) - Pi^-_n(K2)],  R1(K2 node) = -R1(K1 node),
+// and on the boundary (outward n, inflow moments J_in, Pi_in of the side):
+//   R0 = w_f [J_in + alpha phi - F^+_n],  R1 = w_f [(c/3) n E - Pi^+_n - Pi_in].
+struct Half {
+    double Fp, Fm, Pp[2], Pm[2];
+};
+
+// half-range moments of node j for the normal +x (axis 0) or +y (axis 1):
+// F^pm = sum_{Omega_axis >< 0} w Omega_axis I and the x, y components of
+// Pi^pm = sum_{Omega_axis >< 0} w Omega Omega_axis I; quadrants in the
+// canonical order (+,+), (-,+), (-,-), (+,-)
+__device__ __forceinline__ Half half_pos_axis(const double *__restrict__ qm, int j, int axis) {
+    const double *q = qm + (size_t)j * 24;
+    const int p0 = 0, p1 = axis == 0 ? 3 : 1;  // quadrants with Omega along +axis
+    const int m0 = axis == 0 ? 1 : 2, m1 = axis == 0 ? 2 : 3;
+    const int kF = 1 + axis;                    // F_x or F_y
+    const int kP0 = axis == 0 ? 3 : 4, kP1 = axis == 0 ? 4 : 5;  // (Pi_xx, Pi_xy) or (Pi_xy, Pi_yy)
+    Half h;
+    h.Fp = q[p0 * 6 + kF] + q[p1 * 6 + kF];
+    h.Fm = q[m0 * 6 + kF] + q[m1 * 6 + kF];
+    h.Pp[0] = q[p0 * 6 + kP0] + q[p1 * 6 + kP0];
+    h.Pp[1] = q[p0 * 6 + kP1] + q[p1 * 6 + kP1];
+    h.Pm[0] = q[m0 * 6 + kP0] + q[m1 * 6 + kP0];
+    h.Pm[1] = q[m0 * 6 + kP1] + q[m1 * 6 + kP1];
+    return h;
+}
+
+__device__ __forceinline__ double qm_tot(const double *__restrict__ qm, int j, int k) {
+    const double *q = qm + (size_t)j * 24;
+    return q[k] + q[6 + k] + q[12 + k] + q[18 + k];
+}
+
+__global__ void __launch_bounds__(BLOCK)
+consistent_kernel(Geo G, const double *__restrict__ qm, const double *__restrict__ jin,
+                  const double *__restrict__ pin, double *__restrict__ R0,
+                  double *__restrict__ R1f) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= G.ncell) return;
+    const Cell C = cell_of(G, k);
+    const double ca2 = 0.5 * G.c * G.alpha, c3 = G.c3, ic = 1.0 / G.c;
+    for (int nloc = 0; nloc < 4; ++nloc) {
+        const int a = nloc & 1, b = nloc >> 1;
+        const int j = k * 4 + nloc;
+        const double phi = qm_tot(qm, j, 0), Ej = phi * ic;
+        double r0 = 0.0, r1[2] = {0.0, 0.0};
+        for (int axis = 0; axis < 2; ++axis) {
+            const bool high = axis == 0 ? a == 1 : b == 1;  // node on the +axis face of its cell
+            const bool has_nb = axis == 0 ? (high ? C.R : C.L) : (high ? C.T : C.B);
+            const double wf = axis == 0 ? G.wfx : G.wfy;
+            const int side = axis == 0 ? (high ? 1 : 0) : (high ? 3 : 2);
+            const Half hj = half_pos_axis(qm, j, axis);
+            if (has_nb) {
+                const int nbcell = axis == 0 ? (high ? k + 1 : k - 1) : (high ? k + G.nx : k - G.nx);
+                const int nbloc = axis == 0 ? ((1 - a) + 2 * b) : (a + 2 * (1 - b));
+                const int jn = nbcell * 4 + nbloc;
+                const Half hn = half_pos_axis(qm, jn, axis);
+                const double En = qm_tot(qm, jn, 0) * ic;
+                // K1 = low side, K2 = high side of the face; n = +axis
+                const Half &h1 = high ? hj : hn, &h2 = high ? hn : hj;
+                const double E1 = high ? Ej : En, E2 = high ? En : Ej;
+                const double F1n = qm_tot(qm, high ? j : jn, 1 + axis);
+                const double q0 = wf * (F1n + ca2 * (E1 - E2) - h1.Fp - h2.Fm);
+                const double qx = wf * ((axis == 0 ? c3 * E2 : 0.0) - h1.Pp[0] - h2.Pm[0]);
+                const double qy = wf * ((axis == 1 ? c3 * E2 : 0.0) - h1.Pp[1] - h2.Pm[1]);
+                const double sgn = high ? 1.0 : -1.0;  // the K1 node takes +, the K2 node -
+                r0 += sgn * q0;
+                r1[0] += sgn * qx;
+                r1[1] += sgn * qy;
+            } else {
+                // boundary, outward normal s * e_axis; the half ranges of
+                // -e_axis are minus the opposite half ranges of +e_axis
+                const double sn = high ? 1.0 : -1.0;
+                const double Fp = high ? hj.Fp : -hj.Fm;
+                const double Px = high ? hj.Pp[0] : -hj.Pm[0];
+                const double Py = high ? hj.Pp[1] : -hj.Pm[1];
+                r0 += wf * (jin[side] + G.alpha * phi - Fp);
+                r1[0] += wf * ((axis == 0 ? c3 * sn * Ej : 0.0) - Px - pin[side * 2]);
+                r1[1] += wf * ((axis == 1 ? c3 * sn * Ej : 0.0) - Py - pin[side * 2 + 1]);
+            }
+        }
+        R0[j] = r0;
+        R1f[(size_t)j * 2] = r1[0];
+        R1f[(size_t)j * 2 + 1] = r1[1];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // E* = phi / c and F* = F from the moments of the previous step's intensity
 // (the high-order time-edge sources of Sec. 6.1).  One thread per node.
 __global__ void timeedge_kernel(int N, int D, int nm, double inv_c, const double *__restrict__ mom,
@@ -360,8 +457,9 @@ __global__ void timeedge_kernel(int N, int D, int nm, double inv_c, const double
 //             - int_Gamma0 [v] . {T n}   (Sec. 4, independent closures).
 __global__ void __launch_bounds__(BLOCK)
 prepare_kernel(Geo G, const double *__restrict__ clo, int nc, double inv_cdt,
-               const double *__restrict__ Fstar, double *__restrict__ iaF, double *__restrict__ bF,
-               double *__restrict__ ub, Scalars *sc) {
+               const double *__restrict__ Fstar, const double *__restrict__ R1f,
+               double *__restrict__ iaF, double *__restrict__ bF, double *__restrict__ ub,
+               Scalars *sc) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) sc->elim_max = 0;
     if (t >= G.N) return;
@@ -383,15 +481,20 @@ prepare_kernel(Geo G, const double *__restrict__ clo, int nc, double inv_cdt,
         double r = G.m * (D == 1 ? cl[6] : cl[9 + d]);
         r += (2 * a - 1) * G.lx * (Tt(node(k, 0, b), d, 0) + Tt(node(k, 1, b), d, 0));
         if (D == 2) r += (2 * b - 1) * G.ly * (Tt(node(k, a, 0), d, 1) + Tt(node(k, a, 1), d, 1));
-        if (a == 1 && ix + 1 < G.nx)
-            r -= G.wfx * 0.5 * (Tt(t, d, 0) + Tt(node(k + 1, 0, b), d, 0));
-        else if (a == 0 && ix > 0)
-            r += G.wfx * 0.5 * (Tt(t, d, 0) + Tt(node(k - 1, 1, b), d, 0));
-        if (D == 2) {
-            if (b == 1 && iy + 1 < G.ny)
-                r -= G.wfy * 0.5 * (Tt(t, d, 1) + Tt(node(k + G.nx, a, 0), d, 1));
-            else if (b == 0 && iy > 0)
-                r += G.wfy * 0.5 * (Tt(t, d, 1) + Tt(node(k - G.nx, a, 1), d, 1));
+        if (R1f) {
+            r += R1f[(size_t)t * D + d];  // consistent method: face and boundary corrections
+        } else {
+            // independent method: - int_Gamma0 [v] . {T n}
+            if (a == 1 && ix + 1 < G.nx)
+                r -= G.wfx * 0.5 * (Tt(t, d, 0) + Tt(node(k + 1, 0, b), d, 0));
+            else if (a == 0 && ix > 0)
+                r += G.wfx * 0.5 * (Tt(t, d, 0) + Tt(node(k - 1, 1, b), d, 0));
+            if (D == 2) {
+                if (b == 1 && iy + 1 < G.ny)
+                    r -= G.wfy * 0.5 * (Tt(t, d, 1) + Tt(node(k + G.nx, a, 0), d, 1));
+                else if (b == 0 && iy > 0)
+                    r += G.wfy * 0.5 * (Tt(t, d, 1) + Tt(node(k - G.nx, a, 1), d, 1));
+            }
         }
         const double bv = G.m * inv_cdt * Fstar[(size_t)t * D + d] + r;
         bF[(size_t)t * D + d] = bv;
@@ -409,7 +512,8 @@ __global__ void __launch_bounds__(BLOCK)
 newton_setup_kernel(Geo G, const double *__restrict__ clo, int nc, double a_rad, double dt,
                     const double *__restrict__ T, const double *__restrict__ Tstar,
                     const double *__restrict__ cv, const double *__restrict__ Estar,
-                    const double *__restrict__ jin2, const double *__restrict__ iaF,
+                    const double *__restrict__ jin2, const double *__restrict__ R0,
+                    const double *__restrict__ iaF,
                     const double *__restrict__ ub, const double *__restrict__ E,
                     double *__restrict__ aE_out, double *__restrict__ idiag, double *__restrict__ x,
                     double *__restrict__ r, double *__restrict__ z, double *__restrict__ p0,
@@ -438,17 +542,25 @@ newton_setup_kernel(Geo G, const double *__restrict__ clo, int nc, double a_rad,
             aE[n] = G.m * G.c * (sE + inv_cdt - nu * sE);
             bE[n] = G.m * (sP * B0 + nu * qT0 + Es[n] / dt);
         }
-        // Marshak boundary: -2 int_Gamma_b u F_in, F_in the incoming partial current
+        if (R0) {
+            // consistent method: face and boundary corrections (the inflow included)
+            double r0[NN];
+            ldc<NN>(R0, k, r0);
 #pragma unroll
-        for (int b = 0; b < NN / 2; ++b) {
-            if (!C.L) bE[2 * b] += G.wfx * jin2[0];
-            if (!C.R) bE[2 * b + 1] += G.wfx * jin2[1];
-        }
-        if constexpr (NN == 4) {
+            for (int n = 0; n < NN; ++n) bE[n] += r0[n];
+        } else {
+            // Marshak boundary: -2 int_Gamma_b u F_in, F_in the incoming partial current
 #pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                if (!C.B) bE[a] += G.wfy * jin2[2];
-                if (!C.T) bE[a + 2] += G.wfy * jin2[3];
+            for (int b = 0; b < NN / 2; ++b) {
+                if (!C.L) bE[2 * b] += G.wfx * jin2[0];
+                if (!C.R) bE[2 * b + 1] += G.wfx * jin2[1];
+            }
+            if constexpr (NN == 4) {
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    if (!C.B) bE[a] += G.wfy * jin2[2];
+                    if (!C.T) bE[a + 2] += G.wfy * jin2[3];
+                }
             }
         }
         double efu[NN], dg[NN], q[NN], e[NN], rv[NN], zv[NN], idg[NN];
@@ -668,6 +780,9 @@ struct sm_lo_state {
     double *aE, *iaF, *bF, *ub, *idiag, *x, *r, *z, *pb[2], *q, *Estar, *Fstar, *Tstar, *Tin, *Ein;
     double *part = nullptr;
     double *jin2 = nullptr;     // [4] 2 |F_in| per side
+    double *R0 = nullptr, *R1f = nullptr;  // consistent-method sources [node], [node][2]
+    double *qmom_int = nullptr;            // per-quadrant moments used by sm_step
+    double *jinc = nullptr, *pinc = nullptr;  // inflow moments J_in [4], Pi_in [4][2]
     double *sigma = nullptr;    // sigma_g(T^k) of the running step
     double *clo = nullptr;      // closures when the caller passes none
     smk::lo::Scalars *sc = nullptr;
@@ -719,6 +834,7 @@ Geo make_geo(const sm_problem *p) {
     G.ky = G.c3 * G.ly;
     G.fx = G.c3 * G.wfx;
     G.fy = G.c3 * G.wfy;
+    G.alpha = p->alpha;
     const double ca = G.c * p->alpha;
     G.px = 0.5 * ca * G.wfx;
     G.py = 0.5 * ca * G.wfy;
@@ -803,6 +919,14 @@ sm_status lo_ensure(sm_problem *p) {
     const size_t nblk = (size_t)std::max(w.nblk_cell, w.nblk_node);
     LO_CUDA(cudaMalloc(&w.part, sizeof(double) * 3 * nblk));
     LO_CUDA(cudaMalloc(&w.jin2, sizeof(double) * 4));
+    if (p->dim == 2) {
+        LO_CUDA(cudaMalloc(&w.R0, sizeof(double) * (size_t)N * 3));
+        w.R1f = w.R0 + N;
+        LO_CUDA(cudaMalloc(&w.qmom_int, sizeof(double) * (size_t)N * 24));
+        LO_CUDA(cudaMalloc(&w.jinc, sizeof(double) * 12));
+        w.pinc = w.jinc + 4;
+        p->workspace_bytes += sizeof(double) * ((size_t)N * 27 + 12);
+    }
     LO_CUDA(cudaMalloc(&w.sigma, sizeof(double) * (size_t)p->G * p->ncell));
     LO_CUDA(cudaMalloc(&w.clo, sizeof(double) * (size_t)N * p->nc));
     LO_CUDA(cudaMalloc(&w.sc, sizeof(smk::lo::Scalars)));
@@ -827,6 +951,24 @@ sm_status lo_ensure(sm_problem *p) {
         jin2[s] = 2.0 * acc * Iin;
     }
     LO_CUDA(cudaMemcpy(w.jin2, jin2, sizeof(jin2), cudaMemcpyHostToDevice));
+    if (p->dim == 2) {
+        // consistent method: J_in = sum_{Omega.n<0} w |Omega.n| I_in and
+        // Pi_in = sum_{Omega.n<0} w Omega (Omega.n) I_in per side
+        double jp[12] = {0};
+        for (int s = 0; s < 4; ++s) {
+            const double Tb = p->desc.T_bdr[s];
+            const double Iin = Tb > 0 ? p->desc.a * p->desc.c * Tb * Tb * Tb * Tb / (4.0 * PI) : 0.0;
+            for (int d = 0; d < p->nd; ++d) {
+                const double on = p->omx[d] * nrm[s][0] + p->omy[d] * nrm[s][1];
+                if (on < 0) {
+                    jp[s] += p->w[d] * -on * Iin;
+                    jp[4 + 2 * s] += p->w[d] * p->omx[d] * on * Iin;
+                    jp[4 + 2 * s + 1] += p->w[d] * p->omy[d] * on * Iin;
+                }
+            }
+        }
+        LO_CUDA(cudaMemcpy(w.jinc, jp, sizeof(jp), cudaMemcpyHostToDevice));
+    }
     return p->dim == 2 ? build_graph<4>(p, w) : build_graph<2>(p, w);
 }
 
@@ -841,6 +983,8 @@ sm_status read_scalars(sm_problem *p) {
 sm_status check_params(const sm_step_params &prm) {
     if (prm.max_outer < 1 || prm.max_inner < 1 || prm.max_pcg < 1 || prm.max_elim < 1)
         return lo_fail(SM_ERR_INVALID_ARG, "iteration limits must be >= 1");
+    if (prm.method != SM_METHOD_INDEPENDENT && prm.method != SM_METHOD_CONSISTENT)
+        return lo_fail(SM_ERR_INVALID_ARG, "method must be SM_METHOD_INDEPENDENT or CONSISTENT");
     if (!(prm.eps_outer >= 0) || !(prm.eps_inner >= 0) || !(prm.pcg_rtol > 0) ||
         !(prm.elim_rtol > 0) || !(prm.T_floor > 0))
         return lo_fail(SM_ERR_INVALID_ARG,
@@ -855,19 +999,28 @@ sm_status check_params(const sm_step_params &prm) {
 template <int NN>
 sm_status lo_solve(sm_problem *p, const double *clo, const double *Tstar, const double *cv,
                    double *T, double *E, double *F, const sm_step_params &prm,
-                   sm_step_stats *st) {
+                   sm_step_stats *st, const double *qmom) {
     sm_lo_state &w = *p->lo;
     const Geo G = make_geo(p);
     cudaStream_t s = p->stream;
     const double dt = p->desc.dt, a = p->desc.a;
+    const double *R0 = nullptr, *R1f = nullptr;
+    if (qmom) {  // consistent method (2D)
+        smk::lo::consistent_kernel<<<w.nblk_cell, BLOCK, 0, s>>>(G, qmom, w.jinc, w.pinc, w.R0,
+                                                                 w.R1f);
+        LO_CUDA(cudaGetLastError());
+        p->launches++;
+        R0 = w.R0;
+        R1f = w.R1f;
+    }
     smk::lo::prepare_kernel<<<w.nblk_node, BLOCK, 0, s>>>(G, clo, p->nc, 1.0 / (G.c * dt),
-                                                          w.Fstar, w.iaF, w.bF, w.ub, w.sc);
+                                                          w.Fstar, R1f, w.iaF, w.bF, w.ub, w.sc);
     LO_CUDA(cudaGetLastError());
     p->launches++;
     double d1 = -1.0;
     for (int it = 1; it <= prm.max_inner; ++it) {
         smk::lo::newton_setup_kernel<NN><<<w.nblk_cell, BLOCK, 0, s>>>(
-            G, clo, p->nc, a, dt, T, Tstar, cv, w.Estar, w.jin2, w.iaF, w.ub, E, w.aE, w.idiag,
+            G, clo, p->nc, a, dt, T, Tstar, cv, w.Estar, w.jin2, R0, w.iaF, w.ub, E, w.aE, w.idiag,
             w.x, w.r, w.z, w.pb[0], prm.pcg_rtol, prm.max_pcg, w.part, w.sc);
         LO_CUDA(cudaGetLastError());
         LO_CUDA(cudaGraphLaunch(w.exec, s));
@@ -902,9 +1055,10 @@ sm_status lo_solve(sm_problem *p, const double *clo, const double *Tstar, const 
 }
 
 sm_status run_lo(sm_problem *p, const double *clo, const double *Tstar, const double *cv,
-                 double *T, double *E, double *F, const sm_step_params &prm, sm_step_stats *st) {
-    return p->dim == 2 ? lo_solve<4>(p, clo, Tstar, cv, T, E, F, prm, st)
-                       : lo_solve<2>(p, clo, Tstar, cv, T, E, F, prm, st);
+                 double *T, double *E, double *F, const sm_step_params &prm, sm_step_stats *st,
+                 const double *qmom) {
+    return p->dim == 2 ? lo_solve<4>(p, clo, Tstar, cv, T, E, F, prm, st, qmom)
+                       : lo_solve<2>(p, clo, Tstar, cv, T, E, F, prm, st, nullptr);
 }
 
 sm_status check_lo_problem(sm_problem *p) {
@@ -922,7 +1076,7 @@ void lo_free(sm_problem *p) {
     if (w.exec) cudaGraphExecDestroy(w.exec);
     if (w.graph) cudaGraphDestroy(w.graph);
     if (w.cap) cudaStreamDestroy(w.cap);
-    void *bufs[] = {w.buf, w.part, w.jin2, w.sigma, w.clo, w.sc};
+    void *bufs[] = {w.buf, w.part, w.jin2, w.sigma, w.clo, w.sc, w.R0, w.qmom_int, w.jinc};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (w.h_sc) cudaFreeHost(w.h_sc);
@@ -944,6 +1098,7 @@ void sm_default_step_params(sm_step_params *prm) {
     prm->max_inner = 30;
     prm->max_pcg = 5000;
     prm->max_elim = 40;
+    prm->method = SM_METHOD_INDEPENDENT;
 }
 
 sm_status sm_loworder_newton(sm_problem *p, const double *closures_dev, const double *T_star_dev,
@@ -967,8 +1122,17 @@ sm_status sm_loworder_newton(sm_problem *p, const double *closures_dev, const do
         w.N, w.D, p->nm, 1.0 / p->desc.c, moments_star_dev, w.Estar, w.Fstar);
     LO_CUDA(cudaGetLastError());
     p->launches++;
+    const double *qmom = nullptr;
+    if (prm.method == SM_METHOD_CONSISTENT) {
+        if (p->dim != 2) return lo_fail(SM_ERR_UNSUPPORTED, "the consistent method is 2D only");
+        if (!p->qmom_dev)
+            return lo_fail(SM_ERR_INVALID_ARG,
+                           "the consistent method needs the per-quadrant moments of the last "
+                           "sweep: register a buffer with sm_set_quadrant_moments and sweep");
+        qmom = p->qmom_dev;
+    }
     sm_step_stats st{};
-    LO_TRY(run_lo(p, closures_dev, T_star_dev, cv_dev, T_dev, E_dev, F_dev, prm, &st));
+    LO_TRY(run_lo(p, closures_dev, T_star_dev, cv_dev, T_dev, E_dev, F_dev, prm, &st, qmom));
     st.converged = 1;
     if (stats) *stats = st;
     return SM_OK;
@@ -994,6 +1158,16 @@ sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, 
     cudaStream_t s = p->stream;
     const int N = w.N;
     double *clo = closures_dev ? closures_dev : w.clo;
+    const bool consistent = prm.method == SM_METHOD_CONSISTENT;
+    if (consistent && p->dim != 2)
+        return lo_fail(SM_ERR_UNSUPPORTED, "the consistent method is 2D only");
+    double *qmom_saved = p->qmom_dev;
+    const double *qmom = nullptr;
+    if (consistent) {
+        // the sweeps of this step also leave their per-quadrant moments
+        qmom = qmom_saved ? qmom_saved : w.qmom_int;
+        LO_TRY(sm_set_quadrant_moments(p, const_cast<double *>(qmom)));
+    }
     // opacities frozen at T^k for the whole step (Sec. 3, Rem. opacity)
     LO_TRY(sm_opacity(p, T_dev, scale_dev, w.sigma));
     smk::lo::timeedge_kernel<<<w.nblk_node, BLOCK, 0, s>>>(N, w.D, p->nm, 1.0 / p->desc.c,
@@ -1010,7 +1184,7 @@ sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, 
         // high-order solve with the current T: emission, sweep, moments, closures
         LO_TRY(sm_sweep(p, T_dev, w.sigma, I_prev_dev, I_next_dev, moments_dev, clo));
         LO_TRY(sm_synchronize(p));
-        LO_TRY(run_lo(p, clo, w.Tstar, cv_dev, T_dev, E_dev, F_dev, prm, &st));
+        LO_TRY(run_lo(p, clo, w.Tstar, cv_dev, T_dev, E_dev, F_dev, prm, &st, qmom));
         smk::lo::outer_change_kernel<<<w.nblk_node, BLOCK, 0, s>>>(N, T_dev, E_dev, w.Tin, w.Ein,
                                                                   w.part, w.sc);
         LO_CUDA(cudaGetLastError());
@@ -1025,6 +1199,7 @@ sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, 
             break;
         }
     }
+    if (consistent && !qmom_saved) LO_TRY(sm_set_quadrant_moments(p, nullptr));
     if (stats) *stats = st;
     return SM_OK;
 }

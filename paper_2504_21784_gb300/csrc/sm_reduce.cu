@@ -11,11 +11,14 @@
 
 namespace smk {
 
+// qmom (2D, sets = quadrants): per-quadrant phi, F_x, F_y and the second
+// moments Pi = sum w Omega Omega I (Pi_xx, Pi_xy, Pi_yy) per node, for the
+// consistent method's half-range closures.
 template <typename RT>
 __global__ void reduce_kernel(int dim, int nnodes_total, int nm, int nsets, size_t set_stride,
                               double inv_c, const RT *__restrict__ part,
                               const double *__restrict__ gray, double *__restrict__ mom,
-                              double *__restrict__ clo) {
+                              double *__restrict__ clo, double *__restrict__ qmom) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;  // (cell, node)
     if (t >= nnodes_total) return;
     double acc[9];
@@ -25,6 +28,16 @@ __global__ void reduce_kernel(int dim, int nnodes_total, int nm, int nsets, size
     for (int s = 0; s < nsets; ++s) {
         const RT *ps = pp + (size_t)s * set_stride;
         for (int m = 0; m < nm; ++m) acc[m] += (double)ps[m];
+        if (qmom) {
+            double *o = qmom + ((size_t)t * 4 + s) * 6;
+            const double ph = (double)ps[0];
+            o[0] = ph;
+            o[1] = (double)ps[1];
+            o[2] = (double)ps[2];
+            o[3] = (double)ps[3] + ph / 3.0;
+            o[4] = (double)ps[4];
+            o[5] = (double)ps[5] + ph / 3.0;
+        }
     }
     if (mom) {
         for (int m = 0; m < nm; ++m) mom[(size_t)t * nm + m] = acc[m];
@@ -59,17 +72,19 @@ __global__ void reduce_kernel(int dim, int nnodes_total, int nm, int nsets, size
 }
 
 cudaError_t launch_reduce(const sm_problem *p, const void *part, int n_part, double *mom,
-                          double *clo, cudaStream_t s) {
+                          double *clo, cudaStream_t s, double *qmom) {
     const int n = p->ncell * p->nn;
     const int threads = 128;
     const size_t stride = (size_t)n * p->nm;
     const double inv_c = 1.0 / p->desc.c;
     if (p->prec == 32)
         reduce_kernel<float><<<(n + threads - 1) / threads, threads, 0, s>>>(
-            p->dim, n, p->nm, n_part, stride, inv_c, (const float *)part, p->d_gray, mom, clo);
+            p->dim, n, p->nm, n_part, stride, inv_c, (const float *)part, p->d_gray, mom, clo,
+            qmom);
     else
         reduce_kernel<double><<<(n + threads - 1) / threads, threads, 0, s>>>(
-            p->dim, n, p->nm, n_part, stride, inv_c, (const double *)part, p->d_gray, mom, clo);
+            p->dim, n, p->nm, n_part, stride, inv_c, (const double *)part, p->d_gray, mom, clo,
+            qmom);
     return cudaGetLastError();
 }
 

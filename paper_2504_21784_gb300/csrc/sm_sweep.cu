@@ -530,7 +530,7 @@ __device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay,
                 d2 = fma(c[t], e4[t], d2);
             }
         }
-        RT *ac = acc + (size_t)cell * 36;
+        RT *ac = acc + ((size_t)(A.qmom ? q * A.ncell : 0) + cell) * 36;
         atomicAdd(ac + m1, d1);
         if (lane < 4) atomicAdd(ac + m2, d2);
         __syncwarp();  // Mb is rewritten by the next row
