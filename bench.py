@@ -188,7 +188,8 @@ def cpu_baseline(cfg, budget_s: float = 8.0):
                       f"({upd} updates, {dt:.1f} s), FP64 oracle sweep only, OpenMP over pairs"}
 
 
-def converged_steps(sm, W, cfg, prec: int, n_steps: int, stream, autotune: bool = True):
+def converged_steps(sm, W, cfg, prec: int, n_steps: int, stream, autotune: bool = True,
+                    method: int = 0):
     """Seconds per converged time step (Algorithm 1 through sm_step) from the
     equilibrium initial state T = T0, I = B_g(T0)/4pi (whose moments are
     phi = a c T0^4, F = 0), with the paper's iteration controls.  One
@@ -219,7 +220,8 @@ def converged_steps(sm, W, cfg, prec: int, n_steps: int, stream, autotune: bool 
         for k in range(1 + n_steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            st = prob.step(scale, cv, T, E, F, mom, I[k % 2], I[(k + 1) % 2])
+            st = prob.step(scale, cv, T, E, F, mom, I[k % 2], I[(k + 1) % 2],
+                           params=sm.step_params(method=method))
             torch.cuda.synchronize()
             if k >= 1:
                 secs.append(time.perf_counter() - t0)
@@ -246,9 +248,13 @@ def step_metric(sm, W, cfgs, n_steps: int, stream):
     for cfg in cfgs:
         r32, T32 = converged_steps(sm, W, cfg, 32, n_steps, stream)
         r64, T64 = converged_steps(sm, W, cfg, 64, n_steps, stream)
+        c32, Tc32 = converged_steps(sm, W, cfg, 32, n_steps, stream, method=sm.METHOD_CONSISTENT)
         res[cfg.name] = {"fp32": r32, "fp64": r64,
                          "fp64_over_fp32_time": r64["s_per_step"] / r32["s_per_step"],
                          "fp32_vs_fp64_T_rel": float(np.abs(T32 - T64).max() / np.abs(T64).max()),
+                         "consistent_fp32": c32,
+                         "consistent_vs_independent_T_rel":
+                             float(np.abs(Tc32 - T32).max() / np.abs(T32).max()),
                          "steps_timed": n_steps, "warmup_steps": 1,
                          "state": "equilibrium start T0 = %g, steps 2..%d" % (cfg.T0, n_steps + 1)}
     return res
