@@ -607,6 +607,10 @@ void orc_moments(int dim, int ncell, int ndir, const double *omx, const double *
 {
     const int nn = (dim == 1) ? 2 : 4;
     const int nm = (dim == 1) ? 5 : 9;
+    /* cells are independent: the threads split them, each sum keeps its order */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (int k = 0; k < ncell; ++k) {
         for (int n = 0; n < nn; ++n) {
             orc_kahan acc[9];

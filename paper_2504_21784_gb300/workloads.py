@@ -224,6 +224,33 @@ def intensity_random(n_dir: int, n_groups: int, n_cells: int, n_nodes: int, seed
     return scale * np.exp(rng.standard_normal((n_dir, n_groups, n_cells, n_nodes)) - 2.0)
 
 
+def in_precision(x: np.ndarray, precision: int) -> np.ndarray:
+    """x as a sweep of the given precision stores it: rounded to the nearest
+    FP32 value for the FP32 sweep, unchanged for FP64 (as float64 either way),
+    so that both sides of a comparison read the same previous intensity."""
+    x = np.asarray(x, dtype=np.float64)
+    return x.astype(np.float32).astype(np.float64) if precision == 32 else x
+
+
+class SeparableIntensity:
+    """A seeded previous intensity I[d][g][cell][node] = s a_d b_g c_{cell,node}
+    with lognormal factors, exactly representable in FP32 (so the FP32 and
+    FP64 sweeps read the same values), produced one direction at a time so that
+    full-size workloads never need the whole array on the host."""
+
+    def __init__(self, n_dir: int, n_groups: int, n_cells: int, n_nodes: int, seed: int,
+                 scale: float = 0.05):
+        rng = np.random.default_rng(seed)
+        self.a = scale * np.exp(0.3 * rng.standard_normal(n_dir))
+        self.b = np.exp(0.5 * rng.standard_normal(n_groups))
+        self.c = np.exp(0.5 * rng.standard_normal((n_cells, n_nodes)) - 2.0)
+        self.n_dir = n_dir
+
+    def direction(self, d: int) -> np.ndarray:
+        """[g][cell][node] of direction d."""
+        return in_precision(self.a[d] * np.multiply.outer(self.b, self.c), 32)
+
+
 @dataclasses.dataclass
 class BatchMember:
     cfg: Config

@@ -45,7 +45,6 @@ class Case:
 
 def build_case(sm, cfg: W.Config, precision: int, seed: int = 0, with_prev: bool = True,
                **tiling) -> Case:
-    import torch
     prob = sm.Problem.from_config(cfg, precision, **tiling)
     nn = cfg.n_nodes
     T = W.temperature_wave(cfg, seed=seed + 1)
@@ -56,8 +55,7 @@ def build_case(sm, cfg: W.Config, precision: int, seed: int = 0, with_prev: bool
     if with_prev:
         Ic = W.intensity_random(cfg.n_dir, cfg.n_groups, cfg.n_cells, nn, seed=seed + 3,
                                 scale=0.05)
-        packed = prob.pack(torch.from_numpy(Ic).cuda())
-        I_prev = prob.unpack(packed).cpu().numpy()  # what the sweep really reads
+        I_prev = W.in_precision(Ic, precision)  # what the sweep really reads
     q = O.emission(cfg.edges, cfg.a, cfg.c, T, sigma)
     infl = O.inflow(cfg.edges, cfg.a, cfg.c, cfg.T_bdr)
     return Case(cfg, prob, T, scale, sigma, I_prev, q, infl, omx, omy, w)
@@ -88,3 +86,46 @@ def run_oracle(case: Case):
     mom = O.moments(cfg.dim, case.omx, case.omy, case.w, case.sigma, I)
     clo = O.closures(cfg.dim, cfg.edges, cfg.c, case.sigma, case.T, mom)
     return I, mom, clo
+
+
+def field_err(got, ref, scale_field=None, axis=None):
+    """max |got - ref| / max|scale| (per slice along leading axes when axis given)."""
+    sc = ref if scale_field is None else scale_field
+    d = np.abs(np.asarray(got) - np.asarray(ref))
+    if axis is None:
+        return float(d.max() / max(np.abs(sc).max(), 1e-300))
+    red = tuple(range(axis, d.ndim))
+    return float(np.max(d.max(axis=red) / np.maximum(np.abs(sc).max(axis=red), 1e-300)))
+
+
+def parity_errors(cfg, gpu, ref):
+    """Per-field relative errors of (intensity, moments, closures); intensity
+    None skips its two entries."""
+    Ig, mg, cg = gpu
+    Io, mo, co = ref
+    dim = cfg.dim
+    e = {}
+    if Ig is not None:
+        e["I"] = field_err(Ig, Io, axis=2)  # per (d, g) slice
+        e["I_elem"] = rel_err(Ig, Io, 1e-12)
+    if dim == 2:
+        phi, se = 0, 6
+        groups = {"phi": [0], "F,T": [1, 2, 3, 4, 5], "SE": [6], "SF": [7, 8]}
+        scale_of = {"phi": 0, "F,T": 0, "SE": 6, "SF": 6}
+        sE, sF, sP, corr, E_, vec = 6, 7, 8, [9, 10], 0, [1, 2, 3, 4, 5]
+    else:
+        phi, se = 0, 3
+        groups = {"phi": [0], "F,T": [1, 2], "SE": [3], "SF": [4]}
+        scale_of = {"phi": 0, "F,T": 0, "SE": 3, "SF": 3}
+        sE, sF, sP, corr, E_, vec = 3, 4, 5, [6], 0, [1, 2]
+    for name, ms in groups.items():
+        e["mom_" + name] = max(field_err(mg[..., m], mo[..., m], mo[..., scale_of[name]])
+                               for m in ms)
+    e["clo_E"] = field_err(cg[..., E_], co[..., E_])
+    e["clo_F,T"] = max(field_err(cg[..., j], co[..., j], co[..., E_] * cfg.c) for j in vec)
+    e["clo_sigE"] = field_err(cg[..., sE] * mo[..., phi], co[..., sE] * mo[..., phi],
+                               mo[..., se])
+    e["clo_sigF,P"] = max(rel_err(cg[..., j], co[..., j], 0.0) for j in (sF, sP))
+    e["clo_corr"] = max(field_err(cg[..., j], co[..., j], co[..., sF] * mo[..., phi])
+                        for j in corr)
+    return e

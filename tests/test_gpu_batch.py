@@ -27,13 +27,20 @@ MEMBERS = [  # uneven meshes, 32/64/128 directions, group counts giving GW = 2, 
 ]
 
 
+def _host_inputs(cfg, seed, precision):
+    """Seeded host inputs of member `seed`: nodal T, per-cell scale and I^k as
+    the sweep of the given precision stores it."""
+    T = W.temperature_wave(cfg, seed=seed)
+    scale = W.blocky_two_material(cfg.nx, cfg.ny, seed=100 + seed, block=4, thick=50.0)
+    Ic = W.intensity_random(cfg.n_dir, cfg.n_groups, cfg.n_cells, 4, seed=seed + 3, scale=0.05)
+    return T, scale, W.in_precision(Ic, precision)
+
+
 def _inputs(sm, prob, cfg, seed):
     import torch
-    T = torch.from_numpy(W.temperature_wave(cfg, seed=seed)).cuda()
-    scale = torch.from_numpy(W.blocky_two_material(cfg.nx, cfg.ny, seed=100 + seed, block=4,
-                                                   thick=50.0)).cuda()
-    sigma = prob.opacity(T, scale)
-    Ic = W.intensity_random(cfg.n_dir, cfg.n_groups, cfg.n_cells, 4, seed=seed + 3, scale=0.05)
+    T, scale, Ic = _host_inputs(cfg, seed, prob.info["precision"])
+    T = torch.from_numpy(T).cuda()
+    sigma = prob.opacity(T, torch.from_numpy(scale).cuda())
     Ip = prob.pack(torch.from_numpy(Ic).cuda())
     return T, sigma, Ip
 
@@ -85,8 +92,8 @@ def test_batch_fp64_matches_oracle(gpu_lib):
     cfgs = MEMBERS[:4]
     b, T, S, Ip, Io, M, C = _run_batch(sm, cfgs, 64)
     for i, cfg in enumerate(cfgs):
-        Tn, Sn = T[i].cpu().numpy(), S[i].cpu().numpy()
-        Ipc = b.members[i].unpack(Ip[i]).cpu().numpy()
+        Tn, scale, Ipc = _host_inputs(cfg, i, 64)
+        Sn = O.opacity(cfg.opacity_kind, cfg.opacity_alpha, cfg.edges, Tn, scale)
         omx, omy, w = O.quadrature(2, cfg.n_polar, cfg.n_azim)
         q = O.emission(cfg.edges, cfg.a, cfg.c, Tn, Sn)
         infl = O.inflow(cfg.edges, cfg.a, cfg.c, cfg.T_bdr)

@@ -54,12 +54,14 @@ def test_quadrant_moments_match_oracle(gpu_lib):
     m1 = prob.new_moments()
     prob.sweep(cu(T), cu(sigma), Ip, Io, m1)
     prob.synchronize()
-    I = prob.unpack(Io).cpu().numpy()
     omx, omy, w = O.quadrature(2, cfg.n_polar, cfg.n_azim)
+    q = O.emission(cfg.edges, cfg.a, cfg.c, T, sigma)
+    infl = O.inflow(cfg.edges, cfg.a, cfg.c, cfg.T_bdr)
+    I = O.sweep(2, cfg.nx, cfg.ny, cfg.extent, omx, omy, sigma, 1.0 / (cfg.c * cfg.dt), q, Ik, infl)
     ref = OC.quadrant_moments(omx, omy, w, I)
     got = qm.cpu().numpy()
     for k in range(6):
-        assert _field(got[..., k], ref[..., k], scale=ref[..., 0]) < 1e-13
+        assert _field(got[..., k], ref[..., k], scale=ref[..., 0]) < 1e-11
     # registering the per-quadrant moments leaves the ordinary moments unchanged
     assert _field(m1.cpu().numpy(), m0.cpu().numpy(), scale=m0.cpu().numpy()[..., 0]) < 1e-13
     prob.set_quadrant_moments(None)
@@ -132,8 +134,8 @@ def _gpu_step(sm, cfg, precision, T0, scale, cv, I0, method, tight=True):
     prob = sm.Problem.from_config(cfg, precision)
     cu = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
     omx, omy, w = O.quadrature(2, cfg.n_polar, cfg.n_azim)
-    Ip = prob.pack(cu(I0))
-    I0r = prob.unpack(Ip).cpu().numpy()
+    I0r = W.in_precision(I0, precision)
+    Ip = prob.pack(cu(I0r))
     sigma0 = O.opacity(cfg.opacity_kind, cfg.opacity_alpha, cfg.edges, T0, scale)
     mom = cu(O.moments(2, omx, omy, w, sigma0, I0r))
     T, E, F = cu(T0), prob.new_nodal(), prob.new_flux()

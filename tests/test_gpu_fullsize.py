@@ -1,0 +1,226 @@
+"""Parity at the full workload sizes, in the launch configuration the
+benchmark times (autotuned tiling), against the FP64 oracle element by
+element.  The oracle sweeps one direction (all its groups) at a time and sums
+the moments direction by direction (they are linear in the intensity), so the
+host never holds more than one direction's intensity; the GPU keeps its whole
+unpacked result on the device and hands over one direction at a time.
+
+* 2D multigroup, 256x256 cells, 128 directions, 64 groups: FP32 and FP64
+  sweeps (every intensity, moment and closure) and the opacity kernel;
+* 2D gray two-material channel, 128x128 cells, 128 directions: the same;
+* batched: the 64 uneven problems in one persistent launch (FP32), every
+  member against the oracle;
+* adjoint, 128x128 cells, 64 directions, 16 groups, 20 steps with
+  checkpointing: gradient against central differences of the GPU forward.
+
+The previous intensity is a seeded separable field, exactly representable in
+FP32, so both sweep precisions read the same input and one oracle pass serves
+both.  Tolerances as in test_gpu_parity.py: 1e-11 (FP64), 1e-5 (FP32), per
+field.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2504_21784_gb300 import workloads as W
+
+from _cases import parity_errors
+
+pytestmark = pytest.mark.gpu
+
+TOL = {64: 1e-11, 32: 1e-5}
+
+
+def _cu(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _canonical_on_device(cfg, gen):
+    """The whole previous intensity [d][g][cell][node] on the device, filled one
+    direction at a time from the host generator."""
+    import torch
+    canon = torch.empty((cfg.n_dir, cfg.n_groups, cfg.n_cells, cfg.n_nodes),
+                        dtype=torch.float64, device="cuda")
+    for d in range(cfg.n_dir):
+        canon[d].copy_(torch.from_numpy(gen.direction(d)))
+    return canon
+
+
+def _oracle_by_direction(cfg, T, sigma, gen, on_direction):
+    """The oracle sweep of every (direction, group), one direction at a time;
+    on_direction(d, I_d) sees each direction's [g][cell][node] intensity.
+    Returns the oracle's moments and closures."""
+    omx, omy, w = O.quadrature(2, cfg.n_polar, cfg.n_azim)
+    q = O.emission(cfg.edges, cfg.a, cfg.c, T, sigma)
+    infl = O.inflow(cfg.edges, cfg.a, cfg.c, cfg.T_bdr)
+    inv_cdt = 1.0 / (cfg.c * cfg.dt)
+    G = cfg.n_groups
+    mom = np.zeros((cfg.n_cells, 4, 9))
+    for d in range(cfg.n_dir):
+        I_d = O.sweep_pairs(2, cfg.nx, cfg.ny, cfg.extent, omx, omy, sigma, inv_cdt, q,
+                            gen.direction(d), infl, [(d, g) for g in range(G)])
+        mom += O.moments(2, omx[d:d + 1], omy[d:d + 1], w[d:d + 1], sigma, I_d[None])
+        on_direction(d, I_d)
+    clo = O.closures(2, cfg.edges, cfg.c, sigma, T, mom)
+    return mom, clo
+
+
+class _IntensityErrors:
+    """Largest per-(direction, group) field error of each GPU result."""
+
+    def __init__(self, runs):
+        self.runs = runs                      # {label: unpacked device intensity}
+        self.err = {k: 0.0 for k in runs}
+
+    def __call__(self, d, I_d):
+        scale = np.maximum(np.abs(I_d).max(axis=(1, 2)), 1e-300)
+        for k, Iu in self.runs.items():
+            diff = np.abs(Iu[d].cpu().numpy() - I_d).max(axis=(1, 2))
+            self.err[k] = max(self.err[k], float((diff / scale).max()))
+
+
+def _gpu_sweep(sm, cfg, precision, T, sigma, canon, scale=None):
+    """One sweep in the benchmark's launch configuration: autotuned tiling,
+    previous intensity read, moments and closures fused."""
+    prob = sm.Problem.from_config(cfg, precision)
+    Td, Sd = _cu(T), _cu(sigma)
+    sig_g = prob.opacity(Td, _cu(scale)).cpu().numpy() if scale is not None else None
+    Ip = prob.pack(canon)
+    Io = prob.empty_intensity()
+    prob.autotune(Td, Sd, Ip, Io, reps=1)
+    mom, clo = prob.new_moments(), prob.new_closures()
+    prob.sweep(Td, Sd, Ip, Io, mom, clo)
+    prob.synchronize()
+    tiling = {k: prob.info[k] for k in ("strip_width", "prefetch_rows", "groups_per_warp",
+                                        "n_tasks")}
+    del Ip
+    Iu = prob.unpack(Io)
+    del Io
+    out = (Iu, mom.cpu().numpy(), clo.cpu().numpy(), sig_g, tiling)
+    prob.close()
+    return out
+
+
+def _full_sweep_parity(sm, cfg, seed):
+    import torch
+    T = W.temperature_wave(cfg)
+    scale = W.scale_field(cfg)
+    sigma = O.opacity(cfg.opacity_kind, cfg.opacity_alpha, cfg.edges, T, scale)
+    gen = W.SeparableIntensity(cfg.n_dir, cfg.n_groups, cfg.n_cells, 4, seed=seed)
+    canon = _canonical_on_device(cfg, gen)
+    runs, rest = {}, {}
+    for prec in (32, 64):
+        Iu, mg, cg, sig_g, tiling = _gpu_sweep(sm, cfg, prec, T, sigma, canon, scale)
+        runs[prec] = Iu
+        rest[prec] = (mg, cg, sig_g, tiling)
+    del canon
+    torch.cuda.empty_cache()
+    ierr = _IntensityErrors(runs)
+    mo, co = _oracle_by_direction(cfg, T, sigma, gen, ierr)
+    for prec in (32, 64):
+        mg, cg, sig_g, tiling = rest[prec]
+        e = parity_errors(cfg, (None, mg, cg), (None, mo, co))
+        e["I"] = ierr.err[prec]
+        e["opacity"] = float(np.max(np.abs(sig_g - sigma) / sigma))
+        print(f"[{cfg.name} fp{prec} {tiling}] " +
+              "  ".join(f"{k} {v:.2e}" for k, v in e.items()))
+        assert e.pop("opacity") < 1e-13
+        bad = {k: v for k, v in e.items() if not v <= TOL[prec]}
+        assert not bad, f"fp{prec} parity above {TOL[prec]}: {bad}"
+    del runs
+    torch.cuda.empty_cache()
+
+
+def test_multigroup_full_size_parity(gpu_lib):
+    """256x256 cells x 128 directions x 64 groups (5.4e8 updates)."""
+    _full_sweep_parity(gpu_lib, W.multigroup_2d(), seed=31)
+
+
+def test_gray_channel_full_size_parity(gpu_lib):
+    """128x128 cells x 128 directions, walls 1e4 times thicker than the channel."""
+    _full_sweep_parity(gpu_lib, W.gray_channel_2d(), seed=32)
+
+
+def test_batched_full_size_parity(gpu_lib):
+    """The 64 uneven problems (32^2..256^2 cells, 32..128 directions, 8..32
+    groups) in one persistent launch with the autotuned batch tiling, FP32;
+    every member against the oracle."""
+    import torch
+    sm = gpu_lib
+    members = W.batched_2d()
+    cfgs = [m.cfg for m in members]
+    b = sm.Batch(cfgs, 32)
+    T, S, Ip, Io, M, C, inputs = [], [], [], [], [], [], []
+    for i, (mem, h) in enumerate(zip(members, b.members)):
+        Tn = W.temperature_wave(mem.cfg)
+        sig = O.opacity(mem.cfg.opacity_kind, mem.cfg.opacity_alpha, mem.cfg.edges, Tn, mem.scale)
+        gen = W.SeparableIntensity(mem.cfg.n_dir, mem.cfg.n_groups, mem.cfg.n_cells, 4,
+                                   seed=200 + i)
+        canon = _canonical_on_device(mem.cfg, gen)
+        Ip.append(h.pack(canon))
+        del canon
+        T.append(_cu(Tn))
+        S.append(_cu(sig))
+        Io.append(h.empty_intensity())
+        M.append(h.new_moments())
+        C.append(h.new_closures())
+        inputs.append((Tn, sig, gen))
+    torch.cuda.empty_cache()
+    b.autotune(T, S, Ip, Io, reps=1)
+    b.sweep(T, S, Ip, Io, M, C)
+    b.synchronize()
+    info = b.info()
+    worst = {}
+    for i, (cfg, h) in enumerate(zip(cfgs, b.members)):
+        Tn, sig, gen = inputs[i]
+        ierr = _IntensityErrors({32: h.unpack(Io[i])})
+        mo, co = _oracle_by_direction(cfg, Tn, sig, gen, ierr)
+        e = parity_errors(cfg, (None, M[i].cpu().numpy(), C[i].cpu().numpy()), (None, mo, co))
+        e["I"] = ierr.err[32]
+        for k, v in e.items():
+            worst[k] = max(worst.get(k, 0.0), v)
+        bad = {k: v for k, v in e.items() if not v <= TOL[32]}
+        assert not bad, f"member {i} ({cfg.name}) parity above {TOL[32]}: {bad}"
+        del ierr
+        torch.cuda.empty_cache()
+    print(f"[batched x{len(cfgs)} strip {info['strip_width']} prefetch {info['prefetch_rows']}] "
+          + "  ".join(f"{k} {v:.2e}" for k, v in worst.items()))
+    b.close()
+
+
+def test_adjoint_full_size_matches_central_differences(gpu_lib):
+    """The adjoint workload from the warm start (T0 = 0.3), 20 steps with
+    checkpoints every sqrt(20) steps: dJ/ds_K against central differences
+    (h = 1e-4 s_K) of the GPU forward on 4 seeded cells among those whose
+    sensitivity is at least 1e-3 of the largest (smaller ones move J by less
+    than its FP64 rounding)."""
+    import torch
+    from paper_2504_21784_gb300 import adjoint as A
+    sm = gpu_lib
+    cfg = W.adjoint_2d_warm()
+    prob = sm.Problem.from_config(cfg, 64)
+    T0 = torch.full((cfg.n_cells, 4), cfg.T0, dtype=torch.float64, device="cuda")
+    cv = torch.full((cfg.n_cells, 4), cfg.cv, dtype=torch.float64, device="cuda")
+    s = _cu(W.scale_field(cfg))
+    st = A.LeakageSetup(prob, cv, T0, A.equilibrium_intensity(prob, T0), cfg.steps, 0,
+                        tol=1e-13, max_iter=5000, dt=cfg.dt)
+    s.requires_grad_(True)
+    J = A.leakage(s, st)
+    J.backward()
+    g = s.grad.detach().cpu().numpy()
+    cand = np.flatnonzero(np.abs(g) >= 1e-3 * np.abs(g).max())
+    cells = np.random.default_rng(7).choice(cand, min(4, cand.size), replace=False)
+    errs = []
+    with torch.no_grad():
+        for k in cells:
+            h = 1e-4 * s[k].item()
+            sp, sm_ = s.detach().clone(), s.detach().clone()
+            sp[k] += h
+            sm_[k] -= h
+            fd = (A.leakage(sp, st).item() - A.leakage(sm_, st).item()) / (2 * h)
+            errs.append(abs(fd - g[k]) / abs(g[k]))
+    print(f"adjoint {cfg.name}: J {J.item():.6e}, {cand.size} candidate cells, "
+          f"fd rel err max {max(errs):.2e}")
+    assert max(errs) < 1e-4
+    prob.close()

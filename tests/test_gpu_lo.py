@@ -257,8 +257,8 @@ def test_step_matches_oracle(gpu_lib, name):
     omx, omy, w = O.quadrature(dim, cfg.n_polar, cfg.n_azim)
     cu = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
     Ik = W.intensity_random(cfg.n_dir, G, ncell, nn, seed=12, scale=0.05)
+    Ik = W.in_precision(Ik, precision)  # what the sweep reads in its precision
     Ip = prob.pack(cu(Ik))
-    Ik = prob.unpack(Ip).cpu().numpy()  # what the sweep reads in its precision
     sigma_k = O.opacity(cfg.opacity_kind, cfg.opacity_alpha, cfg.edges, Tk, scale)
     mom_k = O.moments(dim, omx, omy, w, sigma_k, Ik)
     n_outer = 3

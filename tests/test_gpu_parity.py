@@ -19,7 +19,7 @@ import pytest
 import oracle as O
 from paper_2504_21784_gb300 import workloads as W
 
-from _cases import build_case, config, rel_err, run_gpu, run_oracle
+from _cases import build_case, config, parity_errors, rel_err, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -49,51 +49,11 @@ CASES_1D = {
 }
 
 
-def _field_err(got, ref, scale_field=None, axis=None):
-    """max |got - ref| / max|scale| (per slice along leading axes when axis given)."""
-    sc = ref if scale_field is None else scale_field
-    d = np.abs(np.asarray(got) - np.asarray(ref))
-    if axis is None:
-        return float(d.max() / max(np.abs(sc).max(), 1e-300))
-    red = tuple(range(axis, d.ndim))
-    return float(np.max(d.max(axis=red) / np.maximum(np.abs(sc).max(axis=red), 1e-300)))
-
-
-def parity_errors(case, gpu, ref):
-    Ig, mg, cg = gpu
-    Io, mo, co = ref
-    dim = case.cfg.dim
-    e = {}
-    e["I"] = _field_err(Ig, Io, axis=2)  # per (d, g) slice
-    e["I_elem"] = rel_err(Ig, Io, 1e-12)
-    if dim == 2:
-        phi, se = 0, 6
-        groups = {"phi": [0], "F,T": [1, 2, 3, 4, 5], "SE": [6], "SF": [7, 8]}
-        scale_of = {"phi": 0, "F,T": 0, "SE": 6, "SF": 6}
-        sE, sF, sP, corr, E_, vec = 6, 7, 8, [9, 10], 0, [1, 2, 3, 4, 5]
-    else:
-        phi, se = 0, 3
-        groups = {"phi": [0], "F,T": [1, 2], "SE": [3], "SF": [4]}
-        scale_of = {"phi": 0, "F,T": 0, "SE": 3, "SF": 3}
-        sE, sF, sP, corr, E_, vec = 3, 4, 5, [6], 0, [1, 2]
-    for name, ms in groups.items():
-        e["mom_" + name] = max(_field_err(mg[..., m], mo[..., m], mo[..., scale_of[name]])
-                               for m in ms)
-    e["clo_E"] = _field_err(cg[..., E_], co[..., E_])
-    e["clo_F,T"] = max(_field_err(cg[..., j], co[..., j], co[..., E_] * case.cfg.c) for j in vec)
-    e["clo_sigE"] = _field_err(cg[..., sE] * mo[..., phi], co[..., sE] * mo[..., phi],
-                               mo[..., se])
-    e["clo_sigF,P"] = max(rel_err(cg[..., j], co[..., j], 0.0) for j in (sF, sP))
-    e["clo_corr"] = max(_field_err(cg[..., j], co[..., j], co[..., sF] * mo[..., phi])
-                        for j in corr)
-    return e
-
-
 def _check_all(case, precision, label):
     rtol = TOL[precision]
     Ig, mg, cg, _ = run_gpu(case)
     ref = run_oracle(case)
-    e = parity_errors(case, (Ig, mg, cg), ref)
+    e = parity_errors(case.cfg, (Ig, mg, cg), ref)
     print(f"[{label} fp{precision}] " + "  ".join(f"{k} {v:.2e}" for k, v in e.items()) +
           f"  ({case.prob.info['n_tasks']} tasks, {case.prob.info['n_strips']} strips)")
     bad = {k: v for k, v in e.items() if k != "I_elem" and not v <= rtol}
