@@ -235,24 +235,36 @@ __device__ __forceinline__ float rcp_fast(float x) {
 }
 __device__ __forceinline__ double rcp_fast(double x) { return __drcp_rn(x); }
 
+// Correctly rounded product and sum that the compiler never contracts into an
+// FMA: every rounding of the cell solve is fixed by the source, so the same
+// problem gives bit-identical intensities from every kernel it is compiled
+// into (single-problem and batched launches).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
 __host__ __device__ inline size_t stage_bytes(int rsize, int GW, int GSLOT) {
     return (size_t)GW * 32 * 4 * rsize + (size_t)GSLOT * SREC * rsize;
 }
 // ---------------------------------------------------------------------------
 // Shared-memory layout of one 2D sweep CTA: W warps, each owning S stages of
 // stg bytes (prefetched I^k and source records), an x-face ring for ring_gw
-// slots and the moment buffers; after them W*S mbarriers and two row
-// counters per warp.
+// slots and the per-lane moment weights; after them W*S mbarriers and two
+// row counters per warp.  A row's stage, once its cell solves have read it,
+// doubles as that row's moment transpose buffer ([8][MROW]) before the
+// prefetch of a later row overwrites it, so a stage is at least that large.
 struct Layout2D {
-    size_t stg, wsz, ring_off, mb_off;
+    size_t stg, wsz, ring_off, wt_off;
 };
 
 __host__ __device__ inline Layout2D layout2d(int rsize, int S, size_t stg, int ring_gw) {
     Layout2D L;
-    L.stg = stg;
-    L.ring_off = (size_t)S * stg;
-    L.mb_off = L.ring_off + (size_t)RING * ring_gw * 32 * 2 * rsize;
-    L.wsz = L.mb_off + (size_t)(8 + 6) * MROW * rsize;
+    const size_t mb = ((size_t)8 * MROW * rsize + 15) & ~(size_t)15;
+    L.stg = stg > mb ? stg : mb;
+    L.ring_off = (size_t)S * L.stg;
+    L.wt_off = L.ring_off + (size_t)RING * ring_gw * 32 * 2 * rsize;
+    L.wsz = L.wt_off + (size_t)6 * MROW * rsize;
     return L;
 }
 
@@ -273,11 +285,13 @@ size_t sweep2d_stage_bytes(int prec, int GW, int GSLOT) {
     return stage_bytes(prec == 32 ? 4 : 8, GW, GSLOT);
 }
 
-// One task of the 2D sweep: strip sr of warp task wg (quadrant, direction
+// One task of the 2D sweep: strip sr of warp task wg (quadrant Q, direction
 // block, group block) of the problem A, every warp of the CTA sweeping one
-// cell column of the strip from the upwind to the downwind edge.
-template <typename RT, int GW, class Args>
-__device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay, const int task,
+// cell column of the strip from the upwind to the downwind edge.  The
+// quadrant is a template parameter so that the upwind/downwind roles of the
+// four nodes are compile-time register indices.
+template <typename RT, int GW, int Q, class Args>
+__device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &Lay, const int task,
                                              unsigned char *smem_raw, uint64_t *bars,
                                              volatile int *rows_done, volatile int *cons,
                                              volatile int *s_abort, uint32_t &phase,
@@ -291,8 +305,7 @@ __device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay,
     const size_t stg = Lay.stg, wsz = Lay.wsz, ring_off = Lay.ring_off;
     unsigned char *wbase = smem_raw + (size_t)w * wsz;
     uint64_t *mybars = bars + (size_t)w * S;
-    RT *Mb = reinterpret_cast<RT *>(wbase + Lay.mb_off);  // [8][MROW]: s_n, ss_n per lane
-    RT *Wt = Mb + 8 * MROW;                               // [6][MROW]: weights per lane
+    RT *Wt = reinterpret_cast<RT *>(wbase + Lay.wt_off);  // [6][MROW]: weights per lane
     const RT *src = static_cast<const RT *>(A.src);
     const RT *inflow = static_cast<const RT *>(A.inflow);
     const RT *Ip = static_cast<const RT *>(A.I_prev);
@@ -310,9 +323,10 @@ __device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay,
     const int vrow2 = k2 < 6 ? 3 : 7, wrow2 = k2 < 6 ? k2 : k2 - 6;
     const int NWG = A.NQ * A.NWT;
     const int sr = task / NWG, wg = task - sr * NWG;
-    const int q = wg / A.NWT, wt = wg - q * A.NWT;
-    const int sx = (q == 0 || q == 3) ? 1 : -1;
-    const int sy = (q < 2) ? 1 : -1;
+    constexpr int q = Q;
+    const int wt = wg - q * A.NWT;
+    constexpr int sx = (Q == 0 || Q == 3) ? 1 : -1;
+    constexpr int sy = (Q < 2) ? 1 : -1;
     const int strip = sx > 0 ? sr : A.NS - 1 - sr;
     const int x0 = strip * W;
     const int ws = min(W, nx - x0);
@@ -321,6 +335,7 @@ __device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay,
     const int db = wt / A.NGB, gb = wt - db * A.NGB;
     const LaneConst &L = A.lanes[(q * A.DB + db) * 32 + lane];
     const RT mu = (RT)L.mu, eta = (RT)L.eta;
+    const RT two_mu = mul_rn((RT)2, mu), two_eta = mul_rn((RT)2, eta);
 #pragma unroll
     for (int k = 0; k < 6; ++k) Wt[k * MROW + lane] = (RT)L.wm[k];
     const int g_lo = L.g_lo;
@@ -335,9 +350,9 @@ __device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay,
         Y1[gw] = by;
         bx[gw] = inflow[side_x * A.Gp + g];
     }
-    const int au = sx > 0 ? 0 : 1, bu = sy > 0 ? 0 : 1;
-    const int nuu = au + 2 * bu, ndu = (1 - au) + 2 * bu;
-    const int nud = au + 2 * (1 - bu), ndd = (1 - au) + 2 * (1 - bu);
+    constexpr int au = sx > 0 ? 0 : 1, bu = sy > 0 ? 0 : 1;
+    constexpr int nuu = au + 2 * bu, ndu = (1 - au) + 2 * bu;
+    constexpr int nud = au + 2 * (1 - bu), ndd = (1 - au) + 2 * (1 - bu);
     // memory quadrant of the intensities: the geometric one, or its reverse
     // for adjoint sweeps (the transposed operator of Omega is that of -Omega)
     const size_t wtbase = ((size_t)(A.reverse ? (q ^ 2) : q) * A.NWT + wt) * A.ncell;
@@ -438,24 +453,24 @@ __device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay,
 #pragma unroll
                 for (int n = 0; n < 4; ++n) Sn[n] = fma(inv_cdt, Ik[n], Sn[n]);
             }
-            const RT iA = rcp_fast(sgt + mu + eta);
-            const RT m = mu * iA, e = eta * iA;
-            const RT ruu = (Sn[nuu] + two * (mu * X0[gw] + eta * Y0[gw])) * iA;
-            const RT rdu = fma(two * eta, Y1[gw], Sn[ndu]) * iA;
-            const RT rud = fma(two * mu, X1[gw], Sn[nud]) * iA;
-            const RT rdd = Sn[ndd] * iA;
+            const RT iA = rcp_fast(add_rn(add_rn(sgt, mu), eta));
+            const RT m = mul_rn(mu, iA), e = mul_rn(eta, iA);
+            const RT ruu = mul_rn(fma(two, fma(mu, X0[gw], mul_rn(eta, Y0[gw])), Sn[nuu]), iA);
+            const RT rdu = mul_rn(fma(two_eta, Y1[gw], Sn[ndu]), iA);
+            const RT rud = mul_rn(fma(two_mu, X1[gw], Sn[nud]), iA);
+            const RT rdd = mul_rn(Sn[ndd], iA);
             const RT P = fma(m, m, fma(e, e, (RT)1));
-            const RT z = two * m * e;
-            const RT iD = rcp_fast(fma(P, P, -z * z));
-            const RT wuu = fma(P, ruu, z * rdd);
-            const RT wdu = fma(P, rdu, -z * rud);
-            const RT wud = fma(P, rud, -z * rdu);
-            const RT wdd = fma(P, rdd, z * ruu);
+            const RT z = mul_rn(mul_rn(two, m), e);
+            const RT iD = rcp_fast(fma(P, P, -mul_rn(z, z)));
+            const RT wuu = fma(P, ruu, mul_rn(z, rdd));
+            const RT wdu = fma(P, rdu, -mul_rn(z, rud));
+            const RT wud = fma(P, rud, -mul_rn(z, rdu));
+            const RT wdd = fma(P, rdd, mul_rn(z, ruu));
             RT I4[4];
-            I4[nuu] = (wuu - m * wdu - e * wud) * iD;
-            I4[ndu] = (wdu + m * wuu - e * wdd) * iD;
-            I4[nud] = (wud - m * wdd + e * wuu) * iD;
-            I4[ndd] = (wdd + m * wud + e * wdu) * iD;
+            I4[nuu] = mul_rn(fma(-e, wud, fma(-m, wdu, wuu)), iD);
+            I4[ndu] = mul_rn(fma(-e, wdd, fma(m, wuu, wdu)), iD);
+            I4[nud] = mul_rn(fma(e, wuu, fma(-m, wdd, wud)), iD);
+            I4[ndd] = mul_rn(fma(e, wdu, fma(m, wud, wdd)), iD);
             st4_stream(io + (size_t)gw * 128, I4);
             X0[gw] = I4[ndu];  // x-outflow -> next column
             X1[gw] = I4[ndd];
@@ -463,17 +478,10 @@ __device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay,
             Y1[gw] = I4[ndd];
 #pragma unroll
             for (int n = 0; n < 4; ++n) {
-                s4[n] += I4[n];
+                s4[n] = add_rn(s4[n], I4[n]);
                 ss4[n] = fma(sgm, I4[n], ss4[n]);
             }
         }
-        // the stage is free: prefetch row jj + S into it
-        __syncwarp();
-        if (lane == 0 && jj + S < ny) {
-            fence_proxy_async_smem();
-            issue(jj + S);
-        }
-        if (jj + S < ny) issued = jj + S;
         // (d) hand the x-outflow downwind
         if (w < ws - 1) {
             ok = smem_wait_geq(cons + w, jj + 1 - RING, A.ctrl, A.timeout_ns, s_abort);
@@ -508,15 +516,19 @@ __device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay,
                 st_release(myflag, ep | (unsigned long long)(jj + 1));
             }
         }
-        // (e) moments of this cell: transpose through shared memory, then
-        // lane m forms moment m = n*9 + k as a dot product over the 32 lanes
+        // (e) moments of this cell: transpose through shared memory (this
+        // row's stage, read by every lane by now), then lane m forms moment
+        // m = n*9 + k as a dot product over the 32 lanes
+        RT *Mb = reinterpret_cast<RT *>(wbase + (size_t)st * stg);  // [8][MROW]
+        __syncwarp();
 #pragma unroll
         for (int n = 0; n < 4; ++n) {
             Mb[n * MROW + lane] = s4[n];
             Mb[(4 + n) * MROW + lane] = ss4[n];
         }
         __syncwarp();
-        RT d1 = 0, d2 = 0;
+        // four partial sums per dot product: dependent chains of 8, not 32
+        RT d1p[4] = {0, 0, 0, 0}, d2p[4] = {0, 0, 0, 0};
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             RT a[4], b[4], c[4], e4[4];
@@ -526,14 +538,23 @@ __device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay,
             lds4(Wt + wrow2 * MROW + 4 * i, e4);
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                d1 = fma(a[t], b[t], d1);
-                d2 = fma(c[t], e4[t], d2);
+                d1p[t] = fma(a[t], b[t], d1p[t]);
+                d2p[t] = fma(c[t], e4[t], d2p[t]);
             }
         }
+        const RT d1 = (d1p[0] + d1p[1]) + (d1p[2] + d1p[3]);
+        const RT d2 = (d2p[0] + d2p[1]) + (d2p[2] + d2p[3]);
         RT *ac = acc + ((size_t)(A.qmom ? q * A.ncell : 0) + cell) * 36;
         atomicAdd(ac + m1, d1);
         if (lane < 4) atomicAdd(ac + m2, d2);
-        __syncwarp();  // Mb is rewritten by the next row
+        // the stage is free: prefetch row jj + S into it (the proxy fence
+        // orders this warp's reads and writes of it before the copy)
+        __syncwarp();
+        if (lane == 0 && jj + S < ny) {
+            fence_proxy_async_smem();
+            issue(jj + S);
+        }
+        if (jj + S < ny) issued = jj + S;
     }
     if (!ok) {
         // wait (bounded) for this warp's copies still in flight, then leave
@@ -546,6 +567,34 @@ __device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay,
             phase ^= 1u << st;
         }
         *s_abort = 1;
+    }
+}
+
+template <typename RT, int GW, class Args>
+__device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay, const int task,
+                                             unsigned char *smem_raw, uint64_t *bars,
+                                             volatile int *rows_done, volatile int *cons,
+                                             volatile int *s_abort, uint32_t &phase,
+                                             const unsigned long long epoch) {
+    const int NWG = A.NQ * A.NWT;
+    const int q = (task % NWG) / A.NWT;
+    switch (q) {
+        case 0:
+            sweep2d_task_q<RT, GW, 0>(A, Lay, task, smem_raw, bars, rows_done, cons, s_abort,
+                                      phase, epoch);
+            break;
+        case 1:
+            sweep2d_task_q<RT, GW, 1>(A, Lay, task, smem_raw, bars, rows_done, cons, s_abort,
+                                      phase, epoch);
+            break;
+        case 2:
+            sweep2d_task_q<RT, GW, 2>(A, Lay, task, smem_raw, bars, rows_done, cons, s_abort,
+                                      phase, epoch);
+            break;
+        default:
+            sweep2d_task_q<RT, GW, 3>(A, Lay, task, smem_raw, bars, rows_done, cons, s_abort,
+                                      phase, epoch);
+            break;
     }
 }
 
@@ -646,14 +695,15 @@ __global__ void __launch_bounds__(512) sweep2d_batch_kernel(const __grid_constan
 // ---------------------------------------------------------------------------
 // 1D: one warp per warp task sweeps the whole line (the paper's 1D problems
 // have at most a few thousand cells); per-warp partial moments.
-template <typename RT, int GW>
-__global__ void __launch_bounds__(256) sweep1d_kernel(const SweepArgs A) {
+// Q: the direction half (0: mu > 0, 1: mu < 0), a template parameter so that
+// the upwind/downwind node roles are compile-time register indices.
+template <typename RT, int GW, int Q>
+__device__ __forceinline__ void sweep1d_warp(const SweepArgs &A, const int gwarp) {
     using R2 = typename V2<RT>::t;
     const int lane = threadIdx.x & 31;
-    const int gwarp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    if (gwarp >= A.NQ * A.NWT) return;
-    const int q = gwarp / A.NWT, wt = gwarp - q * A.NWT;
-    const int sx = q == 0 ? 1 : -1;
+    constexpr int q = Q;
+    const int wt = gwarp - q * A.NWT;
+    constexpr int sx = q == 0 ? 1 : -1;
     const int nx = A.nx, ncell = A.ncell;
     const int db = wt / A.NGB, gb = wt - db * A.NGB;
     const LaneConst &L = A.lanes[(q * A.DB + db) * 32 + lane];
@@ -674,7 +724,7 @@ __global__ void __launch_bounds__(256) sweep1d_kernel(const SweepArgs A) {
         gidx[gw] = gb * (GW * A.LG) + gw * A.LG + L.g_lo;
         X[gw] = inflow[side * A.Gp + gidx[gw]];
     }
-    const int au = sx > 0 ? 0 : 1;
+    constexpr int au = sx > 0 ? 0 : 1;
     const size_t wtbase = (size_t)(q * A.NWT + wt) * ncell;
     for (int i = 0; i < nx; ++i) {
         const int cell = sx > 0 ? i : nx - 1 - i;
@@ -725,6 +775,16 @@ __global__ void __launch_bounds__(256) sweep1d_kernel(const SweepArgs A) {
         if ((lane & 3) == 0) pd[lane >> 2] = v[0];
         if ((lane & 15) == 0) pd[8 + (lane >> 4)] = v[8];
     }
+}
+
+template <typename RT, int GW>
+__global__ void __launch_bounds__(256) sweep1d_kernel(const SweepArgs A) {
+    const int gwarp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (gwarp >= A.NQ * A.NWT) return;
+    if (gwarp < A.NWT)
+        sweep1d_warp<RT, GW, 0>(A, gwarp);
+    else
+        sweep1d_warp<RT, GW, 1>(A, gwarp);
 }
 
 // ---------------------------------------------------------------------------

@@ -140,8 +140,11 @@ def _gpu_step(sm, cfg, precision, T0, scale, cv, I0, method, tight=True):
     mom = cu(O.moments(2, omx, omy, w, sigma0, I0r))
     T, E, F = cu(T0), prob.new_nodal(), prob.new_flux()
     In = prob.empty_intensity()
-    kw = dict(eps_outer=1e-14, max_outer=400, eps_inner=1e-14, max_inner=40, pcg_rtol=1e-15,
-              elim_rtol=1e-15, max_elim=80) if tight else {}
+    # the FP32 sweep's outer iteration settles at its rounding floor (relative
+    # changes ~1e-8, possibly cycling between neighbouring FP32 states), so its
+    # stopping tolerance sits above that floor
+    kw = dict(eps_outer=1e-14 if precision == 64 else 1e-7, max_outer=400, eps_inner=1e-14,
+              max_inner=40, pcg_rtol=1e-15, elim_rtol=1e-15, max_elim=80) if tight else {}
     st = prob.step(cu(scale), cu(cv), T, E, F, mom, Ip, In,
                    params=sm.step_params(method=method, **kw))
     return prob, T.cpu().numpy(), E.cpu().numpy(), mom.cpu().numpy(), In, st, I0r
