@@ -8,7 +8,11 @@
 //   x >= 2: 1 - (15/pi^4) sum_n e^{-nx} (x^3/n + 3x^2/n^2 + 6x/n^3 + 6/n^4)
 // and the Rosseland integral by parts, R(x) = P(x) - (15/4pi^4) x^4/(e^x-1),
 // which gives r_g with dB_g/dT = 4 a c T^3 r_g (Sec. 2); for x < 2 the factor
-// x/(e^x-1) is the Bernoulli generating series itself.  A group whose lower
+// x/(e^x-1) is the Bernoulli generating series itself.  Between x = 1 and
+// x = 12, where those series need the most terms, both functions come from
+// degree-10 Taylor expansions about the nearest of the centres 1, 1.25, ...,
+// 12 (|x - c| <= 1/8), whose coefficients the host derives once from
+// P'(x) = (15/pi^4) x^3/(e^x - 1) in extended precision.  A group whose lower
 // reduced edge is in the tail branch is differenced in tails (1 - P) to keep
 // relative accuracy; the lowest edge is 0 and the highest infinity so that
 // sum_g b_g = 1.
@@ -37,6 +41,73 @@ __constant__ double c_inv_n[NTAIL][4];
 // and the rounded remainder; the table holds 2^{-j/64}, j = 0..63.
 __constant__ double c_exp[3];
 __device__ double g_exp2_tab[64];
+// Taylor tables: centre j at c_j = XT0 + j/4; per centre two series of NTAY
+// coefficients in h = x - c_j, (P, R) for c_j < 2 and (1 - P, 1 - R) for
+// c_j >= 2 (so that the tails keep their relative accuracy).
+constexpr double XT0 = 1.0, XT1 = 12.0;
+constexpr int NCEN = 45;  // (XT1 - XT0) * 4 + 1
+constexpr int NTAY = 11;  // remainder (1/8 / 2pi)^11 < 1e-18 of the leading term
+constexpr int JSW = 4;     // centres j < JSW lie below XSWITCH
+__device__ double g_ptab[NCEN][2][NTAY];
+__device__ double g_pcen[NCEN];
+
+// Taylor coefficients of the tables, in long double.  With E(h) = e^{c+h} - 1,
+// g = 1/E, f = (c+h)^3 g and F4 = (c+h) f as power series in h:
+// P(c+h) = P(c) + (15/pi^4) sum_k f_k h^{k+1}/(k+1), and
+// R = P - (15/(4 pi^4)) F4; P(c) = 1 - Q(c) with Q(c) from the exponential
+// series (all its terms, to e^{-200 c}).
+static void planck_taylor_tables(double out[NCEN][2][NTAY]) {
+    typedef long double LD;
+    const LD PI = 3.141592653589793238462643383279502884L;
+    const LD C = 15.0L / (PI * PI * PI * PI);
+    for (int j = 0; j < NCEN; ++j) {
+        const LD c = (LD)XT0 + 0.25L * j;
+        LD Q = 0.0L;
+        for (int n = 200; n >= 1; --n) {
+            const LD m = n;
+            Q += expl(-m * c) * (c * c * c / m + 3.0L * c * c / (m * m) + 6.0L * c / (m * m * m) +
+                                 6.0L / (m * m * m * m));
+        }
+        Q *= C;
+        LD E[NTAY + 1], g[NTAY + 1], f[NTAY + 1], F4[NTAY + 1];
+        const LD ec = expl(c);
+        LD fact = 1.0L;
+        for (int k = 0; k <= NTAY; ++k) {
+            if (k) fact *= k;
+            E[k] = ec / fact;
+        }
+        E[0] = expm1l(c);
+        for (int k = 0; k <= NTAY; ++k) {
+            LD acc = (k == 0) ? 1.0L : 0.0L;
+            for (int i = 1; i <= k; ++i) acc -= E[i] * g[k - i];
+            g[k] = acc / E[0];
+        }
+        const LD a[4] = {c * c * c, 3.0L * c * c, 3.0L * c, 1.0L};
+        for (int k = 0; k <= NTAY; ++k) {
+            LD acc = 0.0L;
+            for (int i = 0; i <= 3 && i <= k; ++i) acc += a[i] * g[k - i];
+            f[k] = acc;
+        }
+        for (int k = 0; k <= NTAY; ++k) F4[k] = c * f[k] + (k ? f[k - 1] : 0.0L);
+        LD pk[NTAY], rk[NTAY];
+        pk[0] = 1.0L - Q;
+        for (int k = 1; k < NTAY; ++k) pk[k] = C * f[k - 1] / k;
+        for (int k = 0; k < NTAY; ++k) rk[k] = pk[k] - 0.25L * C * F4[k];
+        const bool tail = j >= JSW;
+        for (int k = 0; k < NTAY; ++k) {
+            if (!tail) {
+                out[j][0][k] = (double)pk[k];
+                out[j][1][k] = (double)rk[k];
+            } else if (k == 0) {
+                out[j][0][0] = (double)Q;
+                out[j][1][0] = (double)(Q + 0.25L * C * F4[0]);
+            } else {
+                out[j][0][k] = (double)-pk[k];
+                out[j][1][k] = (double)-rk[k];
+            }
+        }
+    }
+}
 
 static bool g_tables_ready[128] = {false};
 
@@ -72,6 +143,10 @@ void planck_upload_tables(void) {
     const double cexp[3] = {(double)(64.0L / ln2), l64_hi, (double)(l64 - (long double)l64_hi)};
     double tab[64];
     for (int j = 0; j < 64; ++j) tab[j] = (double)exp2l(-(long double)j / 64.0L);
+    static double ptab[NCEN][2][NTAY];
+    planck_taylor_tables(ptab);
+    double pcen[NCEN];
+    for (int j = 0; j < NCEN; ++j) pcen[j] = XT0 + 0.25 * j;
     double invn[NTAIL][4];
     for (int n = 1; n <= NTAIL; ++n) {
         double r = 1.0 / n;
@@ -84,7 +159,9 @@ void planck_upload_tables(void) {
         cudaMemcpyToSymbol(c_bern, bern, sizeof(bern)) == cudaSuccess &&
         cudaMemcpyToSymbol(c_inv_n, invn, sizeof(invn)) == cudaSuccess &&
         cudaMemcpyToSymbol(c_exp, cexp, sizeof(cexp)) == cudaSuccess &&
-        cudaMemcpyToSymbol(g_exp2_tab, tab, sizeof(tab)) == cudaSuccess)
+        cudaMemcpyToSymbol(g_exp2_tab, tab, sizeof(tab)) == cudaSuccess &&
+        cudaMemcpyToSymbol(g_ptab, ptab, sizeof(ptab)) == cudaSuccess &&
+        cudaMemcpyToSymbol(g_pcen, pcen, sizeof(pcen)) == cudaSuccess)
         g_tables_ready[dev] = true;
 }
 
@@ -112,6 +189,9 @@ struct EdgeVals {
 // N = ceil(38.2/x).
 // Both are decided in FP32 on xf = (float)x: a count only needs to be large
 // enough, and FP64 compares and divisions are scarce on this GPU.
+__device__ __forceinline__ bool in_taylor(float xf) {
+    return xf >= (float)XT0 && xf < (float)XT1;
+}
 __device__ __forceinline__ int head_terms(float xf) {
     return xf <= 0.25f ? 6 : xf <= 0.5f ? 7 : xf <= 1.0f ? 10 : xf <= 1.5f ? 14 : NBERN;
 }
@@ -149,6 +229,24 @@ __device__ __forceinline__ EdgeVals edge_vals(double x, int K, int N) {
     }
     if (isinf(xf)) {
         e.P = 1.0; e.Q = 0.0; e.R = 1.0; e.RQ = 0.0; e.tail = true;
+        return e;
+    }
+    if (in_taylor(xf)) {
+        const int j = __float2int_rn((xf - (float)XT0) * 4.0f);  // nearest centre
+        const double h = x - __ldg(&g_pcen[j]);
+        const double *t = &g_ptab[j][0][0];
+        double a = __ldg(t + NTAY - 1), b = __ldg(t + 2 * NTAY - 1);
+#pragma unroll
+        for (int k = NTAY - 2; k >= 0; --k) {
+            a = fma(a, h, __ldg(t + k));
+            b = fma(b, h, __ldg(t + NTAY + k));
+        }
+        if (j < JSW) {
+            e.P = a; e.Q = 1.0 - a; e.R = b; e.RQ = 1.0 - b;
+        } else {
+            e.Q = a; e.P = 1.0 - a; e.RQ = b; e.R = 1.0 - b;
+        }
+        e.tail = xf >= (float)XSWITCH;
         return e;
     }
     if (xf < (float)XSWITCH) {
@@ -206,8 +304,8 @@ __device__ __forceinline__ EdgeVals edge_vals(double x, int K, int N) {
 
 __device__ __forceinline__ EdgeVals edge_vals(double x) {
     const float xf = (float)x;
-    return edge_vals(x, xf < (float)XSWITCH ? head_terms(xf) : NBERN,
-                     xf >= (float)XSWITCH ? tail_terms(xf) : 1);
+    return edge_vals(x, (xf < (float)XSWITCH && !in_taylor(xf)) ? head_terms(xf) : 1,
+                     (xf >= (float)XSWITCH && !in_taylor(xf)) ? tail_terms(xf) : 1);
 }
 
 // b_g and r_g of the group between reduced edges lo < hi
@@ -278,11 +376,13 @@ __global__ void emission_kernel(int ncell, int nn, int G, int Gp, const double *
         // every higher group has b = r = 0: skip their series
         const bool skip = lo.tail && lo.Q == 0.0 && lo.RQ == 0.0;
         const float xf = (float)xhi;
+        const bool tab = in_taylor(xf);
         const int K = __reduce_max_sync(
-            0xffffffffu, (!skip && xf < (float)XSWITCH) ? head_terms(xf) : 1);
+            0xffffffffu, (!skip && !tab && xf < (float)XSWITCH) ? head_terms(xf) : 1);
         const int N = __reduce_max_sync(
-            0xffffffffu,
-            (!skip && xf >= (float)XSWITCH && xf < (float)XCLOSED) ? tail_terms(xf) : 1);
+            0xffffffffu, (!skip && !tab && xf >= (float)XSWITCH && xf < (float)XCLOSED)
+                             ? tail_terms(xf)
+                             : 1);
         const EdgeVals hi = skip ? lo : edge_vals(xhi, K, N);
         double b, r;
         group_br(lo, hi, b, r);

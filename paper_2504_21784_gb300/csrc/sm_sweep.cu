@@ -341,14 +341,15 @@ __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &La
     const int g_lo = L.g_lo;
     const int side_x = sx > 0 ? 0 : 1, side_y = sy > 0 ? 2 : 3;
     RT X0[GW], X1[GW], Y0[GW], Y1[GW];  // x-inflow (rows u,d), y-inflow (columns u,d)
-    RT bx[GW];                          // boundary x-inflow (first column of strip 0)
+    // boundary x-inflow of this lane's slots (first column of strip 0), slot
+    // gw at bxin[gw * A.LG]; re-read per row rather than held in registers
+    const RT *bxin = inflow + side_x * A.Gp + gb * GSLOT + g_lo;
 #pragma unroll
     for (int gw = 0; gw < GW; ++gw) {
         const int g = gb * GSLOT + gw * A.LG + g_lo;
         const RT by = inflow[side_y * A.Gp + g];
         Y0[gw] = by;
         Y1[gw] = by;
-        bx[gw] = inflow[side_x * A.Gp + g];
     }
     constexpr int au = sx > 0 ? 0 : 1, bu = sy > 0 ? 0 : 1;
     constexpr int nuu = au + 2 * bu, ndu = (1 - au) + 2 * bu;
@@ -398,8 +399,9 @@ __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &La
         if (w == 0 && sr == 0) {
 #pragma unroll
             for (int gw = 0; gw < GW; ++gw) {
-                X0[gw] = bx[gw];
-                X1[gw] = bx[gw];
+                const RT b = __ldg(bxin + gw * A.LG);
+                X0[gw] = b;
+                X1[gw] = b;
             }
         } else if (global_in) {
             ok = flag_wait_geq(upflag, ep | (unsigned long long)(jj + 1), seen, A.ctrl,
