@@ -501,11 +501,17 @@ sm_status sm_create_problem(const sm_problem_desc *d, void *stream, sm_problem *
 
     // ---- tiling
     if (p->dim == 2) {
+        // auto: the widest strip (most warps per CTA) whose shared memory
+        // fits, with two prefetched rows
         int W = d->strip_width, S = d->prefetch_rows;
-        if (W == 0) W = 8;
         if (S == 0) S = 2;
-        st = apply_tiling(p, W, S);
-        if (st && d->strip_width == 0 && d->prefetch_rows == 0) st = apply_tiling(p, 2, 2);
+        if (W == 0) {
+            st = SM_ERR_UNSUPPORTED;
+            for (int wc : {16, 12, 8, 4, 2})
+                if ((st = apply_tiling(p, wc, S)) == SM_OK) break;
+        } else {
+            st = apply_tiling(p, W, S);
+        }
         if (st) {
             free_all(p);
             delete p;

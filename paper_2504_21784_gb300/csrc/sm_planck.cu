@@ -9,9 +9,9 @@
 // and the Rosseland integral by parts, R(x) = P(x) - (15/4pi^4) x^4/(e^x-1),
 // which gives r_g with dB_g/dT = 4 a c T^3 r_g (Sec. 2); for x < 2 the factor
 // x/(e^x-1) is the Bernoulli generating series itself.  Between x = 1 and
-// x = 12, where those series need the most terms, both functions come from
-// degree-10 Taylor expansions about the nearest of the centres 1, 1.25, ...,
-// 12 (|x - c| <= 1/8), whose coefficients the host derives once from
+// x = 37, where those series need the most terms, both functions come from
+// degree-7 Taylor expansions about the nearest of the centres 1, 1 + 1/8,
+// ..., 37 (|x - c| <= 1/16), whose coefficients the host derives once from
 // P'(x) = (15/pi^4) x^3/(e^x - 1) in extended precision.  A group whose lower
 // reduced edge is in the tail branch is differenced in tails (1 - P) to keep
 // relative accuracy; the lowest edge is 0 and the highest infinity so that
@@ -41,13 +41,14 @@ __constant__ double c_inv_n[NTAIL][4];
 // and the rounded remainder; the table holds 2^{-j/64}, j = 0..63.
 __constant__ double c_exp[3];
 __device__ double g_exp2_tab[64];
-// Taylor tables: centre j at c_j = XT0 + j/4; per centre two series of NTAY
-// coefficients in h = x - c_j, (P, R) for c_j < 2 and (1 - P, 1 - R) for
+// Taylor tables: centre j at c_j = XT0 + j/TSTEP; per centre two series of
+// NTAY coefficients in h = x - c_j, (P, R) for c_j < 2 and (1 - P, 1 - R) for
 // c_j >= 2 (so that the tails keep their relative accuracy).
-constexpr double XT0 = 1.0, XT1 = 12.0;
-constexpr int NCEN = 45;  // (XT1 - XT0) * 4 + 1
-constexpr int NTAY = 11;  // remainder (1/8 / 2pi)^11 < 1e-18 of the leading term
-constexpr int JSW = 4;     // centres j < JSW lie below XSWITCH
+constexpr double XT0 = 1.0, XT1 = 37.0;
+constexpr int TSTEP = 8;   // centres per unit of x
+constexpr int NCEN = 289;  // (XT1 - XT0) * TSTEP + 1
+constexpr int NTAY = 9;    // remainder (1/16 / 2pi)^9 < 1e-17 of the leading term
+constexpr int JSW = 8;     // centres j < JSW lie below XSWITCH
 __device__ double g_ptab[NCEN][2][NTAY];
 __device__ double g_pcen[NCEN];
 
@@ -61,7 +62,7 @@ static void planck_taylor_tables(double out[NCEN][2][NTAY]) {
     const LD PI = 3.141592653589793238462643383279502884L;
     const LD C = 15.0L / (PI * PI * PI * PI);
     for (int j = 0; j < NCEN; ++j) {
-        const LD c = (LD)XT0 + 0.25L * j;
+        const LD c = (LD)XT0 + (LD)j / TSTEP;
         LD Q = 0.0L;
         for (int n = 200; n >= 1; --n) {
             const LD m = n;
@@ -146,7 +147,7 @@ void planck_upload_tables(void) {
     static double ptab[NCEN][2][NTAY];
     planck_taylor_tables(ptab);
     double pcen[NCEN];
-    for (int j = 0; j < NCEN; ++j) pcen[j] = XT0 + 0.25 * j;
+    for (int j = 0; j < NCEN; ++j) pcen[j] = XT0 + (double)j / TSTEP;
     double invn[NTAIL][4];
     for (int n = 1; n <= NTAIL; ++n) {
         double r = 1.0 / n;
@@ -220,9 +221,10 @@ __device__ __forceinline__ double exp_neg(double x) {
 // K, N: head and tail term counts to use (at least head_terms(x) and
 // tail_terms(x)); callers that keep a warp converged pass the warp maximum,
 // so that every lane reads the same coefficient at each step.
-__device__ __forceinline__ EdgeVals edge_vals(double x, int K, int N) {
+// xf: x rounded to FP32 or computed in FP32 (it only steers branches and
+// term counts, which all have margin for its relative error below 1e-6).
+__device__ __forceinline__ EdgeVals edge_vals(double x, float xf, int K, int N) {
     EdgeVals e;
-    const float xf = (float)x;
     if (!(xf > 0.0f)) {
         e.P = 0.0; e.Q = 1.0; e.R = 0.0; e.RQ = 1.0; e.tail = false;
         return e;
@@ -232,7 +234,7 @@ __device__ __forceinline__ EdgeVals edge_vals(double x, int K, int N) {
         return e;
     }
     if (in_taylor(xf)) {
-        const int j = __float2int_rn((xf - (float)XT0) * 4.0f);  // nearest centre
+        const int j = __float2int_rn((xf - (float)XT0) * (float)TSTEP);  // nearest centre
         const double h = x - __ldg(&g_pcen[j]);
         const double *t = &g_ptab[j][0][0];
         double a = __ldg(t + NTAY - 1), b = __ldg(t + 2 * NTAY - 1);
@@ -304,7 +306,7 @@ __device__ __forceinline__ EdgeVals edge_vals(double x, int K, int N) {
 
 __device__ __forceinline__ EdgeVals edge_vals(double x) {
     const float xf = (float)x;
-    return edge_vals(x, (xf < (float)XSWITCH && !in_taylor(xf)) ? head_terms(xf) : 1,
+    return edge_vals(x, xf, (xf < (float)XSWITCH && !in_taylor(xf)) ? head_terms(xf) : 1,
                      (xf >= (float)XSWITCH && !in_taylor(xf)) ? tail_terms(xf) : 1);
 }
 
@@ -348,13 +350,19 @@ __global__ void opacity_kernel(int ncell, int nn, int G, int kind, double alpha,
 // Emission (row a1): one thread per (cell, node), walking the group edges once.
 // Writes the sweep's source records src[cell][g][8] = {q at the nodes (unused
 // node slots 0), sigma~, sigma, 0, 0} in the sweep precision; padding groups
-// get no source and sigma~ = 1.
+// get no source and sigma~ = 1.  The Planck and Rosseland means take
+// sum_g b_g = sum_g r_g = 1 (the lowest edge is 0, the highest infinity).
+// Launched with one warp per block and (G + 1) floats of dynamic shared
+// memory: the edges in FP32, for the branch decisions.
 template <typename RT>
 __global__ void emission_kernel(int ncell, int nn, int G, int Gp, const double *__restrict__ edges,
                                 double acT4_scale, double inv_cdt, const double *__restrict__ T,
                                 const double *__restrict__ sigma, RT *__restrict__ src,
                                 double *__restrict__ gray, double *__restrict__ qcanon,
                                 unsigned int *ctrl) {
+    extern __shared__ float s_edges[];
+    for (int i = threadIdx.x; i <= G; i += 32) s_edges[i] = (float)edges[i];
+    __syncwarp();
     // Lanes past the last node evaluate a copy of it and store nothing, so
     // that every warp stays converged through the edge loop (the series term
     // counts below are warp maxima).
@@ -367,15 +375,19 @@ __global__ void emission_kernel(int ncell, int nn, int G, int Gp, const double *
     if (active && (!(Tn > 0.0) || !isfinite(Tn))) atomicOr(ctrl + CTRL_STATUS, ST_NONPHYSICAL);
     const double B4 = acT4_scale * Tn * Tn * Tn * Tn;  // a c T^4 / 4 pi
     const double invT = 1.0 / Tn;
+    const float invTf = 1.0f / (float)Tn;
     EdgeVals lo = edge_vals(0.0);
-    double nb = 0.0, db = 0.0, nr = 0.0, dr = 0.0;
+    double nb = 0.0, nr = 0.0;
     RT *rec0 = src + (size_t)cell * Gp * 8;
     for (int g = 0; g < G; ++g) {
-        const double xhi = (g == G - 1) ? INFINITY : edges[g + 1] * invT;
+        const bool last = g == G - 1;
+        const double xhi = last ? INFINITY : edges[g + 1] * invT;
+        const float xf = last ? INFINITY : s_edges[g + 1] * invTf;
         // beyond x ~ 745 the tails 1 - P and 1 - R underflow to exactly 0, so
-        // every higher group has b = r = 0: skip their series
-        const bool skip = lo.tail && lo.Q == 0.0 && lo.RQ == 0.0;
-        const float xf = (float)xhi;
+        // every higher group has b = r = 0: skip their series (tested on the
+        // bits, both tails being +0 there)
+        const bool skip = lo.tail && ((__double_as_longlong(lo.Q) |
+                                       __double_as_longlong(lo.RQ)) == 0);
         const bool tab = in_taylor(xf);
         const int K = __reduce_max_sync(
             0xffffffffu, (!skip && !tab && xf < (float)XSWITCH) ? head_terms(xf) : 1);
@@ -383,14 +395,12 @@ __global__ void emission_kernel(int ncell, int nn, int G, int Gp, const double *
             0xffffffffu, (!skip && !tab && xf >= (float)XSWITCH && xf < (float)XCLOSED)
                              ? tail_terms(xf)
                              : 1);
-        const EdgeVals hi = skip ? lo : edge_vals(xhi, K, N);
+        const EdgeVals hi = skip ? lo : edge_vals(xhi, xf, K, N);
         double b, r;
         group_br(lo, hi, b, r);
         const double sg = sigma[(size_t)g * ncell + cell];
         nb = fma(b, sg, nb);
-        db += b;
         nr = fma(r, sg, nr);
-        dr += r;
         const double qv = sg * b * B4;
         if (active) {
             rec0[(size_t)g * 8 + node] = (RT)qv;
@@ -417,8 +427,8 @@ __global__ void emission_kernel(int ncell, int nn, int G, int Gp, const double *
         rec[6] = (RT)0;
         rec[7] = (RT)0;
     }
-    gray[(size_t)t * 2 + 0] = nb / db;
-    gray[(size_t)t * 2 + 1] = nr / dr;
+    gray[(size_t)t * 2 + 0] = nb;
+    gray[(size_t)t * 2 + 1] = nr;
 }
 
 // Group Planck functions and their temperature derivatives at the nodes,
@@ -578,11 +588,11 @@ cudaError_t launch_emission(const sm_problem *p, const double *T, const double *
     const int blocks = (n + threads - 1) / threads;
     const double scale = p->desc.a * p->desc.c / (4.0 * PI_D);
     if (p->prec == 32)
-        emission_kernel<float><<<blocks, threads, 0, s>>>(
+        emission_kernel<float><<<blocks, threads, (p->G + 1) * sizeof(float), s>>>(
             p->ncell, p->nn, p->G, p->Gp, p->d_edges, scale, p->inv_cdt, T, sigma,
             (float *)p->d_src, p->d_gray, q_canon, p->d_ctrl);
     else
-        emission_kernel<double><<<blocks, threads, 0, s>>>(
+        emission_kernel<double><<<blocks, threads, (p->G + 1) * sizeof(float), s>>>(
             p->ncell, p->nn, p->G, p->Gp, p->d_edges, scale, p->inv_cdt, T, sigma,
             (double *)p->d_src, p->d_gray, q_canon, p->d_ctrl);
     return cudaGetLastError();
