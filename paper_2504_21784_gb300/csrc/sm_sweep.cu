@@ -24,8 +24,9 @@
 // directions).  A CTA takes one warp task over a strip of W cell columns,
 // one warp per column; each warp walks its column in upwind row order with
 // the y-inflow carried in registers.  The x-inflow of a row comes from the
-// warp of the upwind column through a shared-memory ring (pairwise row
-// counters, back-pressure of R rows), and across strips from the upwind CTA
+// warp of the upwind column through a shared-memory ring of RING rows, each
+// slot guarded by a "full" and an "empty" mbarrier (the waiting warp is
+// suspended by the hardware instead of polling), and across strips from the upwind CTA
 // through an L2-resident face buffer and a per-(warp task, strip) row counter
 // (release / acquire).  So the W warps of a CTA run one row apart, a staircase
 // wavefront with no CTA-wide barrier inside a task.  Each warp prefetches
@@ -116,6 +117,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// arrive (release, CTA scope) of the executing thread
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 // global -> shared bulk copy; bytes and both addresses multiples of 16
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile(
@@ -140,30 +145,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsign
     for (unsigned it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 31) == 0) {
-            if (*s_abort) return false;
-            if (global_ns() - t0 > timeout_ns) {
-                raise_timeout(ctrl, s_abort);
-                return false;
-            }
-        }
-    }
-}
-
-// Bounded wait (every lane) until a shared counter reaches target.  The
-// neighbouring warp usually publishes within a few hundred cycles, so the
-// wait spins on the shared counter first and only then backs off with
-// __nanosleep (a sleeping warp can oversleep by about a microsecond).
-__device__ __forceinline__ bool smem_wait_geq(volatile int *cnt, int target, unsigned int *ctrl,
-                                              long long timeout_ns, volatile int *s_abort) {
-    if (*cnt >= target) return true;
-#pragma unroll 1
-    for (int spin = 0; spin < 256; ++spin)
-        if (*cnt >= target) return true;
-    const long long t0 = global_ns();
-    for (unsigned it = 1;; ++it) {
-        __nanosleep(32);
-        if (*cnt >= target) return true;
-        if ((it & 15) == 0) {
             if (*s_abort) return false;
             if (global_ns() - t0 > timeout_ns) {
                 raise_timeout(ctrl, s_abort);
@@ -250,8 +231,9 @@ __host__ __device__ inline size_t stage_bytes(int rsize, int GW, int GSLOT) {
 // ---------------------------------------------------------------------------
 // Shared-memory layout of one 2D sweep CTA: W warps, each owning S stages of
 // stg bytes (prefetched I^k and source records), an x-face ring for ring_gw
-// slots and the per-lane moment weights; after them W*S mbarriers and two
-// row counters per warp.  A row's stage, once its cell solves have read it,
+// slots and the per-lane moment weights; after them W*S stage mbarriers and
+// the ring mbarriers (W*RING "full", W*RING "empty").  A row's stage, once
+// its cell solves have read it,
 // doubles as that row's moment transpose buffer ([8][MROW]) before the
 // prefetch of a later row overwrites it, so a stage is at least that large.
 struct Layout2D {
@@ -269,7 +251,7 @@ __host__ __device__ inline Layout2D layout2d(int rsize, int S, size_t stg, int r
 }
 
 __host__ __device__ inline size_t layout2d_total(const Layout2D &L, int W, int S) {
-    return (size_t)W * L.wsz + (size_t)W * S * 8 + 2 * W * sizeof(int) + 64;
+    return (size_t)W * L.wsz + (size_t)W * S * 8 + (size_t)2 * W * RING * 8 + 64;
 }
 
 size_t sweep2d_smem_bytes(int prec, int W, int GW, int S, int GSLOT) {
@@ -293,9 +275,9 @@ size_t sweep2d_stage_bytes(int prec, int GW, int GSLOT) {
 template <typename RT, int GW, int Q, class Args>
 __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &Lay, const int task,
                                              unsigned char *smem_raw, uint64_t *bars,
-                                             volatile int *rows_done, volatile int *cons,
-                                             volatile int *s_abort, uint32_t &phase,
-                                             const unsigned long long epoch) {
+                                             uint64_t *ring_bars, uint32_t &ring_p,
+                                             uint32_t &ring_c, volatile int *s_abort,
+                                             uint32_t &phase, const unsigned long long epoch) {
     using R2 = typename V2<RT>::t;
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
@@ -394,7 +376,6 @@ __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &La
     for (; jj < ny && ok; ++jj) {
         const int y = row_y(jj);
         const int st = jj % S;
-        const int slot = jj % RING;
         // (a) x-inflow
         if (w == 0 && sr == 0) {
 #pragma unroll
@@ -415,21 +396,23 @@ __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &La
                 X1[gw] = f.y;
             }
         } else {
-            ok = smem_wait_geq(rows_done + (w - 1), jj + 1, A.ctrl, A.timeout_ns, s_abort);
+            // the upwind column's ring: wait until its row is in ("full"),
+            // read it, hand the slot back ("empty"); every lane waits and
+            // arrives (acquire / release of its own accesses)
+            const uint32_t c = ring_c;
+            const int slot = (int)(c % RING);
+            ok = mbar_wait(ring_bars + (w - 1) * RING + slot, (c / RING) & 1u, A.ctrl,
+                           A.timeout_ns, s_abort);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
-            __threadfence_block();
 #pragma unroll
             for (int gw = 0; gw < GW; ++gw) {
                 const R2 f = ring_in[(slot * GW + gw) * 32 + lane];
                 X0[gw] = f.x;
                 X1[gw] = f.y;
             }
-            __syncwarp();
-            if (lane == 0) {
-                __threadfence_block();
-                cons[w - 1] = jj + 1;  // ring slot of the upwind column is free again
-            }
+            mbar_arrive(ring_bars + (W + w - 1) * RING + slot);
+            ring_c = c + 1;
         }
         // (b) this row's prefetched I^k and sources
         ok = mbar_wait(mybars + st, (phase >> st) & 1u, A.ctrl, A.timeout_ns, s_abort);
@@ -486,9 +469,16 @@ __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &La
         }
         // (d) hand the x-outflow downwind
         if (w < ws - 1) {
-            ok = smem_wait_geq(cons + w, jj + 1 - RING, A.ctrl, A.timeout_ns, s_abort);
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) break;
+            // this column's ring: once the slot's previous row has been read
+            // ("empty"), write the row and mark it "full"
+            const uint32_t r = ring_p;
+            const int slot = (int)(r % RING);
+            if (r >= RING) {
+                ok = mbar_wait(ring_bars + (W + w) * RING + slot, ((r / RING) + 1) & 1u, A.ctrl,
+                               A.timeout_ns, s_abort);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+            }
 #pragma unroll
             for (int gw = 0; gw < GW; ++gw) {
                 R2 f;
@@ -496,11 +486,8 @@ __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &La
                 f.y = X1[gw];
                 ring_out[(slot * GW + gw) * 32 + lane] = f;
             }
-            __syncwarp();
-            if (lane == 0) {
-                __threadfence_block();
-                rows_done[w] = jj + 1;
-            }
+            mbar_arrive(ring_bars + w * RING + slot);
+            ring_p = r + 1;
         } else if (global_out) {
 #pragma unroll
             for (int gw = 0; gw < GW; ++gw) {
@@ -575,27 +562,27 @@ __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &La
 template <typename RT, int GW, class Args>
 __device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay, const int task,
                                              unsigned char *smem_raw, uint64_t *bars,
-                                             volatile int *rows_done, volatile int *cons,
-                                             volatile int *s_abort, uint32_t &phase,
-                                             const unsigned long long epoch) {
+                                             uint64_t *ring_bars, uint32_t &ring_p,
+                                             uint32_t &ring_c, volatile int *s_abort,
+                                             uint32_t &phase, const unsigned long long epoch) {
     const int NWG = A.NQ * A.NWT;
     const int q = (task % NWG) / A.NWT;
     switch (q) {
         case 0:
-            sweep2d_task_q<RT, GW, 0>(A, Lay, task, smem_raw, bars, rows_done, cons, s_abort,
-                                      phase, epoch);
+            sweep2d_task_q<RT, GW, 0>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c,
+                                      s_abort, phase, epoch);
             break;
         case 1:
-            sweep2d_task_q<RT, GW, 1>(A, Lay, task, smem_raw, bars, rows_done, cons, s_abort,
-                                      phase, epoch);
+            sweep2d_task_q<RT, GW, 1>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c,
+                                      s_abort, phase, epoch);
             break;
         case 2:
-            sweep2d_task_q<RT, GW, 2>(A, Lay, task, smem_raw, bars, rows_done, cons, s_abort,
-                                      phase, epoch);
+            sweep2d_task_q<RT, GW, 2>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c,
+                                      s_abort, phase, epoch);
             break;
         default:
-            sweep2d_task_q<RT, GW, 3>(A, Lay, task, smem_raw, bars, rows_done, cons, s_abort,
-                                      phase, epoch);
+            sweep2d_task_q<RT, GW, 3>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c,
+                                      s_abort, phase, epoch);
             break;
     }
 }
@@ -608,24 +595,22 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const __grid_constant__ Sw
     const int W = A.W, S = A.S;
     const Layout2D Lay = layout2d((int)sizeof(RT), S, stage_bytes((int)sizeof(RT), GW, GW * A.LG), GW);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)W * Lay.wsz);
-    volatile int *rows_done = reinterpret_cast<volatile int *>(bars + (size_t)W * S);
-    volatile int *cons = rows_done + W;
+    uint64_t *ring_bars = bars + (size_t)W * S;
     if (threadIdx.x < W * S) mbar_init(bars + threadIdx.x, 1);
+    if (threadIdx.x < 2 * W * RING) mbar_init(ring_bars + threadIdx.x, 32);
     if (threadIdx.x == 0) s_abort = 0;
     fence_mbar_init();
-    uint32_t phase = 0;  // parity bit per stage of this warp
+    uint32_t phase = 0;   // parity bit per stage of this warp
+    uint32_t ring_p = 0;  // rows this warp has put in its ring, all tasks
+    uint32_t ring_c = 0;  // rows this warp has taken from the upwind ring
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_task = (int)atomicAdd(A.ctrl + CTRL_QUEUE, 1u);
-        if (threadIdx.x < W) {
-            rows_done[threadIdx.x] = 0;
-            cons[threadIdx.x] = 0;
-        }
         __syncthreads();
         const int task = s_task;
         if (task >= A.n_tasks || s_abort) return;
-        sweep2d_task<RT, GW>(A, Lay, task, smem_raw, bars, rows_done, cons, &s_abort, phase,
-                             A.epoch);
+        sweep2d_task<RT, GW>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c, &s_abort,
+                             phase, A.epoch);
     }
 }
 
@@ -646,22 +631,18 @@ __global__ void __launch_bounds__(512) sweep2d_batch_kernel(const __grid_constan
     const int W = B.W, S = B.S;
     const Layout2D Lay = layout2d((int)sizeof(RT), S, B.stg, B.ring_gw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)W * Lay.wsz);
-    volatile int *rows_done = reinterpret_cast<volatile int *>(bars + (size_t)W * S);
-    volatile int *cons = rows_done + W;
+    uint64_t *ring_bars = bars + (size_t)W * S;
     if (threadIdx.x < W * S) mbar_init(bars + threadIdx.x, 1);
+    if (threadIdx.x < 2 * W * RING) mbar_init(ring_bars + threadIdx.x, 32);
     if (threadIdx.x == 0) s_abort = 0;
     fence_mbar_init();
     const unsigned long long epoch = *B.epoch;
-    uint32_t phase = 0;
+    uint32_t phase = 0, ring_p = 0, ring_c = 0;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
             const int t = (int)atomicAdd(B.ctrl + CTRL_QUEUE, 1u);
             s_task = t < B.n_tasks ? B.tasks[t] : make_int2(-1, -1);
-        }
-        if (threadIdx.x < W) {
-            rows_done[threadIdx.x] = 0;
-            cons[threadIdx.x] = 0;
         }
         __syncthreads();
         const int2 pt = s_task;
@@ -675,20 +656,20 @@ __global__ void __launch_bounds__(512) sweep2d_batch_kernel(const __grid_constan
         __syncthreads();
         switch (s_args.GW) {
             case 1:
-                sweep2d_task<RT, 1>(s_args, Lay, pt.y, smem_raw, bars, rows_done, cons, &s_abort,
-                                    phase, epoch);
+                sweep2d_task<RT, 1>(s_args, Lay, pt.y, smem_raw, bars, ring_bars, ring_p, ring_c,
+                                    &s_abort, phase, epoch);
                 break;
             case 2:
-                sweep2d_task<RT, 2>(s_args, Lay, pt.y, smem_raw, bars, rows_done, cons, &s_abort,
-                                    phase, epoch);
+                sweep2d_task<RT, 2>(s_args, Lay, pt.y, smem_raw, bars, ring_bars, ring_p, ring_c,
+                                    &s_abort, phase, epoch);
                 break;
             case 4:
-                sweep2d_task<RT, 4>(s_args, Lay, pt.y, smem_raw, bars, rows_done, cons, &s_abort,
-                                    phase, epoch);
+                sweep2d_task<RT, 4>(s_args, Lay, pt.y, smem_raw, bars, ring_bars, ring_p, ring_c,
+                                    &s_abort, phase, epoch);
                 break;
             default:
-                sweep2d_task<RT, 8>(s_args, Lay, pt.y, smem_raw, bars, rows_done, cons, &s_abort,
-                                    phase, epoch);
+                sweep2d_task<RT, 8>(s_args, Lay, pt.y, smem_raw, bars, ring_bars, ring_p, ring_c,
+                                    &s_abort, phase, epoch);
                 break;
         }
     }
