@@ -127,6 +127,36 @@ def test_emission_matches_oracle(gpu_lib, G):
     assert e < 1e-12
 
 
+def test_emission_at_branch_boundaries(gpu_lib):
+    """Nodal temperatures that put one group edge at each switch of the GPU's
+    Planck evaluation (head series / Taylor tables / tail series / one-term
+    tail / underflow), just below, on and just above it: every group of every
+    node against the oracle, elementwise."""
+    import torch
+    G = 24
+    cfg = config(2, 8, 6, G, 1, 1)
+    edges = cfg.edges
+    xs = [0.5, 0.9999, 1.0, 1.0001, 1.06, 1.9999, 2.0, 2.0001, 11.98, 12.0, 12.03, 36.9999,
+          37.0, 37.0001, 100.0, 700.0, 744.0, 746.0]
+    rng = np.random.default_rng(5)
+    T = np.empty((cfg.n_cells, 4))
+    for i in range(T.size):
+        x = xs[i % len(xs)]
+        e = edges[1 + rng.integers(0, G - 1)]   # an interior edge
+        T.flat[i] = e / x
+    T = np.clip(T, 1e-3, 1e3)
+    prob = gpu_lib.Problem.from_config(cfg, 64)
+    sig = O.opacity(cfg.opacity_kind, cfg.opacity_alpha, cfg.edges, T, np.ones(cfg.n_cells))
+    ref = O.emission(cfg.edges, cfg.a, cfg.c, T, sig)
+    got = prob.emission(torch.from_numpy(T).cuda(), torch.from_numpy(sig).cuda()).cpu().numpy()
+    prob.synchronize()
+    # relative per element; values below the normal FP64 range (the last
+    # groups before the underflow) are compared against a 1e-280 floor
+    e = float(np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-280)))
+    print(f"emission at branch switches: {e:.3e}")
+    assert e < 1e-12
+
+
 def test_tiling_does_not_change_intensity(gpu_lib):
     """The per-(d,g) arithmetic is independent of the strip width and of the
     warps per CTA: the intensity is bitwise identical, moments agree to the
