@@ -11,7 +11,10 @@ unpacked result on the device and hands over one direction at a time.
 * batched: the 64 uneven problems in one persistent launch (FP32), every
   member against the oracle;
 * adjoint, 128x128 cells, 64 directions, 16 groups, 20 steps with
-  checkpointing: gradient against central differences of the GPU forward.
+  checkpointing: gradient against central differences of the GPU forward;
+* time steps of Algorithm 1: the 1D Marshak wave (200 cells, S8) over its ten
+  steps, and one step of the 2D gray channel with the paper's iteration
+  controls, against the oracle's steps.
 
 The previous intensity is a seeded separable field, exactly representable in
 FP32, so both sweep precisions read the same input and one oracle pass serves
@@ -224,3 +227,88 @@ def test_adjoint_full_size_matches_central_differences(gpu_lib):
           f"fd rel err max {max(errs):.2e}")
     assert max(errs) < 1e-4
     prob.close()
+
+
+def _gpu_steps(sm, cfg, precision, T0, I0, mom0, scale, cv, nsteps, params):
+    """nsteps time steps of Algorithm 1 through sm_step; returns T, E and the
+    per-step statistics."""
+    import torch
+    prob = sm.Problem.from_config(cfg, precision)
+    T, E, F = _cu(T0), prob.new_nodal(), prob.new_flux()
+    mom = _cu(mom0)
+    Ip = prob.pack(_cu(W.in_precision(I0, precision)))
+    stats = []
+    for _ in range(nsteps):
+        In = prob.empty_intensity()
+        stats.append(prob.step(_cu(scale), _cu(cv), T, E, F, mom, Ip, In,
+                               params=sm.step_params(**params)))
+        Ip = In
+    out = T.cpu().numpy(), E.cpu().numpy(), stats
+    prob.close()
+    del torch
+    return out
+
+
+def _oracle_steps(cfg, T0, I0, mom0, scale, cv, nsteps, prm):
+    from oracle import lo as L
+    T, I, mom = T0, I0, mom0
+    stats = []
+    for _ in range(nsteps):
+        T, E, F, I, mom, st = L.sm_step(cfg, scale, cv, T, I, mom, prm)
+        stats.append(st)
+    return T, E, stats
+
+
+def _equilibrium_start(cfg):
+    from oracle import lo as L
+    n, nn = cfg.n_cells, cfg.n_nodes
+    T0 = np.full((n, nn), cfg.T0)
+    scale = W.scale_field(cfg)
+    cv = np.full((n, nn), cfg.cv)
+    omx, omy, w = O.quadrature(cfg.dim, cfg.n_polar, cfg.n_azim)
+    I0 = L.equilibrium_intensity(cfg, T0, omx)
+    sig = O.opacity(cfg.opacity_kind, cfg.opacity_alpha, cfg.edges, T0, scale)
+    return T0, I0, O.moments(cfg.dim, omx, omy, w, sig, I0), scale, cv
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_marshak_ten_steps_match_oracle(gpu_lib, precision):
+    """The 1D Marshak-type wave, 200 cells, S8, ten backward-Euler steps from
+    T = 0.01 with the inflow at T = 1, every step converged tightly on both
+    sides: the temperature and energy after each of the ten steps."""
+    from oracle import lo as L
+    cfg = W.marshak_1d()
+    T0, I0, mom0, scale, cv = _equilibrium_start(cfg)
+    tight = dict(eps_outer=1e-13 if precision == 64 else 1e-7, max_outer=400, eps_inner=1e-14,
+                 max_inner=60, pcg_rtol=1e-15, elim_rtol=1e-15, max_elim=100)
+    prm = L.StepParams(eps_outer=1e-13, max_outer=400,
+                       lo=L.LOParams(eps_inner=1e-14, max_inner=60, elim_rtol=1e-15, max_elim=100))
+    Tr, Er, str_ = _oracle_steps(cfg, T0, I0, mom0, scale, cv, cfg.steps, prm)
+    Tg, Eg, stg = _gpu_steps(gpu_lib, cfg, precision, T0, I0, mom0, scale, cv, cfg.steps, tight)
+    eT = float(np.abs(Tg - Tr).max() / np.abs(Tr).max())
+    eE = float(np.abs(Eg - Er).max() / np.abs(Er).max())
+    front = float(np.mean(Tr > 0.5))
+    print(f"marshak fp{precision}: T {eT:.2e} E {eE:.2e}; hot fraction {front:.2f}; outer "
+          f"{[s['outer_iters'] for s in stg]} (oracle {[s['outer'] for s in str_]})")
+    assert all(s["converged"] == 1 for s in stg)
+    tol = TOL[precision]
+    assert eT < tol and eE < tol
+
+
+def test_gray_channel_step_matches_oracle(gpu_lib):
+    """The 2D gray channel at full size (128x128 cells, 128 directions), one
+    step from the equilibrium start with the paper's iteration controls, FP64
+    and FP32 sweeps: each within 1e-5 of the oracle's step (the accuracy at
+    which the two paths' seconds per step are compared)."""
+    from oracle import lo as L
+    cfg = W.gray_channel_2d()
+    T0, I0, mom0, scale, cv = _equilibrium_start(cfg)
+    Tr, Er, str_ = _oracle_steps(cfg, T0, I0, mom0, scale, cv, 1, L.StepParams())
+    for precision in (64, 32):
+        Tg, Eg, stg = _gpu_steps(gpu_lib, cfg, precision, T0, I0, mom0, scale, cv, 1, {})
+        eT = float(np.abs(Tg - Tr).max() / np.abs(Tr).max())
+        eE = float(np.abs(Eg - Er).max() / np.abs(Er).max())
+        print(f"gray channel fp{precision}: T {eT:.2e} E {eE:.2e}; outer "
+              f"{stg[0]['outer_iters']} (oracle {str_[0]['outer']})")
+        assert stg[0]["converged"] == 1
+        assert eT < 1e-5 and eE < 1e-5
