@@ -48,6 +48,9 @@ def parse():
                     help="time steps timed per path in the step comparison (after 1 warm-up step)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched 64-problem measurement")
+    ap.add_argument("--no-config-sweeps", action="store_true",
+                    help="skip the per-configuration sweep rates (1D slab, gray channel, "
+                         "adjoint-size problem)")
     ap.add_argument("--adjoint-fd-cells", type=int, default=4,
                     help="cells of the adjoint finite-difference check (0: skip the adjoint)")
     return ap.parse_args()
@@ -182,8 +185,13 @@ def cpu_baseline(cfg, budget_s: float = 8.0):
     O.sweep_pairs(2, cfg.nx, cfg.ny, cfg.extent, omx, omy, sig, inv, q, None, infl, sample)
     dt = time.perf_counter() - t0
     upd = n * cfg.n_cells
+    one = sample[:8]
+    t0 = time.perf_counter()
+    O.sweep_pairs(2, cfg.nx, cfg.ny, cfg.extent, omx, omy, sig, inv, q, None, infl, one,
+                  nthreads=1)
+    v1 = len(one) * cfg.n_cells / (time.perf_counter() - t0)
     return {"value": upd / dt, "unit": "cell-dir-group updates/s", "cores": cores,
-            "kind": "oracle",
+            "value_one_thread": v1, "kind": "oracle",
             "sample": f"{n} random (direction, group) sweeps of the full {cfg.nx}x{cfg.ny} mesh "
                       f"({upd} updates, {dt:.1f} s), FP64 oracle sweep only, OpenMP over pairs"}
 
@@ -237,6 +245,58 @@ def converged_steps(sm, W, cfg, prec: int, n_steps: int, stream, autotune: bool 
         Tn = T.cpu().numpy()
         prob.close()
         return out, Tn
+
+
+def config_sweeps(sm, W, stream, reps: int = 20):
+    """Metric 1 on the other single-problem configurations: whole hot-path
+    passes (emission + sweep with fused moments + reduction/closures) on the
+    1D Marshak slab, the 2D gray channel and the adjoint-size problem, FP32
+    and FP64 sweeps, autotuned tiling, one step of history as I^k; updates/s
+    of the pass and the sweep kernel's share of the measured copy bandwidth
+    (the 1D slab has 1,600 updates per sweep: latency-bound by nature)."""
+    import torch
+    peak, _ = measured_peaks()
+    out = {}
+    for cfg in (W.marshak_1d(), W.gray_channel_2d(), W.adjoint_2d()):
+        res = {}
+        for prec in (32, 64):
+            with torch.cuda.stream(stream):
+                prob = sm.Problem.from_config(cfg, prec, stream=stream)
+                T = torch.from_numpy(W.temperature_wave(cfg)).cuda()
+                sigma = prob.opacity(T, torch.from_numpy(W.scale_field(cfg)).cuda())
+                I = [prob.empty_intensity(), prob.empty_intensity()]
+                mom, clo = prob.new_moments(), prob.new_closures()
+                prob.sweep(T, sigma, None, I[0], mom, clo)
+                if cfg.dim == 2:
+                    prob.autotune(T, sigma, I[0], I[1], reps=2)
+                for i in range(3):
+                    prob.sweep(T, sigma, I[i % 2], I[(i + 1) % 2], mom, clo)
+                prob.synchronize()
+                prob.set_profiling(True)
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                for i in range(reps):
+                    prob.sweep(T, sigma, I[i % 2], I[(i + 1) % 2], mom, clo)
+                ev1.record(stream)
+                ev1.synchronize()
+                prob.synchronize()
+                kt = prob.kernel_times()
+                prob.set_profiling(False)
+                ms = ev0.elapsed_time(ev1) / reps
+                sweep_ms = kt["sweep_ms"] / max(kt["count"], 1)
+                alg = algorithmic_bytes(cfg, prec) if cfg.dim == 2 else None
+                r = {"updates_per_s": cfg.updates / (ms * 1e-3), "ms_per_pass": ms,
+                     "sweep_ms": sweep_ms}
+                if alg is not None:
+                    r["sweep_hbm_frac"] = alg["per_launch"] / (sweep_ms * 1e-3) / 1e9 / peak
+                    r["tiling"] = {k: prob.info[k] for k in ("strip_width", "prefetch_rows",
+                                                             "groups_per_warp")}
+                res[f"fp{prec}"] = r
+                prob.close()
+        out[cfg.name] = res
+    torch.cuda.empty_cache()
+    return out
 
 
 def step_metric(sm, W, cfgs, n_steps: int, stream):
@@ -553,6 +613,8 @@ def main():
         torch.cuda.empty_cache()
         line["step_metric"] = step_metric(sm, W, [W.multigroup_2d(), W.gray_channel_2d()],
                                           args.step_steps, stream)
+    if not args.no_config_sweeps and not (args.nx or args.groups):
+        line["config_sweeps"] = config_sweeps(sm, W, stream)
     if not args.no_batched and not (args.nx or args.groups):
         line["batched"] = batched_metric(sm, W, stream, max(3, args.steps // 2), 3)
     if args.adjoint_fd_cells > 0 and not (args.nx or args.groups):

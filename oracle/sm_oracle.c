@@ -553,8 +553,9 @@ int orc_sweep_pairs(int dim, int nx, int ny, double x0, double x1, double y0, do
     const int np = pairs ? npairs : ndir * G;
     int err = 0;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+    /* nthreads > 0 limits this call only (num_threads clause) */
+    const int nth = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err) num_threads(nth)
 #endif
     for (int pi = 0; pi < np; ++pi) {
         int d = pairs ? pairs[2 * pi] : pi / G;

@@ -188,6 +188,8 @@ sm_status record(sm_batch *b, const Ptrs &q, sm_batch::Entry &e) {
     for (size_t i = 0; i < n; ++i) {
         args[i] = smk::make_sweep_args(b->probs[i], q.I_prev ? q.I_prev[i] : nullptr, q.I_out[i]);
         args[i].ctrl = b->d_ctrl;
+        // the members share one queue: the batch's task count decides
+        args[i].publish = smk::publish_rows(b->n_tasks, b->resident);
     }
     B_CUDA(cudaMalloc(&e.d_args, sizeof(smk::SweepArgs) * n));
     B_CUDA(cudaMemcpy(e.d_args, args.data(), sizeof(smk::SweepArgs) * n, cudaMemcpyHostToDevice));
@@ -306,7 +308,7 @@ sm_status sm_create_batch(const sm_problem_desc *descs, int n, void *stream, sm_
             return bail(b_fail(SM_ERR_CUDA, "fork event"));
     for (int i = 0; i < n; ++i) {
         sm_problem *p = nullptr;
-        const sm_status st = sm_create_problem(&descs[i], stream, &p);
+        const sm_status st = smk::create_batch_member(&descs[i], stream, &p);
         if (st != SM_OK) return bail(st);
         // the member reports to the batch's control words
         cudaFree(p->d_ctrl);

@@ -54,7 +54,19 @@ struct SweepArgs {
     int reverse;             // 2D: sweep -Omega for every direction; I_prev / I_out of
                              // geometric quadrant q live at quadrant q^2 (adjoint sweeps)
     int qmom;                // 2D: accumulate moments per quadrant, [q][cell][36]
+    int publish;             // 2D: rows per release of a strip's x-faces downwind
 };
+
+// Rows per release of a strip's x-faces to the downwind strip: the release
+// costs a gpu-scope fence, so a sweep with several tasks per resident CTA
+// (throughput-bound) batches 8 rows; one with fewer tasks than twice the
+// resident CTAs (latency-bound: every strip of a chain in flight at once)
+// releases every 2 rows to shorten the lag between strips.
+inline int publish_rows(int n_tasks, int resident) { return n_tasks >= 2 * resident ? 8 : 2; }
+
+// sm_create_problem for a batch member: the automatic slots-per-lane choice
+// maximises the work per warp (the batch supplies the parallelism).
+sm_status create_batch_member(const sm_problem_desc *d, void *stream, sm_problem **out);
 
 // Many problems in one persistent 2D sweep launch (sweep2d_batch_kernel).
 struct BatchSweepArgs {

@@ -296,6 +296,7 @@ sm_status sm_sweep_static(const sm_problem_desc *d, void *stream, const double *
     size_t smem = 0;
     const int resident = smk::sweep2d_max_resident(&p, p.W, p.S, &smem);
     if (resident <= 0) return static_fail(SM_ERR_UNSUPPORTED, "sweep tiling does not fit");
+    a.publish = smk::publish_rows(a.n_tasks, resident);
     ST_CUDA(smk::launch_sweep2d(&p, a, std::min(a.n_tasks, resident), s));
     ST_CUDA(smk::launch_reduce(&p, p.d_mom_acc, 1, moments ? moments : p.d_mom_tmp, closures, s));
     ST_CUDA(smk::launch_pack(&p, I_out_canon, Io, 1, s));

@@ -205,7 +205,6 @@ template <int OFF, int CNT, typename RT> struct TRed {
 constexpr int RING = 2;   // rows of x-face buffering between neighbouring warps
 constexpr int SREC = 8;   // source record: q at 4 nodes, sigma~, sigma, 2 pad
 constexpr int MROW = 36;  // padded row length of the moment transpose buffers
-constexpr int PUBLISH_ROWS = 8;  // rows per release of a strip's x-faces to the next strip
 
 // Reciprocal: the FP32 path uses the hardware approximation (relative error
 // below 2^-22, far inside the FP32 sweep's tolerance); FP64 stays IEEE.
@@ -497,10 +496,10 @@ __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &La
                 __stcg(face + ((fidx_out + y) * GW + gw) * 32 + lane, f);
             }
             __syncwarp();
-            // release the rows to the downwind strip in batches of PUBLISH_ROWS:
+            // release the rows to the downwind strip in batches of A.publish:
             // the gpu-scope fence is paid once per batch
             if (lane == 0 && !(A.fault_skip_publish && sr == 0) &&
-                ((jj + 1) % PUBLISH_ROWS == 0 || jj + 1 == ny)) {
+                ((jj + 1) % max(A.publish, 1) == 0 || jj + 1 == ny)) {
                 __threadfence();
                 st_release(myflag, ep | (unsigned long long)(jj + 1));
             }

@@ -74,7 +74,8 @@ def test_batch_equals_single_sweeps(gpu_lib, precision):
     b, T, S, Ip, Io, M, C = _run_batch(sm, MEMBERS, precision, tiling=(4, 3))
     tol = 1e-6 if precision == 32 else 1e-13
     for i, cfg in enumerate(MEMBERS):
-        p = sm.Problem.from_config(cfg, precision, strip_width=4, prefetch_rows=3)
+        p = sm.Problem.from_config(cfg, precision, strip_width=4, prefetch_rows=3,
+                                   groups_per_warp=b.members[i].info["groups_per_warp"])
         assert p.info["groups_per_warp"] == b.members[i].info["groups_per_warp"]
         Io1 = p.empty_intensity()
         m1, c1 = p.new_moments(), p.new_closures()
@@ -175,7 +176,8 @@ def test_c5_workload_batch(gpu_lib):
     order = np.argsort([c.n_cells * c.n_dir * c.n_groups for c in cfgs])[:3]
     for i in order:
         p = sm.Problem.from_config(cfgs[i], 32, strip_width=b.info()["strip_width"],
-                                   prefetch_rows=b.info()["prefetch_rows"])
+                                   prefetch_rows=b.info()["prefetch_rows"],
+                                   groups_per_warp=b.members[i].info["groups_per_warp"])
         Io1 = p.empty_intensity()
         p.sweep(T[i], S[i], None, Io1)
         p.synchronize()
@@ -191,8 +193,8 @@ def test_problems_sharing_a_kernel_launch_in_any_order(gpu_lib):
     sm = gpu_lib
     big = _cfg(10, 12, 10, 32, 2, 4)
     small = _cfg(11, 9, 9, 16, 4, 8)
-    pb = sm.Problem.from_config(big, 32, strip_width=8, prefetch_rows=4)
-    ps = sm.Problem.from_config(small, 32, strip_width=2, prefetch_rows=2)
+    pb = sm.Problem.from_config(big, 32, strip_width=8, prefetch_rows=4, groups_per_warp=8)
+    ps = sm.Problem.from_config(small, 32, strip_width=2, prefetch_rows=2, groups_per_warp=8)
     assert pb.info["groups_per_warp"] == ps.info["groups_per_warp"] == 8
     for p, cfg in ((pb, big), (ps, small), (pb, big)):
         T, S, Ip = _inputs(sm, p, cfg, seed=1)
