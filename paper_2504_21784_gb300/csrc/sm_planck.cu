@@ -2,20 +2,21 @@
 // multigroup opacity, emission source (row a1), boundary inflow and the
 // closures recomputed from a temperature (row a4 standalone).
 //
-// P(x) = (15/pi^4) int_0^x t^3/(e^t-1) dt is evaluated with the two series
-// used by Clark (Sec. 2, Eq. planck and the b_g definition):
-//   x <  2: x^3/3 - x^4/8 + sum_k B_2k x^(2k+3) / ((2k)! (2k+3))
-//   x >= 2: 1 - (15/pi^4) sum_n e^{-nx} (x^3/n + 3x^2/n^2 + 6x/n^3 + 6/n^4)
+// P(x) = (15/pi^4) int_0^x t^3/(e^t-1) dt rests on the two series used by
+// Clark (Sec. 2, Eq. planck and the b_g definition):
+//   small x: x^3/3 - x^4/8 + sum_k B_2k x^(2k+3) / ((2k)! (2k+3))
+//   large x: 1 - (15/pi^4) sum_n e^{-nx} (x^3/n + 3x^2/n^2 + 6x/n^3 + 6/n^4)
 // and the Rosseland integral by parts, R(x) = P(x) - (15/4pi^4) x^4/(e^x-1),
-// which gives r_g with dB_g/dT = 4 a c T^3 r_g (Sec. 2); for x < 2 the factor
-// x/(e^x-1) is the Bernoulli generating series itself.  Between x = 1 and
-// x = 37, where those series need the most terms, both functions come from
-// degree-7 Taylor expansions about the nearest of the centres 1, 1 + 1/8,
-// ..., 37 (|x - c| <= 1/16), whose coefficients the host derives once from
-// P'(x) = (15/pi^4) x^3/(e^x - 1) in extended precision.  A group whose lower
-// reduced edge is in the tail branch is differenced in tails (1 - P) to keep
-// relative accuracy; the lowest edge is 0 and the highest infinity so that
-// sum_g b_g = 1.
+// which gives r_g with dB_g/dT = 4 a c T^3 r_g (Sec. 2); for small x the
+// factor x/(e^x-1) is the Bernoulli generating series itself.  The GPU takes
+// the first series for x < 1, the first term of the second for x >= 37 (the
+// next is below double rounding), and in between, where both series need the
+// most terms, degree-7 Taylor expansions about the nearest of the centres 1,
+// 1 + 1/16, ..., 37 (|x - c| <= 1/32), whose coefficients the host derives
+// once from P'(x) = (15/pi^4) x^3/(e^x - 1) in extended precision.  A group
+// whose lower reduced edge is at or above the switch near x = 2 is differenced
+// in tails (1 - P) to keep relative accuracy; the lowest edge is 0 and the
+// highest infinity so that sum_g b_g = 1.
 #include <math.h>
 
 #include "sm_internal.cuh"
@@ -23,8 +24,6 @@
 namespace smk {
 
 constexpr int NBERN = 18;   // head terms: (2/2pi)^36 < 1e-17
-constexpr int NTAIL = 24;   // tail terms: e^{-2*24} ~ 1e-21
-constexpr double XSWITCH = 2.0;
 // from x = 37 on, e^{-x} < 1e-16: the tail series keeps its first term only
 constexpr double XCLOSED = 37.0;
 constexpr double PI_D = 3.14159265358979323846;
@@ -35,7 +34,6 @@ constexpr double C15 = 15.0 / (PI_D * PI_D * PI_D * PI_D);
 // Euler-Maclaurin tail (k >= 2) and zeta(2) = pi^2/6.
 __constant__ double c_head[NBERN];
 __constant__ double c_bern[NBERN];   // B_2k/(2k)!, k = 1..NBERN
-__constant__ double c_inv_n[NTAIL][4];
 // e^{-x} by the table-driven method of Tang (ACM TOMS 15, 1989): 64/ln2, and
 // ln2/64 split into a 32-bit high part (exact products with the step index)
 // and the rounded remainder; the table holds 2^{-j/64}, j = 0..63.
@@ -45,10 +43,11 @@ __device__ double g_exp2_tab[64];
 // NTAY coefficients in h = x - c_j, (P, R) for c_j < 2 and (1 - P, 1 - R) for
 // c_j >= 2 (so that the tails keep their relative accuracy).
 constexpr double XT0 = 1.0, XT1 = 37.0;
-constexpr int TSTEP = 8;   // centres per unit of x
-constexpr int NCEN = 289;  // (XT1 - XT0) * TSTEP + 1
-constexpr int NTAY = 9;    // remainder (1/16 / 2pi)^9 < 1e-17 of the leading term
-constexpr int JSW = 8;     // centres j < JSW lie below XSWITCH
+constexpr int TSTEP = 16;  // centres per unit of x
+constexpr int NCEN = 577;  // (XT1 - XT0) * TSTEP + 1
+constexpr int NTAY = 8;    // remainder (1/32 / 2pi)^8 < 1e-18 of the leading term
+constexpr int JSW = 16;    // centres j < JSW lie below x = 2: P, R; from there on 1 - P, 1 - R
+static_assert(XT1 == XCLOSED, "the Taylor tables end where the one-term tail takes over");
 __device__ double g_ptab[NCEN][2][NTAY];
 __device__ double g_pcen[NCEN];
 
@@ -148,17 +147,8 @@ void planck_upload_tables(void) {
     planck_taylor_tables(ptab);
     double pcen[NCEN];
     for (int j = 0; j < NCEN; ++j) pcen[j] = XT0 + (double)j / TSTEP;
-    double invn[NTAIL][4];
-    for (int n = 1; n <= NTAIL; ++n) {
-        double r = 1.0 / n;
-        invn[n - 1][0] = r;
-        invn[n - 1][1] = r * r;
-        invn[n - 1][2] = r * r * r;
-        invn[n - 1][3] = r * r * r * r;
-    }
     if (cudaMemcpyToSymbol(c_head, head, sizeof(head)) == cudaSuccess &&
         cudaMemcpyToSymbol(c_bern, bern, sizeof(bern)) == cudaSuccess &&
-        cudaMemcpyToSymbol(c_inv_n, invn, sizeof(invn)) == cudaSuccess &&
         cudaMemcpyToSymbol(c_exp, cexp, sizeof(cexp)) == cudaSuccess &&
         cudaMemcpyToSymbol(g_exp2_tab, tab, sizeof(tab)) == cudaSuccess &&
         cudaMemcpyToSymbol(g_ptab, ptab, sizeof(ptab)) == cudaSuccess &&
@@ -166,38 +156,25 @@ void planck_upload_tables(void) {
         g_tables_ready[dev] = true;
 }
 
-// 1/d for d in [1/2, 1] by the Newton-Raphson reciprocal iteration
-// r <- r (2 - d r) from an FP32 seed (relative error below 2^-23): each step
-// squares the error, so two steps reach double rounding.  Four FMAs, where a
-// correctly rounded FP64 division costs several times more on this GPU.
-__device__ __forceinline__ double recip_nr(double d) {
-    double r = (double)__frcp_rn((float)d);
-    r = fma(r, fma(-d, r, 1.0), r);
-    r = fma(r, fma(-d, r, 1.0), r);
-    return r;
-}
-
-// Values of the cumulative spectra at one reduced edge x = nu/T.
+// Values of the cumulative spectra at one reduced edge x = nu/T, in the form
+// the group differences need: below the switch (tail false) v = P(x),
+// rv = R(x); from the switch on (tail true) v = 1 - P(x), rv = 1 - R(x), which
+// keeps the relative accuracy of the tails.  The switch sits at x = 2 (the
+// first table centre at or above it takes the tail form, so inside the table
+// it falls at 2 - 1/32); tail is non-decreasing in x.
 struct EdgeVals {
-    double P, Q;   // P(x), 1 - P(x)
-    double R, RQ;  // R(x), 1 - R(x)
-    bool tail;     // x in the tail branch
+    double v, rv;
+    bool tail;
 };
 
-// Terms of the head series (x < 2) needed for a truncation error below 2^-56
-// of its leading term, and of the tail series (2 <= x < 37): the first
-// omitted tail term, e^{-N x}/(N+1) of the first, is below 2^-55 for
-// N = ceil(38.2/x).
-// Both are decided in FP32 on xf = (float)x: a count only needs to be large
-// enough, and FP64 compares and divisions are scarce on this GPU.
+// Terms of the head series (x < 1) for a truncation error below 2^-56 of its
+// leading term, decided in FP32 on xf (a count only needs to be large enough,
+// and FP64 compares are scarce on this GPU).
 __device__ __forceinline__ bool in_taylor(float xf) {
     return xf >= (float)XT0 && xf < (float)XT1;
 }
 __device__ __forceinline__ int head_terms(float xf) {
     return xf <= 0.25f ? 6 : xf <= 0.5f ? 7 : xf <= 1.0f ? 10 : xf <= 1.5f ? 14 : NBERN;
-}
-__device__ __forceinline__ int tail_terms(float xf) {
-    return min(NTAIL, (int)ceilf(__fdividef(38.25f, xf)));
 }
 
 // e^{-x} for 0 <= x < 708 (normal results): x = N ln2/64 + r with
@@ -218,19 +195,19 @@ __device__ __forceinline__ double exp_neg(double x) {
     return __ldg(&g_exp2_tab[n & 63]) * p * scale;
 }
 
-// K, N: head and tail term counts to use (at least head_terms(x) and
-// tail_terms(x)); callers that keep a warp converged pass the warp maximum,
-// so that every lane reads the same coefficient at each step.
-// xf: x rounded to FP32 or computed in FP32 (it only steers branches and
-// term counts, which all have margin for its relative error below 1e-6).
-__device__ __forceinline__ EdgeVals edge_vals(double x, float xf, int K, int N) {
+// K: head-series terms to use (at least head_terms(xf)); callers that keep a
+// warp converged pass the warp maximum, so that every lane reads the same
+// coefficient at each step.  xf: x rounded to FP32 or computed in FP32 (it
+// only steers branches and term counts, which have margin for its relative
+// error below 1e-6).
+__device__ __forceinline__ EdgeVals edge_vals(double x, float xf, int K) {
     EdgeVals e;
-    if (!(xf > 0.0f)) {
-        e.P = 0.0; e.Q = 1.0; e.R = 0.0; e.RQ = 1.0; e.tail = false;
+    if (!(xf > 0.0f)) {  // x = 0: P = R = 0
+        e.v = 0.0; e.rv = 0.0; e.tail = false;
         return e;
     }
-    if (isinf(xf)) {
-        e.P = 1.0; e.Q = 0.0; e.R = 1.0; e.RQ = 0.0; e.tail = true;
+    if (isinf(xf)) {     // x = infinity: 1 - P = 1 - R = 0
+        e.v = 0.0; e.rv = 0.0; e.tail = true;
         return e;
     }
     if (in_taylor(xf)) {
@@ -243,15 +220,12 @@ __device__ __forceinline__ EdgeVals edge_vals(double x, float xf, int K, int N) 
             a = fma(a, h, __ldg(t + k));
             b = fma(b, h, __ldg(t + NTAY + k));
         }
-        if (j < JSW) {
-            e.P = a; e.Q = 1.0 - a; e.R = b; e.RQ = 1.0 - b;
-        } else {
-            e.Q = a; e.P = 1.0 - a; e.RQ = b; e.R = 1.0 - b;
-        }
-        e.tail = xf >= (float)XSWITCH;
+        e.v = a; e.rv = b; e.tail = j >= JSW;  // the table holds the same forms
         return e;
     }
-    if (xf < (float)XSWITCH) {
+    if (xf < (float)XT0) {
+        // head series: P = (15/pi^4) (x^3/3 - x^4/8 + sum d_k x^(2k+3)), and
+        // x^4/(e^x - 1) = x^3 (1 - x/2 + sum B_2k x^2k/(2k)!)
         const double y = x * x;
         double poly = c_head[K - 1], pb = c_bern[K - 1];
         for (int k = K - 2; k >= 0; --k) {
@@ -261,64 +235,44 @@ __device__ __forceinline__ EdgeVals edge_vals(double x, float xf, int K, int N) 
         poly *= y;
         pb *= y;
         const double x3 = y * x;
-        const double s = x3 * ((1.0 / 3.0) - 0.125 * x + poly);
-        e.P = C15 * s;
-        e.Q = 1.0 - e.P;
-        // x^4/(e^x - 1) = x^3 * x/(e^x - 1), with x/(e^x - 1) = 1 - x/2 + sum B_2k x^2k/(2k)!
-        const double rx = 0.25 * C15 * x3 * (1.0 - 0.5 * x + pb);
-        e.R = e.P - rx;
-        e.RQ = e.Q + rx;
+        const double P = C15 * (x3 * ((1.0 / 3.0) - 0.125 * x + poly));
+        e.v = P;
+        e.rv = P - 0.25 * C15 * x3 * (1.0 - 0.5 * x + pb);
         e.tail = false;
         return e;
     }
+    // x >= 37: only the n = 1 term of the tail series is above double rounding,
+    // 1 - P = (15/pi^4) e^{-x} (x^3 + 3x^2 + 6x + 6), and 1/(1 - e^{-x}) = 1
     const double e1 = xf < 708.0f ? exp_neg(x) : exp(-x);
     const double x2 = x * x;
-    if (xf >= (float)XCLOSED) {
-        // only the n = 1 term is above double rounding: 1 - P = (15/pi^4) e^{-x}
-        // (x^3 + 3x^2 + 6x + 6), and 1/(1 - e^{-x}) = 1
-        e.Q = C15 * e1 * fma(fma(x + 3.0, x, 6.0), x, 6.0);
-        e.P = 1.0 - e.Q;
-        const double rx = 0.25 * C15 * (x2 * x2) * e1;
-        e.R = e.P - rx;
-        e.RQ = e.Q + rx;
-        e.tail = true;
-        return e;
-    }
-    // sum_n u^n (x^3/n + 3x^2/n^2 + 6x/n^3 + 6/n^4) = x^3 Li_1(u) + 3x^2 Li_2(u)
-    // + 6x Li_3(u) + 6 Li_4(u), u = e^{-x}, each polylogarithm by Horner in u
-    const int nmax = N;
-    double L1 = 0.0, L2 = 0.0, L3 = 0.0, L4 = 0.0;
-    for (int n = nmax - 1; n >= 0; --n) {
-        L1 = fma(L1, e1, c_inv_n[n][0]);
-        L2 = fma(L2, e1, c_inv_n[n][1]);
-        L3 = fma(L3, e1, c_inv_n[n][2]);
-        L4 = fma(L4, e1, c_inv_n[n][3]);
-    }
-    const double sum = e1 * fma(x2 * x, L1, fma(3.0 * x2, L2, fma(6.0 * x, L3, 6.0 * L4)));
-    e.Q = C15 * sum;
-    e.P = 1.0 - e.Q;
-    const double rx = 0.25 * C15 * (x2 * x2) * e1 * recip_nr(1.0 - e1);
-    e.R = e.P - rx;
-    e.RQ = e.Q + rx;
+    const double Q = C15 * e1 * fma(fma(x + 3.0, x, 6.0), x, 6.0);
+    e.v = Q;
+    e.rv = Q + 0.25 * C15 * (x2 * x2) * e1;
     e.tail = true;
     return e;
 }
 
 __device__ __forceinline__ EdgeVals edge_vals(double x) {
     const float xf = (float)x;
-    return edge_vals(x, xf, (xf < (float)XSWITCH && !in_taylor(xf)) ? head_terms(xf) : 1,
-                     (xf >= (float)XSWITCH && !in_taylor(xf)) ? tail_terms(xf) : 1);
+    return edge_vals(x, xf, xf < (float)XT0 ? head_terms(xf) : 1);
 }
 
-// b_g and r_g of the group between reduced edges lo < hi
+// b_g and r_g of the group between reduced edges lo < hi (lo.tail implies
+// hi.tail): differences of tails when the lower edge is in the tail form,
+// else of P and R (converting the upper edge where it crosses the switch)
 __device__ __forceinline__ void group_br(const EdgeVals &lo, const EdgeVals &hi, double &b,
                                          double &r) {
     if (lo.tail) {
-        b = lo.Q - hi.Q;
-        r = lo.RQ - hi.RQ;
+        b = lo.v - hi.v;
+        r = lo.rv - hi.rv;
     } else {
-        b = hi.P - lo.P;
-        r = hi.R - lo.R;
+        double hv = hi.v, hr = hi.rv;
+        if (hi.tail) {
+            hv = 1.0 - hv;
+            hr = 1.0 - hr;
+        }
+        b = hv - lo.v;
+        r = hr - lo.rv;
     }
 }
 
@@ -386,16 +340,11 @@ __global__ void emission_kernel(int ncell, int nn, int G, int Gp, const double *
         // beyond x ~ 745 the tails 1 - P and 1 - R underflow to exactly 0, so
         // every higher group has b = r = 0: skip their series (tested on the
         // bits, both tails being +0 there)
-        const bool skip = lo.tail && ((__double_as_longlong(lo.Q) |
-                                       __double_as_longlong(lo.RQ)) == 0);
-        const bool tab = in_taylor(xf);
-        const int K = __reduce_max_sync(
-            0xffffffffu, (!skip && !tab && xf < (float)XSWITCH) ? head_terms(xf) : 1);
-        const int N = __reduce_max_sync(
-            0xffffffffu, (!skip && !tab && xf >= (float)XSWITCH && xf < (float)XCLOSED)
-                             ? tail_terms(xf)
-                             : 1);
-        const EdgeVals hi = skip ? lo : edge_vals(xhi, xf, K, N);
+        const bool skip = lo.tail && ((__double_as_longlong(lo.v) |
+                                       __double_as_longlong(lo.rv)) == 0);
+        const int K = __reduce_max_sync(0xffffffffu,
+                                        (!skip && xf < (float)XT0) ? head_terms(xf) : 1);
+        const EdgeVals hi = skip ? lo : edge_vals(xhi, xf, K);
         double b, r;
         group_br(lo, hi, b, r);
         const double sg = sigma[(size_t)g * ncell + cell];
@@ -450,7 +399,7 @@ __global__ void planck_parts_kernel(int ncell, int nn, int G, const double *__re
     double s = 0.0;
     for (int g = 0; g < G; ++g) {
         const double xhi = (g == G - 1) ? INFINITY : edges[g + 1] * invT;
-        const EdgeVals hi = (lo.tail && lo.Q == 0.0 && lo.RQ == 0.0) ? lo : edge_vals(xhi);
+        const EdgeVals hi = (lo.tail && lo.v == 0.0 && lo.rv == 0.0) ? lo : edge_vals(xhi);
         double b, r;
         group_br(lo, hi, b, r);
         const double sg = sigma[(size_t)g * ncell + cell];
