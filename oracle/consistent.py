@@ -1,5 +1,5 @@
 """Consistent SM low-order sources (Sec. 4, consistent method) for the lumped
-upwind DG transport discretization, 2D.
+upwind DG transport discretization, 1D slab and 2D.
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
@@ -32,6 +32,11 @@ plus the volume terms of the independent method (int v.sum_g (sigma_F -
 sigma_g) F_g and int grad v : T).  Reading: the paper's garbled half-range
 macros are these quantities, and its phi_HO in the boundary and P terms is the
 energy density E_HO (dimensional consistency with c alpha and c/3).
+
+In 1D the faces are points (w_f = 1), n = +-1, and the two half ranges are
+the directions with mu > 0 and mu < 0; they are stored in the layout of the 2D
+quadrant moments (mu > 0 as quadrant (+,+), mu < 0 as (-,+), the other two
+zero; components phi, F, 0, Pi, 0, 0) so that the same half-range sums apply.
 """
 from __future__ import annotations
 
@@ -41,6 +46,20 @@ from . import lo as L
 
 # canonical quadrant order (signs of Omega_x, Omega_y)
 QUAD_SIGNS = ((1, 1), (-1, 1), (-1, -1), (1, -1))
+
+
+def half_moments_1d(mu, w, I):
+    """1D: qm[cell][node][q][k] in the 2D quadrant layout: q = 0 sums the
+    directions with mu > 0, q = 1 those with mu < 0 (q = 2, 3 zero); k: phi,
+    F = sum w mu I, 0, Pi = sum w mu^2 I, 0, 0.  I canonical [d][g][cell][node]."""
+    Ig = I.sum(axis=1)
+    ncell, nn = Ig.shape[1:]
+    qm = np.zeros((ncell, nn, 4, 6))
+    for q, sel in ((0, mu > 0), (1, mu < 0)):
+        m_, ww, X = mu[sel], w[sel], Ig[sel]
+        for k, f in ((0, ww), (1, ww * m_), (3, ww * m_ * m_)):
+            qm[:, :, q, k] = np.einsum("d,dkn->kn", f, X)
+    return qm
 
 
 def quadrant_moments(omx, omy, w, I):
@@ -86,26 +105,30 @@ def inflow_moments(omx, omy, w, I_in, n):
 
 
 def consistent_sources(m: L.Mesh, c, alpha, clo, omx, omy, w, I, I_in_side):
-    """(R1, bnd): the first-moment source (flattened [node][2]) and the
+    """(R1, bnd): the first-moment source (flattened [node][dim]) and the
     zeroth-moment face source (replacing the independent boundary source) of
     the consistent method, from the high-order intensity I [d][g][cell][node],
     the closures clo (volume terms) and the gray inflow per side."""
-    assert m.dim == 2
+    D = m.dim
     N = m.nnode
-    qm = quadrant_moments(omx, omy, w, I).reshape(N, 4, 6)
+    if D == 1:
+        qm = half_moments_1d(omx, w, I).reshape(N, 4, 6)
+    else:
+        qm = quadrant_moments(omx, omy, w, I).reshape(N, 4, 6)
     tot = qm.sum(axis=1)
     phi = tot[:, 0]
     E = phi / c
-    F = tot[:, 1:3]
+    F = tot[:, 1:1 + D]
     hr = {}
     for n in ((1.0, 0.0), (-1.0, 0.0), (0.0, 1.0), (0.0, -1.0)):
         hr[n] = half_range(qm, n)
     R0 = np.zeros(N)
-    R1 = L.closure_sources(m, clo, face_term=False).reshape(N, 2)
+    R1 = L.closure_sources(m, clo, face_term=False).reshape(N, D)
     for kind, n, wf, pairs in L.faces(m):
-        nv = np.array(n[:2])
+        nv = np.array(n[:D])
         key = (float(n[0]), float(n[1]))
         Fp, Fm, Pp, Pm = hr[key]
+        Pp, Pm = Pp[:, :D], Pm[:, :D]
         if kind == "int":
             for n1, n2 in pairs:
                 r0 = wf * (F[n1] @ nv + 0.5 * c * alpha * (E[n1] - E[n2]) - Fp[n1] - Fm[n2])
@@ -116,8 +139,8 @@ def consistent_sources(m: L.Mesh, c, alpha, clo, omx, omy, w, I, I_in_side):
                 R1[n2] -= r1
         else:
             side = n[2]
-            J_in, Pi_in = inflow_moments(omx, omy, w, I_in_side[side], nv)
+            J_in, Pi_in = inflow_moments(omx, omy, w, I_in_side[side], np.array(n[:2]))
             for nb, _ in pairs:
                 R0[nb] += wf * (J_in + alpha * phi[nb] - Fp[nb])
-                R1[nb] += wf * ((c / 3.0) * nv * E[nb] - Pp[nb] - Pi_in)
+                R1[nb] += wf * ((c / 3.0) * nv * E[nb] - Pp[nb] - Pi_in[:D])
     return R1.reshape(-1), R0
