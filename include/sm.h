@@ -187,7 +187,7 @@ sm_status sm_closures(sm_problem *p, const double *moments_dev, const double *T_
 /* low-order closures (Sec. 4): independent (first-moment corrections only)
  * or consistent (face and boundary corrections from the half-range moments
  * of the high-order intensity, so that the converged low-order solution
- * equals the high-order moments; 2D) */
+ * equals the high-order moments; 1D and 2D) */
 enum { SM_METHOD_INDEPENDENT = 0, SM_METHOD_CONSISTENT = 1 };
 
 typedef struct {
@@ -233,7 +233,7 @@ void sm_default_step_params(sm_step_params *params_host);
  * Boundary: Marshak-type with the gray isotropic inflow of desc.T_bdr.
  * params->method = SM_METHOD_CONSISTENT uses the consistent sources from
  * the per-quadrant moments of the last sweep (registered with
- * sm_set_quadrant_moments; 2D).  Needs desc.dt > 0.  Errors: INVALID_ARG, NO_CONVERGENCE (conjugate
+ * sm_set_quadrant_moments).  Needs desc.dt > 0.  Errors: INVALID_ARG, NO_CONVERGENCE (conjugate
  * gradients broke down), NONPHYSICAL (non-finite iterate), CUDA, OOM (the
  * low-order workspace is allocated on first use).  A capped iteration is
  * not an error: see stats.  stats_host may be NULL. */
@@ -242,7 +242,9 @@ void sm_default_step_params(sm_step_params *params_host);
  * new intensity (quadrants in the canonical order; per quadrant phi, F_x,
  * F_y, Pi_xx, Pi_xy, Pi_yy with Pi = sum w Omega Omega I, all groups): the
  * input of the consistent method, from which every half-range current and
- * second moment on axis-aligned faces follows.  2D only.  The moment
+ * second moment on axis-aligned faces follows.  1D: quadrant 0 holds the
+ * directions with mu > 0, quadrant 1 those with mu < 0 (phi, F, 0, Pi_xx,
+ * 0, 0; quadrants 2 and 3 zero), the same layout.  In 2D the moment
  * accumulator grows to four quadrants (allocated here).  Synchronizes. */
 sm_status sm_set_quadrant_moments(sm_problem *p, double *qmom_dev);
 

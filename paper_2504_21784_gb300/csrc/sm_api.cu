@@ -230,8 +230,8 @@ sm_status sweep_pass(sm_problem *p, const void *I_prev, void *I_out, double *mom
     ++p->epoch;
     smk::SweepArgs a = make_args(p, I_prev, I_out);
     a.reverse = reverse;
-    const bool qm = p->qmom_dev != nullptr && p->dim == 2 && !reverse;
-    a.qmom = qm ? 1 : 0;
+    const bool qm = p->qmom_dev != nullptr && !reverse;
+    a.qmom = qm && p->dim == 2 ? 1 : 0;  // 1D: the per-warp partials are per half already
     if (p->dim == 2) {
         SM_CUDA(cudaMemsetAsync(p->d_ctrl, 0, 2 * sizeof(unsigned int), s));
         SM_CUDA(cudaMemsetAsync(p->d_mom_acc, 0, (size_t)(qm ? 4 : 1) * p->ncell * 36 * p->rsize,
@@ -249,7 +249,8 @@ sm_status sweep_pass(sm_problem *p, const void *I_prev, void *I_out, double *mom
             SM_CUDA(smk::launch_reduce(p, p->d_mom_acc, qm ? 4 : 1, m, clo, s,
                                        qm ? p->qmom_dev : nullptr));
         else
-            SM_CUDA(smk::launch_reduce(p, p->d_part, p->NQ * p->NWT, m, clo, s));
+            SM_CUDA(smk::launch_reduce(p, p->d_part, p->NQ * p->NWT, m, clo, s,
+                                       qm ? p->qmom_dev : nullptr, p->NWT));
         p->launches++;
     }
     return SM_OK;
@@ -717,10 +718,9 @@ sm_status sm_synchronize(sm_problem *p) {
 
 sm_status sm_set_quadrant_moments(sm_problem *p, double *qmom_dev) {
     if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
-    if (p->dim != 2) return fail(SM_ERR_UNSUPPORTED, "quadrant moments are 2D only");
     if (p->batch_owned) return fail(SM_ERR_INVALID_ARG, "this problem belongs to a batch");
     SM_CUDA(cudaStreamSynchronize(p->stream));
-    if (qmom_dev && !p->qmom_acc4) {
+    if (qmom_dev && p->dim == 2 && !p->qmom_acc4) {
         // the moment accumulator becomes [quadrant][cell][36]
         sm_status st = dev_alloc(&p->d_mom_acc, (size_t)4 * p->ncell * 36 * p->rsize, nullptr);
         if (st) return st;

@@ -94,7 +94,8 @@ cudaError_t launch_closures_from_T(const sm_problem *p, const double *mom, const
 cudaError_t launch_sweep2d(const sm_problem *p, const SweepArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_sweep1d(const sm_problem *p, const SweepArgs &a, cudaStream_t s);
 cudaError_t launch_reduce(const sm_problem *p, const void *part, int n_part, double *mom,
-                          double *clo, cudaStream_t s, double *qmom = nullptr);
+                          double *clo, cudaStream_t s, double *qmom = nullptr,
+                          int sets_per_q = 1);
 cudaError_t launch_pack(const sm_problem *p, const double *canon, void *packed, int unpack,
                         cudaStream_t s);
 int sweep2d_max_resident(const sm_problem *p, int W, int S, size_t *smem_out);

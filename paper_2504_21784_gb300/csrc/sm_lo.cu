@@ -439,6 +439,46 @@ consistent_kernel(Geo G, const double *__restrict__ qm, const double *__restrict
     }
 }
 
+// The same corrections on the 1D slab (point faces, w_f = 1, n = +-1): the
+// half ranges of mu > 0 and mu < 0 are quadrants 0 and 1 of the moment
+// layout, so half_pos_axis(., ., 0) applies unchanged.  One thread per cell.
+__global__ void __launch_bounds__(BLOCK)
+consistent1d_kernel(Geo G, const double *__restrict__ qm, const double *__restrict__ jin,
+                    const double *__restrict__ pin, double *__restrict__ R0,
+                    double *__restrict__ R1f) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= G.ncell) return;
+    const double ca2 = 0.5 * G.c * G.alpha, c3 = G.c3, ic = 1.0 / G.c;
+    for (int a = 0; a < 2; ++a) {
+        const int j = k * 2 + a;
+        const double phi = qm_tot(qm, j, 0), Ej = phi * ic;
+        const bool high = a == 1;  // node on the +x face of its cell
+        const bool has_nb = high ? k + 1 < G.nx : k > 0;
+        const Half hj = half_pos_axis(qm, j, 0);
+        double r0, r1;
+        if (has_nb) {
+            const int jn = high ? j + 1 : j - 1;  // the neighbour cell's node on this face
+            const Half hn = half_pos_axis(qm, jn, 0);
+            const double En = qm_tot(qm, jn, 0) * ic;
+            const Half &h1 = high ? hj : hn, &h2 = high ? hn : hj;
+            const double E1 = high ? Ej : En, E2 = high ? En : Ej;
+            const double F1n = qm_tot(qm, high ? j : jn, 1);
+            const double sgn = high ? 1.0 : -1.0;
+            r0 = sgn * (F1n + ca2 * (E1 - E2) - h1.Fp - h2.Fm);
+            r1 = sgn * (c3 * E2 - h1.Pp[0] - h2.Pm[0]);
+        } else {
+            const double sn = high ? 1.0 : -1.0;
+            const int side = high ? 1 : 0;
+            const double Fp = high ? hj.Fp : -hj.Fm;
+            const double Px = high ? hj.Pp[0] : -hj.Pm[0];
+            r0 = jin[side] + G.alpha * phi - Fp;
+            r1 = c3 * sn * Ej - Px - pin[side * 2];
+        }
+        R0[j] = r0;
+        R1f[j] = r1;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // E* = phi / c and F* = F from the moments of the previous step's intensity
 // (the high-order time-edge sources of Sec. 6.1).  One thread per node.
@@ -919,7 +959,7 @@ sm_status lo_ensure(sm_problem *p) {
     const size_t nblk = (size_t)std::max(w.nblk_cell, w.nblk_node);
     LO_CUDA(cudaMalloc(&w.part, sizeof(double) * 3 * nblk));
     LO_CUDA(cudaMalloc(&w.jin2, sizeof(double) * 4));
-    if (p->dim == 2) {
+    {  // consistent method: R0 [N], R1f [N][dim], quadrant moments, inflow moments
         LO_CUDA(cudaMalloc(&w.R0, sizeof(double) * (size_t)N * 3));
         w.R1f = w.R0 + N;
         LO_CUDA(cudaMalloc(&w.qmom_int, sizeof(double) * (size_t)N * 24));
@@ -951,7 +991,7 @@ sm_status lo_ensure(sm_problem *p) {
         jin2[s] = 2.0 * acc * Iin;
     }
     LO_CUDA(cudaMemcpy(w.jin2, jin2, sizeof(jin2), cudaMemcpyHostToDevice));
-    if (p->dim == 2) {
+    {
         // consistent method: J_in = sum_{Omega.n<0} w |Omega.n| I_in and
         // Pi_in = sum_{Omega.n<0} w Omega (Omega.n) I_in per side
         double jp[12] = {0};
@@ -959,11 +999,12 @@ sm_status lo_ensure(sm_problem *p) {
             const double Tb = p->desc.T_bdr[s];
             const double Iin = Tb > 0 ? p->desc.a * p->desc.c * Tb * Tb * Tb * Tb / (4.0 * PI) : 0.0;
             for (int d = 0; d < p->nd; ++d) {
-                const double on = p->omx[d] * nrm[s][0] + p->omy[d] * nrm[s][1];
+                const double oy = p->dim == 2 ? p->omy[d] : 0.0;
+                const double on = p->omx[d] * nrm[s][0] + oy * nrm[s][1];
                 if (on < 0) {
                     jp[s] += p->w[d] * -on * Iin;
                     jp[4 + 2 * s] += p->w[d] * p->omx[d] * on * Iin;
-                    jp[4 + 2 * s + 1] += p->w[d] * p->omy[d] * on * Iin;
+                    jp[4 + 2 * s + 1] += p->w[d] * oy * on * Iin;
                 }
             }
         }
@@ -1005,9 +1046,13 @@ sm_status lo_solve(sm_problem *p, const double *clo, const double *Tstar, const 
     cudaStream_t s = p->stream;
     const double dt = p->desc.dt, a = p->desc.a;
     const double *R0 = nullptr, *R1f = nullptr;
-    if (qmom) {  // consistent method (2D)
-        smk::lo::consistent_kernel<<<w.nblk_cell, BLOCK, 0, s>>>(G, qmom, w.jinc, w.pinc, w.R0,
-                                                                 w.R1f);
+    if (qmom) {  // consistent method
+        if (NN == 4)
+            smk::lo::consistent_kernel<<<w.nblk_cell, BLOCK, 0, s>>>(G, qmom, w.jinc, w.pinc,
+                                                                     w.R0, w.R1f);
+        else
+            smk::lo::consistent1d_kernel<<<w.nblk_cell, BLOCK, 0, s>>>(G, qmom, w.jinc, w.pinc,
+                                                                       w.R0, w.R1f);
         LO_CUDA(cudaGetLastError());
         p->launches++;
         R0 = w.R0;
@@ -1058,7 +1103,7 @@ sm_status run_lo(sm_problem *p, const double *clo, const double *Tstar, const do
                  double *T, double *E, double *F, const sm_step_params &prm, sm_step_stats *st,
                  const double *qmom) {
     return p->dim == 2 ? lo_solve<4>(p, clo, Tstar, cv, T, E, F, prm, st, qmom)
-                       : lo_solve<2>(p, clo, Tstar, cv, T, E, F, prm, st, nullptr);
+                       : lo_solve<2>(p, clo, Tstar, cv, T, E, F, prm, st, qmom);
 }
 
 sm_status check_lo_problem(sm_problem *p) {
@@ -1124,7 +1169,6 @@ sm_status sm_loworder_newton(sm_problem *p, const double *closures_dev, const do
     p->launches++;
     const double *qmom = nullptr;
     if (prm.method == SM_METHOD_CONSISTENT) {
-        if (p->dim != 2) return lo_fail(SM_ERR_UNSUPPORTED, "the consistent method is 2D only");
         if (!p->qmom_dev)
             return lo_fail(SM_ERR_INVALID_ARG,
                            "the consistent method needs the per-quadrant moments of the last "
@@ -1159,8 +1203,6 @@ sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, 
     const int N = w.N;
     double *clo = closures_dev ? closures_dev : w.clo;
     const bool consistent = prm.method == SM_METHOD_CONSISTENT;
-    if (consistent && p->dim != 2)
-        return lo_fail(SM_ERR_UNSUPPORTED, "the consistent method is 2D only");
     double *qmom_saved = p->qmom_dev;
     const double *qmom = nullptr;
     if (consistent) {

@@ -11,32 +11,52 @@
 
 namespace smk {
 
-// qmom (2D, sets = quadrants): per-quadrant phi, F_x, F_y and the second
-// moments Pi = sum w Omega Omega I (Pi_xx, Pi_xy, Pi_yy) per node, for the
-// consistent method's half-range closures.
+// qmom: per-quadrant phi, F_x, F_y and the second moments Pi = sum w Omega
+// Omega I (Pi_xx, Pi_xy, Pi_yy) per node, for the consistent method's
+// half-range closures; set s belongs to quadrant s / sets_per_q (2D: the sets
+// are the quadrants; 1D: the per-warp partials, NWT warps per half, with the
+// halves mu > 0 and mu < 0 as quadrants 0 and 1 and phi, F, 0, Pi_xx, 0, 0).
 template <typename RT>
 __global__ void reduce_kernel(int dim, int nnodes_total, int nm, int nsets, size_t set_stride,
                               double inv_c, const RT *__restrict__ part,
                               const double *__restrict__ gray, double *__restrict__ mom,
-                              double *__restrict__ clo, double *__restrict__ qmom) {
+                              double *__restrict__ clo, double *__restrict__ qmom,
+                              int sets_per_q) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;  // (cell, node)
     if (t >= nnodes_total) return;
     double acc[9];
 #pragma unroll
     for (int m = 0; m < 9; ++m) acc[m] = 0.0;
+    double qa[4][6];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) qa[q][k] = 0.0;
     const RT *pp = part + (size_t)t * nm;
     for (int s = 0; s < nsets; ++s) {
         const RT *ps = pp + (size_t)s * set_stride;
         for (int m = 0; m < nm; ++m) acc[m] += (double)ps[m];
         if (qmom) {
-            double *o = qmom + ((size_t)t * 4 + s) * 6;
-            const double ph = (double)ps[0];
+            const int q = min(s / sets_per_q, 3);
+            if (dim == 2) {
+                for (int k = 0; k < 6; ++k) qa[q][k] += (double)ps[k];
+            } else {
+                qa[q][0] += (double)ps[0];
+                qa[q][1] += (double)ps[1];
+                qa[q][3] += (double)ps[2];
+            }
+        }
+    }
+    if (qmom) {
+        for (int q = 0; q < 4; ++q) {
+            double *o = qmom + ((size_t)t * 4 + q) * 6;
+            const double ph = qa[q][0];
             o[0] = ph;
-            o[1] = (double)ps[1];
-            o[2] = (double)ps[2];
-            o[3] = (double)ps[3] + ph / 3.0;
-            o[4] = (double)ps[4];
-            o[5] = (double)ps[5] + ph / 3.0;
+            o[1] = qa[q][1];
+            o[2] = qa[q][2];
+            o[3] = qa[q][3] + ph / 3.0;
+            o[4] = qa[q][4];
+            o[5] = dim == 2 ? qa[q][5] + ph / 3.0 : 0.0;
         }
     }
     if (mom) {
@@ -72,7 +92,7 @@ __global__ void reduce_kernel(int dim, int nnodes_total, int nm, int nsets, size
 }
 
 cudaError_t launch_reduce(const sm_problem *p, const void *part, int n_part, double *mom,
-                          double *clo, cudaStream_t s, double *qmom) {
+                          double *clo, cudaStream_t s, double *qmom, int sets_per_q) {
     const int n = p->ncell * p->nn;
     const int threads = 128;
     const size_t stride = (size_t)n * p->nm;
@@ -80,11 +100,11 @@ cudaError_t launch_reduce(const sm_problem *p, const void *part, int n_part, dou
     if (p->prec == 32)
         reduce_kernel<float><<<(n + threads - 1) / threads, threads, 0, s>>>(
             p->dim, n, p->nm, n_part, stride, inv_c, (const float *)part, p->d_gray, mom, clo,
-            qmom);
+            qmom, sets_per_q);
     else
         reduce_kernel<double><<<(n + threads - 1) / threads, threads, 0, s>>>(
             p->dim, n, p->nm, n_part, stride, inv_c, (const double *)part, p->d_gray, mom, clo,
-            qmom);
+            qmom, sets_per_q);
     return cudaGetLastError();
 }
 
