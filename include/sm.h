@@ -68,9 +68,14 @@ typedef struct {
     double T_bdr[4];           /* boundary temperature per side: left, right, bottom, top;
                                   <= 0 means vacuum (zero inflow) */
     int precision;             /* sweep arithmetic: 32 (FP32) or 64 (FP64) */
-    int groups_per_warp;       /* (d,g) slots per lane of a warp task: 1, 2, 4, 8; 0 = auto */
-    int strip_width;           /* 2D: cell columns per CTA, one warp per column, 1..16; 0 = auto */
-    int prefetch_rows;         /* 2D: rows each warp prefetches by TMA, 2..8; 0 = auto */
+    int groups_per_warp;       /* (d,g) slots per lane of a warp task: 1, 2, 4, 8; 0 = auto:
+                                  the largest power of two up to 8 (FP32) or 4 (FP64) that
+                                  the groups fill, halved while the problem has fewer than
+                                  16 independent wavefront chains (quadrant x direction
+                                  block x group block); batch members keep the largest */
+    int strip_width;           /* 2D: cell columns per CTA, one warp per column, 1..16; 0 = auto:
+                                  the widest of 16, 12, 8, 4, 2 whose shared memory fits */
+    int prefetch_rows;         /* 2D: rows each warp prefetches by TMA, 2..8; 0 = auto (2) */
 } sm_problem_desc;
 
 typedef struct {
