@@ -35,9 +35,11 @@
 // atomic queue in upwind-strip order, so every awaited producer is already
 // running (no deadlock for any grid size), and every wait is bounded in time
 // (status word + abort flag, never a trap).  Per cell, each lane sums its GW
-// intensities, forms the 36 weighted moments, the warp reduces them by a
-// transpose-butterfly and adds them with vector atomics to an L2-resident
-// per-cell accumulator.
+// intensities (plain and sigma-weighted, per node), the warp transposes the
+// sums through shared memory, each lane forms one of the 36 weighted moments
+// as a dot product over the 32 lanes (the last four split over octets of
+// lanes and finished by shuffles), and the moments are added with atomics to
+// an L2-resident per-cell accumulator.
 #include <stdint.h>
 
 #include "sm_internal.cuh"
@@ -297,11 +299,13 @@ __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &La
     const RT two = (RT)2;
     const uint32_t bytes_I = Ip ? (uint32_t)(GW * 32 * 4 * sizeof(RT)) : 0u;
     const uint32_t bytes_S = (uint32_t)(GSLOT * SREC * sizeof(RT));
-    // moment this lane assembles (and, for lanes 0..3, a second one): m = n*9 + k
+    // moment this lane assembles whole, m = n*9 + k, and the eighth of moment
+    // 32 + lane/8 (source lanes 4 (lane % 8) .. +3) it adds to its octet's sum
     const int m1 = lane, n1 = m1 / 9, k1 = m1 % 9;
     const int vrow1 = k1 < 6 ? n1 : 4 + n1, wrow1 = k1 < 6 ? k1 : k1 - 6;
-    const int m2 = 32 + (lane & 3), k2 = m2 % 9;
+    const int m2 = 32 + (lane >> 3), k2 = m2 % 9;
     const int vrow2 = k2 < 6 ? 3 : 7, wrow2 = k2 < 6 ? k2 : k2 - 6;
+    const int c2 = 4 * (lane & 7);
     const int NWG = A.NQ * A.NWT;
     const int sr = task / NWG, wg = task - sr * NWG;
     constexpr int q = Q;
@@ -516,25 +520,29 @@ __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &La
         }
         __syncwarp();
         // four partial sums per dot product: dependent chains of 8, not 32
-        RT d1p[4] = {0, 0, 0, 0}, d2p[4] = {0, 0, 0, 0};
+        RT d1p[4] = {0, 0, 0, 0};
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            RT a[4], b[4], c[4], e4[4];
+            RT a[4], b[4];
             lds4(Mb + vrow1 * MROW + 4 * i, a);
             lds4(Wt + wrow1 * MROW + 4 * i, b);
-            lds4(Mb + vrow2 * MROW + 4 * i, c);
-            lds4(Wt + wrow2 * MROW + 4 * i, e4);
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                d1p[t] = fma(a[t], b[t], d1p[t]);
-                d2p[t] = fma(c[t], e4[t], d2p[t]);
-            }
+            for (int t = 0; t < 4; ++t) d1p[t] = fma(a[t], b[t], d1p[t]);
         }
         const RT d1 = (d1p[0] + d1p[1]) + (d1p[2] + d1p[3]);
-        const RT d2 = (d2p[0] + d2p[1]) + (d2p[2] + d2p[3]);
+        RT d2;
+        {
+            RT c[4], e4[4];
+            lds4(Mb + vrow2 * MROW + c2, c);
+            lds4(Wt + wrow2 * MROW + c2, e4);
+            d2 = fma(c[3], e4[3], fma(c[2], e4[2], fma(c[1], e4[1], c[0] * e4[0])));
+            d2 += __shfl_xor_sync(0xffffffffu, d2, 1);
+            d2 += __shfl_xor_sync(0xffffffffu, d2, 2);
+            d2 += __shfl_xor_sync(0xffffffffu, d2, 4);
+        }
         RT *ac = acc + ((size_t)(A.qmom ? q * A.ncell : 0) + cell) * 36;
         atomicAdd(ac + m1, d1);
-        if (lane < 4) atomicAdd(ac + m2, d2);
+        if ((lane & 7) == 0) atomicAdd(ac + m2, d2);
         // the stage is free: prefetch row jj + S into it (the proxy fence
         // orders this warp's reads and writes of it before the copy)
         __syncwarp();
