@@ -25,12 +25,11 @@
 // 1/diag(S) precomputed so that conjugate-gradient iterations divide nothing,
 // and the pointwise temperature Newton step taken with an FP32 reciprocal of
 // its derivative (a quasi-Newton step: the root is unchanged).  PCG scalars
-// never leave the device: every grid-wide sum is finished by the last block
-// to arrive (deterministic fixed-order sums, no floating-point atomics), and
-// the iteration runs as a device-side WHILE loop (a conditional node of a
-// CUDA graph) whose condition a one-thread kernel clears when the iteration
-// has converged, broken down or reached its cap -- that kernel also counts
-// loop trips against a hard bound, so the loop always ends.
+// never leave the device: grid-wide sums are deterministic fixed-order sums
+// (no floating-point atomics), and the whole conjugate-gradient solve of a
+// Newton iteration is one cooperative launch whose blocks meet at grid
+// barriers with bounded waits, so the host synchronises once per Newton
+// iteration (its stopping test) whatever the number of PCG iterations.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -42,14 +41,13 @@ namespace smk {
 namespace lo {
 
 constexpr int BLOCK = 128;
-enum { DONE_NO = 0, DONE_CONVERGED = 1, DONE_BREAKDOWN = 2, DONE_CAPPED = 3 };
+enum { DONE_NO = 0, DONE_CONVERGED = 1, DONE_BREAKDOWN = 2, DONE_CAPPED = 3, DONE_TIMEOUT = 4 };
 
 struct Scalars {
     double alpha, beta, rz, bnorm, rr, d2, n2, rtol;
     int done, iters, max_iters, elim_max;
-    int body_runs;       // trips of the device loop in the running solve
     unsigned int count;  // arrivals of the running kernel's blocks
-    int pad[2];
+    unsigned int bar_count, bar_gen;  // grid barrier of the persistent PCG kernel
 };
 
 struct Geo {
@@ -112,6 +110,31 @@ struct Dir {
         double a[NN], b[NN];
         ldc<NN>(z, k, a);
         ldc<NN>(p, k, b);
+#pragma unroll
+        for (int i = 0; i < NN; ++i) o[i] = fma(beta, b[i], a[i]);
+    }
+};
+
+// The same with loads that bypass L1 (ld.global.cg): for values other blocks
+// of the running kernel wrote (the persistent PCG kernel's z and p).
+template <int NN>
+__device__ __forceinline__ void ldc_cg(const double *a, int k, double (&v)[NN]) {
+    const double2 *p = reinterpret_cast<const double2 *>(a + (size_t)k * NN);
+#pragma unroll
+    for (int i = 0; i < NN / 2; ++i) {
+        const double2 t = __ldcg(p + i);
+        v[2 * i] = t.x;
+        v[2 * i + 1] = t.y;
+    }
+}
+template <int NN>
+struct DirCG {
+    const double *z, *p;
+    double beta;
+    __device__ __forceinline__ void get(int k, double (&o)[NN]) const {
+        double a[NN], b[NN];
+        ldc_cg<NN>(z, k, a);
+        ldc_cg<NN>(p, k, b);
 #pragma unroll
         for (int i = 0; i < NN; ++i) o[i] = fma(beta, b[i], a[i]);
     }
@@ -630,92 +653,181 @@ newton_setup_kernel(Geo G, const double *__restrict__ clo, int nc, double a_rad,
         sc->bnorm = sqrt(v[2]);
         sc->beta = 0.0;
         sc->iters = 0;
-        sc->body_runs = 0;
         sc->rtol = rtol;
         sc->max_iters = max_iters;
+        sc->bar_count = 0u;  // the persistent PCG kernel's barrier starts empty
         sc->done = sqrt(v[0]) <= rtol * sc->bnorm ? DONE_CONVERGED : DONE_NO;
     }
 }
 
-// PCG, first half of an iteration: p = z + beta p_old (stored for this cell,
-// formed on the fly for its neighbours), q = S p, alpha = rz / (p.q).
-template <int NN>
-__global__ void __launch_bounds__(BLOCK)
-pcg_matvec_kernel(Geo G, const double *__restrict__ aE, const double *__restrict__ iaF,
-                  const double *__restrict__ z, const double *__restrict__ p_old,
-                  double *__restrict__ p_new, double *__restrict__ q, double *part, Scalars *sc) {
-    if (sc->done) return;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    double v[1] = {0.0};
-    if (k < G.ncell) {
-        const Cell C = cell_of(G, k);
-        double aEv[NN], qv[NN], pv[NN];
-        ldc<NN>(aE, k, aEv);
-        schur_cell<NN>(G, C, Dir<NN>{z, p_old, sc->beta}, aEv, iaF, qv, pv);
-        stc<NN>(p_new, k, pv);
-        stc<NN>(q, k, qv);
-#pragma unroll
-        for (int n = 0; n < NN; ++n) v[0] += pv[n] * qv[n];
-    }
-    if (grid_sums<1>(v, part, &sc->count)) {
-        if (v[0] > 0.0 && isfinite(v[0]) && isfinite(sc->rz))
-            sc->alpha = sc->rz / v[0];
-        else
-            sc->done = DONE_BREAKDOWN;  // S not positive definite on p, or non-finite data
-    }
+// ---------------------------------------------------------------------------
+// The whole PCG solve in one cooperative launch (all blocks co-resident):
+// each iteration is the matrix-vector phase (p = z + beta p_old on the fly,
+// q = S p, p.q) and the update phase (x, r, z; r.r, r.z), each ending in a
+// grid barrier after which every block sums the blocks' partials in the same
+// fixed order, so all blocks take the same decisions.  Separate partial
+// buffers for the two phases and the alternating p buffers make one barrier
+// per phase enough.  The barrier's wait is bounded in time: a block that
+// gives up records DONE_TIMEOUT and leaves, and the others then give up at
+// their next barrier.
+struct GridBar {
+    unsigned int *count, *gen;
+    unsigned int nblocks;
+    long long limit_ns;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned int *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ long long lo_global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-// PCG, second half: x += alpha p, r -= alpha q, z = r / diag, the stopping
-// test ||r|| <= rtol ||b||, the cap, and beta = (r.z)_new / (r.z)_old.
-template <int NN>
-__global__ void __launch_bounds__(BLOCK)
-pcg_update_kernel(int ncell, const double *__restrict__ p, const double *__restrict__ q,
-                  const double *__restrict__ idiag, double *__restrict__ x, double *__restrict__ r,
-                  double *__restrict__ z, double *part, Scalars *sc) {
-    if (sc->done) return;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const double alpha = sc->alpha;
-    double v[2] = {0.0, 0.0};
-    if (k < ncell) {
-        double pv[NN], qv[NN], dv[NN], xv[NN], rv[NN], zv[NN];
-        ldc<NN>(p, k, pv);
-        ldc<NN>(q, k, qv);
-        ldc<NN>(idiag, k, dv);
-        ldc<NN>(x, k, xv);
-        ldc<NN>(r, k, rv);
-#pragma unroll
-        for (int n = 0; n < NN; ++n) {
-            xv[n] = fma(alpha, pv[n], xv[n]);
-            rv[n] = fma(-alpha, qv[n], rv[n]);
-            zv[n] = rv[n] * dv[n];
-            v[0] += rv[n] * rv[n];
-            v[1] += rv[n] * zv[n];
-        }
-        stc<NN>(x, k, xv);
-        stc<NN>(r, k, rv);
-        stc<NN>(z, k, zv);
-    }
-    if (grid_sums<2>(v, part, &sc->count)) {
-        sc->iters += 1;
-        sc->rr = v[0];
-        if (sqrt(v[0]) <= sc->rtol * sc->bnorm) {
-            sc->done = DONE_CONVERGED;
-        } else if (sc->iters >= sc->max_iters) {
-            sc->done = DONE_CAPPED;
+// false: the wait ran out of time (every thread of the block gets the same answer)
+__device__ bool grid_barrier(const GridBar &b) {
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        const unsigned g = ld_acquire_u32(b.gen);
+        __threadfence();
+        if (atomicAdd(b.count, 1u) == b.nblocks - 1) {
+            atomicExch(b.count, 0u);
+            __threadfence();
+            st_release_u32(b.gen, g + 1);
         } else {
-            sc->beta = v[1] / sc->rz;
-            sc->rz = v[1];
+            const long long t0 = lo_global_ns();
+            while (ld_acquire_u32(b.gen) == g) {
+                if (lo_global_ns() - t0 > b.limit_ns) {
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+// Block totals of K values into part[block]; after a barrier, grid_totals
+// sums the per-block partials in a fixed order (every thread gets them).
+template <int K>
+__device__ void block_partials(double (&v)[K], double *part) {
+    __shared__ double sh[BLOCK / 32][K];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0)
+        for (int k = 0; k < K; ++k) sh[wid][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < K; ++k) {
+            double t = 0.0;
+            for (int w = 0; w < BLOCK / 32; ++w) t += sh[w][k];
+            part[(size_t)blockIdx.x * K + k] = t;
         }
     }
 }
+template <int K>
+__device__ void grid_totals(double (&v)[K], const double *part) {
+    __shared__ double sh[BLOCK / 32][K];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double t = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += BLOCK) t += __ldcg(part + (size_t)b * K + k);
+        v[k] = warp_sum(t);
+    }
+    __syncthreads();
+    if (lane == 0)
+        for (int k = 0; k < K; ++k) sh[wid][k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double t = 0.0;
+        for (int w = 0; w < BLOCK / 32; ++w) t += sh[w][k];
+        v[k] = t;
+    }
+    __syncthreads();
+}
 
-// One thread: ends the device loop when PCG is done, and in any case once
-// the loop has run more trips than the iteration cap allows (two PCG
-// iterations per trip), so the loop ends whatever the reductions report.
-__global__ void pcg_check_kernel(Scalars *sc, cudaGraphConditionalHandle loop) {
-    const int runs = ++sc->body_runs;
-    if (sc->done != DONE_NO || 2 * (long long)runs >= (long long)sc->max_iters + 4)
-        cudaGraphSetConditional(loop, 0);
+template <int NN>
+__global__ void __launch_bounds__(BLOCK)
+pcg_persistent_kernel(Geo G, const double *__restrict__ aE, const double *__restrict__ iaF,
+                      const double *__restrict__ idiag, double *__restrict__ x,
+                      double *__restrict__ r, double *__restrict__ z, double *pb0, double *pb1,
+                      double *__restrict__ q, double *partA, double *partB, Scalars *sc,
+                      GridBar bar) {
+    if (sc->done != DONE_NO) return;  // the same for every block: read before any write
+    double rz = sc->rz, beta = 0.0;
+    const double stop = sc->rtol * sc->bnorm;
+    const int max_iters = sc->max_iters;
+    const int stride = gridDim.x * BLOCK;
+    int it = 0, done = DONE_NO;
+    double rr = 0.0;
+    for (;;) {
+        const double *po = (it & 1) ? pb1 : pb0;
+        double *pn = (it & 1) ? pb0 : pb1;
+        double v1[1] = {0.0};
+        for (int k = blockIdx.x * BLOCK + threadIdx.x; k < G.ncell; k += stride) {
+            const Cell C = cell_of(G, k);
+            double aEv[NN], qv[NN], pv[NN];
+            ldc<NN>(aE, k, aEv);
+            schur_cell<NN>(G, C, DirCG<NN>{z, po, beta}, aEv, iaF, qv, pv);
+            stc<NN>(pn, k, pv);
+            stc<NN>(q, k, qv);
+#pragma unroll
+            for (int n = 0; n < NN; ++n) v1[0] += pv[n] * qv[n];
+        }
+        block_partials<1>(v1, partA);
+        if (!grid_barrier(bar)) { done = DONE_TIMEOUT; break; }
+        grid_totals<1>(v1, partA);
+        if (!(v1[0] > 0.0) || !isfinite(v1[0]) || !isfinite(rz)) { done = DONE_BREAKDOWN; break; }
+        const double alpha = rz / v1[0];
+        double v2[2] = {0.0, 0.0};
+        for (int k = blockIdx.x * BLOCK + threadIdx.x; k < G.ncell; k += stride) {
+            double pv[NN], qv[NN], dv[NN], xv[NN], rv[NN], zv[NN];
+            ldc<NN>(pn, k, pv);
+            ldc<NN>(q, k, qv);
+            ldc<NN>(idiag, k, dv);
+            ldc<NN>(x, k, xv);
+            ldc<NN>(r, k, rv);
+#pragma unroll
+            for (int n = 0; n < NN; ++n) {
+                xv[n] = fma(alpha, pv[n], xv[n]);
+                rv[n] = fma(-alpha, qv[n], rv[n]);
+                zv[n] = rv[n] * dv[n];
+                v2[0] += rv[n] * rv[n];
+                v2[1] += rv[n] * zv[n];
+            }
+            stc<NN>(x, k, xv);
+            stc<NN>(r, k, rv);
+            stc<NN>(z, k, zv);
+        }
+        block_partials<2>(v2, partB);
+        if (!grid_barrier(bar)) { done = DONE_TIMEOUT; break; }
+        grid_totals<2>(v2, partB);
+        ++it;
+        rr = v2[0];
+        if (sqrt(v2[0]) <= stop) { done = DONE_CONVERGED; break; }
+        if (it >= max_iters) { done = DONE_CAPPED; break; }
+        beta = v2[1] / rz;
+        rz = v2[1];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->done = done;
+        sc->iters = it;
+        sc->rr = rr;
+        sc->rz = rz;
+        sc->beta = beta;
+    } else if (done == DONE_TIMEOUT && threadIdx.x == 0) {
+        sc->done = DONE_TIMEOUT;
+    }
 }
 
 // After the linear solve, one thread per cell: E = x, back-substitution
@@ -827,9 +939,7 @@ struct sm_lo_state {
     double *clo = nullptr;      // closures when the caller passes none
     smk::lo::Scalars *sc = nullptr;
     smk::lo::Scalars *h_sc = nullptr;  // pinned mirror
-    cudaStream_t cap = nullptr;        // private stream for graph capture
-    cudaGraph_t graph = nullptr;       // PCG: one WHILE node, two iterations per trip
-    cudaGraphExec_t exec = nullptr;
+    int coop_grid = 0;                 // blocks of the persistent PCG launch (0: not sized yet)
 };
 
 namespace {
@@ -884,40 +994,6 @@ Geo make_geo(const sm_problem *p) {
 }
 
 inline bool aligned16(const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
-
-// The PCG loop as a graph: a WHILE node whose body runs two iterations
-// (the search direction alternates between two buffers) and the check
-// kernel that clears the loop condition.
-template <int NN>
-sm_status build_graph(sm_problem *p, sm_lo_state &w) {
-    const Geo G = make_geo(p);
-    LO_CUDA(cudaStreamCreateWithFlags(&w.cap, cudaStreamNonBlocking));
-    LO_CUDA(cudaGraphCreate(&w.graph, 0));
-    cudaGraphConditionalHandle loop;
-    LO_CUDA(cudaGraphConditionalHandleCreate(&loop, w.graph, 1, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = loop;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    LO_CUDA(cudaGraphAddNode(&node, w.graph, nullptr, nullptr, 0, &cp));
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    LO_CUDA(cudaStreamBeginCaptureToGraph(w.cap, body, nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < 2; ++i) {
-        double *po = w.pb[i], *pn = w.pb[1 - i];
-        smk::lo::pcg_matvec_kernel<NN><<<w.nblk_cell, BLOCK, 0, w.cap>>>(G, w.aE, w.iaF, w.z, po,
-                                                                         pn, w.q, w.part, w.sc);
-        smk::lo::pcg_update_kernel<NN><<<w.nblk_cell, BLOCK, 0, w.cap>>>(
-            G.ncell, pn, w.q, w.idiag, w.x, w.r, w.z, w.part, w.sc);
-    }
-    smk::lo::pcg_check_kernel<<<1, 1, 0, w.cap>>>(w.sc, loop);
-    cudaGraph_t captured = nullptr;
-    LO_CUDA(cudaStreamEndCapture(w.cap, &captured));
-    LO_CUDA(cudaGraphInstantiate(&w.exec, w.graph, 0));
-    return SM_OK;
-}
 
 sm_status lo_ensure(sm_problem *p) {
     if (p->lo) return SM_OK;
@@ -1010,7 +1086,7 @@ sm_status lo_ensure(sm_problem *p) {
         }
         LO_CUDA(cudaMemcpy(w.jinc, jp, sizeof(jp), cudaMemcpyHostToDevice));
     }
-    return p->dim == 2 ? build_graph<4>(p, w) : build_graph<2>(p, w);
+    return SM_OK;
 }
 
 sm_status read_scalars(sm_problem *p) {
@@ -1030,6 +1106,35 @@ sm_status check_params(const sm_step_params &prm) {
         !(prm.elim_rtol > 0) || !(prm.T_floor > 0))
         return lo_fail(SM_ERR_INVALID_ARG,
                        "tolerances must be >= 0 (eps) or > 0 (pcg_rtol, elim_rtol, T_floor)");
+    return SM_OK;
+}
+
+// One cooperative launch runs the whole PCG solve (all blocks co-resident;
+// the grid is at most the blocks that fit on the GPU at once).
+template <int NN>
+sm_status launch_pcg(sm_problem *p, sm_lo_state &w, const Geo &G, cudaStream_t s) {
+    const void *k = (const void *)smk::lo::pcg_persistent_kernel<NN>;
+    if (w.coop_grid == 0) {
+        int dev = 0, nsm = 0, per_sm = 0;
+        LO_CUDA(cudaGetDevice(&dev));
+        LO_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        LO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BLOCK, 0));
+        if (per_sm < 1) return lo_fail(SM_ERR_CUDA, "the PCG kernel does not fit on an SM");
+        w.coop_grid = std::min(w.nblk_cell, per_sm * nsm);
+    }
+    smk::lo::GridBar bar;
+    bar.count = &w.sc->bar_count;
+    bar.gen = &w.sc->bar_gen;
+    bar.nblocks = (unsigned)w.coop_grid;
+    bar.limit_ns = p->timeout_ns;
+    Geo g = G;
+    const double *aE = w.aE, *iaF = w.iaF, *idiag = w.idiag;
+    double *x = w.x, *r = w.r, *z = w.z, *p0 = w.pb[0], *p1 = w.pb[1], *q = w.q;
+    const size_t nblk = (size_t)std::max(w.nblk_cell, w.nblk_node);
+    double *partA = w.part, *partB = w.part + nblk;
+    smk::lo::Scalars *sc = w.sc;
+    void *args[] = {&g, &aE, &iaF, &idiag, &x, &r, &z, &p0, &p1, &q, &partA, &partB, &sc, &bar};
+    LO_CUDA(cudaLaunchCooperativeKernel(k, dim3(w.coop_grid), dim3(BLOCK), args, 0, s));
     return SM_OK;
 }
 
@@ -1068,16 +1173,16 @@ sm_status lo_solve(sm_problem *p, const double *clo, const double *Tstar, const 
             G, clo, p->nc, a, dt, T, Tstar, cv, w.Estar, w.jin2, R0, w.iaF, w.ub, E, w.aE, w.idiag,
             w.x, w.r, w.z, w.pb[0], prm.pcg_rtol, prm.max_pcg, w.part, w.sc);
         LO_CUDA(cudaGetLastError());
-        LO_CUDA(cudaGraphLaunch(w.exec, s));
+        LO_TRY(launch_pcg<NN>(p, w, G, s));
         smk::lo::newton_finish_kernel<NN><<<w.nblk_cell, BLOCK, 0, s>>>(
             G, clo, p->nc, a, dt, w.x, w.iaF, w.bF, Tstar, cv, T, E, F, prm.elim_rtol,
             prm.max_elim, prm.T_floor, w.part, w.sc);
         LO_CUDA(cudaGetLastError());
         LO_TRY(read_scalars(p));
         const smk::lo::Scalars &h = *w.h_sc;
-        // kernels that ran: setup, finish, and per loop trip 4 PCG kernels
-        // (they return at once after convergence) plus the check kernel
-        p->launches += 2 + 5LL * h.body_runs;
+        p->launches += 3;  // setup, the PCG solve, finish
+        if (h.done == smk::lo::DONE_TIMEOUT)
+            return lo_fail(SM_ERR_TIMEOUT, "a grid barrier of the conjugate-gradient kernel ran out of time");
         if (h.done == smk::lo::DONE_BREAKDOWN)
             return lo_fail(SM_ERR_NO_CONVERGENCE,
                            "conjugate gradients broke down: the Schur complement is not positive "
@@ -1118,9 +1223,6 @@ namespace smk {
 void lo_free(sm_problem *p) {
     if (!p->lo) return;
     sm_lo_state &w = *p->lo;
-    if (w.exec) cudaGraphExecDestroy(w.exec);
-    if (w.graph) cudaGraphDestroy(w.graph);
-    if (w.cap) cudaStreamDestroy(w.cap);
     void *bufs[] = {w.buf, w.part, w.jin2, w.sigma, w.clo, w.sc, w.R0, w.qmom_int, w.jinc};
     for (void *b : bufs)
         if (b) cudaFree(b);
