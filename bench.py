@@ -65,6 +65,23 @@ def workload(args):
     return cfg
 
 
+def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
+    """The largest x over the ranks (x itself without a process group): the
+    timed region of a replicated run ends when its slowest rank does."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas that each process
+    units_per_rank units in `seconds` (the max over ranks): weak scaling."""
+    return world * units_per_rank / seconds
+
+
 def algorithmic_bytes(cfg, prec: int) -> dict:
     """Minimal HBM traffic of one sweep-kernel launch: read I^k and write I
     (4 nodes each per update), read the emission (4 nodes) and sigma~, sigma
@@ -535,11 +552,7 @@ def main():
         launches = prob.launch_count() - n0
         ktimes = prob.kernel_times()
         prob.set_profiling(False)
-        ms = ev0.elapsed_time(ev1) / args.steps
-        t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        ms = float(t_max.item())
+        ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist)
 
         # end to end through the host-buffer entry point
         T_h = torch.from_numpy(W.temperature_wave(cfg)).pin_memory().numpy()
@@ -552,11 +565,7 @@ def main():
         t0 = time.perf_counter()
         for i in range(e2e_steps):
             prob.sweep_host(T_h, S_h, I[i % 2], I[(i + 1) % 2], M_h, C_h)
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
-        t_e = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
-        e2e_s = float(t_e.item())
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist)
 
     if rank != 0:
         if dist is not None:
@@ -564,7 +573,7 @@ def main():
         return 0
 
     upd = cfg.updates
-    value = world * upd / (ms * 1e-3)
+    value = replica_rate(world, upd, ms * 1e-3)
     alg = algorithmic_bytes(cfg, prec)
     sweep_ms = ktimes["sweep_ms"] / max(ktimes["count"], 1)
     peak, peak_kind = measured_peaks()
@@ -603,7 +612,7 @@ def main():
                      "kernel": "sweep2d_kernel"},
         "clocks": clocks,
         "gpu_launches": launches,
-        "e2e": {"value": world * upd / e2e_s, "unit": "cell-dir-group updates/s",
+        "e2e": {"value": replica_rate(world, upd, e2e_s), "unit": "cell-dir-group updates/s",
                 "h2d_bytes_per_step": int(T_h.nbytes + S_h.nbytes),
                 "d2h_bytes_per_step": int(M_h.nbytes + C_h.nbytes),
                 "api": "sm_sweep_host (host T, sigma in; moments, closures out)"},
