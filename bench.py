@@ -316,6 +316,51 @@ def config_sweeps(sm, W, stream, reps: int = 20):
     return out
 
 
+def marshak_paper_metric(sm, W, stream):
+    """The Marshak wave in the paper's units (64 cells, S6, 312 steps of
+    8e-12 s to 2.5 ns) through sm_step with the paper's iteration controls:
+    wall time of the whole run per closure method and sweep precision, the
+    outer iterations, and the wave-front position (first cell-mean T below
+    500 eV)."""
+    import numpy as np
+    import torch
+    cfg = W.marshak_paper()
+    n = cfg.n_cells
+    out = {"workload": f"{cfg.name}, {cfg.steps} steps of {cfg.dt:.0e} s"}
+    for method, code in (("independent", sm.METHOD_INDEPENDENT),
+                         ("consistent", sm.METHOD_CONSISTENT)):
+        for prec in (32, 64):
+            with torch.cuda.stream(stream):
+                prob = sm.Problem.from_config(cfg, prec, stream=stream)
+                T = torch.full((n, 2), cfg.T0, dtype=torch.float64, device="cuda")
+                scale = torch.from_numpy(W.scale_field(cfg)).cuda()
+                cv = torch.full((n, 2), cfg.cv, dtype=torch.float64, device="cuda")
+                ones = torch.ones((cfg.n_groups, n), dtype=torch.float64, device="cuda")
+                b = prob.emission(T, ones)  # B(T0)/4pi per node: the equilibrium start
+                Ip = prob.pack(b.unsqueeze(0).expand(cfg.n_dir, -1, -1, -1).contiguous())
+                mom = prob.new_moments()
+                mom.zero_()
+                mom[..., 0] = cfg.a * cfg.c * cfg.T0 ** 4
+                E, F = prob.new_nodal(), prob.new_flux()
+                prm = sm.step_params(method=code)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                outer = 0
+                for _ in range(cfg.steps):
+                    In = prob.empty_intensity()
+                    outer += prob.step(scale, cv, T, E, F, mom, Ip, In, params=prm)["outer_iters"]
+                    Ip = In
+                torch.cuda.synchronize()
+                secs = time.perf_counter() - t0
+                Tm = T.cpu().numpy().mean(axis=1)
+                hot = Tm > 500.0
+                k = int(np.argmin(hot)) if not hot.all() else n
+                out[f"{method}_fp{prec}"] = {"s": secs, "outer_iters": outer,
+                                             "front_cm": k * 0.05 / n}
+                prob.close()
+    return out
+
+
 def step_metric(sm, W, cfgs, n_steps: int, stream):
     """Metric 2: FP32 vs FP64 sweep path, seconds per converged step, with
     the FP32 path's temperature error against the FP64 path after the same
@@ -624,6 +669,8 @@ def main():
                                           args.step_steps, stream)
     if not args.no_config_sweeps and not (args.nx or args.groups):
         line["config_sweeps"] = config_sweeps(sm, W, stream)
+    if not args.no_step_metric and not (args.nx or args.groups):
+        line["marshak_paper"] = marshak_paper_metric(sm, W, stream)
     if not args.no_batched and not (args.nx or args.groups):
         line["batched"] = batched_metric(sm, W, stream, max(3, args.steps // 2), 3)
     if args.adjoint_fd_cells > 0 and not (args.nx or args.groups):

@@ -46,6 +46,7 @@ class Config:
     T0: float = 0.01
     steps: int = 10
     seed: int = 0
+    scale_1d: float = 100.0      # 1D: per-cell opacity scale s_K (all cells)
 
     @property
     def n_groups(self) -> int:
@@ -129,6 +130,25 @@ def adjoint_2d_warm() -> Config:
     return dataclasses.replace(c, name="adjoint2d_warm_128x128x64x16", T0=0.3)
 
 
+# CGS units with temperatures in eV: the radiation constant a = 4 sigma_SB / c
+# in erg cm^-3 eV^-4 (7.5657e-15 erg cm^-3 K^-4 at 11604.518 K per eV) and c in
+# cm/s
+A_RAD_EV = 7.5657e-15 * 11604.518 ** 4
+C_CM_S = 2.99792458e10
+
+
+def marshak_paper(nx: int = 64, dt: float = 8e-12) -> Config:
+    """The Marshak wave in the paper's units (Sec. 6, Marshak wave definition):
+    [0, 0.05 cm], 2.5 ns, sigma = 1e12 T^-3 cm^-1 (T in eV), c_v = 3e12
+    erg cm^-3 eV^-1, equilibrium at 1 eV, a 1 keV Planck source at x = 0
+    (vacuum at the right end), Gauss-Legendre S6; dt in seconds (8e-12 s is
+    the coarsest step of the paper's time refinement)."""
+    steps = int(round(2.5e-9 / dt))
+    return Config(f"marshakpaper1d_{nx}x6x1", 1, nx, 1, (0.0, 0.05, 0.0, 1.0), GRAY_EDGES.copy(),
+                  6, 0, OPACITY_POWER, 0.0, (1000.0, 0.0, 0.0, 0.0), a=A_RAD_EV, c=C_CM_S, dt=dt,
+                  cv=3e12, T0=1.0, steps=steps, scale_1d=1e12)
+
+
 CONFIGS = {
     "c1": marshak_1d,
     "c2": gray_channel_2d,
@@ -178,7 +198,7 @@ def scale_field(cfg: Config, seed: Optional[int] = None) -> np.ndarray:
     """Per-cell opacity scale s_K for the problem's material layout."""
     seed = cfg.seed if seed is None else seed
     if cfg.dim == 1:
-        return np.full(cfg.n_cells, 100.0)
+        return np.full(cfg.n_cells, cfg.scale_1d)
     if cfg.opacity_kind == OPACITY_POWER:
         return np.where(channel_mask(cfg), 0.2, 2000.0)
     rng = np.random.default_rng(seed)
