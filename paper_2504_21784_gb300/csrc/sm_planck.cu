@@ -11,8 +11,8 @@
 // factor x/(e^x-1) is the Bernoulli generating series itself.  The GPU takes
 // the first series for x < 1, the first term of the second for x >= 37 (the
 // next is below double rounding), and in between, where both series need the
-// most terms, degree-7 Taylor expansions about the nearest of the centres 1,
-// 1 + 1/16, ..., 37 (|x - c| <= 1/32), whose coefficients the host derives
+// most terms, degree-6 Taylor expansions about the nearest of the centres 1,
+// 1 + 1/32, ..., 37 (|x - c| <= 1/64), whose coefficients the host derives
 // once from P'(x) = (15/pi^4) x^3/(e^x - 1) in extended precision.  A group
 // whose lower reduced edge is at or above the switch near x = 2 is differenced
 // in tails (1 - P) to keep relative accuracy; the lowest edge is 0 and the
@@ -43,10 +43,10 @@ __device__ double g_exp2_tab[64];
 // NTAY coefficients in h = x - c_j, (P, R) for c_j < 2 and (1 - P, 1 - R) for
 // c_j >= 2 (so that the tails keep their relative accuracy).
 constexpr double XT0 = 1.0, XT1 = 37.0;
-constexpr int TSTEP = 16;  // centres per unit of x
-constexpr int NCEN = 577;  // (XT1 - XT0) * TSTEP + 1
-constexpr int NTAY = 8;    // remainder (1/32 / 2pi)^8 < 1e-18 of the leading term
-constexpr int JSW = 16;    // centres j < JSW lie below x = 2: P, R; from there on 1 - P, 1 - R
+constexpr int TSTEP = 32;  // centres per unit of x
+constexpr int NCEN = 1153;  // (XT1 - XT0) * TSTEP + 1
+constexpr int NTAY = 7;    // remainder (1/64 / 2pi)^7 < 1e-18 of the leading term
+constexpr int JSW = 32;    // centres j < JSW lie below x = 2: P, R; from there on 1 - P, 1 - R
 static_assert(XT1 == XCLOSED, "the Taylor tables end where the one-term tail takes over");
 __device__ double g_ptab[NCEN][2][NTAY];
 __device__ double g_pcen[NCEN];
