@@ -26,10 +26,10 @@
 // and the pointwise temperature Newton step taken with an FP32 reciprocal of
 // its derivative (a quasi-Newton step: the root is unchanged).  PCG scalars
 // never leave the device: grid-wide sums are deterministic fixed-order sums
-// (no floating-point atomics), and the whole conjugate-gradient solve of a
-// Newton iteration is one cooperative launch whose blocks meet at grid
-// barriers with bounded waits, so the host synchronises once per Newton
-// iteration (its stopping test) whatever the number of PCG iterations.
+// (no floating-point atomics), and the whole Newton iteration of a low-order
+// solve -- set-up, conjugate gradients and finish of every Newton step, and
+// the stopping tests -- is one cooperative launch whose blocks meet at grid
+// barriers with bounded waits, so the host synchronises once per solve.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -47,8 +47,11 @@ struct Scalars {
     double alpha, beta, rz, bnorm, rr, d2, n2, rtol;
     int done, iters, max_iters, elim_max;
     unsigned int count;  // arrivals of the running kernel's blocks
-    unsigned int bar_count, bar_gen;  // grid barrier of the persistent PCG kernel
+    unsigned int bar_count, bar_gen;  // grid barrier of the cooperative kernels
+    // statistics of the last low-order solve (cooperative Newton kernel)
+    int newton_iters, pcg_total, pcg_max, pcg_capped, status;
 };
+enum { LO_OK = 0, LO_BREAKDOWN = 1, LO_TIMEOUT = 2, LO_NONFINITE = 3 };
 
 struct Geo {
     int dim, nx, ny, ncell, N;
@@ -127,6 +130,11 @@ __device__ __forceinline__ void ldc_cg(const double *a, int k, double (&v)[NN]) 
         v[2 * i + 1] = t.y;
     }
 }
+template <int NN>
+struct VecCG {
+    const double *v;
+    __device__ __forceinline__ void get(int k, double (&o)[NN]) const { ldc_cg<NN>(v, k, o); }
+};
 template <int NN>
 struct DirCG {
     const double *z, *p;
@@ -524,7 +532,11 @@ prepare_kernel(Geo G, const double *__restrict__ clo, int nc, double inv_cdt,
                double *__restrict__ iaF, double *__restrict__ bF, double *__restrict__ ub,
                Scalars *sc) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t == 0) sc->elim_max = 0;
+    if (t == 0) {
+        sc->elim_max = 0;
+        sc->bar_count = 0u;  // the cooperative kernel's barrier starts empty
+        sc->status = LO_OK;
+    }
     if (t >= G.N) return;
     const int D = G.dim, NN = D == 2 ? 4 : 2;
     const int k = t / NN, n = t - k * NN;
@@ -565,111 +577,13 @@ prepare_kernel(Geo G, const double *__restrict__ clo, int nc, double inv_cdt,
     }
 }
 
-// Per Newton iteration, one thread per cell: linearise the emission about
-// the current T (Sec. 5), form aE = m c (sigma~_E - nu sigma_E), the Schur
-// right-hand side b_E - A_EF u_b with b_E = m (sigma_P B(T0) + nu q_T0 +
-// E*/dt) + the Marshak inflow, 1/diag(S), and start PCG from x = E:
-// r = rhs - S x, z = r / diag, p = z.
-template <int NN>
-__global__ void __launch_bounds__(BLOCK)
-newton_setup_kernel(Geo G, const double *__restrict__ clo, int nc, double a_rad, double dt,
-                    const double *__restrict__ T, const double *__restrict__ Tstar,
-                    const double *__restrict__ cv, const double *__restrict__ Estar,
-                    const double *__restrict__ jin2, const double *__restrict__ R0,
-                    const double *__restrict__ iaF,
-                    const double *__restrict__ ub, const double *__restrict__ E,
-                    double *__restrict__ aE_out, double *__restrict__ idiag, double *__restrict__ x,
-                    double *__restrict__ r, double *__restrict__ z, double *__restrict__ p0,
-                    double rtol, int max_iters, double *part, Scalars *sc) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    double v[3] = {0.0, 0.0, 0.0};
-    if (k < G.ncell) {
-        const Cell C = cell_of(G, k);
-        double T0[NN], Ts[NN], cvv[NN], Es[NN], aE[NN], bE[NN];
-        ldc<NN>(T, k, T0);
-        ldc<NN>(Tstar, k, Ts);
-        ldc<NN>(cv, k, cvv);
-        ldc<NN>(Estar, k, Es);
-        const double inv_cdt = 1.0 / (G.c * dt);
-#pragma unroll
-        for (int n = 0; n < NN; ++n) {
-            const double *cl = clo + ((size_t)k * NN + n) * nc;
-            const double sE = cl[NN == 4 ? 6 : 3], sP = cl[NN == 4 ? 8 : 5];
-            const double Tn = T0[n];
-            const double B0 = a_rad * G.c * (Tn * Tn * Tn * Tn);
-            const double dB = 4.0 * a_rad * G.c * (Tn * Tn * Tn);
-            const double cv_dt = cvv[n] / dt;
-            const double den = cv_dt + sP * dB;
-            const double nu = den > 0.0 ? sP * dB / den : 0.0;  // pseudo-fission coefficient
-            const double qT0 = cv_dt * (Ts[n] - Tn) - sP * B0;
-            aE[n] = G.m * G.c * (sE + inv_cdt - nu * sE);
-            bE[n] = G.m * (sP * B0 + nu * qT0 + Es[n] / dt);
-        }
-        if (R0) {
-            // consistent method: face and boundary corrections (the inflow included)
-            double r0[NN];
-            ldc<NN>(R0, k, r0);
-#pragma unroll
-            for (int n = 0; n < NN; ++n) bE[n] += r0[n];
-        } else {
-            // Marshak boundary: -2 int_Gamma_b u F_in, F_in the incoming partial current
-#pragma unroll
-            for (int b = 0; b < NN / 2; ++b) {
-                if (!C.L) bE[2 * b] += G.wfx * jin2[0];
-                if (!C.R) bE[2 * b + 1] += G.wfx * jin2[1];
-            }
-            if constexpr (NN == 4) {
-#pragma unroll
-                for (int a = 0; a < 2; ++a) {
-                    if (!C.B) bE[a] += G.wfy * jin2[2];
-                    if (!C.T) bE[a + 2] += G.wfy * jin2[3];
-                }
-            }
-        }
-        double efu[NN], dg[NN], q[NN], e[NN], rv[NN], zv[NN], idg[NN];
-        ef_cell<NN>(G, C, ub, efu);
-        diag_cell<NN>(G, C, aE, iaF, dg);
-        schur_cell<NN>(G, C, Vec<NN>{E}, aE, iaF, q, e);
-#pragma unroll
-        for (int n = 0; n < NN; ++n) {
-            const double rhs = bE[n] - efu[n];
-            rv[n] = rhs - q[n];
-            idg[n] = 1.0 / dg[n];
-            zv[n] = rv[n] * idg[n];
-            v[0] += rv[n] * rv[n];
-            v[1] += rv[n] * zv[n];
-            v[2] += rhs * rhs;
-        }
-        stc<NN>(aE_out, k, aE);
-        stc<NN>(idiag, k, idg);
-        stc<NN>(x, k, e);
-        stc<NN>(r, k, rv);
-        stc<NN>(z, k, zv);
-        stc<NN>(p0, k, zv);
-    }
-    if (grid_sums<3>(v, part, &sc->count)) {
-        sc->rr = v[0];
-        sc->rz = v[1];
-        sc->bnorm = sqrt(v[2]);
-        sc->beta = 0.0;
-        sc->iters = 0;
-        sc->rtol = rtol;
-        sc->max_iters = max_iters;
-        sc->bar_count = 0u;  // the persistent PCG kernel's barrier starts empty
-        sc->done = sqrt(v[0]) <= rtol * sc->bnorm ? DONE_CONVERGED : DONE_NO;
-    }
-}
-
 // ---------------------------------------------------------------------------
-// The whole PCG solve in one cooperative launch (all blocks co-resident):
-// each iteration is the matrix-vector phase (p = z + beta p_old on the fly,
-// q = S p, p.q) and the update phase (x, r, z; r.r, r.z), each ending in a
-// grid barrier after which every block sums the blocks' partials in the same
-// fixed order, so all blocks take the same decisions.  Separate partial
-// buffers for the two phases and the alternating p buffers make one barrier
-// per phase enough.  The barrier's wait is bounded in time: a block that
-// gives up records DONE_TIMEOUT and leaves, and the others then give up at
-// their next barrier.
+// Grid-wide synchronisation for the cooperative low-order kernel (all blocks
+// co-resident): a barrier of our own whose wait is bounded in time (a block
+// that gives up records a timeout and leaves, and the others then give up at
+// their next barrier), and reductions whose per-block partials every block
+// sums in the same fixed order after the barrier, so that all blocks take the
+// same decisions.
 struct GridBar {
     unsigned int *count, *gen;
     unsigned int nblocks;
@@ -756,81 +670,107 @@ __device__ void grid_totals(double (&v)[K], const double *part) {
     __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// The whole Newton iteration of a low-order solve in one cooperative launch:
+// per Newton iteration the set-up phase (linearisation, Schur right-hand
+// side, residual and preconditioned residual of the start x = E), the PCG
+// phases and the finish phase (back-substitution and pointwise temperature
+// elimination), each reduction
+// closed by a grid barrier, and the stopping test of Eq. relative_tol taken
+// by every block on the same grid totals.  The conjugate-gradient iteration
+// alternates a matrix-vector phase (p = z + beta p_old formed on the fly for
+// the neighbours, q = S p, p.q) and an update phase (x, r, z; r.r, r.z).
+// Partial sums of consecutive reductions go to different buffers (A: set-up, B / C: the two PCG phases,
+// D: finish), so one barrier per reduction suffices.  Values other blocks
+// wrote in the same launch (E, x, z, p of neighbour cells) are read past L1.
+struct NewtonArgs {
+    Geo G;
+    const double *clo;
+    int nc;
+    double a_rad, dt;
+    double *T, *E, *F;
+    const double *Tstar, *cv, *Estar, *jin2, *R0, *iaF, *ub, *bF;
+    double *aE, *idiag, *x, *r, *z, *pb0, *pb1, *q;
+    double *partA, *partB, *partC, *partD;
+    double pcg_rtol, eps_inner, elim_rtol, T_floor;
+    int max_pcg, max_inner, max_elim;
+    Scalars *sc;
+    GridBar bar;
+};
+
+// Per Newton iteration, for cell k: linearise the emission about
+// the current T (Sec. 5), form aE = m c (sigma~_E - nu sigma_E), the Schur
+// right-hand side b_E - A_EF u_b with b_E = m (sigma_P B(T0) + nu q_T0 +
+// E*/dt) + the Marshak inflow, 1/diag(S), and start PCG from x = E:
+// r = rhs - S x, z = r / diag, p = z.
 template <int NN>
-__global__ void __launch_bounds__(BLOCK)
-pcg_persistent_kernel(Geo G, const double *__restrict__ aE, const double *__restrict__ iaF,
-                      const double *__restrict__ idiag, double *__restrict__ x,
-                      double *__restrict__ r, double *__restrict__ z, double *pb0, double *pb1,
-                      double *__restrict__ q, double *partA, double *partB, Scalars *sc,
-                      GridBar bar) {
-    if (sc->done != DONE_NO) return;  // the same for every block: read before any write
-    double rz = sc->rz, beta = 0.0;
-    const double stop = sc->rtol * sc->bnorm;
-    const int max_iters = sc->max_iters;
-    const int stride = gridDim.x * BLOCK;
-    int it = 0, done = DONE_NO;
-    double rr = 0.0;
-    for (;;) {
-        const double *po = (it & 1) ? pb1 : pb0;
-        double *pn = (it & 1) ? pb0 : pb1;
-        double v1[1] = {0.0};
-        for (int k = blockIdx.x * BLOCK + threadIdx.x; k < G.ncell; k += stride) {
-            const Cell C = cell_of(G, k);
-            double aEv[NN], qv[NN], pv[NN];
-            ldc<NN>(aE, k, aEv);
-            schur_cell<NN>(G, C, DirCG<NN>{z, po, beta}, aEv, iaF, qv, pv);
-            stc<NN>(pn, k, pv);
-            stc<NN>(q, k, qv);
+__device__ __forceinline__ void newton_setup_cell(const NewtonArgs &A, int k, double (&v)[3]) {
+    const Geo &G = A.G;
+    const Cell C = cell_of(G, k);
+    double T0[NN], Ts[NN], cvv[NN], Es[NN], aE[NN], bE[NN];
+    ldc<NN>(A.T, k, T0);
+    ldc<NN>(A.Tstar, k, Ts);
+    ldc<NN>(A.cv, k, cvv);
+    ldc<NN>(A.Estar, k, Es);
+    const double inv_cdt = 1.0 / (G.c * A.dt);
 #pragma unroll
-            for (int n = 0; n < NN; ++n) v1[0] += pv[n] * qv[n];
+    for (int n = 0; n < NN; ++n) {
+        const double *cl = A.clo + ((size_t)k * NN + n) * A.nc;
+        const double sE = cl[NN == 4 ? 6 : 3], sP = cl[NN == 4 ? 8 : 5];
+        const double Tn = T0[n];
+        const double B0 = A.a_rad * G.c * (Tn * Tn * Tn * Tn);
+        const double dB = 4.0 * A.a_rad * G.c * (Tn * Tn * Tn);
+        const double cv_dt = cvv[n] / A.dt;
+        const double den = cv_dt + sP * dB;
+        const double nu = den > 0.0 ? sP * dB / den : 0.0;  // pseudo-fission coefficient
+        const double qT0 = cv_dt * (Ts[n] - Tn) - sP * B0;
+        aE[n] = G.m * G.c * (sE + inv_cdt - nu * sE);
+        bE[n] = G.m * (sP * B0 + nu * qT0 + Es[n] / A.dt);
+    }
+    if (A.R0) {
+        // consistent method: face and boundary corrections (the inflow included)
+        double r0[NN];
+        ldc<NN>(A.R0, k, r0);
+#pragma unroll
+        for (int n = 0; n < NN; ++n) bE[n] += r0[n];
+    } else {
+        // Marshak boundary: -2 int_Gamma_b u F_in, F_in the incoming partial current
+#pragma unroll
+        for (int b = 0; b < NN / 2; ++b) {
+            if (!C.L) bE[2 * b] += G.wfx * A.jin2[0];
+            if (!C.R) bE[2 * b + 1] += G.wfx * A.jin2[1];
         }
-        block_partials<1>(v1, partA);
-        if (!grid_barrier(bar)) { done = DONE_TIMEOUT; break; }
-        grid_totals<1>(v1, partA);
-        if (!(v1[0] > 0.0) || !isfinite(v1[0]) || !isfinite(rz)) { done = DONE_BREAKDOWN; break; }
-        const double alpha = rz / v1[0];
-        double v2[2] = {0.0, 0.0};
-        for (int k = blockIdx.x * BLOCK + threadIdx.x; k < G.ncell; k += stride) {
-            double pv[NN], qv[NN], dv[NN], xv[NN], rv[NN], zv[NN];
-            ldc<NN>(pn, k, pv);
-            ldc<NN>(q, k, qv);
-            ldc<NN>(idiag, k, dv);
-            ldc<NN>(x, k, xv);
-            ldc<NN>(r, k, rv);
+        if constexpr (NN == 4) {
 #pragma unroll
-            for (int n = 0; n < NN; ++n) {
-                xv[n] = fma(alpha, pv[n], xv[n]);
-                rv[n] = fma(-alpha, qv[n], rv[n]);
-                zv[n] = rv[n] * dv[n];
-                v2[0] += rv[n] * rv[n];
-                v2[1] += rv[n] * zv[n];
+            for (int a = 0; a < 2; ++a) {
+                if (!C.B) bE[a] += G.wfy * A.jin2[2];
+                if (!C.T) bE[a + 2] += G.wfy * A.jin2[3];
             }
-            stc<NN>(x, k, xv);
-            stc<NN>(r, k, rv);
-            stc<NN>(z, k, zv);
         }
-        block_partials<2>(v2, partB);
-        if (!grid_barrier(bar)) { done = DONE_TIMEOUT; break; }
-        grid_totals<2>(v2, partB);
-        ++it;
-        rr = v2[0];
-        if (sqrt(v2[0]) <= stop) { done = DONE_CONVERGED; break; }
-        if (it >= max_iters) { done = DONE_CAPPED; break; }
-        beta = v2[1] / rz;
-        rz = v2[1];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        sc->done = done;
-        sc->iters = it;
-        sc->rr = rr;
-        sc->rz = rz;
-        sc->beta = beta;
-    } else if (done == DONE_TIMEOUT && threadIdx.x == 0) {
-        sc->done = DONE_TIMEOUT;
+    double efu[NN], dg[NN], q[NN], e[NN], rv[NN], zv[NN], idg[NN];
+    ef_cell<NN>(G, C, A.ub, efu);
+    diag_cell<NN>(G, C, aE, A.iaF, dg);
+    schur_cell<NN>(G, C, VecCG<NN>{A.E}, aE, A.iaF, q, e);
+#pragma unroll
+    for (int n = 0; n < NN; ++n) {
+        const double rhs = bE[n] - efu[n];
+        rv[n] = rhs - q[n];
+        idg[n] = 1.0 / dg[n];
+        zv[n] = rv[n] * idg[n];
+        v[0] += rv[n] * rv[n];
+        v[1] += rv[n] * zv[n];
+        v[2] += rhs * rhs;
     }
+    stc<NN>(A.aE, k, aE);
+    stc<NN>(A.idiag, k, idg);
+    stc<NN>(A.x, k, e);
+    stc<NN>(A.r, k, rv);
+    stc<NN>(A.z, k, zv);
+    stc<NN>(A.pb0, k, zv);
 }
 
-// After the linear solve, one thread per cell: E = x, back-substitution
+// After the linear solve, for cell k: E = x, back-substitution
 // F = A_FF^-1 (b_F - A_FE E), then the pointwise nonlinear elimination of T
 // (Eq. nonlinear_T_update, lumped): (C_v/dt) T + sigma_P a c T^4 =
 // c sigma_E E + (C_v/dt) T*, iterated from the current T and floored at
@@ -840,64 +780,151 @@ pcg_persistent_kernel(Geo G, const double *__restrict__ aE, const double *__rest
 // Sums ||u_new - u_old||^2 and ||u_new||^2 over u = (T, E) for
 // Eq. relative_tol.
 template <int NN>
-__global__ void __launch_bounds__(BLOCK)
-newton_finish_kernel(Geo G, const double *__restrict__ clo, int nc, double a_rad, double dt,
-                     const double *__restrict__ x, const double *__restrict__ iaF,
-                     const double *__restrict__ bF, const double *__restrict__ Tstar,
-                     const double *__restrict__ cv, double *__restrict__ T, double *__restrict__ E,
-                     double *__restrict__ F, double rtol, int maxit, double T_floor, double *part,
-                     Scalars *sc) {
+__device__ __forceinline__ void newton_finish_cell(const NewtonArgs &A, int k, double (&v)[2],
+                                                   int &its_max) {
     constexpr int D = NN == 4 ? 2 : 1;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    double v[2] = {0.0, 0.0};
-    int its_max = 0;
-    if (k < G.ncell) {
-        const Cell C = cell_of(G, k);
-        double e[NN], ax[NN], ay[NN], ia[NN], Told[NN], Ts[NN], cvv[NN], Eold[NN], Tn[NN];
-        fe_cell<NN>(G, C, Vec<NN>{x}, e, ax, ay);
-        ldc<NN>(iaF, k, ia);
-        ldc<NN>(T, k, Told);
-        ldc<NN>(Tstar, k, Ts);
-        ldc<NN>(cv, k, cvv);
-        ldc<NN>(E, k, Eold);
+    const Geo &G = A.G;
+    const Cell C = cell_of(G, k);
+    double e[NN], ax[NN], ay[NN], ia[NN], Told[NN], Ts[NN], cvv[NN], Eold[NN], Tn[NN];
+    fe_cell<NN>(G, C, VecCG<NN>{A.x}, e, ax, ay);
+    ldc<NN>(A.iaF, k, ia);
+    ldc<NN>(A.T, k, Told);
+    ldc<NN>(A.Tstar, k, Ts);
+    ldc<NN>(A.cv, k, cvv);
+    ldc<NN>(A.E, k, Eold);
 #pragma unroll
-        for (int n = 0; n < NN; ++n) {
-            const size_t nd = (size_t)k * NN + n;
-            F[nd * D] = (bF[nd * D] - ax[n]) * ia[n];
-            if constexpr (D == 2) F[nd * D + 1] = (bF[nd * D + 1] - ay[n]) * ia[n];
-            const double *cl = clo + nd * nc;
-            const double sE = cl[NN == 4 ? 6 : 3], sP = cl[NN == 4 ? 8 : 5];
-            const double cv_dt = cvv[n] / dt;
-            const double k4 = sP * a_rad * G.c;
-            const double rhs = G.c * sE * e[n] + cv_dt * Ts[n];
-            double y = Told[n];
-            int its;
-            for (its = 1; its <= maxit; ++its) {
-                const double y3 = y * y * y;
-                const double f = cv_dt * y + k4 * y3 * y - rhs;
-                const double df = cv_dt + 4.0 * k4 * y3;
-                const double adf = fabs(df);
-                const double rdf = (adf > 1e-30 && adf < 1e30) ? (double)__frcp_rn((float)df)
-                                                               : 1.0 / df;
-                const double yn = fmax(y - f * rdf, T_floor);
-                const bool conv = fabs(yn - y) <= rtol * fabs(yn);
-                y = yn;
-                if (conv) break;
-            }
-            its_max = max(its_max, min(its, maxit));
-            Tn[n] = y;
-            const double dT = y - Told[n], dE = e[n] - Eold[n];
-            v[0] += dT * dT + dE * dE;
-            v[1] += y * y + e[n] * e[n];
+    for (int n = 0; n < NN; ++n) {
+        const size_t nd = (size_t)k * NN + n;
+        A.F[nd * D] = (A.bF[nd * D] - ax[n]) * ia[n];
+        if constexpr (D == 2) A.F[nd * D + 1] = (A.bF[nd * D + 1] - ay[n]) * ia[n];
+        const double *cl = A.clo + nd * A.nc;
+        const double sE = cl[NN == 4 ? 6 : 3], sP = cl[NN == 4 ? 8 : 5];
+        const double cv_dt = cvv[n] / A.dt;
+        const double k4 = sP * A.a_rad * G.c;
+        const double rhs = G.c * sE * e[n] + cv_dt * Ts[n];
+        double y = Told[n];
+        int its;
+        for (its = 1; its <= A.max_elim; ++its) {
+            const double y3 = y * y * y;
+            const double f = cv_dt * y + k4 * y3 * y - rhs;
+            const double df = cv_dt + 4.0 * k4 * y3;
+            const double adf = fabs(df);
+            const double rdf = (adf > 1e-30 && adf < 1e30) ? (double)__frcp_rn((float)df)
+                                                           : 1.0 / df;
+            const double yn = fmax(y - f * rdf, A.T_floor);
+            const bool conv = fabs(yn - y) <= A.elim_rtol * fabs(yn);
+            y = yn;
+            if (conv) break;
         }
-        stc<NN>(T, k, Tn);
-        stc<NN>(E, k, e);
+        its_max = max(its_max, min(its, A.max_elim));
+        Tn[n] = y;
+        const double dT = y - Told[n], dE = e[n] - Eold[n];
+        v[0] += dT * dT + dE * dE;
+        v[1] += y * y + e[n] * e[n];
     }
-    const int wmax = __reduce_max_sync(0xffffffffu, its_max);
-    if ((threadIdx.x & 31) == 0 && wmax > 0) atomicMax(&sc->elim_max, wmax);
-    if (grid_sums<2>(v, part, &sc->count)) {
-        sc->d2 = v[0];
-        sc->n2 = v[1];
+    stc<NN>(A.T, k, Tn);
+    stc<NN>(A.E, k, e);
+}
+
+// at least 4 blocks per SM (128 registers per thread): a 256x256 mesh (512
+// blocks of cells) then runs without grid-stride repeats
+template <int NN>
+__global__ void __launch_bounds__(BLOCK, 4) lo_newton_kernel(const NewtonArgs A) {
+    const Geo &G = A.G;
+    const int stride = gridDim.x * BLOCK;
+    const int k0 = blockIdx.x * BLOCK + threadIdx.x;
+    int status = LO_OK, newton = 0, pcg_total = 0, pcg_max = 0, capped = 0;
+    double d1 = -1.0;
+    for (int it = 1; it <= A.max_inner; ++it) {
+        // set-up
+        double v3[3] = {0.0, 0.0, 0.0};
+        for (int k = k0; k < G.ncell; k += stride) newton_setup_cell<NN>(A, k, v3);
+        block_partials<3>(v3, A.partA);
+        if (!grid_barrier(A.bar)) { status = LO_TIMEOUT; break; }
+        grid_totals<3>(v3, A.partA);
+        double rz = v3[1], beta = 0.0;
+        const double stop = A.pcg_rtol * sqrt(v3[2]);
+        int done = sqrt(v3[0]) <= stop ? DONE_CONVERGED : DONE_NO, iters = 0;
+        // conjugate gradients on S E = b (start x = E, p = z)
+        while (done == DONE_NO) {
+            const double *po = (iters & 1) ? A.pb1 : A.pb0;
+            double *pn = (iters & 1) ? A.pb0 : A.pb1;
+            double v1[1] = {0.0};
+            for (int k = k0; k < G.ncell; k += stride) {
+                const Cell C = cell_of(G, k);
+                double aEv[NN], qv[NN], pv[NN];
+                ldc<NN>(A.aE, k, aEv);
+                schur_cell<NN>(G, C, DirCG<NN>{A.z, po, beta}, aEv, A.iaF, qv, pv);
+                stc<NN>(pn, k, pv);
+                stc<NN>(A.q, k, qv);
+#pragma unroll
+                for (int n = 0; n < NN; ++n) v1[0] += pv[n] * qv[n];
+            }
+            block_partials<1>(v1, A.partB);
+            if (!grid_barrier(A.bar)) { done = DONE_TIMEOUT; break; }
+            grid_totals<1>(v1, A.partB);
+            if (!(v1[0] > 0.0) || !isfinite(v1[0]) || !isfinite(rz)) { done = DONE_BREAKDOWN; break; }
+            const double alpha = rz / v1[0];
+            double v2[2] = {0.0, 0.0};
+            for (int k = k0; k < G.ncell; k += stride) {
+                double pv[NN], qv[NN], dv[NN], xv[NN], rv[NN], zv[NN];
+                ldc<NN>(pn, k, pv);
+                ldc<NN>(A.q, k, qv);
+                ldc<NN>(A.idiag, k, dv);
+                ldc<NN>(A.x, k, xv);
+                ldc<NN>(A.r, k, rv);
+#pragma unroll
+                for (int n = 0; n < NN; ++n) {
+                    xv[n] = fma(alpha, pv[n], xv[n]);
+                    rv[n] = fma(-alpha, qv[n], rv[n]);
+                    zv[n] = rv[n] * dv[n];
+                    v2[0] += rv[n] * rv[n];
+                    v2[1] += rv[n] * zv[n];
+                }
+                stc<NN>(A.x, k, xv);
+                stc<NN>(A.r, k, rv);
+                stc<NN>(A.z, k, zv);
+            }
+            block_partials<2>(v2, A.partC);
+            if (!grid_barrier(A.bar)) { done = DONE_TIMEOUT; break; }
+            grid_totals<2>(v2, A.partC);
+            ++iters;
+            if (sqrt(v2[0]) <= stop) { done = DONE_CONVERGED; break; }
+            if (iters >= A.max_pcg) { done = DONE_CAPPED; break; }
+            beta = v2[1] / rz;
+            rz = v2[1];
+        }
+        if (done == DONE_TIMEOUT) { status = LO_TIMEOUT; break; }
+        if (done == DONE_BREAKDOWN) { status = LO_BREAKDOWN; break; }
+        pcg_total += iters;
+        pcg_max = max(pcg_max, iters);
+        if (done != DONE_CONVERGED) ++capped;
+        ++newton;
+        // finish: back-substitution and pointwise elimination
+        double v2[2] = {0.0, 0.0};
+        int its_max = 0;
+        for (int k = k0; k < G.ncell; k += stride) newton_finish_cell<NN>(A, k, v2, its_max);
+        const int wmax = __reduce_max_sync(0xffffffffu, its_max);
+        if ((threadIdx.x & 31) == 0 && wmax > 0) atomicMax(&A.sc->elim_max, wmax);
+        block_partials<2>(v2, A.partD);
+        if (!grid_barrier(A.bar)) { status = LO_TIMEOUT; break; }
+        grid_totals<2>(v2, A.partD);
+        const double dn = sqrt(v2[0]), un = sqrt(v2[1]);
+        if (!isfinite(dn)) { status = LO_NONFINITE; break; }
+        if (d1 < 0.0) d1 = dn;
+        // Eq. relative_tol, plus a round-off guard for an update that is
+        // already at round-off level
+        if (dn == 0.0 || dn < A.eps_inner * d1 || dn <= 1e-14 * un) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Scalars *sc = A.sc;
+        sc->newton_iters = newton;
+        sc->pcg_total = pcg_total;
+        sc->pcg_max = pcg_max;
+        sc->pcg_capped = capped;
+        if (status != LO_OK) sc->status = status;
+    } else if (status == LO_TIMEOUT && threadIdx.x == 0) {
+        A.sc->status = LO_TIMEOUT;
     }
 }
 
@@ -1033,7 +1060,7 @@ sm_status lo_ensure(sm_problem *p) {
     w.Tin = take(N);
     w.Ein = take(N);
     const size_t nblk = (size_t)std::max(w.nblk_cell, w.nblk_node);
-    LO_CUDA(cudaMalloc(&w.part, sizeof(double) * 3 * nblk));
+    LO_CUDA(cudaMalloc(&w.part, sizeof(double) * 8 * nblk));
     LO_CUDA(cudaMalloc(&w.jin2, sizeof(double) * 4));
     {  // consistent method: R0 [N], R1f [N][dim], quadrant moments, inflow moments
         LO_CUDA(cudaMalloc(&w.R0, sizeof(double) * (size_t)N * 3));
@@ -1109,39 +1136,72 @@ sm_status check_params(const sm_step_params &prm) {
     return SM_OK;
 }
 
-// One cooperative launch runs the whole PCG solve (all blocks co-resident;
-// the grid is at most the blocks that fit on the GPU at once).
+// One cooperative launch runs the whole Newton iteration (all blocks
+// co-resident: the grid is at most the blocks that fit on the GPU at once).
 template <int NN>
-sm_status launch_pcg(sm_problem *p, sm_lo_state &w, const Geo &G, cudaStream_t s) {
-    const void *k = (const void *)smk::lo::pcg_persistent_kernel<NN>;
+sm_status launch_newton(sm_problem *p, sm_lo_state &w, const Geo &G, const double *clo,
+                        double *T, double *E, double *F, const double *Tstar, const double *cv,
+                        const double *R0, const sm_step_params &prm) {
+    const void *k = (const void *)smk::lo::lo_newton_kernel<NN>;
     if (w.coop_grid == 0) {
         int dev = 0, nsm = 0, per_sm = 0;
         LO_CUDA(cudaGetDevice(&dev));
         LO_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         LO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BLOCK, 0));
-        if (per_sm < 1) return lo_fail(SM_ERR_CUDA, "the PCG kernel does not fit on an SM");
+        if (per_sm < 1) return lo_fail(SM_ERR_CUDA, "the low-order kernel does not fit on an SM");
         w.coop_grid = std::min(w.nblk_cell, per_sm * nsm);
     }
-    smk::lo::GridBar bar;
-    bar.count = &w.sc->bar_count;
-    bar.gen = &w.sc->bar_gen;
-    bar.nblocks = (unsigned)w.coop_grid;
-    bar.limit_ns = p->timeout_ns;
-    Geo g = G;
-    const double *aE = w.aE, *iaF = w.iaF, *idiag = w.idiag;
-    double *x = w.x, *r = w.r, *z = w.z, *p0 = w.pb[0], *p1 = w.pb[1], *q = w.q;
     const size_t nblk = (size_t)std::max(w.nblk_cell, w.nblk_node);
-    double *partA = w.part, *partB = w.part + nblk;
-    smk::lo::Scalars *sc = w.sc;
-    void *args[] = {&g, &aE, &iaF, &idiag, &x, &r, &z, &p0, &p1, &q, &partA, &partB, &sc, &bar};
-    LO_CUDA(cudaLaunchCooperativeKernel(k, dim3(w.coop_grid), dim3(BLOCK), args, 0, s));
+    smk::lo::NewtonArgs A;
+    A.G = G;
+    A.clo = clo;
+    A.nc = p->nc;
+    A.a_rad = p->desc.a;
+    A.dt = p->desc.dt;
+    A.T = T;
+    A.E = E;
+    A.F = F;
+    A.Tstar = Tstar;
+    A.cv = cv;
+    A.Estar = w.Estar;
+    A.jin2 = w.jin2;
+    A.R0 = R0;
+    A.iaF = w.iaF;
+    A.ub = w.ub;
+    A.bF = w.bF;
+    A.aE = w.aE;
+    A.idiag = w.idiag;
+    A.x = w.x;
+    A.r = w.r;
+    A.z = w.z;
+    A.pb0 = w.pb[0];
+    A.pb1 = w.pb[1];
+    A.q = w.q;
+    A.partA = w.part;
+    A.partB = w.part + 3 * nblk;
+    A.partC = w.part + 4 * nblk;
+    A.partD = w.part + 6 * nblk;
+    A.pcg_rtol = prm.pcg_rtol;
+    A.eps_inner = prm.eps_inner;
+    A.elim_rtol = prm.elim_rtol;
+    A.T_floor = prm.T_floor;
+    A.max_pcg = prm.max_pcg;
+    A.max_inner = prm.max_inner;
+    A.max_elim = prm.max_elim;
+    A.sc = w.sc;
+    A.bar.count = &w.sc->bar_count;
+    A.bar.gen = &w.sc->bar_gen;
+    A.bar.nblocks = (unsigned)w.coop_grid;
+    A.bar.limit_ns = p->timeout_ns;
+    void *args[] = {&A};
+    LO_CUDA(cudaLaunchCooperativeKernel(k, dim3(w.coop_grid), dim3(BLOCK), args, 0, p->stream));
     return SM_OK;
 }
 
 // The Newton iteration of Sec. 5 on the gray system with fixed closures.
 // Time-edge sources in w.Estar / w.Fstar; T, E hold the initial guesses and
 // receive the result, F receives the flux of the last linear solve.  One
-// host synchronisation per Newton iteration (its stopping test).
+// cooperative launch and one host synchronisation per solve.
 template <int NN>
 sm_status lo_solve(sm_problem *p, const double *clo, const double *Tstar, const double *cv,
                    double *T, double *E, double *F, const sm_step_params &prm,
@@ -1149,7 +1209,7 @@ sm_status lo_solve(sm_problem *p, const double *clo, const double *Tstar, const 
     sm_lo_state &w = *p->lo;
     const Geo G = make_geo(p);
     cudaStream_t s = p->stream;
-    const double dt = p->desc.dt, a = p->desc.a;
+    const double dt = p->desc.dt;
     const double *R0 = nullptr, *R1f = nullptr;
     if (qmom) {  // consistent method
         if (NN == 4)
@@ -1167,39 +1227,23 @@ sm_status lo_solve(sm_problem *p, const double *clo, const double *Tstar, const 
                                                           w.Fstar, R1f, w.iaF, w.bF, w.ub, w.sc);
     LO_CUDA(cudaGetLastError());
     p->launches++;
-    double d1 = -1.0;
-    for (int it = 1; it <= prm.max_inner; ++it) {
-        smk::lo::newton_setup_kernel<NN><<<w.nblk_cell, BLOCK, 0, s>>>(
-            G, clo, p->nc, a, dt, T, Tstar, cv, w.Estar, w.jin2, R0, w.iaF, w.ub, E, w.aE, w.idiag,
-            w.x, w.r, w.z, w.pb[0], prm.pcg_rtol, prm.max_pcg, w.part, w.sc);
-        LO_CUDA(cudaGetLastError());
-        LO_TRY(launch_pcg<NN>(p, w, G, s));
-        smk::lo::newton_finish_kernel<NN><<<w.nblk_cell, BLOCK, 0, s>>>(
-            G, clo, p->nc, a, dt, w.x, w.iaF, w.bF, Tstar, cv, T, E, F, prm.elim_rtol,
-            prm.max_elim, prm.T_floor, w.part, w.sc);
-        LO_CUDA(cudaGetLastError());
-        LO_TRY(read_scalars(p));
-        const smk::lo::Scalars &h = *w.h_sc;
-        p->launches += 3;  // setup, the PCG solve, finish
-        if (h.done == smk::lo::DONE_TIMEOUT)
-            return lo_fail(SM_ERR_TIMEOUT, "a grid barrier of the conjugate-gradient kernel ran out of time");
-        if (h.done == smk::lo::DONE_BREAKDOWN)
-            return lo_fail(SM_ERR_NO_CONVERGENCE,
-                           "conjugate gradients broke down: the Schur complement is not positive "
-                           "definite on the search direction, or the data is not finite");
-        st->pcg_iters_total += h.iters;
-        st->pcg_iters_max = std::max(st->pcg_iters_max, h.iters);
-        if (h.done != smk::lo::DONE_CONVERGED) st->pcg_capped++;
-        st->newton_iters_total++;
-        const double dn = std::sqrt(h.d2), un = std::sqrt(h.n2);
-        if (!std::isfinite(dn))
-            return lo_fail(SM_ERR_NONPHYSICAL, "the low-order Newton iterate is not finite");
-        if (d1 < 0) d1 = dn;
-        st->newton_iters_max = std::max(st->newton_iters_max, it);
-        // Eq. relative_tol, plus a round-off guard for an update that is
-        // already at round-off level
-        if (dn == 0.0 || dn < prm.eps_inner * d1 || dn <= 1e-14 * un) break;
-    }
+    LO_TRY(launch_newton<NN>(p, w, G, clo, T, E, F, Tstar, cv, R0, prm));
+    p->launches++;
+    LO_TRY(read_scalars(p));
+    const smk::lo::Scalars &h = *w.h_sc;
+    if (h.status == smk::lo::LO_TIMEOUT)
+        return lo_fail(SM_ERR_TIMEOUT, "a grid barrier of the low-order kernel ran out of time");
+    if (h.status == smk::lo::LO_BREAKDOWN)
+        return lo_fail(SM_ERR_NO_CONVERGENCE,
+                       "conjugate gradients broke down: the Schur complement is not positive "
+                       "definite on the search direction, or the data is not finite");
+    if (h.status == smk::lo::LO_NONFINITE)
+        return lo_fail(SM_ERR_NONPHYSICAL, "the low-order Newton iterate is not finite");
+    st->pcg_iters_total += h.pcg_total;
+    st->pcg_iters_max = std::max(st->pcg_iters_max, h.pcg_max);
+    st->pcg_capped += h.pcg_capped;
+    st->newton_iters_total += h.newton_iters;
+    st->newton_iters_max = std::max(st->newton_iters_max, h.newton_iters);
     st->elim_iters_max = std::max(st->elim_iters_max, w.h_sc->elim_max);
     return SM_OK;
 }
