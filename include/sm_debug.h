@@ -24,6 +24,11 @@ sm_status sm_debug_set_wait_limit_ns(sm_problem *p, long long ns);
 /* Non-zero: strip 0 of each chain withholds its row counters (see above). */
 sm_status sm_debug_skip_publish(sm_problem *p, int enable);
 
+/* Non-zero: the last block of the cooperative low-order kernel leaves before
+ * its first grid barrier, so every other block's barrier wait runs into the
+ * time limit; the solve returns SM_ERR_TIMEOUT and the problem stays usable. */
+sm_status sm_debug_withhold_lo_block(sm_problem *p, int enable);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,8 @@ EXPORTED = ["sm_create_problem", "sm_destroy_problem", "sm_get_info", "sm_set_st
             "sm_closures", "sm_sweep_host", "sm_pack_intensity", "sm_unpack_intensity",
             "sm_synchronize", "sm_autotune", "sm_set_profiling", "sm_get_kernel_times",
             "sm_launch_count", "sm_last_error", "sm_status_string",
-            "sm_debug_set_wait_limit_ns", "sm_debug_skip_publish", "sm_sweep_static",
+            "sm_debug_set_wait_limit_ns", "sm_debug_skip_publish", "sm_debug_withhold_lo_block",
+            "sm_sweep_static",
             "sm_default_step_params", "sm_loworder_newton", "sm_step",
             "sm_create_batch", "sm_destroy_batch", "sm_batch_problem", "sm_batch_get_info",
             "sm_batch_set_stream", "sm_batch_set_tiling", "sm_batch_sweep",
@@ -139,6 +140,7 @@ def load():
         "sm_get_kernel_times": [P, PD, ctypes.POINTER(ctypes.c_int)],
         "sm_debug_set_wait_limit_ns": [P, ctypes.c_longlong],
         "sm_debug_skip_publish": [P, I],
+        "sm_debug_withhold_lo_block": [P, I],
         "sm_sweep_static": [ctypes.POINTER(ProblemDesc), P, P, P, P, P, P, P],
         "sm_loworder_newton": [P, P, P, P, P, P, P, P, ctypes.POINTER(StepParams),
                                ctypes.POINTER(StepStats)],
@@ -439,6 +441,9 @@ class Problem:
 
     def debug_skip_publish(self, on: bool):
         _check(load().sm_debug_skip_publish(self._h, 1 if on else 0))
+
+    def debug_withhold_lo_block(self, on: bool):
+        _check(load().sm_debug_withhold_lo_block(self._h, 1 if on else 0))
 
 
 def _desc_of(cfg, precision: int, keep):

@@ -824,6 +824,11 @@ sm_status sm_debug_skip_publish(sm_problem *p, int enable) {
     p->fault_skip_publish = enable != 0;
     return SM_OK;
 }
+sm_status sm_debug_withhold_lo_block(sm_problem *p, int enable) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    p->fault_withhold_block = enable != 0;
+    return SM_OK;
+}
 
 }  // extern "C"
 

@@ -164,6 +164,7 @@ struct sm_problem {
     unsigned long long epoch = 0;
     long long timeout_ns = 2000000000LL;
     int fault_skip_publish = 0;
+    int fault_withhold_block = 0;  // test hook: a low-order block skips its barriers
     cudaStream_t stream = nullptr;
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;  // 4 events per timed sweep, read back lazily

@@ -696,6 +696,7 @@ struct NewtonArgs {
     int max_pcg, max_inner, max_elim;
     Scalars *sc;
     GridBar bar;
+    int withhold;  // test hook: the last block leaves before its first barrier
 };
 
 // Per Newton iteration, for cell k: linearise the emission about
@@ -830,6 +831,7 @@ __device__ __forceinline__ void newton_finish_cell(const NewtonArgs &A, int k, d
 // blocks of cells) then runs without grid-stride repeats
 template <int NN>
 __global__ void __launch_bounds__(BLOCK, 4) lo_newton_kernel(const NewtonArgs A) {
+    if (A.withhold && blockIdx.x == gridDim.x - 1) return;
     const Geo &G = A.G;
     const int stride = gridDim.x * BLOCK;
     const int k0 = blockIdx.x * BLOCK + threadIdx.x;
@@ -1193,6 +1195,7 @@ sm_status launch_newton(sm_problem *p, sm_lo_state &w, const Geo &G, const doubl
     A.bar.gen = &w.sc->bar_gen;
     A.bar.nblocks = (unsigned)w.coop_grid;
     A.bar.limit_ns = p->timeout_ns;
+    A.withhold = p->fault_withhold_block;
     void *args[] = {&A};
     LO_CUDA(cudaLaunchCooperativeKernel(k, dim3(w.coop_grid), dim3(BLOCK), args, 0, p->stream));
     return SM_OK;

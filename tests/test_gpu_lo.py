@@ -310,3 +310,28 @@ def test_step_default_params_converges(gpu_lib):
     assert st["converged"] == 1 and st["outer_iters"] == st_r["outer"]
     assert _field(T.cpu().numpy(), Tr) < 1e-8
     assert _field(E.cpu().numpy(), Er) < 1e-8
+
+
+def test_barrier_timeout_reports_status_and_recovers(gpu_lib):
+    """The cooperative low-order kernel with one block withheld (a test hook:
+    it leaves before its first grid barrier): every other block's bounded
+    barrier wait runs out, the solve returns SM_ERR_TIMEOUT without any fault,
+    and the next solve of the same problem equals one of a fresh problem."""
+    sm = gpu_lib
+    cfg = _cfg(2, 40, 36)   # several blocks of cells
+    m, clo, T, cv, mom_k, alpha, jin2 = _lo_inputs(cfg, seed=31)
+    Estar = mom_k[..., 0] / cfg.c
+    ref = _gpu_lo(sm, cfg, clo, T, cv, mom_k, T, Estar)
+    import torch
+    prob = sm.Problem.from_config(cfg, 64)
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    prob.debug_wait_limit_ns(50_000_000)  # 50 ms
+    prob.debug_withhold_lo_block(True)
+    with pytest.raises(sm.SMError) as ei:
+        prob.loworder_newton(cu(clo), cu(T), cu(cv), cu(mom_k), cu(T.copy()), cu(Estar.copy()))
+    assert ei.value.code == 6  # SM_ERR_TIMEOUT
+    prob.debug_withhold_lo_block(False)
+    prob.debug_wait_limit_ns(2_000_000_000)
+    Tg, Eg = cu(T.copy()), cu(Estar.copy())
+    prob.loworder_newton(cu(clo), cu(T), cu(cv), cu(mom_k), Tg, Eg)
+    assert np.array_equal(Tg.cpu().numpy(), ref[0]) and np.array_equal(Eg.cpu().numpy(), ref[1])
