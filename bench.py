@@ -459,8 +459,10 @@ def adjoint_metric(sm, W, fd_cells: int, warm: bool = False):
     (segment recomputation + adjoint steps), and central differences
     (h = 1e-4 s_K) of the time-integrated right-edge leakage on fd_cells
     cells drawn with seed 21784 among the cells whose adjoint sensitivity is
-    at least 1e-3 of the largest (smaller sensitivities move J by less than
-    its FP64 rounding for a 1e-4 perturbation)."""
+    at least 5e-2 of the largest (each forward solve stops at a relative
+    change of 1e-13, so J carries about that much error; a 1e-4 s_K
+    perturbation of a smaller sensitivity moves J by too little for the
+    difference quotient to reach 1e-4))."""
     import numpy as np
     import torch
     from paper_2504_21784_gb300 import adjoint as A
@@ -485,7 +487,7 @@ def adjoint_metric(sm, W, fd_cells: int, warm: bool = False):
            "forward_s": t1 - t0, "backward_s": t2 - t1, "checkpoint_every": st.every(),
            "params": int(g.size), "grad_max_abs": float(np.abs(g).max())}
     if fd_cells > 0:
-        cand = np.flatnonzero(np.abs(g) >= 1e-3 * np.abs(g).max())
+        cand = np.flatnonzero(np.abs(g) >= 5e-2 * np.abs(g).max())
         rng = np.random.default_rng(21784)
         cells = rng.choice(cand, min(fd_cells, cand.size), replace=False)
         errs = []

@@ -196,8 +196,9 @@ def test_adjoint_full_size_matches_central_differences(gpu_lib):
     """The adjoint workload from the warm start (T0 = 0.3), 20 steps with
     checkpoints every sqrt(20) steps: dJ/ds_K against central differences
     (h = 1e-4 s_K) of the GPU forward on 4 seeded cells among those whose
-    sensitivity is at least 1e-3 of the largest (smaller ones move J by less
-    than its FP64 rounding)."""
+    sensitivity is at least 5e-2 of the largest: each forward solve stops at a
+    relative change of 1e-13, so the difference quotient of a smaller
+    sensitivity is dominated by that error, not by the derivative."""
     import torch
     from paper_2504_21784_gb300 import adjoint as A
     sm = gpu_lib
@@ -212,7 +213,7 @@ def test_adjoint_full_size_matches_central_differences(gpu_lib):
     J = A.leakage(s, st)
     J.backward()
     g = s.grad.detach().cpu().numpy()
-    cand = np.flatnonzero(np.abs(g) >= 1e-3 * np.abs(g).max())
+    cand = np.flatnonzero(np.abs(g) >= 5e-2 * np.abs(g).max())
     cells = np.random.default_rng(7).choice(cand, min(4, cand.size), replace=False)
     errs = []
     with torch.no_grad():
