@@ -175,10 +175,11 @@ sm_status sm_closures(sm_problem *p, const double *moments_dev, const double *T_
 /* ------------------------------------------------------------------------
  * Gray low-order solve and the full time step (Sec. 4 independent LDG
  * system, Sec. 5 Newton iteration, Algorithm 1).  All low-order arithmetic
- * is FP64 on the device; the host only drives the iterations (it reads a
- * few scalars per conjugate-gradient chunk and per Newton iteration), so
- * both calls synchronize the problem's stream and cannot be captured into
- * a CUDA graph.
+ * is FP64 on the device: a low-order solve is one cooperative launch (the
+ * Newton iteration with its conjugate-gradient solves and stopping tests),
+ * after which the host reads its statistics; sm_step also reads the outer
+ * iteration's change per iteration.  Both calls therefore synchronize the
+ * problem's stream and cannot be captured into a CUDA graph.
  * ---------------------------------------------------------------------- */
 
 /* Iteration controls.  Defaults (sm_default_step_params) are the paper's
