@@ -44,8 +44,8 @@ constexpr int BLOCK = 128;
 enum { DONE_NO = 0, DONE_CONVERGED = 1, DONE_BREAKDOWN = 2, DONE_CAPPED = 3, DONE_TIMEOUT = 4 };
 
 struct Scalars {
-    double alpha, beta, rz, bnorm, rr, d2, n2, rtol;
-    int done, iters, max_iters, elim_max;
+    double d2, n2;       // outer iteration: squared norms of the change of (T, E) and of (T, E)
+    int elim_max;        // most temperature-elimination iterations of any node
     unsigned int count;  // arrivals of the running kernel's blocks
     unsigned int bar_count, bar_gen;  // grid barrier of the cooperative kernels
     // statistics of the last low-order solve (cooperative Newton kernel)
@@ -99,27 +99,9 @@ __device__ __forceinline__ void stc(double *__restrict__ a, int k, const double 
     for (int i = 0; i < NN / 2; ++i) p[i] = make_double2(v[2 * i], v[2 * i + 1]);
 }
 
-template <int NN>
-struct Vec {
-    const double *v;
-    __device__ __forceinline__ void get(int k, double (&o)[NN]) const { ldc<NN>(v, k, o); }
-};
-// PCG search direction formed on the fly: p = z + beta p_old
-template <int NN>
-struct Dir {
-    const double *z, *p;
-    double beta;
-    __device__ __forceinline__ void get(int k, double (&o)[NN]) const {
-        double a[NN], b[NN];
-        ldc<NN>(z, k, a);
-        ldc<NN>(p, k, b);
-#pragma unroll
-        for (int i = 0; i < NN; ++i) o[i] = fma(beta, b[i], a[i]);
-    }
-};
-
-// The same with loads that bypass L1 (ld.global.cg): for values other blocks
-// of the running kernel wrote (the persistent PCG kernel's z and p).
+// Accessors of the nodal values of cell k, with loads that bypass L1
+// (ld.global.cg): the cooperative low-order kernel reads values that other
+// blocks of the same launch wrote (E, x, and the PCG's z and p).
 template <int NN>
 __device__ __forceinline__ void ldc_cg(const double *a, int k, double (&v)[NN]) {
     const double2 *p = reinterpret_cast<const double2 *>(a + (size_t)k * NN);
@@ -135,6 +117,7 @@ struct VecCG {
     const double *v;
     __device__ __forceinline__ void get(int k, double (&o)[NN]) const { ldc_cg<NN>(v, k, o); }
 };
+// PCG search direction formed on the fly: p = z + beta p_old
 template <int NN>
 struct DirCG {
     const double *z, *p;
