@@ -2,7 +2,9 @@
 element by element, on seeded inputs that span several strips, several warp
 tasks, padded lanes and groups, and ragged strip tails.
 
-Tolerances (spec contract; derivation in the design doc):
+Tolerances (the FP64 bound leaves room for the reordered sums of the fused
+moments and the table-driven Planck functions; the FP32 bound for the
+rounding of I, q and the cell solve to single precision):
   FP64 sweep:  1e-11 relative      FP32 sweep:  1e-5 relative
 "Relative" is taken per field, as the paper reports errors relative to the
 magnitude of the reference: every element's error is divided by the largest
