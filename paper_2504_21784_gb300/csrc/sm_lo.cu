@@ -6,7 +6,8 @@
 //    pseudo-fission linearisation of the emission (Eq. pseudo_fission) and the
 //    pointwise nonlinear temperature elimination (Eq. nonlinear_T_update);
 //  * the Schur complement in E (Eq. schur), symmetric positive definite for
-//    lumped forms, solved by preconditioned conjugate gradients;
+//    lumped forms, solved by Jacobi-preconditioned conjugate gradients in
+//    the single-reduction form of Chronopoulos and Gear;
 //  * Algorithm 1 (outer fixed point between the transport sweep and the
 //    low-order solve) with the relative stopping rule Eq. relative_tol.
 //
@@ -47,7 +48,7 @@ struct Scalars {
     double d2, n2;       // outer iteration: squared norms of the change of (T, E) and of (T, E)
     int elim_max;        // most temperature-elimination iterations of any node
     unsigned int count;  // arrivals of the running kernel's blocks
-    unsigned int bar_count, bar_gen;  // grid barrier of the cooperative kernels
+    unsigned int bar_count;  // arrivals at the cooperative kernel's grid barriers
     // statistics of the last low-order solve (cooperative Newton kernel)
     int newton_iters, pcg_total, pcg_max, pcg_capped, status;
 };
@@ -101,7 +102,7 @@ __device__ __forceinline__ void stc(double *__restrict__ a, int k, const double 
 
 // Accessors of the nodal values of cell k, with loads that bypass L1
 // (ld.global.cg): the cooperative low-order kernel reads values that other
-// blocks of the same launch wrote (E, x, and the PCG's z and p).
+// blocks of the same launch wrote (E, x, diag(S) and the PCG's r, w, s).
 template <int NN>
 __device__ __forceinline__ void ldc_cg(const double *a, int k, double (&v)[NN]) {
     const double2 *p = reinterpret_cast<const double2 *>(a + (size_t)k * NN);
@@ -116,19 +117,6 @@ template <int NN>
 struct VecCG {
     const double *v;
     __device__ __forceinline__ void get(int k, double (&o)[NN]) const { ldc_cg<NN>(v, k, o); }
-};
-// PCG search direction formed on the fly: p = z + beta p_old
-template <int NN>
-struct DirCG {
-    const double *z, *p;
-    double beta;
-    __device__ __forceinline__ void get(int k, double (&o)[NN]) const {
-        double a[NN], b[NN];
-        ldc_cg<NN>(z, k, a);
-        ldc_cg<NN>(p, k, b);
-#pragma unroll
-        for (int i = 0; i < NN; ++i) o[i] = fma(beta, b[i], a[i]);
-    }
 };
 
 // Node numbering inside a cell: n = a + 2b (2D), n = a (1D); a, b = 0 on the
@@ -566,9 +554,13 @@ prepare_kernel(Geo G, const double *__restrict__ clo, int nc, double inv_cdt,
 // that gives up records a timeout and leaves, and the others then give up at
 // their next barrier), and reductions whose per-block partials every block
 // sums in the same fixed order after the barrier, so that all blocks take the
-// same decisions.
+// same decisions.  The barrier counts arrivals on one counter that is never
+// reset inside a launch (the solve's set-up kernel zeroes it): barrier number
+// j is complete once the counter reaches j * nblocks, so a block arrives with
+// one release-ordered atomic and waits with acquire loads, and the last
+// arrival has nothing more to publish.
 struct GridBar {
-    unsigned int *count, *gen;
+    unsigned int *count;
     unsigned int nblocks;
     long long limit_ns;
 };
@@ -578,8 +570,8 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned int *p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void atom_add_release_u32(unsigned int *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ long long lo_global_ns() {
     long long t;
@@ -587,24 +579,22 @@ __device__ __forceinline__ long long lo_global_ns() {
     return t;
 }
 
-// false: the wait ran out of time (every thread of the block gets the same answer)
-__device__ bool grid_barrier(const GridBar &b) {
+// false: the wait ran out of time (every thread of the block gets the same
+// answer).  `target` is the block's running arrival target (thread 0's copy
+// is the one used), starting at 0 in every launch.
+__device__ bool grid_barrier(const GridBar &b, unsigned &target) {
     __syncthreads();
     int ok = 1;
     if (threadIdx.x == 0) {
-        const unsigned g = ld_acquire_u32(b.gen);
-        __threadfence();
-        if (atomicAdd(b.count, 1u) == b.nblocks - 1) {
-            atomicExch(b.count, 0u);
-            __threadfence();
-            st_release_u32(b.gen, g + 1);
-        } else {
-            const long long t0 = lo_global_ns();
-            while (ld_acquire_u32(b.gen) == g) {
-                if (lo_global_ns() - t0 > b.limit_ns) {
-                    ok = 0;
-                    break;
-                }
+        target += b.nblocks;
+        // release: the block's writes (ordered before this thread's by the
+        // __syncthreads above) become visible with the arrival
+        atom_add_release_u32(b.count, 1u);
+        const long long t0 = lo_global_ns();
+        while ((int)(ld_acquire_u32(b.count) - target) < 0) {
+            if (lo_global_ns() - t0 > b.limit_ns) {
+                ok = 0;
+                break;
             }
         }
     }
@@ -655,17 +645,31 @@ __device__ void grid_totals(double (&v)[K], const double *part) {
 
 // ---------------------------------------------------------------------------
 // The whole Newton iteration of a low-order solve in one cooperative launch:
-// per Newton iteration the set-up phase (linearisation, Schur right-hand
-// side, residual and preconditioned residual of the start x = E), the PCG
-// phases and the finish phase (back-substitution and pointwise temperature
-// elimination), each reduction
-// closed by a grid barrier, and the stopping test of Eq. relative_tol taken
-// by every block on the same grid totals.  The conjugate-gradient iteration
-// alternates a matrix-vector phase (p = z + beta p_old formed on the fly for
-// the neighbours, q = S p, p.q) and an update phase (x, r, z; r.r, r.z).
-// Partial sums of consecutive reductions go to different buffers (A: set-up, B / C: the two PCG phases,
-// D: finish), so one barrier per reduction suffices.  Values other blocks
-// wrote in the same launch (E, x, z, p of neighbour cells) are read past L1.
+// per Newton iteration a set-up phase (linearisation, Schur right-hand side,
+// residual of the start x = E), the conjugate-gradient phases and the finish
+// phase (back-substitution and pointwise temperature elimination), each
+// closed by a grid barrier, and the stopping test of Eq. relative_tol taken by
+// every block on the same grid totals.  The preconditioner is Jacobi,
+// u = r / diag(S).  Two forms of the conjugate gradients (mathematically the
+// same iterates):
+//  * textbook (SINGLE = false): a matrix-vector phase (p = u + beta p_old
+//    formed on the fly for the neighbours, q = S p, p.q) and an update phase
+//    (x, r, u; r.r, r.u), two grid reductions per iteration;
+//  * single-reduction (SINGLE = true), the form of Chronopoulos and Gear
+//    (J. Comput. Appl. Math. 25, 1989): with w = S u, gamma = r.u, delta = w.u,
+//      beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old),
+//      p = u + beta p, s = w + beta s (= S p), x += alpha p, r -= alpha s,
+//    and the next u, w = S u, gamma, delta and r.r in the same phase, one grid
+//    reduction per iteration (plus one set-up phase for the first w).  The
+//    product needs the new u of the neighbour cells: each cell forms them on
+//    the fly from the neighbours' r, w and s of the previous phase, which are
+//    double-buffered.  That costs about 40 FP64 operations per cell and saves
+//    a barrier, which pays only while the FP64 pipes are lightly loaded; the
+//    host picks the form from the cells per SM sub-partition.
+// Partial sums of consecutive reductions go to different buffers (A: set-up,
+// B / C: the conjugate-gradient phases, D: finish), so one barrier per
+// reduction suffices.  Values other blocks wrote in the same launch (E, x and
+// the search vectors of neighbour cells) are read past L1.
 struct NewtonArgs {
     Geo G;
     const double *clo;
@@ -673,7 +677,8 @@ struct NewtonArgs {
     double a_rad, dt;
     double *T, *E, *F;
     const double *Tstar, *cv, *Estar, *jin2, *R0, *iaF, *ub, *bF;
-    double *aE, *idiag, *x, *r, *z, *pb0, *pb1, *q;
+    double *aE, *idiag, *x, *p;
+    double *r[2], *w[2], *s[2];  // double-buffered by iteration parity
     double *partA, *partB, *partC, *partD;
     double pcg_rtol, eps_inner, elim_rtol, T_floor;
     int max_pcg, max_inner, max_elim;
@@ -682,12 +687,39 @@ struct NewtonArgs {
     int withhold;  // test hook: the last block leaves before its first barrier
 };
 
+// The preconditioned residual u of cell k for the next matrix-vector product,
+// from values of the previous phase: before the first iteration (START)
+// u = r / diag(S), else u = (r - alpha s) / diag(S) with s = w + beta s_old
+// (s_old = 0 and beta = 0 in the first iteration).  The owner of the cell
+// forms its own r and s with the same operations, so both agree bit for bit.
+template <int NN, bool START>
+struct NextU {
+    const double *r, *w, *s, *idg;
+    double alpha, beta;
+    __device__ __forceinline__ void get(int k, double (&o)[NN]) const {
+        double rv[NN], dv[NN];
+        ldc_cg<NN>(r, k, rv);
+        ldc_cg<NN>(idg, k, dv);
+        if constexpr (START) {
+#pragma unroll
+            for (int i = 0; i < NN; ++i) o[i] = rv[i] * dv[i];
+        } else {
+            double wv[NN], sv[NN];
+            ldc_cg<NN>(w, k, wv);
+            ldc_cg<NN>(s, k, sv);
+#pragma unroll
+            for (int i = 0; i < NN; ++i) o[i] = fma(-alpha, fma(beta, sv[i], wv[i]), rv[i]) * dv[i];
+        }
+    }
+};
+
 // Per Newton iteration, for cell k: linearise the emission about
 // the current T (Sec. 5), form aE = m c (sigma~_E - nu sigma_E), the Schur
 // right-hand side b_E - A_EF u_b with b_E = m (sigma_P B(T0) + nu q_T0 +
-// E*/dt) + the Marshak inflow, 1/diag(S), and start PCG from x = E:
-// r = rhs - S x, z = r / diag, p = z.
-template <int NN>
+// E*/dt) + the Marshak inflow, 1/diag(S), and the residual of the start
+// x = E: r = rhs - S x.  Sums ||rhs||^2 (the PCG stopping test's scale); the
+// textbook form also starts u = r / diag(S), p = u and sums r.r and r.u.
+template <int NN, bool SINGLE>
 __device__ __forceinline__ void newton_setup_cell(const NewtonArgs &A, int k, double (&v)[3]) {
     const Geo &G = A.G;
     const Cell C = cell_of(G, k);
@@ -732,7 +764,7 @@ __device__ __forceinline__ void newton_setup_cell(const NewtonArgs &A, int k, do
             }
         }
     }
-    double efu[NN], dg[NN], q[NN], e[NN], rv[NN], zv[NN], idg[NN];
+    double efu[NN], dg[NN], q[NN], e[NN], rv[NN], idg[NN], zv[NN];
     ef_cell<NN>(G, C, A.ub, efu);
     diag_cell<NN>(G, C, aE, A.iaF, dg);
     schur_cell<NN>(G, C, VecCG<NN>{A.E}, aE, A.iaF, q, e);
@@ -741,18 +773,37 @@ __device__ __forceinline__ void newton_setup_cell(const NewtonArgs &A, int k, do
         const double rhs = bE[n] - efu[n];
         rv[n] = rhs - q[n];
         idg[n] = 1.0 / dg[n];
-        zv[n] = rv[n] * idg[n];
-        v[0] += rv[n] * rv[n];
-        v[1] += rv[n] * zv[n];
-        v[2] += rhs * rhs;
+        v[0] += rhs * rhs;
+        if constexpr (!SINGLE) {
+            zv[n] = rv[n] * idg[n];
+            v[1] += rv[n] * rv[n];
+            v[2] += rv[n] * zv[n];
+        }
     }
     stc<NN>(A.aE, k, aE);
     stc<NN>(A.idiag, k, idg);
     stc<NN>(A.x, k, e);
-    stc<NN>(A.r, k, rv);
-    stc<NN>(A.z, k, zv);
-    stc<NN>(A.pb0, k, zv);
+    stc<NN>(A.r[0], k, rv);
+    if constexpr (!SINGLE) {
+        stc<NN>(A.r[1], k, zv);  // u
+        stc<NN>(A.w[0], k, zv);  // p
+    }
 }
+
+// Textbook form: the search direction of cell k formed on the fly,
+// p = u + beta p_old (values of the previous phase, read past L1)
+template <int NN>
+struct DirCG {
+    const double *u, *p;
+    double beta;
+    __device__ __forceinline__ void get(int k, double (&o)[NN]) const {
+        double a[NN], b[NN];
+        ldc_cg<NN>(u, k, a);
+        ldc_cg<NN>(p, k, b);
+#pragma unroll
+        for (int i = 0; i < NN; ++i) o[i] = fma(beta, b[i], a[i]);
+    }
+};
 
 // After the linear solve, for cell k: E = x, back-substitution
 // F = A_FF^-1 (b_F - A_FE E), then the pointwise nonlinear elimination of T
@@ -812,72 +863,164 @@ __device__ __forceinline__ void newton_finish_cell(const NewtonArgs &A, int k, d
 
 // at least 4 blocks per SM (128 registers per thread): a 256x256 mesh (512
 // blocks of cells) then runs without grid-stride repeats
-template <int NN>
+template <int NN, bool SINGLE>
 __global__ void __launch_bounds__(BLOCK, 4) lo_newton_kernel(const NewtonArgs A) {
     if (A.withhold && blockIdx.x == gridDim.x - 1) return;
     const Geo &G = A.G;
     const int stride = gridDim.x * BLOCK;
     const int k0 = blockIdx.x * BLOCK + threadIdx.x;
     int status = LO_OK, newton = 0, pcg_total = 0, pcg_max = 0, capped = 0;
+    unsigned bar_target = 0;  // arrivals that complete the next grid barrier
     double d1 = -1.0;
     for (int it = 1; it <= A.max_inner; ++it) {
-        // set-up
-        double v3[3] = {0.0, 0.0, 0.0};
-        for (int k = k0; k < G.ncell; k += stride) newton_setup_cell<NN>(A, k, v3);
-        block_partials<3>(v3, A.partA);
-        if (!grid_barrier(A.bar)) { status = LO_TIMEOUT; break; }
-        grid_totals<3>(v3, A.partA);
-        double rz = v3[1], beta = 0.0;
-        const double stop = A.pcg_rtol * sqrt(v3[2]);
-        int done = sqrt(v3[0]) <= stop ? DONE_CONVERGED : DONE_NO, iters = 0;
-        // conjugate gradients on S E = b (start x = E, p = z)
-        while (done == DONE_NO) {
-            const double *po = (iters & 1) ? A.pb1 : A.pb0;
-            double *pn = (iters & 1) ? A.pb0 : A.pb1;
-            double v1[1] = {0.0};
-            for (int k = k0; k < G.ncell; k += stride) {
-                const Cell C = cell_of(G, k);
-                double aEv[NN], qv[NN], pv[NN];
-                ldc<NN>(A.aE, k, aEv);
-                schur_cell<NN>(G, C, DirCG<NN>{A.z, po, beta}, aEv, A.iaF, qv, pv);
-                stc<NN>(pn, k, pv);
-                stc<NN>(A.q, k, qv);
+        // set-up: linearisation, r = rhs - S E, ||rhs||^2 (textbook form:
+        // also u, p = u, r.r, r.u)
+        double v0[3] = {0.0, 0.0, 0.0};
+        for (int k = k0; k < G.ncell; k += stride) newton_setup_cell<NN, SINGLE>(A, k, v0);
+        block_partials<3>(v0, A.partA);
+        if (!grid_barrier(A.bar, bar_target)) { status = LO_TIMEOUT; break; }
+        grid_totals<3>(v0, A.partA);
+        const double stop = A.pcg_rtol * sqrt(v0[0]);
+        int done = DONE_NO, iters = 0;
+        if constexpr (SINGLE) {
+            // second set-up phase: u = r / diag(S), w = S u; r.u, w.u, r.r;
+            // p = s = 0 before the first iteration
+            double v3[3] = {0.0, 0.0, 0.0};
+            {
+                const NextU<NN, true> nu{A.r[0], nullptr, nullptr, A.idiag, 0.0, 0.0};
+                double zero[NN];
 #pragma unroll
-                for (int n = 0; n < NN; ++n) v1[0] += pv[n] * qv[n];
-            }
-            block_partials<1>(v1, A.partB);
-            if (!grid_barrier(A.bar)) { done = DONE_TIMEOUT; break; }
-            grid_totals<1>(v1, A.partB);
-            if (!(v1[0] > 0.0) || !isfinite(v1[0]) || !isfinite(rz)) { done = DONE_BREAKDOWN; break; }
-            const double alpha = rz / v1[0];
-            double v2[2] = {0.0, 0.0};
-            for (int k = k0; k < G.ncell; k += stride) {
-                double pv[NN], qv[NN], dv[NN], xv[NN], rv[NN], zv[NN];
-                ldc<NN>(pn, k, pv);
-                ldc<NN>(A.q, k, qv);
-                ldc<NN>(A.idiag, k, dv);
-                ldc<NN>(A.x, k, xv);
-                ldc<NN>(A.r, k, rv);
+                for (int n = 0; n < NN; ++n) zero[n] = 0.0;
+                for (int k = k0; k < G.ncell; k += stride) {
+                    const Cell C = cell_of(G, k);
+                    double aEv[NN], wv[NN], uv[NN], rv[NN];
+                    ldc<NN>(A.aE, k, aEv);
+                    schur_cell<NN>(G, C, nu, aEv, A.iaF, wv, uv);
+                    ldc<NN>(A.r[0], k, rv);
+                    stc<NN>(A.w[0], k, wv);
+                    stc<NN>(A.s[1], k, zero);
+                    stc<NN>(A.p, k, zero);
 #pragma unroll
-                for (int n = 0; n < NN; ++n) {
-                    xv[n] = fma(alpha, pv[n], xv[n]);
-                    rv[n] = fma(-alpha, qv[n], rv[n]);
-                    zv[n] = rv[n] * dv[n];
-                    v2[0] += rv[n] * rv[n];
-                    v2[1] += rv[n] * zv[n];
+                    for (int n = 0; n < NN; ++n) {
+                        v3[0] += rv[n] * uv[n];
+                        v3[1] += wv[n] * uv[n];
+                        v3[2] += rv[n] * rv[n];
+                    }
                 }
-                stc<NN>(A.x, k, xv);
-                stc<NN>(A.r, k, rv);
-                stc<NN>(A.z, k, zv);
             }
-            block_partials<2>(v2, A.partC);
-            if (!grid_barrier(A.bar)) { done = DONE_TIMEOUT; break; }
-            grid_totals<2>(v2, A.partC);
-            ++iters;
-            if (sqrt(v2[0]) <= stop) { done = DONE_CONVERGED; break; }
-            if (iters >= A.max_pcg) { done = DONE_CAPPED; break; }
-            beta = v2[1] / rz;
-            rz = v2[1];
+            block_partials<3>(v3, A.partB);
+            if (!grid_barrier(A.bar, bar_target)) { status = LO_TIMEOUT; break; }
+            grid_totals<3>(v3, A.partB);
+            // conjugate gradients on S E = b from x = E, one reduction per
+            // iteration; iteration i reads r_i, w_i (buffers i % 2) and s_{i-1}
+            // (buffer (i + 1) % 2) and writes s_i, r_{i+1}, w_{i+1}
+            double gam = v3[0], del = v3[1], rr = v3[2], gam_old = 0.0, alpha_old = 0.0;
+            while (true) {
+                if (sqrt(rr) <= stop) { done = DONE_CONVERGED; break; }
+                if (iters >= A.max_pcg) { done = DONE_CAPPED; break; }
+                const double beta = iters == 0 ? 0.0 : gam / gam_old;
+                const double den = iters == 0 ? del : del - beta * gam / alpha_old;
+                if (!(den > 0.0) || !isfinite(den) || !isfinite(gam)) { done = DONE_BREAKDOWN; break; }
+                const double alpha = gam / den;
+                const int cur = iters & 1, nxt = cur ^ 1;
+                const NextU<NN, false> nu{A.r[cur], A.w[cur], A.s[nxt], A.idiag, alpha, beta};
+                double v[3] = {0.0, 0.0, 0.0};
+                for (int k = k0; k < G.ncell; k += stride) {
+                    const Cell C = cell_of(G, k);
+                    double rv[NN], wv[NN], sv[NN], pv[NN], xv[NN], dv[NN];
+                    ldc<NN>(A.r[cur], k, rv);
+                    ldc<NN>(A.w[cur], k, wv);
+                    ldc<NN>(A.s[nxt], k, sv);
+                    ldc<NN>(A.p, k, pv);
+                    ldc<NN>(A.idiag, k, dv);
+                    ldc<NN>(A.x, k, xv);
+#pragma unroll
+                    for (int n = 0; n < NN; ++n) {
+                        pv[n] = fma(beta, pv[n], rv[n] * dv[n]);
+                        sv[n] = fma(beta, sv[n], wv[n]);
+                        xv[n] = fma(alpha, pv[n], xv[n]);
+                        rv[n] = fma(-alpha, sv[n], rv[n]);
+                        // r.u and r.r of the new residual (u = r / diag(S), as
+                        // the matrix-vector product below forms it)
+                        v[0] += rv[n] * (rv[n] * dv[n]);
+                        v[2] += rv[n] * rv[n];
+                    }
+                    stc<NN>(A.p, k, pv);
+                    stc<NN>(A.x, k, xv);
+                    stc<NN>(A.s[cur], k, sv);
+                    stc<NN>(A.r[nxt], k, rv);
+                    double aEv[NN], wn[NN], un[NN];
+                    ldc<NN>(A.aE, k, aEv);
+                    schur_cell<NN>(G, C, nu, aEv, A.iaF, wn, un);
+                    stc<NN>(A.w[nxt], k, wn);
+#pragma unroll
+                    for (int n = 0; n < NN; ++n) v[1] += wn[n] * un[n];
+                }
+                double *part = cur ? A.partB : A.partC;
+                block_partials<3>(v, part);
+                if (!grid_barrier(A.bar, bar_target)) { done = DONE_TIMEOUT; break; }
+                grid_totals<3>(v, part);
+                ++iters;
+                gam_old = gam;
+                alpha_old = alpha;
+                gam = v[0];
+                del = v[1];
+                rr = v[2];
+            }
+        } else {
+            // textbook form (start x = E, p = u): buffers r = r[0], u = r[1],
+            // p = w[0] / w[1] by iteration parity, q = s[0]
+            double *const rb = A.r[0], *const ub = A.r[1], *const qb = A.s[0];
+            double rz = v0[2], beta = 0.0;
+            if (sqrt(v0[1]) <= stop) done = DONE_CONVERGED;
+            while (done == DONE_NO) {
+                const double *po = (iters & 1) ? A.w[1] : A.w[0];
+                double *pn = (iters & 1) ? A.w[0] : A.w[1];
+                double v1[1] = {0.0};
+                for (int k = k0; k < G.ncell; k += stride) {
+                    const Cell C = cell_of(G, k);
+                    double aEv[NN], qv[NN], pv[NN];
+                    ldc<NN>(A.aE, k, aEv);
+                    schur_cell<NN>(G, C, DirCG<NN>{ub, po, beta}, aEv, A.iaF, qv, pv);
+                    stc<NN>(pn, k, pv);
+                    stc<NN>(qb, k, qv);
+#pragma unroll
+                    for (int n = 0; n < NN; ++n) v1[0] += pv[n] * qv[n];
+                }
+                block_partials<1>(v1, A.partB);
+                if (!grid_barrier(A.bar, bar_target)) { done = DONE_TIMEOUT; break; }
+                grid_totals<1>(v1, A.partB);
+                if (!(v1[0] > 0.0) || !isfinite(v1[0]) || !isfinite(rz)) { done = DONE_BREAKDOWN; break; }
+                const double alpha = rz / v1[0];
+                double v2[2] = {0.0, 0.0};
+                for (int k = k0; k < G.ncell; k += stride) {
+                    double pv[NN], qv[NN], dv[NN], xv[NN], rv[NN], zv[NN];
+                    ldc<NN>(pn, k, pv);
+                    ldc<NN>(qb, k, qv);
+                    ldc<NN>(A.idiag, k, dv);
+                    ldc<NN>(A.x, k, xv);
+                    ldc<NN>(rb, k, rv);
+#pragma unroll
+                    for (int n = 0; n < NN; ++n) {
+                        xv[n] = fma(alpha, pv[n], xv[n]);
+                        rv[n] = fma(-alpha, qv[n], rv[n]);
+                        zv[n] = rv[n] * dv[n];
+                        v2[0] += rv[n] * rv[n];
+                        v2[1] += rv[n] * zv[n];
+                    }
+                    stc<NN>(A.x, k, xv);
+                    stc<NN>(rb, k, rv);
+                    stc<NN>(ub, k, zv);
+                }
+                block_partials<2>(v2, A.partC);
+                if (!grid_barrier(A.bar, bar_target)) { done = DONE_TIMEOUT; break; }
+                grid_totals<2>(v2, A.partC);
+                ++iters;
+                if (sqrt(v2[0]) <= stop) { done = DONE_CONVERGED; break; }
+                if (iters >= A.max_pcg) { done = DONE_CAPPED; break; }
+                beta = v2[1] / rz;
+                rz = v2[1];
+            }
         }
         if (done == DONE_TIMEOUT) { status = LO_TIMEOUT; break; }
         if (done == DONE_BREAKDOWN) { status = LO_BREAKDOWN; break; }
@@ -892,7 +1035,7 @@ __global__ void __launch_bounds__(BLOCK, 4) lo_newton_kernel(const NewtonArgs A)
         const int wmax = __reduce_max_sync(0xffffffffu, its_max);
         if ((threadIdx.x & 31) == 0 && wmax > 0) atomicMax(&A.sc->elim_max, wmax);
         block_partials<2>(v2, A.partD);
-        if (!grid_barrier(A.bar)) { status = LO_TIMEOUT; break; }
+        if (!grid_barrier(A.bar, bar_target)) { status = LO_TIMEOUT; break; }
         grid_totals<2>(v2, A.partD);
         const double dn = sqrt(v2[0]), un = sqrt(v2[1]);
         if (!isfinite(dn)) { status = LO_NONFINITE; break; }
@@ -941,7 +1084,8 @@ outer_change_kernel(int N, const double *__restrict__ T, const double *__restric
 struct sm_lo_state {
     int N = 0, D = 0, NN = 0, nblk_cell = 0, nblk_node = 0;
     double *buf = nullptr;  // every node array in one allocation
-    double *aE, *iaF, *bF, *ub, *idiag, *x, *r, *z, *pb[2], *q, *Estar, *Fstar, *Tstar, *Tin, *Ein;
+    double *aE, *iaF, *bF, *ub, *idiag, *x, *p, *r[2], *wv[2], *s[2], *Estar, *Fstar, *Tstar, *Tin,
+        *Ein;
     double *part = nullptr;
     double *jin2 = nullptr;     // [4] 2 |F_in| per side
     double *R0 = nullptr, *R1f = nullptr;  // consistent-method sources [node], [node][2]
@@ -952,12 +1096,18 @@ struct sm_lo_state {
     smk::lo::Scalars *sc = nullptr;
     smk::lo::Scalars *h_sc = nullptr;  // pinned mirror
     int coop_grid = 0;                 // blocks of the persistent PCG launch (0: not sized yet)
+    bool single_reduction = false;     // conjugate-gradient form of that launch
 };
 
 namespace {
 
 using smk::lo::BLOCK;
 using smk::lo::Geo;
+
+// doubles of the per-block partial-sum buffer: the cooperative kernel's four
+// reduction buffers (3 + 3 + 3 + 2 values per block); the outer iteration's
+// change norms use the first 2
+constexpr size_t PART_PER_BLOCK = 11;
 
 sm_status lo_fail(sm_status s, const std::string &m) {
     smk::set_last_error(m.c_str());
@@ -1019,7 +1169,7 @@ sm_status lo_ensure(sm_problem *p) {
     w.NN = p->nn;
     w.nblk_cell = (p->ncell + BLOCK - 1) / BLOCK;
     w.nblk_node = (N + BLOCK - 1) / BLOCK;
-    const size_t nS = 13, nV = 3;  // node arrays and [node][dim] arrays
+    const size_t nS = 15, nV = 3;  // node arrays and [node][dim] arrays
     const size_t buf_elems = (size_t)N * nS + (size_t)N * D * nV;
     LO_CUDA(cudaMalloc(&w.buf, sizeof(double) * buf_elems));
     double *b = w.buf;
@@ -1035,17 +1185,18 @@ sm_status lo_ensure(sm_problem *p) {
     w.iaF = take(N);
     w.idiag = take(N);
     w.x = take(N);
-    w.r = take(N);
-    w.z = take(N);
-    w.pb[0] = take(N);
-    w.pb[1] = take(N);
-    w.q = take(N);
+    w.p = take(N);
+    for (int i = 0; i < 2; ++i) {
+        w.r[i] = take(N);
+        w.wv[i] = take(N);
+        w.s[i] = take(N);
+    }
     w.Estar = take(N);
     w.Tstar = take(N);
     w.Tin = take(N);
     w.Ein = take(N);
     const size_t nblk = (size_t)std::max(w.nblk_cell, w.nblk_node);
-    LO_CUDA(cudaMalloc(&w.part, sizeof(double) * 8 * nblk));
+    LO_CUDA(cudaMalloc(&w.part, sizeof(double) * PART_PER_BLOCK * nblk));
     LO_CUDA(cudaMalloc(&w.jin2, sizeof(double) * 4));
     {  // consistent method: R0 [N], R1f [N][dim], quadrant moments, inflow moments
         LO_CUDA(cudaMalloc(&w.R0, sizeof(double) * (size_t)N * 3));
@@ -1060,7 +1211,8 @@ sm_status lo_ensure(sm_problem *p) {
     LO_CUDA(cudaMalloc(&w.sc, sizeof(smk::lo::Scalars)));
     LO_CUDA(cudaMemset(w.sc, 0, sizeof(smk::lo::Scalars)));
     LO_CUDA(cudaMallocHost(&w.h_sc, sizeof(smk::lo::Scalars)));
-    p->workspace_bytes += sizeof(double) * (buf_elems + 3 * nblk + 4 + (size_t)p->G * p->ncell +
+    p->workspace_bytes += sizeof(double) * (buf_elems + PART_PER_BLOCK * nblk + 4 +
+                                            (size_t)p->G * p->ncell +
                                             (size_t)N * p->nc) +
                           sizeof(smk::lo::Scalars);
     // 2 |F_in| per side: 2 sum_{Omega.n<0} w |Omega.n| I_in with the gray
@@ -1127,12 +1279,20 @@ template <int NN>
 sm_status launch_newton(sm_problem *p, sm_lo_state &w, const Geo &G, const double *clo,
                         double *T, double *E, double *F, const double *Tstar, const double *cv,
                         const double *R0, const sm_step_params &prm) {
-    const void *k = (const void *)smk::lo::lo_newton_kernel<NN>;
     if (w.coop_grid == 0) {
         int dev = 0, nsm = 0, per_sm = 0;
         LO_CUDA(cudaGetDevice(&dev));
         LO_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        LO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BLOCK, 0));
+        // the single-reduction form while the cells come to at most 1.5 warps
+        // per SM sub-partition (4 per SM): measured on GB300, it saves 3 % of
+        // a 128^2 gray step and 9 % of the 64-cell slab, and costs 3 % on
+        // 256^2 meshes (3.4 warps per sub-partition), where the extra FP64
+        // work of forming the neighbours' u outweighs the saved barrier
+        const long long warps = ((long long)p->ncell + 31) / 32;
+        w.single_reduction = 2 * warps <= 3LL * 4 * nsm;
+        const void *k0 = w.single_reduction ? (const void *)smk::lo::lo_newton_kernel<NN, true>
+                                            : (const void *)smk::lo::lo_newton_kernel<NN, false>;
+        LO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k0, BLOCK, 0));
         if (per_sm < 1) return lo_fail(SM_ERR_CUDA, "the low-order kernel does not fit on an SM");
         w.coop_grid = std::min(w.nblk_cell, per_sm * nsm);
     }
@@ -1157,15 +1317,19 @@ sm_status launch_newton(sm_problem *p, sm_lo_state &w, const Geo &G, const doubl
     A.aE = w.aE;
     A.idiag = w.idiag;
     A.x = w.x;
-    A.r = w.r;
-    A.z = w.z;
-    A.pb0 = w.pb[0];
-    A.pb1 = w.pb[1];
-    A.q = w.q;
+    A.p = w.p;
+    for (int i = 0; i < 2; ++i) {
+        A.r[i] = w.r[i];
+        A.w[i] = w.wv[i];
+        A.s[i] = w.s[i];
+    }
+    // per-block partial sums of the kernel's reductions: A, B, C (up to 3
+    // values each), D (2), disjoint
     A.partA = w.part;
     A.partB = w.part + 3 * nblk;
-    A.partC = w.part + 4 * nblk;
-    A.partD = w.part + 6 * nblk;
+    A.partC = w.part + 6 * nblk;
+    A.partD = w.part + 9 * nblk;
+    static_assert(PART_PER_BLOCK >= 11, "room for the partial sums A, B, C, D");
     A.pcg_rtol = prm.pcg_rtol;
     A.eps_inner = prm.eps_inner;
     A.elim_rtol = prm.elim_rtol;
@@ -1175,11 +1339,12 @@ sm_status launch_newton(sm_problem *p, sm_lo_state &w, const Geo &G, const doubl
     A.max_elim = prm.max_elim;
     A.sc = w.sc;
     A.bar.count = &w.sc->bar_count;
-    A.bar.gen = &w.sc->bar_gen;
     A.bar.nblocks = (unsigned)w.coop_grid;
     A.bar.limit_ns = p->timeout_ns;
     A.withhold = p->fault_withhold_block;
     void *args[] = {&A};
+    const void *k = w.single_reduction ? (const void *)smk::lo::lo_newton_kernel<NN, true>
+                                       : (const void *)smk::lo::lo_newton_kernel<NN, false>;
     LO_CUDA(cudaLaunchCooperativeKernel(k, dim3(w.coop_grid), dim3(BLOCK), args, 0, p->stream));
     return SM_OK;
 }
