@@ -29,6 +29,20 @@ sm_status sm_debug_skip_publish(sm_problem *p, int enable);
  * time limit; the solve returns SM_ERR_TIMEOUT and the problem stays usable. */
 sm_status sm_debug_withhold_lo_block(sm_problem *p, int enable);
 
+/* Form of the conjugate gradients in the low-order solves of this problem:
+ * SM_DEBUG_PCG_AUTO (the library's choice: the single-reduction form while the
+ * mesh has at most 1.5 warps of cells per SM sub-partition, else the textbook
+ * form), SM_DEBUG_PCG_TEXTBOOK (two grid reductions per iteration) or
+ * SM_DEBUG_PCG_SINGLE (Chronopoulos-Gear, one reduction per iteration).  The
+ * forms compute the same iterates up to rounding.  INVALID_ARG for other
+ * values. */
+enum { SM_DEBUG_PCG_AUTO = 0, SM_DEBUG_PCG_TEXTBOOK = 1, SM_DEBUG_PCG_SINGLE = 2 };
+sm_status sm_debug_set_pcg_form(sm_problem *p, int form);
+
+/* The form (SM_DEBUG_PCG_TEXTBOOK or SM_DEBUG_PCG_SINGLE) that the problem's
+ * last low-order solve used, or SM_DEBUG_PCG_AUTO if it has run none. */
+sm_status sm_debug_get_pcg_form(const sm_problem *p, int *form);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,7 @@ EXPORTED = ["sm_create_problem", "sm_destroy_problem", "sm_get_info", "sm_set_st
             "sm_synchronize", "sm_autotune", "sm_set_profiling", "sm_get_kernel_times",
             "sm_launch_count", "sm_last_error", "sm_status_string",
             "sm_debug_set_wait_limit_ns", "sm_debug_skip_publish", "sm_debug_withhold_lo_block",
+            "sm_debug_set_pcg_form", "sm_debug_get_pcg_form",
             "sm_sweep_static",
             "sm_default_step_params", "sm_loworder_newton", "sm_step",
             "sm_create_batch", "sm_destroy_batch", "sm_batch_problem", "sm_batch_get_info",
@@ -141,6 +142,8 @@ def load():
         "sm_debug_set_wait_limit_ns": [P, ctypes.c_longlong],
         "sm_debug_skip_publish": [P, I],
         "sm_debug_withhold_lo_block": [P, I],
+        "sm_debug_set_pcg_form": [P, I],
+        "sm_debug_get_pcg_form": [P, ctypes.POINTER(ctypes.c_int)],
         "sm_sweep_static": [ctypes.POINTER(ProblemDesc), P, P, P, P, P, P, P],
         "sm_loworder_newton": [P, P, P, P, P, P, P, P, ctypes.POINTER(StepParams),
                                ctypes.POINTER(StepStats)],
@@ -444,6 +447,18 @@ class Problem:
 
     def debug_withhold_lo_block(self, on: bool):
         _check(load().sm_debug_withhold_lo_block(self._h, 1 if on else 0))
+
+    #: conjugate-gradient forms of the low-order solve (sm_debug.h)
+    PCG_FORMS = {"auto": 0, "textbook": 1, "single": 2}
+
+    def debug_set_pcg_form(self, form: str):
+        _check(load().sm_debug_set_pcg_form(self._h, self.PCG_FORMS[form]))
+
+    def debug_pcg_form(self) -> str:
+        """The form the last low-order solve used ("auto": none yet)."""
+        v = ctypes.c_int()
+        _check(load().sm_debug_get_pcg_form(self._h, ctypes.byref(v)))
+        return {v_: k for k, v_ in self.PCG_FORMS.items()}[v.value]
 
 
 def _desc_of(cfg, precision: int, keep):

@@ -830,6 +830,20 @@ sm_status sm_debug_withhold_lo_block(sm_problem *p, int enable) {
     return SM_OK;
 }
 
+sm_status sm_debug_set_pcg_form(sm_problem *p, int form) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    if (form != SM_DEBUG_PCG_AUTO && form != SM_DEBUG_PCG_TEXTBOOK && form != SM_DEBUG_PCG_SINGLE)
+        return fail(SM_ERR_INVALID_ARG, "form must be SM_DEBUG_PCG_AUTO, _TEXTBOOK or _SINGLE");
+    p->lo_pcg_form = form;
+    return SM_OK;
+}
+
+sm_status sm_debug_get_pcg_form(const sm_problem *p, int *form) {
+    if (!p || !form) return fail(SM_ERR_INVALID_ARG, "NULL problem or output");
+    *form = p->lo_pcg_form_used;
+    return SM_OK;
+}
+
 }  // extern "C"
 
 namespace smk {

@@ -165,6 +165,8 @@ struct sm_problem {
     long long timeout_ns = 2000000000LL;
     int fault_skip_publish = 0;
     int fault_withhold_block = 0;  // test hook: a low-order block skips its barriers
+    int lo_pcg_form = 0;           // test hook: SM_DEBUG_PCG_* (0: the library's choice)
+    int lo_pcg_form_used = 0;      // form of the last low-order solve (0: none yet)
     cudaStream_t stream = nullptr;
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;  // 4 events per timed sweep, read back lazily

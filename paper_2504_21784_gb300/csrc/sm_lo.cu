@@ -1095,8 +1095,8 @@ struct sm_lo_state {
     double *clo = nullptr;      // closures when the caller passes none
     smk::lo::Scalars *sc = nullptr;
     smk::lo::Scalars *h_sc = nullptr;  // pinned mirror
-    int coop_grid = 0;                 // blocks of the persistent PCG launch (0: not sized yet)
-    bool single_reduction = false;     // conjugate-gradient form of that launch
+    int coop_grid[2] = {0, 0};  // blocks of the cooperative launch per PCG form (0: not sized)
+    int nsm = 0;                // SMs of the device (0: not queried yet)
 };
 
 namespace {
@@ -1279,22 +1279,28 @@ template <int NN>
 sm_status launch_newton(sm_problem *p, sm_lo_state &w, const Geo &G, const double *clo,
                         double *T, double *E, double *F, const double *Tstar, const double *cv,
                         const double *R0, const sm_step_params &prm) {
-    if (w.coop_grid == 0) {
-        int dev = 0, nsm = 0, per_sm = 0;
+    if (w.nsm == 0) {
+        int dev = 0;
         LO_CUDA(cudaGetDevice(&dev));
-        LO_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        // the single-reduction form while the cells come to at most 1.5 warps
-        // per SM sub-partition (4 per SM): measured on GB300, it saves 3 % of
-        // a 128^2 gray step and 9 % of the 64-cell slab, and costs 3 % on
-        // 256^2 meshes (3.4 warps per sub-partition), where the extra FP64
-        // work of forming the neighbours' u outweighs the saved barrier
-        const long long warps = ((long long)p->ncell + 31) / 32;
-        w.single_reduction = 2 * warps <= 3LL * 4 * nsm;
-        const void *k0 = w.single_reduction ? (const void *)smk::lo::lo_newton_kernel<NN, true>
-                                            : (const void *)smk::lo::lo_newton_kernel<NN, false>;
-        LO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k0, BLOCK, 0));
+        LO_CUDA(cudaDeviceGetAttribute(&w.nsm, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int nsm = w.nsm;
+    // the single-reduction form while the cells come to at most 1.5 warps per
+    // SM sub-partition (4 per SM): measured on GB300, it saves 3 % of a 128^2
+    // gray step and 9 % of the 64-cell slab, and costs 3 % on 256^2 meshes
+    // (3.4 warps per sub-partition), where the extra FP64 work of forming the
+    // neighbours' u outweighs the saved barrier
+    const long long warps = ((long long)p->ncell + 31) / 32;
+    const bool single = p->lo_pcg_form == SM_DEBUG_PCG_AUTO ? 2 * warps <= 3LL * 4 * nsm
+                                                             : p->lo_pcg_form == SM_DEBUG_PCG_SINGLE;
+    const void *k = single ? (const void *)smk::lo::lo_newton_kernel<NN, true>
+                           : (const void *)smk::lo::lo_newton_kernel<NN, false>;
+    int &grid = w.coop_grid[single ? 1 : 0];
+    if (grid == 0) {
+        int per_sm = 0;
+        LO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BLOCK, 0));
         if (per_sm < 1) return lo_fail(SM_ERR_CUDA, "the low-order kernel does not fit on an SM");
-        w.coop_grid = std::min(w.nblk_cell, per_sm * nsm);
+        grid = std::min(w.nblk_cell, per_sm * nsm);
     }
     const size_t nblk = (size_t)std::max(w.nblk_cell, w.nblk_node);
     smk::lo::NewtonArgs A;
@@ -1339,13 +1345,12 @@ sm_status launch_newton(sm_problem *p, sm_lo_state &w, const Geo &G, const doubl
     A.max_elim = prm.max_elim;
     A.sc = w.sc;
     A.bar.count = &w.sc->bar_count;
-    A.bar.nblocks = (unsigned)w.coop_grid;
+    A.bar.nblocks = (unsigned)grid;
     A.bar.limit_ns = p->timeout_ns;
     A.withhold = p->fault_withhold_block;
     void *args[] = {&A};
-    const void *k = w.single_reduction ? (const void *)smk::lo::lo_newton_kernel<NN, true>
-                                       : (const void *)smk::lo::lo_newton_kernel<NN, false>;
-    LO_CUDA(cudaLaunchCooperativeKernel(k, dim3(w.coop_grid), dim3(BLOCK), args, 0, p->stream));
+    LO_CUDA(cudaLaunchCooperativeKernel(k, dim3(grid), dim3(BLOCK), args, 0, p->stream));
+    p->lo_pcg_form_used = single ? SM_DEBUG_PCG_SINGLE : SM_DEBUG_PCG_TEXTBOOK;
     return SM_OK;
 }
 

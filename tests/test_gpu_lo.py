@@ -10,6 +10,11 @@ solution differs from the direct solve by at most ~1e-11 relative, measured
 per field (T, E against their largest value; F against c times the largest
 E, since F vanishes near equilibrium).  A full step with the FP32 sweep
 inherits the sweep's 1e-6-level rounding through the closures: 1e-5.
+
+The library has two forms of the conjugate gradients (two grid reductions per
+iteration, or the single-reduction form of Chronopoulos and Gear) and picks
+one by mesh size; the oracle comparisons run both, forced through the
+sm_debug_set_pcg_form test hook.
 """
 import math
 
@@ -62,9 +67,10 @@ def _lo_inputs(cfg, seed):
     return m, clo, T, cv, mom_k, alpha, jin2
 
 
-def _gpu_lo(sm, cfg, clo, Tstar, cv, mom_k, T0, E0, **prm):
+def _gpu_lo(sm, cfg, clo, Tstar, cv, mom_k, T0, E0, form="auto", **prm):
     import torch
     prob = sm.Problem.from_config(cfg, 64)
+    prob.debug_set_pcg_form(form)
     cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     T = cu(T0.copy())
     E = cu(E0.copy())
@@ -82,8 +88,14 @@ LO_CASES = {
 }
 
 
+# both forms of the conjugate gradients (textbook: two grid reductions per
+# iteration; single: Chronopoulos-Gear, one), forced through the test hook
+PCG_FORMS = ("textbook", "single")
+
+
+@pytest.mark.parametrize("form", PCG_FORMS)
 @pytest.mark.parametrize("name", list(LO_CASES))
-def test_loworder_newton_matches_oracle(gpu_lib, name):
+def test_loworder_newton_matches_oracle(gpu_lib, name, form):
     dim, nx, ny = LO_CASES[name]
     cfg = _cfg(dim, nx, ny)
     m, clo, T, cv, mom_k, alpha, jin2 = _lo_inputs(cfg, seed=11 + nx)
@@ -93,14 +105,40 @@ def test_loworder_newton_matches_oracle(gpu_lib, name):
     prm = L.LOParams(eps_inner=1e-13, max_inner=40, elim_rtol=1e-15, max_elim=80)
     Tr, Er, Fr, st_r = L.lo_newton(m, ops, cfg.c, cfg.a, cfg.dt, alpha, clo, T, cv, Estar, Fstar,
                                    jin2, T, Estar, prm)
-    Tg, Eg, Fg, st_g, _ = _gpu_lo(gpu_lib, cfg, clo, T, cv, mom_k, T, Estar, eps_inner=1e-13,
-                                  max_inner=40, pcg_rtol=1e-15, elim_rtol=1e-15, max_elim=80)
+    Tg, Eg, Fg, st_g, prob = _gpu_lo(gpu_lib, cfg, clo, T, cv, mom_k, T, Estar, form=form,
+                                     eps_inner=1e-13, max_inner=40, pcg_rtol=1e-15,
+                                     elim_rtol=1e-15, max_elim=80)
+    assert prob.debug_pcg_form() == form
     eT, eE = _field(Tg, Tr), _field(Eg, Er)
     eF = _field(Fg, Fr, scale=cfg.c * Er)
-    print(f"{name}: T {eT:.2e} E {eE:.2e} F {eF:.2e} newton {st_g['newton_iters_total']} "
+    print(f"{name} {form}: T {eT:.2e} E {eE:.2e} F {eF:.2e} newton {st_g['newton_iters_total']} "
           f"(oracle {st_r['newton']}) pcg max {st_g['pcg_iters_max']}")
     assert eT < TOL_LO and eE < TOL_LO and eF < TOL_LO
     assert st_g["pcg_capped"] == 0
+
+
+def test_pcg_forms_agree_on_a_large_mesh(gpu_lib):
+    """200x200 cells (1250 warps of cells, above the single-reduction form's
+    1.5 warps per SM sub-partition on 152 SMs): the library's choice is the
+    textbook form, a small mesh gets the single-reduction form, and the two
+    forms give the same solve to the accuracy of the linear solves."""
+    cfg = _cfg(2, 200, 200)
+    m, clo, T, cv, mom_k, alpha, jin2 = _lo_inputs(cfg, seed=17)
+    Estar = mom_k[..., 0] / cfg.c
+    kw = dict(eps_inner=1e-13, max_inner=40, pcg_rtol=1e-14, elim_rtol=1e-15, max_elim=80)
+    Ta, Ea, Fa, sa, pa = _gpu_lo(gpu_lib, cfg, clo, T, cv, mom_k, T, Estar, **kw)
+    Tb, Eb, Fb, sb, pb = _gpu_lo(gpu_lib, cfg, clo, T, cv, mom_k, T, Estar, form="single", **kw)
+    assert pa.debug_pcg_form() == "textbook" and pb.debug_pcg_form() == "single"
+    eT, eE = _field(Tb, Ta), _field(Eb, Ea)
+    eF = _field(Fb, Fa, scale=cfg.c * Ea)
+    print(f"forms: T {eT:.2e} E {eE:.2e} F {eF:.2e} pcg {sa['pcg_iters_total']} / "
+          f"{sb['pcg_iters_total']} newton {sa['newton_iters_total']} / {sb['newton_iters_total']}")
+    assert eT < TOL_LO and eE < TOL_LO and eF < TOL_LO
+    assert sa["newton_iters_total"] == sb["newton_iters_total"]
+    small = _cfg(2, 7, 5)
+    m, clo, T, cv, mom_k, alpha, jin2 = _lo_inputs(small, seed=18)
+    *_, ps = _gpu_lo(gpu_lib, small, clo, T, cv, mom_k, T, mom_k[..., 0] / small.c)
+    assert ps.debug_pcg_form() == "single"
 
 
 def test_loworder_default_tolerances_match_oracle(gpu_lib):
@@ -241,8 +279,9 @@ STEP_CASES = {
 }
 
 
+@pytest.mark.parametrize("form", PCG_FORMS)
 @pytest.mark.parametrize("name", list(STEP_CASES))
-def test_step_matches_oracle(gpu_lib, name):
+def test_step_matches_oracle(gpu_lib, name, form):
     """A fixed number of outer iterations of Algorithm 1 on both sides."""
     import torch
     sm = gpu_lib
@@ -250,6 +289,7 @@ def test_step_matches_oracle(gpu_lib, name):
     kind = W.OPACITY_POWER if G == 1 else W.OPACITY_LARSEN
     cfg = _cfg(dim, nx, ny, G=G, kind=kind, T_bdr=(1.0, 0.2, 0.6, 0.0))
     prob = sm.Problem.from_config(cfg, precision)
+    prob.debug_set_pcg_form(form)
     ncell, nn = cfg.n_cells, cfg.n_nodes
     rng = np.random.default_rng(5 + nx)
     Tk = W.temperature_random(ncell, nn, seed=3 + nx, lo=0.1, hi=0.8)
