@@ -82,3 +82,28 @@ def test_invalid_descriptors_rejected_before_cuda(lib):
     rc, _ = create(dim=1, n_polar=5)
     assert rc == 1
     assert so.sm_status_string(6) == b"SM_ERR_TIMEOUT"
+
+
+def test_null_handles_rejected_before_cuda(lib):
+    """Entry points that take a problem or batch handle return
+    SM_ERR_INVALID_ARG with a message for a NULL handle, before any CUDA call
+    (so this runs without a GPU)."""
+    import paper_2504_21784_gb300 as sm
+    so = sm.load()
+    out = ctypes.c_int()
+    calls = {
+        "sm_synchronize": lambda: so.sm_synchronize(None),
+        "sm_set_profiling": lambda: so.sm_set_profiling(None, 1),
+        "sm_debug_set_wait_limit_ns": lambda: so.sm_debug_set_wait_limit_ns(None, 1000),
+        "sm_debug_skip_publish": lambda: so.sm_debug_skip_publish(None, 1),
+        "sm_debug_withhold_lo_block": lambda: so.sm_debug_withhold_lo_block(None, 1),
+        "sm_debug_set_pcg_form": lambda: so.sm_debug_set_pcg_form(None, 1),
+        "sm_debug_get_pcg_form": lambda: so.sm_debug_get_pcg_form(None, ctypes.byref(out)),
+        "sm_batch_synchronize": lambda: so.sm_batch_synchronize(None),
+    }
+    for name, call in calls.items():
+        rc = call()
+        assert rc == 1, (name, rc)
+        assert so.sm_last_error(), name
+    # the destructors accept NULL as a no-op (include/sm.h)
+    assert so.sm_destroy_problem(None) == 0 and so.sm_destroy_batch(None) == 0
