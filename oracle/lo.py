@@ -13,8 +13,12 @@ Follows:
 * the semi-implicit backward Euler system (Eq. smm_be) with the HO time-edge
   sources E*, F* (Sec. 6.1, time-edge choice);
 * the Newton iteration with frozen gray opacities and nonlinear temperature
-  elimination (Sec. 5, Eqs. absem, nonlinear_T_update), here solving the full
-  linearised block system directly (no Schur complement, no Krylov method);
+  elimination (Sec. 5, Eqs. absem, nonlinear_T_update), each linearised block
+  system solved by a sparse direct method (no Krylov method): A_FF is
+  diagonal under lumping, so F is eliminated exactly and the Schur complement
+  of Eq. schur is factorised by sparse LU; the whole block system can be
+  solved directly instead (``LOParams.linear = "block"``), which a pin checks
+  gives the same solution;
 * Algorithm 1 with the stopping rule Eq. relative_tol.
 All forms are lumped with the 2-point Gauss-Lobatto rule (Sec. 6).
 
@@ -37,7 +41,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from . import (closures, emission, group_spectra, inflow, moments, opacity, quadrature, sweep,
-               alpha as quad_alpha)
+               sweep_pairs, alpha as quad_alpha)
 
 
 # --------------------------------------------------------------------------- mesh helpers
@@ -182,14 +186,16 @@ def closure_sources(m: Mesh, clo: np.ndarray, face_term: bool = True):
     r = np.zeros(N * D)
     # int v . sum_g (sigma_F - sigma_g) F_g   (lumped)
     r += (mass * Ccorr).reshape(-1)
-    # int grad_h v : T  = sum_q m (grad u_i)_l T_{d l}
-    for k in range(m.ncell):
-        base = k * m.nn
-        for i in range(m.nn):
-            for q in range(m.nn):
-                g = grad_at_corner(m, i, q)
-                for d in range(D):
-                    r[(base + i) * D + d] += mass * sum(g[l] * Tten[base + q, d, l] for l in range(D))
+    # int grad_h v : T  = sum_q m (grad u_i)_l T_{d l}, for every cell at once
+    rc = r.reshape(m.ncell, m.nn, D)
+    Tc = Tten.reshape(m.ncell, m.nn, D, D)
+    for i in range(m.nn):
+        for q in range(m.nn):
+            g = grad_at_corner(m, i, q)
+            for d in range(D):
+                for l in range(D):
+                    if g[l] != 0.0:
+                        rc[:, i, d] += mass * g[l] * Tc[:, q, d, l]
     # - int_Gamma0 [v] . {T n}
     for kind, n, wf, pairs in faces(m):
         if kind != "int" or not face_term:
@@ -230,6 +236,7 @@ class LOParams:
     elim_rtol: float = 1e-10
     max_elim: int = 40
     T_floor: float = 1e-8
+    linear: str = "schur"      # "schur" (F eliminated, Eq. schur) or "block"
 
 
 def eliminate_T(T0, a, c, cv_dt, sigP, sigE, E, Tstar, rtol, maxit, T_floor):
@@ -292,9 +299,18 @@ def lo_newton(m: Mesh, ops, c, a, dt, alpha, clo, T_k, cv, Estar, Fstar, jin2, T
         qT0 = cv_dt * (Tk - T) - sP * B0
         AEE = P + sp.diags(mass * c * (sEt - nu * sE))
         bE = mass * (sP * B0 + nu * qT0 + Estar.reshape(-1) / dt) + bnd
-        K = sp.bmat([[AFF, AFE], [AEF, AEE]], format="csc")
-        sol = spla.spsolve(K, np.concatenate([bF, bE]))
-        F, E = sol[:N * D], sol[N * D:]
+        if prm.linear == "block":
+            K = sp.bmat([[AFF, AFE], [AEF, AEE]], format="csc")
+            sol = spla.spsolve(K, np.concatenate([bF, bE]))
+            F, E = sol[:N * D], sol[N * D:]
+        else:
+            # A_FF F + A_FE E = b_F with A_FF diagonal: F = A_FF^{-1}(b_F - A_FE E);
+            # then S E = b_E - A_EF A_FF^{-1} b_F with S = A_EE - A_EF A_FF^{-1} A_FE
+            # (Eq. schur), factorised by sparse LU in a symmetric fill-reducing order
+            affi = 1.0 / AFF.diagonal()
+            S = (AEE - AEF @ sp.diags(affi) @ AFE).tocsc()
+            E = spla.spsolve(S, bE - AEF @ (affi * bF), permc_spec="MMD_AT_PLUS_A")
+            F = affi * (bF - AFE @ E)
         T, ite = eliminate_T(T, a, c, cv_dt, sP, sE, E, Tk, prm.elim_rtol, prm.max_elim,
                              prm.T_floor)
         stats["elim_max"] = max(stats["elim_max"], ite)
@@ -341,21 +357,56 @@ def equilibrium_intensity(cfg, T0, omx):
     return I
 
 
+_OPS_CACHE: dict = {}
+
+
+def cached_operators(m: Mesh, c: float, alpha: float):
+    """lo_operators of a mesh, assembled once and kept for the next steps (they
+    depend on the geometry, c and alpha only)."""
+    key = (m.dim, m.nx, m.ny, m.hx, m.hy, float(c), float(alpha))
+    if key not in _OPS_CACHE:
+        if len(_OPS_CACHE) >= 2:
+            _OPS_CACHE.clear()
+        _OPS_CACHE[key] = lo_operators(m, c, alpha)
+    return _OPS_CACHE[key]
+
+
 def sm_step(cfg, scale, cv, T_k, I_k, mom_k, prm: StepParams):
     """One time step of Algorithm 1 (semi-implicit backward Euler, Eq. smm_be).
-    T_k [cell][node], I_k [d][g][cell][node], mom_k = HO moments of I_k.
+    T_k [cell][node], mom_k = HO moments of I_k.  I_k is [d][g][cell][node], or
+    a function of d returning direction d's [g][cell][node] intensity: then each
+    sweep runs one direction (all its groups) at a time and sums the moments
+    direction by direction (they are linear in I), so that the whole intensity
+    is never held; the returned I is then None (independent method only).
     Returns (T, E, F, I, mom, stats)."""
     m = make_mesh(cfg.dim, cfg.nx, cfg.ny, cfg.extent)
     omx, omy, w = quadrature(cfg.dim, cfg.n_polar, cfg.n_azim)
     alpha = quad_alpha(omx, w)
     c, a, dt = cfg.c, cfg.a, cfg.dt
     inv_cdt = 1.0 / (c * dt)
-    ops = lo_operators(m, c, alpha)
+    ops = cached_operators(m, c, alpha)
     infl = inflow(cfg.edges, a, c, cfg.T_bdr)
     I_in_side = infl.sum(axis=1)
     jin2 = boundary_partial_currents(cfg.dim, omx, omy, w, I_in_side)
     sigma = opacity(cfg.opacity_kind, cfg.opacity_alpha, cfg.edges, T_k, scale)  # sigma_g(T^k)
     D = cfg.dim
+    G = sigma.shape[0]
+    streamed = callable(I_k)
+    if streamed and prm.method != "independent":
+        raise ValueError("the direction-streamed step supports the independent method only")
+
+    def high_order(T):
+        q = emission(cfg.edges, a, c, T, sigma)
+        if not streamed:
+            I = sweep(cfg.dim, cfg.nx, cfg.ny, cfg.extent, omx, omy, sigma, inv_cdt, q, I_k, infl)
+            return I, moments(cfg.dim, omx, omy, w, sigma, I)
+        mom = np.zeros_like(mom_k)
+        for d in range(len(omx)):
+            I_d = sweep_pairs(cfg.dim, cfg.nx, cfg.ny, cfg.extent, omx, omy, sigma, inv_cdt, q,
+                              I_k(d), infl, [(d, g) for g in range(G)])
+            mom += moments(cfg.dim, omx[d:d + 1], omy[d:d + 1], w[d:d + 1], sigma, I_d[None])
+        return None, mom
+
     Estar = mom_k[..., 0] / c                      # HO time-edge sources (Sec. 6.1)
     Fstar = mom_k[..., 1:1 + D]
     T, E = T_k.copy(), Estar.copy()
@@ -363,9 +414,7 @@ def sm_step(cfg, scale, cv, T_k, I_k, mom_k, prm: StepParams):
     d1 = None
     stats = {"outer": 0, "newton": [], "elim_max": 0}
     for it in range(1, prm.max_outer + 1):
-        q = emission(cfg.edges, a, c, T, sigma)
-        I = sweep(cfg.dim, cfg.nx, cfg.ny, cfg.extent, omx, omy, sigma, inv_cdt, q, I_k, infl)
-        mom = moments(cfg.dim, omx, omy, w, sigma, I)
+        I, mom = high_order(T)
         clo = closures(cfg.dim, cfg.edges, c, sigma, T, mom)
         R1 = bnd = None
         if prm.method == "consistent":

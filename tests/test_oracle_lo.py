@@ -150,3 +150,23 @@ def test_step_reproduces_infinite_medium(dim):
     assert np.max(np.abs(E - Eans)) < 1e-12 * Eans
     assert np.max(np.abs(mom[..., 0] / c - Eans)) < 1e-11 * Eans
     assert np.max(np.abs(F)) < 1e-11 * c * Eans
+
+
+@pytest.mark.parametrize("dim,nx,ny", [(1, 12, 1), (2, 5, 4)])
+def test_schur_solve_equals_block_solve(dim, nx, ny):
+    """Eliminating the diagonal A_FF exactly and solving the Schur complement
+    (Eq. schur) gives the solution of the whole linearised block system."""
+    cfg, m, clo, T, cv, mom_k, alpha, jin2 = _lo_case(dim, nx, ny, seed=11)
+    ops = L.lo_operators(m, 1.0, alpha)
+    Estar = mom_k[..., 0]
+    Fstar = mom_k[..., 1:1 + dim]
+    out = {}
+    for linear in ("schur", "block"):
+        prm = L.LOParams(eps_inner=1e-14, max_inner=30, elim_rtol=1e-15, max_elim=60,
+                         linear=linear)
+        out[linear] = L.lo_newton(m, ops, 1.0, 1.0, cfg.dt, alpha, clo, T, cv, Estar, Fstar,
+                                  jin2, T, Estar, prm)
+    (Ts, Es, Fs, _), (Tb, Eb, Fb, _) = out["schur"], out["block"]
+    assert np.max(np.abs(Ts - Tb)) < 1e-13 * np.abs(Tb).max()
+    assert np.max(np.abs(Es - Eb)) < 1e-13 * np.abs(Eb).max()
+    assert np.max(np.abs(Fs - Fb)) < 1e-12 * np.abs(Eb).max()
