@@ -341,12 +341,18 @@ sm_status sm_get_kernel_times(sm_problem *p, double *ms_host, int *count_host);
  * 32x32 cells x 32 directions x 8 groups in FP32 fits).
  *
  * The first call on a device (with that device current) looks up the
- * array's device address with cudaGetSymbolAddress; make it before any
- * stream capture.  The call is synchronous on stream (a cudaStream_t, NULL
- * for the legacy default stream) and returns SM_ERR_TIMEOUT or
- * SM_ERR_NONPHYSICAL like sm_synchronize.  All calls share the one array,
- * which keeps the previous call's contents (the parts that must start at
- * zero are cleared by each call): calls that overlap on the GPU race. */
+ * array's device address with cudaGetSymbolAddress, and the first call in
+ * the process uploads the Planck tables (synchronous copies); make it before
+ * any stream capture.  The call waits for its own stream only (a
+ * cudaStream_t, NULL for the legacy default stream): the device status is
+ * read by an asynchronous copy on that stream, then that stream is
+ * synchronized; it returns SM_ERR_TIMEOUT or SM_ERR_NONPHYSICAL like
+ * sm_synchronize.  It uses about 40 KB of the calling thread's stack.  All
+ * calls share the one array, which keeps the previous call's contents (the
+ * parts that must start at zero are cleared by each call): calls that
+ * overlap on the GPU race.  Descriptor errors are those of
+ * sm_create_problem, plus dim != 2, n_groups > 256 and n_polar * n_azim
+ * > 128 (each factor is checked before the product). */
 sm_status sm_sweep_static(const sm_problem_desc *desc, void *stream, const double *T_nodal_dev,
                           const double *sigma_dev, const double *I_prev_canon_dev,
                           double *I_out_canon_dev, double *moments_dev, double *closures_dev);

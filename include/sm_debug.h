@@ -43,6 +43,14 @@ sm_status sm_debug_set_pcg_form(sm_problem *p, int form);
  * last low-order solve used, or SM_DEBUG_PCG_AUTO if it has run none. */
 sm_status sm_debug_get_pcg_form(const sm_problem *p, int *form);
 
+/* out_dev[i] = e^{-x_dev[i]} for i < n, evaluated by the emission kernels'
+ * table-driven routine (Tang's method) for 0 <= x < 708, so that a test can
+ * compare it with CUDA's exp directly; elsewhere out_dev[i] = exp(-x) of the
+ * CUDA math library.  FP64 device arrays; asynchronous on stream (a
+ * cudaStream_t, NULL = legacy default stream).  INVALID_ARG for n < 0 or a
+ * NULL array with n > 0. */
+sm_status sm_debug_exp_neg(const double *x_dev, double *out_dev, int n, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,7 @@ EXPORTED = ["sm_create_problem", "sm_destroy_problem", "sm_get_info", "sm_set_st
             "sm_synchronize", "sm_autotune", "sm_set_profiling", "sm_get_kernel_times",
             "sm_launch_count", "sm_last_error", "sm_status_string",
             "sm_debug_set_wait_limit_ns", "sm_debug_skip_publish", "sm_debug_withhold_lo_block",
-            "sm_debug_set_pcg_form", "sm_debug_get_pcg_form",
+            "sm_debug_set_pcg_form", "sm_debug_get_pcg_form", "sm_debug_exp_neg",
             "sm_sweep_static",
             "sm_default_step_params", "sm_loworder_newton", "sm_step",
             "sm_create_batch", "sm_destroy_batch", "sm_batch_problem", "sm_batch_get_info",
@@ -144,6 +144,7 @@ def load():
         "sm_debug_withhold_lo_block": [P, I],
         "sm_debug_set_pcg_form": [P, I],
         "sm_debug_get_pcg_form": [P, ctypes.POINTER(ctypes.c_int)],
+        "sm_debug_exp_neg": [P, P, I, P],
         "sm_sweep_static": [ctypes.POINTER(ProblemDesc), P, P, P, P, P, P, P],
         "sm_loworder_newton": [P, P, P, P, P, P, P, P, ctypes.POINTER(StepParams),
                                ctypes.POINTER(StepStats)],

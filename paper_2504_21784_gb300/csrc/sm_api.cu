@@ -291,6 +291,46 @@ SweepArgs make_sweep_args(const sm_problem *p, const void *I_prev, void *I_out) 
 }
 }  // namespace smk
 
+namespace smk {
+const char *check_desc(const sm_problem_desc *d) {
+    if (d->dim != 1 && d->dim != 2) return "dim must be 1 or 2";
+    if (d->nx < 1 || (d->dim == 2 && d->ny < 1)) return "empty mesh: nx and ny must be >= 1";
+    if ((long long)d->nx * (d->dim == 2 ? d->ny : 1) > (1LL << 30))
+        return "mesh too large (more than 2^30 cells)";
+    if (!std::isfinite(d->x0) || !std::isfinite(d->x1) || !(d->x1 > d->x0) ||
+        (d->dim == 2 && (!std::isfinite(d->y0) || !std::isfinite(d->y1) || !(d->y1 > d->y0))))
+        return "domain extent must be finite and positive";
+    if (d->n_groups < 1 || !d->group_edges) return "n_groups must be >= 1 with group_edges";
+    for (int g = 0; g <= d->n_groups; ++g) {
+        if (!(d->group_edges[g] > 0.0) || !std::isfinite(d->group_edges[g]))
+            return "group edges must be positive and finite";
+        if (g > 0 && !(d->group_edges[g] > d->group_edges[g - 1]))
+            return "group edges must be ascending";
+    }
+    if (d->dim == 1 && (d->n_polar < 2 || d->n_polar % 2 || d->n_polar > 4096))
+        return "1D quadrature order must be even, 2..4096";
+    // each factor bounded before any product of the two is formed
+    if (d->dim == 2 && (d->n_polar < 1 || d->n_azim < 1 || d->n_polar > 4096 || d->n_azim > 4096))
+        return "2D quadrature needs 1 <= n_polar, n_azim <= 4096";
+    if (!(d->a > 0.0) || !(d->c > 0.0) || !std::isfinite(d->a) || !std::isfinite(d->c))
+        return "a and c must be finite and > 0";
+    if (!std::isfinite(d->dt)) return "dt must be finite";
+    for (int k = 0; k < 4; ++k)
+        if (!std::isfinite(d->T_bdr[k])) return "boundary temperatures must be finite";
+    if (d->precision != 32 && d->precision != 64) return "precision must be 32 or 64";
+    if (d->opacity_kind != SM_OPACITY_POWER && d->opacity_kind != SM_OPACITY_LARSEN)
+        return "unknown opacity_kind";
+    if (!std::isfinite(d->opacity_alpha)) return "opacity_alpha must be finite";
+    if (d->groups_per_warp != 0 && d->groups_per_warp != 1 && d->groups_per_warp != 2 &&
+        d->groups_per_warp != 4 && d->groups_per_warp != 8)
+        return "groups_per_warp must be 0, 1, 2, 4 or 8";
+    if (d->strip_width < 0 || d->strip_width > 16) return "strip_width out of range (0..16)";
+    if (d->prefetch_rows < 0 || d->prefetch_rows > 8 || d->prefetch_rows == 1)
+        return "prefetch_rows must be 0 or 2..8";
+    return nullptr;
+}
+}  // namespace smk
+
 extern "C" {
 
 const char *sm_last_error(void) { return g_err.c_str(); }
@@ -316,37 +356,7 @@ static sm_status create_problem(const sm_problem_desc *d, void *stream, sm_probl
                                 int standalone) {
     if (!d || !out) return fail(SM_ERR_INVALID_ARG, "desc and out must be non-NULL");
     *out = nullptr;
-    if (d->dim != 1 && d->dim != 2) return fail(SM_ERR_INVALID_ARG, "dim must be 1 or 2");
-    if (d->nx < 1 || (d->dim == 2 && d->ny < 1))
-        return fail(SM_ERR_INVALID_ARG, "empty mesh: nx and ny must be >= 1");
-    if ((long long)d->nx * (d->dim == 2 ? d->ny : 1) > (1LL << 30))
-        return fail(SM_ERR_INVALID_ARG, "mesh too large (more than 2^30 cells)");
-    if (!(d->x1 > d->x0) || (d->dim == 2 && !(d->y1 > d->y0)))
-        return fail(SM_ERR_INVALID_ARG, "domain extent must be positive");
-    if (d->n_groups < 1 || !d->group_edges)
-        return fail(SM_ERR_INVALID_ARG, "n_groups must be >= 1 with group_edges");
-    for (int g = 0; g <= d->n_groups; ++g) {
-        if (!(d->group_edges[g] > 0.0) || !std::isfinite(d->group_edges[g]))
-            return fail(SM_ERR_INVALID_ARG, "group edges must be positive and finite");
-        if (g > 0 && !(d->group_edges[g] > d->group_edges[g - 1]))
-            return fail(SM_ERR_INVALID_ARG, "group edges must be ascending");
-    }
-    if (d->dim == 1 && (d->n_polar < 2 || d->n_polar % 2))
-        return fail(SM_ERR_INVALID_ARG, "1D quadrature order must be even and >= 2");
-    if (d->dim == 2 && (d->n_polar < 1 || d->n_azim < 1))
-        return fail(SM_ERR_INVALID_ARG, "2D quadrature needs n_polar, n_azim >= 1");
-    if (!(d->a > 0.0) || !(d->c > 0.0)) return fail(SM_ERR_INVALID_ARG, "a and c must be > 0");
-    if (d->precision != 32 && d->precision != 64)
-        return fail(SM_ERR_INVALID_ARG, "precision must be 32 or 64");
-    if (d->opacity_kind != SM_OPACITY_POWER && d->opacity_kind != SM_OPACITY_LARSEN)
-        return fail(SM_ERR_INVALID_ARG, "unknown opacity_kind");
-    if (d->groups_per_warp != 0 && d->groups_per_warp != 1 && d->groups_per_warp != 2 &&
-        d->groups_per_warp != 4 && d->groups_per_warp != 8)
-        return fail(SM_ERR_INVALID_ARG, "groups_per_warp must be 0, 1, 2, 4 or 8");
-    if (d->strip_width < 0 || d->strip_width > 16)
-        return fail(SM_ERR_INVALID_ARG, "strip_width out of range (0..16)");
-    if (d->prefetch_rows < 0 || d->prefetch_rows > 8 || d->prefetch_rows == 1)
-        return fail(SM_ERR_INVALID_ARG, "prefetch_rows must be 0 or 2..8");
+    if (const char *why = smk::check_desc(d)) return fail(SM_ERR_INVALID_ARG, why);
 
     smk::planck_upload_tables();
     sm_problem *p = new sm_problem();

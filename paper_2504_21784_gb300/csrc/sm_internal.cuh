@@ -106,6 +106,9 @@ cudaError_t launch_sweep2d_batch(int prec, const BatchSweepArgs &b, int grid, si
                                  cudaStream_t s);
 int sweep2d_batch_max_resident(int prec, int W, size_t smem);
 void planck_upload_tables(void);
+// Descriptor checks shared by sm_create_problem and sm_sweep_static: NULL when
+// the descriptor is valid, else a static message (allocates nothing).
+const char *check_desc(const sm_problem_desc *d);
 // Set the thread-local message returned by sm_last_error() (no allocation
 // beyond the message string of at most 255 characters).
 void set_last_error(const char *msg);

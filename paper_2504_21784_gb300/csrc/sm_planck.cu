@@ -19,6 +19,8 @@
 // highest infinity so that sum_g b_g = 1.
 #include <math.h>
 
+#include <atomic>
+
 #include "sm_internal.cuh"
 
 namespace smk {
@@ -109,12 +111,13 @@ static void planck_taylor_tables(double out[NCEN][2][NTAY]) {
     }
 }
 
-static bool g_tables_ready[128] = {false};
+// set once a device has its tables; two threads uploading at once write the same data
+static std::atomic<bool> g_tables_ready[128];
 
 void planck_upload_tables(void) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return;
-    if (g_tables_ready[dev]) return;
+    if (g_tables_ready[dev].load(std::memory_order_acquire)) return;
     double head[NBERN], bern[NBERN];
     for (int k = 1; k <= NBERN; ++k) {
         const int s = 2 * k;
@@ -153,7 +156,7 @@ void planck_upload_tables(void) {
         cudaMemcpyToSymbol(g_exp2_tab, tab, sizeof(tab)) == cudaSuccess &&
         cudaMemcpyToSymbol(g_ptab, ptab, sizeof(ptab)) == cudaSuccess &&
         cudaMemcpyToSymbol(g_pcen, pcen, sizeof(pcen)) == cudaSuccess)
-        g_tables_ready[dev] = true;
+        g_tables_ready[dev].store(true, std::memory_order_release);
 }
 
 // Values of the cumulative spectra at one reduced edge x = nu/T, in the form
@@ -250,6 +253,14 @@ __device__ __forceinline__ EdgeVals edge_vals(double x, float xf, int K) {
     e.rv = Q + 0.25 * C15 * (x2 * x2) * e1;
     e.tail = true;
     return e;
+}
+
+// Test hook kernel: e^{-x} by exp_neg where it applies (0 <= x < 708).
+__global__ void exp_neg_kernel(const double *__restrict__ x, double *__restrict__ out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = x[i];
+    out[i] = (v >= 0.0 && v < 708.0) ? exp_neg(v) : exp(-v);
 }
 
 __device__ __forceinline__ EdgeVals edge_vals(double x) {
@@ -585,3 +596,18 @@ cudaError_t launch_closures_from_T(const sm_problem *p, const double *mom, const
 }
 
 }  // namespace smk
+
+extern "C" sm_status sm_debug_exp_neg(const double *x, double *out, int n, void *stream) {
+    if (n < 0 || (n > 0 && (!x || !out))) {
+        smk::set_last_error("sm_debug_exp_neg: n >= 0 and non-NULL arrays required");
+        return SM_ERR_INVALID_ARG;
+    }
+    if (n == 0) return SM_OK;
+    smk::planck_upload_tables();
+    smk::exp_neg_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(x, out, n);
+    if (cudaGetLastError() != cudaSuccess) {
+        smk::set_last_error("sm_debug_exp_neg: launch failed");
+        return SM_ERR_CUDA;
+    }
+    return SM_OK;
+}

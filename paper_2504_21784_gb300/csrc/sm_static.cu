@@ -17,12 +17,19 @@
 // The scratch array exists once per GPU that loads the library and is held
 // until the process exits.  Host code cannot use the array's name as a
 // device address, so the first call on each device (with that device
-// current) looks the address up with cudaGetSymbolAddress and caches it;
-// make that first call before any stream capture.  All calls share the
-// array: calls that overlap on the GPU (two streams, two threads, two
+// current) looks the address up with cudaGetSymbolAddress and caches it; the
+// first call in the process also uploads the Planck tables (synchronous
+// copies to constant memory).  Make that first call before any stream
+// capture.  Two threads making their first call at once both look the
+// address up and store the same value (an atomic store).  All calls share
+// the array: calls that overlap on the GPU (two streams, two threads, two
 // devices' worth of work on one device) race and corrupt each other.  The
-// call is synchronous (it waits for its stream to read the device status).
+// call is synchronous on its stream only: it reads the device status with an
+// asynchronous copy on that stream and waits for that stream, not for the
+// device.  Host stack use is about 40 KB (the lane tables of at most 16
+// quadrant x direction-block rows).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -34,12 +41,12 @@ namespace {
 constexpr size_t SM_STATIC_SCRATCH_BYTES = 16u << 20;  // 16 MiB per device
 constexpr int MAX_DEVICES = 128;
 constexpr int MAX_DIRS = 512;       // 4 quadrants x up to 128 directions
-constexpr int MAX_LANE_ROWS = 64;   // quadrants x direction blocks
+constexpr int MAX_LANE_ROWS = 16;   // quadrants x direction blocks: 4 x (128 / 32)
 constexpr int MAX_GROUPS = 256;
 
 static __device__ __align__(256) unsigned char g_static_scratch[SM_STATIC_SCRATCH_BYTES];
 
-void *g_scratch_addr[MAX_DEVICES] = {nullptr};
+std::atomic<void *> g_scratch_addr[MAX_DEVICES];  // zero-initialised (static storage)
 
 sm_status static_fail(sm_status s, const char *msg) {
     smk::set_last_error(msg);  // reported by sm_last_error()
@@ -90,37 +97,25 @@ sm_status sm_sweep_static(const sm_problem_desc *d, void *stream, const double *
     if (!d) return static_fail(SM_ERR_INVALID_ARG, "desc is NULL");
     if (!T || !sigma || !I_out_canon)
         return static_fail(SM_ERR_INVALID_ARG, "T_nodal_dev, sigma_dev and I_out_dev are required");
+    if (const char *why = smk::check_desc(d)) return static_fail(SM_ERR_INVALID_ARG, why);
     if (d->dim != 2) return static_fail(SM_ERR_INVALID_ARG, "sm_sweep_static supports dim = 2 only");
-    if (d->nx < 1 || d->ny < 1) return static_fail(SM_ERR_INVALID_ARG, "empty mesh");
-    if (!(d->x1 > d->x0) || !(d->y1 > d->y0))
-        return static_fail(SM_ERR_INVALID_ARG, "domain extent must be positive");
-    if (d->n_groups < 1 || d->n_groups > MAX_GROUPS || !d->group_edges)
-        return static_fail(SM_ERR_INVALID_ARG, "need 1 <= n_groups <= 256 and group_edges");
-    for (int g = 0; g <= d->n_groups; ++g)
-        if (!(d->group_edges[g] > 0.0) || (g > 0 && !(d->group_edges[g] > d->group_edges[g - 1])))
-            return static_fail(SM_ERR_INVALID_ARG, "group edges must be positive and ascending");
-    if (d->n_polar < 1 || d->n_azim < 1 || d->n_polar * d->n_azim > 128)
+    if (d->n_groups > MAX_GROUPS)
+        return static_fail(SM_ERR_INVALID_ARG, "sm_sweep_static supports n_groups <= 256");
+    // each factor is bounded (by check_desc and here) before the product
+    if (d->n_polar > 128 || d->n_azim > 128 || d->n_polar * d->n_azim > 128)
         return static_fail(SM_ERR_INVALID_ARG, "need 1 <= n_polar * n_azim <= 128");
-    if (!(d->a > 0.0) || !(d->c > 0.0)) return static_fail(SM_ERR_INVALID_ARG, "a, c must be > 0");
-    if (d->precision != 32 && d->precision != 64)
-        return static_fail(SM_ERR_INVALID_ARG, "precision must be 32 or 64");
-    if (d->opacity_kind != SM_OPACITY_POWER && d->opacity_kind != SM_OPACITY_LARSEN)
-        return static_fail(SM_ERR_INVALID_ARG, "unknown opacity_kind");
-    if (d->groups_per_warp != 0 && d->groups_per_warp != 1 && d->groups_per_warp != 2 &&
-        d->groups_per_warp != 4 && d->groups_per_warp != 8)
-        return static_fail(SM_ERR_INVALID_ARG, "groups_per_warp must be 0, 1, 2, 4 or 8");
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)
         return static_fail(SM_ERR_CUDA, "no current CUDA device");
-    if (!g_scratch_addr[dev]) {
-        void *addr = nullptr;
+    void *addr = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!addr) {
         const cudaError_t e = cudaGetSymbolAddress(&addr, g_static_scratch);
         if (e != cudaSuccess || !addr)
             return static_fail(SM_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
-        g_scratch_addr[dev] = addr;
+        g_scratch_addr[dev].store(addr, std::memory_order_release);
     }
-    unsigned char *base = static_cast<unsigned char *>(g_scratch_addr[dev]);
+    unsigned char *base = static_cast<unsigned char *>(addr);
     smk::planck_upload_tables();
 
     // A problem description on the stack: scalar fields only (its vectors stay
@@ -300,9 +295,10 @@ sm_status sm_sweep_static(const sm_problem_desc *d, void *stream, const double *
     ST_CUDA(smk::launch_sweep2d(&p, a, std::min(a.n_tasks, resident), s));
     ST_CUDA(smk::launch_reduce(&p, p.d_mom_acc, 1, moments ? moments : p.d_mom_tmp, closures, s));
     ST_CUDA(smk::launch_pack(&p, I_out_canon, Io, 1, s));
-    ST_CUDA(cudaStreamSynchronize(s));
+    // the status words, read on this stream only (no device-wide synchronization)
     unsigned int ctrl[smk::CTRL_WORDS];
-    ST_CUDA(cudaMemcpy(ctrl, base + o_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost));
+    ST_CUDA(cudaMemcpyAsync(ctrl, base + o_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, s));
+    ST_CUDA(cudaStreamSynchronize(s));
 #undef ST_CUDA
     if (ctrl[smk::CTRL_STATUS] & smk::ST_TIMEOUT)
         return static_fail(SM_ERR_TIMEOUT, "a wavefront wait exceeded its time limit");

@@ -81,7 +81,7 @@ def test_adjoint_gradient_matches_oracle(gpu_lib, kind, G):
     err = np.abs(g - gref).max() / np.abs(gref).max()
     print(f"kind {kind}: J {abs(Jg.item() - J) / J:.2e} grad {err:.2e}")
     assert abs(Jg.item() - J) < 1e-11 * J
-    assert err < 1e-9
+    assert err < 1e-11
 
 
 def test_adjoint_gradient_matches_gpu_finite_differences(gpu_lib):

@@ -10,10 +10,13 @@ rounding of I, q and the cell solve to single precision):
 magnitude of the reference: every element's error is divided by the largest
 magnitude of its field -- one (direction, group) slice of the intensity, one
 moment component (F and T are measured against phi, SF against SE, as they
-vanish near equilibrium).  Dividing by the element itself is meaningless at
-the nodes where the lumped-DG solution (no positivity fix-up) passes through
-zero.  sigma_E = SE/phi is compared weighted by phi for the same reason, the
-additive correction against sigma_F * phi.  Elementwise ratios are printed.
+vanish near equilibrium).  The intensity is also bounded element by element
+("I_elem"): each node's error against its own magnitude plus 1e-2 of the
+largest magnitude at its cell's nodes (the lumped-DG solution has no
+positivity fix-up and can pass through zero inside a cell, where dividing by
+the element itself is meaningless), so cells far below their slice's maximum
+are held to the same relative bar.  sigma_E = SE/phi is compared weighted by
+phi for the same reason, the additive correction against sigma_F * phi.
 """
 import numpy as np
 import pytest
@@ -58,7 +61,7 @@ def _check_all(case, precision, label):
     e = parity_errors(case.cfg, (Ig, mg, cg), ref)
     print(f"[{label} fp{precision}] " + "  ".join(f"{k} {v:.2e}" for k, v in e.items()) +
           f"  ({case.prob.info['n_tasks']} tasks, {case.prob.info['n_strips']} strips)")
-    bad = {k: v for k, v in e.items() if k != "I_elem" and not v <= rtol}
+    bad = {k: v for k, v in e.items() if not v <= rtol}
     assert not bad, f"parity above {rtol}: {bad}"
     return Ig
 
@@ -227,3 +230,37 @@ def test_launch_count_and_kernel_times(gpu_lib):
     t = case.prob.kernel_times()
     assert t["count"] == 1 and t["sweep_ms"] > 0
     assert case.prob.launch_count() - n0 >= 3
+
+
+def test_exp_neg_matches_cuda_exp(gpu_lib):
+    """The emission kernels' table-driven e^{-x} (Tang's method, a 2^{-j/64}
+    table and a degree-6 polynomial) against CUDA's exp over [0, 708): two
+    million uniform and log-uniform points, the table's reduction knots
+    k ln2/64 with their floating-point neighbours, and the ends.  Both are
+    within about an ulp of e^{-x}, so they differ by at most 2 ulp (and each
+    stays within 2 ulp of the host's exp)."""
+    import ctypes
+    import torch
+    rng = np.random.default_rng(708)
+    knots = np.arange(0, int(708 * 64 / np.log(2))) * (np.log(2) / 64)
+    x = np.concatenate([rng.uniform(0.0, 708.0, 1 << 20),
+                        np.exp(rng.uniform(np.log(1e-300), np.log(708.0), 1 << 20)),
+                        knots, np.nextafter(knots, 0.0), np.nextafter(knots, 708.0),
+                        [0.0, 5e-324, 1e-300, 1e-16, 0.5, 1.0, np.nextafter(708.0, 0.0)]])
+    x = x[(x >= 0.0) & (x < 708.0)]
+    xd = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xd)
+    lib = gpu_lib.load()
+    rc = lib.sm_debug_exp_neg(ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                              int(x.size), None)
+    assert rc == 0, lib.sm_last_error().decode()
+    ref = torch.exp(-xd)                       # CUDA's exp
+    torch.cuda.synchronize()
+    got, ref = out.cpu().numpy(), ref.cpu().numpy()
+    ulp = np.spacing(np.abs(ref))
+    e_cuda = float(np.max(np.abs(got - ref) / ulp))
+    host = np.exp(-x)
+    e_host = float(np.max(np.abs(got - host) / np.spacing(np.abs(host))))
+    print(f"exp_neg over {x.size} points: {e_cuda:.2f} ulp from CUDA exp, {e_host:.2f} ulp "
+          f"from the host's exp")
+    assert e_cuda <= 2.0 and e_host <= 2.0

@@ -107,3 +107,42 @@ def test_null_handles_rejected_before_cuda(lib):
         assert so.sm_last_error(), name
     # the destructors accept NULL as a no-op (include/sm.h)
     assert so.sm_destroy_problem(None) == 0 and so.sm_destroy_batch(None) == 0
+
+
+def test_static_entry_rejects_bad_descriptors_before_cuda(lib):
+    """sm_sweep_static validates its descriptor before any CUDA call: huge
+    direction counts whose product would overflow an int, non-finite group
+    edges or boundary temperatures, and a mesh beyond 2^30 cells are refused
+    with SM_ERR_INVALID_ARG (so this runs without a GPU)."""
+    import numpy as np
+    import paper_2504_21784_gb300 as sm
+    so = sm.load()
+    edges = np.array([0.1, 1.0, 10.0])
+    inf_edges = np.array([0.1, 1.0, np.inf])
+    dummy = ctypes.c_void_p(16)   # never dereferenced: validation comes first
+
+    def call(**kw):
+        d = sm.ProblemDesc()
+        d.dim, d.nx, d.ny = 2, 4, 4
+        d.x0, d.x1, d.y0, d.y1 = 0, 1, 0, 1
+        d.n_groups = 2
+        d.group_edges = edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.n_polar, d.n_azim = 1, 1
+        d.a, d.c, d.dt = 1.0, 1.0, 0.1
+        d.precision = 32
+        for k, v in kw.items():
+            if k == "T_bdr":
+                d.T_bdr[0] = v
+            else:
+                setattr(d, k, v)
+        rc = so.sm_sweep_static(ctypes.byref(d), None, dummy, dummy, None, dummy, None, None)
+        return rc, so.sm_last_error().decode()
+
+    for kw in (dict(n_polar=65536, n_azim=65536), dict(n_polar=1 << 16, n_azim=1 << 15),
+               dict(n_polar=200, n_azim=1), dict(n_polar=12, n_azim=12),
+               dict(group_edges=inf_edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               dict(T_bdr=float("nan")), dict(nx=1 << 16, ny=1 << 16), dict(dim=1),
+               dict(dt=float("inf"))):
+        rc, msg = call(**kw)
+        assert rc == 1, (kw, rc, msg)
+        assert msg

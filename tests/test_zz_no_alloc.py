@@ -1,12 +1,22 @@
-"""The allocation-free entry point sm_sweep_static against sm_sweep.
+"""The allocation-free entry point sm_sweep_static against sm_sweep and the
+oracle.
 
 sm_sweep_static serves callers that cannot call cudaMalloc (and so cannot
 create a problem workspace): it keeps every intermediate buffer in one static
-device array.  This test calls it through the C ABI twice in a row -- the
+device array.  Each case calls it through the C ABI twice in a row -- the
 second call starting from the first call's intensity, so the shared scratch
-is reused with stale contents from the previous call -- and checks both
-results against the regular sm_sweep path within the parity tolerance of the
-FP32 sweep (1e-5 per field).  This file is collected last on purpose.
+is reused with stale contents from the previous call -- and checks
+
+* the intensity bit for bit against the regular sm_sweep path with the same
+  slots per lane (the same cell solves in the same order), and the moments
+  and all eleven closure fields within 1e-12 (FP64) / 2e-6 (FP32) of it (the
+  moments are summed with atomics, in another order);
+* every output against the FP64 oracle within the parity bars, 1e-11 (FP64)
+  and 1e-5 (FP32) per field;
+* that the call leaves the device's free memory unchanged.
+
+FP32 and FP64 sweeps, with and without a previous intensity.  This file is
+collected last on purpose.
 """
 import ctypes
 
@@ -16,14 +26,15 @@ import pytest
 import oracle as O
 from paper_2504_21784_gb300 import workloads as W
 
-from _cases import config
+from _cases import config, parity_errors
 
 pytestmark = pytest.mark.gpu
 
-RTOL = 1e-5
+TOL = {64: 1e-11, 32: 1e-5}
+SAME = {64: 1e-12, 32: 2e-6}
 
 
-def _desc(sm, cfg, precision, edges):
+def _desc(sm, cfg, precision, edges, gw=1):
     d = sm.ProblemDesc()
     d.dim, d.nx, d.ny = 2, cfg.nx, cfg.ny
     d.x0, d.x1, d.y0, d.y1 = cfg.extent
@@ -35,6 +46,7 @@ def _desc(sm, cfg, precision, edges):
     for i in range(4):
         d.T_bdr[i] = cfg.T_bdr[i]
     d.precision = precision
+    d.groups_per_warp = gw
     return d
 
 
@@ -44,24 +56,27 @@ def _field_err(got, ref, axis):
     return float(np.max(d.max(axis=red) / np.maximum(np.abs(ref).max(axis=red), 1e-300)))
 
 
-def test_static_entry_matches_sm_sweep_twice(gpu_lib):
+@pytest.mark.parametrize("with_prev", [True, False])
+@pytest.mark.parametrize("precision", [32, 64])
+def test_static_entry_matches_sm_sweep_twice(gpu_lib, precision, with_prev):
     import torch
     sm = gpu_lib
     lib = sm.load()
     cfg = config(2, 24, 20, 6, 2, 4, T_bdr=(1.0, 0.0, 0.3, 0.0))
     edges = np.ascontiguousarray(cfg.edges)
-    prob = sm.Problem.from_config(cfg, 32)
-    T = torch.from_numpy(W.temperature_wave(cfg, seed=4)).cuda()
-    sig = torch.from_numpy(O.opacity(cfg.opacity_kind, cfg.opacity_alpha, cfg.edges,
-                                     W.temperature_wave(cfg, seed=4),
-                                     W.scale_field(cfg, seed=5))).cuda()
+    prob = sm.Problem.from_config(cfg, precision, groups_per_warp=1)
+    Tn = W.temperature_wave(cfg, seed=4)
+    sig_n = O.opacity(cfg.opacity_kind, cfg.opacity_alpha, cfg.edges, Tn,
+                      W.scale_field(cfg, seed=5))
+    T = torch.from_numpy(Tn).cuda()
+    sig = torch.from_numpy(sig_n).cuda()
     I0 = torch.from_numpy(W.intensity_random(cfg.n_dir, cfg.n_groups, cfg.n_cells, 4, seed=6,
                                              scale=0.05)).cuda()
     stream = torch.cuda.current_stream()
-    desc = _desc(sm, cfg, 32, edges)
+    desc = _desc(sm, cfg, precision, edges)
 
     # regular path: two sweeps in a row
-    Ip = prob.pack(I0)
+    Ip = prob.pack(I0) if with_prev else None
     refs = []
     for _ in range(2):
         Io = prob.empty_intensity()
@@ -72,24 +87,44 @@ def test_static_entry_matches_sm_sweep_twice(gpu_lib):
         Ip = Io
 
     # allocation-free path: two calls in a row, canonical layouts
-    Iprev = prob.unpack(prob.pack(I0))  # same FP32-rounded start as the regular path
+    Iprev = prob.unpack(prob.pack(I0)) if with_prev else None  # the same rounded start
+    mom = torch.empty((cfg.n_cells, 4, 9), dtype=torch.float64, device="cuda")
+    clo = torch.empty((cfg.n_cells, 4, 11), dtype=torch.float64, device="cuda")
+    omx, omy, w = O.quadrature(2, cfg.n_polar, cfg.n_azim)
+    q = O.emission(cfg.edges, cfg.a, cfg.c, Tn, sig_n)
+    infl = O.inflow(cfg.edges, cfg.a, cfg.c, cfg.T_bdr)
     for k in range(2):
-        Iout = torch.empty_like(Iprev)
-        mom = torch.empty((cfg.n_cells, 4, 9), dtype=torch.float64, device="cuda")
-        clo = torch.empty((cfg.n_cells, 4, 11), dtype=torch.float64, device="cuda")
+        Iout = torch.empty((cfg.n_dir, cfg.n_groups, cfg.n_cells, 4), dtype=torch.float64,
+                           device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         rc = lib.sm_sweep_static(ctypes.byref(desc), ctypes.c_void_p(stream.cuda_stream),
-                                 T.data_ptr(), sig.data_ptr(), Iprev.data_ptr(), Iout.data_ptr(),
-                                 mom.data_ptr(), clo.data_ptr())
+                                 T.data_ptr(), sig.data_ptr(),
+                                 Iprev.data_ptr() if Iprev is not None else None,
+                                 Iout.data_ptr(), mom.data_ptr(), clo.data_ptr())
         assert rc == 0, lib.sm_last_error().decode()
+        free1 = torch.cuda.mem_get_info()[0]
         I_ref, m_ref, c_ref = refs[k]
-        e_I = _field_err(Iout.cpu().numpy(), I_ref, 2)
-        m = mom.cpu().numpy()
-        e_phi = _field_err(m[..., 0], m_ref[..., 0], 0)
-        e_F = float(np.abs(m[..., 1:6] - m_ref[..., 1:6]).max() / np.abs(m_ref[..., 0]).max())
-        e_SE = _field_err(m[..., 6], m_ref[..., 6], 0)
-        e_E = _field_err(clo.cpu().numpy()[..., 0], c_ref[..., 0], 0)
-        print(f"call {k}: I {e_I:.2e} phi {e_phi:.2e} F,T {e_F:.2e} SE {e_SE:.2e} E {e_E:.2e}")
-        assert max(e_I, e_phi, e_F, e_SE, e_E) <= RTOL
+        Ig, m, c = Iout.cpu().numpy(), mom.cpu().numpy(), clo.cpu().numpy()
+        same_I = bool(np.array_equal(Ig, I_ref))
+        e_m = max(_field_err(m[..., j], m_ref[..., j], 0) for j in range(9))
+        e_c = max(_field_err(c[..., j], c_ref[..., j], 0) for j in range(11))
+        # the oracle, from the same (rounded) previous intensity
+        Ik = Iprev.cpu().numpy() if Iprev is not None else None
+        Ir = O.sweep(2, cfg.nx, cfg.ny, cfg.extent, omx, omy, sig_n, 1.0 / (cfg.c * cfg.dt), q,
+                     Ik, infl)
+        mr = O.moments(2, omx, omy, w, sig_n, Ir)
+        cr = O.closures(2, cfg.edges, cfg.c, sig_n, Tn, mr)
+        e = parity_errors(cfg, (Ig, m, c), (Ir, mr, cr))
+        print(f"fp{precision} prev {with_prev} call {k}: intensity identical {same_I}, moments "
+              f"{e_m:.2e} closures {e_c:.2e} vs sm_sweep; oracle " +
+              "  ".join(f"{n} {v:.2e}" for n, v in e.items()) +
+              f"; free memory change {free0 - free1} B")
+        assert same_I
+        assert e_m <= SAME[precision] and e_c <= SAME[precision]
+        bad = {n: v for n, v in e.items() if not v <= TOL[precision]}
+        assert not bad, f"parity above {TOL[precision]}: {bad}"
+        assert free1 == free0
         Iprev = Iout
 
 
@@ -99,7 +134,7 @@ def test_static_entry_rejects_oversized_problem(gpu_lib):
     lib = sm.load()
     cfg = config(2, 256, 256, 64, 4, 8)
     edges = np.ascontiguousarray(cfg.edges)
-    desc = _desc(sm, cfg, 32, edges)
+    desc = _desc(sm, cfg, 32, edges, gw=0)
     dummy = torch.zeros(16, dtype=torch.float64, device="cuda")
     rc = lib.sm_sweep_static(ctypes.byref(desc), None, dummy.data_ptr(), dummy.data_ptr(), None,
                              dummy.data_ptr(), None, None)
