@@ -237,6 +237,7 @@ class LOParams:
     max_elim: int = 40
     T_floor: float = 1e-8
     linear: str = "schur"      # "schur" (F eliminated, Eq. schur) or "block"
+    source_form: str = "factored"  # or "pseudo_fission" (the printed form; see lo_newton)
 
 
 def eliminate_T(T0, a, c, cv_dt, sigP, sigE, E, Tstar, rtol, maxit, T_floor):
@@ -296,9 +297,23 @@ def lo_newton(m: Mesh, ops, c, a, dt, alpha, clo, T_k, cv, Estar, Fstar, jin2, T
         dB = 4.0 * a * c * T ** 3
         den = cv_dt + sP * dB
         nu = sP * dB / den                     # pseudo-fission coefficient (Eq. pseudo_fission)
-        qT0 = cv_dt * (Tk - T) - sP * B0
-        AEE = P + sp.diags(mass * c * (sEt - nu * sE))
-        bE = mass * (sP * B0 + nu * qT0 + Estar.reshape(-1) / dt) + bnd
+        if prm.source_form == "pseudo_fission":
+            # as printed: sigma~_E - nu sigma_E and sigma_P B + nu q_T0 with
+            # q_T0 = C_v/dt (T* - T) - sigma_P B
+            qT0 = cv_dt * (Tk - T) - sP * B0
+            coefE = sEt - nu * sE
+            src = sP * B0 + nu * qT0
+        else:
+            # the same two terms with 1 - nu = (C_v/dt) / den written out, so that
+            # nu sigma_E is never subtracted from sigma_E, nor nu sigma_P B from
+            # sigma_P B: where sigma_P dB >> C_v/dt (optically thick, nu -> 1)
+            # those differences cancel catastrophically and the Newton iterates
+            # inherit their rounding
+            omnu = cv_dt / den
+            coefE = sE * omnu + inv_cdt
+            src = sP * B0 * omnu + nu * cv_dt * (Tk - T)
+        AEE = P + sp.diags(mass * c * coefE)
+        bE = mass * (src + Estar.reshape(-1) / dt) + bnd
         if prm.linear == "block":
             K = sp.bmat([[AFF, AFE], [AEF, AEE]], format="csc")
             sol = spla.spsolve(K, np.concatenate([bF, bE]))
@@ -306,10 +321,14 @@ def lo_newton(m: Mesh, ops, c, a, dt, alpha, clo, T_k, cv, Estar, Fstar, jin2, T
         else:
             # A_FF F + A_FE E = b_F with A_FF diagonal: F = A_FF^{-1}(b_F - A_FE E);
             # then S E = b_E - A_EF A_FF^{-1} b_F with S = A_EE - A_EF A_FF^{-1} A_FE
-            # (Eq. schur), factorised by sparse LU in a symmetric fill-reducing order
+            # (Eq. schur).  S is symmetric positive definite (Sec. 5), so it is
+            # factorised by sparse LU with diagonal pivots (stable for SPD
+            # matrices, the LU form of Cholesky) in a symmetric fill-reducing order
             affi = 1.0 / AFF.diagonal()
             S = (AEE - AEF @ sp.diags(affi) @ AFE).tocsc()
-            E = spla.spsolve(S, bE - AEF @ (affi * bF), permc_spec="MMD_AT_PLUS_A")
+            lu = spla.splu(S, permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0,
+                           options=dict(SymmetricMode=True))
+            E = lu.solve(bE - AEF @ (affi * bF))
             F = affi * (bF - AFE @ E)
         T, ite = eliminate_T(T, a, c, cv_dt, sP, sE, E, Tk, prm.elim_rtol, prm.max_elim,
                              prm.T_floor)

@@ -170,3 +170,25 @@ def test_schur_solve_equals_block_solve(dim, nx, ny):
     assert np.max(np.abs(Ts - Tb)) < 1e-13 * np.abs(Tb).max()
     assert np.max(np.abs(Es - Eb)) < 1e-13 * np.abs(Eb).max()
     assert np.max(np.abs(Fs - Fb)) < 1e-12 * np.abs(Eb).max()
+
+
+@pytest.mark.parametrize("dim,nx,ny", [(1, 12, 1), (2, 5, 4)])
+def test_factored_newton_source_equals_printed_form(dim, nx, ny):
+    """The Newton linearisation written with 1 - nu = (C_v/dt)/(C_v/dt + sigma_P dB)
+    (sigma_E (1 - nu) + 1/(c dt), sigma_P B (1 - nu) + nu C_v/dt (T* - T))
+    is the printed pseudo-fission form (sigma~_E - nu sigma_E,
+    sigma_P B + nu q_T0, Sec. 5): on a case without stiff cancellation the two
+    give the same solve."""
+    cfg, m, clo, T, cv, mom_k, alpha, jin2 = _lo_case(dim, nx, ny, seed=13)
+    ops = L.lo_operators(m, 1.0, alpha)
+    Estar = mom_k[..., 0]
+    Fstar = mom_k[..., 1:1 + dim]
+    out = {}
+    for form in ("factored", "pseudo_fission"):
+        prm = L.LOParams(eps_inner=1e-14, max_inner=30, elim_rtol=1e-15, max_elim=60,
+                         source_form=form)
+        out[form] = L.lo_newton(m, ops, 1.0, 1.0, cfg.dt, alpha, clo, T, cv, Estar, Fstar,
+                                jin2, T, Estar, prm)
+    (Ta, Ea, _, _), (Tb, Eb, _, _) = out["factored"], out["pseudo_fission"]
+    assert np.max(np.abs(Ta - Tb)) < 1e-13 * np.abs(Tb).max()
+    assert np.max(np.abs(Ea - Eb)) < 1e-13 * np.abs(Eb).max()
