@@ -40,6 +40,11 @@ def parse():
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--workload", default="multigroup2d",
+                    choices=["multigroup2d", "adjoint2d", "graychannel2d"],
+                    help="problem of the main line: the 256^2 x 128 x 64 multigroup workload "
+                         "(default), the 128^2 x 64 x 16 adjoint-size problem or the 128^2 x "
+                         "128 gray channel (profiling cases; the extra metrics are skipped)")
     ap.add_argument("--nx", type=int, default=0, help="override cells per axis (profiling cases)")
     ap.add_argument("--groups", type=int, default=0, help="override the group count")
     ap.add_argument("--no-step-metric", action="store_true",
@@ -61,10 +66,11 @@ def parse():
 
 def workload(args):
     from paper_2504_21784_gb300 import workloads as W
-    cfg = W.multigroup_2d()
+    cfg = {"multigroup2d": W.multigroup_2d, "adjoint2d": W.adjoint_2d,
+           "graychannel2d": W.gray_channel_2d}[args.workload]()
     if args.nx or args.groups:
         cfg = cfg.resized(args.nx or cfg.nx, n_groups=args.groups or None)
-        cfg.name = f"multigroup2d_{cfg.nx}x{cfg.ny}x{cfg.n_dir}x{cfg.n_groups}"
+        cfg.name = f"{args.workload}_{cfg.nx}x{cfg.ny}x{cfg.n_dir}x{cfg.n_groups}"
     return cfg
 
 
@@ -499,15 +505,19 @@ def adjoint_metric(sm, W, fd_cells: int, warm: bool = False):
     (segment recomputation + adjoint steps), and central differences
     (h = 1e-4 s_K) of the time-integrated right-edge leakage on fd_cells
     cells drawn with seed 21784 from a set fixed before the gradient is
-    known: the four cell columns next to the right edge.  Warm start (T0 =
-    0.3): error per cell relative to its own sensitivity.  Configured start
-    (T0 = 0.01): the leakage depends on a handful of edge cells only, so the
-    error is stated relative to the largest sensitivity of the drawn cells."""
+    known.  Warm start (T0 = 0.3): cells of the four columns next to the
+    right edge, error per cell relative to its own sensitivity.  Configured
+    start (T0 = 0.01): the leakage depends on a handful of edge cells only,
+    so the cells come from the right-edge column and the error is stated
+    relative to the largest sensitivity of all cells (most drawn cells have
+    none, which the difference quotients must confirm)."""
     import numpy as np
     import torch
     from paper_2504_21784_gb300 import adjoint as A
     cfg = W.adjoint_2d_warm() if warm else W.adjoint_2d()
-    band = np.array([iy * cfg.nx + ix for iy in range(cfg.ny) for ix in range(cfg.nx - 4, cfg.nx)])
+    cols = 4 if warm else 1
+    band = np.array([iy * cfg.nx + ix for iy in range(cfg.ny)
+                     for ix in range(cfg.nx - cols, cfg.nx)])
     cells = np.random.default_rng(21784).choice(band, min(fd_cells, band.size), replace=False)
     prob = sm.Problem.from_config(cfg, 64)
     T0 = torch.full((cfg.n_cells, 4), cfg.T0, dtype=torch.float64, device="cuda")
@@ -539,11 +549,12 @@ def adjoint_metric(sm, W, fd_cells: int, warm: bool = False):
                 fds.append((A.leakage(sp, st).item() - A.leakage(sm_, st).item()) / (2 * h))
         fds = np.array(fds)
         gk = g[cells]
-        ref = np.abs(gk) if warm else np.full(gk.shape, np.abs(gk).max())
+        ref = np.abs(gk) if warm else np.full(gk.shape, np.abs(g).max())
         errs = np.abs(fds - gk) / ref
-        out.update({"fd_cells": int(len(cells)), "fd_set": "4 columns next to the right edge",
+        out.update({"fd_cells": int(len(cells)),
+                    "fd_set": f"{cols} column(s) next to the right edge",
                     "fd_h": "1e-4 s_K",
-                    "fd_error": "per cell" if warm else "against the largest drawn sensitivity",
+                    "fd_error": "per cell" if warm else "against the largest sensitivity",
                     "fd_max_rel_err": float(errs.max()),
                     "fd_median_rel_err": float(np.median(errs))})
     prob.close()
@@ -625,6 +636,7 @@ def main():
         torch.cuda.synchronize()
 
     cfg = workload(args)
+    custom = bool(args.nx or args.groups or args.workload != "multigroup2d")
     prec = args.precision
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -730,18 +742,18 @@ def main():
                 "d2h_bytes_per_step": int(M_h.nbytes + C_h.nbytes),
                 "api": "sm_sweep_host (host T, sigma in; moments, closures out)"},
     }
-    if not args.no_step_metric and not (args.nx or args.groups):
+    if not args.no_step_metric and not custom:
         del I, mom, clo, sigma, prob
         torch.cuda.empty_cache()
         line["step_metric"] = step_metric(sm, W, [W.multigroup_2d(), W.gray_channel_2d()],
                                           args.step_steps, stream)
-    if not args.no_config_sweeps and not (args.nx or args.groups):
+    if not args.no_config_sweeps and not custom:
         line["config_sweeps"] = config_sweeps(sm, W, stream)
-    if not args.no_step_metric and not (args.nx or args.groups):
+    if not args.no_step_metric and not custom:
         line["marshak_paper"] = marshak_paper_metric(sm, W, stream)
-    if not args.no_batched and not (args.nx or args.groups):
+    if not args.no_batched and not custom:
         line["batched"] = batched_metric(sm, W, stream, max(3, args.steps // 2), 3)
-    if args.adjoint_fd_cells > 0 and not (args.nx or args.groups):
+    if args.adjoint_fd_cells > 0 and not custom:
         line["adjoint"] = adjoint_metric(sm, W, args.adjoint_cold_fd_cells)
         line["adjoint_warm"] = adjoint_metric(sm, W, args.adjoint_fd_cells, warm=True)
     if not args.no_cpu_baseline:

@@ -738,10 +738,15 @@ __device__ __forceinline__ void newton_setup_cell(const NewtonArgs &A, int k, do
         const double dB = 4.0 * A.a_rad * G.c * (Tn * Tn * Tn);
         const double cv_dt = cvv[n] / A.dt;
         const double den = cv_dt + sP * dB;
-        const double nu = den > 0.0 ? sP * dB / den : 0.0;  // pseudo-fission coefficient
-        const double qT0 = cv_dt * (Ts[n] - Tn) - sP * B0;
-        aE[n] = G.m * G.c * (sE + inv_cdt - nu * sE);
-        bE[n] = G.m * (sP * B0 + nu * qT0 + Es[n] / A.dt);
+        const double rden = den > 0.0 ? 1.0 / den : 0.0;
+        const double nu = sP * dB * rden;                     // pseudo-fission coefficient
+        const double omnu = den > 0.0 ? cv_dt * rden : 1.0;  // 1 - nu, formed without the difference
+        // sigma~_E - nu sigma_E = sigma_E (1 - nu) + 1/(c dt) and sigma_P B + nu q_T0 =
+        // sigma_P B (1 - nu) + nu C_v/dt (T* - T): where sigma_P dB >> C_v/dt
+        // (optically thick, nu -> 1) the printed differences cancel catastrophically
+        // and the Newton iterates would inherit their rounding
+        aE[n] = G.m * G.c * (sE * omnu + inv_cdt);
+        bE[n] = G.m * (sP * B0 * omnu + nu * cv_dt * (Ts[n] - Tn) + Es[n] / A.dt);
     }
     if (A.R0) {
         // consistent method: face and boundary corrections (the inflow included)

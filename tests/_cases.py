@@ -88,19 +88,34 @@ def run_oracle(case: Case):
     return I, mom, clo
 
 
-def cell_elem_err(got, ref, cell_floor=1e-2, slice_floor=1e-20):
+#: unit roundoff of the sweep precisions
+UNIT_ROUNDOFF = {64: 2.0 ** -53, 32: 2.0 ** -24}
+
+
+def elem_bound(cfg, precision, rel_tol):
+    """(relative, cell) coefficients of the element-wise intensity bound
+    |got - ref| <= r |ref| + a max|ref over the element's cell|:
+    r = max(rel_tol, 2 u (nx + ny)) -- a cell solve errs by a few units of
+    roundoff of its inputs and those errors add up along an upwind path of at
+    most nx + ny cells (the contraction factor is at most 1) -- and a = 64 u,
+    the cancellation inside one lumped cell solve (no positivity fix-up: a
+    node can pass through zero while its cell's other nodes set the scale)."""
+    u = UNIT_ROUNDOFF[precision]
+    path = cfg.nx + (cfg.ny if cfg.dim == 2 else 0)
+    return max(rel_tol, 2.0 * u * path), 64.0 * u
+
+
+def cell_elem_err(got, ref, rel, cell):
     """Element-wise intensity error of [..][cell][node] arrays (leading axes:
-    direction, group): max |got - ref| / (|ref| + cell_floor * the largest |ref|
-    at the nodes of the element's cell + slice_floor * the largest |ref| of
-    its (direction, group) slice).  The cell term is the local magnitude: the
-    lumped solution has no positivity fix-up and can pass through zero inside a
-    cell, where a relative error is meaningless but the cell's other nodes still
-    set the scale; the slice term only keeps values below the FP32 range out."""
+    direction, group) against the bound of elem_bound: max |got - ref| /
+    (rel |ref| + cell * the largest |ref| at the nodes of the element's cell
+    + 1e-30 * the largest |ref| of its slice, which only keeps values below
+    the FP32 range out); at most 1 when the bound holds."""
     got = np.asarray(got, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
     a = np.abs(ref)
-    scale = (a + cell_floor * a.max(axis=-1, keepdims=True) +
-             slice_floor * a.max(axis=(-2, -1), keepdims=True) + 1e-300)
+    scale = (rel * a + cell * a.max(axis=-1, keepdims=True) +
+             1e-30 * a.max(axis=(-2, -1), keepdims=True) + 1e-300)
     return float(np.max(np.abs(got - ref) / scale))
 
 
@@ -114,16 +129,20 @@ def field_err(got, ref, scale_field=None, axis=None):
     return float(np.max(d.max(axis=red) / np.maximum(np.abs(sc).max(axis=red), 1e-300)))
 
 
-def parity_errors(cfg, gpu, ref):
+def parity_errors(cfg, gpu, ref, precision=None, rel_tol=None):
     """Per-field relative errors of (intensity, moments, closures); intensity
-    None skips its two entries."""
+    None skips its entries.  With precision and rel_tol, "I_elem" is the ratio
+    of the largest element-wise intensity error to its bound (elem_bound),
+    scaled by rel_tol so that it compares with the same bar as the fields."""
     Ig, mg, cg = gpu
     Io, mo, co = ref
     dim = cfg.dim
     e = {}
     if Ig is not None:
         e["I"] = field_err(Ig, Io, axis=2)  # per (d, g) slice
-        e["I_elem"] = cell_elem_err(Ig, Io)
+        if precision is not None:
+            r, a = elem_bound(cfg, precision, rel_tol)
+            e["I_elem"] = rel_tol * cell_elem_err(Ig, Io, r, a)
     if dim == 2:
         phi, se = 0, 6
         groups = {"phi": [0], "F,T": [1, 2, 3, 4, 5], "SE": [6], "SF": [7, 8]}

@@ -26,7 +26,7 @@ import pytest
 import oracle as O
 from paper_2504_21784_gb300 import workloads as W
 
-from _cases import cell_elem_err, parity_errors
+from _cases import cell_elem_err, elem_bound, parity_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -69,11 +69,13 @@ def _oracle_by_direction(cfg, T, sigma, gen, on_direction):
 
 
 class _IntensityErrors:
-    """Largest per-(direction, group) field error of each GPU result, and the
-    largest element-wise error (cell_elem_err)."""
+    """Largest per-(direction, group) field error of each GPU result (keyed
+    by sweep precision), and the largest element-wise error against its bound
+    (_cases.elem_bound), scaled by the precision's bar."""
 
-    def __init__(self, runs):
-        self.runs = runs                      # {label: unpacked device intensity}
+    def __init__(self, runs, cfg):
+        self.runs = runs                      # {precision: unpacked device intensity}
+        self.cfg = cfg
         self.err = {k: 0.0 for k in runs}
         self.elem = {k: 0.0 for k in runs}
 
@@ -83,7 +85,8 @@ class _IntensityErrors:
             got = Iu[d].cpu().numpy()
             diff = np.abs(got - I_d).max(axis=(1, 2))
             self.err[k] = max(self.err[k], float((diff / scale).max()))
-            self.elem[k] = max(self.elem[k], cell_elem_err(got, I_d))
+            r, a = elem_bound(self.cfg, k, TOL[k])
+            self.elem[k] = max(self.elem[k], TOL[k] * cell_elem_err(got, I_d, r, a))
 
 
 def _gpu_sweep(sm, cfg, precision, T, sigma, canon, scale=None):
@@ -122,7 +125,7 @@ def _full_sweep_parity(sm, cfg, seed):
         rest[prec] = (mg, cg, sig_g, tiling)
     del canon
     torch.cuda.empty_cache()
-    ierr = _IntensityErrors(runs)
+    ierr = _IntensityErrors(runs, cfg)
     mo, co = _oracle_by_direction(cfg, T, sigma, gen, ierr)
     for prec in (32, 64):
         mg, cg, sig_g, tiling = rest[prec]
@@ -181,7 +184,7 @@ def test_batched_full_size_parity(gpu_lib):
     worst = {}
     for i, (cfg, h) in enumerate(zip(cfgs, b.members)):
         Tn, sig, gen = inputs[i]
-        ierr = _IntensityErrors({32: h.unpack(Io[i])})
+        ierr = _IntensityErrors({32: h.unpack(Io[i])}, cfg)
         mo, co = _oracle_by_direction(cfg, Tn, sig, gen, ierr)
         e = parity_errors(cfg, (None, M[i].cpu().numpy(), C[i].cpu().numpy()), (None, mo, co))
         e["I"] = ierr.err[32]

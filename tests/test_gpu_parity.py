@@ -12,10 +12,12 @@ magnitude of its field -- one (direction, group) slice of the intensity, one
 moment component (F and T are measured against phi, SF against SE, as they
 vanish near equilibrium).  The intensity is also bounded element by element
 ("I_elem"): each node's error against its own magnitude plus 1e-2 of the
-largest magnitude at its cell's nodes (the lumped-DG solution has no
-positivity fix-up and can pass through zero inside a cell, where dividing by
-the element itself is meaningless), so cells far below their slice's maximum
-are held to the same relative bar.  sigma_E = SE/phi is compared weighted by
+largest magnitude at its cell's nodes times 64 units of roundoff (the
+lumped-DG solution has no positivity fix-up and can pass through zero inside
+a cell, where dividing by the element itself is meaningless), with the
+relative part max(bar, 2 u (nx + ny)) -- per-cell roundoff adding up along an
+upwind path (_cases.elem_bound) -- so cells far below their slice's maximum
+are held to a relative bar too.  sigma_E = SE/phi is compared weighted by
 phi for the same reason, the additive correction against sigma_F * phi.
 """
 import numpy as np
@@ -58,7 +60,7 @@ def _check_all(case, precision, label):
     rtol = TOL[precision]
     Ig, mg, cg, _ = run_gpu(case)
     ref = run_oracle(case)
-    e = parity_errors(case.cfg, (Ig, mg, cg), ref)
+    e = parity_errors(case.cfg, (Ig, mg, cg), ref, precision, rtol)
     print(f"[{label} fp{precision}] " + "  ".join(f"{k} {v:.2e}" for k, v in e.items()) +
           f"  ({case.prob.info['n_tasks']} tasks, {case.prob.info['n_strips']} strips)")
     bad = {k: v for k, v in e.items() if not v <= rtol}
