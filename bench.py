@@ -432,61 +432,87 @@ def batched_metric(sm, W, stream, steps: int, warmup: int):
     """The 64-problem batched workload (uneven 32^2..256^2 meshes, 8-32
     groups, 32/64/128 directions, blocky two-material layouts), FP32 sweep:
     whole passes of sm_batch_sweep (prologue, emissions, ONE persistent
-    sweep launch, reductions; replayed from CUDA graphs, the two intensity
-    buffers alternating) after autotuning the batch tiling, against the same
-    problems swept one after another through sm_sweep."""
+    sweep launch with fused moments, moment sums and closures; replayed from
+    CUDA graphs, the two intensity buffers alternating) after autotuning the
+    batch tiling; the batched sweep kernel's own time from live profiled
+    passes (CUDA events) and its share of the measured HBM copy bandwidth;
+    the same problems swept one after another through sm_sweep; and seconds
+    per batched time step (sm_batch_step, FP32 sweep / FP64 low-order, the
+    paper's iteration controls) from the equilibrium start."""
     import torch
     members = W.batched_2d()
     cfgs = [m.cfg for m in members]
     upd = float(sum(c.n_cells * c.n_dir * c.n_groups for c in cfgs))
+    alg = sum(algorithmic_bytes(c, 32)["per_launch"] for c in cfgs)
+    peak, peak_kind = measured_peaks()
     out = {"workload": "batched2d_64x(32..256)^2x(32..128)x(8..32)", "problems": len(cfgs),
            "updates_per_pass": upd}
     with torch.cuda.stream(stream):
-        b = sm.Batch(cfgs, 32, stream=stream)
-        T, S, I0, I1 = [], [], [], []
+        gw = sm.tune_batch_slots(cfgs, 32, reps=2, stream=stream)  # slots per lane
+        b = sm.Batch(cfgs, 32, stream=stream, groups_per_warp=gw)
+        out["slots_per_lane"] = {str(v): gw.count(v) for v in sorted(set(gw))}
+        T, S, I0, I1, M, C = [], [], [], [], [], []
         for mem, h in zip(members, b.members):
             t = torch.from_numpy(W.temperature_wave(mem.cfg)).cuda()
             T.append(t)
             S.append(h.opacity(t, torch.from_numpy(mem.scale).cuda()))
             I0.append(h.empty_intensity())
             I1.append(h.empty_intensity())
-        b.sweep(T, S, None, I0, None, None)
+            M.append(h.new_moments())
+            C.append(h.new_closures())
+        b.sweep(T, S, None, I0, M, C)
         b.synchronize()
         b.autotune(T, S, I0, I1, reps=1)
         bufs = [I0, I1]
         for i in range(warmup):
-            b.sweep(T, S, bufs[i % 2], bufs[(i + 1) % 2], None, None)
+            b.sweep(T, S, bufs[i % 2], bufs[(i + 1) % 2], M, C)
         b.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for i in range(steps):
-            b.sweep(T, S, bufs[i % 2], bufs[(i + 1) % 2], None, None)
+            b.sweep(T, S, bufs[i % 2], bufs[(i + 1) % 2], M, C)
         ev1.record(stream)
         ev1.synchronize()
         b.synchronize()
         ms = ev0.elapsed_time(ev1) / steps
+        # the batched sweep kernel alone: live passes with events around it
+        b.set_profiling(True)
+        for i in range(steps):
+            b.sweep(T, S, bufs[i % 2], bufs[(i + 1) % 2], M, C)
+        kt = b.kernel_times()
+        b.set_profiling(False)
+        b.synchronize()
+        sweep_ms = kt["sweep_ms"] / max(kt["count"], 1)
+        achieved = alg / (sweep_ms * 1e-3) / 1e9
         info = b.info()
         out.update({"value": upd / (ms * 1e-3), "unit": "cell-dir-group updates/s",
-                    "ms_per_pass": ms,
+                    "ms_per_pass": ms, "pass": "emission + batched sweep with fused moments + "
+                    "moment sums and closures (graph replay)",
+                    "kernel_ms": {"emission": kt["emission_ms"] / max(kt["count"], 1),
+                                  "sweep": sweep_ms,
+                                  "reduce_closures": kt["reduce_ms"] / max(kt["count"], 1)},
+                    "roofline": {"bound": "hbm", "kernel": "sweep2d_batch_kernel",
+                                 "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                 "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                                 "algorithmic_bytes": alg},
                     "tiling": {"strip_width": info["strip_width"],
                                "prefetch_rows": info["prefetch_rows"],
                                "resident_ctas": info["resident_ctas"],
                                "queue_items": info["n_tasks"]},
                     "launches_per_pass": 2 + 2 * len(cfgs), "graph": "replayed"})
         del I1
-        b.close()
         # the same problems one after another (single-problem sweeps)
         probs = [sm.Problem.from_config(c, 32, stream=stream) for c in cfgs]
         Io = [p.empty_intensity() for p in probs]
-        for p, t, s_, io in zip(probs, T, S, Io):
-            p.sweep(t, s_, None, io)
+        for p, t, s_, io, m_, c_ in zip(probs, T, S, Io, M, C):
+            p.sweep(t, s_, None, io, m_, c_)
         torch.cuda.synchronize()
         reps = max(1, steps // 2)
         ev0.record(stream)
         for _ in range(reps):
-            for p, t, s_, io in zip(probs, T, S, Io):
-                p.sweep(t, s_, None, io)
+            for p, t, s_, io, m_, c_ in zip(probs, T, S, Io, M, C):
+                p.sweep(t, s_, None, io, m_, c_)
         ev1.record(stream)
         ev1.synchronize()
         ms_seq = ev0.elapsed_time(ev1) / reps
@@ -494,8 +520,51 @@ def batched_metric(sm, W, stream, steps: int, warmup: int):
         out["batched_speedup"] = ms_seq / ms
         for p in probs:
             p.close()
+        del Io, M, C
+        torch.cuda.empty_cache()
+        out["step"] = batched_step_metric(sm, W, b, members, stream)
+        b.close()
     torch.cuda.empty_cache()
     return out
+
+
+def batched_step_metric(sm, W, b, members, stream, n_steps: int = 3):
+    """Seconds per time step of all 64 members through sm_batch_step (FP32
+    sweep, FP64 low-order, the paper's iteration controls) from the
+    equilibrium start T = T0, I = B_g(T0)/4pi; one warm-up step, then
+    n_steps timed steps."""
+    import torch
+    st = []
+    for mem, h in zip(members, b.members):
+        cfg = mem.cfg
+        nc = cfg.n_cells
+        T = torch.full((nc, 4), cfg.T0, dtype=torch.float64, device="cuda")
+        ones = torch.ones((cfg.n_groups, nc), dtype=torch.float64, device="cuda")
+        bq = h.emission(T, ones)  # unit opacity: B_g(T0)/4pi per node
+        I = [h.pack(bq.unsqueeze(0).expand(cfg.n_dir, -1, -1, -1).contiguous()),
+             h.empty_intensity()]
+        mom = h.new_moments()
+        mom.zero_()
+        mom[..., 0] = cfg.a * cfg.c * cfg.T0 ** 4
+        st.append(dict(scale=torch.from_numpy(mem.scale).cuda(),
+                       cv=torch.full((nc, 4), cfg.cv, dtype=torch.float64, device="cuda"),
+                       T=T, E=h.new_nodal(), F=h.new_flux(), mom=mom, I=I))
+    secs, outer = [], []
+    for k in range(1 + n_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stats = b.step([s["scale"] for s in st], [s["cv"] for s in st], [s["T"] for s in st],
+                       [s["E"] for s in st], [s["F"] for s in st], [s["mom"] for s in st],
+                       [s["I"][k % 2] for s in st], [s["I"][(k + 1) % 2] for s in st])
+        torch.cuda.synchronize()
+        if k >= 1:
+            secs.append(time.perf_counter() - t0)
+            outer.append(max(x["outer_iters"] for x in stats))
+    return {"s_per_step": sum(secs) / len(secs), "members": len(st),
+            "outer_iters_max_per_step": outer,
+            "converged": all(x["converged"] for x in stats),
+            "method": "sm_batch_step: FP32 sweep / FP64 low-order, paper controls",
+            "state": "equilibrium start, steps 2..%d" % (n_steps + 1)}
 
 
 def adjoint_metric(sm, W, fd_cells: int, warm: bool = False):

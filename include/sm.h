@@ -393,9 +393,9 @@ sm_status sm_create_batch(const sm_problem_desc *descs, int n, void *stream, sm_
 sm_status sm_destroy_batch(sm_batch *b);
 /* Borrowed handle of member i, for sm_get_info, sm_get_quadrature,
  * sm_opacity, sm_emission, sm_closures, sm_pack_intensity and
- * sm_unpack_intensity.  sm_sweep, sm_sweep_host, sm_autotune, sm_set_tiling
- * and sm_destroy_problem refuse batch members (INVALID_ARG): their wavefront
- * counters belong to the batch. */
+ * sm_unpack_intensity.  sm_sweep, sm_sweep_host, sm_autotune, sm_set_tiling,
+ * sm_step and sm_destroy_problem refuse batch members (INVALID_ARG): their
+ * wavefront counters belong to the batch; sm_batch_step advances them. */
 sm_status sm_batch_problem(sm_batch *b, int i, sm_problem **out);
 sm_status sm_batch_get_info(const sm_batch *b, sm_batch_info *out);
 sm_status sm_batch_set_stream(sm_batch *b, void *stream);
@@ -422,6 +422,51 @@ sm_status sm_batch_synchronize(sm_batch *b);
 sm_status sm_batch_autotune(sm_batch *b, const double *const *T_nodal_dev,
                             const double *const *sigma_dev, const void *const *I_prev_dev,
                             void *const *I_out_dev, int reps);
+
+/* Slots per lane -- the (direction, group) pairs each lane of a warp task
+ * carries, i.e. the (d,g) work per CTA -- for the members of a batch,
+ * picked by timing (this library's autotuner; the packed layout depends on
+ * it, so it is chosen before the batch is created): for each cap c = 8, 4,
+ * 2, 1 a temporary batch is built from descs whose members take min(c,
+ * their automatic choice), its strip width and prefetch depth are autotuned,
+ * and reps passes are timed on synthetic inputs (T = 1, unit opacity, zero
+ * intensities; the sweep's cost does not depend on the values).  The
+ * members' slots of the fastest cap go to gw_out[i] (n entries), for use as
+ * descs[i].groups_per_warp; members whose descriptor fixes groups_per_warp
+ * keep it.  Allocates and frees its temporary buffers.  Synchronous. */
+sm_status sm_batch_tune_slots(const sm_problem_desc *descs, int n, void *stream, int reps,
+                              int *gw_out);
+
+/* Kernel timing of batched passes with CUDA events on the batch's stream.
+ * While enabled, each pass runs live (launched directly, not replayed from a
+ * graph) with events around its three stages, for up to 4096 passes;
+ * sm_batch_get_kernel_times synchronizes and returns the summed milliseconds
+ * and the number of passes timed, then resets them.  ms_host[0] = prologue,
+ * moment clearing and emissions, [1] = the batched sweep kernel, [2] =
+ * moment sums and closures. */
+sm_status sm_batch_set_profiling(sm_batch *b, int enable);
+sm_status sm_batch_get_kernel_times(sm_batch *b, double *ms_host, int *count_host);
+
+/* One time step of Algorithm 1 for every member of the batch (the batched
+ * form of sm_step, independent closures): per outer iteration ONE batched
+ * pass (emission, the persistent sweep launch over all unconverged members,
+ * moments and closures, replayed from a CUDA graph), then each unconverged
+ * member's FP64 low-order Newton solve (one cooperative launch each, queued
+ * without host waits) and its change of u = (T, E); one host
+ * synchronisation per outer iteration.  Each member stops by
+ * Eq. relative_tol on its own, exactly as sm_step would: a converged member
+ * is skipped by later passes (its tasks, emission and reductions are masked
+ * on the device, so the recorded graphs stay valid) and keeps the results
+ * of its last iteration.  Each argument is a HOST array of n device
+ * pointers laid out as sm_step's (I_prev[i], I_next[i] packed in member i's
+ * layout; closures may be NULL or hold NULL entries: the library's own
+ * buffer).  stats_host (may be NULL) receives n entries.  Errors as sm_step,
+ * plus UNSUPPORTED for params->method = SM_METHOD_CONSISTENT.  Synchronous. */
+sm_status sm_batch_step(sm_batch *b, const double *const *scale_dev, const double *const *cv_dev,
+                        double *const *T_dev, double *const *E_dev, double *const *F_dev,
+                        double *const *moments_dev, const void *const *I_prev_dev,
+                        void *const *I_next_dev, double *const *closures_dev,
+                        const sm_step_params *params_host, sm_step_stats *stats_host);
 
 /* ------------------------------------------------------------------------
  * Time-dependent high-order problem and its discrete adjoint: the gradient

@@ -36,7 +36,8 @@ EXPORTED = ["sm_create_problem", "sm_destroy_problem", "sm_get_info", "sm_set_st
             "sm_create_batch", "sm_destroy_batch", "sm_batch_problem", "sm_batch_get_info",
             "sm_batch_set_stream", "sm_batch_set_tiling", "sm_batch_sweep",
             "sm_batch_synchronize", "sm_batch_autotune", "sm_ho_step", "sm_leakage",
-            "sm_adjoint_step", "sm_set_quadrant_moments"]
+            "sm_adjoint_step", "sm_set_quadrant_moments", "sm_batch_step",
+            "sm_batch_set_profiling", "sm_batch_get_kernel_times", "sm_batch_tune_slots"]
 
 
 class SMError(RuntimeError):
@@ -159,6 +160,11 @@ def load():
         "sm_batch_sweep": [P, PP, PP, PP, PP, PP, PP],
         "sm_batch_synchronize": [P],
         "sm_batch_autotune": [P, PP, PP, PP, PP, I],
+        "sm_batch_step": [P, PP, PP, PP, PP, PP, PP, PP, PP, PP, ctypes.POINTER(StepParams),
+                          ctypes.POINTER(StepStats)],
+        "sm_batch_set_profiling": [P, I],
+        "sm_batch_tune_slots": [ctypes.POINTER(ProblemDesc), I, P, I, ctypes.POINTER(ctypes.c_int)],
+        "sm_batch_get_kernel_times": [P, PD, ctypes.POINTER(ctypes.c_int)],
         "sm_ho_step": [P, P, P, P, P, P, D, I, ctypes.POINTER(ctypes.c_int)],
         "sm_set_quadrant_moments": [P, P],
         "sm_leakage": [P, P, PD],
@@ -506,7 +512,9 @@ class Batch:
     (``sm_batch_*``); each pass is recorded once as a CUDA graph per buffer
     set and replayed afterwards."""
 
-    def __init__(self, cfgs, precision: int = 32, stream=None):
+    def __init__(self, cfgs, precision: int = 32, stream=None, groups_per_warp=None):
+        """groups_per_warp: None (each member's automatic choice) or one value
+        per member (e.g. from tune_batch_slots)."""
         import torch
         lib = load()
         self._torch = torch
@@ -514,6 +522,8 @@ class Batch:
         descs = (ProblemDesc * len(cfgs))()
         for i, cfg in enumerate(cfgs):
             descs[i] = _desc_of(cfg, precision, keep)
+            if groups_per_warp is not None:
+                descs[i].groups_per_warp = int(groups_per_warp[i])
         if stream is None:
             stream = torch.cuda.current_stream()
         self._stream = stream
@@ -549,6 +559,31 @@ class Batch:
     def synchronize(self):
         _check(load().sm_batch_synchronize(self._h))
 
+    def set_profiling(self, on: bool):
+        _check(load().sm_batch_set_profiling(self._h, 1 if on else 0))
+
+    def kernel_times(self) -> dict:
+        """Summed milliseconds of the timed passes: prologue and emissions,
+        the batched sweep kernel, moment sums and closures."""
+        ms = (ctypes.c_double * 3)()
+        cnt = ctypes.c_int()
+        _check(load().sm_batch_get_kernel_times(self._h, ms, ctypes.byref(cnt)))
+        return {"emission_ms": ms[0], "sweep_ms": ms[1], "reduce_ms": ms[2], "count": cnt.value}
+
+    def step(self, scale, cv, T, E, F, moments, I_prev, I_next, closures=None,
+             params: Optional[StepParams] = None) -> list:
+        """One time step of Algorithm 1 for every member (sm_batch_step): lists
+        of tensors, one per member, updated in place as by Problem.step.
+        Returns the per-member iteration counts."""
+        n = len(self.members)
+        st = (StepStats * n)()
+        cl = _ptr_array(closures) if closures is not None else None
+        keep = [_ptr_array(scale), _ptr_array(cv), _ptr_array(T), _ptr_array(E), _ptr_array(F),
+                _ptr_array(moments), _ptr_array(I_prev), _ptr_array(I_next), cl]
+        _check(load().sm_batch_step(self._h, *keep,
+                                    ctypes.byref(params) if params is not None else None, st))
+        return [_stats(st[i]) for i in range(n)]
+
     def autotune(self, T, sigma, I_prev, I_out, reps: int = 2):
         n = len(self.members)
         Ip = _ptr_array(I_prev if I_prev is not None else [None] * n)
@@ -569,6 +604,22 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def tune_batch_slots(cfgs, precision: int = 32, reps: int = 2, stream=None) -> list:
+    """Slots per lane for the members of a batch, picked by timing
+    (sm_batch_tune_slots); pass the result to Batch(groups_per_warp=...)."""
+    import torch
+    keep = []
+    descs = (ProblemDesc * len(cfgs))()
+    for i, cfg in enumerate(cfgs):
+        descs[i] = _desc_of(cfg, precision, keep)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    out = (ctypes.c_int * len(cfgs))()
+    _check(load().sm_batch_tune_slots(descs, len(cfgs), ctypes.c_void_p(stream.cuda_stream),
+                                      int(reps), out))
+    return list(out)
 
 
 def sweep_static(cfg, precision: int, T, sigma, I_prev, I_out, moments=None, closures=None,

@@ -36,6 +36,8 @@ struct sm_batch {
     std::vector<cudaEvent_t> ev;     // fork / join events
     unsigned int *d_ctrl = nullptr;  // [CTRL_WORDS], shared with every member
     unsigned long long *d_epoch = nullptr;
+    int *d_active = nullptr;         // [n] member swept by the next pass (1) or skipped (0)
+    bool all_active = true;          // d_active holds all ones
     int2 *d_tasks = nullptr;
     int n_tasks = 0, tasks_cap = 0;
     int W = 8, S = 2, ring_gw = 1, resident = 0;
@@ -51,6 +53,12 @@ struct sm_batch {
     std::vector<Entry> cache;
     unsigned long long clock = 0;
     long long launches = 0;
+    // profiling: passes run live (not from a graph) with 4 events each around
+    // the emission, the batched sweep and the reductions
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    int n_timed = 0;
+    smk::SweepArgs *d_args_live = nullptr;
 };
 
 namespace {
@@ -181,20 +189,30 @@ std::vector<uintptr_t> make_key(const sm_batch *b, const Ptrs &q) {
     return k;
 }
 
-// Records the pass for the buffers q into a graph.
-sm_status record(sm_batch *b, const Ptrs &q, sm_batch::Entry &e) {
+// The members' sweep arguments for the buffers q.
+std::vector<smk::SweepArgs> member_args(const sm_batch *b, const Ptrs &q) {
     const size_t n = b->probs.size();
     std::vector<smk::SweepArgs> args(n);
     for (size_t i = 0; i < n; ++i) {
         args[i] = smk::make_sweep_args(b->probs[i], q.I_prev ? q.I_prev[i] : nullptr, q.I_out[i]);
         args[i].ctrl = b->d_ctrl;
+        args[i].active = b->d_active + i;
         // the members share one queue: the batch's task count decides
         args[i].publish = smk::publish_rows(b->n_tasks, b->resident);
     }
-    B_CUDA(cudaMalloc(&e.d_args, sizeof(smk::SweepArgs) * n));
-    B_CUDA(cudaMemcpy(e.d_args, args.data(), sizeof(smk::SweepArgs) * n, cudaMemcpyHostToDevice));
+    return args;
+}
+
+// Enqueues one pass on stream c (being captured, or live): prologue,
+// per-problem emission and moment clearing on parallel branches, the batched
+// sweep, per-problem moment sums and closures.  ev (live profiling only):
+// four timing events recorded before the emissions, around the sweep and
+// after the reductions.
+sm_status enqueue_pass(sm_batch *b, const Ptrs &q, const smk::SweepArgs *d_args,
+                       cudaStream_t c, cudaEvent_t *ev) {
+    const size_t n = b->probs.size();
     smk::BatchSweepArgs B;
-    B.args = e.d_args;
+    B.args = d_args;
     B.tasks = b->d_tasks;
     B.n_tasks = b->n_tasks;
     B.W = b->W;
@@ -204,8 +222,7 @@ sm_status record(sm_batch *b, const Ptrs &q, sm_batch::Entry &e) {
     B.ctrl = b->d_ctrl;
     B.epoch = b->d_epoch;
     const int grid = std::min(b->n_tasks, b->resident);
-    cudaStream_t c = b->cap;
-    B_CUDA(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal));
+    if (ev) B_CUDA(cudaEventRecord(ev[0], c));
     smk::batch_prologue_kernel<<<1, 1, 0, c>>>(b->d_ctrl, b->d_epoch);
     // per-problem emission and moment clearing on parallel branches
     B_CUDA(cudaEventRecord(b->ev[0], c));
@@ -214,13 +231,15 @@ sm_status record(sm_batch *b, const Ptrs &q, sm_batch::Entry &e) {
         sm_problem *p = b->probs[i];
         cudaStream_t s = b->side[i % N_SIDE];
         B_CUDA(cudaMemsetAsync(p->d_mom_acc, 0, (size_t)p->ncell * 36 * p->rsize, s));
-        B_CUDA(smk::launch_emission(p, q.T[i], q.sigma[i], nullptr, s));
+        B_CUDA(smk::launch_emission(p, q.T[i], q.sigma[i], nullptr, s, b->d_active + i));
     }
     for (int k = 0; k < N_SIDE; ++k) {
         B_CUDA(cudaEventRecord(b->ev[1 + k], b->side[k]));
         B_CUDA(cudaStreamWaitEvent(c, b->ev[1 + k], 0));
     }
+    if (ev) B_CUDA(cudaEventRecord(ev[1], c));
     B_CUDA(smk::launch_sweep2d_batch(b->prec, B, grid, b->smem, c));
+    if (ev) B_CUDA(cudaEventRecord(ev[2], c));
     // per-problem moment sums and closures
     B_CUDA(cudaEventRecord(b->ev[0], c));
     for (int k = 0; k < N_SIDE; ++k) B_CUDA(cudaStreamWaitEvent(b->side[k], b->ev[0], 0));
@@ -228,18 +247,76 @@ sm_status record(sm_batch *b, const Ptrs &q, sm_batch::Entry &e) {
         sm_problem *p = b->probs[i];
         double *m = (q.mom && q.mom[i]) ? q.mom[i] : p->d_mom_tmp;
         B_CUDA(smk::launch_reduce(p, p->d_mom_acc, 1, m, q.clo ? q.clo[i] : nullptr,
-                                  b->side[i % N_SIDE]));
+                                  b->side[i % N_SIDE], nullptr, 1, b->d_active + i));
     }
     for (int k = 0; k < N_SIDE; ++k) {
         B_CUDA(cudaEventRecord(b->ev[1 + k], b->side[k]));
         B_CUDA(cudaStreamWaitEvent(c, b->ev[1 + k], 0));
     }
-    B_CUDA(cudaStreamEndCapture(c, &e.graph));
+    if (ev) B_CUDA(cudaEventRecord(ev[3], c));
+    return SM_OK;
+}
+
+// Records the pass for the buffers q into a graph.
+sm_status record(sm_batch *b, const Ptrs &q, sm_batch::Entry &e) {
+    const size_t n = b->probs.size();
+    const std::vector<smk::SweepArgs> args = member_args(b, q);
+    B_CUDA(cudaMalloc(&e.d_args, sizeof(smk::SweepArgs) * n));
+    B_CUDA(cudaMemcpy(e.d_args, args.data(), sizeof(smk::SweepArgs) * n, cudaMemcpyHostToDevice));
+    cudaStream_t c = b->cap;
+    B_CUDA(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal));
+    const sm_status st = enqueue_pass(b, q, e.d_args, c, nullptr);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(c, &g);
+    e.graph = g;
+    if (st != SM_OK) return st;
+    B_CUDA(ce);
     B_CUDA(cudaGraphInstantiate(&e.exec, e.graph, 0));
     return SM_OK;
 }
 
+// One pass launched directly on the batch's stream with timing events.
+sm_status run_live(sm_batch *b, const Ptrs &q) {
+    const size_t n = b->probs.size();
+    if (!b->d_args_live) B_CUDA(cudaMalloc(&b->d_args_live, sizeof(smk::SweepArgs) * n));
+    const std::vector<smk::SweepArgs> args = member_args(b, q);
+    // from pageable memory: staged before the call returns
+    B_CUDA(cudaMemcpyAsync(b->d_args_live, args.data(), sizeof(smk::SweepArgs) * n,
+                           cudaMemcpyHostToDevice, b->stream));
+    cudaEvent_t *ev = nullptr;
+    if (b->n_timed < 4096) {
+        while ((int)b->ev_pool.size() < 4 * (b->n_timed + 1)) {
+            cudaEvent_t e;
+            B_CUDA(cudaEventCreate(&e));
+            b->ev_pool.push_back(e);
+        }
+        ev = &b->ev_pool[4 * b->n_timed++];
+    }
+    B_TRY(enqueue_pass(b, q, b->d_args_live, b->stream, ev));
+    b->launches += 2 + 2 * (long long)n;
+    return SM_OK;
+}
+
+// Which members the next pass sweeps (one flag per member; NULL: all).  The
+// flags live on the device, so the recorded graphs stay valid.
+sm_status set_active(sm_batch *b, const unsigned char *active) {
+    const size_t n = b->probs.size();
+    bool all = true;
+    if (active)
+        for (size_t i = 0; i < n; ++i) all = all && active[i];
+    if (all && b->all_active) return SM_OK;
+    std::vector<int> v(n, 1);
+    if (active)
+        for (size_t i = 0; i < n; ++i) v[i] = active[i] ? 1 : 0;
+    // from pageable memory: the call returns once v has been staged
+    B_CUDA(cudaMemcpyAsync(b->d_active, v.data(), sizeof(int) * n, cudaMemcpyHostToDevice,
+                           b->stream));
+    b->all_active = all;
+    return SM_OK;
+}
+
 sm_status run(sm_batch *b, const Ptrs &q) {
+    if (b->profiling) return run_live(b, q);
     std::vector<uintptr_t> key = make_key(b, q);
     sm_batch::Entry *hit = nullptr;
     for (auto &e : b->cache)
@@ -272,6 +349,30 @@ sm_status run(sm_batch *b, const Ptrs &q) {
 
 }  // namespace
 
+namespace smk {
+const std::vector<sm_problem *> &batch_members(const sm_batch *b) { return b->probs; }
+cudaStream_t batch_stream(const sm_batch *b) { return b->stream; }
+sm_status batch_pass(sm_batch *b, const double *const *T, const double *const *sigma,
+                     const void *const *I_prev, void *const *I_out, double *const *mom,
+                     double *const *clo, const unsigned char *active_host) {
+    const Ptrs q{T, sigma, I_prev, I_out, mom, clo};
+    B_TRY(check_ptrs(b, q));
+    B_TRY(set_active(b, active_host));
+    return run(b, q);
+}
+sm_status batch_status(sm_batch *b) {
+    unsigned int status = 0;
+    B_CUDA(cudaMemcpyAsync(&status, b->d_ctrl + smk::CTRL_STATUS, sizeof(status),
+                           cudaMemcpyDeviceToHost, b->stream));
+    B_CUDA(cudaStreamSynchronize(b->stream));
+    if (!status) return SM_OK;
+    B_CUDA(cudaMemsetAsync(b->d_ctrl + smk::CTRL_STATUS, 0, sizeof(unsigned int), b->stream));
+    if (status & smk::ST_TIMEOUT)
+        return b_fail(SM_ERR_TIMEOUT, "a wavefront wait exceeded its time limit");
+    return b_fail(SM_ERR_NONPHYSICAL, "non-positive or non-finite temperature");
+}
+}  // namespace smk
+
 extern "C" {
 
 sm_status sm_create_batch(const sm_problem_desc *descs, int n, void *stream, sm_batch **out) {
@@ -291,8 +392,12 @@ sm_status sm_create_batch(const sm_problem_desc *descs, int n, void *stream, sm_
         sm_destroy_batch(b);
         return s;
     };
+    const std::vector<int> ones(n, 1);
     if (cudaMalloc(&b->d_ctrl, smk::CTRL_WORDS * sizeof(unsigned int)) != cudaSuccess ||
         cudaMalloc(&b->d_epoch, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&b->d_active, sizeof(int) * n) != cudaSuccess ||
+        cudaMemcpy(b->d_active, ones.data(), sizeof(int) * n, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
         cudaMemset(b->d_ctrl, 0, smk::CTRL_WORDS * sizeof(unsigned int)) != cudaSuccess ||
         cudaMemset(b->d_epoch, 0, sizeof(unsigned long long)) != cudaSuccess)
         return bail(b_fail(SM_ERR_OOM, "batch control words"));
@@ -343,6 +448,9 @@ sm_status sm_destroy_batch(sm_batch *b) {
     if (b->d_tasks) cudaFree(b->d_tasks);
     if (b->d_ctrl) cudaFree(b->d_ctrl);
     if (b->d_epoch) cudaFree(b->d_epoch);
+    if (b->d_active) cudaFree(b->d_active);
+    if (b->d_args_live) cudaFree(b->d_args_live);
+    for (auto e : b->ev_pool) cudaEventDestroy(e);
     delete b;
     return SM_OK;
 }
@@ -387,6 +495,7 @@ sm_status sm_batch_sweep(sm_batch *b, const double *const *T_dev, const double *
     if (!b) return b_fail(SM_ERR_INVALID_ARG, "NULL batch");
     const Ptrs q{T_dev, sigma_dev, I_prev_dev, I_out_dev, moments_dev, closures_dev};
     B_TRY(check_ptrs(b, q));
+    B_TRY(set_active(b, nullptr));
     return run(b, q);
 }
 
@@ -405,12 +514,38 @@ sm_status sm_batch_synchronize(sm_batch *b) {
     return SM_OK;
 }
 
+sm_status sm_batch_set_profiling(sm_batch *b, int enable) {
+    if (!b) return b_fail(SM_ERR_INVALID_ARG, "NULL batch");
+    B_CUDA(cudaStreamSynchronize(b->stream));
+    b->profiling = enable != 0;
+    b->n_timed = 0;
+    return SM_OK;
+}
+
+sm_status sm_batch_get_kernel_times(sm_batch *b, double *ms, int *count) {
+    if (!b || !ms || !count) return b_fail(SM_ERR_INVALID_ARG, "NULL argument");
+    B_CUDA(cudaStreamSynchronize(b->stream));
+    ms[0] = ms[1] = ms[2] = 0.0;
+    for (int k = 0; k < b->n_timed; ++k) {
+        cudaEvent_t *ev = &b->ev_pool[4 * k];
+        for (int j = 0; j < 3; ++j) {
+            float t = 0.f;
+            B_CUDA(cudaEventElapsedTime(&t, ev[j], ev[j + 1]));
+            ms[j] += t;
+        }
+    }
+    *count = b->n_timed;
+    b->n_timed = 0;
+    return SM_OK;
+}
+
 sm_status sm_batch_autotune(sm_batch *b, const double *const *T_dev,
                             const double *const *sigma_dev, const void *const *I_prev_dev,
                             void *const *I_out_dev, int reps) {
     if (!b) return b_fail(SM_ERR_INVALID_ARG, "NULL batch");
     const Ptrs q{T_dev, sigma_dev, I_prev_dev, I_out_dev, nullptr, nullptr};
     B_TRY(check_ptrs(b, q));
+    B_TRY(set_active(b, nullptr));
     if (reps < 1) reps = 1;
     cudaEvent_t e0, e1;
     B_CUDA(cudaEventCreate(&e0));
@@ -443,6 +578,92 @@ sm_status sm_batch_autotune(sm_batch *b, const double *const *T_dev,
     cudaEventDestroy(e1);
     const sm_status st = set_tiling(b, bW, bS);
     return result != SM_OK ? result : st;
+}
+
+sm_status sm_batch_tune_slots(const sm_problem_desc *descs, int n, void *stream, int reps,
+                              int *gw_out) {
+    if (!descs || n < 1 || !gw_out) return b_fail(SM_ERR_INVALID_ARG, "descs, n >= 1, gw_out");
+    if (reps < 1) reps = 1;
+    // every member's automatic choice (the largest that its groups fill)
+    std::vector<int> auto_gw(n);
+    {
+        sm_batch *b = nullptr;
+        B_TRY(sm_create_batch(descs, n, stream, &b));
+        for (int i = 0; i < n; ++i) auto_gw[i] = b->probs[i]->GW;
+        sm_destroy_batch(b);
+    }
+    const int caps[] = {8, 4, 2, 1};
+    float best = 1e30f;
+    std::vector<int> best_gw(auto_gw);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    B_CUDA(cudaEventCreate(&e0));
+    B_CUDA(cudaEventCreate(&e1));
+    sm_status result = SM_OK;
+    for (int cap : caps) {
+        std::vector<sm_problem_desc> d(descs, descs + n);
+        std::vector<int> gw(n);
+        bool differs = cap == caps[0];
+        for (int i = 0; i < n; ++i) {
+            gw[i] = descs[i].groups_per_warp ? descs[i].groups_per_warp : std::min(cap, auto_gw[i]);
+            d[i].groups_per_warp = gw[i];
+            differs = differs || gw[i] != std::min(cap * 2, auto_gw[i]);
+        }
+        if (!differs) continue;  // the same layout as the previous cap
+        sm_batch *b = nullptr;
+        if ((result = sm_create_batch(d.data(), n, stream, &b)) != SM_OK) break;
+        // synthetic inputs: T = 1 at every node, unit opacity, zero intensities
+        std::vector<void *> owned;
+        std::vector<const double *> T(n), sg(n);
+        std::vector<const void *> Ip(n);
+        std::vector<void *> Io(n);
+        for (int i = 0; i < n && result == SM_OK; ++i) {
+            const sm_problem *p = b->probs[i];
+            const size_t nn = (size_t)p->ncell * p->nn, ng = (size_t)p->G * p->ncell;
+            const size_t ib = (size_t)p->NQ * p->NWT * p->ncell * p->GW * 32 * p->nn * p->rsize;
+            void *t = nullptr, *s = nullptr, *a = nullptr, *o = nullptr;
+            if (cudaMalloc(&t, nn * sizeof(double)) != cudaSuccess ||
+                cudaMalloc(&s, ng * sizeof(double)) != cudaSuccess ||
+                cudaMalloc(&a, ib) != cudaSuccess || cudaMalloc(&o, ib) != cudaSuccess) {
+                for (void *x : {t, s, a, o})
+                    if (x) cudaFree(x);
+                result = b_fail(SM_ERR_OOM, "slot tuning buffers");
+                break;
+            }
+            owned.insert(owned.end(), {t, s, a, o});
+            const std::vector<double> one(std::max(nn, ng), 1.0);
+            cudaMemcpy(t, one.data(), nn * sizeof(double), cudaMemcpyHostToDevice);
+            cudaMemcpy(s, one.data(), ng * sizeof(double), cudaMemcpyHostToDevice);
+            cudaMemset(a, 0, ib);
+            T[i] = static_cast<const double *>(t);
+            sg[i] = static_cast<const double *>(s);
+            Ip[i] = a;
+            Io[i] = o;
+        }
+        float ms = 1e30f;
+        if (result == SM_OK)
+            result = sm_batch_autotune(b, T.data(), sg.data(), Ip.data(), Io.data(), 1);
+        if (result == SM_OK) {
+            const Ptrs q{T.data(), sg.data(), Ip.data(), Io.data(), nullptr, nullptr};
+            result = run(b, q);  // warm-up (records the graph)
+            cudaEventRecord(e0, b->stream);
+            for (int r = 0; r < reps && result == SM_OK; ++r) result = run(b, q);
+            cudaEventRecord(e1, b->stream);
+            if (result == SM_OK) result = sm_batch_synchronize(b);
+            if (result == SM_OK) cudaEventElapsedTime(&ms, e0, e1);
+        }
+        sm_destroy_batch(b);
+        for (void *x : owned) cudaFree(x);
+        if (result != SM_OK) break;
+        if (ms < best) {
+            best = ms;
+            best_gw = gw;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (result != SM_OK) return result;
+    for (int i = 0; i < n; ++i) gw_out[i] = best_gw[i];
+    return SM_OK;
 }
 
 }  // extern "C"

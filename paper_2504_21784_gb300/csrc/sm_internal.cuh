@@ -55,6 +55,8 @@ struct SweepArgs {
                              // geometric quadrant q live at quadrant q^2 (adjoint sweeps)
     int qmom;                // 2D: accumulate moments per quadrant, [q][cell][36]
     int publish;             // 2D: rows per release of a strip's x-faces downwind
+    const int *active;       // batch member: its tasks are skipped while *active == 0
+                             // (NULL: always swept)
 };
 
 // Rows per release of a strip's x-faces to the downwind strip: the release
@@ -83,7 +85,7 @@ struct BatchSweepArgs {
 cudaError_t launch_opacity(const sm_problem *p, const double *T, const double *scale,
                            double *sigma, cudaStream_t s);
 cudaError_t launch_emission(const sm_problem *p, const double *T, const double *sigma,
-                            double *q_canon, cudaStream_t s);
+                            double *q_canon, cudaStream_t s, const int *active = nullptr);
 cudaError_t launch_inflow(const sm_problem *p, cudaStream_t s);
 cudaError_t launch_planck_parts(const sm_problem *p, const double *T, const double *sigma,
                                 double *B4, double *cB, double *sdB, cudaStream_t s);
@@ -95,7 +97,7 @@ cudaError_t launch_sweep2d(const sm_problem *p, const SweepArgs &a, int grid, cu
 cudaError_t launch_sweep1d(const sm_problem *p, const SweepArgs &a, cudaStream_t s);
 cudaError_t launch_reduce(const sm_problem *p, const void *part, int n_part, double *mom,
                           double *clo, cudaStream_t s, double *qmom = nullptr,
-                          int sets_per_q = 1);
+                          int sets_per_q = 1, const int *active = nullptr);
 cudaError_t launch_pack(const sm_problem *p, const double *canon, void *packed, int unpack,
                         cudaStream_t s);
 int sweep2d_max_resident(const sm_problem *p, int W, int S, size_t *smem_out);
@@ -121,12 +123,23 @@ sm_status sweep_only(sm_problem *p, const void *I_prev, void *I_out, double *mom
                      int reverse);
 // Free the adjoint workspace (no-op when unused).
 void adjoint_free(sm_problem *p);
+// The batch object as seen by the time step (sm_batch_step): its members, its
+// stream, one whole pass (graph replay) for the members whose active flag is
+// set (active_host: one flag per member; NULL: all), and the device status
+// of the last passes (SM_OK, TIMEOUT or NONPHYSICAL; cleared).
+const std::vector<sm_problem *> &batch_members(const sm_batch *b);
+cudaStream_t batch_stream(const sm_batch *b);
+sm_status batch_pass(sm_batch *b, const double *const *T, const double *const *sigma,
+                     const void *const *I_prev, void *const *I_out, double *const *mom,
+                     double *const *clo, const unsigned char *active_host);
+sm_status batch_status(sm_batch *b);
 // Tiling and sweep arguments of one problem (used by the batch object).
 sm_status apply_tiling_ext(sm_problem *p, int W, int S);
 SweepArgs make_sweep_args(const sm_problem *p, const void *I_prev, void *I_out);
 
 }  // namespace smk
 
+struct sm_batch;      // batched problems (sm_batch.cu)
 struct sm_lo_state;   // low-order solve workspace, created on first use
 struct sm_adj_state;  // adjoint workspace, created on first use
 

@@ -1364,9 +1364,9 @@ sm_status launch_newton(sm_problem *p, sm_lo_state &w, const Geo &G, const doubl
 // receive the result, F receives the flux of the last linear solve.  One
 // cooperative launch and one host synchronisation per solve.
 template <int NN>
-sm_status lo_solve(sm_problem *p, const double *clo, const double *Tstar, const double *cv,
-                   double *T, double *E, double *F, const sm_step_params &prm,
-                   sm_step_stats *st, const double *qmom) {
+sm_status lo_launch(sm_problem *p, const double *clo, const double *Tstar, const double *cv,
+                    double *T, double *E, double *F, const sm_step_params &prm,
+                    const double *qmom) {
     sm_lo_state &w = *p->lo;
     const Geo G = make_geo(p);
     cudaStream_t s = p->stream;
@@ -1390,7 +1390,13 @@ sm_status lo_solve(sm_problem *p, const double *clo, const double *Tstar, const 
     p->launches++;
     LO_TRY(launch_newton<NN>(p, w, G, clo, T, E, F, Tstar, cv, R0, prm));
     p->launches++;
-    LO_TRY(read_scalars(p));
+    return SM_OK;
+}
+
+// Status and statistics of the last low-order solve from the pinned mirror
+// of its scalars (the caller has copied and synchronized them).
+sm_status lo_collect(sm_problem *p, sm_step_stats *st) {
+    sm_lo_state &w = *p->lo;
     const smk::lo::Scalars &h = *w.h_sc;
     if (h.status == smk::lo::LO_TIMEOUT)
         return lo_fail(SM_ERR_TIMEOUT, "a grid barrier of the low-order kernel ran out of time");
@@ -1409,11 +1415,52 @@ sm_status lo_solve(sm_problem *p, const double *clo, const double *Tstar, const 
     return SM_OK;
 }
 
+// Launches a low-order solve without waiting for it.
+sm_status launch_lo(sm_problem *p, const double *clo, const double *Tstar, const double *cv,
+                    double *T, double *E, double *F, const sm_step_params &prm,
+                    const double *qmom) {
+    return p->dim == 2 ? lo_launch<4>(p, clo, Tstar, cv, T, E, F, prm, qmom)
+                       : lo_launch<2>(p, clo, Tstar, cv, T, E, F, prm, qmom);
+}
+
 sm_status run_lo(sm_problem *p, const double *clo, const double *Tstar, const double *cv,
                  double *T, double *E, double *F, const sm_step_params &prm, sm_step_stats *st,
                  const double *qmom) {
-    return p->dim == 2 ? lo_solve<4>(p, clo, Tstar, cv, T, E, F, prm, st, qmom)
-                       : lo_solve<2>(p, clo, Tstar, cv, T, E, F, prm, st, qmom);
+    LO_TRY(launch_lo(p, clo, Tstar, cv, T, E, F, prm, qmom));
+    LO_TRY(read_scalars(p));
+    return lo_collect(p, st);
+}
+
+// Start of a time step (Algorithm 1) for problem p, on its stream: sigma_g at
+// the step's start temperature (frozen for the step, Sec. 3 Rem. opacity),
+// the time-edge sources E* = phi/c, F* = F of the previous step's moments
+// (Sec. 6.1), T* = T^k, and the start of the outer iteration E = E*, T = T^k.
+sm_status step_begin(sm_problem *p, const double *scale, double *T, double *E,
+                     const double *moments) {
+    sm_lo_state &w = *p->lo;
+    cudaStream_t s = p->stream;
+    const int N = w.N;
+    LO_TRY(sm_opacity(p, T, scale, w.sigma));
+    smk::lo::timeedge_kernel<<<w.nblk_node, BLOCK, 0, s>>>(N, w.D, p->nm, 1.0 / p->desc.c,
+                                                          moments, w.Estar, w.Fstar);
+    LO_CUDA(cudaGetLastError());
+    p->launches++;
+    LO_CUDA(cudaMemcpyAsync(w.Tstar, T, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    LO_CUDA(cudaMemcpyAsync(w.Tin, T, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    LO_CUDA(cudaMemcpyAsync(w.Ein, w.Estar, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    LO_CUDA(cudaMemcpyAsync(E, w.Estar, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    return SM_OK;
+}
+
+// ||u - u_in|| and ||u|| of the outer iteration (u = (T, E)) into the
+// scalars, then u_in <- u.
+sm_status launch_outer_change(sm_problem *p, const double *T, const double *E) {
+    sm_lo_state &w = *p->lo;
+    smk::lo::outer_change_kernel<<<w.nblk_node, BLOCK, 0, p->stream>>>(w.N, T, E, w.Tin, w.Ein,
+                                                                      w.part, w.sc);
+    LO_CUDA(cudaGetLastError());
+    p->launches++;
+    return SM_OK;
 }
 
 sm_status check_lo_problem(sm_problem *p) {
@@ -1517,16 +1564,7 @@ sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, 
         qmom = qmom_saved ? qmom_saved : w.qmom_int;
         LO_TRY(sm_set_quadrant_moments(p, const_cast<double *>(qmom)));
     }
-    // opacities frozen at T^k for the whole step (Sec. 3, Rem. opacity)
-    LO_TRY(sm_opacity(p, T_dev, scale_dev, w.sigma));
-    smk::lo::timeedge_kernel<<<w.nblk_node, BLOCK, 0, s>>>(N, w.D, p->nm, 1.0 / p->desc.c,
-                                                          moments_dev, w.Estar, w.Fstar);
-    LO_CUDA(cudaGetLastError());
-    p->launches++;
-    LO_CUDA(cudaMemcpyAsync(w.Tstar, T_dev, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
-    LO_CUDA(cudaMemcpyAsync(w.Tin, T_dev, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
-    LO_CUDA(cudaMemcpyAsync(w.Ein, w.Estar, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
-    LO_CUDA(cudaMemcpyAsync(E_dev, w.Estar, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    LO_TRY(step_begin(p, scale_dev, T_dev, E_dev, moments_dev));
     sm_step_stats st{};
     double d1 = -1.0;
     for (int it = 1; it <= prm.max_outer; ++it) {
@@ -1534,10 +1572,7 @@ sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, 
         LO_TRY(sm_sweep(p, T_dev, w.sigma, I_prev_dev, I_next_dev, moments_dev, clo));
         LO_TRY(sm_synchronize(p));
         LO_TRY(run_lo(p, clo, w.Tstar, cv_dev, T_dev, E_dev, F_dev, prm, &st, qmom));
-        smk::lo::outer_change_kernel<<<w.nblk_node, BLOCK, 0, s>>>(N, T_dev, E_dev, w.Tin, w.Ein,
-                                                                  w.part, w.sc);
-        LO_CUDA(cudaGetLastError());
-        p->launches++;
+        LO_TRY(launch_outer_change(p, T_dev, E_dev));
         LO_TRY(read_scalars(p));
         st.outer_iters = it;
         const double dn = std::sqrt(w.h_sc->d2), un = std::sqrt(w.h_sc->n2);
@@ -1550,6 +1585,86 @@ sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, 
     }
     if (consistent && !qmom_saved) LO_TRY(sm_set_quadrant_moments(p, nullptr));
     if (stats) *stats = st;
+    return SM_OK;
+}
+
+sm_status sm_batch_step(sm_batch *b, const double *const *scale_dev,
+                        const double *const *cv_dev, double *const *T_dev, double *const *E_dev,
+                        double *const *F_dev, double *const *moments_dev,
+                        const void *const *I_prev_dev, void *const *I_next_dev,
+                        double *const *closures_dev, const sm_step_params *params,
+                        sm_step_stats *stats_host) {
+    if (!b || !scale_dev || !cv_dev || !T_dev || !E_dev || !F_dev || !moments_dev ||
+        !I_prev_dev || !I_next_dev)
+        return lo_fail(SM_ERR_INVALID_ARG, "NULL argument to sm_batch_step");
+    sm_step_params prm;
+    if (params)
+        prm = *params;
+    else
+        sm_default_step_params(&prm);
+    LO_TRY(check_params(prm));
+    if (prm.method != SM_METHOD_INDEPENDENT)
+        return lo_fail(SM_ERR_UNSUPPORTED, "sm_batch_step runs the independent method");
+    const std::vector<sm_problem *> &probs = smk::batch_members(b);
+    const int n = (int)probs.size();
+    for (int i = 0; i < n; ++i) {
+        if (!scale_dev[i] || !cv_dev[i] || !T_dev[i] || !E_dev[i] || !F_dev[i] ||
+            !moments_dev[i] || !I_prev_dev[i] || !I_next_dev[i])
+            return lo_fail(SM_ERR_INVALID_ARG,
+                           "member " + std::to_string(i) + ": NULL argument to sm_batch_step");
+        if (!aligned16(cv_dev[i]) || !aligned16(T_dev[i]) || !aligned16(E_dev[i]))
+            return lo_fail(SM_ERR_INVALID_ARG, "T, cv and E must be 16-byte aligned");
+        LO_TRY(check_lo_problem(probs[i]));
+    }
+    std::vector<const double *> sig(n);
+    std::vector<double *> clo(n);
+    for (int i = 0; i < n; ++i) {
+        sm_problem *p = probs[i];
+        sig[i] = p->lo->sigma;
+        clo[i] = closures_dev && closures_dev[i] ? closures_dev[i] : p->lo->clo;
+        LO_TRY(step_begin(p, scale_dev[i], T_dev[i], E_dev[i], moments_dev[i]));
+    }
+    std::vector<sm_step_stats> st(n);
+    std::vector<double> d1(n, -1.0);
+    std::vector<unsigned char> active(n, 1);
+    int n_active = n;
+    const cudaStream_t s = smk::batch_stream(b);
+    for (int it = 1; it <= prm.max_outer && n_active > 0; ++it) {
+        // high-order solve of every unconverged member in one batched pass
+        // (emission, one persistent sweep launch, moments, closures)
+        LO_TRY(smk::batch_pass(b, T_dev, sig.data(), I_prev_dev, I_next_dev, moments_dev,
+                               clo.data(), active.data()));
+        // their low-order solves, one cooperative launch each, queued on the
+        // batch's stream without waiting in between
+        for (int i = 0; i < n; ++i) {
+            if (!active[i]) continue;
+            sm_problem *p = probs[i];
+            sm_lo_state &w = *p->lo;
+            LO_TRY(launch_lo(p, clo[i], w.Tstar, cv_dev[i], T_dev[i], E_dev[i], F_dev[i], prm,
+                             nullptr));
+            LO_TRY(launch_outer_change(p, T_dev[i], E_dev[i]));
+            LO_CUDA(cudaMemcpyAsync(w.h_sc, w.sc, sizeof(smk::lo::Scalars),
+                                    cudaMemcpyDeviceToHost, s));
+        }
+        LO_TRY(smk::batch_status(b));  // synchronizes the stream
+        for (int i = 0; i < n; ++i) {
+            if (!active[i]) continue;
+            sm_problem *p = probs[i];
+            LO_TRY(lo_collect(p, &st[i]));
+            const double dn = std::sqrt(p->lo->h_sc->d2), un = std::sqrt(p->lo->h_sc->n2);
+            st[i].outer_iters = it;
+            st[i].last_change = dn;
+            if (d1[i] < 0) d1[i] = dn;
+            // Eq. relative_tol per member, with the round-off guard of sm_step
+            if (dn == 0.0 || dn < prm.eps_outer * d1[i] || dn <= 1e-14 * un) {
+                st[i].converged = 1;
+                active[i] = 0;
+                --n_active;
+            }
+        }
+    }
+    if (stats_host)
+        for (int i = 0; i < n; ++i) stats_host[i] = st[i];
     return SM_OK;
 }
 

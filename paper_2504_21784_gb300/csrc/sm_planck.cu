@@ -324,7 +324,8 @@ __global__ void emission_kernel(int ncell, int nn, int G, int Gp, const double *
                                 double acT4_scale, double inv_cdt, const double *__restrict__ T,
                                 const double *__restrict__ sigma, RT *__restrict__ src,
                                 double *__restrict__ gray, double *__restrict__ qcanon,
-                                unsigned int *ctrl) {
+                                unsigned int *ctrl, const int *__restrict__ member_on) {
+    if (member_on && *member_on == 0) return;  // a batch member that is not swept this pass
     extern __shared__ float s_edges[];
     for (int i = threadIdx.x; i <= G; i += 32) s_edges[i] = (float)edges[i];
     __syncwarp();
@@ -540,7 +541,7 @@ cudaError_t launch_opacity(const sm_problem *p, const double *T, const double *s
 }
 
 cudaError_t launch_emission(const sm_problem *p, const double *T, const double *sigma,
-                            double *q_canon, cudaStream_t s) {
+                            double *q_canon, cudaStream_t s, const int *active) {
     // one warp per block: node costs differ by up to ~2x (hot nodes have more
     // edges below the underflow point), and small blocks keep the last wave short
     const int threads = 32;
@@ -550,11 +551,11 @@ cudaError_t launch_emission(const sm_problem *p, const double *T, const double *
     if (p->prec == 32)
         emission_kernel<float><<<blocks, threads, (p->G + 1) * sizeof(float), s>>>(
             p->ncell, p->nn, p->G, p->Gp, p->d_edges, scale, p->inv_cdt, T, sigma,
-            (float *)p->d_src, p->d_gray, q_canon, p->d_ctrl);
+            (float *)p->d_src, p->d_gray, q_canon, p->d_ctrl, active);
     else
         emission_kernel<double><<<blocks, threads, (p->G + 1) * sizeof(float), s>>>(
             p->ncell, p->nn, p->G, p->Gp, p->d_edges, scale, p->inv_cdt, T, sigma,
-            (double *)p->d_src, p->d_gray, q_canon, p->d_ctrl);
+            (double *)p->d_src, p->d_gray, q_canon, p->d_ctrl, active);
     return cudaGetLastError();
 }
 

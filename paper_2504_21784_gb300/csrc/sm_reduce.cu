@@ -21,9 +21,9 @@ __global__ void reduce_kernel(int dim, int nnodes_total, int nm, int nsets, size
                               double inv_c, const RT *__restrict__ part,
                               const double *__restrict__ gray, double *__restrict__ mom,
                               double *__restrict__ clo, double *__restrict__ qmom,
-                              int sets_per_q) {
+                              int sets_per_q, const int *__restrict__ active) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;  // (cell, node)
-    if (t >= nnodes_total) return;
+    if (t >= nnodes_total || (active && *active == 0)) return;
     double acc[9];
 #pragma unroll
     for (int m = 0; m < 9; ++m) acc[m] = 0.0;
@@ -92,7 +92,8 @@ __global__ void reduce_kernel(int dim, int nnodes_total, int nm, int nsets, size
 }
 
 cudaError_t launch_reduce(const sm_problem *p, const void *part, int n_part, double *mom,
-                          double *clo, cudaStream_t s, double *qmom, int sets_per_q) {
+                          double *clo, cudaStream_t s, double *qmom, int sets_per_q,
+                          const int *active) {
     const int n = p->ncell * p->nn;
     const int threads = 128;
     const size_t stride = (size_t)n * p->nm;
@@ -100,11 +101,11 @@ cudaError_t launch_reduce(const sm_problem *p, const void *part, int n_part, dou
     if (p->prec == 32)
         reduce_kernel<float><<<(n + threads - 1) / threads, threads, 0, s>>>(
             p->dim, n, p->nm, n_part, stride, inv_c, (const float *)part, p->d_gray, mom, clo,
-            qmom, sets_per_q);
+            qmom, sets_per_q, active);
     else
         reduce_kernel<double><<<(n + threads - 1) / threads, threads, 0, s>>>(
             p->dim, n, p->nm, n_part, stride, inv_c, (const double *)part, p->d_gray, mom, clo,
-            qmom, sets_per_q);
+            qmom, sets_per_q, active);
     return cudaGetLastError();
 }
 

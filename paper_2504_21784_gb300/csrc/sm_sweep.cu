@@ -661,6 +661,8 @@ __global__ void __launch_bounds__(512) sweep2d_batch_kernel(const __grid_constan
                 to[i] = from[i];
         }
         __syncthreads();
+        // a member not swept this pass: none of its tasks runs, so none waits
+        if (s_args.active && *s_args.active == 0) continue;
         switch (s_args.GW) {
             case 1:
                 sweep2d_task<RT, 1>(s_args, Lay, pt.y, smem_raw, bars, ring_bars, ring_p, ring_c,

@@ -202,3 +202,102 @@ def test_problems_sharing_a_kernel_launch_in_any_order(gpu_lib):
         p.sweep(T, S, Ip, Io)
         p.synchronize()
         assert bool(torch.isfinite(p.unpack(Io)).all())
+
+
+# the step's parity mode: the paper's epsilon for the outer and Newton
+# iterations (Eq. relative_tol), inner solves to round-off
+_STEP_ORACLE = dict(eps_outer=1e-3, max_outer=100)
+_STEP_LO = dict(eps_inner=1e-3, max_inner=30, elim_rtol=1e-15, max_elim=100)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_batch_step_matches_oracle(gpu_lib, precision):
+    """Two time steps of Algorithm 1 for all six uneven members at once
+    (sm_batch_step: one batched pass per outer iteration, FP64 low-order
+    solves, per-member stopping) against the oracle's steps of each member:
+    T and E within 1e-11 (FP64 sweep) / 1e-5 (FP32 sweep) of the field's
+    largest magnitude, and, on the FP64 path, each member's own outer and
+    Newton iteration counts.  Members start from radiative equilibrium at a
+    seeded non-uniform temperature, with two-material opacity maps."""
+    import torch
+    from oracle import lo as L
+    sm = gpu_lib
+    cu = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    tol = {64: 1e-11, 32: 1e-5}[precision]
+    b = sm.Batch(MEMBERS, precision)
+    state, ref = [], []
+    prm_o = L.StepParams(lo=L.LOParams(**_STEP_LO), **_STEP_ORACLE)
+    for i, cfg in enumerate(MEMBERS):
+        rng = np.random.default_rng(40 + i)
+        T0 = 0.05 + 0.5 * rng.random((cfg.n_cells, 4))
+        scale = W.blocky_two_material(cfg.nx, cfg.ny, seed=100 + i, block=4, thick=50.0)
+        cv = np.full((cfg.n_cells, 4), 0.3)
+        omx, omy, w = O.quadrature(2, cfg.n_polar, cfg.n_azim)
+        I0 = W.in_precision(L.equilibrium_intensity(cfg, T0, omx), precision)
+        sig0 = O.opacity(cfg.opacity_kind, cfg.opacity_alpha, cfg.edges, T0, scale)
+        mom0 = O.moments(2, omx, omy, w, sig0, I0)
+        T, I, mom, steps = T0, I0, mom0, []
+        for _ in range(2):
+            T, E, F, I, mom, st = L.sm_step(cfg, scale, cv, T, I, mom, prm_o)
+            steps.append((T, E, st))
+        ref.append(steps)
+        m = b.members[i]
+        state.append(dict(scale=cu(scale), cv=cu(cv), T=cu(T0), E=m.new_nodal(), F=m.new_flux(),
+                          mom=cu(mom0), I=[m.pack(cu(I0)), m.empty_intensity()]))
+    prm = sm.step_params(eps_outer=1e-3, eps_inner=1e-3, pcg_rtol=1e-15, max_pcg=20000,
+                         elim_rtol=1e-15, max_elim=100)
+    worst = {"T": 0.0, "E": 0.0}
+    for k in range(2):
+        stats = b.step([s["scale"] for s in state], [s["cv"] for s in state],
+                       [s["T"] for s in state], [s["E"] for s in state],
+                       [s["F"] for s in state], [s["mom"] for s in state],
+                       [s["I"][k % 2] for s in state], [s["I"][(k + 1) % 2] for s in state],
+                       params=prm)
+        outer = []
+        for i, s in enumerate(state):
+            Tr, Er, st = ref[i][k]
+            eT = _rel(s["T"].cpu().numpy(), Tr)
+            eE = _rel(s["E"].cpu().numpy(), Er)
+            worst["T"] = max(worst["T"], eT)
+            worst["E"] = max(worst["E"], eE)
+            assert stats[i]["converged"] == 1
+            if precision == 64:
+                assert stats[i]["outer_iters"] == st["outer"], (i, k, stats[i], st)
+                assert stats[i]["newton_iters_total"] == sum(st["newton"]), (i, k)
+            outer.append((stats[i]["outer_iters"], st["outer"]))
+        print(f"batched step {k + 1} fp{precision}: outer (batch, oracle) per member {outer}")
+    print(f"batched steps fp{precision}: worst T {worst['T']:.2e} E {worst['E']:.2e}")
+    assert worst["T"] < tol and worst["E"] < tol
+    b.close()
+
+
+def test_slot_tuner_choices_are_valid_and_sweep_correctly(gpu_lib):
+    """sm_batch_tune_slots picks, per member, slots per lane in {1, 2, 4, 8}
+    no larger than the member's automatic choice; a batch built with them
+    sweeps every member exactly as single-problem sweeps with the same slots."""
+    sm = gpu_lib
+    gw = sm.tune_batch_slots(MEMBERS, 32, reps=1)
+    auto = sm.Batch(MEMBERS, 32)
+    auto_gw = [m.info["groups_per_warp"] for m in auto.members]
+    auto.close()
+    assert all(g in (1, 2, 4, 8) and g <= a for g, a in zip(gw, auto_gw)), (gw, auto_gw)
+    b = sm.Batch(MEMBERS, 32, groups_per_warp=gw)
+    assert [m.info["groups_per_warp"] for m in b.members] == gw
+    T, S, Ip, Io = [], [], [], []
+    for i, (cfg, m) in enumerate(zip(MEMBERS, b.members)):
+        t, s, ip = _inputs(sm, m, cfg, seed=i)
+        T.append(t)
+        S.append(s)
+        Ip.append(ip)
+        Io.append(m.empty_intensity())
+    b.sweep(T, S, Ip, Io)
+    b.synchronize()
+    for i, cfg in enumerate(MEMBERS):
+        p = sm.Problem.from_config(cfg, 32, groups_per_warp=gw[i])
+        Io1 = p.empty_intensity()
+        p.sweep(T[i], S[i], Ip[i], Io1)
+        p.synchronize()
+        assert bool((p.unpack(Io1) == b.members[i].unpack(Io[i])).all()), i
+        p.close()
+    print(f"tuned slots per lane {gw} (automatic {auto_gw})")
+    b.close()

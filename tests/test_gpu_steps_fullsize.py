@@ -87,8 +87,9 @@ def _compare(label, gpu, ref, precision):
     st = gpu["stats"]
     same = (st["outer_iters"] == ref["outer"] and
             st["newton_iters_total"] == sum(ref["newton"]))
+    extra = "" if "T_node" in e else f"  T_node {t_node:.2e} (printed only)"
     print(f"[{label} fp{precision}] " + "  ".join(f"{k} {v:.2e}" for k, v in e.items()) +
-          f"  T_node {t_node:.2e}  outer {st['outer_iters']} newton {st['newton_iters_total']} pcg max "
+          f"{extra}  outer {st['outer_iters']} newton {st['newton_iters_total']} pcg max "
           f"{st['pcg_iters_max']} capped {st['pcg_capped']} (oracle outer {ref['outer']} "
           f"newton {sum(ref['newton'])})")
     return e, same
