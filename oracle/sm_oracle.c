@@ -654,7 +654,10 @@ void orc_moments(int dim, int ncell, int ndir, const double *omx, const double *
 /* are nodal (Rem. opacity); the spectra use the nodal temperature.          */
 /*   2D out per node: [E, Fx, Fy, Txx, Txy, Tyy, sigE, sigF, sigP, Cx, Cy]   */
 /*   1D out per node: [E, F, T, sigE, sigF, sigP, C]                         */
-/* sigma_E falls back to sigma_P where phi == 0.                             */
+/* sigma_E = SE/phi is a mean of the positive group opacities weighted by   */
+/* the group energies; where phi <= 0 or SE <= 0 (the lumped DG intensity,  */
+/* with no positivity fix-up, can dip below zero) it is not defined and     */
+/* falls back to sigma_P.                                                   */
 /* ------------------------------------------------------------------------ */
 void orc_closures(int dim, int ncell, int G, const double *edges, double c, const double *sigma,
                   const double *T_nodal, const double *mom, double *out)
@@ -680,7 +683,8 @@ void orc_closures(int dim, int ncell, int G, const double *edges, double c, cons
             }
             double sP = nb / db, sF = nr / dr;
             double phi = mm[0];
-            double sE = (phi != 0.0) ? mm[dim == 1 ? 3 : 6] / phi : sP;
+            double SE = mm[dim == 1 ? 3 : 6];
+            double sE = (phi > 0.0 && SE > 0.0) ? SE / phi : sP;
             if (dim == 1) {
                 o[0] = phi / c;
                 o[1] = mm[1];

@@ -124,3 +124,33 @@ def test_additive_correction_definition():
     assert np.allclose(out[0, :, 9], (sF - 7.0) * F1[0], rtol=1e-13)
     assert np.allclose(out[0, :, 10], (sF - 7.0) * F1[1], rtol=1e-13)
     assert np.allclose(out[0, :, 6], 7.0, rtol=1e-14)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_sigma_e_falls_back_where_the_energy_weights_are_not_positive(dim):
+    """sigma_E = sum_g sigma_g E_g / sum_g E_g (Eq. sigmaE) is a mean of the
+    positive group opacities; at nodes where phi <= 0 or SE <= 0 (a lumped
+    intensity that dips below zero) it falls back to sigma_P, elsewhere it is
+    SE / phi exactly."""
+    rng = np.random.default_rng(4)
+    edges = W.log_edges(5)
+    ncell, nn = 3, 2 if dim == 1 else 4
+    nm = 5 if dim == 1 else 9
+    T = 0.1 + rng.random((ncell, nn))
+    sigma = np.exp(rng.uniform(-1, 3, (5, ncell)))
+    mom = rng.uniform(0.1, 1.0, (ncell, nn, nm))
+    ise = 3 if dim == 1 else 6
+    mom[0, 0, 0] = -0.2            # phi < 0
+    mom[1, 1, 0] = 0.0             # phi = 0
+    mom[2, 0, ise] = -0.5          # SE < 0
+    mom[2, 1, 0] = -0.3            # both negative: a positive ratio, still undefined
+    mom[2, 1, ise] = -0.6
+    clo = O.closures(dim, edges, 1.0, sigma, T, mom)
+    kE, kP = (3, 5) if dim == 1 else (6, 8)
+    fallback = {(0, 0), (1, 1), (2, 0), (2, 1)}
+    for k in range(ncell):
+        for n in range(nn):
+            if (k, n) in fallback:
+                assert clo[k, n, kE] == clo[k, n, kP]
+            else:
+                assert clo[k, n, kE] == mom[k, n, ise] / mom[k, n, 0]
