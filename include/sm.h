@@ -94,6 +94,7 @@ typedef struct {
     size_t intensity_bytes;
     size_t workspace_bytes;    /* device scratch the library owns */
     double alpha;              /* Eq. alpha: sum w |Omega.n| / sum w with S_N quadrature */
+    int emission_warps;        /* 2D: warps per sweep CTA computing the emission (0: own kernel) */
 } sm_problem_info;
 
 /* Create a problem: builds the S_N set (Sec. 2; Gauss-Legendre in 1D,
@@ -116,6 +117,17 @@ sm_status sm_set_stream(sm_problem *p, void *stream);
  * and the TMA prefetch depth in rows (the packed intensity layout does not
  * depend on them).  0 keeps the current value. */
 sm_status sm_set_tiling(sm_problem *p, int strip_width, int prefetch_rows);
+
+/* Where the emission (row a1) of a 2D pass runs.  0 (the default): its own
+ * kernel, before the sweep kernel.  1..4: fused into the sweep kernel --
+ * every sweep CTA gets that many extra warps (strip_width + warps <= 16)
+ * that compute the emission of the strips ahead of the sweep, strip by
+ * strip in the order the strips are first needed, on the FP64 pipes the
+ * streaming sweep leaves idle; a sweep task whose strip is not complete yet
+ * computes emission items itself until it is.  The source records are the
+ * same either way (the Planck evaluation is shared).  Batch members refuse
+ * (UNSUPPORTED).  sm_autotune also picks between 0 and 2.  Synchronizes. */
+sm_status sm_set_emission_warps(sm_problem *p, int warps);
 
 /* Copy the discrete ordinates {Omega_d, w_d} (Sec. 2) to host arrays of
  * n_dir entries each in the canonical order (omy is all zero in 1D). */
@@ -163,7 +175,9 @@ sm_status sm_sweep(sm_problem *p, const double *T_nodal_dev, const double *sigma
                    double *closures_dev);
 
 /* a4. Closures of the gray low-order system from moments (Sec. 2):
- * sigma_E = SE/phi (Eq. sigmaE; sigma_P where phi = 0), sigma_F =
+ * sigma_E = SE/phi (Eq. sigmaE; sigma_P where phi <= 0 or SE <= 0: the
+ * lumped intensity has no positivity fix-up, and the mean of the positive
+ * group opacities is undefined for such weights), sigma_F =
  * sum r_g sigma_g / sum r_g (Eq. sigmaF), sigma_P = sum b_g sigma_g / sum b_g,
  * additive correction sum_g (sigma_F - sigma_g) F_g = sigma_F F - SF
  * (Eq. additive_mg_correction), with nodal spectra at T_nodal.
@@ -303,9 +317,10 @@ sm_status sm_unpack_intensity(sm_problem *p, const void *I_packed_dev, double *I
  * invalid).  Clears the device status word. */
 sm_status sm_synchronize(sm_problem *p);
 
-/* Pick strip_width and prefetch_rows by timing each candidate on the given
- * inputs with CUDA events (reps timed sweeps each after one warm-up); the
- * fastest is kept.  Overwrites I_out_dev.  Synchronous. */
+/* Pick strip_width, prefetch_rows and the fused emission warps (0 or 2) by
+ * timing each candidate whole pass on the given inputs with CUDA events
+ * (reps timed passes each after one warm-up); the fastest is kept.
+ * Overwrites I_out_dev.  Synchronous. */
 sm_status sm_autotune(sm_problem *p, const double *T_nodal_dev, const double *sigma_dev,
                       const void *I_prev_dev, void *I_out_dev, int reps);
 
@@ -442,7 +457,7 @@ sm_status sm_batch_tune_slots(const sm_problem_desc *descs, int n, void *stream,
  * graph) with events around its three stages, for up to 4096 passes;
  * sm_batch_get_kernel_times synchronizes and returns the summed milliseconds
  * and the number of passes timed, then resets them.  ms_host[0] = prologue,
- * moment clearing and emissions, [1] = the batched sweep kernel, [2] =
+ * emissions, [1] = the batched sweep kernel, [2] =
  * moment sums and closures. */
 sm_status sm_batch_set_profiling(sm_batch *b, int enable);
 sm_status sm_batch_get_kernel_times(sm_batch *b, double *ms_host, int *count_host);

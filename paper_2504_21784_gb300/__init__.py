@@ -37,7 +37,8 @@ EXPORTED = ["sm_create_problem", "sm_destroy_problem", "sm_get_info", "sm_set_st
             "sm_batch_set_stream", "sm_batch_set_tiling", "sm_batch_sweep",
             "sm_batch_synchronize", "sm_batch_autotune", "sm_ho_step", "sm_leakage",
             "sm_adjoint_step", "sm_set_quadrant_moments", "sm_batch_step",
-            "sm_batch_set_profiling", "sm_batch_get_kernel_times", "sm_batch_tune_slots"]
+            "sm_batch_set_profiling", "sm_batch_get_kernel_times", "sm_batch_tune_slots",
+            "sm_set_emission_warps"]
 
 
 class SMError(RuntimeError):
@@ -64,7 +65,8 @@ class ProblemInfo(ctypes.Structure):
         "precision", "dirs_per_quadrant", "groups_per_lane_row", "groups_per_warp",
         "n_groups_padded", "n_warp_tasks", "strip_width", "prefetch_rows", "n_tasks", "n_strips")] + [
         ("intensity_elems", ctypes.c_size_t), ("intensity_bytes", ctypes.c_size_t),
-        ("workspace_bytes", ctypes.c_size_t), ("alpha", ctypes.c_double)]
+        ("workspace_bytes", ctypes.c_size_t), ("alpha", ctypes.c_double),
+        ("emission_warps", ctypes.c_int)]
 
 
 class StepParams(ctypes.Structure):
@@ -128,6 +130,7 @@ def load():
         "sm_get_info": [P, ctypes.POINTER(ProblemInfo)],
         "sm_set_stream": [P, P],
         "sm_set_tiling": [P, I, I],
+        "sm_set_emission_warps": [P, I],
         "sm_get_quadrature": [P, PD, PD, PD],
         "sm_opacity": [P, P, P, P],
         "sm_emission": [P, P, P, P],
@@ -280,6 +283,12 @@ class Problem:
 
     def set_tiling(self, strip_width: int = 0, prefetch_rows: int = 0):
         _check(load().sm_set_tiling(self._h, strip_width, prefetch_rows))
+        self.refresh_info()
+
+    def set_emission_warps(self, warps: int):
+        """0: the emission runs as its own kernel; 1..4: that many warps per
+        sweep CTA compute it inside the sweep kernel (sm_set_emission_warps)."""
+        _check(load().sm_set_emission_warps(self._h, int(warps)))
         self.refresh_info()
 
     def set_stream(self, stream):

@@ -98,9 +98,11 @@ void free_all(sm_problem *p) {
     void *bufs[] = {p->d_edges, p->d_inflow, p->d_lanes, p->d_dir_of, p->d_src,
                     p->d_mom_acc, p->d_gray, p->d_part, p->d_face, p->d_flags,
                     p->ctrl_borrowed ? nullptr : p->d_ctrl, p->d_mom_tmp, p->d_T_tmp,
-                    p->d_sig_tmp, p->d_clo_tmp};
+                    p->d_sig_tmp, p->d_clo_tmp, p->d_emit_ctr};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    delete p->tabs;
+    p->tabs = nullptr;
     smk::lo_free(p);
     smk::adjoint_free(p);
     for (auto &e : p->ev_pool)
@@ -122,8 +124,10 @@ cudaEvent_t *timing_events(sm_problem *p, int n) {
 }
 
 // (Re)allocate the tiling-dependent workspace: W cell columns (= warps) per
-// CTA and S prefetched rows per warp for the 2D sweep.
-sm_status apply_tiling(sm_problem *p, int W, int S) {
+// CTA and S prefetched rows per warp for the 2D sweep, and E warps per CTA
+// computing the emission inside the sweep kernel (0: its own kernel; E < 0
+// keeps the current number).
+sm_status apply_tiling(sm_problem *p, int W, int S, int E = -1) {
     if (p->dim == 1) {
         p->W = 1;
         p->S = 0;
@@ -136,11 +140,16 @@ sm_status apply_tiling(sm_problem *p, int W, int S) {
     } else {
         if (W < 1 || W > 16) return fail(SM_ERR_INVALID_ARG, "strip_width must be in 1..16");
         if (S < 2 || S > 8) return fail(SM_ERR_INVALID_ARG, "prefetch_rows must be in 2..8");
+        if (E < 0) E = p->emit_warps;
+        if (E > 4 || W + E > 16)
+            return fail(SM_ERR_INVALID_ARG, "emission warps: 0..4 and strip_width + warps <= 16");
+        if (E > 0 && p->batch_owned)
+            return fail(SM_ERR_UNSUPPORTED, "batch members run the emission as its own kernel");
         const int old_W = p->W, old_S = p->S;
         p->W = W;
         p->S = S;
         size_t smem = 0;
-        const int resident = smk::sweep2d_max_resident(p, W, S, &smem);
+        const int resident = smk::sweep2d_max_resident(p, W, S, &smem, E);
         if (resident <= 0) {
             p->W = old_W;
             p->S = old_S;
@@ -148,7 +157,16 @@ sm_status apply_tiling(sm_problem *p, int W, int S) {
                                                 " B of shared memory per CTA (too much)");
         }
         p->resident = resident;
+        p->emit_warps = E;
         p->NS = (p->nx + W - 1) / W;
+        if (E > 0) {
+            if (!p->tabs) {
+                p->tabs = new smk::PlanckTabs();
+                if (!smk::planck_tabs(p->tabs)) return fail(SM_ERR_CUDA, "Planck tables");
+            }
+            sm_status st = dev_alloc(&p->d_emit_ctr, sizeof(unsigned int) * (1 + p->NS), nullptr);
+            if (st) return st;
+        }
         const size_t nwg = (size_t)p->NQ * p->NWT;
         const size_t fb = nwg * p->NS * p->ny * p->GW * 32 * 2 * p->rsize;
         if (fb != p->face_bytes || !p->d_face) {
@@ -165,7 +183,7 @@ sm_status apply_tiling(sm_problem *p, int W, int S) {
         }
     }
     const size_t mom_scratch = p->dim == 2
-                                   ? (size_t)p->ncell * 36 * p->rsize
+                                   ? (size_t)p->NQ * p->NWT * p->ncell * 36 * p->rsize
                                    : (size_t)p->NQ * p->NWT * p->ncell * p->nn * p->nm * p->rsize;
     p->workspace_bytes = (size_t)p->Gp * p->ncell * 8 * p->rsize +         // source records
                          (size_t)p->ncell * p->nn * 2 * 8 +                 // gray spectra
@@ -223,9 +241,12 @@ sm_status check_intensity_align(const void *I_prev, const void *I_out) {
     return SM_OK;
 }
 
-// Sweep kernel and reduction of one pass (the source records are in place).
+// Sweep kernel and reduction of one pass.  The source records are in place,
+// unless T_emit is given: then the sweep kernel's fused emission warps write
+// them from T_emit and sigma_emit (2D, p->emit_warps > 0).
 sm_status sweep_pass(sm_problem *p, const void *I_prev, void *I_out, double *mom, double *clo,
-                     int reverse, cudaEvent_t *ev) {
+                     int reverse, cudaEvent_t *ev, const double *T_emit = nullptr,
+                     const double *sigma_emit = nullptr) {
     cudaStream_t s = p->stream;
     ++p->epoch;
     smk::SweepArgs a = make_args(p, I_prev, I_out);
@@ -234,10 +255,34 @@ sm_status sweep_pass(sm_problem *p, const void *I_prev, void *I_out, double *mom
     a.qmom = qm && p->dim == 2 ? 1 : 0;  // 1D: the per-warp partials are per half already
     if (p->dim == 2) {
         SM_CUDA(cudaMemsetAsync(p->d_ctrl, 0, 2 * sizeof(unsigned int), s));
-        SM_CUDA(cudaMemsetAsync(p->d_mom_acc, 0, (size_t)(qm ? 4 : 1) * p->ncell * 36 * p->rsize,
-                                s));
         const int grid = std::min(a.n_tasks, p->resident);
-        SM_CUDA(smk::launch_sweep2d(p, a, grid, s));
+        if (T_emit) {
+            smk::EmitArgs e;
+            std::memset(&e, 0, sizeof(e));
+            e.warps = p->emit_warps;
+            e.G = p->G;
+            e.Gp = p->Gp;
+            e.ncell = p->ncell;
+            e.nx = p->nx;
+            e.ny = p->ny;
+            e.W = p->W;
+            e.NS = p->NS;
+            e.per_strip = (p->W * p->ny + 7) / 8;
+            e.items = e.per_strip * p->NS;
+            e.acT4_scale = p->desc.a * p->desc.c / (4.0 * 3.14159265358979323846);
+            e.inv_cdt = p->inv_cdt;
+            e.edges = p->d_edges;
+            e.T = T_emit;
+            e.sigma = sigma_emit;
+            e.gray = p->d_gray;
+            e.ctr = p->d_emit_ctr;
+            e.timeout_ns = p->timeout_ns;
+            e.tabs = *p->tabs;
+            SM_CUDA(cudaMemsetAsync(p->d_emit_ctr, 0, sizeof(unsigned int) * (1 + p->NS), s));
+            SM_CUDA(smk::launch_sweep2d(p, a, grid, s, &e));
+        } else {
+            SM_CUDA(smk::launch_sweep2d(p, a, grid, s));
+        }
     } else {
         SM_CUDA(smk::launch_sweep1d(p, a, s));
     }
@@ -246,8 +291,8 @@ sm_status sweep_pass(sm_problem *p, const void *I_prev, void *I_out, double *mom
     if (mom || clo) {
         double *m = mom ? mom : p->d_mom_tmp;
         if (p->dim == 2)
-            SM_CUDA(smk::launch_reduce(p, p->d_mom_acc, qm ? 4 : 1, m, clo, s,
-                                       qm ? p->qmom_dev : nullptr));
+            SM_CUDA(smk::launch_reduce(p, p->d_mom_acc, p->NQ * p->NWT, m, clo, s,
+                                       qm ? p->qmom_dev : nullptr, p->NWT));
         else
             SM_CUDA(smk::launch_reduce(p, p->d_part, p->NQ * p->NWT, m, clo, s,
                                        qm ? p->qmom_dev : nullptr, p->NWT));
@@ -262,11 +307,15 @@ sm_status run_sweep(sm_problem *p, const double *T, const double *sigma, const v
     cudaStream_t s = p->stream;
     cudaEvent_t *ev = p->profiling ? timing_events(p, p->n_timed) : nullptr;
     if (ev) SM_CUDA(cudaEventRecord(ev[0], s));
-    SM_CUDA(smk::launch_emission(p, T, sigma, nullptr, s));
-    p->launches++;
+    const bool fused = p->dim == 2 && p->emit_warps > 0;
+    if (!fused) {
+        SM_CUDA(smk::launch_emission(p, T, sigma, nullptr, s));
+        p->launches++;
+    }
     if (ev) SM_CUDA(cudaEventRecord(ev[1], s));
     // the moments are always summed in a full pass (into scratch when mom is NULL)
-    sm_status st = sweep_pass(p, I_prev, I_out, mom ? mom : p->d_mom_tmp, clo, 0, ev);
+    sm_status st = sweep_pass(p, I_prev, I_out, mom ? mom : p->d_mom_tmp, clo, 0, ev,
+                              fused ? T : nullptr, fused ? sigma : nullptr);
     if (st != SM_OK) return st;
     if (ev) {
         SM_CUDA(cudaEventRecord(ev[3], s));
@@ -279,7 +328,7 @@ sm_status run_sweep(sm_problem *p, const double *T, const double *sigma, const v
 
 namespace smk {
 void set_last_error(const char *msg) { g_err = msg; }
-sm_status apply_tiling_ext(sm_problem *p, int W, int S) { return apply_tiling(p, W, S); }
+sm_status apply_tiling_ext(sm_problem *p, int W, int S) { return apply_tiling(p, W, S, 0); }
 sm_status sweep_only(sm_problem *p, const void *I_prev, void *I_out, double *mom, double *clo,
                      int reverse) {
     if (reverse && p->dim != 2)
@@ -500,7 +549,8 @@ static sm_status create_problem(const sm_problem_desc *d, void *stream, sm_probl
     SM_TRY(dev_alloc(&p->d_lanes, sizeof(smk::LaneConst) * lanes.size(), &acc));
     SM_TRY(dev_alloc(&p->d_dir_of, sizeof(int) * dir_of.size(), &acc));
     SM_TRY(dev_alloc(&p->d_src, (size_t)p->Gp * p->ncell * 8 * p->rsize, &acc));
-    if (p->dim == 2) SM_TRY(dev_alloc(&p->d_mom_acc, (size_t)p->ncell * 36 * p->rsize, &acc));
+    if (p->dim == 2)
+        SM_TRY(dev_alloc(&p->d_mom_acc, (size_t)p->NQ * p->NWT * p->ncell * 36 * p->rsize, &acc));
     SM_TRY(dev_alloc(&p->d_gray, (size_t)p->ncell * p->nn * 2 * sizeof(double), &acc));
     SM_TRY(dev_alloc(&p->d_ctrl, smk::CTRL_WORDS * sizeof(unsigned int), &acc));
     SM_TRY(dev_alloc(&p->d_mom_tmp, (size_t)p->ncell * p->nn * p->nm * sizeof(double), &acc));
@@ -588,6 +638,7 @@ sm_status sm_get_info(const sm_problem *p, sm_problem_info *o) {
     o->intensity_bytes = o->intensity_elems * p->rsize;
     o->workspace_bytes = p->workspace_bytes;
     o->alpha = p->alpha;
+    o->emission_warps = p->emit_warps;
     return SM_OK;
 }
 
@@ -605,6 +656,18 @@ sm_status sm_set_tiling(sm_problem *p, int strip_width, int prefetch_rows) {
     SM_CUDA(cudaStreamSynchronize(p->stream));
     return apply_tiling(p, strip_width > 0 ? strip_width : p->W,
                         prefetch_rows > 0 ? prefetch_rows : p->S);
+}
+
+sm_status sm_set_emission_warps(sm_problem *p, int warps) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    if (p->batch_owned)
+        return fail(SM_ERR_INVALID_ARG, "this problem belongs to a batch: sweep it with sm_batch_sweep");
+    if (warps < 0 || warps > 4) return fail(SM_ERR_INVALID_ARG, "emission warps must be in 0..4");
+    if (p->dim == 1)
+        return warps == 0 ? SM_OK
+                          : fail(SM_ERR_UNSUPPORTED, "fused emission is a 2D sweep feature");
+    SM_CUDA(cudaStreamSynchronize(p->stream));
+    return apply_tiling(p, p->W, p->S, warps);
 }
 
 sm_status sm_get_quadrature(const sm_problem *p, double *omx, double *omy, double *w) {
@@ -730,12 +793,8 @@ sm_status sm_set_quadrant_moments(sm_problem *p, double *qmom_dev) {
     if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
     if (p->batch_owned) return fail(SM_ERR_INVALID_ARG, "this problem belongs to a batch");
     SM_CUDA(cudaStreamSynchronize(p->stream));
-    if (qmom_dev && p->dim == 2 && !p->qmom_acc4) {
-        // the moment accumulator becomes [quadrant][cell][36]
-        sm_status st = dev_alloc(&p->d_mom_acc, (size_t)4 * p->ncell * 36 * p->rsize, nullptr);
-        if (st) return st;
-        p->qmom_acc4 = true;
-    }
+    // the partial moments are kept per warp task, hence per quadrant: the
+    // reduction forms the quadrant sums from them
     p->qmom_dev = qmom_dev;
     return SM_OK;
 }
@@ -780,9 +839,12 @@ sm_status sm_autotune(sm_problem *p, const double *T, const double *sigma, const
     if (I_prev == I_out) return fail(SM_ERR_INVALID_ARG, "I_prev_dev must not alias I_out_dev");
     if ((st = check_intensity_align(I_prev, I_out))) return st;
     if (reps < 1) reps = 3;
-    const int w_c[] = {2, 4, 6, 8, 12, 16};
+    // strip width x prefetch depth x fused emission warps (0: the emission
+    // kernel runs before the sweep)
+    const int w_c[] = {2, 4, 6, 8, 12, 14, 16};
     const int s_c[] = {2, 3, 4};
-    int best_w = p->W, best_s = p->S;
+    const int e_c[] = {0, 2};
+    int best_w = p->W, best_s = p->S, best_e = p->emit_warps;
     float best_ms = 1e30f;
     const bool prof = p->profiling;
     p->profiling = false;
@@ -792,21 +854,26 @@ sm_status sm_autotune(sm_problem *p, const double *T, const double *sigma, const
     for (int wc : w_c) {
         if (wc > p->nx && wc != 2) continue;
         for (int sc : s_c) {
-            if (apply_tiling(p, wc, sc) != SM_OK) continue;
-            st = run_sweep(p, T, sigma, I_prev, I_out, nullptr, nullptr);  // warm-up
-            if (st) break;
-            SM_CUDA(cudaEventRecord(a, p->stream));
-            for (int r = 0; r < reps && !st; ++r)
-                st = run_sweep(p, T, sigma, I_prev, I_out, nullptr, nullptr);
-            SM_CUDA(cudaEventRecord(b, p->stream));
-            SM_CUDA(cudaEventSynchronize(b));
-            float ms = 0;
-            SM_CUDA(cudaEventElapsedTime(&ms, a, b));
-            if (st == SM_OK && ms < best_ms) {
-                best_ms = ms;
-                best_w = p->W;
-                best_s = p->S;
+            for (int ec : e_c) {
+                if (wc + ec > 16) continue;
+                if (apply_tiling(p, wc, sc, ec) != SM_OK) continue;
+                st = run_sweep(p, T, sigma, I_prev, I_out, nullptr, nullptr);  // warm-up
+                if (st) break;
+                SM_CUDA(cudaEventRecord(a, p->stream));
+                for (int r = 0; r < reps && !st; ++r)
+                    st = run_sweep(p, T, sigma, I_prev, I_out, nullptr, nullptr);
+                SM_CUDA(cudaEventRecord(b, p->stream));
+                SM_CUDA(cudaEventSynchronize(b));
+                float ms = 0;
+                SM_CUDA(cudaEventElapsedTime(&ms, a, b));
+                if (st == SM_OK && ms < best_ms) {
+                    best_ms = ms;
+                    best_w = p->W;
+                    best_s = p->S;
+                    best_e = p->emit_warps;
+                }
             }
+            if (st) break;
         }
         if (st) break;
     }
@@ -814,7 +881,7 @@ sm_status sm_autotune(sm_problem *p, const double *T, const double *sigma, const
     cudaEventDestroy(b);
     p->profiling = prof;
     sm_status sync = sm_synchronize(p);
-    sm_status fin = apply_tiling(p, best_w, best_s);
+    sm_status fin = apply_tiling(p, best_w, best_s, best_e);
     if (st) return st;
     if (sync) return sync;
     return fin;

@@ -4,8 +4,8 @@
 // row counters, moment accumulators); the sweep of every member runs in one
 // launch of sweep2d_batch_kernel, whose CTAs take (problem, task) items from
 // one queue.  The whole pass -- a one-thread prologue (task queue, abort flag,
-// epoch), per-problem emission and moment clearing, the batched sweep, per-
-// problem moment sums and closures -- is recorded once as a CUDA graph for a
+// epoch), per-problem emission, the batched sweep, per-problem moment sums
+// and closures -- is recorded once as a CUDA graph for a
 // given set of caller buffers and replayed afterwards; per-problem kernels sit
 // on parallel branches of the graph so that small members run concurrently.
 #include <algorithm>
@@ -204,7 +204,7 @@ std::vector<smk::SweepArgs> member_args(const sm_batch *b, const Ptrs &q) {
 }
 
 // Enqueues one pass on stream c (being captured, or live): prologue,
-// per-problem emission and moment clearing on parallel branches, the batched
+// per-problem emission on parallel branches, the batched
 // sweep, per-problem moment sums and closures.  ev (live profiling only):
 // four timing events recorded before the emissions, around the sweep and
 // after the reductions.
@@ -224,13 +224,12 @@ sm_status enqueue_pass(sm_batch *b, const Ptrs &q, const smk::SweepArgs *d_args,
     const int grid = std::min(b->n_tasks, b->resident);
     if (ev) B_CUDA(cudaEventRecord(ev[0], c));
     smk::batch_prologue_kernel<<<1, 1, 0, c>>>(b->d_ctrl, b->d_epoch);
-    // per-problem emission and moment clearing on parallel branches
+    // per-problem emission on parallel branches
     B_CUDA(cudaEventRecord(b->ev[0], c));
     for (int k = 0; k < N_SIDE; ++k) B_CUDA(cudaStreamWaitEvent(b->side[k], b->ev[0], 0));
     for (size_t i = 0; i < n; ++i) {
         sm_problem *p = b->probs[i];
         cudaStream_t s = b->side[i % N_SIDE];
-        B_CUDA(cudaMemsetAsync(p->d_mom_acc, 0, (size_t)p->ncell * 36 * p->rsize, s));
         B_CUDA(smk::launch_emission(p, q.T[i], q.sigma[i], nullptr, s, b->d_active + i));
     }
     for (int k = 0; k < N_SIDE; ++k) {
@@ -246,8 +245,8 @@ sm_status enqueue_pass(sm_batch *b, const Ptrs &q, const smk::SweepArgs *d_args,
     for (size_t i = 0; i < n; ++i) {
         sm_problem *p = b->probs[i];
         double *m = (q.mom && q.mom[i]) ? q.mom[i] : p->d_mom_tmp;
-        B_CUDA(smk::launch_reduce(p, p->d_mom_acc, 1, m, q.clo ? q.clo[i] : nullptr,
-                                  b->side[i % N_SIDE], nullptr, 1, b->d_active + i));
+        B_CUDA(smk::launch_reduce(p, p->d_mom_acc, p->NQ * p->NWT, m, q.clo ? q.clo[i] : nullptr,
+                                  b->side[i % N_SIDE], nullptr, p->NWT, b->d_active + i));
     }
     for (int k = 0; k < N_SIDE; ++k) {
         B_CUDA(cudaEventRecord(b->ev[1 + k], b->side[k]));

@@ -9,6 +9,7 @@
 
 #include "../../include/sm.h"
 #include "../../include/sm_debug.h"
+#include "sm_planck.cuh"
 
 namespace smk {
 
@@ -44,7 +45,7 @@ struct SweepArgs {
     const void *I_prev;      // packed or null
     void *I_out;             // packed
     void *part;              // 1D: [NQ*NWT][cell][10] per-warp partial moments
-    void *mom_acc;           // 2D: [cell][36] moment accumulator (zeroed per sweep)
+    void *mom_acc;           // 2D: [NQ*NWT][cell][36] partial moments per warp task
     void *face;              // 2D: [NQ*NWT][NS][ny][GW][32][2]
     unsigned long long *flags;  // 2D: [NQ*NWT][NS]
     unsigned int *ctrl;
@@ -53,10 +54,29 @@ struct SweepArgs {
     int fault_skip_publish;  // test hook: strip 0 never publishes
     int reverse;             // 2D: sweep -Omega for every direction; I_prev / I_out of
                              // geometric quadrant q live at quadrant q^2 (adjoint sweeps)
-    int qmom;                // 2D: accumulate moments per quadrant, [q][cell][36]
+    int qmom;                // 2D: per-quadrant moments wanted (the partials keep them apart)
     int publish;             // 2D: rows per release of a strip's x-faces downwind
     const int *active;       // batch member: its tasks are skipped while *active == 0
                              // (NULL: always swept)
+};
+
+// Emission fused into the 2D sweep kernel: `warps` extra warps per CTA
+// compute the emission (row a1) of the strips ahead of the sweep while the
+// sweep warps stream, and sweep warps whose task's strip is not ready yet help
+// with it.  Work items are 8 cells (32 nodes) of one strip, taken in the
+// order the strips are first needed (0, NS-1, 1, NS-2, ...: quadrants sweep
+// the strips from both sides); every strip has `per_strip` items (the ragged
+// last strip's surplus items are empty).  ctr[0] is the item queue and
+// ctr[1 + s] the items of strip s done (zeroed before each launch).
+struct EmitArgs {
+    int warps;                 // 0: the emission runs as its own kernel before the sweep
+    int G, Gp, ncell, nx, ny, W, NS, per_strip, items;
+    double acT4_scale, inv_cdt;
+    const double *edges, *T, *sigma;
+    double *gray;
+    unsigned int *ctr;
+    long long timeout_ns;
+    PlanckTabs tabs;
 };
 
 // Rows per release of a strip's x-faces to the downwind strip: the release
@@ -93,14 +113,17 @@ cudaError_t launch_opacity_shape(const sm_problem *p, const double *T, double *f
                                  cudaStream_t s);
 cudaError_t launch_closures_from_T(const sm_problem *p, const double *mom, const double *T,
                                    const double *sigma, double *out, cudaStream_t s);
-cudaError_t launch_sweep2d(const sm_problem *p, const SweepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_sweep2d(const sm_problem *p, const SweepArgs &a, int grid, cudaStream_t s,
+                           const EmitArgs *e = nullptr);
 cudaError_t launch_sweep1d(const sm_problem *p, const SweepArgs &a, cudaStream_t s);
 cudaError_t launch_reduce(const sm_problem *p, const void *part, int n_part, double *mom,
                           double *clo, cudaStream_t s, double *qmom = nullptr,
                           int sets_per_q = 1, const int *active = nullptr);
 cudaError_t launch_pack(const sm_problem *p, const double *canon, void *packed, int unpack,
                         cudaStream_t s);
-int sweep2d_max_resident(const sm_problem *p, int W, int S, size_t *smem_out);
+// CTAs of the 2D sweep that fit on the GPU for W sweep warps, S stages and
+// emit_warps fused emission warps (0 if none fit); *smem_out: bytes per CTA.
+int sweep2d_max_resident(const sm_problem *p, int W, int S, size_t *smem_out, int emit_warps = 0);
 size_t sweep2d_smem_bytes(int prec, int W, int GW, int S, int GSLOT);
 size_t sweep2d_stage_bytes(int prec, int GW, int GSLOT);
 size_t sweep2d_batch_smem_bytes(int prec, int W, int S, size_t stg, int ring_gw);
@@ -108,6 +131,9 @@ cudaError_t launch_sweep2d_batch(int prec, const BatchSweepArgs &b, int grid, si
                                  cudaStream_t s);
 int sweep2d_batch_max_resident(int prec, int W, size_t smem);
 void planck_upload_tables(void);
+// Fills the Planck tables' kernel-parameter form (uploads them first); false
+// on a CUDA error.
+bool planck_tabs(PlanckTabs *out);
 // Descriptor checks shared by sm_create_problem and sm_sweep_static: NULL when
 // the descriptor is valid, else a static message (allocates nothing).
 const char *check_desc(const sm_problem_desc *d);
@@ -158,14 +184,17 @@ struct sm_problem {
     int DQ, DQP, DQL, LG, DB, GW, GSLOT, Gp, NGB, NWT;
     // tiling (2D): W cell columns (= warps) per CTA, S prefetched rows per warp
     int W, S, NS;
-    int resident = 0;  // 2D sweep CTAs that fit on the GPU for (W, S)
+    int emit_warps = 0;  // 2D: emission warps fused into the sweep kernel (0: separate kernel)
+    int resident = 0;  // 2D sweep CTAs that fit on the GPU for (W, S, emit_warps)
+    unsigned int *d_emit_ctr = nullptr;  // [1 + NS] fused-emission queue and strip counters
+    smk::PlanckTabs *tabs = nullptr;     // host copy of the tables' parameter form
     // device buffers
     double *d_edges = nullptr;      // [G+1]
     void *d_inflow = nullptr;       // [4][Gp] sweep precision
     smk::LaneConst *d_lanes = nullptr;
     int *d_dir_of = nullptr;        // [NQ][DB][32] canonical direction (or -1)
     void *d_src = nullptr;          // [cell][Gp][8] source records
-    void *d_mom_acc = nullptr;      // 2D: [cell][36] moment accumulator
+    void *d_mom_acc = nullptr;      // 2D: [NQ*NWT][cell][36] partial moments per warp task
     double *d_gray = nullptr;       // [cell][node][2] sigma_P, sigma_F
     void *d_part = nullptr;         // 1D: per-warp partial moments
     void *d_face = nullptr;
@@ -192,7 +221,7 @@ struct sm_problem {
     sm_lo_state *lo = nullptr;
     sm_adj_state *adj = nullptr;
     double *qmom_dev = nullptr;  // per-quadrant moments [cell][node][4][6] filled by each sweep
-    bool qmom_acc4 = false;      // moment accumulator sized for four quadrants
+    bool qmom_acc4 = false;      // (unused: the partial moments are per warp task)
     bool batch_owned = false;    // member of an sm_batch: swept only by the batch
     bool ctrl_borrowed = false;  // d_ctrl belongs to the batch
 };

@@ -1650,7 +1650,10 @@ sm_status sm_batch_step(sm_batch *b, const double *const *scale_dev,
         for (int i = 0; i < n; ++i) {
             if (!active[i]) continue;
             sm_problem *p = probs[i];
-            LO_TRY(lo_collect(p, &st[i]));
+            const sm_status lr = lo_collect(p, &st[i]);
+            if (lr != SM_OK)
+                return lo_fail(lr, "member " + std::to_string(i) + ", outer iteration " +
+                                       std::to_string(it) + ": " + sm_last_error());
             const double dn = std::sqrt(p->lo->h_sc->d2), un = std::sqrt(p->lo->h_sc->n2);
             st[i].outer_iters = it;
             st[i].last_change = dn;

@@ -70,7 +70,7 @@ __global__ void reduce_kernel(int dim, int nnodes_total, int nm, int nsets, size
             o[0] = phi * inv_c;
             o[1] = acc[1];
             o[2] = acc[2];
-            o[3] = (phi != 0.0) ? acc[3] / phi : sP;
+            o[3] = (phi > 0.0 && acc[3] > 0.0) ? acc[3] / phi : sP;
             o[4] = sF;
             o[5] = sP;
             o[6] = sF * acc[1] - acc[4];
@@ -82,7 +82,7 @@ __global__ void reduce_kernel(int dim, int nnodes_total, int nm, int nsets, size
             o[3] = acc[3];
             o[4] = acc[4];
             o[5] = acc[5];
-            o[6] = (phi != 0.0) ? acc[6] / phi : sP;
+            o[6] = (phi > 0.0 && acc[6] > 0.0) ? acc[6] / phi : sP;
             o[7] = sF;
             o[8] = sP;
             o[9] = sF * acc[1] - acc[7];

@@ -233,7 +233,7 @@ sm_status sm_sweep_static(const sm_problem_desc *d, void *stream, const double *
     const size_t o_dir = take(sizeof(int) * nlanes);
     const size_t o_src = take((size_t)p.ncell * p.Gp * 8 * p.rsize);
     const size_t o_gray = take((size_t)p.ncell * p.nn * 2 * sizeof(double));
-    const size_t o_acc = take((size_t)p.ncell * 36 * p.rsize);
+    const size_t o_acc = take(nwg * p.ncell * 36 * p.rsize);
     const size_t o_face = take(nwg * p.NS * p.ny * p.GW * 32 * 2 * p.rsize);
     const size_t o_mom = take((size_t)p.ncell * p.nn * p.nm * sizeof(double));
     const size_t o_Ip = take(ielems * p.rsize);
@@ -265,11 +265,11 @@ sm_status sm_sweep_static(const sm_problem_desc *d, void *stream, const double *
     do {                                                                    \
         if ((x) != cudaSuccess) return static_fail(SM_ERR_CUDA, #x " failed"); \
     } while (0)
-    // what must start at zero: control words (queue, abort, status), the
-    // wavefront row counters (epoch 1 below) and the moment accumulator
+    // what must start at zero: control words (queue, abort, status) and the
+    // wavefront row counters (epoch 1 below); every partial moment slot is
+    // written by its warp task
     ST_CUDA(cudaMemsetAsync(base + o_ctrl, 0, smk::CTRL_WORDS * sizeof(unsigned int), s));
     ST_CUDA(cudaMemsetAsync(base + o_flags, 0, nwg * p.NS * 8, s));
-    ST_CUDA(cudaMemsetAsync(base + o_acc, 0, (size_t)p.ncell * 36 * p.rsize, s));
     ST_CUDA(cudaMemcpyAsync(p.d_edges, d->group_edges, sizeof(double) * (p.G + 1),
                             cudaMemcpyHostToDevice, s));
     ST_CUDA(cudaMemcpyAsync(p.d_lanes, lanes, sizeof(smk::LaneConst) * nlanes,
@@ -293,7 +293,8 @@ sm_status sm_sweep_static(const sm_problem_desc *d, void *stream, const double *
     if (resident <= 0) return static_fail(SM_ERR_UNSUPPORTED, "sweep tiling does not fit");
     a.publish = smk::publish_rows(a.n_tasks, resident);
     ST_CUDA(smk::launch_sweep2d(&p, a, std::min(a.n_tasks, resident), s));
-    ST_CUDA(smk::launch_reduce(&p, p.d_mom_acc, 1, moments ? moments : p.d_mom_tmp, closures, s));
+    ST_CUDA(smk::launch_reduce(&p, p.d_mom_acc, (int)nwg, moments ? moments : p.d_mom_tmp,
+                               closures, s, nullptr, p.NWT));
     ST_CUDA(smk::launch_pack(&p, I_out_canon, Io, 1, s));
     // the status words, read on this stream only (no device-wide synchronization)
     unsigned int ctrl[smk::CTRL_WORDS];

@@ -38,9 +38,11 @@
 // intensities (plain and sigma-weighted, per node), the warp transposes the
 // sums through shared memory, each lane forms one of the 36 weighted moments
 // as a dot product over the 32 lanes (the last four split over octets of
-// lanes and finished by shuffles), and the moments are added with atomics to
-// an L2-resident per-cell accumulator.
+// lanes and finished by shuffles), and the warp task stores them in its own
+// slot of the per-(warp task, cell) partial moments; the reduction sums the
+// warp tasks in a fixed order, so the moments are reproducible bit for bit.
 #include <stdint.h>
+#include <string.h>
 
 #include "sm_internal.cuh"
 
@@ -82,6 +84,19 @@ __device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
     unsigned v;
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// orders this thread's generic-proxy view of global memory before its later
+// async-proxy (TMA) reads of it
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 __device__ __forceinline__ long long global_ns() {
     long long t;
@@ -268,6 +283,97 @@ size_t sweep2d_stage_bytes(int prec, int GW, int GSLOT) {
     return stage_bytes(prec == 32 ? 4 : 8, GW, GSLOT);
 }
 
+// ---------------------------------------------------------------------------
+// Fused emission (EmitArgs): the Planck tables reached through the kernel
+// parameter.
+struct ParamTabs {
+    const PlanckTabs *t;
+    __device__ __forceinline__ double head(int k) const { return t->head[k]; }
+    __device__ __forceinline__ double bern(int k) const { return t->bern[k]; }
+    __device__ __forceinline__ double cexp(int i) const { return t->cexp[i]; }
+    __device__ __forceinline__ double exp2(int j) const { return __ldg(t->exp2 + j); }
+    __device__ __forceinline__ double pcen(int j) const { return __ldg(t->pcen + j); }
+    __device__ __forceinline__ const double *ptab(int j) const { return t->ptab + (size_t)j * 2 * NTAY; }
+};
+
+// Strip of the r-th place in the order the strips are first needed: the
+// quadrants with Omega_x > 0 start at strip 0, the others at strip NS - 1.
+__device__ __forceinline__ int emit_strip_of_rank(int r, int NS) {
+    return (r & 1) ? NS - 1 - (r >> 1) : (r >> 1);
+}
+
+// One emission item (8 cells of strip s, one node per lane) by the calling
+// warp, then its completion released to strip s's counter.  Kept out of line
+// so that the sweep's register allocation does not grow with it.
+template <typename RT>
+__device__ __noinline__ void emit_item(const EmitArgs &E, RT *src, unsigned int *ctrl, int item,
+                                       const float *s_edges) {
+    const int lane = threadIdx.x & 31;
+    const int s = emit_strip_of_rank(item / E.per_strip, E.NS);
+    const int k = item % E.per_strip;
+    const int x0 = s * E.W, ws = min(E.W, E.nx - x0);
+    const int ncells = ws * E.ny;
+    if (8 * k < ncells) {  // (warp-uniform) the ragged strip's surplus items are empty
+        int ci = 8 * k + (lane >> 2);
+        const bool active = ci < ncells;
+        if (!active) ci = ncells - 1;  // a copy of a real node, nothing stored
+        const int cell = (ci / ws) * E.nx + x0 + (ci % ws);
+        emit_node<RT>(cell, lane & 3, active, E.ncell, 4, E.G, E.Gp, E.edges, s_edges,
+                      E.acT4_scale, E.inv_cdt, E.T, E.sigma, src, E.gray, nullptr,
+                      ctrl + CTRL_STATUS, ST_NONPHYSICAL, ParamTabs{&E.tabs});
+    }
+    __threadfence();  // every lane's records, before the release below
+    __syncwarp();
+    if (lane == 0) red_release_add_u32(E.ctr + 1 + s, 1u);
+}
+
+// Claims the next emission item for the calling warp (-1: none left).
+__device__ __forceinline__ int emit_claim(const EmitArgs &E) {
+    int it = 0;
+    if ((threadIdx.x & 31) == 0) it = (int)atomicAdd(E.ctr, 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    return it < E.items ? it : -1;
+}
+
+// Before a task of strip s issues its first copy of the source records: wait
+// until the strip's emission is complete, processing emission items while
+// any is left (every item is claimed by a running warp and never waits, so
+// the wait ends); then order the strip's records before this warp's TMA
+// reads.  false: the wait ran out of time or the sweep was aborted.
+template <typename RT>
+__device__ bool emit_wait_strip(const EmitArgs &E, RT *src, unsigned int *ctrl, int s,
+                                const float *s_edges, volatile int *s_abort) {
+    const int lane = threadIdx.x & 31;
+    const unsigned need = (unsigned)E.per_strip;
+    long long t0 = 0;
+    for (unsigned it = 0;; ++it) {
+        unsigned done = 0;
+        if (lane == 0) done = ld_acquire_u32(E.ctr + 1 + s);
+        done = __shfl_sync(0xffffffffu, done, 0);
+        if (done >= need) break;
+        const int item = emit_claim(E);
+        if (item >= 0) {
+            emit_item<RT>(E, src, ctrl, item, s_edges);
+            continue;
+        }
+        // every item is taken: the strip's last ones are being finished
+        if (t0 == 0) t0 = global_ns();
+        __nanosleep(128);
+        if ((it & 15) == 0) {
+            const bool stop = *s_abort || ld_relaxed(ctrl + CTRL_ABORT) ||
+                              global_ns() - t0 > E.timeout_ns;
+            if (__any_sync(0xffffffffu, stop)) {
+                if (global_ns() - t0 > E.timeout_ns) raise_timeout(ctrl, s_abort);
+                *s_abort = 1;
+                return false;
+            }
+        }
+    }
+    if (lane == 0) fence_proxy_async_global();
+    __syncwarp();
+    return true;
+}
+
 // One task of the 2D sweep: strip sr of warp task wg (quadrant Q, direction
 // block, group block) of the problem A, every warp of the CTA sweeping one
 // cell column of the strip from the upwind to the downwind edge.  The
@@ -278,7 +384,8 @@ __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &La
                                              unsigned char *smem_raw, uint64_t *bars,
                                              uint64_t *ring_bars, uint32_t &ring_p,
                                              uint32_t &ring_c, volatile int *s_abort,
-                                             uint32_t &phase, const unsigned long long epoch) {
+                                             uint32_t &phase, const unsigned long long epoch,
+                                             const EmitArgs *E, const float *s_edges) {
     using R2 = typename V2<RT>::t;
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
@@ -369,6 +476,9 @@ __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &La
     };
     int issued = -1;    // highest row whose copy was issued
     int consumed = 0;   // rows whose stage has been waited for
+    // fused emission: this strip's source records must be complete first
+    if (E && !emit_wait_strip<RT>(*E, const_cast<RT *>(src), A.ctrl, strip, s_edges, s_abort))
+        return;
     if (lane == 0) {
         fence_proxy_async_smem();
         for (int jj = 0; jj < min(S, ny); ++jj) issue(jj);
@@ -540,9 +650,12 @@ __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &La
             d2 += __shfl_xor_sync(0xffffffffu, d2, 2);
             d2 += __shfl_xor_sync(0xffffffffu, d2, 4);
         }
-        RT *ac = acc + ((size_t)(A.qmom ? q * A.ncell : 0) + cell) * 36;
-        atomicAdd(ac + m1, d1);
-        if ((lane & 7) == 0) atomicAdd(ac + m2, d2);
+        // this warp task's share of the cell's moments: a slot of its own
+        // (no atomics), summed over the warp tasks in a fixed order by the
+        // reduction, so that the moments do not depend on the schedule
+        RT *ac = acc + ((size_t)wg * A.ncell + cell) * 36;
+        ac[m1] = d1;
+        if ((lane & 7) == 0) ac[m2] = d2;
         // the stage is free: prefetch row jj + S into it (the proxy fence
         // orders this warp's reads and writes of it before the copy)
         __syncwarp();
@@ -571,31 +684,41 @@ __device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay,
                                              unsigned char *smem_raw, uint64_t *bars,
                                              uint64_t *ring_bars, uint32_t &ring_p,
                                              uint32_t &ring_c, volatile int *s_abort,
-                                             uint32_t &phase, const unsigned long long epoch) {
+                                             uint32_t &phase, const unsigned long long epoch,
+                                             const EmitArgs *E = nullptr,
+                                             const float *s_edges = nullptr) {
     const int NWG = A.NQ * A.NWT;
     const int q = (task % NWG) / A.NWT;
     switch (q) {
         case 0:
             sweep2d_task_q<RT, GW, 0>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c,
-                                      s_abort, phase, epoch);
+                                      s_abort, phase, epoch, E, s_edges);
             break;
         case 1:
             sweep2d_task_q<RT, GW, 1>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c,
-                                      s_abort, phase, epoch);
+                                      s_abort, phase, epoch, E, s_edges);
             break;
         case 2:
             sweep2d_task_q<RT, GW, 2>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c,
-                                      s_abort, phase, epoch);
+                                      s_abort, phase, epoch, E, s_edges);
             break;
         default:
             sweep2d_task_q<RT, GW, 3>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c,
-                                      s_abort, phase, epoch);
+                                      s_abort, phase, epoch, E, s_edges);
             break;
     }
 }
 
+// barrier of the W sweep warps only (the fused emission warps never join it)
+__device__ __forceinline__ void sweep_warps_sync(int nthreads) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// W sweep warps (one per cell column of the strip), plus E.warps fused
+// emission warps when E.warps > 0 (EmitArgs).
 template <typename RT, int GW>
-__global__ void __launch_bounds__(512) sweep2d_kernel(const __grid_constant__ SweepArgs A) {
+__global__ void __launch_bounds__(512) sweep2d_kernel(const __grid_constant__ SweepArgs A,
+                                                      const __grid_constant__ EmitArgs E) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_task;
     __shared__ volatile int s_abort;
@@ -603,21 +726,38 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const __grid_constant__ Sw
     const Layout2D Lay = layout2d((int)sizeof(RT), S, stage_bytes((int)sizeof(RT), GW, GW * A.LG), GW);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)W * Lay.wsz);
     uint64_t *ring_bars = bars + (size_t)W * S;
+    float *s_edges = reinterpret_cast<float *>(
+        smem_raw + ((layout2d_total(Lay, W, S) + 15) & ~(size_t)15));
     if (threadIdx.x < W * S) mbar_init(bars + threadIdx.x, 1);
     if (threadIdx.x < 2 * W * RING) mbar_init(ring_bars + threadIdx.x, 32);
     if (threadIdx.x == 0) s_abort = 0;
+    if (E.warps)
+        for (int i = threadIdx.x; i <= E.G; i += blockDim.x) s_edges[i] = (float)E.edges[i];
     fence_mbar_init();
+    __syncthreads();
+    if ((int)(threadIdx.x >> 5) >= W) {
+        // fused emission warps: emission items until none is left (they never
+        // wait on anything, so every strip's emission completes)
+        RT *src = static_cast<RT *>(const_cast<void *>(A.src));
+        while (!s_abort && !ld_relaxed(A.ctrl + CTRL_ABORT)) {
+            const int item = emit_claim(E);
+            if (item < 0) break;
+            emit_item<RT>(E, src, A.ctrl, item, s_edges);
+        }
+        return;
+    }
+    const EmitArgs *Ep = E.warps ? &E : nullptr;
     uint32_t phase = 0;   // parity bit per stage of this warp
     uint32_t ring_p = 0;  // rows this warp has put in its ring, all tasks
     uint32_t ring_c = 0;  // rows this warp has taken from the upwind ring
     for (;;) {
-        __syncthreads();
+        sweep_warps_sync(W * 32);
         if (threadIdx.x == 0) s_task = (int)atomicAdd(A.ctrl + CTRL_QUEUE, 1u);
-        __syncthreads();
+        sweep_warps_sync(W * 32);
         const int task = s_task;
         if (task >= A.n_tasks || s_abort) return;
         sweep2d_task<RT, GW>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c, &s_abort,
-                             phase, A.epoch);
+                             phase, A.epoch, Ep, s_edges);
     }
 }
 
@@ -806,24 +946,39 @@ static const void *kernel2d_ptr(int GW) {
     }
 }
 
-cudaError_t launch_sweep2d(const sm_problem *p, const SweepArgs &a, int grid, cudaStream_t s) {
-    const size_t smem = sweep2d_smem_bytes(p->prec, a.W, a.GW, a.S, a.GW * a.LG);
-    const void *k = (p->prec == 32) ? kernel2d_ptr<float>(a.GW) : kernel2d_ptr<double>(a.GW);
-    SweepArgs args = a;
-    void *params[] = {&args};
-    return cudaLaunchKernel(k, dim3(grid), dim3(a.W * 32), params, smem, s);
+// Dynamic shared memory of a 2D sweep CTA: the sweep layout, plus the group
+// edges in FP32 for fused emission warps.
+static size_t sweep2d_smem_total(int prec, int W, int GW, int S, int GSLOT, int emit_warps,
+                                 int G) {
+    size_t smem = sweep2d_smem_bytes(prec, W, GW, S, GSLOT);
+    if (emit_warps) smem = ((smem + 15) & ~(size_t)15) + (size_t)(G + 1) * sizeof(float);
+    return smem;
 }
 
-// Configures the shared-memory limit of the 2D kernel for (W, S) and returns
-// how many CTAs fit on the whole GPU (0 if none).
-int sweep2d_max_resident(const sm_problem *p, int W, int S, size_t *smem_out) {
-    const size_t smem = sweep2d_smem_bytes(p->prec, W, p->GW, S, p->GSLOT);
+cudaError_t launch_sweep2d(const sm_problem *p, const SweepArgs &a, int grid, cudaStream_t s,
+                           const EmitArgs *e) {
+    EmitArgs none;
+    memset(&none, 0, sizeof(none));
+    EmitArgs ea = e ? *e : none;
+    const size_t smem = sweep2d_smem_total(p->prec, a.W, a.GW, a.S, a.GW * a.LG, ea.warps, p->G);
+    const void *k = (p->prec == 32) ? kernel2d_ptr<float>(a.GW) : kernel2d_ptr<double>(a.GW);
+    SweepArgs args = a;
+    void *params[] = {&args, &ea};
+    return cudaLaunchKernel(k, dim3(grid), dim3((a.W + ea.warps) * 32), params, smem, s);
+}
+
+// Configures the shared-memory limit of the 2D kernel for (W, S, emission
+// warps) and returns how many CTAs fit on the whole GPU (0 if none).
+int sweep2d_max_resident(const sm_problem *p, int W, int S, size_t *smem_out, int emit_warps) {
+    const size_t smem = sweep2d_smem_total(p->prec, W, p->GW, S, p->GSLOT, emit_warps, p->G);
     if (smem_out) *smem_out = smem;
+    if ((W + emit_warps) * 32 > 512) return 0;
     const void *k = (p->prec == 32) ? kernel2d_ptr<float>(p->GW) : kernel2d_ptr<double>(p->GW);
     int nsm = 0;
     if (!allow_dynamic_smem(k, smem, &nsm)) return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, W * 32, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (W + emit_warps) * 32, smem) !=
+        cudaSuccess)
         return 0;
     return per_sm * nsm;
 }

@@ -266,3 +266,39 @@ def test_exp_neg_matches_cuda_exp(gpu_lib):
     print(f"exp_neg over {x.size} points: {e_cuda:.2f} ulp from CUDA exp, {e_host:.2f} ulp "
           f"from the host's exp")
     assert e_cuda <= 2.0 and e_host <= 2.0
+
+
+FUSED = {
+    # name: (config kwargs, tiling kwargs, fused emission warps)
+    "ragged_lanes": (dict(nx=37, ny=21, G=5, npol=2, naz=3),
+                     dict(strip_width=8, prefetch_rows=2, groups_per_warp=1), 2),
+    "gw4_dirblocks": (dict(nx=17, ny=9, G=6, npol=4, naz=16),
+                      dict(strip_width=3, prefetch_rows=3, groups_per_warp=4), 4),
+    "gray_channel": (dict(nx=32, ny=32, G=1, npol=4, naz=8, kind=W.OPACITY_POWER),
+                     dict(strip_width=14, prefetch_rows=2, groups_per_warp=1), 2),
+    "steady_allsides": (dict(nx=9, ny=14, G=4, npol=2, naz=4, dt=0.0,
+                             T_bdr=(1.0, 0.5, 0.25, 0.8)),
+                        dict(strip_width=5, prefetch_rows=6, groups_per_warp=2), 1),
+    "many_groups": (dict(nx=29, ny=40, G=64, npol=4, naz=8),
+                    dict(strip_width=12, prefetch_rows=2, groups_per_warp=4), 2),
+}
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("name", sorted(FUSED))
+def test_fused_emission_parity(gpu_lib, name, precision):
+    """The emission computed inside the sweep kernel (sm_set_emission_warps:
+    extra warps per CTA, sweep warps helping while their strip is not ready)
+    against the oracle, with ragged strips, padded lanes and groups, and the
+    same pass with the emission as its own kernel: intensities within 1e-6
+    (FP32, the source records rounded alike) / 1e-13 (FP64) of each other."""
+    ck, tk, warps = FUSED[name]
+    cfg = config(2, **ck)
+    case = build_case(gpu_lib, cfg, precision, seed=sum(map(ord, name)) % 1000 + 17, **tk)
+    I_sep, _, _, _ = run_gpu(case)
+    case.prob.set_emission_warps(warps)
+    assert case.prob.info["emission_warps"] == warps
+    Ig = _check_all(case, precision, f"{name} fused x{warps}")
+    same = float(np.max(np.abs(Ig - I_sep)) / np.abs(I_sep).max())
+    print(f"  fused vs separate emission: {same:.2e}")
+    assert same <= (1e-6 if precision == 32 else 1e-13)
