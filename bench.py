@@ -260,13 +260,14 @@ def cpu_baseline(cfg, budget_s: float = 6.0, passes: int = 3):
 
 
 def converged_steps(sm, W, cfg, prec: int, n_steps: int, stream, autotune: bool = True,
-                    method: int = 0):
+                    method: int = 0, refine: bool = False):
     """Seconds per converged time step (Algorithm 1 through sm_step) from the
     equilibrium initial state T = T0, I = B_g(T0)/4pi (whose moments are
     phi = a c T0^4, F = 0), with the paper's iteration controls.  One
     warm-up step (allocates the low-order workspace), then n_steps timed
     steps of the same evolution.  sm_step synchronizes internally, so the
-    host clock brackets the device work."""
+    host clock brackets the device work.  refine: the FP32 sweeps with FP64
+    defect correction (an FP64-state problem, sm_step_params.refine = 1)."""
     import torch
     with torch.cuda.stream(stream):
         prob = sm.Problem.from_config(cfg, prec, stream=stream)
@@ -292,7 +293,7 @@ def converged_steps(sm, W, cfg, prec: int, n_steps: int, stream, autotune: bool 
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st = prob.step(scale, cv, T, E, F, mom, I[k % 2], I[(k + 1) % 2],
-                           params=sm.step_params(method=method))
+                           params=sm.step_params(method=method, refine=1 if refine else 0))
             torch.cuda.synchronize()
             if k >= 1:
                 secs.append(time.perf_counter() - t0)
@@ -305,6 +306,8 @@ def converged_steps(sm, W, cfg, prec: int, n_steps: int, stream, autotune: bool 
                "converged": all(s["converged"] for s in stats),
                "tiling": {k: prob.info[k] for k in ("strip_width", "prefetch_rows",
                                                     "groups_per_warp")}}
+        if refine:
+            out["refine_corrections"] = [s["refine_corrections"] for s in stats]
         Tn = T.cpu().numpy()
         prob.close()
         return out, Tn
@@ -417,9 +420,14 @@ def step_metric(sm, W, cfgs, n_steps: int, stream):
         r32, T32 = converged_steps(sm, W, cfg, 32, n_steps, stream)
         r64, T64 = converged_steps(sm, W, cfg, 64, n_steps, stream)
         c32, Tc32 = converged_steps(sm, W, cfg, 32, n_steps, stream, method=sm.METHOD_CONSISTENT)
+        rr, Trr = converged_steps(sm, W, cfg, 64, n_steps, stream, refine=True)
         res[cfg.name] = {"fp32": r32, "fp64": r64,
                          "fp64_over_fp32_time": r64["s_per_step"] / r32["s_per_step"],
                          "fp32_vs_fp64_T_rel": float(np.abs(T32 - T64).max() / np.abs(T64).max()),
+                         "fp32_refined": rr,
+                         "fp64_over_refined_time": r64["s_per_step"] / rr["s_per_step"],
+                         "refined_vs_fp64_T_rel":
+                             float(np.abs(Trr - T64).max() / np.abs(T64).max()),
                          "consistent_fp32": c32,
                          "consistent_vs_independent_T_rel":
                              float(np.abs(Tc32 - T32).max() / np.abs(T32).max()),
@@ -532,7 +540,22 @@ def batched_step_metric(sm, W, b, members, stream, n_steps: int = 3):
     """Seconds per time step of all 64 members through sm_batch_step (FP32
     sweep, FP64 low-order, the paper's iteration controls) from the
     equilibrium start T = T0, I = B_g(T0)/4pi; one warm-up step, then
-    n_steps timed steps."""
+    n_steps timed steps.  The members' low-order solves run in one
+    cooperative launch (the library's default); the same steps with one
+    launch per member, from the same start, are timed beside it."""
+    res, T1 = _batched_steps(W, b, members, n_steps)
+    b.set_batched_lo(False)
+    try:
+        res["lo_one_launch_per_member"], T2 = _batched_steps(W, b, members, n_steps)
+    finally:
+        b.set_batched_lo(True)
+    # the two launch forms solve the same systems (their grid sums differ in order)
+    res["lo_forms_T_rel_diff"] = max(float((a - c).abs().max() / c.abs().max())
+                                     for a, c in zip(T1, T2))
+    return res
+
+
+def _batched_steps(W, b, members, n_steps):
     import torch
     st = []
     for mem, h in zip(members, b.members):
@@ -564,7 +587,7 @@ def batched_step_metric(sm, W, b, members, stream, n_steps: int = 3):
             "outer_iters_max_per_step": outer,
             "converged": all(x["converged"] for x in stats),
             "method": "sm_batch_step: FP32 sweep / FP64 low-order, paper controls",
-            "state": "equilibrium start, steps 2..%d" % (n_steps + 1)}
+            "state": "equilibrium start, steps 2..%d" % (n_steps + 1)}, [s["T"] for s in st]
 
 
 def adjoint_metric(sm, W, fd_cells: int, warm: bool = False):
@@ -668,15 +691,19 @@ def run_reference(args):
 
 def metric2_summary(sm_res: dict) -> dict:
     """Metric 2 in brief (printed last on the line): seconds per converged
-    step of the FP32- and FP64-sweep paths and their temperature difference."""
+    step of the FP32- and FP64-sweep paths and their temperature difference,
+    and of the FP32 sweeps with FP64 defect correction."""
     out = {}
     for name, r in sm_res.items():
         out[name] = {"fp32_s_per_step": r["fp32"]["s_per_step"],
                      "fp64_s_per_step": r["fp64"]["s_per_step"],
                      "fp64_over_fp32": r["fp64_over_fp32_time"],
                      "fp32_vs_fp64_T_rel": r["fp32_vs_fp64_T_rel"],
+                     "fp32_refined_s_per_step": r["fp32_refined"]["s_per_step"],
+                     "refined_vs_fp64_T_rel": r["refined_vs_fp64_T_rel"],
                      "outer_iters_fp32": r["fp32"]["outer_iters"],
-                     "outer_iters_fp64": r["fp64"]["outer_iters"]}
+                     "outer_iters_fp64": r["fp64"]["outer_iters"],
+                     "refine_corrections": r["fp32_refined"]["refine_corrections"]}
     return out
 
 

@@ -218,6 +218,7 @@ typedef struct {
     double T_floor;     /* lower bound imposed on T by the elimination */
     int max_outer, max_inner, max_pcg, max_elim;
     int method;         /* SM_METHOD_INDEPENDENT (default) or SM_METHOD_CONSISTENT */
+    int refine;         /* 1: FP64 defect correction with FP32 sweeps (see sm_step) */
 } sm_step_params;
 
 /* Iteration counts of one call. */
@@ -231,6 +232,7 @@ typedef struct {
     int elim_iters_max;     /* largest pointwise elimination count at any node */
     int converged;          /* 1 when the outer iteration met eps_outer within max_outer */
     double last_change;     /* ||u^{l} - u^{l-1}||_2, u = (T, E), of the last outer iteration */
+    int refine_corrections; /* FP32 correction sweeps of the step (params->refine = 1), else 0 */
 } sm_step_stats;
 
 void sm_default_step_params(sm_step_params *params_host);
@@ -286,6 +288,16 @@ sm_status sm_loworder_newton(sm_problem *p, const double *closures_dev, const do
  *     time-edge sources), on exit those of I_next;
  *   I_prev_dev: packed I^k; I_next_dev: packed I^{k+1} (out; no aliasing);
  *   closures_dev[cell][node][n_closures]: last closures (out; may be NULL).
+ * With params->refine = 1 (2D, a precision-64 problem: FP64 state and
+ * emission, independent method) each outer iteration replaces the FP64 sweep
+ * by defect corrections of the intensity iterate (which starts at I^k): the
+ * FP64 residual of the lumped DG equations at the iterate, an FP32 sweep of
+ * the correction with zero inflow and the FP64 update, repeated (at most 4
+ * times) until a correction is below 1e-8 of the iterate; then the FP64
+ * moments of the iterate.  The FP32 sweeps then give the FP64 sweep's
+ * intensity up to rounding, and the step the FP64 step's result;
+ * stats->refine_corrections counts the corrections.  Synchronizes after each
+ * correction.
  * With params->method = SM_METHOD_CONSISTENT (2D) the sweeps also form
  * per-quadrant moments (in the buffer registered with
  * sm_set_quadrant_moments, else in the library's own) and the low-order
@@ -317,7 +329,7 @@ sm_status sm_unpack_intensity(sm_problem *p, const void *I_packed_dev, double *I
  * invalid).  Clears the device status word. */
 sm_status sm_synchronize(sm_problem *p);
 
-/* Pick strip_width, prefetch_rows and the fused emission warps (0 or 2) by
+/* Pick strip_width, prefetch_rows and the fused emission warps (0, 2 or 4) by
  * timing each candidate whole pass on the given inputs with CUDA events
  * (reps timed passes each after one warm-up); the fastest is kept.
  * Overwrites I_out_dev.  Synchronous. */
@@ -357,8 +369,8 @@ sm_status sm_get_kernel_times(sm_problem *p, double *ms_host, int *count_host);
  *
  * The first call on a device (with that device current) looks up the
  * array's device address with cudaGetSymbolAddress, and the first call in
- * the process uploads the Planck tables (synchronous copies); make it before
- * any stream capture.  The call waits for its own stream only (a
+ * the process uploads the Planck tables (synchronous copies).  The call
+ * waits for its own stream only (a
  * cudaStream_t, NULL for the legacy default stream): the device status is
  * read by an asynchronous copy on that stream, then that stream is
  * synchronized; it returns SM_ERR_TIMEOUT or SM_ERR_NONPHYSICAL like
@@ -465,10 +477,12 @@ sm_status sm_batch_get_kernel_times(sm_batch *b, double *ms_host, int *count_hos
 /* One time step of Algorithm 1 for every member of the batch (the batched
  * form of sm_step, independent closures): per outer iteration ONE batched
  * pass (emission, the persistent sweep launch over all unconverged members,
- * moments and closures, replayed from a CUDA graph), then each unconverged
- * member's FP64 low-order Newton solve (one cooperative launch each, queued
- * without host waits) and its change of u = (T, E); one host
- * synchronisation per outer iteration.  Each member stops by
+ * moments and closures, replayed from a CUDA graph), then the FP64
+ * low-order Newton solves of all unconverged members in ONE cooperative
+ * launch (each member on its own share of the co-resident blocks, in
+ * proportion to its cells, with its own grid barriers, Newton and PCG
+ * iterations and stopping tests) and each member's change of u = (T, E);
+ * one host synchronisation per outer iteration.  Each member stops by
  * Eq. relative_tol on its own, exactly as sm_step would: a converged member
  * is skipped by later passes (its tasks, emission and reductions are masked
  * on the device, so the recorded graphs stay valid) and keeps the results

@@ -43,6 +43,13 @@ sm_status sm_debug_set_pcg_form(sm_problem *p, int form);
  * last low-order solve used, or SM_DEBUG_PCG_AUTO if it has run none. */
 sm_status sm_debug_get_pcg_form(const sm_problem *p, int *form);
 
+/* Low-order solves of sm_batch_step: non-zero (the default) runs every
+ * member's Newton iteration in one cooperative launch, each member on its own
+ * share of the blocks; 0 runs one cooperative launch per member, one after
+ * another, as sm_step does.  Both solve the same systems (the block counts,
+ * and so the order of the grid sums, differ).  INVALID_ARG for a NULL batch. */
+sm_status sm_debug_set_batch_lo(sm_batch *b, int batched);
+
 /* out_dev[i] = e^{-x_dev[i]} for i < n, evaluated by the emission kernels'
  * table-driven routine (Tang's method) for 0 <= x < 708, so that a test can
  * compare it with CUDA's exp directly; elsewhere out_dev[i] = exp(-x) of the

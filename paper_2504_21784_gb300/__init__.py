@@ -31,6 +31,7 @@ EXPORTED = ["sm_create_problem", "sm_destroy_problem", "sm_get_info", "sm_set_st
             "sm_launch_count", "sm_last_error", "sm_status_string",
             "sm_debug_set_wait_limit_ns", "sm_debug_skip_publish", "sm_debug_withhold_lo_block",
             "sm_debug_set_pcg_form", "sm_debug_get_pcg_form", "sm_debug_exp_neg",
+            "sm_debug_set_batch_lo",
             "sm_sweep_static",
             "sm_default_step_params", "sm_loworder_newton", "sm_step",
             "sm_create_batch", "sm_destroy_batch", "sm_batch_problem", "sm_batch_get_info",
@@ -75,14 +76,14 @@ class StepParams(ctypes.Structure):
                 ("pcg_rtol", ctypes.c_double), ("elim_rtol", ctypes.c_double),
                 ("T_floor", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("max_inner", ctypes.c_int), ("max_pcg", ctypes.c_int),
-                ("max_elim", ctypes.c_int), ("method", ctypes.c_int)]
+                ("max_elim", ctypes.c_int), ("method", ctypes.c_int), ("refine", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in (
         "outer_iters", "newton_iters_total", "newton_iters_max", "pcg_iters_total",
         "pcg_iters_max", "pcg_capped", "elim_iters_max", "converged")] + [
-        ("last_change", ctypes.c_double)]
+        ("last_change", ctypes.c_double), ("refine_corrections", ctypes.c_int)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -149,6 +150,7 @@ def load():
         "sm_debug_set_pcg_form": [P, I],
         "sm_debug_get_pcg_form": [P, ctypes.POINTER(ctypes.c_int)],
         "sm_debug_exp_neg": [P, P, I, P],
+        "sm_debug_set_batch_lo": [P, I],
         "sm_sweep_static": [ctypes.POINTER(ProblemDesc), P, P, P, P, P, P, P],
         "sm_loworder_newton": [P, P, P, P, P, P, P, P, ctypes.POINTER(StepParams),
                                ctypes.POINTER(StepStats)],
@@ -592,6 +594,11 @@ class Batch:
         _check(load().sm_batch_step(self._h, *keep,
                                     ctypes.byref(params) if params is not None else None, st))
         return [_stats(st[i]) for i in range(n)]
+
+    def set_batched_lo(self, on: bool):
+        """Test hook (sm_debug_set_batch_lo): the members' low-order solves of
+        Batch.step in one launch (default) or one launch per member."""
+        _check(load().sm_debug_set_batch_lo(self._h, 1 if on else 0))
 
     def autotune(self, T, sigma, I_prev, I_out, reps: int = 2):
         n = len(self.members)

@@ -105,6 +105,7 @@ void free_all(sm_problem *p) {
     p->tabs = nullptr;
     smk::lo_free(p);
     smk::adjoint_free(p);
+    smk::refine_free(p);
     for (auto &e : p->ev_pool)
         if (e) cudaEventDestroy(e);
     p->ev_pool.clear();
@@ -843,7 +844,7 @@ sm_status sm_autotune(sm_problem *p, const double *T, const double *sigma, const
     // kernel runs before the sweep)
     const int w_c[] = {2, 4, 6, 8, 12, 14, 16};
     const int s_c[] = {2, 3, 4};
-    const int e_c[] = {0, 2};
+    const int e_c[] = {0, 2, 4};
     int best_w = p->W, best_s = p->S, best_e = p->emit_warps;
     float best_ms = 1e30f;
     const bool prof = p->profiling;

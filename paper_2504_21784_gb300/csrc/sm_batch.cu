@@ -59,6 +59,8 @@ struct sm_batch {
     std::vector<cudaEvent_t> ev_pool;
     int n_timed = 0;
     smk::SweepArgs *d_args_live = nullptr;
+    void *lo_scratch = nullptr;  // the batched low-order launch's arguments (sm_lo.cu)
+    int lo_batched = 1;          // low-order solves in one launch (1) or one per member (0)
 };
 
 namespace {
@@ -351,6 +353,8 @@ sm_status run(sm_batch *b, const Ptrs &q) {
 namespace smk {
 const std::vector<sm_problem *> &batch_members(const sm_batch *b) { return b->probs; }
 cudaStream_t batch_stream(const sm_batch *b) { return b->stream; }
+void *&batch_lo_scratch(sm_batch *b) { return b->lo_scratch; }
+int &batch_lo_mode(sm_batch *b) { return b->lo_batched; }
 sm_status batch_pass(sm_batch *b, const double *const *T, const double *const *sigma,
                      const void *const *I_prev, void *const *I_out, double *const *mom,
                      double *const *clo, const unsigned char *active_host) {
@@ -450,7 +454,14 @@ sm_status sm_destroy_batch(sm_batch *b) {
     if (b->d_active) cudaFree(b->d_active);
     if (b->d_args_live) cudaFree(b->d_args_live);
     for (auto e : b->ev_pool) cudaEventDestroy(e);
+    smk::batch_lo_free(b->lo_scratch);
     delete b;
+    return SM_OK;
+}
+
+sm_status sm_debug_set_batch_lo(sm_batch *b, int batched) {
+    if (!b) return b_fail(SM_ERR_INVALID_ARG, "NULL batch");
+    b->lo_batched = batched != 0;
     return SM_OK;
 }
 

@@ -124,6 +124,22 @@ cudaError_t launch_pack(const sm_problem *p, const double *canon, void *packed, 
 // CTAs of the 2D sweep that fit on the GPU for W sweep warps, S stages and
 // emit_warps fused emission warps (0 if none fit); *smem_out: bytes per CTA.
 int sweep2d_max_resident(const sm_problem *p, int W, int S, size_t *smem_out, int emit_warps = 0);
+// The 2D sweep kernel and the 2D reduction in an explicit arithmetic precision
+// for problem p's layout and tiling (FP32 correction sweeps of FP64 problems).
+int sweep2d_max_resident_prec(int prec, const sm_problem *p, int W, int S, size_t *smem_out);
+cudaError_t launch_sweep2d_prec(int prec, const sm_problem *p, const SweepArgs &a, int grid,
+                                cudaStream_t s);
+cudaError_t launch_reduce_prec(int prec, const sm_problem *p, const void *part, int n_part,
+                               double *mom, double *clo, cudaStream_t s);
+// FP64 defect correction with FP32 sweeps (sm_refine.cu): workspace on first
+// use (FP64 2D problems only), the transport solve of one outer iteration by
+// corrections of the packed FP64 iterate I (residual, FP32 correction sweep,
+// I += d, until the corrections are small) and the FP64 moments of I,
+// release.
+sm_status refine_ensure(sm_problem *p);
+sm_status refine_solve(sm_problem *p, const double *I_k, double *I, double *mom);
+int refine_take_corrections(sm_problem *p);  // corrections since the last call
+void refine_free(sm_problem *p);
 size_t sweep2d_smem_bytes(int prec, int W, int GW, int S, int GSLOT);
 size_t sweep2d_stage_bytes(int prec, int GW, int GSLOT);
 size_t sweep2d_batch_smem_bytes(int prec, int W, int S, size_t stg, int ring_gw);
@@ -159,6 +175,13 @@ sm_status batch_pass(sm_batch *b, const double *const *T, const double *const *s
                      const void *const *I_prev, void *const *I_out, double *const *mom,
                      double *const *clo, const unsigned char *active_host);
 sm_status batch_status(sm_batch *b);
+// Scratch of the batched low-order launch (sm_lo.cu), kept with the batch
+// and released with it.
+void *&batch_lo_scratch(sm_batch *b);
+// 1 (default): the members' low-order solves in one cooperative launch;
+// 0: one launch per member (test hook sm_debug_set_batch_lo).
+int &batch_lo_mode(sm_batch *b);
+void batch_lo_free(void *scratch);
 // Tiling and sweep arguments of one problem (used by the batch object).
 sm_status apply_tiling_ext(sm_problem *p, int W, int S);
 SweepArgs make_sweep_args(const sm_problem *p, const void *I_prev, void *I_out);
@@ -167,6 +190,7 @@ SweepArgs make_sweep_args(const sm_problem *p, const void *I_prev, void *I_out);
 
 struct sm_batch;      // batched problems (sm_batch.cu)
 struct sm_lo_state;   // low-order solve workspace, created on first use
+struct sm_refine_state;  // defect-correction workspace, created on first use
 struct sm_adj_state;  // adjoint workspace, created on first use
 
 struct sm_problem {
@@ -219,6 +243,7 @@ struct sm_problem {
     int64_t launches = 0;
     size_t workspace_bytes = 0;
     sm_lo_state *lo = nullptr;
+    sm_refine_state *refine = nullptr;
     sm_adj_state *adj = nullptr;
     double *qmom_dev = nullptr;  // per-quadrant moments [cell][node][4][6] filled by each sweep
     bool qmom_acc4 = false;      // (unused: the partial moments are per warp task)

@@ -601,10 +601,13 @@ __device__ bool grid_barrier(const GridBar &b, unsigned &target) {
     return __syncthreads_and(ok) != 0;
 }
 
-// Block totals of K values into part[block]; after a barrier, grid_totals
-// sums the per-block partials in a fixed order (every thread gets them).
+// Block totals of K values into part[bid]; after a barrier, grid_totals
+// sums the nb per-block partials in a fixed order (every thread gets them).
+// bid / nb: the block's index among the blocks that solve its problem and
+// their number (the whole grid for one problem; a share of it in the batched
+// launch).
 template <int K>
-__device__ void block_partials(double (&v)[K], double *part) {
+__device__ void block_partials(double (&v)[K], double *part, int bid) {
     __shared__ double sh[BLOCK / 32][K];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -616,18 +619,18 @@ __device__ void block_partials(double (&v)[K], double *part) {
         for (int k = 0; k < K; ++k) {
             double t = 0.0;
             for (int w = 0; w < BLOCK / 32; ++w) t += sh[w][k];
-            part[(size_t)blockIdx.x * K + k] = t;
+            part[(size_t)bid * K + k] = t;
         }
     }
 }
 template <int K>
-__device__ void grid_totals(double (&v)[K], const double *part) {
+__device__ void grid_totals(double (&v)[K], const double *part, int nb) {
     __shared__ double sh[BLOCK / 32][K];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         double t = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += BLOCK) t += __ldcg(part + (size_t)b * K + k);
+        for (int b = threadIdx.x; b < nb; b += BLOCK) t += __ldcg(part + (size_t)b * K + k);
         v[k] = warp_sum(t);
     }
     __syncthreads();
@@ -866,14 +869,14 @@ __device__ __forceinline__ void newton_finish_cell(const NewtonArgs &A, int k, d
     stc<NN>(A.E, k, e);
 }
 
-// at least 4 blocks per SM (128 registers per thread): a 256x256 mesh (512
-// blocks of cells) then runs without grid-stride repeats
+// The Newton iteration of one problem on its nb blocks (bid: this block's
+// index among them).
 template <int NN, bool SINGLE>
-__global__ void __launch_bounds__(BLOCK, 4) lo_newton_kernel(const NewtonArgs A) {
-    if (A.withhold && blockIdx.x == gridDim.x - 1) return;
+__device__ __forceinline__ void lo_newton_body(const NewtonArgs &A, const int bid, const int nb) {
+    if (A.withhold && bid == nb - 1) return;
     const Geo &G = A.G;
-    const int stride = gridDim.x * BLOCK;
-    const int k0 = blockIdx.x * BLOCK + threadIdx.x;
+    const int stride = nb * BLOCK;
+    const int k0 = bid * BLOCK + threadIdx.x;
     int status = LO_OK, newton = 0, pcg_total = 0, pcg_max = 0, capped = 0;
     unsigned bar_target = 0;  // arrivals that complete the next grid barrier
     double d1 = -1.0;
@@ -882,9 +885,9 @@ __global__ void __launch_bounds__(BLOCK, 4) lo_newton_kernel(const NewtonArgs A)
         // also u, p = u, r.r, r.u)
         double v0[3] = {0.0, 0.0, 0.0};
         for (int k = k0; k < G.ncell; k += stride) newton_setup_cell<NN, SINGLE>(A, k, v0);
-        block_partials<3>(v0, A.partA);
+        block_partials<3>(v0, A.partA, bid);
         if (!grid_barrier(A.bar, bar_target)) { status = LO_TIMEOUT; break; }
-        grid_totals<3>(v0, A.partA);
+        grid_totals<3>(v0, A.partA, nb);
         const double stop = A.pcg_rtol * sqrt(v0[0]);
         int done = DONE_NO, iters = 0;
         if constexpr (SINGLE) {
@@ -913,9 +916,9 @@ __global__ void __launch_bounds__(BLOCK, 4) lo_newton_kernel(const NewtonArgs A)
                     }
                 }
             }
-            block_partials<3>(v3, A.partB);
+            block_partials<3>(v3, A.partB, bid);
             if (!grid_barrier(A.bar, bar_target)) { status = LO_TIMEOUT; break; }
-            grid_totals<3>(v3, A.partB);
+            grid_totals<3>(v3, A.partB, nb);
             // conjugate gradients on S E = b from x = E, one reduction per
             // iteration; iteration i reads r_i, w_i (buffers i % 2) and s_{i-1}
             // (buffer (i + 1) % 2) and writes s_i, r_{i+1}, w_{i+1}
@@ -962,9 +965,9 @@ __global__ void __launch_bounds__(BLOCK, 4) lo_newton_kernel(const NewtonArgs A)
                     for (int n = 0; n < NN; ++n) v[1] += wn[n] * un[n];
                 }
                 double *part = cur ? A.partB : A.partC;
-                block_partials<3>(v, part);
+                block_partials<3>(v, part, bid);
                 if (!grid_barrier(A.bar, bar_target)) { done = DONE_TIMEOUT; break; }
-                grid_totals<3>(v, part);
+                grid_totals<3>(v, part, nb);
                 ++iters;
                 gam_old = gam;
                 alpha_old = alpha;
@@ -992,9 +995,9 @@ __global__ void __launch_bounds__(BLOCK, 4) lo_newton_kernel(const NewtonArgs A)
 #pragma unroll
                     for (int n = 0; n < NN; ++n) v1[0] += pv[n] * qv[n];
                 }
-                block_partials<1>(v1, A.partB);
+                block_partials<1>(v1, A.partB, bid);
                 if (!grid_barrier(A.bar, bar_target)) { done = DONE_TIMEOUT; break; }
-                grid_totals<1>(v1, A.partB);
+                grid_totals<1>(v1, A.partB, nb);
                 if (!(v1[0] > 0.0) || !isfinite(v1[0]) || !isfinite(rz)) { done = DONE_BREAKDOWN; break; }
                 const double alpha = rz / v1[0];
                 double v2[2] = {0.0, 0.0};
@@ -1017,9 +1020,9 @@ __global__ void __launch_bounds__(BLOCK, 4) lo_newton_kernel(const NewtonArgs A)
                     stc<NN>(rb, k, rv);
                     stc<NN>(ub, k, zv);
                 }
-                block_partials<2>(v2, A.partC);
+                block_partials<2>(v2, A.partC, bid);
                 if (!grid_barrier(A.bar, bar_target)) { done = DONE_TIMEOUT; break; }
-                grid_totals<2>(v2, A.partC);
+                grid_totals<2>(v2, A.partC, nb);
                 ++iters;
                 if (sqrt(v2[0]) <= stop) { done = DONE_CONVERGED; break; }
                 if (iters >= A.max_pcg) { done = DONE_CAPPED; break; }
@@ -1039,9 +1042,9 @@ __global__ void __launch_bounds__(BLOCK, 4) lo_newton_kernel(const NewtonArgs A)
         for (int k = k0; k < G.ncell; k += stride) newton_finish_cell<NN>(A, k, v2, its_max);
         const int wmax = __reduce_max_sync(0xffffffffu, its_max);
         if ((threadIdx.x & 31) == 0 && wmax > 0) atomicMax(&A.sc->elim_max, wmax);
-        block_partials<2>(v2, A.partD);
+        block_partials<2>(v2, A.partD, bid);
         if (!grid_barrier(A.bar, bar_target)) { status = LO_TIMEOUT; break; }
-        grid_totals<2>(v2, A.partD);
+        grid_totals<2>(v2, A.partD, nb);
         const double dn = sqrt(v2[0]), un = sqrt(v2[1]);
         if (!isfinite(dn)) { status = LO_NONFINITE; break; }
         if (d1 < 0.0) d1 = dn;
@@ -1049,7 +1052,7 @@ __global__ void __launch_bounds__(BLOCK, 4) lo_newton_kernel(const NewtonArgs A)
         // already at round-off level
         if (dn == 0.0 || dn < A.eps_inner * d1 || dn <= 1e-14 * un) break;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (bid == 0 && threadIdx.x == 0) {
         Scalars *sc = A.sc;
         sc->newton_iters = newton;
         sc->pcg_total = pcg_total;
@@ -1059,6 +1062,49 @@ __global__ void __launch_bounds__(BLOCK, 4) lo_newton_kernel(const NewtonArgs A)
     } else if (status == LO_TIMEOUT && threadIdx.x == 0) {
         A.sc->status = LO_TIMEOUT;
     }
+}
+
+// at least 4 blocks per SM (128 registers per thread): a 256x256 mesh (512
+// blocks of cells) then runs without grid-stride repeats
+template <int NN, bool SINGLE>
+__global__ void __launch_bounds__(BLOCK, 4) lo_newton_kernel(const NewtonArgs A) {
+    lo_newton_body<NN, SINGLE>(A, blockIdx.x, gridDim.x);
+}
+
+// The low-order solves of many problems in one cooperative launch: blocks
+// first[m] .. first[m + 1] - 1 solve problem m (its own arguments, partial
+// sums, barrier counter and scalars), each problem with its own PCG form.
+// The problems share nothing, so each runs its own Newton and PCG
+// iterations and stopping tests; every block of the launch is co-resident,
+// so a problem's barriers wait only on blocks that are running.
+template <int NN>
+__global__ void __launch_bounds__(BLOCK, 4)
+lo_newton_batch_kernel(const NewtonArgs *__restrict__ args, const int *__restrict__ single,
+                       const int *__restrict__ first, int n) {
+    __shared__ NewtonArgs sA;
+    __shared__ int s_m;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n - 1;  // the last m with first[m] <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (first[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        s_m = lo;
+    }
+    __syncthreads();
+    const int m = s_m;
+    {
+        const unsigned *src = reinterpret_cast<const unsigned *>(args + m);
+        unsigned *dst = reinterpret_cast<unsigned *>(&sA);
+        static_assert(sizeof(NewtonArgs) % 4 == 0, "word copy");
+        for (int i = threadIdx.x; i < (int)(sizeof(NewtonArgs) / 4); i += BLOCK) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int bid = (int)blockIdx.x - first[m], nb = first[m + 1] - first[m];
+    if (single[m])
+        lo_newton_body<NN, true>(sA, bid, nb);
+    else
+        lo_newton_body<NN, false>(sA, bid, nb);
 }
 
 // Outer iteration, one thread per node: ||u - u_in||^2 and ||u||^2 for
@@ -1113,6 +1159,14 @@ using smk::lo::Geo;
 // reduction buffers (3 + 3 + 3 + 2 values per block); the outer iteration's
 // change norms use the first 2
 constexpr size_t PART_PER_BLOCK = 11;
+
+#define SM_LO_CUDA_LAUNCH(call)                                                      \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess)                                                     \
+            return lo_fail(SM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        p->launches++;                                                             \
+    } while (0)
 
 sm_status lo_fail(sm_status s, const std::string &m) {
     smk::set_last_error(m.c_str());
@@ -1278,35 +1332,31 @@ sm_status check_params(const sm_step_params &prm) {
     return SM_OK;
 }
 
-// One cooperative launch runs the whole Newton iteration (all blocks
-// co-resident: the grid is at most the blocks that fit on the GPU at once).
-template <int NN>
-sm_status launch_newton(sm_problem *p, sm_lo_state &w, const Geo &G, const double *clo,
-                        double *T, double *E, double *F, const double *Tstar, const double *cv,
-                        const double *R0, const sm_step_params &prm) {
+sm_status sm_count(sm_lo_state &w) {
     if (w.nsm == 0) {
         int dev = 0;
         LO_CUDA(cudaGetDevice(&dev));
         LO_CUDA(cudaDeviceGetAttribute(&w.nsm, cudaDevAttrMultiProcessorCount, dev));
     }
-    const int nsm = w.nsm;
-    // the single-reduction form while the cells come to at most 1.5 warps per
-    // SM sub-partition (4 per SM): measured on GB300, it saves 3 % of a 128^2
-    // gray step and 9 % of the 64-cell slab, and costs 3 % on 256^2 meshes
-    // (3.4 warps per sub-partition), where the extra FP64 work of forming the
-    // neighbours' u outweighs the saved barrier
+    return SM_OK;
+}
+
+// The PCG form of problem p: the single-reduction form while the cells come
+// to at most 1.5 warps per SM sub-partition (4 per SM): measured on GB300, it
+// saves 3 % of a 128^2 gray step and 9 % of the 64-cell slab, and costs 3 %
+// on 256^2 meshes (3.4 warps per sub-partition), where the extra FP64 work of
+// forming the neighbours' u outweighs the saved barrier.
+bool single_form(const sm_problem *p, int nsm) {
     const long long warps = ((long long)p->ncell + 31) / 32;
-    const bool single = p->lo_pcg_form == SM_DEBUG_PCG_AUTO ? 2 * warps <= 3LL * 4 * nsm
-                                                             : p->lo_pcg_form == SM_DEBUG_PCG_SINGLE;
-    const void *k = single ? (const void *)smk::lo::lo_newton_kernel<NN, true>
-                           : (const void *)smk::lo::lo_newton_kernel<NN, false>;
-    int &grid = w.coop_grid[single ? 1 : 0];
-    if (grid == 0) {
-        int per_sm = 0;
-        LO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BLOCK, 0));
-        if (per_sm < 1) return lo_fail(SM_ERR_CUDA, "the low-order kernel does not fit on an SM");
-        grid = std::min(w.nblk_cell, per_sm * nsm);
-    }
+    return p->lo_pcg_form == SM_DEBUG_PCG_AUTO ? 2 * warps <= 3LL * 4 * nsm
+                                               : p->lo_pcg_form == SM_DEBUG_PCG_SINGLE;
+}
+
+// The arguments of problem p's Newton kernel on nblocks blocks.
+smk::lo::NewtonArgs newton_args(sm_problem *p, sm_lo_state &w, const Geo &G, const double *clo,
+                                double *T, double *E, double *F, const double *Tstar,
+                                const double *cv, const double *R0, const sm_step_params &prm,
+                                int nblocks) {
     const size_t nblk = (size_t)std::max(w.nblk_cell, w.nblk_node);
     smk::lo::NewtonArgs A;
     A.G = G;
@@ -1350,9 +1400,30 @@ sm_status launch_newton(sm_problem *p, sm_lo_state &w, const Geo &G, const doubl
     A.max_elim = prm.max_elim;
     A.sc = w.sc;
     A.bar.count = &w.sc->bar_count;
-    A.bar.nblocks = (unsigned)grid;
+    A.bar.nblocks = (unsigned)nblocks;
     A.bar.limit_ns = p->timeout_ns;
     A.withhold = p->fault_withhold_block;
+    return A;
+}
+
+// One cooperative launch runs the whole Newton iteration (all blocks
+// co-resident: the grid is at most the blocks that fit on the GPU at once).
+template <int NN>
+sm_status launch_newton(sm_problem *p, sm_lo_state &w, const Geo &G, const double *clo,
+                        double *T, double *E, double *F, const double *Tstar, const double *cv,
+                        const double *R0, const sm_step_params &prm) {
+    LO_TRY(sm_count(w));
+    const bool single = single_form(p, w.nsm);
+    const void *k = single ? (const void *)smk::lo::lo_newton_kernel<NN, true>
+                           : (const void *)smk::lo::lo_newton_kernel<NN, false>;
+    int &grid = w.coop_grid[single ? 1 : 0];
+    if (grid == 0) {
+        int per_sm = 0;
+        LO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BLOCK, 0));
+        if (per_sm < 1) return lo_fail(SM_ERR_CUDA, "the low-order kernel does not fit on an SM");
+        grid = std::min(w.nblk_cell, per_sm * w.nsm);
+    }
+    smk::lo::NewtonArgs A = newton_args(p, w, G, clo, T, E, F, Tstar, cv, R0, prm, grid);
     void *args[] = {&A};
     LO_CUDA(cudaLaunchCooperativeKernel(k, dim3(grid), dim3(BLOCK), args, 0, p->stream));
     p->lo_pcg_form_used = single ? SM_DEBUG_PCG_SINGLE : SM_DEBUG_PCG_TEXTBOOK;
@@ -1469,9 +1540,112 @@ sm_status check_lo_problem(sm_problem *p) {
     return lo_ensure(p);
 }
 
+// Arguments of the batched low-order launch: per problem its Newton kernel
+// arguments, its PCG form and its first block (pinned host copies and their
+// device mirrors; rewritten before every launch, after the previous one has
+// been waited for).
+struct BatchLO {
+    smk::lo::NewtonArgs *h_args = nullptr, *d_args = nullptr;
+    int *h_int = nullptr, *d_int = nullptr;  // single[cap], first[cap + 1]
+    int cap = 0;
+    int per_sm = 0;  // co-resident blocks of the batched kernel per SM
+};
+
+// The low-order solves (independent method) of the problems `members` in one
+// cooperative launch on stream s, after each one's preparation kernel.
+// Every problem gets blocks in proportion to its cells (at least one, at
+// most one per BLOCK cells) out of all the blocks that fit on the GPU at
+// once; with fewer blocks than its single-problem launch a problem runs more
+// cells per thread (grid-stride loops) and sums its block partials in
+// another order.
+sm_status batch_lo_launch(sm_batch *b, const std::vector<int> &members,
+                          const std::vector<sm_problem *> &probs, const double *const *clo,
+                          const double *const *cv, double *const *T, double *const *E,
+                          double *const *F, const sm_step_params &prm, cudaStream_t s) {
+    const int n = (int)members.size();
+    if (n == 0) return SM_OK;
+    void *&slot = smk::batch_lo_scratch(b);
+    if (!slot) slot = new BatchLO();
+    BatchLO &L = *static_cast<BatchLO *>(slot);
+    if (L.cap < n) {
+        if (L.h_args) cudaFreeHost(L.h_args);
+        if (L.d_args) cudaFree(L.d_args);
+        if (L.h_int) cudaFreeHost(L.h_int);
+        if (L.d_int) cudaFree(L.d_int);
+        L.h_args = L.d_args = nullptr;
+        L.h_int = L.d_int = nullptr;
+        L.cap = 0;
+        LO_CUDA(cudaMallocHost(&L.h_args, sizeof(smk::lo::NewtonArgs) * n));
+        LO_CUDA(cudaMalloc(&L.d_args, sizeof(smk::lo::NewtonArgs) * n));
+        LO_CUDA(cudaMallocHost(&L.h_int, sizeof(int) * (2 * n + 1)));
+        LO_CUDA(cudaMalloc(&L.d_int, sizeof(int) * (2 * n + 1)));
+        L.cap = n;
+    }
+    sm_lo_state &w0 = *probs[members[0]]->lo;
+    LO_TRY(sm_count(w0));
+    const int nsm = w0.nsm;
+    const void *k = (const void *)smk::lo::lo_newton_batch_kernel<4>;
+    if (L.per_sm == 0) {
+        LO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L.per_sm, k, BLOCK, 0));
+        if (L.per_sm < 1) return lo_fail(SM_ERR_CUDA, "the batched low-order kernel does not fit on an SM");
+    }
+    const long long cap_blocks = (long long)L.per_sm * nsm;
+    if (n > cap_blocks)
+        return lo_fail(SM_ERR_UNSUPPORTED, "more batch members than co-resident low-order blocks");
+    // blocks per problem: one each, the rest in proportion to the cells
+    std::vector<long long> need(n), nb(n, 1);
+    long long extra_need = 0;
+    for (int i = 0; i < n; ++i) {
+        need[i] = probs[members[i]]->lo->nblk_cell;
+        extra_need += need[i] - 1;
+    }
+    const long long rest = cap_blocks - n;
+    for (int i = 0; i < n; ++i) {
+        const long long e = extra_need <= rest ? need[i] - 1
+                                               : (long long)((double)(need[i] - 1) * rest / extra_need);
+        nb[i] += std::min(e, need[i] - 1);
+    }
+    int *single = L.h_int, *first = L.h_int + n;
+    first[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        sm_problem *p = probs[members[i]];
+        sm_lo_state &w = *p->lo;
+        const int m = members[i];
+        const Geo G = make_geo(p);
+        smk::lo::prepare_kernel<<<w.nblk_node, BLOCK, 0, s>>>(
+            G, clo[m], p->nc, 1.0 / (G.c * p->desc.dt), w.Fstar, nullptr, w.iaF, w.bF, w.ub, w.sc);
+        LO_CUDA(cudaGetLastError());
+        p->launches++;
+        L.h_args[i] = newton_args(p, w, G, clo[m], T[m], E[m], F[m], w.Tstar, cv[m], nullptr, prm,
+                                  (int)nb[i]);
+        single[i] = single_form(p, nsm) ? 1 : 0;
+        first[i + 1] = first[i] + (int)nb[i];
+        p->lo_pcg_form_used = single[i] ? SM_DEBUG_PCG_SINGLE : SM_DEBUG_PCG_TEXTBOOK;
+    }
+    LO_CUDA(cudaMemcpyAsync(L.d_args, L.h_args, sizeof(smk::lo::NewtonArgs) * n,
+                            cudaMemcpyHostToDevice, s));
+    LO_CUDA(cudaMemcpyAsync(L.d_int, L.h_int, sizeof(int) * (2 * n + 1), cudaMemcpyHostToDevice, s));
+    const smk::lo::NewtonArgs *da = L.d_args;
+    const int *ds = L.d_int, *df = L.d_int + n;
+    int nn = n;
+    void *args[] = {&da, &ds, &df, &nn};
+    LO_CUDA(cudaLaunchCooperativeKernel(k, dim3(first[n]), dim3(BLOCK), args, 0, s));
+    probs[members[0]]->launches++;
+    return SM_OK;
+}
+
 }  // namespace
 
 namespace smk {
+void batch_lo_free(void *scratch) {
+    if (!scratch) return;
+    BatchLO *L = static_cast<BatchLO *>(scratch);
+    if (L->h_args) cudaFreeHost(L->h_args);
+    if (L->d_args) cudaFree(L->d_args);
+    if (L->h_int) cudaFreeHost(L->h_int);
+    if (L->d_int) cudaFree(L->d_int);
+    delete L;
+}
 void lo_free(sm_problem *p) {
     if (!p->lo) return;
     sm_lo_state &w = *p->lo;
@@ -1498,6 +1672,7 @@ void sm_default_step_params(sm_step_params *prm) {
     prm->max_pcg = 5000;
     prm->max_elim = 40;
     prm->method = SM_METHOD_INDEPENDENT;
+    prm->refine = 0;
 }
 
 sm_status sm_loworder_newton(sm_problem *p, const double *closures_dev, const double *T_star_dev,
@@ -1557,6 +1732,15 @@ sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, 
     const int N = w.N;
     double *clo = closures_dev ? closures_dev : w.clo;
     const bool consistent = prm.method == SM_METHOD_CONSISTENT;
+    const bool refine = prm.refine != 0;
+    if (refine) {
+        if (consistent)
+            return lo_fail(SM_ERR_UNSUPPORTED, "the FP64 defect correction runs the independent method");
+        if (I_prev_dev == I_next_dev)
+            return lo_fail(SM_ERR_INVALID_ARG, "I_prev_dev and I_next_dev must not alias");
+        LO_TRY(smk::refine_ensure(p));
+        smk::refine_take_corrections(p);  // count this step's corrections only
+    }
     double *qmom_saved = p->qmom_dev;
     const double *qmom = nullptr;
     if (consistent) {
@@ -1565,11 +1749,24 @@ sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, 
         LO_TRY(sm_set_quadrant_moments(p, const_cast<double *>(qmom)));
     }
     LO_TRY(step_begin(p, scale_dev, T_dev, E_dev, moments_dev));
+    if (refine) {
+        // the iterate starts at I^k (its moments are moments_dev on entry)
+        const size_t bytes = (size_t)p->NQ * p->NWT * p->ncell * p->GW * 32 * p->nn * p->rsize;
+        LO_CUDA(cudaMemcpyAsync(I_next_dev, I_prev_dev, bytes, cudaMemcpyDeviceToDevice, s));
+    }
     sm_step_stats st{};
     double d1 = -1.0;
     for (int it = 1; it <= prm.max_outer; ++it) {
         // high-order solve with the current T: emission, sweep, moments, closures
-        LO_TRY(sm_sweep(p, T_dev, w.sigma, I_prev_dev, I_next_dev, moments_dev, clo));
+        if (refine) {
+            // FP64 residuals of the iterate and FP32 correction sweeps
+            SM_LO_CUDA_LAUNCH(smk::launch_emission(p, T_dev, w.sigma, nullptr, s));
+            LO_TRY(smk::refine_solve(p, static_cast<const double *>(I_prev_dev),
+                                     static_cast<double *>(I_next_dev), moments_dev));
+            SM_LO_CUDA_LAUNCH(smk::launch_closures_from_T(p, moments_dev, T_dev, w.sigma, clo, s));
+        } else {
+            LO_TRY(sm_sweep(p, T_dev, w.sigma, I_prev_dev, I_next_dev, moments_dev, clo));
+        }
         LO_TRY(sm_synchronize(p));
         LO_TRY(run_lo(p, clo, w.Tstar, cv_dev, T_dev, E_dev, F_dev, prm, &st, qmom));
         LO_TRY(launch_outer_change(p, T_dev, E_dev));
@@ -1583,6 +1780,7 @@ sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, 
             break;
         }
     }
+    if (refine) st.refine_corrections = smk::refine_take_corrections(p);
     if (consistent && !qmom_saved) LO_TRY(sm_set_quadrant_moments(p, nullptr));
     if (stats) *stats = st;
     return SM_OK;
@@ -1605,6 +1803,8 @@ sm_status sm_batch_step(sm_batch *b, const double *const *scale_dev,
     LO_TRY(check_params(prm));
     if (prm.method != SM_METHOD_INDEPENDENT)
         return lo_fail(SM_ERR_UNSUPPORTED, "sm_batch_step runs the independent method");
+    if (prm.refine)
+        return lo_fail(SM_ERR_UNSUPPORTED, "sm_batch_step has no FP64 defect correction");
     const std::vector<sm_problem *> &probs = smk::batch_members(b);
     const int n = (int)probs.size();
     for (int i = 0; i < n; ++i) {
@@ -1629,19 +1829,28 @@ sm_status sm_batch_step(sm_batch *b, const double *const *scale_dev,
     std::vector<unsigned char> active(n, 1);
     int n_active = n;
     const cudaStream_t s = smk::batch_stream(b);
+    // the batched low-order launch for 2D members (every member of a batch is
+    // 2D) unless a test forces one launch per member
+    const bool lo_batched = probs[0]->dim == 2 && smk::batch_lo_mode(b) != 0;
     for (int it = 1; it <= prm.max_outer && n_active > 0; ++it) {
         // high-order solve of every unconverged member in one batched pass
         // (emission, one persistent sweep launch, moments, closures)
         LO_TRY(smk::batch_pass(b, T_dev, sig.data(), I_prev_dev, I_next_dev, moments_dev,
                                clo.data(), active.data()));
-        // their low-order solves, one cooperative launch each, queued on the
-        // batch's stream without waiting in between
-        for (int i = 0; i < n; ++i) {
-            if (!active[i]) continue;
+        // their low-order solves in one cooperative launch (2D members), or
+        // one launch each, queued on the batch's stream without waiting in
+        // between
+        std::vector<int> act;
+        for (int i = 0; i < n; ++i)
+            if (active[i]) act.push_back(i);
+        if (lo_batched)
+            LO_TRY(batch_lo_launch(b, act, probs, clo.data(), cv_dev, T_dev, E_dev, F_dev, prm, s));
+        for (int i : act) {
             sm_problem *p = probs[i];
             sm_lo_state &w = *p->lo;
-            LO_TRY(launch_lo(p, clo[i], w.Tstar, cv_dev[i], T_dev[i], E_dev[i], F_dev[i], prm,
-                             nullptr));
+            if (!lo_batched)
+                LO_TRY(launch_lo(p, clo[i], w.Tstar, cv_dev[i], T_dev[i], E_dev[i], F_dev[i], prm,
+                                 nullptr));
             LO_TRY(launch_outer_change(p, T_dev[i], E_dev[i]));
             LO_CUDA(cudaMemcpyAsync(w.h_sc, w.sc, sizeof(smk::lo::Scalars),
                                     cudaMemcpyDeviceToHost, s));

@@ -1,5 +1,5 @@
-// Row a3 (final stage) and a4: sum the partial moments (the 2D sweep's single
-// accumulator, or the 1D sweep's per-warp partials in a fixed order) in FP64
+// Row a3 (final stage) and a4: sum the partial moments (the 2D sweep's
+// per-warp-task partials, the 1D sweep's per-warp partials) in a fixed order in FP64
 // and form the gray low-order closures of Sec. 2
 // (Eqs. sigmaE, sigmaF, sigma_P, additive_mg_correction) from them and the
 // nodal spectra left by the emission pass.  Also the pack / unpack kernels
@@ -91,6 +91,136 @@ __global__ void reduce_kernel(int dim, int nnodes_total, int nm, int nsets, size
     }
 }
 
+// The 2D form: the partials are [set][cell][36] (36 = 4 nodes x 9 moments, one
+// set per warp task).  A block of 8 cells x 36 slots: thread (cell, slot) sums
+// its slot over the sets in order (coalesced: the block reads 288 consecutive
+// values per set), the per-quadrant sums too when qmom is wanted; then one
+// thread per node forms the node's moments and closures from shared memory.
+constexpr int RCELLS = 8;
+
+// A fixed-order sum of the sets.  FP32 partials are summed as an unevaluated
+// pair (s, c) of FP32 numbers: TwoSum (Knuth) yields each addition's rounding
+// error exactly and the errors are summed on the side (Ogita, Rump and Oishi,
+// "Accurate sum and dot product", 2005: Sum2), so the pair carries the sum to
+// about twice FP32's precision at FP32 cost and becomes one FP64 value once per
+// slot.  On this GPU an FP64 add or conversion issues at 1/64 of the FP32 rate:
+// an FP64 running sum (a conversion and an add per set) made the reduction
+// FP64-bound at a sixth of the HBM bandwidth.
+template <typename RT> struct SetSum;
+template <> struct SetSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct SetSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = __fadd_rn(s, x);
+        const float z = __fsub_rn(t, s);
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z)));
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+template <typename RT>
+__global__ void __launch_bounds__(RCELLS * 36)
+reduce2d_kernel(int ncell, int nsets, double inv_c, const RT *__restrict__ part,
+                const double *__restrict__ gray, double *__restrict__ mom,
+                double *__restrict__ clo, double *__restrict__ qmom, int sets_per_q,
+                const int *__restrict__ active) {
+    if (active && *active == 0) return;  // a batch member that is not swept this pass
+    __shared__ double s_sum[RCELLS][36];
+    __shared__ double s_q[RCELLS][4][24];  // per quadrant: nodes x {phi, Fx, Fy, Pxx, Pxy, Pyy}
+    const int c = threadIdx.x / 36, m = threadIdx.x - 36 * c;
+    const int cell = blockIdx.x * RCELLS + c;
+    const size_t stride = (size_t)ncell * 36;
+    double acc = 0.0;
+    if (cell < ncell) {
+        const RT *pp = part + (size_t)cell * 36 + m;
+        const int k = m % 9;
+        if (qmom && k < 6) {
+            for (int q = 0; q < 4; ++q) {
+                SetSum<RT> qa;
+                const int s0 = min(q * sets_per_q, nsets), s1 = q == 3 ? nsets : min(s0 + sets_per_q, nsets);
+                for (int s = s0; s < s1; ++s) qa.add(pp[(size_t)s * stride]);
+                s_q[c][q][(m / 9) * 6 + k] = qa.value();
+                acc += qa.value();
+            }
+        } else {
+            SetSum<RT> sum;
+            int s = 0;
+            for (; s + 4 <= nsets; s += 4) {
+                const RT a0 = pp[(size_t)s * stride];
+                const RT a1 = pp[(size_t)(s + 1) * stride];
+                const RT a2 = pp[(size_t)(s + 2) * stride];
+                const RT a3 = pp[(size_t)(s + 3) * stride];
+                sum.add(a0);
+                sum.add(a1);
+                sum.add(a2);
+                sum.add(a3);
+            }
+            for (; s < nsets; ++s) sum.add(pp[(size_t)s * stride]);
+            acc = sum.value();
+        }
+    }
+    s_sum[c][m] = acc;
+    __syncthreads();
+    if (threadIdx.x >= RCELLS * 4) return;
+    const int cc = threadIdx.x >> 2, node = threadIdx.x & 3;
+    const int cl = blockIdx.x * RCELLS + cc;
+    if (cl >= ncell) return;
+    const size_t t = (size_t)cl * 4 + node;
+    const double *a = &s_sum[cc][node * 9];
+    if (qmom) {
+        for (int q = 0; q < 4; ++q) {
+            const double *v = &s_q[cc][q][node * 6];
+            double *o = qmom + (t * 4 + q) * 6;
+            const double ph = v[0];
+            o[0] = ph;
+            o[1] = v[1];
+            o[2] = v[2];
+            o[3] = v[3] + ph / 3.0;
+            o[4] = v[4];
+            o[5] = v[5] + ph / 3.0;
+        }
+    }
+    if (mom)
+        for (int k = 0; k < 9; ++k) mom[t * 9 + k] = a[k];
+    if (clo) {
+        const double sP = gray[t * 2 + 0], sF = gray[t * 2 + 1];
+        const double phi = a[0];
+        double *o = clo + t * 11;
+        o[0] = phi * inv_c;
+        o[1] = a[1];
+        o[2] = a[2];
+        o[3] = a[3];
+        o[4] = a[4];
+        o[5] = a[5];
+        o[6] = (phi > 0.0 && a[6] > 0.0) ? a[6] / phi : sP;
+        o[7] = sF;
+        o[8] = sP;
+        o[9] = sF * a[1] - a[7];
+        o[10] = sF * a[2] - a[8];
+    }
+}
+
+// The 2D reduction of partials in precision prec (the FP32 correction sweeps
+// of an FP64 problem's defect correction).
+cudaError_t launch_reduce_prec(int prec, const sm_problem *p, const void *part, int n_part,
+                               double *mom, double *clo, cudaStream_t s) {
+    const int blocks = (p->ncell + RCELLS - 1) / RCELLS;
+    const double inv_c = 1.0 / p->desc.c;
+    if (prec == 32)
+        reduce2d_kernel<float><<<blocks, RCELLS * 36, 0, s>>>(
+            p->ncell, n_part, inv_c, (const float *)part, p->d_gray, mom, clo, nullptr, 1, nullptr);
+    else
+        reduce2d_kernel<double><<<blocks, RCELLS * 36, 0, s>>>(
+            p->ncell, n_part, inv_c, (const double *)part, p->d_gray, mom, clo, nullptr, 1,
+            nullptr);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reduce(const sm_problem *p, const void *part, int n_part, double *mom,
                           double *clo, cudaStream_t s, double *qmom, int sets_per_q,
                           const int *active) {
@@ -98,6 +228,18 @@ cudaError_t launch_reduce(const sm_problem *p, const void *part, int n_part, dou
     const int threads = 128;
     const size_t stride = (size_t)n * p->nm;
     const double inv_c = 1.0 / p->desc.c;
+    if (p->dim == 2) {
+        const int blocks = (p->ncell + RCELLS - 1) / RCELLS;
+        if (p->prec == 32)
+            reduce2d_kernel<float><<<blocks, RCELLS * 36, 0, s>>>(
+                p->ncell, n_part, inv_c, (const float *)part, p->d_gray, mom, clo, qmom, sets_per_q,
+                active);
+        else
+            reduce2d_kernel<double><<<blocks, RCELLS * 36, 0, s>>>(
+                p->ncell, n_part, inv_c, (const double *)part, p->d_gray, mom, clo, qmom,
+                sets_per_q, active);
+        return cudaGetLastError();
+    }
     if (p->prec == 32)
         reduce_kernel<float><<<(n + threads - 1) / threads, threads, 0, s>>>(
             p->dim, n, p->nm, n_part, stride, inv_c, (const float *)part, p->d_gray, mom, clo,

@@ -19,8 +19,7 @@
 // device address, so the first call on each device (with that device
 // current) looks the address up with cudaGetSymbolAddress and caches it; the
 // first call in the process also uploads the Planck tables (synchronous
-// copies to constant memory).  Make that first call before any stream
-// capture.  Two threads making their first call at once both look the
+// copies to constant memory).  Two threads making their first call at once both look the
 // address up and store the same value (an atomic store).  All calls share
 // the array: calls that overlap on the GPU (two streams, two threads, two
 // devices' worth of work on one device) race and corrupt each other.  The

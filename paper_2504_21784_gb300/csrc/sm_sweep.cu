@@ -955,6 +955,31 @@ static size_t sweep2d_smem_total(int prec, int W, int GW, int S, int GSLOT, int 
     return smem;
 }
 
+// The 2D sweep kernel of arithmetic precision prec for problem p's layout and
+// tiling (the FP32 correction sweeps of an FP64 problem's defect correction).
+int sweep2d_max_resident_prec(int prec, const sm_problem *p, int W, int S, size_t *smem_out) {
+    const size_t smem = sweep2d_smem_bytes(prec, W, p->GW, S, p->GSLOT);
+    if (smem_out) *smem_out = smem;
+    const void *k = (prec == 32) ? kernel2d_ptr<float>(p->GW) : kernel2d_ptr<double>(p->GW);
+    int nsm = 0;
+    if (!allow_dynamic_smem(k, smem, &nsm)) return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, W * 32, smem) != cudaSuccess)
+        return 0;
+    return per_sm * nsm;
+}
+
+cudaError_t launch_sweep2d_prec(int prec, const sm_problem *p, const SweepArgs &a, int grid,
+                                cudaStream_t s) {
+    EmitArgs none;
+    memset(&none, 0, sizeof(none));
+    const size_t smem = sweep2d_smem_bytes(prec, a.W, a.GW, a.S, a.GW * a.LG);
+    const void *k = (prec == 32) ? kernel2d_ptr<float>(a.GW) : kernel2d_ptr<double>(a.GW);
+    SweepArgs args = a;
+    void *params[] = {&args, &none};
+    return cudaLaunchKernel(k, dim3(grid), dim3(a.W * 32), params, smem, s);
+}
+
 cudaError_t launch_sweep2d(const sm_problem *p, const SweepArgs &a, int grid, cudaStream_t s,
                            const EmitArgs *e) {
     EmitArgs none;

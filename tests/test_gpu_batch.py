@@ -210,21 +210,24 @@ _STEP_ORACLE = dict(eps_outer=1e-3, max_outer=100)
 _STEP_LO = dict(eps_inner=1e-3, max_inner=30, elim_rtol=1e-15, max_elim=100)
 
 
-@pytest.mark.parametrize("precision", [64, 32])
-def test_batch_step_matches_oracle(gpu_lib, precision):
+@pytest.mark.parametrize("precision,batched_lo", [(64, True), (32, True), (64, False)])
+def test_batch_step_matches_oracle(gpu_lib, precision, batched_lo):
     """Two time steps of Algorithm 1 for all six uneven members at once
     (sm_batch_step: one batched pass per outer iteration, FP64 low-order
-    solves, per-member stopping) against the oracle's steps of each member:
-    T and E within 1e-11 (FP64 sweep) / 1e-5 (FP32 sweep) of the field's
-    largest magnitude, and, on the FP64 path, each member's own outer and
-    Newton iteration counts.  Members start from radiative equilibrium at a
-    seeded non-uniform temperature, with two-material opacity maps."""
+    solves -- all members' in one cooperative launch, or, through the test
+    hook, one launch per member -- and per-member stopping) against the
+    oracle's steps of each member: T and E within 1e-11 (FP64 sweep) / 1e-5
+    (FP32 sweep) of the field's largest magnitude, and, on the FP64 path, each
+    member's own outer and Newton iteration counts.  Members start from
+    radiative equilibrium at a seeded non-uniform temperature, with
+    two-material opacity maps."""
     import torch
     from oracle import lo as L
     sm = gpu_lib
     cu = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
     tol = {64: 1e-11, 32: 1e-5}[precision]
     b = sm.Batch(MEMBERS, precision)
+    b.set_batched_lo(batched_lo)
     state, ref = [], []
     prm_o = L.StepParams(lo=L.LOParams(**_STEP_LO), **_STEP_ORACLE)
     for i, cfg in enumerate(MEMBERS):
@@ -265,8 +268,10 @@ def test_batch_step_matches_oracle(gpu_lib, precision):
                 assert stats[i]["outer_iters"] == st["outer"], (i, k, stats[i], st)
                 assert stats[i]["newton_iters_total"] == sum(st["newton"]), (i, k)
             outer.append((stats[i]["outer_iters"], st["outer"]))
-        print(f"batched step {k + 1} fp{precision}: outer (batch, oracle) per member {outer}")
-    print(f"batched steps fp{precision}: worst T {worst['T']:.2e} E {worst['E']:.2e}")
+        print(f"batched step {k + 1} fp{precision} (low-order solves batched {batched_lo}): "
+              f"outer (batch, oracle) per member {outer}")
+    print(f"batched steps fp{precision} (low-order solves batched {batched_lo}): "
+          f"worst T {worst['T']:.2e} E {worst['E']:.2e}")
     assert worst["T"] < tol and worst["E"] < tol
     b.close()
 

@@ -1,0 +1,130 @@
+"""FP64 defect correction of the FP32 sweep path (sm_step_params.refine):
+each outer iteration of Algorithm 1 forms the FP64 residual of the lumped DG
+transport equations at the intensity iterate and corrects it with FP32
+sweeps until the corrections are below 1e-8 of the iterate, so that the
+FP32 sweeps reach the FP64 solution.
+
+* multigroup and gray 2D cases, fixed outer-iteration counts (1 to 4): T, E,
+  F, phi and the returned intensity within 1e-11 of the oracle's FP64 step
+  (the FP64 bar), where the plain FP32 sweep path only reaches ~1e-7;
+* several steps in a row with the paper's controls: the same iteration counts
+  as the oracle and 1e-11 agreement at every step;
+* the option refuses FP32-state problems and the consistent method.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import lo as L
+from paper_2504_21784_gb300 import workloads as W
+
+from _cases import config
+
+pytestmark = pytest.mark.gpu
+
+
+def _field(a, b, scale=None):
+    s = np.abs(b).max() if scale is None else np.abs(scale).max()
+    return float(np.abs(a - b).max() / s)
+
+
+def _case(dim_nx_ny_G, seed):
+    nx, ny, G = dim_nx_ny_G
+    kind = W.OPACITY_POWER if G == 1 else W.OPACITY_LARSEN
+    cfg = config(2, nx, ny, G, 2, 4, kind=kind, T_bdr=(1.0, 0.2, 0.6, 0.0))
+    ncell, nn = cfg.n_cells, 4
+    rng = np.random.default_rng(seed)
+    Tk = W.temperature_random(ncell, nn, seed=seed + 1, lo=0.1, hi=0.8)
+    scale = W.scale_field(cfg, seed=seed + 2)
+    cv = 0.3 + 0.2 * rng.random((ncell, nn))
+    omx, omy, w = O.quadrature(2, cfg.n_polar, cfg.n_azim)
+    Ik = W.intensity_random(cfg.n_dir, G, ncell, nn, seed=seed + 3, scale=0.05)
+    sigma_k = O.opacity(cfg.opacity_kind, cfg.opacity_alpha, cfg.edges, Tk, scale)
+    mom_k = O.moments(2, omx, omy, w, sigma_k, Ik)
+    return cfg, Tk, scale, cv, Ik, mom_k
+
+
+@pytest.mark.parametrize("shape,n_outer", [((14, 11, 6), 1), ((14, 11, 6), 4),
+                                           ((17, 9, 1), 2), ((17, 9, 1), 3)])
+def test_refined_step_matches_oracle_fixed_iterations(gpu_lib, shape, n_outer):
+    import torch
+    sm = gpu_lib
+    cfg, Tk, scale, cv, Ik, mom_k = _case(shape, seed=7 + shape[0])
+    prm_o = L.StepParams(eps_outer=0.0, max_outer=n_outer,
+                         lo=L.LOParams(eps_inner=1e-13, max_inner=40, elim_rtol=1e-15,
+                                       max_elim=80))
+    Tr, Er, Fr, Ir, momr, st_r = L.sm_step(cfg, scale, cv, Tk, Ik, mom_k, prm_o)
+    cu = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    out = {}
+    for refine in (1, 0):
+        prec = 64 if refine else 32
+        prob = sm.Problem.from_config(cfg, prec)
+        T, E, F, mom = cu(Tk), prob.new_nodal(), prob.new_flux(), cu(mom_k)
+        Ip = prob.pack(cu(W.in_precision(Ik, prec)))
+        In = prob.empty_intensity()
+        st = prob.step(cu(scale), cu(cv), T, E, F, mom, Ip, In,
+                       params=sm.step_params(eps_outer=0.0, max_outer=n_outer, eps_inner=1e-13,
+                                             max_inner=40, pcg_rtol=1e-15, elim_rtol=1e-15,
+                                             max_elim=80, refine=refine))
+        # eps_outer = 0: n_outer iterations unless the change reaches round-off
+        # level first (both sides stop there alike)
+        assert st["outer_iters"] == st_r["outer"] <= n_outer
+        if refine:
+            corr = st["refine_corrections"]
+            assert st["outer_iters"] <= corr <= 4 * st["outer_iters"]
+        Ig = prob.unpack(In).cpu().numpy()
+        out[refine] = {"T": _field(T.cpu().numpy(), Tr), "E": _field(E.cpu().numpy(), Er),
+                       "F": _field(F.cpu().numpy(), Fr, scale=cfg.c * Er),
+                       "phi": _field(mom.cpu().numpy()[..., 0], momr[..., 0]),
+                       "I": max(_field(Ig[d, g], Ir[d, g]) for d in range(cfg.n_dir)
+                                for g in range(cfg.n_groups))}
+        prob.close()
+    print(f"{shape}, {n_outer} outer: refined FP32 sweeps ({corr} corrections) "
+          + "  ".join(f"{k} {v:.2e}" for k, v in out[1].items())
+          + " | plain FP32 sweep " + "  ".join(f"{k} {v:.2e}" for k, v in out[0].items()))
+    assert all(v < 1e-11 for v in out[1].values()), out[1]
+
+
+def test_refined_steps_match_oracle_with_paper_controls(gpu_lib):
+    """Three steps in a row with the paper's epsilon (parity mode): the same
+    outer and Newton counts as the oracle and 1e-11 agreement at each step."""
+    import torch
+    sm = gpu_lib
+    cfg, Tk, scale, cv, Ik, mom_k = _case((16, 12, 5), seed=21)
+    prm_o = L.StepParams(eps_outer=1e-3, max_outer=100,
+                         lo=L.LOParams(eps_inner=1e-3, max_inner=30, elim_rtol=1e-15,
+                                       max_elim=100))
+    cu = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    prob = sm.Problem.from_config(cfg, 64)
+    T, E, F, mom = cu(Tk), prob.new_nodal(), prob.new_flux(), cu(mom_k)
+    I = [prob.pack(cu(Ik)), prob.empty_intensity()]
+    prm = sm.step_params(eps_outer=1e-3, eps_inner=1e-3, pcg_rtol=1e-15, max_pcg=20000,
+                         elim_rtol=1e-15, max_elim=100, refine=1)
+    Tr, Ir, momr = Tk, Ik, mom_k
+    for k in range(3):
+        Tr, Er, Fr, Ir, momr, st_r = L.sm_step(cfg, scale, cv, Tr, Ir, momr, prm_o)
+        st = prob.step(cu(scale), cu(cv), T, E, F, mom, I[k % 2], I[(k + 1) % 2], params=prm)
+        eT, eE = _field(T.cpu().numpy(), Tr), _field(E.cpu().numpy(), Er)
+        print(f"refined step {k + 1}: T {eT:.2e} E {eE:.2e} outer {st['outer_iters']} "
+              f"corrections {st['refine_corrections']} "
+              f"(oracle {st_r['outer']}) newton {st['newton_iters_total']} "
+              f"(oracle {sum(st_r['newton'])})")
+        assert st["outer_iters"] == st_r["outer"]
+        assert st["newton_iters_total"] == sum(st_r["newton"])
+        assert eT < 1e-11 and eE < 1e-11
+    prob.close()
+
+
+def test_refine_refuses_fp32_state_and_the_consistent_method(gpu_lib):
+    import torch
+    sm = gpu_lib
+    cfg, Tk, scale, cv, Ik, mom_k = _case((8, 8, 3), seed=3)
+    cu = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    for prec, method in ((32, sm.METHOD_INDEPENDENT), (64, sm.METHOD_CONSISTENT)):
+        prob = sm.Problem.from_config(cfg, prec)
+        with pytest.raises(sm.SMError) as ei:
+            prob.step(cu(scale), cu(cv), cu(Tk), prob.new_nodal(), prob.new_flux(), cu(mom_k),
+                      prob.pack(cu(Ik)), prob.empty_intensity(),
+                      params=sm.step_params(refine=1, method=method))
+        assert ei.value.code == 7  # SM_ERR_UNSUPPORTED
+        prob.close()

@@ -6,6 +6,8 @@ adjoint workload's gradient against central differences on a fixed cell set.
 * 2D multigroup (256x256 cells, 128 directions, 64 groups): one step from the
   equilibrium start, FP64 and FP32 sweeps (the oracle sweeps one direction at a
   time: the previous intensity B_g(T0)/4pi is the same for every direction);
+* both: also the FP32 sweeps with FP64 defect correction (sm_step_params.refine,
+  FP64 state), held to the FP64 bar;
 * adjoint workload (128x128 cells, 64 directions, 16 groups, 20 steps, warm
   start): dJ/ds_K against central differences of the GPU forward on 32 cells
   drawn (seed 21784) from the four cell columns next to the right edge, a set
@@ -47,19 +49,20 @@ def _cu(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-def _gpu_steps(sm, cfg, precision, nsteps, state):
+def _gpu_steps(sm, cfg, precision, nsteps, state, refine=0):
     """nsteps steps of Algorithm 1 through sm_step from the equilibrium start;
-    per step T, E, phi and the statistics."""
+    per step T, E, phi and the statistics (refine = 1: FP64 state, FP32
+    correction sweeps)."""
     import torch
     T0, I_dir, mom0, scale, cv = state
-    prob = sm.Problem.from_config(cfg, precision)
+    prob = sm.Problem.from_config(cfg, 64 if refine else precision)
     canon = _cu(I_dir)[None].expand(cfg.n_dir, -1, -1, -1).contiguous()
     Ip = prob.pack(canon)
     del canon
     torch.cuda.empty_cache()
     T, E, F, mom = _cu(T0), prob.new_nodal(), prob.new_flux(), _cu(mom0)
     sc, cvd = _cu(scale), _cu(cv)
-    prm = sm.step_params(**PARITY_GPU)
+    prm = sm.step_params(refine=refine, **PARITY_GPU)
     out = []
     for _ in range(nsteps):
         In = prob.empty_intensity()
@@ -143,14 +146,16 @@ def test_multigroup_step_matches_oracle(gpu_lib):
     cfg = W.multigroup_2d()
     state = J.start_state(cfg)
     gpu = {p: _gpu_steps(gpu_lib, cfg, p, 1, state)[0] for p in (64, 32)}
+    gpu["refined"] = _gpu_steps(gpu_lib, cfg, 32, 1, state, refine=1)[0]
     ref = J.result("multigroup_1")
-    for p in (64, 32):
-        e, same = _compare(cfg.name, gpu[p], ref, p)
+    for p in (64, 32, "refined"):
+        bar = 64 if p == "refined" else p   # the refined FP32 path is held to the FP64 bar
+        e, same = _compare(f"{cfg.name}{' refined' if p == 'refined' else ''}", gpu[p], ref, bar)
         assert gpu[p]["stats"]["converged"] == 1
-        if p == 64:
-            assert same, "FP64 path took other iteration counts than the oracle"
-        bad = {k: v for k, v in e.items() if not v <= TOL[p]}
-        assert not bad, f"fp{p} step parity above {TOL[p]}: {bad}"
+        if bar == 64:
+            assert same, f"{p} path took other iteration counts than the oracle"
+        bad = {k: v for k, v in e.items() if not v <= TOL[bar]}
+        assert not bad, f"{p} step parity above {TOL[bar]}: {bad}"
 
 
 @pytest.mark.oracle_job("gray_channel_20")
@@ -160,19 +165,24 @@ def test_gray_channel_twenty_steps_match_oracle(gpu_lib):
     cfg = W.gray_channel_2d()
     state = J.start_state(cfg)
     gpu = {p: _gpu_steps(gpu_lib, cfg, p, cfg.steps, state) for p in (64, 32)}
+    gpu["refined"] = _gpu_steps(gpu_lib, cfg, 32, cfg.steps, state, refine=1)
     ref = J.result("gray_channel_20")
     assert len(ref) == cfg.steps
-    worst = {64: {}, 32: {}}
+    paths = (64, 32, "refined")
+    worst = {p: {} for p in paths}
     for k in range(cfg.steps):
-        for p in (64, 32):
-            e, same = _compare(f"{cfg.name} step {k + 1}", gpu[p][k], ref[k], p)
+        for p in paths:
+            bar = 64 if p == "refined" else p   # the refined FP32 path: the FP64 bar
+            e, same = _compare(f"{cfg.name} step {k + 1}{' refined' if p == 'refined' else ''}",
+                               gpu[p][k], ref[k], bar)
             assert gpu[p][k]["stats"]["converged"] == 1
-            if p == 64:
-                assert same, f"FP64 path took other iteration counts than the oracle at step {k + 1}"
+            if bar == 64:
+                assert same, f"{p} path took other iteration counts than the oracle at step {k + 1}"
             for n, v in e.items():
                 worst[p][n] = max(worst[p].get(n, 0.0), v)
-    for p in (64, 32):
-        print(f"[{cfg.name} 20 steps fp{p}] worst " +
+    for p in paths:
+        bar = 64 if p == "refined" else p
+        print(f"[{cfg.name} 20 steps {p}] worst " +
               "  ".join(f"{n} {v:.2e}" for n, v in worst[p].items()))
-        bad = {n: v for n, v in worst[p].items() if not v <= TOL[p]}
-        assert not bad, f"fp{p} step parity above {TOL[p]}: {bad}"
+        bad = {n: v for n, v in worst[p].items() if not v <= TOL[bar]}
+        assert not bad, f"{p} step parity above {TOL[bar]}: {bad}"
