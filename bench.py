@@ -357,7 +357,8 @@ def config_sweeps(sm, W, stream, reps: int = 20):
                 if alg is not None:
                     r["sweep_hbm_frac"] = alg["per_launch"] / (sweep_ms * 1e-3) / 1e9 / peak
                     r["tiling"] = {k: prob.info[k] for k in ("strip_width", "prefetch_rows",
-                                                             "groups_per_warp")}
+                                                             "groups_per_warp", "tail_strips",
+                                                             "emission_warps")}
                 res[f"fp{prec}"] = r
                 prob.close()
         out[cfg.name] = res
@@ -821,7 +822,8 @@ def main():
                    f"({prob.info['intensity_bytes'] / 1e9:.1f} GB per intensity copy)",
                    "tiling": {k: prob.info[k] for k in ("strip_width", "prefetch_rows",
                                                         "groups_per_warp", "n_tasks",
-                                                        "n_strips")},
+                                                        "n_strips", "tail_strips",
+                                                        "emission_warps")},
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "kernel_ms": {"emission": ktimes["emission_ms"] / max(ktimes["count"], 1),
                       "sweep": sweep_ms,

@@ -95,6 +95,7 @@ typedef struct {
     size_t workspace_bytes;    /* device scratch the library owns */
     double alpha;              /* Eq. alpha: sum w |Omega.n| / sum w with S_N quadrature */
     int emission_warps;        /* 2D: warps per sweep CTA computing the emission (0: own kernel) */
+    int tail_strips;           /* 2D: half-width strips at each end of the x range (0: uniform) */
 } sm_problem_info;
 
 /* Create a problem: builds the S_N set (Sec. 2; Gauss-Legendre in 1D,
@@ -126,8 +127,22 @@ sm_status sm_set_tiling(sm_problem *p, int strip_width, int prefetch_rows);
  * streaming sweep leaves idle; a sweep task whose strip is not complete yet
  * computes emission items itself until it is.  The source records are the
  * same either way (the Planck evaluation is shared).  Batch members refuse
- * (UNSUPPORTED).  sm_autotune also picks between 0 and 2.  Synchronizes. */
+ * (UNSUPPORTED), and so does a problem with tail strips (below).  sm_autotune
+ * also picks among 0, 2 and 4.  Synchronizes. */
 sm_status sm_set_emission_warps(sm_problem *p, int warps);
+
+/* Strip layout of the 2D wavefront: n (0..4) strips of strip_width / 2 cell
+ * columns at each end of the x range, full-width strips in between (0, the
+ * default: every strip full width, the last one ragged).  The persistent
+ * sweep grid takes the strips' tasks in upwind order; the sweeps in both x
+ * directions end on half-width strips, so the last, partial wave of tasks is
+ * shorter.  The results do not depend on the layout (the packed intensity
+ * layout does not change).  Needs an even strip_width, at least one
+ * full-width strip in between (else the layout falls back to 0, reported by
+ * sm_get_info) and the separate emission kernel (UNSUPPORTED with fused
+ * emission warps or for a batch member).  sm_autotune also picks among 0, 1
+ * and 2.  Synchronizes. */
+sm_status sm_set_tail_strips(sm_problem *p, int n);
 
 /* Copy the discrete ordinates {Omega_d, w_d} (Sec. 2) to host arrays of
  * n_dir entries each in the canonical order (omy is all zero in 1D). */
@@ -291,13 +306,16 @@ sm_status sm_loworder_newton(sm_problem *p, const double *closures_dev, const do
  * With params->refine = 1 (2D, a precision-64 problem: FP64 state and
  * emission, independent method) each outer iteration replaces the FP64 sweep
  * by defect corrections of the intensity iterate (which starts at I^k): the
- * FP64 residual of the lumped DG equations at the iterate, an FP32 sweep of
- * the correction with zero inflow and the FP64 update, repeated (at most 4
- * times) until a correction is below 1e-8 of the iterate; then the FP64
- * moments of the iterate.  The FP32 sweeps then give the FP64 sweep's
- * intensity up to rounding, and the step the FP64 step's result;
- * stats->refine_corrections counts the corrections.  Synchronizes after each
- * correction.
+ * residual of the lumped DG equations at the iterate, an FP32 sweep of the
+ * correction with zero inflow and the update, repeated (at most 4 times)
+ * until a correction is below 1e-8 of the iterate; then the moments of the
+ * iterate.  The residual, the update and the moment sums run in double-FP32
+ * arithmetic (each value a pair of FP32 numbers, about 48 significant bits,
+ * on the FP32 pipes), so the FP32 sweeps give the FP64 sweep's intensity to
+ * about 1e-14 and the step the FP64 step's result; during the step I_next
+ * holds the iterate as such pairs (its contents are unspecified if the step
+ * fails) and is converted to FP64 at its end.  stats->refine_corrections
+ * counts the corrections.  Synchronizes after each correction.
  * With params->method = SM_METHOD_CONSISTENT (2D) the sweeps also form
  * per-quadrant moments (in the buffer registered with
  * sm_set_quadrant_moments, else in the library's own) and the low-order
@@ -329,7 +347,8 @@ sm_status sm_unpack_intensity(sm_problem *p, const void *I_packed_dev, double *I
  * invalid).  Clears the device status word. */
 sm_status sm_synchronize(sm_problem *p);
 
-/* Pick strip_width, prefetch_rows and the fused emission warps (0, 2 or 4) by
+/* Pick strip_width, prefetch_rows, the fused emission warps (0, 2 or 4) and
+ * the tail strips (0, 1 or 2, with the separate emission kernel only) by
  * timing each candidate whole pass on the given inputs with CUDA events
  * (reps timed passes each after one warm-up); the fastest is kept.
  * Overwrites I_out_dev.  Synchronous. */

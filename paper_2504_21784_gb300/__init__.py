@@ -31,7 +31,7 @@ EXPORTED = ["sm_create_problem", "sm_destroy_problem", "sm_get_info", "sm_set_st
             "sm_launch_count", "sm_last_error", "sm_status_string",
             "sm_debug_set_wait_limit_ns", "sm_debug_skip_publish", "sm_debug_withhold_lo_block",
             "sm_debug_set_pcg_form", "sm_debug_get_pcg_form", "sm_debug_exp_neg",
-            "sm_debug_set_batch_lo",
+            "sm_debug_set_batch_lo", "sm_set_tail_strips",
             "sm_sweep_static",
             "sm_default_step_params", "sm_loworder_newton", "sm_step",
             "sm_create_batch", "sm_destroy_batch", "sm_batch_problem", "sm_batch_get_info",
@@ -67,7 +67,7 @@ class ProblemInfo(ctypes.Structure):
         "n_groups_padded", "n_warp_tasks", "strip_width", "prefetch_rows", "n_tasks", "n_strips")] + [
         ("intensity_elems", ctypes.c_size_t), ("intensity_bytes", ctypes.c_size_t),
         ("workspace_bytes", ctypes.c_size_t), ("alpha", ctypes.c_double),
-        ("emission_warps", ctypes.c_int)]
+        ("emission_warps", ctypes.c_int), ("tail_strips", ctypes.c_int)]
 
 
 class StepParams(ctypes.Structure):
@@ -151,6 +151,7 @@ def load():
         "sm_debug_get_pcg_form": [P, ctypes.POINTER(ctypes.c_int)],
         "sm_debug_exp_neg": [P, P, I, P],
         "sm_debug_set_batch_lo": [P, I],
+        "sm_set_tail_strips": [P, I],
         "sm_sweep_static": [ctypes.POINTER(ProblemDesc), P, P, P, P, P, P, P],
         "sm_loworder_newton": [P, P, P, P, P, P, P, P, ctypes.POINTER(StepParams),
                                ctypes.POINTER(StepStats)],
@@ -291,6 +292,12 @@ class Problem:
         """0: the emission runs as its own kernel; 1..4: that many warps per
         sweep CTA compute it inside the sweep kernel (sm_set_emission_warps)."""
         _check(load().sm_set_emission_warps(self._h, int(warps)))
+        self.refresh_info()
+
+    def set_tail_strips(self, n: int):
+        """n half-width strips at each end of the x range (sm_set_tail_strips;
+        0: uniform strips)."""
+        _check(load().sm_set_tail_strips(self._h, int(n)))
         self.refresh_info()
 
     def set_stream(self, stream):

@@ -98,7 +98,7 @@ void free_all(sm_problem *p) {
     void *bufs[] = {p->d_edges, p->d_inflow, p->d_lanes, p->d_dir_of, p->d_src,
                     p->d_mom_acc, p->d_gray, p->d_part, p->d_face, p->d_flags,
                     p->ctrl_borrowed ? nullptr : p->d_ctrl, p->d_mom_tmp, p->d_T_tmp,
-                    p->d_sig_tmp, p->d_clo_tmp, p->d_emit_ctr};
+                    p->d_sig_tmp, p->d_clo_tmp, p->d_emit_ctr, p->d_strip_x0};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete p->tabs;
@@ -124,11 +124,33 @@ cudaEvent_t *timing_events(sm_problem *p, int n) {
     return &p->ev_pool[4 * n];
 }
 
+// First cell column of each strip (and nx) for strips of W columns with
+// `tail` strips of W/2 columns at each end of the x range; empty when that
+// layout does not exist (tail > 0 needs an even W and at least one strip of
+// W columns in between).
+std::vector<int> strip_layout(int nx, int W, int tail) {
+    std::vector<int> x0;
+    if (tail <= 0) return x0;
+    const int h = W / 2, mid = nx - 2 * tail * h;
+    if (W % 2 || h < 1 || mid < W) return x0;
+    int x = 0;
+    for (int i = 0; i < tail; ++i, x += h) x0.push_back(x);
+    for (; x < tail * h + mid; x += W) x0.push_back(x);
+    x = tail * h + mid;
+    for (int i = 0; i < tail; ++i, x += h) x0.push_back(x);
+    x0.push_back(nx);
+    return x0;
+}
+
 // (Re)allocate the tiling-dependent workspace: W cell columns (= warps) per
-// CTA and S prefetched rows per warp for the 2D sweep, and E warps per CTA
+// CTA and S prefetched rows per warp for the 2D sweep, E warps per CTA
 // computing the emission inside the sweep kernel (0: its own kernel; E < 0
-// keeps the current number).
-sm_status apply_tiling(sm_problem *p, int W, int S, int E = -1) {
+// keeps the current number), and `tail` half-width strips at each end of the
+// x range (shorter tasks for the partial last wave of the persistent grid;
+// tail < 0 keeps the current number, which falls to 0 where the layout does
+// not exist).  The strips' tasks go through the queue in the same upwind
+// order either way.
+sm_status apply_tiling(sm_problem *p, int W, int S, int E = -1, int tail = -1) {
     if (p->dim == 1) {
         p->W = 1;
         p->S = 0;
@@ -146,6 +168,13 @@ sm_status apply_tiling(sm_problem *p, int W, int S, int E = -1) {
             return fail(SM_ERR_INVALID_ARG, "emission warps: 0..4 and strip_width + warps <= 16");
         if (E > 0 && p->batch_owned)
             return fail(SM_ERR_UNSUPPORTED, "batch members run the emission as its own kernel");
+        if (tail < 0) tail = p->tail;
+        if (tail > 0 && (E > 0 || p->batch_owned))
+            return fail(SM_ERR_UNSUPPORTED,
+                        "half-width end strips need the separate emission kernel and a problem "
+                        "of its own");
+        std::vector<int> x0 = strip_layout(p->nx, W, tail);
+        if (x0.empty()) tail = 0;
         const int old_W = p->W, old_S = p->S;
         p->W = W;
         p->S = S;
@@ -159,7 +188,14 @@ sm_status apply_tiling(sm_problem *p, int W, int S, int E = -1) {
         }
         p->resident = resident;
         p->emit_warps = E;
-        p->NS = (p->nx + W - 1) / W;
+        p->tail = tail;
+        p->NS = tail > 0 ? (int)x0.size() - 1 : (p->nx + W - 1) / W;
+        if (tail > 0) {
+            sm_status st = dev_alloc(&p->d_strip_x0, sizeof(int) * x0.size(), nullptr);
+            if (st) return st;
+            SM_CUDA(cudaMemcpy(p->d_strip_x0, x0.data(), sizeof(int) * x0.size(),
+                               cudaMemcpyHostToDevice));
+        }
         if (E > 0) {
             if (!p->tabs) {
                 p->tabs = new smk::PlanckTabs();
@@ -226,6 +262,7 @@ smk::SweepArgs make_args(const sm_problem *p, const void *I_prev, void *I_out) {
     a.timeout_ns = p->timeout_ns;
     a.fault_skip_publish = p->fault_skip_publish;
     a.publish = smk::publish_rows(a.n_tasks, p->resident);
+    a.strip_x0 = p->tail > 0 ? p->d_strip_x0 : nullptr;
     return a;
 }
 
@@ -640,6 +677,7 @@ sm_status sm_get_info(const sm_problem *p, sm_problem_info *o) {
     o->workspace_bytes = p->workspace_bytes;
     o->alpha = p->alpha;
     o->emission_warps = p->emit_warps;
+    o->tail_strips = p->tail;
     return SM_OK;
 }
 
@@ -657,6 +695,16 @@ sm_status sm_set_tiling(sm_problem *p, int strip_width, int prefetch_rows) {
     SM_CUDA(cudaStreamSynchronize(p->stream));
     return apply_tiling(p, strip_width > 0 ? strip_width : p->W,
                         prefetch_rows > 0 ? prefetch_rows : p->S);
+}
+
+sm_status sm_set_tail_strips(sm_problem *p, int n) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    if (p->batch_owned)
+        return fail(SM_ERR_INVALID_ARG, "this problem belongs to a batch: sweep it with sm_batch_sweep");
+    if (n < 0 || n > 4) return fail(SM_ERR_INVALID_ARG, "tail strips must be in 0..4");
+    if (p->dim == 1) return n == 0 ? SM_OK : fail(SM_ERR_UNSUPPORTED, "tail strips are a 2D sweep feature");
+    SM_CUDA(cudaStreamSynchronize(p->stream));
+    return apply_tiling(p, p->W, p->S, -1, n);
 }
 
 sm_status sm_set_emission_warps(sm_problem *p, int warps) {
@@ -841,11 +889,13 @@ sm_status sm_autotune(sm_problem *p, const double *T, const double *sigma, const
     if ((st = check_intensity_align(I_prev, I_out))) return st;
     if (reps < 1) reps = 3;
     // strip width x prefetch depth x fused emission warps (0: the emission
-    // kernel runs before the sweep)
+    // kernel runs before the sweep) x half-width end strips (with the
+    // separate emission kernel only)
     const int w_c[] = {2, 4, 6, 8, 12, 14, 16};
     const int s_c[] = {2, 3, 4};
     const int e_c[] = {0, 2, 4};
-    int best_w = p->W, best_s = p->S, best_e = p->emit_warps;
+    const int t_c[] = {0, 1, 2};
+    int best_w = p->W, best_s = p->S, best_e = p->emit_warps, best_t = p->tail;
     float best_ms = 1e30f;
     const bool prof = p->profiling;
     p->profiling = false;
@@ -857,22 +907,28 @@ sm_status sm_autotune(sm_problem *p, const double *T, const double *sigma, const
         for (int sc : s_c) {
             for (int ec : e_c) {
                 if (wc + ec > 16) continue;
-                if (apply_tiling(p, wc, sc, ec) != SM_OK) continue;
-                st = run_sweep(p, T, sigma, I_prev, I_out, nullptr, nullptr);  // warm-up
-                if (st) break;
-                SM_CUDA(cudaEventRecord(a, p->stream));
-                for (int r = 0; r < reps && !st; ++r)
-                    st = run_sweep(p, T, sigma, I_prev, I_out, nullptr, nullptr);
-                SM_CUDA(cudaEventRecord(b, p->stream));
-                SM_CUDA(cudaEventSynchronize(b));
-                float ms = 0;
-                SM_CUDA(cudaEventElapsedTime(&ms, a, b));
-                if (st == SM_OK && ms < best_ms) {
-                    best_ms = ms;
-                    best_w = p->W;
-                    best_s = p->S;
-                    best_e = p->emit_warps;
+                for (int tc : t_c) {
+                    if (tc > 0 && ec > 0) continue;
+                    if (apply_tiling(p, wc, sc, ec, tc) != SM_OK) continue;
+                    if (p->tail != tc) continue;  // that layout does not exist here
+                    st = run_sweep(p, T, sigma, I_prev, I_out, nullptr, nullptr);  // warm-up
+                    if (st) break;
+                    SM_CUDA(cudaEventRecord(a, p->stream));
+                    for (int r = 0; r < reps && !st; ++r)
+                        st = run_sweep(p, T, sigma, I_prev, I_out, nullptr, nullptr);
+                    SM_CUDA(cudaEventRecord(b, p->stream));
+                    SM_CUDA(cudaEventSynchronize(b));
+                    float ms = 0;
+                    SM_CUDA(cudaEventElapsedTime(&ms, a, b));
+                    if (st == SM_OK && ms < best_ms) {
+                        best_ms = ms;
+                        best_w = p->W;
+                        best_s = p->S;
+                        best_e = p->emit_warps;
+                        best_t = p->tail;
+                    }
                 }
+                if (st) break;
             }
             if (st) break;
         }
@@ -882,7 +938,7 @@ sm_status sm_autotune(sm_problem *p, const double *T, const double *sigma, const
     cudaEventDestroy(b);
     p->profiling = prof;
     sm_status sync = sm_synchronize(p);
-    sm_status fin = apply_tiling(p, best_w, best_s, best_e);
+    sm_status fin = apply_tiling(p, best_w, best_s, best_e, best_t);
     if (st) return st;
     if (sync) return sync;
     return fin;

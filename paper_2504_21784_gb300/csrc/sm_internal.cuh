@@ -58,6 +58,8 @@ struct SweepArgs {
     int publish;             // 2D: rows per release of a strip's x-faces downwind
     const int *active;       // batch member: its tasks are skipped while *active == 0
                              // (NULL: always swept)
+    const int *strip_x0;     // 2D: [NS + 1] first cell column of each strip and nx
+                             // (NULL: strip s starts at s * W, the last one ragged)
 };
 
 // Emission fused into the 2D sweep kernel: `warps` extra warps per CTA
@@ -131,13 +133,17 @@ cudaError_t launch_sweep2d_prec(int prec, const sm_problem *p, const SweepArgs &
                                 cudaStream_t s);
 cudaError_t launch_reduce_prec(int prec, const sm_problem *p, const void *part, int n_part,
                                double *mom, double *clo, cudaStream_t s);
-// FP64 defect correction with FP32 sweeps (sm_refine.cu): workspace on first
-// use (FP64 2D problems only), the transport solve of one outer iteration by
-// corrections of the packed FP64 iterate I (residual, FP32 correction sweep,
-// I += d, until the corrections are small) and the FP64 moments of I,
+// FP64-accurate defect correction with FP32 sweeps (sm_refine.cu): workspace
+// on first use (FP64 2D problems only); at the start of a step I^k and the
+// iterate (in the caller's packed FP64 buffer I) as pairs of FP32 numbers;
+// the transport solve of one outer iteration by corrections of the iterate
+// (residual, FP32 correction sweep, I += d, until the corrections are small)
+// and the moments of I; at the end of the step I joined back into FP64;
 // release.
 sm_status refine_ensure(sm_problem *p);
-sm_status refine_solve(sm_problem *p, const double *I_k, double *I, double *mom);
+sm_status refine_begin(sm_problem *p, const double *I_k, void *I);
+sm_status refine_solve(sm_problem *p, void *I, double *mom);
+sm_status refine_end(sm_problem *p, void *I);
 int refine_take_corrections(sm_problem *p);  // corrections since the last call
 void refine_free(sm_problem *p);
 size_t sweep2d_smem_bytes(int prec, int W, int GW, int S, int GSLOT);
@@ -209,6 +215,8 @@ struct sm_problem {
     // tiling (2D): W cell columns (= warps) per CTA, S prefetched rows per warp
     int W, S, NS;
     int emit_warps = 0;  // 2D: emission warps fused into the sweep kernel (0: separate kernel)
+    int tail = 0;        // 2D: half-width strips at each end of the x range (0: uniform strips)
+    int *d_strip_x0 = nullptr;  // [NS + 1] first column of each strip when tail > 0
     int resident = 0;  // 2D sweep CTAs that fit on the GPU for (W, S, emit_warps)
     unsigned int *d_emit_ctr = nullptr;  // [1 + NS] fused-emission queue and strip counters
     smk::PlanckTabs *tabs = nullptr;     // host copy of the tables' parameter form

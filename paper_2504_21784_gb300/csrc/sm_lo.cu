@@ -1750,19 +1750,18 @@ sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, 
     }
     LO_TRY(step_begin(p, scale_dev, T_dev, E_dev, moments_dev));
     if (refine) {
-        // the iterate starts at I^k (its moments are moments_dev on entry)
-        const size_t bytes = (size_t)p->NQ * p->NWT * p->ncell * p->GW * 32 * p->nn * p->rsize;
-        LO_CUDA(cudaMemcpyAsync(I_next_dev, I_prev_dev, bytes, cudaMemcpyDeviceToDevice, s));
+        // I^k as pairs of FP32 numbers; the iterate (held as pairs in the
+        // caller's I_next buffer until the end of the step) starts there
+        LO_TRY(smk::refine_begin(p, static_cast<const double *>(I_prev_dev), I_next_dev));
     }
     sm_step_stats st{};
     double d1 = -1.0;
     for (int it = 1; it <= prm.max_outer; ++it) {
         // high-order solve with the current T: emission, sweep, moments, closures
         if (refine) {
-            // FP64 residuals of the iterate and FP32 correction sweeps
+            // residuals of the iterate and FP32 correction sweeps
             SM_LO_CUDA_LAUNCH(smk::launch_emission(p, T_dev, w.sigma, nullptr, s));
-            LO_TRY(smk::refine_solve(p, static_cast<const double *>(I_prev_dev),
-                                     static_cast<double *>(I_next_dev), moments_dev));
+            LO_TRY(smk::refine_solve(p, I_next_dev, moments_dev));
             SM_LO_CUDA_LAUNCH(smk::launch_closures_from_T(p, moments_dev, T_dev, w.sigma, clo, s));
         } else {
             LO_TRY(sm_sweep(p, T_dev, w.sigma, I_prev_dev, I_next_dev, moments_dev, clo));
@@ -1780,7 +1779,11 @@ sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, 
             break;
         }
     }
-    if (refine) st.refine_corrections = smk::refine_take_corrections(p);
+    if (refine) {
+        LO_TRY(smk::refine_end(p, I_next_dev));  // the iterate back into FP64
+        LO_TRY(sm_synchronize(p));
+        st.refine_corrections = smk::refine_take_corrections(p);
+    }
     if (consistent && !qmom_saved) LO_TRY(sm_set_quadrant_moments(p, nullptr));
     if (stats) *stats = st;
     return SM_OK;

@@ -1,28 +1,43 @@
-// FP64 defect correction of the transport solve with FP32 sweeps (the FP32
-// sweep path refined to FP64 accuracy inside the outer SM iteration).
+// FP64-accurate defect correction of the transport solve with FP32 sweeps
+// (the FP32 sweep path refined to the FP64 solution inside the outer SM
+// iteration).
 //
-// The state -- the intensity iterate, the previous step's intensity, the
-// emission records -- is FP64 (a precision-64 problem).  Each outer iteration
-// of Algorithm 1 replaces the FP64 sweep by corrections of the iterate I
-// (which starts at I^k), each
-//   1. the FP64 residual of the lumped upwind-DG equations (Eq. dgsn_transport
-//      with the time term of Eq. smm_be_transport) at I:
+// The caller's state -- the previous step's intensity I^k, the intensity of
+// the step, the emission records -- is FP64 (a precision-64 problem).  Each
+// outer iteration of Algorithm 1 replaces the FP64 sweep by corrections of
+// an intensity iterate I (which starts at I^k), each
+//   1. the residual of the lumped upwind-DG equations (Eq. dgsn_transport with
+//      the time term of Eq. smm_be_transport) at I:
 //      r = S + (upwind face terms of I) - M I per node, S = q + I^k/(c dt),
 //      stored in FP32;
 //   2. an FP32 sweep of the correction, M d = r + (upwind face terms of d)
 //      with zero inflow (the sweep kernel with q = 0 and r in place of I^k,
 //      1/(c dt) -> 1);
-//   3. I += d in FP64,
+//   3. I += d,
 // until a correction is below 1e-8 of the iterate (at most MAX_CORR per outer
 // iteration): a correction leaves the FP32 solve's relative error of d, so
-// the next one is that much smaller and the iterate reaches the FP64 solution
-// of the transport equations for the outer iteration's temperature -- the same
-// intensity the FP64 sweep computes, up to rounding.  One correction per outer
-// iteration would not do: its FP32 error would enter the closures and, through
-// the low-order solve, the next temperature, and the outer iteration carries
-// such errors along.  Then the FP64 moments of the iterate, read from it
-// directly (the sweep's fused FP32 moments of d would carry FP32 rounding of
-// the large first corrections into every later moment).
+// the next one is that much smaller and the iterate reaches the solution of
+// the transport equations for the outer iteration's temperature -- the FP64
+// sweep's intensity, up to rounding.  One correction per outer iteration
+// would not do: its FP32 error would enter the closures and, through the
+// low-order solve, the next temperature, and the outer iteration carries
+// such errors along.  Then the moments of the iterate, read from it directly
+// (the sweep's fused FP32 moments of d would carry FP32 rounding of the large
+// first corrections into every later moment).
+//
+// Double-FP32 arithmetic.  This GPU issues FP64 at 1/64 of its FP32 rate: an
+// FP64 residual (about 30 FP64 operations per cell, direction and group) and
+// FP64 updates and moment sums made the refined step slower than the FP64
+// sweep path.  So the iterate, I^k and the records are held during the step
+// as unevaluated sums hi + lo of two FP32 numbers (about 48 significant bits),
+// and the residual, the update and the moment sums use error-free FP32
+// transformations (TwoSum of Knuth, the FMA form of Dekker's product) on the
+// FP32 pipes; FP64 is used only to split the FP64 inputs into pairs once per
+// step (and the records once per outer iteration), to join the iterate back
+// into FP64 at the end of the step, and for the 36 dot products per (cell,
+// quadrant) of the moments.  The pairs keep their full precision for values
+// above about 1e-30 (below that the low part loses bits to FP32's range);
+// the residual's error is then about 2^-44 of the magnitude of its terms.
 //
 // The local cell system is the sweep kernel's (per node, divided by the nodal
 // mass; u / d = upwind / downwind side, A = sigma~ + mu + eta, mu =
@@ -33,12 +48,6 @@
 //   [ 0  -eta -mu  A  ] [I_dd]   [S_dd                      ]
 // with X the x-outflow of the upwind cell (its downwind-x nodes) or the
 // boundary inflow, Y the same along y.
-//
-// Cost on this GPU: the residual takes about 30 FP64 operations per
-// (cell, direction, group), the update 8 and the moments 9, against some 90 of
-// the FP64 sweep, and FP64 issues at 1/64 of the FP32 rate; with two
-// corrections per outer iteration the refined path costs about what the FP64
-// sweep does.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -50,17 +59,139 @@ namespace smk {
 constexpr int MAX_CORR = 4;         // corrections per outer iteration, at most
 constexpr double CORR_TOL = 1e-8;   // stop once max |d| <= CORR_TOL max |I|
 
+// ---------------------------------------------------------------------------
+// double-FP32 numbers (x = hi + lo, |lo| <= ulp(hi)/2); every operation is an
+// explicitly rounded FP32 operation, so the compiler neither contracts nor
+// reorders them.
+
+// a + b = s + e exactly (Knuth)
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return make_float2(s, e);
+}
+// a + b, absolute error within about 2^-44 (|a| + |b|) also where a and b
+// cancel (the residual's case)
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    float2 s = two_sum(a.x, b.x);
+    s.y = __fadd_rn(s.y, __fadd_rn(a.y, b.y));
+    return two_sum(s.x, s.y);
+}
+__device__ __forceinline__ float2 df_sub(float2 a, float2 b) {
+    return df_add(a, make_float2(-b.x, -b.y));
+}
+// a * b: the product of the high parts exactly (its error by one FMA), the
+// cross terms in FP32
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    return two_sum(p, e);
+}
+// a + d for an FP32 d
+__device__ __forceinline__ float2 df_add_f(float2 a, float d) {
+    float2 s = two_sum(a.x, d);
+    s.y = __fadd_rn(s.y, a.y);
+    return two_sum(s.x, s.y);
+}
+// the pair nearest to an FP64 x (FP64 operations: used once per value and step)
+__device__ __forceinline__ float2 df_split(double x) {
+    const float hi = __double2float_rn(x);
+    return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+__device__ __forceinline__ double df_join(float2 a) { return (double)a.x + (double)a.y; }
+
 struct RefineArgs {
     int nx, ny, ncell, NQ, NWT, NGB, DB, LG, GW, Gp;
-    double inv_cdt;
+    float2 inv_cdt;
     const LaneConst *lanes;
-    const double *src;     // [cell][Gp][8] FP64 records: q at the nodes, sigma~, sigma
-    const double *inflow;  // [4][Gp] FP64
-    const double *I_k;     // packed FP64 I^k (NULL: zero)
-    const double *I;       // packed FP64 iterate
-    float *r;              // packed FP32 residual (out)
-    size_t n_elems;        // packed elements / 4 (one thread each)
+    const float2 *mueta;    // [NQ*DB*32][2] mu, eta per lane as pairs
+    const float2 *rec;      // [cell][Gp][6] q at the 4 nodes, sigma~, sigma as pairs
+    const float2 *inflow;   // [4][Gp] pairs
+    const float2 *I_k;      // packed I^k as pairs ([element][node])
+    const float2 *I;        // packed iterate as pairs
+    float *r;               // packed FP32 residual (out)
+    size_t n_elems;         // packed elements (four nodes each; one thread each)
 };
+
+// The residual of one packed element (warp task wg of quadrant Q, cell,
+// slot, lane): four nodes.  The quadrant is a template parameter so that the
+// upwind/downwind roles of the nodes are compile-time register indices.
+template <int Q>
+__device__ __forceinline__ void residual_elem(const RefineArgs &R, const size_t e, const int lane,
+                                              const int slot, const int cell, const int wt) {
+    const int db = wt / R.NGB, gb = wt - db * R.NGB;
+    const int li = (Q * R.DB + db) * 32 + lane;
+    const LaneConst &L = R.lanes[li];
+    float4 *ro = reinterpret_cast<float4 *>(R.r) + e;
+    if (!L.valid) {
+        *ro = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const int g = gb * R.GW * R.LG + slot * R.LG + L.g_lo;
+    constexpr int sx = (Q == 0 || Q == 3) ? 1 : -1, sy = Q < 2 ? 1 : -1;
+    constexpr int au = sx > 0 ? 0 : 1, bu = sy > 0 ? 0 : 1;
+    constexpr int nuu = au + 2 * bu, ndu = (1 - au) + 2 * bu;
+    constexpr int nud = au + 2 * (1 - bu), ndd = (1 - au) + 2 * (1 - bu);
+    const int ix = cell % R.nx, iy = cell / R.nx;
+    // the packed elements of the same (warp task, slot, lane) at another cell
+    const ptrdiff_t cell_stride = (ptrdiff_t)R.GW * 32;
+    const float2 *Ic = R.I + e * 4;
+    float2 I[4], S[4];
+    const float2 *rec = R.rec + ((size_t)cell * R.Gp + g) * 6;
+    const float2 *ik = R.I_k + e * 4;
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        I[n] = Ic[n];
+        S[n] = df_add(rec[n], df_mul(R.inv_cdt, ik[n]));
+    }
+    float2 Xu, Xd, Yu, Yd;
+    if (ix - sx >= 0 && ix - sx < R.nx) {
+        const float2 *nb = Ic - sx * cell_stride * 4;
+        Xu = nb[ndu];
+        Xd = nb[ndd];
+    } else {
+        Xu = Xd = R.inflow[(sx > 0 ? 0 : 1) * R.Gp + g];
+    }
+    if (iy - sy >= 0 && iy - sy < R.ny) {
+        const float2 *nb = Ic - sy * (ptrdiff_t)R.nx * cell_stride * 4;
+        Yu = nb[nud];
+        Yd = nb[ndd];
+    } else {
+        Yu = Yd = R.inflow[(sy > 0 ? 2 : 3) * R.Gp + g];
+    }
+    const float2 mu = R.mueta[li * 2], eta = R.mueta[li * 2 + 1];
+    const float2 mu2 = make_float2(2.f * mu.x, 2.f * mu.y);  // exact
+    const float2 eta2 = make_float2(2.f * eta.x, 2.f * eta.y);
+    const float2 A = df_add(df_add(rec[4], mu), eta);
+    float r[4];
+    {
+        const float2 in = df_add(S[nuu], df_add(df_mul(mu2, Xu), df_mul(eta2, Yu)));
+        const float2 out = df_add(df_mul(A, I[nuu]), df_add(df_mul(mu, I[ndu]), df_mul(eta, I[nud])));
+        const float2 d = df_sub(in, out);
+        r[nuu] = __fadd_rn(d.x, d.y);
+    }
+    {
+        const float2 in = df_add(S[ndu], df_mul(eta2, Yd));
+        const float2 out = df_add(df_sub(df_mul(A, I[ndu]), df_mul(mu, I[nuu])), df_mul(eta, I[ndd]));
+        const float2 d = df_sub(in, out);
+        r[ndu] = __fadd_rn(d.x, d.y);
+    }
+    {
+        const float2 in = df_add(S[nud], df_mul(mu2, Xd));
+        const float2 out = df_add(df_sub(df_mul(A, I[nud]), df_mul(eta, I[nuu])), df_mul(mu, I[ndd]));
+        const float2 d = df_sub(in, out);
+        r[nud] = __fadd_rn(d.x, d.y);
+    }
+    {
+        const float2 out = df_sub(df_sub(df_mul(A, I[ndd]), df_mul(eta, I[ndu])), df_mul(mu, I[nud]));
+        const float2 d = df_sub(S[ndd], out);
+        r[ndd] = __fadd_rn(d.x, d.y);
+    }
+    *ro = make_float4(r[0], r[1], r[2], r[3]);
+}
 
 // One thread per (warp task, cell, slot, lane): the residual of its four
 // nodes.  Padding lanes (no direction) get r = 0, so their correction is 0.
@@ -74,109 +205,60 @@ __global__ void __launch_bounds__(256) residual_kernel(const RefineArgs R) {
     const int cell = (int)(rest % R.ncell);
     const int wg = (int)(rest / R.ncell);
     const int q = wg / R.NWT, wt = wg - q * R.NWT;
-    const int db = wt / R.NGB, gb = wt - db * R.NGB;
-    const LaneConst &L = R.lanes[(q * R.DB + db) * 32 + lane];
-    float *ro = R.r + e * 4;
-    const int g = gb * R.GW * R.LG + slot * R.LG + L.g_lo;
-    if (!L.valid) {
-        for (int n = 0; n < 4; ++n) ro[n] = 0.0f;
-        return;
+    switch (q) {
+        case 0: residual_elem<0>(R, e, lane, slot, cell, wt); break;
+        case 1: residual_elem<1>(R, e, lane, slot, cell, wt); break;
+        case 2: residual_elem<2>(R, e, lane, slot, cell, wt); break;
+        default: residual_elem<3>(R, e, lane, slot, cell, wt); break;
     }
-    const int sx = (q == 0 || q == 3) ? 1 : -1, sy = q < 2 ? 1 : -1;
-    const int au = sx > 0 ? 0 : 1, bu = sy > 0 ? 0 : 1;
-    const int nuu = au + 2 * bu, ndu = (1 - au) + 2 * bu;
-    const int nud = au + 2 * (1 - bu), ndd = (1 - au) + 2 * (1 - bu);
-    const int ix = cell % R.nx, iy = cell / R.nx;
-    // the packed elements of the same (warp task, slot, lane) at another cell
-    const size_t cell_stride = (size_t)R.GW * 32;
-    const double *Ic = R.I + e * 4;
-    double I[4], S[4];
-    for (int n = 0; n < 4; ++n) I[n] = Ic[n];
-    const double *rec = R.src + ((size_t)cell * R.Gp + g) * 8;
-    for (int n = 0; n < 4; ++n) S[n] = rec[n];
-    if (R.I_k) {
-        const double *ik = R.I_k + e * 4;
-        for (int n = 0; n < 4; ++n) S[n] = fma(R.inv_cdt, ik[n], S[n]);
-    }
-    double Xu, Xd, Yu, Yd;
-    if (ix - sx >= 0 && ix - sx < R.nx) {
-        const double *nb = Ic - (ptrdiff_t)(sx * (ptrdiff_t)cell_stride) * 4;
-        Xu = nb[ndu];
-        Xd = nb[ndd];
-    } else {
-        Xu = Xd = R.inflow[(sx > 0 ? 0 : 1) * R.Gp + g];
-    }
-    if (iy - sy >= 0 && iy - sy < R.ny) {
-        const double *nb = Ic - (ptrdiff_t)(sy * (ptrdiff_t)R.nx * (ptrdiff_t)cell_stride) * 4;
-        Yu = nb[nud];
-        Yd = nb[ndd];
-    } else {
-        Yu = Yd = R.inflow[(sy > 0 ? 2 : 3) * R.Gp + g];
-    }
-    const double mu = L.mu, eta = L.eta;
-    const double A = rec[4] + mu + eta;
-    double r[4];
-    r[nuu] = S[nuu] + 2.0 * (mu * Xu + eta * Yu) - (A * I[nuu] + mu * I[ndu] + eta * I[nud]);
-    r[ndu] = S[ndu] + 2.0 * eta * Yd - (A * I[ndu] - mu * I[nuu] + eta * I[ndd]);
-    r[nud] = S[nud] + 2.0 * mu * Xd - (A * I[nud] - eta * I[nuu] + mu * I[ndd]);
-    r[ndd] = S[ndd] - (A * I[ndd] - eta * I[ndu] - mu * I[nud]);
-    for (int n = 0; n < 4; ++n) ro[n] = (float)r[n];
 }
 
-// I += d (FP64 iterate, FP32 correction, the same packed layout, one
-// element of four nodes per thread), with max |d| and max |I| after the
-// update: non-negative IEEE numbers order like their bit patterns, so the
-// maxima are integer atomics on the bits (no FP64 compare).
-__global__ void __launch_bounds__(256) update_kernel(double *__restrict__ I,
+// I += d (the iterate as pairs, the FP32 correction in the same packed
+// layout, one element of four nodes per thread), with max |d| and max |I|
+// after the update: non-negative FP32 numbers order like their bit patterns,
+// so the maxima are integer atomics on the bits.
+__global__ void __launch_bounds__(256) update_kernel(float2 *__restrict__ I,
                                                      const float *__restrict__ d, size_t n_elems,
-                                                     unsigned long long *__restrict__ maxes) {
-    unsigned long long md = 0, mi = 0;
+                                                     unsigned int *__restrict__ maxes) {
+    unsigned md = 0, mi = 0;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_elems;
          e += (size_t)gridDim.x * blockDim.x) {
         const float4 dv = reinterpret_cast<const float4 *>(d)[e];
-        double2 *ip = reinterpret_cast<double2 *>(I) + e * 2;
-        double2 a = ip[0], b = ip[1];
-        a.x += (double)dv.x;
-        a.y += (double)dv.y;
-        b.x += (double)dv.z;
-        b.y += (double)dv.w;
-        ip[0] = a;
-        ip[1] = b;
-        const unsigned dm = max(max(__float_as_uint(fabsf(dv.x)), __float_as_uint(fabsf(dv.y))),
-                                max(__float_as_uint(fabsf(dv.z)), __float_as_uint(fabsf(dv.w))));
-        const unsigned long long abs_mask = 0x7fffffffffffffffull;
-        const unsigned long long im =
-            max(max((unsigned long long)__double_as_longlong(a.x) & abs_mask,
-                    (unsigned long long)__double_as_longlong(a.y) & abs_mask),
-                max((unsigned long long)__double_as_longlong(b.x) & abs_mask,
-                    (unsigned long long)__double_as_longlong(b.y) & abs_mask));
-        md = max(md, (unsigned long long)dm);
-        mi = max(mi, im);
+        float4 *ip = reinterpret_cast<float4 *>(I + e * 4);
+        const float4 a = ip[0], b = ip[1];
+        const float2 n0 = df_add_f(make_float2(a.x, a.y), dv.x);
+        const float2 n1 = df_add_f(make_float2(a.z, a.w), dv.y);
+        const float2 n2 = df_add_f(make_float2(b.x, b.y), dv.z);
+        const float2 n3 = df_add_f(make_float2(b.z, b.w), dv.w);
+        ip[0] = make_float4(n0.x, n0.y, n1.x, n1.y);
+        ip[1] = make_float4(n2.x, n2.y, n3.x, n3.y);
+        md = max(md, max(max(__float_as_uint(fabsf(dv.x)), __float_as_uint(fabsf(dv.y))),
+                         max(__float_as_uint(fabsf(dv.z)), __float_as_uint(fabsf(dv.w)))));
+        mi = max(mi, max(max(__float_as_uint(fabsf(n0.x)), __float_as_uint(fabsf(n1.x))),
+                         max(__float_as_uint(fabsf(n2.x)), __float_as_uint(fabsf(n3.x)))));
     }
-    for (int off = 16; off >= 1; off >>= 1) {
-        md = max(md, __shfl_xor_sync(0xffffffffu, md, off));
-        mi = max(mi, __shfl_xor_sync(0xffffffffu, mi, off));
-    }
+    md = __reduce_max_sync(0xffffffffu, md);
+    mi = __reduce_max_sync(0xffffffffu, mi);
     if ((threadIdx.x & 31) == 0) {
         atomicMax(maxes + 0, md);
         atomicMax(maxes + 1, mi);
     }
 }
 
-// FP64 moments of the packed FP64 iterate, per node: one warp per (quadrant,
-// direction block, cell); each lane sums its direction's intensities over all
-// groups of the direction block, plain and sigma-weighted (sigma_g from the
-// records), the sums pass through shared memory, and each lane forms one of
-// the 36 moments (4 nodes x {phi, F, P} and sigma-weighted {phi, F}) as the
-// dot product of the 32 lanes' sums with their weights; partial moments per
-// (quadrant, direction block) go to part[qd][cell][36] for the fixed-order
-// reduction.  Padding lanes have zero weights and padding groups zero
-// intensity.
+// Moments of the iterate, per node: one warp per (quadrant, direction block,
+// cell); each lane sums its direction's intensities over all groups of the
+// direction block as pairs, plain and sigma-weighted (sigma_g from the
+// records), the sums (joined into FP64) pass through shared memory, and each
+// lane forms one of the 36 moments (4 nodes x {phi, F, P} and sigma-weighted
+// {phi, F}) as the FP64 dot product of the 32 lanes' sums with their
+// weights; partial moments per (quadrant, direction block) go to
+// part[qd][cell][36] for the fixed-order reduction.  Padding lanes have zero
+// weights and padding groups zero intensity.
 constexpr int MOM_WARPS = 4;
 __global__ void __launch_bounds__(MOM_WARPS * 32)
-moments64_kernel(const double *__restrict__ I, const LaneConst *__restrict__ lanes,
-                 const double *__restrict__ src, int ncell, int NQ, int DB, int NGB, int NWT,
-                 int GW, int LG, int Gp, double *__restrict__ part) {
+moments_kernel(const float2 *__restrict__ I, const LaneConst *__restrict__ lanes,
+               const float2 *__restrict__ rec, int ncell, int NQ, int DB, int NGB, int NWT,
+               int GW, int LG, int Gp, double *__restrict__ part) {
     __shared__ double sh[MOM_WARPS][8][33];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const long long wglob = (long long)blockIdx.x * MOM_WARPS + wi;
@@ -184,27 +266,30 @@ moments64_kernel(const double *__restrict__ I, const LaneConst *__restrict__ lan
     const int qd = (int)(wglob / ncell), cell = (int)(wglob - (long long)qd * ncell);
     const int q = qd / DB, db = qd - q * DB;
     const LaneConst &L = lanes[qd * 32 + lane];
-    double s[4] = {0.0, 0.0, 0.0, 0.0}, ss[4] = {0.0, 0.0, 0.0, 0.0};
+    float2 s[4], ss[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) s[n] = ss[n] = make_float2(0.f, 0.f);
     for (int gb = 0; gb < NGB; ++gb) {
         const int wt = db * NGB + gb;
         const size_t e0 = (((size_t)q * NWT + wt) * ncell + cell) * GW;
         for (int gw = 0; gw < GW; ++gw) {
             const int g = gb * GW * LG + gw * LG + L.g_lo;
-            const double sg = src[((size_t)cell * Gp + g) * 8 + 5];
-            const double2 *ip = reinterpret_cast<const double2 *>(I) + ((e0 + gw) * 32 + lane) * 2;
-            const double2 a = ip[0], b = ip[1];
-            const double v[4] = {a.x, a.y, b.x, b.y};
+            const float2 sg = rec[((size_t)cell * Gp + g) * 6 + 5];
+            const float4 *ip = reinterpret_cast<const float4 *>(I + ((e0 + gw) * 32 + lane) * 4);
+            const float4 a = ip[0], b = ip[1];
+            const float2 v[4] = {make_float2(a.x, a.y), make_float2(a.z, a.w),
+                                 make_float2(b.x, b.y), make_float2(b.z, b.w)};
 #pragma unroll
             for (int n = 0; n < 4; ++n) {
-                s[n] += v[n];
-                ss[n] = fma(sg, v[n], ss[n]);
+                s[n] = df_add(s[n], v[n]);
+                ss[n] = df_add(ss[n], df_mul(sg, v[n]));
             }
         }
     }
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
-        sh[wi][n][lane] = s[n];
-        sh[wi][4 + n][lane] = ss[n];
+        sh[wi][n][lane] = df_join(s[n]);
+        sh[wi][4 + n][lane] = df_join(ss[n]);
     }
     __syncwarp();
     for (int m = lane; m < 36; m += 32) {
@@ -216,30 +301,64 @@ moments64_kernel(const double *__restrict__ I, const LaneConst *__restrict__ lan
     }
 }
 
-// FP32 records of the correction sweep: no emission (q = 0), the problem's
-// sigma~ and sigma rounded to FP32.
-__global__ void records32_kernel(const double *__restrict__ rec, float *__restrict__ out,
-                                 size_t n) {
+// Per (cell, group): the records as pairs (q at the nodes, sigma~, sigma) for
+// the residual and the moments, and the FP32 records of the correction
+// sweep (no emission, the problem's sigma~ and sigma).
+__global__ void records_kernel(const double *__restrict__ rec, float2 *__restrict__ rec_df,
+                               float *__restrict__ rec32, size_t n) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double *a = rec + i * 8;
-    float *o = out + i * 8;
-    for (int k = 0; k < 4; ++k) o[k] = 0.0f;
-    o[4] = (float)a[4];
-    o[5] = (float)a[5];
-    o[6] = 0.0f;
-    o[7] = 0.0f;
+    float2 *o = rec_df + i * 6;
+    for (int k = 0; k < 6; ++k) o[k] = df_split(a[k]);
+    float *f = rec32 + i * 8;
+    for (int k = 0; k < 4; ++k) f[k] = 0.0f;
+    f[4] = __double2float_rn(a[4]);
+    f[5] = __double2float_rn(a[5]);
+    f[6] = 0.0f;
+    f[7] = 0.0f;
+}
+
+// FP64 values to pairs (n values), and back (in place: each thread reads its
+// two FP32 numbers before it writes the FP64 number over them).
+__global__ void split_kernel(const double *__restrict__ x, float2 *__restrict__ y, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        y[i] = df_split(x[i]);
+}
+__global__ void join_kernel(void *xy, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float2 v = static_cast<const float2 *>(xy)[i];
+        static_cast<double *>(xy)[i] = df_join(v);
+    }
+}
+
+// mu, eta of every lane and the boundary inflow as pairs
+__global__ void tables_kernel(const LaneConst *__restrict__ lanes, int nlanes,
+                              const double *__restrict__ inflow, int ninflow,
+                              float2 *__restrict__ mueta, float2 *__restrict__ inflow_df) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nlanes) {
+        mueta[2 * i] = df_split(lanes[i].mu);
+        mueta[2 * i + 1] = df_split(lanes[i].eta);
+    }
+    if (i < ninflow) inflow_df[i] = df_split(inflow[i]);
 }
 
 }  // namespace smk
 
 struct sm_refine_state {
     float *r = nullptr, *d = nullptr;  // packed FP32 residual and correction
+    float2 *ik = nullptr;              // packed I^k as pairs
+    float2 *rec_df = nullptr;          // [cell][Gp][6] records as pairs
     float *rec32 = nullptr;            // [cell][Gp][8] FP32 records of the correction sweep
     float *inflow0 = nullptr;          // [4][Gp] zero inflow
+    float2 *mueta = nullptr;           // [NQ*DB*32][2]
+    float2 *inflow_df = nullptr;       // [4][Gp]
     double *part = nullptr;            // [NQ*DB][cell][36] partial moments of the iterate
-    unsigned long long *maxes = nullptr;    // max |d|, max |I| of the last update (bits)
-    unsigned long long *h_maxes = nullptr;  // pinned mirror
+    unsigned int *maxes = nullptr;     // max |d|, max |I| of the last update (FP32 bits)
+    unsigned int *h_maxes = nullptr;   // pinned mirror
     int W = 0, S = 0, NS = 0;          // tiling of the FP32 correction sweep
     int resident = 0;                  // its CTAs that fit
     int corrections = 0;               // corrections of the running step
@@ -250,7 +369,8 @@ namespace smk {
 void refine_free(sm_problem *p) {
     if (!p->refine) return;
     sm_refine_state &R = *p->refine;
-    for (void *b : {(void *)R.r, (void *)R.d, (void *)R.rec32, (void *)R.inflow0, (void *)R.part,
+    for (void *b : {(void *)R.r, (void *)R.d, (void *)R.ik, (void *)R.rec_df, (void *)R.rec32,
+                    (void *)R.inflow0, (void *)R.mueta, (void *)R.inflow_df, (void *)R.part,
                     (void *)R.maxes})
         if (b) cudaFree(b);
     if (R.h_maxes) cudaFreeHost(R.h_maxes);
@@ -269,17 +389,30 @@ sm_status refine_ensure(sm_problem *p) {
     const size_t ie = (size_t)p->NQ * p->NWT * p->ncell * p->GW * 32 * 4;
     const size_t nrec = (size_t)p->ncell * p->Gp;
     const size_t npart = (size_t)p->NQ * p->DB * p->ncell * 36;
+    const int nlanes = p->NQ * p->DB * 32;
     if (cudaMalloc(&R.r, ie * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&R.d, ie * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&R.ik, ie * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&R.rec_df, nrec * 6 * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&R.rec32, nrec * 8 * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&R.inflow0, (size_t)4 * p->Gp * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&R.mueta, (size_t)nlanes * 2 * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&R.inflow_df, (size_t)4 * p->Gp * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&R.part, npart * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&R.maxes, 2 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMallocHost(&R.h_maxes, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&R.maxes, 2 * sizeof(unsigned int)) != cudaSuccess ||
+        cudaMallocHost(&R.h_maxes, 2 * sizeof(unsigned int)) != cudaSuccess ||
         cudaMemset(R.inflow0, 0, (size_t)4 * p->Gp * sizeof(float)) != cudaSuccess) {
         refine_free(p);
         set_last_error("FP64 defect correction: device allocation failed");
         return SM_ERR_OOM;
+    }
+    const int ninfl = 4 * p->Gp, nt = std::max(nlanes, ninfl);
+    tables_kernel<<<(nt + 127) / 128, 128, 0, p->stream>>>(
+        p->d_lanes, nlanes, static_cast<const double *>(p->d_inflow), ninfl, R.mueta, R.inflow_df);
+    if (cudaGetLastError() != cudaSuccess) {
+        refine_free(p);
+        set_last_error("FP64 defect correction: table launch failed");
+        return SM_ERR_CUDA;
     }
     // the FP32 correction sweep's tiling: the widest strip (at most 16
     // columns) that fits with two prefetch stages and is no narrower than the
@@ -305,16 +438,71 @@ sm_status refine_ensure(sm_problem *p) {
         return SM_ERR_UNSUPPORTED;
     }
     R.NS = (p->nx + R.W - 1) / R.W;
-    p->workspace_bytes += ie * 8 + nrec * 32 + (size_t)16 * p->Gp + npart * 8 + 16;
+    p->workspace_bytes += ie * 16 + nrec * 80 + (size_t)20 * p->Gp + (size_t)nlanes * 16 +
+                          npart * 8 + 8;
+    return SM_OK;
+}
+
+// Start of a refined step: I^k (FP64, packed) as pairs, and the iterate (held
+// in the caller's FP64 buffer I, of the same size) set to them.
+sm_status refine_begin(sm_problem *p, const double *I_k, void *I) {
+    sm_refine_state &R = *p->refine;
+    const size_t nv = (size_t)p->NQ * p->NWT * p->ncell * p->GW * 32 * 4;
+    const unsigned blocks = (unsigned)std::min<size_t>((nv + 255) / 256, 152 * 16);
+    split_kernel<<<blocks, 256, 0, p->stream>>>(I_k, R.ik, nv);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(I, R.ik, nv * sizeof(float2), cudaMemcpyDeviceToDevice, p->stream) !=
+            cudaSuccess) {
+        set_last_error("FP64 defect correction: split launch failed");
+        return SM_ERR_CUDA;
+    }
+    p->launches++;
+    return SM_OK;
+}
+
+// End of a refined step: the iterate joined back into FP64, in place.
+sm_status refine_end(sm_problem *p, void *I) {
+    const size_t nv = (size_t)p->NQ * p->NWT * p->ncell * p->GW * 32 * 4;
+    const unsigned blocks = (unsigned)std::min<size_t>((nv + 255) / 256, 152 * 16);
+    join_kernel<<<blocks, 256, 0, p->stream>>>(I, nv);
+    if (cudaGetLastError() != cudaSuccess) {
+        set_last_error("FP64 defect correction: join launch failed");
+        return SM_ERR_CUDA;
+    }
+    p->launches++;
     return SM_OK;
 }
 
 // The transport solve of one outer iteration by defect correction of the
-// packed FP64 iterate I (the records hold the emission of the current
-// temperature), then the FP64 moments of I into mom.  I_k: the previous
-// step's intensity.  Synchronizes the stream after each correction (the
-// stopping test reads the maxima).
-sm_status refine_solve(sm_problem *p, const double *I_k, double *I, double *mom) {
+// iterate I (pairs, in the caller's buffer; the records hold the emission of
+// the current temperature), then the moments of I into mom.  Synchronizes
+// the stream after each correction (the stopping test reads the maxima).
+sm_status refine_solve(sm_problem *p, void *I, double *mom) {
+    if (p->refine->NS > p->NS) {
+        // the problem's tiling changed since the workspace was made: the face
+        // buffer and row flags hold p->NS strips, so pick the tiling again
+        // (the step's pairs of I^k are kept)
+        sm_refine_state &O = *p->refine;
+        int W = 0, S = 0, res = 0;
+        for (int w : {16, 14, 12, 8, 6, 4, 2}) {
+            if (w < p->W) break;
+            const int r = sweep2d_max_resident_prec(32, p, w, 2, nullptr);
+            if (r > 0) {
+                W = w;
+                S = 2;
+                res = r;
+                break;
+            }
+        }
+        if (res <= 0 || (p->nx + W - 1) / W > p->NS) {
+            set_last_error("FP64 defect correction: no correction-sweep tiling fits the face buffer");
+            return SM_ERR_UNSUPPORTED;
+        }
+        O.W = W;
+        O.S = S;
+        O.resident = res;
+        O.NS = (p->nx + W - 1) / W;
+    }
     sm_refine_state &R = *p->refine;
     cudaStream_t s = p->stream;
     const size_t ie = (size_t)p->NQ * p->NWT * p->ncell * p->GW * 32 * 4;
@@ -323,10 +511,11 @@ sm_status refine_solve(sm_problem *p, const double *I_k, double *I, double *mom)
         set_last_error(what);
         return SM_ERR_CUDA;
     };
-    records32_kernel<<<(unsigned)((nrec + 255) / 256), 256, 0, s>>>(
-        static_cast<const double *>(p->d_src), R.rec32, nrec);
+    records_kernel<<<(unsigned)((nrec + 255) / 256), 256, 0, s>>>(
+        static_cast<const double *>(p->d_src), R.rec_df, R.rec32, nrec);
     if (cudaGetLastError() != cudaSuccess) return cuda_fail("FP64 defect correction: records launch failed");
     p->launches++;
+    float2 *Iv = static_cast<float2 *>(I);
     RefineArgs A;
     A.nx = p->nx;
     A.ny = p->ny;
@@ -338,12 +527,16 @@ sm_status refine_solve(sm_problem *p, const double *I_k, double *I, double *mom)
     A.LG = p->LG;
     A.GW = p->GW;
     A.Gp = p->Gp;
-    A.inv_cdt = p->inv_cdt;
+    {
+        const float hi = (float)p->inv_cdt;
+        A.inv_cdt = make_float2(hi, (float)(p->inv_cdt - (double)hi));
+    }
     A.lanes = p->d_lanes;
-    A.src = static_cast<const double *>(p->d_src);
-    A.inflow = static_cast<const double *>(p->d_inflow);
-    A.I_k = I_k;
-    A.I = I;
+    A.mueta = R.mueta;
+    A.rec = R.rec_df;
+    A.inflow = R.inflow_df;
+    A.I_k = R.ik;
+    A.I = Iv;
     A.r = R.r;
     A.n_elems = ie / 4;
     for (int c = 0; c < MAX_CORR; ++c) {
@@ -359,37 +552,36 @@ sm_status refine_solve(sm_problem *p, const double *I_k, double *I, double *mom)
         a.W = R.W;
         a.S = R.S;
         a.NS = R.NS;
+        a.strip_x0 = nullptr;  // uniform strips of R.W columns
         a.n_tasks = R.NS * p->NQ * p->NWT;
         a.publish = publish_rows(a.n_tasks, R.resident);
         if (cudaMemsetAsync(p->d_ctrl, 0, 2 * sizeof(unsigned int), s) != cudaSuccess ||
             launch_sweep2d_prec(32, p, a, std::min(a.n_tasks, R.resident), s) != cudaSuccess ||
-            cudaMemsetAsync(R.maxes, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess)
+            cudaMemsetAsync(R.maxes, 0, 2 * sizeof(unsigned int), s) != cudaSuccess)
             return cuda_fail("FP64 defect correction: correction sweep launch failed");
-        update_kernel<<<std::max<size_t>(1, std::min<size_t>((ie / 4 + 255) / 256, 152 * 8)), 256, 0,
-                        s>>>(I, R.d, ie / 4, R.maxes);
+        update_kernel<<<(unsigned)std::max<size_t>(1, std::min<size_t>((ie / 4 + 255) / 256, 152 * 8)),
+                        256, 0, s>>>(Iv, R.d, ie / 4, R.maxes);
         if (cudaGetLastError() != cudaSuccess ||
-            cudaMemcpyAsync(R.h_maxes, R.maxes, 2 * sizeof(unsigned long long),
-                            cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            cudaMemcpyAsync(R.h_maxes, R.maxes, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                            s) != cudaSuccess)
             return cuda_fail("FP64 defect correction: update launch failed");
         p->launches += 3;
         ++R.corrections;
         const sm_status st = sm_synchronize(p);  // also reports a wavefront timeout
         if (st != SM_OK) return st;
-        unsigned dbits = (unsigned)R.h_maxes[0];
-        float dmax;
-        std::memcpy(&dmax, &dbits, sizeof(dmax));
-        double imax;
+        float dmax, imax;
+        std::memcpy(&dmax, &R.h_maxes[0], sizeof(dmax));
         std::memcpy(&imax, &R.h_maxes[1], sizeof(imax));
         if (!std::isfinite(dmax) || !std::isfinite(imax)) {
             set_last_error("FP64 defect correction: the correction is not finite");
             return SM_ERR_NONPHYSICAL;
         }
-        if ((double)dmax <= CORR_TOL * imax) break;
+        if ((double)dmax <= CORR_TOL * (double)imax) break;
     }
     const long long warps = (long long)p->NQ * p->DB * p->ncell;
-    moments64_kernel<<<(unsigned)((warps + MOM_WARPS - 1) / MOM_WARPS), MOM_WARPS * 32, 0, s>>>(
-        I, p->d_lanes, static_cast<const double *>(p->d_src), p->ncell, p->NQ, p->DB, p->NGB,
-        p->NWT, p->GW, p->LG, p->Gp, R.part);
+    moments_kernel<<<(unsigned)((warps + MOM_WARPS - 1) / MOM_WARPS), MOM_WARPS * 32, 0, s>>>(
+        Iv, p->d_lanes, R.rec_df, p->ncell, p->NQ, p->DB, p->NGB, p->NWT, p->GW, p->LG, p->Gp,
+        R.part);
     if (cudaGetLastError() != cudaSuccess ||
         launch_reduce_prec(64, p, R.part, p->NQ * p->DB, mom, nullptr, s) != cudaSuccess)
         return cuda_fail("FP64 defect correction: moments launch failed");

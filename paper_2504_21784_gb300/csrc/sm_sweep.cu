@@ -420,8 +420,8 @@ __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &La
     constexpr int sx = (Q == 0 || Q == 3) ? 1 : -1;
     constexpr int sy = (Q < 2) ? 1 : -1;
     const int strip = sx > 0 ? sr : A.NS - 1 - sr;
-    const int x0 = strip * W;
-    const int ws = min(W, nx - x0);
+    const int x0 = A.strip_x0 ? __ldg(A.strip_x0 + strip) : strip * W;
+    const int ws = A.strip_x0 ? __ldg(A.strip_x0 + strip + 1) - x0 : min(W, nx - x0);
     if (w >= ws) return;  // idle column of a ragged strip
     const int xw = sx > 0 ? x0 + w : x0 + ws - 1 - w;
     const int db = wt / A.NGB, gb = wt - db * A.NGB;

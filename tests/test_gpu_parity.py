@@ -302,3 +302,67 @@ def test_fused_emission_parity(gpu_lib, name, precision):
     same = float(np.max(np.abs(Ig - I_sep)) / np.abs(I_sep).max())
     print(f"  fused vs separate emission: {same:.2e}")
     assert same <= (1e-6 if precision == 32 else 1e-13)
+
+
+TAIL = {
+    # name: (config kwargs, tiling kwargs, tail strips at each end)
+    "w8_tail1": (dict(nx=40, ny=23, G=8, npol=4, naz=8),
+                 dict(strip_width=8, prefetch_rows=2, groups_per_warp=2), 1),
+    "w8_tail2_ragged": (dict(nx=37, ny=19, G=5, npol=2, naz=3),
+                        dict(strip_width=8, prefetch_rows=3, groups_per_warp=1), 2),
+    "w12_tail2_many_groups": (dict(nx=70, ny=31, G=64, npol=4, naz=8),
+                              dict(strip_width=12, prefetch_rows=2, groups_per_warp=4), 2),
+    "w2_tail1_gray": (dict(nx=9, ny=12, G=1, npol=4, naz=8, kind=W.OPACITY_POWER),
+                      dict(strip_width=2, prefetch_rows=2, groups_per_warp=1), 1),
+}
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("name", sorted(TAIL))
+def test_tail_strips_parity(gpu_lib, name, precision):
+    """Half-width strips at both ends of the x range (sm_set_tail_strips),
+    with ragged middle strips and one-column strips: every output against
+    the oracle, and the intensity bit for bit equal to the uniform layout's
+    (the per-(d,g) arithmetic does not depend on the strips), the moments
+    within 1e-15 (FP64) / 1e-6 (FP32) of it."""
+    ck, tk, tail = TAIL[name]
+    cfg = config(2, **ck)
+    case = build_case(gpu_lib, cfg, precision, seed=sum(map(ord, name)) % 1000 + 29, **tk)
+    I_u, m_u, _, _ = run_gpu(case)
+    ns_u = case.prob.info["n_strips"]
+    case.prob.set_tail_strips(tail)
+    info = case.prob.info
+    assert info["tail_strips"] == tail
+    W_ = tk["strip_width"]
+    mid = cfg.nx - tail * W_
+    assert info["n_strips"] == 2 * tail + (mid + W_ - 1) // W_
+    Ig = _check_all(case, precision, f"{name} tail {tail}")
+    _, m_t, _, _ = run_gpu(case)
+    assert np.array_equal(Ig, I_u)
+    assert rel_err(m_t[..., 0], m_u[..., 0], 1e-12) <= (1e-15 if precision == 64 else 1e-6)
+    print(f"  strips {ns_u} -> {info['n_strips']}")
+
+
+def test_tail_strips_fall_back_and_refuse_fused_emission(gpu_lib):
+    """A layout that does not exist (odd strip width, or no full-width strip
+    left in between) falls back to uniform strips; tail strips and fused
+    emission warps exclude each other."""
+    sm = gpu_lib
+    cfg = config(2, 12, 8, 4, 2, 4)
+    case = build_case(gpu_lib, cfg, 32, seed=3, strip_width=5, prefetch_rows=2, groups_per_warp=1)
+    case.prob.set_tail_strips(1)  # odd width
+    assert case.prob.info["tail_strips"] == 0
+    case.prob.set_tiling(8, 2)
+    case.prob.set_tail_strips(2)  # 12 - 2 * 8 < 8: nothing in between
+    assert case.prob.info["tail_strips"] == 0
+    case.prob.set_tail_strips(1)  # [4, 8 ragged to 4, 4]: 12 - 8 = 4 < 8 -> falls back too
+    assert case.prob.info["tail_strips"] == 0
+    case.prob.set_tiling(4, 2)
+    case.prob.set_tail_strips(1)  # [2, 4, 4, 2]
+    assert case.prob.info["tail_strips"] == 1 and case.prob.info["n_strips"] == 4
+    with pytest.raises(sm.SMError):
+        case.prob.set_emission_warps(2)
+    case.prob.set_tail_strips(0)
+    case.prob.set_emission_warps(2)
+    with pytest.raises(sm.SMError):
+        case.prob.set_tail_strips(1)
