@@ -40,6 +40,10 @@ def parse():
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tiling", default="",
+                    help="W,S,E,T: strip width, prefetch rows, fused emission warps and tail "
+                         "strips of the main line, set instead of autotuning (profiling runs "
+                         "that must not spend launches on the autotuner)")
     ap.add_argument("--workload", default="multigroup2d",
                     choices=["multigroup2d", "adjoint2d", "graychannel2d"],
                     help="problem of the main line: the 256^2 x 128 x 64 multigroup workload "
@@ -746,7 +750,16 @@ def main():
         clo = prob.new_closures()
         prob.sweep(T, sigma, None, I[0], mom, clo)  # realistic I^k: one step of history
         prob.synchronize()
-        if not args.no_autotune:  # pick the strip width / prefetch depth (outside timing)
+        if args.tiling:
+            w_, s_, e_, t_ = (int(v) for v in args.tiling.split(","))
+            prob.set_tail_strips(0)
+            prob.set_emission_warps(0)
+            prob.set_tiling(w_, s_)
+            prob.set_emission_warps(e_)
+            prob.set_tail_strips(t_)
+            prob.sweep(T, sigma, None, I[0], mom, clo)
+            prob.synchronize()
+        elif not args.no_autotune:  # pick the strip width / prefetch depth (outside timing)
             prob.autotune(T, sigma, I[0], I[1], reps=2)
             prob.sweep(T, sigma, None, I[0], mom, clo)
             prob.synchronize()

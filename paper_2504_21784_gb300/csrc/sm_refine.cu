@@ -15,7 +15,11 @@
 //      1/(c dt) -> 1);
 //   3. I += d,
 // until a correction is below 1e-8 of the iterate (at most MAX_CORR per outer
-// iteration): a correction leaves the FP32 solve's relative error of d, so
+// iteration).  From the second outer iteration of a step on, the iterate
+// already solves the previous records' equations to that tolerance and only
+// the emission has changed (the opacities are frozen for the step), so the
+// first correction sweeps the change of q itself and skips the residual.  A
+// correction leaves the FP32 solve's relative error of d, so
 // the next one is that much smaller and the iterate reaches the solution of
 // the transport equations for the outer iteration's temperature -- the FP64
 // sweep's intensity, up to rounding.  One correction per outer iteration
@@ -31,8 +35,8 @@
 // sweep path.  So the iterate, I^k and the records are held during the step
 // as unevaluated sums hi + lo of two FP32 numbers (about 48 significant bits),
 // and the residual, the update and the moment sums use error-free FP32
-// transformations (TwoSum of Knuth, the FMA form of Dekker's product) on the
-// FP32 pipes; FP64 is used only to split the FP64 inputs into pairs once per
+// transformations (TwoSum of Knuth, the FMA form of Dekker's product) in
+// compensated sums on the FP32 pipes; FP64 is used only to split the FP64 inputs into pairs once per
 // step (and the records once per outer iteration), to join the iterate back
 // into FP64 at the end of the step, and for the 36 dot products per (cell,
 // quadrant) of the moments.  The pairs keep their full precision for values
@@ -78,24 +82,39 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
     s.y = __fadd_rn(s.y, __fadd_rn(a.y, b.y));
     return two_sum(s.x, s.y);
 }
-__device__ __forceinline__ float2 df_sub(float2 a, float2 b) {
-    return df_add(a, make_float2(-b.x, -b.y));
-}
-// a * b: the product of the high parts exactly (its error by one FMA), the
-// cross terms in FP32
-__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
-    const float p = __fmul_rn(a.x, b.x);
-    float e = __fmaf_rn(a.x, b.x, -p);
-    e = __fmaf_rn(a.x, b.y, e);
-    e = __fmaf_rn(a.y, b.x, e);
-    return two_sum(p, e);
-}
 // a + d for an FP32 d
 __device__ __forceinline__ float2 df_add_f(float2 a, float d) {
     float2 s = two_sum(a.x, d);
     s.y = __fadd_rn(s.y, a.y);
     return two_sum(s.x, s.y);
 }
+// A sum of products and pairs accumulated with compensation (the Dot2 scheme
+// of Ogita, Rump and Oishi, "Accurate sum and dot product", 2005): s carries
+// the running FP32 sum, c the exact errors of its additions (TwoSum) and of
+// the products' high parts (one FMA each) plus the pairs' low parts and cross
+// terms.  The result s + c errs by about 2^-24 of itself plus 2^-44 of the
+// terms' magnitudes, so a sum that cancels to a small residual keeps its
+// accuracy relative to the terms.  About half the operations of summing
+// products of pairs as pairs.
+struct Acc {
+    float s = 0.f, c = 0.f;
+};
+__device__ __forceinline__ void acc_add(Acc &a, float2 v) {  // a += v
+    const float2 t = two_sum(a.s, v.x);
+    a.s = t.x;
+    a.c = __fadd_rn(a.c, __fadd_rn(t.y, v.y));
+}
+__device__ __forceinline__ void acc_mul(Acc &a, float2 x, float2 y) {  // a += x y
+    const float p = __fmul_rn(x.x, y.x);
+    float e = __fmaf_rn(x.x, y.x, -p);
+    e = __fmaf_rn(x.x, y.y, e);
+    e = __fmaf_rn(x.y, y.x, e);
+    const float2 t = two_sum(a.s, p);
+    a.s = t.x;
+    a.c = __fadd_rn(a.c, __fadd_rn(t.y, e));
+}
+__device__ __forceinline__ float2 neg(float2 x) { return make_float2(-x.x, -x.y); }
+
 // the pair nearest to an FP64 x (FP64 operations: used once per value and step)
 __device__ __forceinline__ float2 df_split(double x) {
     const float hi = __double2float_rn(x);
@@ -117,7 +136,8 @@ struct RefineArgs {
 };
 
 // The residual of one packed element (warp task wg of quadrant Q, cell,
-// slot, lane): four nodes.  The quadrant is a template parameter so that the
+// slot, lane): four nodes, each a compensated sum of its source and products
+// of pairs.  The quadrant is a template parameter so that the
 // upwind/downwind roles of the nodes are compile-time register indices.
 template <int Q>
 __device__ __forceinline__ void residual_elem(const RefineArgs &R, const size_t e, const int lane,
@@ -139,13 +159,16 @@ __device__ __forceinline__ void residual_elem(const RefineArgs &R, const size_t 
     // the packed elements of the same (warp task, slot, lane) at another cell
     const ptrdiff_t cell_stride = (ptrdiff_t)R.GW * 32;
     const float2 *Ic = R.I + e * 4;
-    float2 I[4], S[4];
+    float2 I[4];
     const float2 *rec = R.rec + ((size_t)cell * R.Gp + g) * 6;
     const float2 *ik = R.I_k + e * 4;
+    // every node's equation starts from its source S = q + I^k/(c dt)
+    Acc a[4];
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
         I[n] = Ic[n];
-        S[n] = df_add(rec[n], df_mul(R.inv_cdt, ik[n]));
+        acc_add(a[n], rec[n]);
+        acc_mul(a[n], R.inv_cdt, ik[n]);
     }
     float2 Xu, Xd, Yu, Yd;
     if (ix - sx >= 0 && ix - sx < R.nx) {
@@ -165,31 +188,27 @@ __device__ __forceinline__ void residual_elem(const RefineArgs &R, const size_t 
     const float2 mu = R.mueta[li * 2], eta = R.mueta[li * 2 + 1];
     const float2 mu2 = make_float2(2.f * mu.x, 2.f * mu.y);  // exact
     const float2 eta2 = make_float2(2.f * eta.x, 2.f * eta.y);
-    const float2 A = df_add(df_add(rec[4], mu), eta);
+    const float2 mA = neg(df_add(df_add(rec[4], mu), eta));  // -A
+    // r = S + inflow terms - M I, row by row of the cell system
+    acc_mul(a[nuu], mu2, Xu);
+    acc_mul(a[nuu], eta2, Yu);
+    acc_mul(a[nuu], mA, I[nuu]);
+    acc_mul(a[nuu], neg(mu), I[ndu]);
+    acc_mul(a[nuu], neg(eta), I[nud]);
+    acc_mul(a[ndu], eta2, Yd);
+    acc_mul(a[ndu], mA, I[ndu]);
+    acc_mul(a[ndu], mu, I[nuu]);
+    acc_mul(a[ndu], neg(eta), I[ndd]);
+    acc_mul(a[nud], mu2, Xd);
+    acc_mul(a[nud], mA, I[nud]);
+    acc_mul(a[nud], eta, I[nuu]);
+    acc_mul(a[nud], neg(mu), I[ndd]);
+    acc_mul(a[ndd], mA, I[ndd]);
+    acc_mul(a[ndd], eta, I[ndu]);
+    acc_mul(a[ndd], mu, I[nud]);
     float r[4];
-    {
-        const float2 in = df_add(S[nuu], df_add(df_mul(mu2, Xu), df_mul(eta2, Yu)));
-        const float2 out = df_add(df_mul(A, I[nuu]), df_add(df_mul(mu, I[ndu]), df_mul(eta, I[nud])));
-        const float2 d = df_sub(in, out);
-        r[nuu] = __fadd_rn(d.x, d.y);
-    }
-    {
-        const float2 in = df_add(S[ndu], df_mul(eta2, Yd));
-        const float2 out = df_add(df_sub(df_mul(A, I[ndu]), df_mul(mu, I[nuu])), df_mul(eta, I[ndd]));
-        const float2 d = df_sub(in, out);
-        r[ndu] = __fadd_rn(d.x, d.y);
-    }
-    {
-        const float2 in = df_add(S[nud], df_mul(mu2, Xd));
-        const float2 out = df_add(df_sub(df_mul(A, I[nud]), df_mul(eta, I[nuu])), df_mul(mu, I[ndd]));
-        const float2 d = df_sub(in, out);
-        r[nud] = __fadd_rn(d.x, d.y);
-    }
-    {
-        const float2 out = df_sub(df_sub(df_mul(A, I[ndd]), df_mul(eta, I[ndu])), df_mul(mu, I[nud]));
-        const float2 d = df_sub(S[ndd], out);
-        r[ndd] = __fadd_rn(d.x, d.y);
-    }
+#pragma unroll
+    for (int n = 0; n < 4; ++n) r[n] = __fadd_rn(a[n].s, a[n].c);
     *ro = make_float4(r[0], r[1], r[2], r[3]);
 }
 
@@ -266,9 +285,7 @@ moments_kernel(const float2 *__restrict__ I, const LaneConst *__restrict__ lanes
     const int qd = (int)(wglob / ncell), cell = (int)(wglob - (long long)qd * ncell);
     const int q = qd / DB, db = qd - q * DB;
     const LaneConst &L = lanes[qd * 32 + lane];
-    float2 s[4], ss[4];
-#pragma unroll
-    for (int n = 0; n < 4; ++n) s[n] = ss[n] = make_float2(0.f, 0.f);
+    Acc s[4], ss[4];
     for (int gb = 0; gb < NGB; ++gb) {
         const int wt = db * NGB + gb;
         const size_t e0 = (((size_t)q * NWT + wt) * ncell + cell) * GW;
@@ -281,15 +298,15 @@ moments_kernel(const float2 *__restrict__ I, const LaneConst *__restrict__ lanes
                                  make_float2(b.x, b.y), make_float2(b.z, b.w)};
 #pragma unroll
             for (int n = 0; n < 4; ++n) {
-                s[n] = df_add(s[n], v[n]);
-                ss[n] = df_add(ss[n], df_mul(sg, v[n]));
+                acc_add(s[n], v[n]);
+                acc_mul(ss[n], sg, v[n]);
             }
         }
     }
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
-        sh[wi][n][lane] = df_join(s[n]);
-        sh[wi][4 + n][lane] = df_join(ss[n]);
+        sh[wi][n][lane] = (double)s[n].s + (double)s[n].c;
+        sh[wi][4 + n][lane] = (double)ss[n].s + (double)ss[n].c;
     }
     __syncwarp();
     for (int m = lane; m < 36; m += 32) {
@@ -302,19 +319,30 @@ moments_kernel(const float2 *__restrict__ I, const LaneConst *__restrict__ lanes
 }
 
 // Per (cell, group): the records as pairs (q at the nodes, sigma~, sigma) for
-// the residual and the moments, and the FP32 records of the correction
-// sweep (no emission, the problem's sigma~ and sigma).
+// the residual and the moments; the FP32 records of the correction sweep (no
+// emission, the problem's sigma~ and sigma); and, when the pairs held the
+// previous outer iteration's records (dq != NULL), FP32 records whose
+// emission is the change of q since then.
 __global__ void records_kernel(const double *__restrict__ rec, float2 *__restrict__ rec_df,
-                               float *__restrict__ rec32, size_t n) {
+                               float *__restrict__ rec32, float *__restrict__ dq, size_t n) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double *a = rec + i * 8;
     float2 *o = rec_df + i * 6;
-    for (int k = 0; k < 6; ++k) o[k] = df_split(a[k]);
     float *f = rec32 + i * 8;
+    const float s4 = __double2float_rn(a[4]), s5 = __double2float_rn(a[5]);
+    if (dq) {
+        float *h = dq + i * 8;
+        for (int k = 0; k < 4; ++k) h[k] = __double2float_rn(a[k] - df_join(o[k]));
+        h[4] = s4;
+        h[5] = s5;
+        h[6] = 0.0f;
+        h[7] = 0.0f;
+    }
+    for (int k = 0; k < 6; ++k) o[k] = df_split(a[k]);
     for (int k = 0; k < 4; ++k) f[k] = 0.0f;
-    f[4] = __double2float_rn(a[4]);
-    f[5] = __double2float_rn(a[5]);
+    f[4] = s4;
+    f[5] = s5;
     f[6] = 0.0f;
     f[7] = 0.0f;
 }
@@ -353,6 +381,9 @@ struct sm_refine_state {
     float2 *ik = nullptr;              // packed I^k as pairs
     float2 *rec_df = nullptr;          // [cell][Gp][6] records as pairs
     float *rec32 = nullptr;            // [cell][Gp][8] FP32 records of the correction sweep
+    float *rec_dq = nullptr;           // [cell][Gp][8] the same with the change of q as emission
+    bool fresh = true;                 // no outer iteration of this step has run yet
+    bool met = false;                  // the last solve's corrections met the tolerance
     float *inflow0 = nullptr;          // [4][Gp] zero inflow
     float2 *mueta = nullptr;           // [NQ*DB*32][2]
     float2 *inflow_df = nullptr;       // [4][Gp]
@@ -370,6 +401,7 @@ void refine_free(sm_problem *p) {
     if (!p->refine) return;
     sm_refine_state &R = *p->refine;
     for (void *b : {(void *)R.r, (void *)R.d, (void *)R.ik, (void *)R.rec_df, (void *)R.rec32,
+                    (void *)R.rec_dq,
                     (void *)R.inflow0, (void *)R.mueta, (void *)R.inflow_df, (void *)R.part,
                     (void *)R.maxes})
         if (b) cudaFree(b);
@@ -395,6 +427,7 @@ sm_status refine_ensure(sm_problem *p) {
         cudaMalloc(&R.ik, ie * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&R.rec_df, nrec * 6 * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&R.rec32, nrec * 8 * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&R.rec_dq, nrec * 8 * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&R.inflow0, (size_t)4 * p->Gp * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&R.mueta, (size_t)nlanes * 2 * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&R.inflow_df, (size_t)4 * p->Gp * sizeof(float2)) != cudaSuccess ||
@@ -438,7 +471,7 @@ sm_status refine_ensure(sm_problem *p) {
         return SM_ERR_UNSUPPORTED;
     }
     R.NS = (p->nx + R.W - 1) / R.W;
-    p->workspace_bytes += ie * 16 + nrec * 80 + (size_t)20 * p->Gp + (size_t)nlanes * 16 +
+    p->workspace_bytes += ie * 16 + nrec * 112 + (size_t)20 * p->Gp + (size_t)nlanes * 16 +
                           npart * 8 + 8;
     return SM_OK;
 }
@@ -447,6 +480,7 @@ sm_status refine_ensure(sm_problem *p) {
 // in the caller's FP64 buffer I, of the same size) set to them.
 sm_status refine_begin(sm_problem *p, const double *I_k, void *I) {
     sm_refine_state &R = *p->refine;
+    R.fresh = true;
     const size_t nv = (size_t)p->NQ * p->NWT * p->ncell * p->GW * 32 * 4;
     const unsigned blocks = (unsigned)std::min<size_t>((nv + 255) / 256, 152 * 16);
     split_kernel<<<blocks, 256, 0, p->stream>>>(I_k, R.ik, nv);
@@ -511,8 +545,16 @@ sm_status refine_solve(sm_problem *p, void *I, double *mom) {
         set_last_error(what);
         return SM_ERR_CUDA;
     };
+    // after the first outer iteration of the step the iterate solves the
+    // previous records' equations to the stopping tolerance, and only the
+    // emission q has changed since (sigma is frozen for the step), so the
+    // residual is the change of q: the first correction sweeps it directly,
+    // without the residual kernel
+    const bool from_dq = !R.fresh && R.met;
     records_kernel<<<(unsigned)((nrec + 255) / 256), 256, 0, s>>>(
-        static_cast<const double *>(p->d_src), R.rec_df, R.rec32, nrec);
+        static_cast<const double *>(p->d_src), R.rec_df, R.rec32, from_dq ? R.rec_dq : nullptr,
+        nrec);
+    R.fresh = false;
     if (cudaGetLastError() != cudaSuccess) return cuda_fail("FP64 defect correction: records launch failed");
     p->launches++;
     float2 *Iv = static_cast<float2 *>(I);
@@ -540,13 +582,18 @@ sm_status refine_solve(sm_problem *p, void *I, double *mom) {
     A.r = R.r;
     A.n_elems = ie / 4;
     for (int c = 0; c < MAX_CORR; ++c) {
-        residual_kernel<<<(unsigned)((A.n_elems + 255) / 256), 256, 0, s>>>(A);
-        if (cudaGetLastError() != cudaSuccess) return cuda_fail("FP64 defect correction: residual launch failed");
-        // the FP32 correction sweep: source r, no emission, zero inflow, its
-        // own tiling (moments not reduced)
+        const bool dq = from_dq && c == 0;
+        if (!dq) {
+            residual_kernel<<<(unsigned)((A.n_elems + 255) / 256), 256, 0, s>>>(A);
+            if (cudaGetLastError() != cudaSuccess)
+                return cuda_fail("FP64 defect correction: residual launch failed");
+            p->launches++;
+        }
+        // the FP32 correction sweep: source r (or the change of q), no
+        // emission, zero inflow, its own tiling (moments not reduced)
         ++p->epoch;
-        SweepArgs a = make_sweep_args(p, R.r, R.d);
-        a.src = R.rec32;
+        SweepArgs a = make_sweep_args(p, dq ? nullptr : R.r, R.d);
+        a.src = dq ? R.rec_dq : R.rec32;
         a.inflow = R.inflow0;
         a.inv_cdt = 1.0;
         a.W = R.W;
@@ -565,7 +612,7 @@ sm_status refine_solve(sm_problem *p, void *I, double *mom) {
             cudaMemcpyAsync(R.h_maxes, R.maxes, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost,
                             s) != cudaSuccess)
             return cuda_fail("FP64 defect correction: update launch failed");
-        p->launches += 3;
+        p->launches += 2;
         ++R.corrections;
         const sm_status st = sm_synchronize(p);  // also reports a wavefront timeout
         if (st != SM_OK) return st;
@@ -576,7 +623,8 @@ sm_status refine_solve(sm_problem *p, void *I, double *mom) {
             set_last_error("FP64 defect correction: the correction is not finite");
             return SM_ERR_NONPHYSICAL;
         }
-        if ((double)dmax <= CORR_TOL * (double)imax) break;
+        R.met = (double)dmax <= CORR_TOL * (double)imax;
+        if (R.met) break;
     }
     const long long warps = (long long)p->NQ * p->DB * p->ncell;
     moments_kernel<<<(unsigned)((warps + MOM_WARPS - 1) / MOM_WARPS), MOM_WARPS * 32, 0, s>>>(
