@@ -1,6 +1,8 @@
 """Benchmark of the SM hot path (rows a1-a4: emission, sweep, fused moments,
 closures) on the 2D multigroup workload: 256x256 cells, 128 directions,
-64 groups, FP32 sweep arithmetic with FP64 Planck and FP64 moment sums.
+64 groups, FP32 sweep arithmetic; the Planck group integrals of the FP32
+path in double-FP32 arithmetic (about 48 bits; the FP64 path's in FP64); the
+moment sums compensated and finished in FP64.
 
 Prints one JSON line (rank 0).  Metric: cell-direction-group updates/s of
 whole hot-path passes, with the intensity resident in HBM (inputs far larger
@@ -829,8 +831,10 @@ def main():
         "data": "synthetic",
         "config": {"workload": cfg.name, "cells": cfg.n_cells, "directions": cfg.n_dir,
                    "groups": cfg.n_groups,
-                   "step": "emission (FP64 Planck) + sweep with fused moments + FP64 "
-                           "moment reduction + closures",
+                   "step": ("emission (Planck integrals in double-FP32, about 48 bits)"
+                            if prec == 32 else "emission (FP64 Planck)") +
+                           " + sweep with fused moments + fixed-order moment reduction "
+                           "(FP64 result) + closures",
                    "sweep_precision": f"fp{prec}", "l2": "inputs larger than L2 "
                    f"({prob.info['intensity_bytes'] / 1e9:.1f} GB per intensity copy)",
                    "tiling": {k: prob.info[k] for k in ("strip_width", "prefetch_rows",

@@ -43,6 +43,13 @@ sm_status sm_debug_set_pcg_form(sm_problem *p, int form);
  * last low-order solve used, or SM_DEBUG_PCG_AUTO if it has run none. */
 sm_status sm_debug_get_pcg_form(const sm_problem *p, int *form);
 
+/* Emission of an FP32-sweep problem's sweeps: 0 (the default) evaluates the
+ * Planck group integrals in double-FP32 arithmetic (pairs of FP32 numbers,
+ * about 48 significant bits, on the FP32 pipes); non-zero takes the FP64
+ * evaluation that FP64 problems and sm_emission use, so that a test can
+ * compare the two.  INVALID_ARG for a NULL problem. */
+sm_status sm_debug_set_emission_fp64(sm_problem *p, int fp64);
+
 /* Low-order solves of sm_batch_step: non-zero (the default) runs every
  * member's Newton iteration in one cooperative launch, each member on its own
  * share of the blocks; 0 runs one cooperative launch per member, one after

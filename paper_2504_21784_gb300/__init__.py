@@ -31,7 +31,7 @@ EXPORTED = ["sm_create_problem", "sm_destroy_problem", "sm_get_info", "sm_set_st
             "sm_launch_count", "sm_last_error", "sm_status_string",
             "sm_debug_set_wait_limit_ns", "sm_debug_skip_publish", "sm_debug_withhold_lo_block",
             "sm_debug_set_pcg_form", "sm_debug_get_pcg_form", "sm_debug_exp_neg",
-            "sm_debug_set_batch_lo", "sm_set_tail_strips",
+            "sm_debug_set_batch_lo", "sm_set_tail_strips", "sm_debug_set_emission_fp64",
             "sm_sweep_static",
             "sm_default_step_params", "sm_loworder_newton", "sm_step",
             "sm_create_batch", "sm_destroy_batch", "sm_batch_problem", "sm_batch_get_info",
@@ -152,6 +152,7 @@ def load():
         "sm_debug_exp_neg": [P, P, I, P],
         "sm_debug_set_batch_lo": [P, I],
         "sm_set_tail_strips": [P, I],
+        "sm_debug_set_emission_fp64": [P, I],
         "sm_sweep_static": [ctypes.POINTER(ProblemDesc), P, P, P, P, P, P, P],
         "sm_loworder_newton": [P, P, P, P, P, P, P, P, ctypes.POINTER(StepParams),
                                ctypes.POINTER(StepStats)],
@@ -293,6 +294,11 @@ class Problem:
         sweep CTA compute it inside the sweep kernel (sm_set_emission_warps)."""
         _check(load().sm_set_emission_warps(self._h, int(warps)))
         self.refresh_info()
+
+    def set_emission_fp64(self, on: bool):
+        """Test hook (sm_debug_set_emission_fp64): an FP32 problem's sweeps take
+        the FP64 Planck evaluation instead of the double-FP32 one."""
+        _check(load().sm_debug_set_emission_fp64(self._h, 1 if on else 0))
 
     def set_tail_strips(self, n: int):
         """n half-width strips at each end of the x range (sm_set_tail_strips;

@@ -446,6 +446,7 @@ static sm_status create_problem(const sm_problem_desc *d, void *stream, sm_probl
     if (const char *why = smk::check_desc(d)) return fail(SM_ERR_INVALID_ARG, why);
 
     smk::planck_upload_tables();
+    smk::planck_df_upload_tables();
     sm_problem *p = new sm_problem();
     p->desc = *d;
     p->edges.assign(d->group_edges, d->group_edges + d->n_groups + 1);
@@ -969,6 +970,12 @@ sm_status sm_debug_set_pcg_form(sm_problem *p, int form) {
     if (form != SM_DEBUG_PCG_AUTO && form != SM_DEBUG_PCG_TEXTBOOK && form != SM_DEBUG_PCG_SINGLE)
         return fail(SM_ERR_INVALID_ARG, "form must be SM_DEBUG_PCG_AUTO, _TEXTBOOK or _SINGLE");
     p->lo_pcg_form = form;
+    return SM_OK;
+}
+
+sm_status sm_debug_set_emission_fp64(sm_problem *p, int fp64) {
+    if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
+    p->emit_fp64 = fp64 != 0;
     return SM_OK;
 }
 

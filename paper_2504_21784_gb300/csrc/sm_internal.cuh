@@ -153,6 +153,11 @@ cudaError_t launch_sweep2d_batch(int prec, const BatchSweepArgs &b, int grid, si
                                  cudaStream_t s);
 int sweep2d_batch_max_resident(int prec, int W, size_t smem);
 void planck_upload_tables(void);
+// double-FP32 emission of an FP32-sweep problem (sm_planck_df.cu); the
+// tables' host copies it derives its own tables from (sm_planck.cu)
+cudaError_t launch_emission_df(const sm_problem *p, const double *T, const double *sigma,
+                               cudaStream_t s, const int *active);
+bool planck_df_upload_tables(void);  // once per device (synchronous copies)
 // Fills the Planck tables' kernel-parameter form (uploads them first); false
 // on a CUDA error.
 bool planck_tabs(PlanckTabs *out);
@@ -216,6 +221,7 @@ struct sm_problem {
     int W, S, NS;
     int emit_warps = 0;  // 2D: emission warps fused into the sweep kernel (0: separate kernel)
     int tail = 0;        // 2D: half-width strips at each end of the x range (0: uniform strips)
+    int emit_fp64 = 0;   // FP32 problem: sweeps take the FP64 emission kernel (test hook)
     int *d_strip_x0 = nullptr;  // [NS + 1] first column of each strip when tail > 0
     int resident = 0;  // 2D sweep CTAs that fit on the GPU for (W, S, emit_warps)
     unsigned int *d_emit_ctr = nullptr;  // [1 + NS] fused-emission queue and strip counters

@@ -90,11 +90,10 @@ static void planck_taylor_tables(double out[NCEN][2][NTAY]) {
 // set once a device has its tables; two threads uploading at once write the same data
 static std::atomic<bool> g_tables_ready[128];
 
-void planck_upload_tables(void) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return;
-    if (g_tables_ready[dev].load(std::memory_order_acquire)) return;
-    double head[NBERN], bern[NBERN];
+// The host copies of every table (the double-FP32 emission derives its own
+// from them).
+void planck_host_tables(double head[NBERN], double bern[NBERN], double cexp_out[3],
+                        double exp2_tab[64], double (*ptab)[2][NTAY]) {
     for (int k = 1; k <= NBERN; ++k) {
         const int s = 2 * k;
         double zeta;
@@ -119,11 +118,20 @@ void planck_upload_tables(void) {
     int ex = 0;
     frexp((double)l64, &ex);
     const double l64_hi = ldexp(floor(ldexp((double)l64, 32 - ex)), ex - 32);
-    const double cexp[3] = {(double)(64.0L / ln2), l64_hi, (double)(l64 - (long double)l64_hi)};
-    double tab[64];
-    for (int j = 0; j < 64; ++j) tab[j] = (double)exp2l(-(long double)j / 64.0L);
-    static double ptab[NCEN][2][NTAY];
+    cexp_out[0] = (double)(64.0L / ln2);
+    cexp_out[1] = l64_hi;
+    cexp_out[2] = (double)(l64 - (long double)l64_hi);
+    for (int j = 0; j < 64; ++j) exp2_tab[j] = (double)exp2l(-(long double)j / 64.0L);
     planck_taylor_tables(ptab);
+}
+
+void planck_upload_tables(void) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return;
+    if (g_tables_ready[dev].load(std::memory_order_acquire)) return;
+    double head[NBERN], bern[NBERN], cexp[3], tab[64];
+    static double ptab[NCEN][2][NTAY];
+    planck_host_tables(head, bern, cexp, tab, ptab);
     double pcen[NCEN];
     for (int j = 0; j < NCEN; ++j) pcen[j] = XT0 + (double)j / TSTEP;
     if (cudaMemcpyToSymbol(c_head, head, sizeof(head)) == cudaSuccess &&
@@ -383,6 +391,8 @@ cudaError_t launch_emission(const sm_problem *p, const double *T, const double *
     const int n = p->ncell * p->nn;
     const int blocks = (n + threads - 1) / threads;
     const double scale = p->desc.a * p->desc.c / (4.0 * PI_D);
+    // an FP32 problem's sweeps: the double-FP32 evaluation (sm_planck_df.cu)
+    if (p->prec == 32 && !q_canon && !p->emit_fp64) return launch_emission_df(p, T, sigma, s, active);
     if (p->prec == 32)
         emission_kernel<float><<<blocks, threads, (p->G + 1) * sizeof(float), s>>>(
             p->ncell, p->nn, p->G, p->Gp, p->d_edges, scale, p->inv_cdt, T, sigma,

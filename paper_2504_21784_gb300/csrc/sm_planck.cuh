@@ -43,6 +43,12 @@ constexpr int NTAY = 7;    // remainder (1/64 / 2pi)^7 < 1e-18 of the leading te
 constexpr int JSW = 32;    // centres j < JSW lie below x = 2: P, R; from there on 1 - P, 1 - R
 static_assert(XT1 == XCLOSED, "the Taylor tables end where the one-term tail takes over");
 
+// Host copies of the tables (head and Bernoulli coefficients, the exponential's
+// constants and 2^{-j/64} table, the Taylor tables), derived in extended
+// precision (sm_planck.cu).
+void planck_host_tables(double head[NBERN], double bern[NBERN], double cexp[3], double exp2[64],
+                        double (*ptab)[2][NTAY]);
+
 // The tables as a kernel parameter: the series coefficients by value, the
 // larger tables by device address.
 struct PlanckTabs {

@@ -366,3 +366,49 @@ def test_tail_strips_fall_back_and_refuse_fused_emission(gpu_lib):
     case.prob.set_emission_warps(2)
     with pytest.raises(sm.SMError):
         case.prob.set_tail_strips(1)
+
+
+def _branch_temperatures(edges, n, seed):
+    """Nodal temperatures that put one group edge at each switch of the Planck
+    evaluation (head series / Taylor tables / tail series / one-term tail /
+    FP32 range / FP64 underflow), just below, on and just above it."""
+    xs = [0.5, 0.9999, 1.0, 1.0001, 1.06, 1.9999, 2.0, 2.0001, 11.98, 12.0, 12.03, 36.9999,
+          37.0, 37.0001, 86.99, 87.0, 87.01, 100.0, 700.0, 746.0]
+    rng = np.random.default_rng(seed)
+    G = len(edges) - 1
+    T = np.empty(n)
+    for i in range(n):
+        T[i] = edges[1 + rng.integers(0, G - 1)] / xs[i % len(xs)]
+    return np.clip(T, 1e-3, 1e3)
+
+
+@pytest.mark.parametrize("case_name", ["larsen64_wave", "branch_switches"])
+def test_double_fp32_emission_matches_fp64(gpu_lib, case_name):
+    """The FP32-sweep path's emission in double-FP32 arithmetic against the
+    FP64 evaluation (sm_debug_set_emission_fp64) inside the same sweep: the
+    intensities (whose source records are FP32 either way) within 2e-7 of each
+    other per (direction, group) slice, and the nodal Planck and Rosseland numerators
+    (closure fields sigma_F, sigma_P, FP64) within 1e-13, on a multigroup
+    temperature wave and on temperatures that put group edges at every switch
+    of the series."""
+    import torch
+    if case_name == "larsen64_wave":
+        cfg = config(2, 21, 17, 64, 2, 4)
+        case = build_case(gpu_lib, cfg, 32, seed=11, strip_width=8, prefetch_rows=2)
+    else:
+        cfg = config(2, 12, 10, 24, 2, 4)
+        case = build_case(gpu_lib, cfg, 32, seed=12, strip_width=6, prefetch_rows=2)
+        case.T = _branch_temperatures(cfg.edges, cfg.n_cells * 4, 5).reshape(cfg.n_cells, 4)
+        case.sigma = O.opacity(cfg.opacity_kind, cfg.opacity_alpha, cfg.edges, case.T,
+                               case.scale)
+    I_df, m_df, c_df, _ = run_gpu(case)
+    case.prob.set_emission_fp64(True)
+    I_64, m_64, c_64, _ = run_gpu(case)
+    case.prob.set_emission_fp64(False)
+    red = (2, 3)  # per (direction, group): cells x nodes
+    dI = float(np.max(np.abs(I_df - I_64).max(axis=red) /
+                      np.maximum(np.abs(I_64).max(axis=red), 1e-300)))
+    d_num = max(rel_err(c_df[..., k], c_64[..., k], 0.0) for k in (7, 8))
+    print(f"{case_name}: intensity {dI:.2e}, Planck / Rosseland numerators {d_num:.2e}")
+    assert dI <= 2e-7
+    assert d_num <= 1e-13
