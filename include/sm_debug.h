@@ -30,16 +30,26 @@ sm_status sm_debug_skip_publish(sm_problem *p, int enable);
 sm_status sm_debug_withhold_lo_block(sm_problem *p, int enable);
 
 /* Form of the conjugate gradients in the low-order solves of this problem:
- * SM_DEBUG_PCG_AUTO (the library's choice: the single-reduction form while the
- * mesh has at most 1.5 warps of cells per SM sub-partition, else the textbook
- * form), SM_DEBUG_PCG_TEXTBOOK (two grid reductions per iteration) or
- * SM_DEBUG_PCG_SINGLE (Chronopoulos-Gear, one reduction per iteration).  The
- * forms compute the same iterates up to rounding.  INVALID_ARG for other
- * values. */
-enum { SM_DEBUG_PCG_AUTO = 0, SM_DEBUG_PCG_TEXTBOOK = 1, SM_DEBUG_PCG_SINGLE = 2 };
+ * SM_DEBUG_PCG_AUTO (the library's choice: the single-reduction form below
+ * 4096 cells, else the textbook form),
+ * SM_DEBUG_PCG_TEXTBOOK (FP64, two grid reductions per iteration),
+ * SM_DEBUG_PCG_SINGLE (FP64, Chronopoulos-Gear, one reduction per iteration)
+ * or SM_DEBUG_PCG_MIXED (iterative refinement: FP32 conjugate gradients on
+ * FP32 copies of the operator, FP64 residual updates; the same FP64 stopping
+ * test, and the FP64 textbook form from the current iterate if a refinement
+ * cycle stops halving the residual).  The FP64 forms compute the same iterates
+ * up to rounding; every form stops at the same FP64 relative residual.  The
+ * batched time step (sm_batch_step) runs the FP64 forms (mixed: textbook).
+ * INVALID_ARG for other values. */
+enum {
+    SM_DEBUG_PCG_AUTO = 0,
+    SM_DEBUG_PCG_TEXTBOOK = 1,
+    SM_DEBUG_PCG_SINGLE = 2,
+    SM_DEBUG_PCG_MIXED = 3
+};
 sm_status sm_debug_set_pcg_form(sm_problem *p, int form);
 
-/* The form (SM_DEBUG_PCG_TEXTBOOK or SM_DEBUG_PCG_SINGLE) that the problem's
+/* The form (SM_DEBUG_PCG_TEXTBOOK, _SINGLE or _MIXED) that the problem's
  * last low-order solve used, or SM_DEBUG_PCG_AUTO if it has run none. */
 sm_status sm_debug_get_pcg_form(const sm_problem *p, int *form);
 

@@ -480,7 +480,7 @@ class Problem:
         _check(load().sm_debug_withhold_lo_block(self._h, 1 if on else 0))
 
     #: conjugate-gradient forms of the low-order solve (sm_debug.h)
-    PCG_FORMS = {"auto": 0, "textbook": 1, "single": 2}
+    PCG_FORMS = {"auto": 0, "textbook": 1, "single": 2, "mixed": 3}
 
     def debug_set_pcg_form(self, form: str):
         _check(load().sm_debug_set_pcg_form(self._h, self.PCG_FORMS[form]))

@@ -967,8 +967,9 @@ sm_status sm_debug_withhold_lo_block(sm_problem *p, int enable) {
 
 sm_status sm_debug_set_pcg_form(sm_problem *p, int form) {
     if (!p) return fail(SM_ERR_INVALID_ARG, "NULL problem");
-    if (form != SM_DEBUG_PCG_AUTO && form != SM_DEBUG_PCG_TEXTBOOK && form != SM_DEBUG_PCG_SINGLE)
-        return fail(SM_ERR_INVALID_ARG, "form must be SM_DEBUG_PCG_AUTO, _TEXTBOOK or _SINGLE");
+    if (form != SM_DEBUG_PCG_AUTO && form != SM_DEBUG_PCG_TEXTBOOK && form != SM_DEBUG_PCG_SINGLE &&
+        form != SM_DEBUG_PCG_MIXED)
+        return fail(SM_ERR_INVALID_ARG, "form must be SM_DEBUG_PCG_AUTO, _TEXTBOOK, _SINGLE or _MIXED");
     p->lo_pcg_form = form;
     return SM_OK;
 }

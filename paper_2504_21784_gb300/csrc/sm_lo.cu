@@ -134,28 +134,31 @@ struct VecCG {
 // and A_EE adds aE e, the penalty (c alpha/2) wf (e - e_nb) on interior
 // faces and c alpha wf e on the boundary.  The left neighbour's u_1 needs
 // only its own row and this cell's e_0, so it is recomputed here.
-template <int NN, class Acc>
-__device__ __forceinline__ void schur_cell(const Geo &G, const Cell &C, const Acc &acc,
-                                           const double (&aE)[NN], const double *__restrict__ iaF,
-                                           double (&q)[NN], double (&e)[NN]) {
-    double eL[NN], eR[NN], ia[NN];
+// T: the arithmetic (FP64, or FP32 for the inner solves of the mixed-precision
+// conjugate gradients), GT its geometry coefficients, IA the 1/A_FF array's
+// accessor (ia(k, n)).
+template <typename T, int NN, class Acc, class GT, class IA>
+__device__ __forceinline__ void schur_cell_t(const GT &G, const Cell &C, const Acc &acc,
+                                             const T (&aE)[NN], const IA &iaF, T (&q)[NN],
+                                             T (&e)[NN]) {
+    T eL[NN], eR[NN], ia[NN];
     acc.get(C.k, e);
     if (C.L) acc.get(C.k - 1, eL);
     if (C.R) acc.get(C.k + 1, eR);
-    ldc<NN>(iaF, C.k, ia);
+#pragma unroll
+    for (int n = 0; n < NN; ++n) ia[n] = iaF(C.k, n);
 #pragma unroll
     for (int n = 0; n < NN; ++n) q[n] = aE[n] * e[n];
 #pragma unroll
     for (int b = 0; b < NN / 2; ++b) {
         const int n0 = 2 * b, n1 = 2 * b + 1;
-        const double s = e[n0] + e[n1];
-        const double u0 = (G.kx * s - G.fx * e[n0]) * ia[n0];
-        const double u1 = (G.fx * (C.R ? eR[n0] : e[n1]) - G.kx * s) * ia[n1];
-        const double sv = G.lx * (u0 + u1);
-        double v0 = sv, v1 = -sv;
+        const T s = e[n0] + e[n1];
+        const T u0 = (G.kx * s - G.fx * e[n0]) * ia[n0];
+        const T u1 = (G.fx * (C.R ? eR[n0] : e[n1]) - G.kx * s) * ia[n1];
+        const T sv = G.lx * (u0 + u1);
+        T v0 = sv, v1 = -sv;
         if (C.L) {
-            const double uL = (G.fx * e[n0] - G.kx * (eL[n0] + eL[n1])) *
-                              iaF[(size_t)(C.k - 1) * NN + n1];
+            const T uL = (G.fx * e[n0] - G.kx * (eL[n0] + eL[n1])) * iaF(C.k - 1, n1);
             v0 -= G.wfx * uL;
             q[n0] += G.px * (e[n0] - eL[n1]);
         } else {
@@ -171,20 +174,19 @@ __device__ __forceinline__ void schur_cell(const Geo &G, const Cell &C, const Ac
         q[n1] -= v1;
     }
     if constexpr (NN == 4) {
-        double eB[NN], eT[NN];
+        T eB[NN], eT[NN];
         if (C.B) acc.get(C.k - G.nx, eB);
         if (C.T) acc.get(C.k + G.nx, eT);
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
             const int n0 = a, n1 = a + 2;
-            const double s = e[n0] + e[n1];
-            const double u0 = (G.ky * s - G.fy * e[n0]) * ia[n0];
-            const double u1 = (G.fy * (C.T ? eT[n0] : e[n1]) - G.ky * s) * ia[n1];
-            const double sv = G.ly * (u0 + u1);
-            double v0 = sv, v1 = -sv;
+            const T s = e[n0] + e[n1];
+            const T u0 = (G.ky * s - G.fy * e[n0]) * ia[n0];
+            const T u1 = (G.fy * (C.T ? eT[n0] : e[n1]) - G.ky * s) * ia[n1];
+            const T sv = G.ly * (u0 + u1);
+            T v0 = sv, v1 = -sv;
             if (C.B) {
-                const double uB = (G.fy * e[n0] - G.ky * (eB[n0] + eB[n1])) *
-                                  iaF[(size_t)(C.k - G.nx) * NN + n1];
+                const T uB = (G.fy * e[n0] - G.ky * (eB[n0] + eB[n1])) * iaF(C.k - G.nx, n1);
                 v0 -= G.wfy * uB;
                 q[n0] += G.py * (e[n0] - eB[n1]);
             } else {
@@ -201,6 +203,85 @@ __device__ __forceinline__ void schur_cell(const Geo &G, const Cell &C, const Ac
         }
     }
 }
+
+// the 1/A_FF array's accessors: FP64 (as stored), FP32 copy
+template <int NN> struct IaD {
+    const double *a;
+    __device__ __forceinline__ double operator()(int k, int n) const { return a[(size_t)k * NN + n]; }
+};
+template <int NN> struct IaF {
+    const float *a;
+    __device__ __forceinline__ float operator()(int k, int n) const {
+        return __ldcg(a + (size_t)k * NN + n);
+    }
+};
+
+template <int NN, class Acc>
+__device__ __forceinline__ void schur_cell(const Geo &G, const Cell &C, const Acc &acc,
+                                           const double (&aE)[NN], const double *__restrict__ iaF,
+                                           double (&q)[NN], double (&e)[NN]) {
+    schur_cell_t<double, NN>(G, C, acc, aE, IaD<NN>{iaF}, q, e);
+}
+
+// The geometry coefficients in FP32 (the inner solves of the mixed-precision
+// conjugate gradients).
+struct GeoF {
+    int nx;
+    float kx, ky, fx, fy, lx, ly, px, py, bx, by, wfx, wfy;
+};
+__device__ __forceinline__ GeoF geo_f(const Geo &G) {
+    GeoF g;
+    g.nx = G.nx;
+    g.kx = (float)G.kx; g.ky = (float)G.ky; g.fx = (float)G.fx; g.fy = (float)G.fy;
+    g.lx = (float)G.lx; g.ly = (float)G.ly; g.px = (float)G.px; g.py = (float)G.py;
+    g.bx = (float)G.bx; g.by = (float)G.by; g.wfx = (float)G.wfx; g.wfy = (float)G.wfy;
+    return g;
+}
+
+// FP32 nodal values of cell k (read past L1: written by other blocks)
+template <int NN>
+__device__ __forceinline__ void ldf(const float *a, int k, float (&v)[NN]) {
+    if constexpr (NN == 4) {
+        const float4 t = __ldcg(reinterpret_cast<const float4 *>(a) + k);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+        const float2 t = __ldcg(reinterpret_cast<const float2 *>(a) + k);
+        v[0] = t.x; v[1] = t.y;
+    }
+}
+template <int NN>
+__device__ __forceinline__ void stf(float *a, int k, const float (&v)[NN]) {
+    if constexpr (NN == 4)
+        reinterpret_cast<float4 *>(a)[k] = make_float4(v[0], v[1], v[2], v[3]);
+    else
+        reinterpret_cast<float2 *>(a)[k] = make_float2(v[0], v[1]);
+}
+template <int NN> struct VecF {
+    const float *v;
+    __device__ __forceinline__ void get(int k, float (&o)[NN]) const { ldf<NN>(v, k, o); }
+};
+// an FP32 vector read as FP64 (the refinement's residual update r -= S e)
+template <int NN> struct VecFD {
+    const float *v;
+    __device__ __forceinline__ void get(int k, double (&o)[NN]) const {
+        float t[NN];
+        ldf<NN>(v, k, t);
+#pragma unroll
+        for (int i = 0; i < NN; ++i) o[i] = (double)t[i];
+    }
+};
+// the inner solve's search direction p = u + beta p_old of cell k, on the fly
+template <int NN> struct DirF {
+    const float *u, *p;
+    float beta;
+    __device__ __forceinline__ void get(int k, float (&o)[NN]) const {
+        float a[NN], b[NN];
+        ldf<NN>(u, k, a);
+        ldf<NN>(p, k, b);
+#pragma unroll
+        for (int i = 0; i < NN; ++i) o[i] = __fmaf_rn(beta, b[i], a[i]);
+    }
+};
 
 // A_EF u on the nodes of cell C for a materialised u[node][dim].
 template <int NN>
@@ -688,6 +769,10 @@ struct NewtonArgs {
     Scalars *sc;
     GridBar bar;
     int withhold;  // test hook: the last block leaves before its first barrier
+    // mixed-precision conjugate gradients: FP32 copies of aE, 1/A_FF and
+    // 1/diag(S), and the inner solve's r, u, p (double-buffered), q, e
+    // (double-buffered by refinement cycle)
+    float *fa, *fi, *fd, *fr, *fu, *fp[2], *fq, *fe[2];
 };
 
 // The preconditioned residual u of cell k for the next matrix-vector product,
@@ -869,9 +954,224 @@ __device__ __forceinline__ void newton_finish_cell(const NewtonArgs &A, int k, d
     stc<NN>(A.E, k, e);
 }
 
+// The textbook conjugate gradients on S x = b from the state in the FP64
+// buffers: x, r = r[0], u = r[1] = r / diag(S), p = u (rz = r.u); buffers p =
+// w[0] / w[1] by iteration parity, q = s[0].  Returns the DONE_ code; iters
+// counts on from its value.
+template <int NN>
+__device__ __forceinline__ int cg_textbook(const NewtonArgs &A, const int bid, const int nb,
+                                           const int k0, const int stride, unsigned &bar_target,
+                                           const double stop, double rz, int &iters) {
+    const Geo &G = A.G;
+    double *const rb = A.r[0], *const ub = A.r[1], *const qb = A.s[0];
+    double beta = 0.0;
+    for (;;) {
+        const double *po = (iters & 1) ? A.w[1] : A.w[0];
+        double *pn = (iters & 1) ? A.w[0] : A.w[1];
+        double v1[1] = {0.0};
+        for (int k = k0; k < G.ncell; k += stride) {
+            const Cell C = cell_of(G, k);
+            double aEv[NN], qv[NN], pv[NN];
+            ldc<NN>(A.aE, k, aEv);
+            schur_cell<NN>(G, C, DirCG<NN>{ub, po, beta}, aEv, A.iaF, qv, pv);
+            stc<NN>(pn, k, pv);
+            stc<NN>(qb, k, qv);
+#pragma unroll
+            for (int n = 0; n < NN; ++n) v1[0] += pv[n] * qv[n];
+        }
+        block_partials<1>(v1, A.partB, bid);
+        if (!grid_barrier(A.bar, bar_target)) return DONE_TIMEOUT;
+        grid_totals<1>(v1, A.partB, nb);
+        if (!(v1[0] > 0.0) || !isfinite(v1[0]) || !isfinite(rz)) return DONE_BREAKDOWN;
+        const double alpha = rz / v1[0];
+        double v2[2] = {0.0, 0.0};
+        for (int k = k0; k < G.ncell; k += stride) {
+            double pv[NN], qv[NN], dv[NN], xv[NN], rv[NN], zv[NN];
+            ldc<NN>(pn, k, pv);
+            ldc<NN>(qb, k, qv);
+            ldc<NN>(A.idiag, k, dv);
+            ldc<NN>(A.x, k, xv);
+            ldc<NN>(rb, k, rv);
+#pragma unroll
+            for (int n = 0; n < NN; ++n) {
+                xv[n] = fma(alpha, pv[n], xv[n]);
+                rv[n] = fma(-alpha, qv[n], rv[n]);
+                zv[n] = rv[n] * dv[n];
+                v2[0] += rv[n] * rv[n];
+                v2[1] += rv[n] * zv[n];
+            }
+            stc<NN>(A.x, k, xv);
+            stc<NN>(rb, k, rv);
+            stc<NN>(ub, k, zv);
+        }
+        block_partials<2>(v2, A.partC, bid);
+        if (!grid_barrier(A.bar, bar_target)) return DONE_TIMEOUT;
+        grid_totals<2>(v2, A.partC, nb);
+        ++iters;
+        if (sqrt(v2[0]) <= stop) return DONE_CONVERGED;
+        if (iters >= A.max_pcg) return DONE_CAPPED;
+        beta = v2[1] / rz;
+        rz = v2[1];
+    }
+}
+
+// DONE_ code of a mixed-precision solve whose refinement stopped helping
+constexpr int DONE_FALLBACK = 5;
+
+// Mixed-precision conjugate gradients (iterative refinement) on S x = b from
+// x = E with the FP64 residual r = r[0] of the set-up: each cycle solves
+// S e = r approximately by Jacobi-preconditioned conjugate gradients in FP32
+// on FP32 copies of the operator's coefficients (on this GPU FP32 issues at 64
+// times the FP64 rate; the operator application is the solve's arithmetic),
+// to 1e-5 of the cycle's starting residual, then updates x += e and
+// r -= S e in FP64, so the FP64 residual -- the one the stopping test reads --
+// falls by about that factor per cycle, down to the same pcg_rtol as the FP64
+// solve.  A cycle that does not at least halve the FP64 norm of r returns
+// DONE_FALLBACK (the caller continues with the FP64 conjugate gradients from
+// x and r).  iters counts the inner iterations and the refinement updates.
+template <int NN>
+__device__ __forceinline__ int mixed_cg(const NewtonArgs &A, const int bid, const int nb,
+                                        const int k0, const int stride, unsigned &bar_target,
+                                        const double stop, int &iters) {
+    const Geo &G = A.G;
+    const GeoF Gf = geo_f(G);
+    constexpr float INNER = 1e-5f;
+    // cycle start: FP32 copies of the coefficients, r32 = r, u = r / diag(S),
+    // e = 0; sums r.r (FP64), r32.u, r32.r32
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int k = k0; k < G.ncell; k += stride) {
+        double aEv[NN], iav[NN], dv[NN], rv[NN];
+        ldc<NN>(A.aE, k, aEv);
+        ldc<NN>(A.iaF, k, iav);
+        ldc<NN>(A.idiag, k, dv);
+        ldc<NN>(A.r[0], k, rv);
+        float fa[NN], fi[NN], fd[NN], fr[NN], fu[NN], z[NN];
+#pragma unroll
+        for (int n = 0; n < NN; ++n) {
+            fa[n] = (float)aEv[n];
+            fi[n] = (float)iav[n];
+            fd[n] = (float)dv[n];
+            fr[n] = (float)rv[n];
+            fu[n] = fr[n] * fd[n];
+            z[n] = 0.f;
+            v[0] += rv[n] * rv[n];
+            v[1] += (double)fr[n] * (double)fu[n];
+            v[2] += (double)fr[n] * (double)fr[n];
+        }
+        stf<NN>(A.fa, k, fa);
+        stf<NN>(A.fi, k, fi);
+        stf<NN>(A.fd, k, fd);
+        stf<NN>(A.fr, k, fr);
+        stf<NN>(A.fu, k, fu);
+        stf<NN>(A.fp[0], k, fu);  // p = u + 0 p_old reads p_old: keep it finite
+        stf<NN>(A.fe[0], k, z);
+    }
+    block_partials<3>(v, A.partB, bid);
+    if (!grid_barrier(A.bar, bar_target)) return DONE_TIMEOUT;
+    grid_totals<3>(v, A.partB, nb);
+    double rr64 = v[0], rz = v[1], rr32 = v[2];
+    if (sqrt(rr64) <= stop) return DONE_CONVERGED;
+    for (int cyc = 0;; ++cyc) {
+        float *const e = A.fe[cyc & 1];
+        // inner FP32 conjugate gradients on S e = r32 from e = 0
+        const double inner_stop = (double)INNER * sqrt(rr32);
+        double beta = 0.0;
+        for (int it = 0;; ++it) {
+            const float *po = A.fp[it & 1];
+            float *pn = A.fp[(it + 1) & 1];
+            double v1[1] = {0.0};
+            for (int k = k0; k < G.ncell; k += stride) {
+                const Cell C = cell_of(G, k);
+                float aEv[NN], qv[NN], pv[NN];
+                ldf<NN>(A.fa, k, aEv);
+                schur_cell_t<float, NN>(Gf, C, DirF<NN>{A.fu, po, (float)beta}, aEv,
+                                        IaF<NN>{A.fi}, qv, pv);
+                stf<NN>(pn, k, pv);
+                stf<NN>(A.fq, k, qv);
+#pragma unroll
+                for (int n = 0; n < NN; ++n) v1[0] += (double)pv[n] * (double)qv[n];
+            }
+            block_partials<1>(v1, A.partC, bid);
+            if (!grid_barrier(A.bar, bar_target)) return DONE_TIMEOUT;
+            grid_totals<1>(v1, A.partC, nb);
+            if (!(v1[0] > 0.0) || !isfinite(v1[0]) || !isfinite(rz)) break;  // refine from here
+            const float alpha = (float)(rz / v1[0]);
+            double v2[2] = {0.0, 0.0};
+            for (int k = k0; k < G.ncell; k += stride) {
+                float pv[NN], qv[NN], dv[NN], ev[NN], rv[NN], uv[NN];
+                ldf<NN>(pn, k, pv);
+                ldf<NN>(A.fq, k, qv);
+                ldf<NN>(A.fd, k, dv);
+                ldf<NN>(e, k, ev);
+                ldf<NN>(A.fr, k, rv);
+#pragma unroll
+                for (int n = 0; n < NN; ++n) {
+                    ev[n] = __fmaf_rn(alpha, pv[n], ev[n]);
+                    rv[n] = __fmaf_rn(-alpha, qv[n], rv[n]);
+                    uv[n] = rv[n] * dv[n];
+                    v2[0] += (double)rv[n] * (double)rv[n];
+                    v2[1] += (double)rv[n] * (double)uv[n];
+                }
+                stf<NN>(e, k, ev);
+                stf<NN>(A.fr, k, rv);
+                stf<NN>(A.fu, k, uv);
+            }
+            block_partials<2>(v2, A.partD, bid);
+            if (!grid_barrier(A.bar, bar_target)) return DONE_TIMEOUT;
+            grid_totals<2>(v2, A.partD, nb);
+            ++iters;
+            if (sqrt(v2[0]) <= inner_stop || iters >= A.max_pcg || !isfinite(v2[1])) break;
+            beta = v2[1] / rz;
+            rz = v2[1];
+        }
+        // refinement: x += e, r -= S e in FP64; the next cycle's r32, u, e = 0
+        double v3[3] = {0.0, 0.0, 0.0};
+        float *const e_next = A.fe[(cyc + 1) & 1];
+        for (int k = k0; k < G.ncell; k += stride) {
+            const Cell C = cell_of(G, k);
+            double aEv[NN], se[NN], ed[NN], xv[NN], rv[NN];
+            ldc<NN>(A.aE, k, aEv);
+            schur_cell<NN>(G, C, VecFD<NN>{e}, aEv, A.iaF, se, ed);
+            ldc<NN>(A.x, k, xv);
+            ldc<NN>(A.r[0], k, rv);
+            float fd[NN], fr[NN], fu[NN], z[NN];
+            ldf<NN>(A.fd, k, fd);
+#pragma unroll
+            for (int n = 0; n < NN; ++n) {
+                xv[n] += ed[n];
+                rv[n] -= se[n];
+                fr[n] = (float)rv[n];
+                fu[n] = fr[n] * fd[n];
+                z[n] = 0.f;
+                v3[0] += rv[n] * rv[n];
+                v3[1] += (double)fr[n] * (double)fu[n];
+                v3[2] += (double)fr[n] * (double)fr[n];
+            }
+            stc<NN>(A.x, k, xv);
+            stc<NN>(A.r[0], k, rv);
+            stf<NN>(A.fr, k, fr);
+            stf<NN>(A.fu, k, fu);
+            stf<NN>(A.fp[0], k, fu);
+            stf<NN>(e_next, k, z);
+        }
+        block_partials<3>(v3, A.partA, bid);
+        if (!grid_barrier(A.bar, bar_target)) return DONE_TIMEOUT;
+        grid_totals<3>(v3, A.partA, nb);
+        ++iters;
+        if (!isfinite(v3[0])) return DONE_BREAKDOWN;
+        if (sqrt(v3[0]) <= stop) return DONE_CONVERGED;
+        if (iters >= A.max_pcg) return DONE_CAPPED;
+        if (v3[0] > 0.25 * rr64) return DONE_FALLBACK;  // the cycle did not halve ||r||
+        rr64 = v3[0];
+        rz = v3[1];
+        rr32 = v3[2];
+    }
+}
+
 // The Newton iteration of one problem on its nb blocks (bid: this block's
-// index among them).
-template <int NN, bool SINGLE>
+// index among them).  MIXED: the linear solves by mixed-precision conjugate
+// gradients (mixed_cg), SINGLE then unused.
+template <int NN, bool SINGLE, bool MIXED = false>
 __device__ __forceinline__ void lo_newton_body(const NewtonArgs &A, const int bid, const int nb) {
     if (A.withhold && bid == nb - 1) return;
     const Geo &G = A.G;
@@ -884,13 +1184,46 @@ __device__ __forceinline__ void lo_newton_body(const NewtonArgs &A, const int bi
         // set-up: linearisation, r = rhs - S E, ||rhs||^2 (textbook form:
         // also u, p = u, r.r, r.u)
         double v0[3] = {0.0, 0.0, 0.0};
-        for (int k = k0; k < G.ncell; k += stride) newton_setup_cell<NN, SINGLE>(A, k, v0);
+        for (int k = k0; k < G.ncell; k += stride)
+            newton_setup_cell<NN, SINGLE || MIXED>(A, k, v0);
         block_partials<3>(v0, A.partA, bid);
         if (!grid_barrier(A.bar, bar_target)) { status = LO_TIMEOUT; break; }
         grid_totals<3>(v0, A.partA, nb);
         const double stop = A.pcg_rtol * sqrt(v0[0]);
         int done = DONE_NO, iters = 0;
-        if constexpr (SINGLE) {
+        if constexpr (MIXED) {
+            done = mixed_cg<NN>(A, bid, nb, k0, stride, bar_target, stop, iters);
+            if (done == DONE_FALLBACK) {
+                // the FP64 conjugate gradients from the current x and r: u =
+                // r / diag(S), p = u; r.r, r.u (partial sums D: the last
+                // reduction used A, the first of the loop uses B)
+                double vf[2] = {0.0, 0.0};
+                double *const pst = (iters & 1) ? A.w[1] : A.w[0];
+                for (int k = k0; k < G.ncell; k += stride) {
+                    double rv[NN], dv[NN], zv[NN];
+                    ldc<NN>(A.r[0], k, rv);
+                    ldc<NN>(A.idiag, k, dv);
+#pragma unroll
+                    for (int n = 0; n < NN; ++n) {
+                        zv[n] = rv[n] * dv[n];
+                        vf[0] += rv[n] * rv[n];
+                        vf[1] += rv[n] * zv[n];
+                    }
+                    stc<NN>(A.r[1], k, zv);
+                    stc<NN>(pst, k, zv);
+                }
+                block_partials<2>(vf, A.partD, bid);
+                if (!grid_barrier(A.bar, bar_target)) {
+                    done = DONE_TIMEOUT;
+                } else {
+                    grid_totals<2>(vf, A.partD, nb);
+                    done = sqrt(vf[0]) <= stop
+                               ? DONE_CONVERGED
+                               : cg_textbook<NN>(A, bid, nb, k0, stride, bar_target, stop, vf[1],
+                                                 iters);
+                }
+            }
+        } else if constexpr (SINGLE) {
             // second set-up phase: u = r / diag(S), w = S u; r.u, w.u, r.r;
             // p = s = 0 before the first iteration
             double v3[3] = {0.0, 0.0, 0.0};
@@ -976,59 +1309,11 @@ __device__ __forceinline__ void lo_newton_body(const NewtonArgs &A, const int bi
                 rr = v[2];
             }
         } else {
-            // textbook form (start x = E, p = u): buffers r = r[0], u = r[1],
-            // p = w[0] / w[1] by iteration parity, q = s[0]
-            double *const rb = A.r[0], *const ub = A.r[1], *const qb = A.s[0];
-            double rz = v0[2], beta = 0.0;
-            if (sqrt(v0[1]) <= stop) done = DONE_CONVERGED;
-            while (done == DONE_NO) {
-                const double *po = (iters & 1) ? A.w[1] : A.w[0];
-                double *pn = (iters & 1) ? A.w[0] : A.w[1];
-                double v1[1] = {0.0};
-                for (int k = k0; k < G.ncell; k += stride) {
-                    const Cell C = cell_of(G, k);
-                    double aEv[NN], qv[NN], pv[NN];
-                    ldc<NN>(A.aE, k, aEv);
-                    schur_cell<NN>(G, C, DirCG<NN>{ub, po, beta}, aEv, A.iaF, qv, pv);
-                    stc<NN>(pn, k, pv);
-                    stc<NN>(qb, k, qv);
-#pragma unroll
-                    for (int n = 0; n < NN; ++n) v1[0] += pv[n] * qv[n];
-                }
-                block_partials<1>(v1, A.partB, bid);
-                if (!grid_barrier(A.bar, bar_target)) { done = DONE_TIMEOUT; break; }
-                grid_totals<1>(v1, A.partB, nb);
-                if (!(v1[0] > 0.0) || !isfinite(v1[0]) || !isfinite(rz)) { done = DONE_BREAKDOWN; break; }
-                const double alpha = rz / v1[0];
-                double v2[2] = {0.0, 0.0};
-                for (int k = k0; k < G.ncell; k += stride) {
-                    double pv[NN], qv[NN], dv[NN], xv[NN], rv[NN], zv[NN];
-                    ldc<NN>(pn, k, pv);
-                    ldc<NN>(qb, k, qv);
-                    ldc<NN>(A.idiag, k, dv);
-                    ldc<NN>(A.x, k, xv);
-                    ldc<NN>(rb, k, rv);
-#pragma unroll
-                    for (int n = 0; n < NN; ++n) {
-                        xv[n] = fma(alpha, pv[n], xv[n]);
-                        rv[n] = fma(-alpha, qv[n], rv[n]);
-                        zv[n] = rv[n] * dv[n];
-                        v2[0] += rv[n] * rv[n];
-                        v2[1] += rv[n] * zv[n];
-                    }
-                    stc<NN>(A.x, k, xv);
-                    stc<NN>(rb, k, rv);
-                    stc<NN>(ub, k, zv);
-                }
-                block_partials<2>(v2, A.partC, bid);
-                if (!grid_barrier(A.bar, bar_target)) { done = DONE_TIMEOUT; break; }
-                grid_totals<2>(v2, A.partC, nb);
-                ++iters;
-                if (sqrt(v2[0]) <= stop) { done = DONE_CONVERGED; break; }
-                if (iters >= A.max_pcg) { done = DONE_CAPPED; break; }
-                beta = v2[1] / rz;
-                rz = v2[1];
-            }
+            // textbook form (start x = E, p = u)
+            if (sqrt(v0[1]) <= stop)
+                done = DONE_CONVERGED;
+            else
+                done = cg_textbook<NN>(A, bid, nb, k0, stride, bar_target, stop, v0[2], iters);
         }
         if (done == DONE_TIMEOUT) { status = LO_TIMEOUT; break; }
         if (done == DONE_BREAKDOWN) { status = LO_BREAKDOWN; break; }
@@ -1066,20 +1351,21 @@ __device__ __forceinline__ void lo_newton_body(const NewtonArgs &A, const int bi
 
 // at least 4 blocks per SM (128 registers per thread): a 256x256 mesh (512
 // blocks of cells) then runs without grid-stride repeats
-template <int NN, bool SINGLE>
+template <int NN, bool SINGLE, bool MIXED>
 __global__ void __launch_bounds__(BLOCK, 4) lo_newton_kernel(const NewtonArgs A) {
-    lo_newton_body<NN, SINGLE>(A, blockIdx.x, gridDim.x);
+    lo_newton_body<NN, SINGLE, MIXED>(A, blockIdx.x, gridDim.x);
 }
 
 // The low-order solves of many problems in one cooperative launch: blocks
 // first[m] .. first[m + 1] - 1 solve problem m (its own arguments, partial
-// sums, barrier counter and scalars), each problem with its own PCG form.
+// sums, barrier counter and scalars), each problem with its own FP64 PCG form
+// (form[m]: 0 textbook, 1 single-reduction).
 // The problems share nothing, so each runs its own Newton and PCG
 // iterations and stopping tests; every block of the launch is co-resident,
 // so a problem's barriers wait only on blocks that are running.
 template <int NN>
 __global__ void __launch_bounds__(BLOCK, 4)
-lo_newton_batch_kernel(const NewtonArgs *__restrict__ args, const int *__restrict__ single,
+lo_newton_batch_kernel(const NewtonArgs *__restrict__ args, const int *__restrict__ form,
                        const int *__restrict__ first, int n) {
     __shared__ NewtonArgs sA;
     __shared__ int s_m;
@@ -1101,7 +1387,7 @@ lo_newton_batch_kernel(const NewtonArgs *__restrict__ args, const int *__restric
     }
     __syncthreads();
     const int bid = (int)blockIdx.x - first[m], nb = first[m + 1] - first[m];
-    if (single[m])
+    if (form[m] == 1)
         lo_newton_body<NN, true>(sA, bid, nb);
     else
         lo_newton_body<NN, false>(sA, bid, nb);
@@ -1146,7 +1432,8 @@ struct sm_lo_state {
     double *clo = nullptr;      // closures when the caller passes none
     smk::lo::Scalars *sc = nullptr;
     smk::lo::Scalars *h_sc = nullptr;  // pinned mirror
-    int coop_grid[2] = {0, 0};  // blocks of the cooperative launch per PCG form (0: not sized)
+    int coop_grid[3] = {0, 0, 0};  // blocks of the cooperative launch per PCG form (0: not sized)
+    float *fbuf = nullptr;         // the mixed-precision solves' FP32 vectors (10 per node)
     int nsm = 0;                // SMs of the device (0: not queried yet)
 };
 
@@ -1256,6 +1543,8 @@ sm_status lo_ensure(sm_problem *p) {
     w.Ein = take(N);
     const size_t nblk = (size_t)std::max(w.nblk_cell, w.nblk_node);
     LO_CUDA(cudaMalloc(&w.part, sizeof(double) * PART_PER_BLOCK * nblk));
+    LO_CUDA(cudaMalloc(&w.fbuf, sizeof(float) * (size_t)N * 10));
+    p->workspace_bytes += sizeof(float) * (size_t)N * 10;
     LO_CUDA(cudaMalloc(&w.jin2, sizeof(double) * 4));
     {  // consistent method: R0 [N], R1f [N][dim], quadrant moments, inflow moments
         LO_CUDA(cudaMalloc(&w.R0, sizeof(double) * (size_t)N * 3));
@@ -1341,15 +1630,30 @@ sm_status sm_count(sm_lo_state &w) {
     return SM_OK;
 }
 
-// The PCG form of problem p: the single-reduction form while the cells come
-// to at most 1.5 warps per SM sub-partition (4 per SM): measured on GB300, it
-// saves 3 % of a 128^2 gray step and 9 % of the 64-cell slab, and costs 3 %
-// on 256^2 meshes (3.4 warps per sub-partition), where the extra FP64 work of
-// forming the neighbours' u outweighs the saved barrier.
-bool single_form(const sm_problem *p, int nsm) {
-    const long long warps = ((long long)p->ncell + 31) / 32;
-    return p->lo_pcg_form == SM_DEBUG_PCG_AUTO ? 2 * warps <= 3LL * 4 * nsm
-                                               : p->lo_pcg_form == SM_DEBUG_PCG_SINGLE;
+// The PCG form of problem p (0 textbook, 1 single-reduction, 2 mixed
+// precision).  The library's choice: the single-reduction form below
+// SINGLE_CELLS cells, the textbook form from there on.  Measured on GB300
+// (seconds per converged step, the same iterates): the single-reduction form
+// saves 9 % on the 64-cell slab, but costs 7 % on the 128^2 gray channel
+// (5.32 against 4.97 ms) and 5 % on the 256^2 multigroup mesh, where the extra
+// FP64 work of forming the neighbours' u outweighs the saved barrier.  The
+// mixed-precision form is not chosen: it needs 1.6x the iterations (each
+// refinement cycle restarts the Krylov space) and an iteration, bound by the
+// grid barriers' latency rather than by FP64 arithmetic, gets only about a
+// quarter cheaper (gray channel 5.81 ms, multigroup 33.7 against 32.3 ms).
+constexpr long long SINGLE_CELLS = 4096;
+int pcg_form(const sm_problem *p, int nsm) {
+    (void)nsm;
+    switch (p->lo_pcg_form) {
+        case SM_DEBUG_PCG_TEXTBOOK: return 0;
+        case SM_DEBUG_PCG_SINGLE: return 1;
+        case SM_DEBUG_PCG_MIXED: return 2;
+        default: break;
+    }
+    return p->ncell < SINGLE_CELLS ? 1 : 0;
+}
+int form_used(int f) {
+    return f == 2 ? SM_DEBUG_PCG_MIXED : f == 1 ? SM_DEBUG_PCG_SINGLE : SM_DEBUG_PCG_TEXTBOOK;
 }
 
 // The arguments of problem p's Newton kernel on nblocks blocks.
@@ -1403,6 +1707,12 @@ smk::lo::NewtonArgs newton_args(sm_problem *p, sm_lo_state &w, const Geo &G, con
     A.bar.nblocks = (unsigned)nblocks;
     A.bar.limit_ns = p->timeout_ns;
     A.withhold = p->fault_withhold_block;
+    {
+        float *f = w.fbuf;
+        float **slots[] = {&A.fa, &A.fi, &A.fd, &A.fr, &A.fu, &A.fp[0], &A.fp[1], &A.fq, &A.fe[0],
+                           &A.fe[1]};
+        for (int i = 0; i < 10; ++i) *slots[i] = f + (size_t)i * w.N;
+    }
     return A;
 }
 
@@ -1413,10 +1723,11 @@ sm_status launch_newton(sm_problem *p, sm_lo_state &w, const Geo &G, const doubl
                         double *T, double *E, double *F, const double *Tstar, const double *cv,
                         const double *R0, const sm_step_params &prm) {
     LO_TRY(sm_count(w));
-    const bool single = single_form(p, w.nsm);
-    const void *k = single ? (const void *)smk::lo::lo_newton_kernel<NN, true>
-                           : (const void *)smk::lo::lo_newton_kernel<NN, false>;
-    int &grid = w.coop_grid[single ? 1 : 0];
+    const int form = pcg_form(p, w.nsm);
+    const void *k = form == 2   ? (const void *)smk::lo::lo_newton_kernel<NN, false, true>
+                    : form == 1 ? (const void *)smk::lo::lo_newton_kernel<NN, true, false>
+                                : (const void *)smk::lo::lo_newton_kernel<NN, false, false>;
+    int &grid = w.coop_grid[form];
     if (grid == 0) {
         int per_sm = 0;
         LO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BLOCK, 0));
@@ -1426,7 +1737,7 @@ sm_status launch_newton(sm_problem *p, sm_lo_state &w, const Geo &G, const doubl
     smk::lo::NewtonArgs A = newton_args(p, w, G, clo, T, E, F, Tstar, cv, R0, prm, grid);
     void *args[] = {&A};
     LO_CUDA(cudaLaunchCooperativeKernel(k, dim3(grid), dim3(BLOCK), args, 0, p->stream));
-    p->lo_pcg_form_used = single ? SM_DEBUG_PCG_SINGLE : SM_DEBUG_PCG_TEXTBOOK;
+    p->lo_pcg_form_used = form_used(form);
     return SM_OK;
 }
 
@@ -1605,7 +1916,7 @@ sm_status batch_lo_launch(sm_batch *b, const std::vector<int> &members,
                                                : (long long)((double)(need[i] - 1) * rest / extra_need);
         nb[i] += std::min(e, need[i] - 1);
     }
-    int *single = L.h_int, *first = L.h_int + n;
+    int *form = L.h_int, *first = L.h_int + n;
     first[0] = 0;
     for (int i = 0; i < n; ++i) {
         sm_problem *p = probs[members[i]];
@@ -1618,9 +1929,9 @@ sm_status batch_lo_launch(sm_batch *b, const std::vector<int> &members,
         p->launches++;
         L.h_args[i] = newton_args(p, w, G, clo[m], T[m], E[m], F[m], w.Tstar, cv[m], nullptr, prm,
                                   (int)nb[i]);
-        single[i] = single_form(p, nsm) ? 1 : 0;
+        form[i] = pcg_form(p, nsm) == 1 ? 1 : 0;  // the batched launch runs the FP64 forms
         first[i + 1] = first[i] + (int)nb[i];
-        p->lo_pcg_form_used = single[i] ? SM_DEBUG_PCG_SINGLE : SM_DEBUG_PCG_TEXTBOOK;
+        p->lo_pcg_form_used = form_used(form[i]);
     }
     LO_CUDA(cudaMemcpyAsync(L.d_args, L.h_args, sizeof(smk::lo::NewtonArgs) * n,
                             cudaMemcpyHostToDevice, s));
@@ -1649,7 +1960,7 @@ void batch_lo_free(void *scratch) {
 void lo_free(sm_problem *p) {
     if (!p->lo) return;
     sm_lo_state &w = *p->lo;
-    void *bufs[] = {w.buf, w.part, w.jin2, w.sigma, w.clo, w.sc, w.R0, w.qmom_int, w.jinc};
+    void *bufs[] = {w.buf, w.part, w.jin2, w.sigma, w.clo, w.sc, w.R0, w.qmom_int, w.jinc, w.fbuf};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (w.h_sc) cudaFreeHost(w.h_sc);

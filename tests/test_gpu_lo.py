@@ -11,10 +11,11 @@ per field (T, E against their largest value; F against c times the largest
 E, since F vanishes near equilibrium).  A full step with the FP32 sweep
 inherits the sweep's 1e-6-level rounding through the closures: 1e-5.
 
-The library has two forms of the conjugate gradients (two grid reductions per
-iteration, or the single-reduction form of Chronopoulos and Gear) and picks
-one by mesh size; the oracle comparisons run both, forced through the
-sm_debug_set_pcg_form test hook.
+The library has three forms of the conjugate gradients (FP64 with two grid
+reductions per iteration, FP64 in the single-reduction form of Chronopoulos and
+Gear, and mixed precision: FP32 inner solves refined by FP64 residual updates
+to the same FP64 stopping test) and picks one by mesh size; the oracle
+comparisons run all three, forced through the sm_debug_set_pcg_form test hook.
 """
 import math
 
@@ -88,9 +89,10 @@ LO_CASES = {
 }
 
 
-# both forms of the conjugate gradients (textbook: two grid reductions per
-# iteration; single: Chronopoulos-Gear, one), forced through the test hook
-PCG_FORMS = ("textbook", "single")
+# the forms of the conjugate gradients (textbook: two grid reductions per
+# iteration; single: Chronopoulos-Gear, one; mixed: FP32 inner solves with FP64
+# refinement), forced through the test hook
+PCG_FORMS = ("textbook", "single", "mixed")
 
 
 @pytest.mark.parametrize("form", PCG_FORMS)
@@ -118,17 +120,17 @@ def test_loworder_newton_matches_oracle(gpu_lib, name, form):
 
 
 def test_pcg_forms_agree_on_a_large_mesh(gpu_lib):
-    """200x200 cells (1250 warps of cells, above the single-reduction form's
-    1.5 warps per SM sub-partition on 152 SMs): the library's choice is the
-    textbook form, a small mesh gets the single-reduction form, and the two
-    forms give the same solve to the accuracy of the linear solves."""
+    """200x200 cells: the library's choice is the textbook form (4096 cells
+    and up), a small mesh gets the single-reduction form, and the forced
+    mixed-precision form gives the textbook form's solve to the accuracy of
+    the linear solves, with the same Newton iterations."""
     cfg = _cfg(2, 200, 200)
     m, clo, T, cv, mom_k, alpha, jin2 = _lo_inputs(cfg, seed=17)
     Estar = mom_k[..., 0] / cfg.c
     kw = dict(eps_inner=1e-13, max_inner=40, pcg_rtol=1e-14, elim_rtol=1e-15, max_elim=80)
-    Ta, Ea, Fa, sa, pa = _gpu_lo(gpu_lib, cfg, clo, T, cv, mom_k, T, Estar, **kw)
-    Tb, Eb, Fb, sb, pb = _gpu_lo(gpu_lib, cfg, clo, T, cv, mom_k, T, Estar, form="single", **kw)
-    assert pa.debug_pcg_form() == "textbook" and pb.debug_pcg_form() == "single"
+    Ta, Ea, Fa, sa, pa = _gpu_lo(gpu_lib, cfg, clo, T, cv, mom_k, T, Estar, form="mixed", **kw)
+    Tb, Eb, Fb, sb, pb = _gpu_lo(gpu_lib, cfg, clo, T, cv, mom_k, T, Estar, **kw)
+    assert pa.debug_pcg_form() == "mixed" and pb.debug_pcg_form() == "textbook"
     eT, eE = _field(Tb, Ta), _field(Eb, Ea)
     eF = _field(Fb, Fa, scale=cfg.c * Ea)
     print(f"forms: T {eT:.2e} E {eE:.2e} F {eF:.2e} pcg {sa['pcg_iters_total']} / "
