@@ -35,24 +35,81 @@ namespace adj {
 
 constexpr int BLOCK = 256;
 
+// Fixed-order sums, so that a forward or adjoint step gives the same bits on
+// every run: each block folds its threads' pairs by warp shuffles and then
+// across its warps in a fixed order and writes one partial pair; finish_kernel
+// (one block) sums the partials in a fixed order into acc.
+__device__ __forceinline__ void block_sum2(double a, double b, double *__restrict__ part) {
+    __shared__ double sa[BLOCK / 32], sb[BLOCK / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sa[wid] = a;
+        sb[wid] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int i = 0; i < BLOCK / 32; ++i) {
+            ta += sa[i];
+            tb += sb[i];
+        }
+        part[2 * blockIdx.x] = ta;
+        part[2 * blockIdx.x + 1] = tb;
+    }
+}
+
+__global__ void __launch_bounds__(BLOCK) finish_kernel(int nb, const double *__restrict__ part,
+                                                       double *__restrict__ acc) {
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nb; i += BLOCK) {
+        a += part[2 * i];
+        b += part[2 * i + 1];
+    }
+    __shared__ double out[2 * BLOCK];
+    out[threadIdx.x] = a;
+    out[BLOCK + threadIdx.x] = b;
+    __syncthreads();
+    for (int h = BLOCK / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            out[threadIdx.x] += out[threadIdx.x + h];
+            out[BLOCK + threadIdx.x] += out[BLOCK + threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        acc[0] = out[0];
+        acc[1] = out[BLOCK];
+    }
+}
+
 // One Newton step of the nodal energy balance with sum_g sigma_g phi_g (SE)
 // fixed; sum_g sigma_g B_g(T) = a c T^4 sigma_P and sum_g sigma_g B'_g =
-// 4 a c T^3 sigma_F from the emission pass at T.  acc += (|dT|^2, |T|^2).
-__global__ void energy_kernel(int N, double ac, double dt, const double *__restrict__ Tn,
-                              const double *__restrict__ cv, const double *__restrict__ gray,
-                              const double *__restrict__ mom, int nm, int ise,
-                              double *__restrict__ T, double *acc) {
+// 4 a c T^3 sigma_F from the emission pass at T.  Block partials of
+// (|dT|^2, |T|^2) in part.
+__global__ void __launch_bounds__(BLOCK)
+    energy_kernel(int N, double ac, double dt, const double *__restrict__ Tn,
+                  const double *__restrict__ cv, const double *__restrict__ gray,
+                  const double *__restrict__ mom, int nm, int ise, double *__restrict__ T,
+                  double *__restrict__ part) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= N) return;
-    const double T0 = T[t];
-    const double cv_dt = cv[t] / dt;
-    const double T3 = T0 * T0 * T0;
-    const double f = cv_dt * (T0 - Tn[t]) + ac * T3 * T0 * gray[2 * t] - mom[(size_t)t * nm + ise];
-    const double fp = cv_dt + 4.0 * ac * T3 * gray[2 * t + 1];
-    const double Tnew = fmax(T0 - f / fp, 0.1 * T0);  // the safeguard never binds near the root
-    T[t] = Tnew;
-    atomicAdd(acc, (Tnew - T0) * (Tnew - T0));
-    atomicAdd(acc + 1, Tnew * Tnew);
+    double dd = 0.0, tt = 0.0;
+    if (t < N) {
+        const double T0 = T[t];
+        const double cv_dt = cv[t] / dt;
+        const double T3 = T0 * T0 * T0;
+        const double f =
+            cv_dt * (T0 - Tn[t]) + ac * T3 * T0 * gray[2 * t] - mom[(size_t)t * nm + ise];
+        const double fp = cv_dt + 4.0 * ac * T3 * gray[2 * t + 1];
+        const double Tnew = fmax(T0 - f / fp, 0.1 * T0);  // the safeguard never binds near the root
+        T[t] = Tnew;
+        dd = (Tnew - T0) * (Tnew - T0);
+        tt = Tnew * Tnew;
+    }
+    block_sum2(dd, tt, part);
 }
 
 // Adjoint source records: q = sigma_g theta at the nodes, sigma~, sigma
@@ -81,25 +138,29 @@ __global__ void source_kernel(int ncell, int nn, int G, int Gp, double inv_cdt,
 }
 
 // theta = (sum_g cB_g sum_d w_d psi_{d,g} + X) / (C_v/dt + sdB) per node;
-// acc += (|dtheta|^2, |theta|^2).  psi canonical [d][g][node].
-__global__ void theta_kernel(int N, int nd, int G, const double *__restrict__ w,
-                             const double *__restrict__ psi, const double *__restrict__ cB,
-                             const double *__restrict__ sdB, const double *__restrict__ cv,
-                             double dt, const double *__restrict__ X, double *__restrict__ theta,
-                             double *acc) {
+// Block partials of (|dtheta|^2, |theta|^2) in part.  psi canonical [d][g][node].
+__global__ void __launch_bounds__(BLOCK)
+    theta_kernel(int N, int nd, int G, const double *__restrict__ w,
+                 const double *__restrict__ psi, const double *__restrict__ cB,
+                 const double *__restrict__ sdB, const double *__restrict__ cv, double dt,
+                 const double *__restrict__ X, double *__restrict__ theta,
+                 double *__restrict__ part) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= N) return;
-    double s = 0.0;
-    for (int g = 0; g < G; ++g) {
-        double ph = 0.0;
-        for (int d = 0; d < nd; ++d) ph += w[d] * psi[((size_t)d * G + g) * N + t];
-        s += cB[(size_t)g * N + t] * ph;
+    double dd = 0.0, tt = 0.0;
+    if (t < N) {
+        double s = 0.0;
+        for (int g = 0; g < G; ++g) {
+            double ph = 0.0;
+            for (int d = 0; d < nd; ++d) ph += w[d] * psi[((size_t)d * G + g) * N + t];
+            s += cB[(size_t)g * N + t] * ph;
+        }
+        const double th = (s + (X ? X[t] : 0.0)) / (cv[t] / dt + sdB[t]);
+        const double d0 = th - theta[t];
+        theta[t] = th;
+        dd = d0 * d0;
+        tt = th * th;
     }
-    const double th = (s + (X ? X[t] : 0.0)) / (cv[t] / dt + sdB[t]);
-    const double d0 = th - theta[t];
-    theta[t] = th;
-    atomicAdd(acc, d0 * d0);
-    atomicAdd(acc + 1, th * th);
+    block_sum2(dd, tt, part);
 }
 
 // G_{g,K} = -sum_{n in K} [sum_d w_d (psi I - psi B4 - theta I) + 4 pi theta B4],
@@ -153,21 +214,26 @@ __global__ void chain_kernel(int ncell, int nn, int G, const double *__restrict_
 // Outgoing partial current through the right edge, lumped at the face's
 // Gauss-Lobatto points: sum_{d: Omega_x > 0} w_d Omega_x sum_g sum (h_y/2) I
 // over the right-edge nodes (a = 1 of the last column).  One thread per
-// (d, g, row); I canonical.
-__global__ void leakage_kernel(int nx, int ny, int nn, int nd, int G, double half_hy,
-                               const double *__restrict__ omx, const double *__restrict__ w,
-                               const double *__restrict__ I, double *acc) {
+// (d, g, row), block partials in part; I canonical.
+__global__ void __launch_bounds__(BLOCK)
+    leakage_kernel(int nx, int ny, int nn, int nd, int G, double half_hy,
+                   const double *__restrict__ omx, const double *__restrict__ w,
+                   const double *__restrict__ I, double *__restrict__ part) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nd * G * ny) return;
-    const int d = i / (G * ny), r = i - d * G * ny;
-    const int g = r / ny, iy = r - g * ny;
-    if (!(omx[d] > 0.0)) return;
-    const size_t N = (size_t)nx * ny * nn;
-    const size_t cell = (size_t)iy * nx + nx - 1;
-    const size_t o = ((size_t)d * G + g) * N + cell * nn;
-    double s = I[o + 1];
-    if (nn == 4) s += I[o + 3];
-    atomicAdd(acc, w[d] * omx[d] * half_hy * s);
+    double v = 0.0;
+    if (i < nd * G * ny) {
+        const int d = i / (G * ny), r = i - d * G * ny;
+        const int g = r / ny, iy = r - g * ny;
+        if (omx[d] > 0.0) {
+            const size_t N = (size_t)nx * ny * nn;
+            const size_t cell = (size_t)iy * nx + nx - 1;
+            const size_t o = ((size_t)d * G + g) * N + cell * nn;
+            double s = I[o + 1];
+            if (nn == 4) s += I[o + 3];
+            v = w[d] * omx[d] * half_hy * s;
+        }
+    }
+    block_sum2(v, 0.0, part);
 }
 
 }  // namespace adj
@@ -176,6 +242,7 @@ __global__ void leakage_kernel(int nx, int ny, int nn, int nd, int G, double hal
 struct sm_adj_state {
     double *buf = nullptr;
     double *sigma, *f, *df, *B4, *cB, *sdB, *theta, *Tn, *mom, *Gs, *psi_c, *I_c, *omx, *w, *acc;
+    double *part;  // per-block partial pairs of the fixed-order sums
     double *h_acc = nullptr;
     void *inflow_adj = nullptr;  // [4][Gp] in the sweep precision
 };
@@ -210,7 +277,9 @@ sm_status adj_ensure(sm_problem *p) {
     sm_adj_state &a = *p->adj;
     const size_t N = (size_t)p->ncell * p->nn, GC = (size_t)p->G * p->ncell, GN = (size_t)p->G * N;
     const size_t canon = (size_t)p->nd * GN;
-    const size_t total = 3 * GC + 2 * GN + 3 * N + N * p->nm + GC + 2 * canon + 2 * p->nd + 4;
+    const size_t nparts = 2 * (size_t)std::max(nblk(N), nblk((size_t)p->nd * p->G * p->ny));
+    const size_t total =
+        3 * GC + 2 * GN + 3 * N + N * p->nm + GC + 2 * canon + 2 * p->nd + 4 + nparts;
     A_CUDA(cudaMalloc(&a.buf, sizeof(double) * total));
     double *b = a.buf;
     auto take = [&](size_t n) {
@@ -233,6 +302,7 @@ sm_status adj_ensure(sm_problem *p) {
     a.omx = take(p->nd);
     a.w = take(p->nd);
     a.acc = take(4);
+    a.part = take(nparts);
     A_CUDA(cudaMemcpy(a.omx, p->omx.data(), sizeof(double) * p->nd, cudaMemcpyHostToDevice));
     A_CUDA(cudaMemcpy(a.w, p->w.data(), sizeof(double) * p->nd, cudaMemcpyHostToDevice));
     A_CUDA(cudaMallocHost(&a.h_acc, sizeof(double) * 4));
@@ -254,8 +324,12 @@ sm_status adj_ensure(sm_problem *p) {
     return SM_OK;
 }
 
-sm_status read_acc(sm_problem *p, double *out2) {
+// Sums the nb block partials in a fixed order and reads the pair back.
+sm_status read_acc(sm_problem *p, int nb, double *out2) {
     sm_adj_state &a = *p->adj;
+    smk::adj::finish_kernel<<<1, BLOCK, 0, p->stream>>>(nb, a.part, a.acc);
+    A_CUDA(cudaGetLastError());
+    p->launches++;
     A_CUDA(cudaMemcpyAsync(a.h_acc, a.acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
     A_CUDA(cudaStreamSynchronize(p->stream));
     out2[0] = a.h_acc[0];
@@ -321,14 +395,13 @@ sm_status sm_ho_step(sm_problem *p, const double *scale_dev, const double *cv_de
     int it = 0;
     for (it = 1; it <= max_iter; ++it) {
         A_TRY(sm_sweep(p, T_dev, a.sigma, I_prev_dev, I_next_dev, a.mom, nullptr));
-        A_CUDA(cudaMemsetAsync(a.acc, 0, 2 * sizeof(double), s));
         smk::adj::energy_kernel<<<nblk(N), BLOCK, 0, s>>>(N, p->desc.a * p->desc.c, p->desc.dt,
                                                           a.Tn, cv_dev, p->d_gray, a.mom, p->nm,
-                                                          ise, T_dev, a.acc);
+                                                          ise, T_dev, a.part);
         A_CUDA(cudaGetLastError());
         p->launches++;
         double h[2];
-        A_TRY(read_acc(p, h));
+        A_TRY(read_acc(p, nblk(N), h));
         if (!std::isfinite(h[0]) || !std::isfinite(h[1]))
             return a_fail(SM_ERR_NONPHYSICAL, "the temperature iterate is not finite");
         if (std::sqrt(h[0]) <= tol * std::sqrt(h[1])) break;
@@ -347,14 +420,13 @@ sm_status sm_leakage(sm_problem *p, const void *I_dev, double *out_host) {
     sm_adj_state &a = *p->adj;
     cudaStream_t s = p->stream;
     A_CUDA(smk::launch_pack(p, a.I_c, const_cast<void *>(I_dev), 1, s));
-    A_CUDA(cudaMemsetAsync(a.acc, 0, 2 * sizeof(double), s));
     const int n = p->nd * p->G * p->ny;
     smk::adj::leakage_kernel<<<nblk(n), BLOCK, 0, s>>>(p->nx, p->ny, p->nn, p->nd, p->G,
-                                                       0.5 * p->hy, a.omx, a.w, a.I_c, a.acc);
+                                                       0.5 * p->hy, a.omx, a.w, a.I_c, a.part);
     A_CUDA(cudaGetLastError());
     p->launches += 2;
     double h[2];
-    A_TRY(read_acc(p, h));
+    A_TRY(read_acc(p, nblk(n), h));
     *out_host = h[0];
     return SM_OK;
 }
@@ -393,13 +465,12 @@ sm_status sm_adjoint_step(sm_problem *p, const double *scale_dev, const double *
     int it = 0;
     for (it = 1; it <= max_iter && st == SM_OK; ++it) {
         if ((st = adjoint_sweep(p, psi_next_dev, psi_out_dev)) != SM_OK) break;
-        cudaMemsetAsync(a.acc, 0, 2 * sizeof(double), s);
         smk::adj::theta_kernel<<<nblk(N), BLOCK, 0, s>>>(N, p->nd, p->G, a.w, a.psi_c, a.cB,
                                                          a.sdB, cv_dev, dt, X_next_dev, a.theta,
-                                                         a.acc);
+                                                         a.part);
         p->launches++;
         double h[2];
-        if ((st = read_acc(p, h)) != SM_OK) break;
+        if ((st = read_acc(p, nblk(N), h)) != SM_OK) break;
         if (!std::isfinite(h[0])) {
             st = a_fail(SM_ERR_NONPHYSICAL, "the adjoint iterate is not finite");
             break;

@@ -125,6 +125,26 @@ def test_checkpointing_does_not_change_the_gradient(gpu_lib):
         assert np.abs(g - grads[0]).max() < 1e-12 * np.abs(grads[0]).max()
 
 
+def test_forward_and_gradient_are_bit_reproducible(gpu_lib):
+    """The convergence norms and the leakage are fixed-order sums, so two runs
+    of the forward and of the checkpointed backward give the same bits (the
+    central differences of J see no run-to-run summation noise).  480 cells:
+    several blocks of the norm and leakage reductions."""
+    from paper_2504_21784_gb300 import adjoint as A
+    sm = gpu_lib
+    cfg, pb, scale, cv, T0, I0 = _pair(nx=24, ny=20, G=4, npol=2, naz=2, seed=5)
+    out = []
+    for _ in range(2):
+        prob, st, s = _setup(sm, cfg, scale, cv, T0, I0, 4, every=2)
+        s.requires_grad_(True)
+        J = A.leakage(s, st)
+        J.backward()
+        out.append((J.item(), s.grad.cpu().numpy()))
+        prob.close()
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1])
+
+
 def test_adjoint_rejects_bad_arguments(gpu_lib):
     import torch
     sm = gpu_lib
