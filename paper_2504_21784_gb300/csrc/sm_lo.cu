@@ -117,6 +117,9 @@ template <int NN>
 struct VecCG {
     const double *v;
     __device__ __forceinline__ void get(int k, double (&o)[NN]) const { ldc_cg<NN>(v, k, o); }
+    __device__ __forceinline__ double get1(int k, int n) const {
+        return __ldcg(v + (size_t)k * NN + n);
+    }
 };
 
 // Node numbering inside a cell: n = a + 2b (2D), n = a (1D); a, b = 0 on the
@@ -204,11 +207,7 @@ __device__ __forceinline__ void schur_cell_t(const GT &G, const Cell &C, const A
     }
 }
 
-// the 1/A_FF array's accessors: FP64 (as stored), FP32 copy
-template <int NN> struct IaD {
-    const double *a;
-    __device__ __forceinline__ double operator()(int k, int n) const { return a[(size_t)k * NN + n]; }
-};
+// the FP32 copy of the 1/A_FF array (mixed-precision inner solves)
 template <int NN> struct IaF {
     const float *a;
     __device__ __forceinline__ float operator()(int k, int n) const {
@@ -216,11 +215,157 @@ template <int NN> struct IaF {
     }
 };
 
+// The stencil of S assembled once per low-order solve: S = A_EE - A_EF
+// A_FF^-1 A_FE depends on the Newton iterate only through aE on its diagonal
+// (A_FF holds the closures' sigma~_F, fixed for the solve), so every other
+// coefficient is formed once from 1/A_FF and the geometry, by differentiating
+// the cell formula of schur_cell_t term by term, and a conjugate-gradient
+// matrix-vector product costs one FMA per coefficient instead of the formula's
+// FP64 work.  Coefficients of cell k at Sc + k * Stencil<NN>::n:
+//   2D: [0..3] geometric diagonal g_n (diag(S) = aE_n + g_n); own-cell
+//       couplings (0,1) 4, (0,2) 5, (1,0) 6, (1,3) 7, (2,0) 8, (2,3) 9,
+//       (3,1) 10, (3,2) 11; neighbour couplings, (row <- cell node):
+//       0 <- L0 12, L1 13, B0 14, B2 15, R0 16, T0 17;
+//       1 <- R0 18, B1 19, B3 20, T1 21;  2 <- L2 22, L3 23, R2 24, T0 25;
+//       3 <- R2 26, T1 27  (L, R, B, T: the left, right, bottom, top cell;
+//       zero where that face is a boundary).
+//   1D: [0..1] g_n; (0,1) 2, (1,0) 3; 0 <- L0 4, L1 5, R0 6; 1 <- R0 7.
+template <int NN> struct Stencil;
+template <> struct Stencil<4> { static constexpr int n = 28; };
+template <> struct Stencil<2> { static constexpr int n = 8; };
+
+// The coefficients one row pair (x) or node column (y) adds, with k_, f_,
+// l_, wf, pen, bnd its kx, fx, lx, wfx, px, bx (or the y ones), ia0 / ia1
+// the 1/A_FF of its low / high node, lo / hi whether its low / high face is
+// interior and iaLo the low neighbour's 1/A_FF at that neighbour's high node.
+// oa = (n0, n1), ob = (n1, n0), hA = (n0 <- hi n0), hB = (n1 <- hi n0),
+// lA = (n0 <- lo n0), lB = (n0 <- lo n1).
+__device__ __forceinline__ void axis_coefs(double k_, double f_, double l_, double wf, double pen,
+                                           double bnd, double ia0, double ia1, bool lo, bool hi,
+                                           double iaLo, double *c, int n0, int n1, int oa, int ob,
+                                           int hA, int hB, int lA, int lB) {
+    // u0 = ia0 (k s - f e_n0), u1 = ia1 (f e^ - k s), s = e_n0 + e_n1,
+    // e^ = the high neighbour's e_n0 (interior face) or e_n1 (boundary)
+    const double a0 = ia0 * (k_ - f_), a1 = ia0 * k_;
+    const double b0 = -ia1 * k_;
+    const double b1 = hi ? -ia1 * k_ : ia1 * (f_ - k_);
+    const double bH = hi ? ia1 * f_ : 0.0;
+    // sv = l (u0 + u1): q_n0 -= sv, q_n1 += sv
+    const double s0 = l_ * (a0 + b0), s1 = l_ * (a1 + b1), sH = l_ * bH;
+    c[n0] -= s0;
+    c[oa] -= s1;
+    c[n1] += s1;
+    c[ob] += s0;
+    if (lo) {
+        // q_n0 += wf uL + pen (e_n0 - eL_n1), uL = iaLo (f e_n0 - k (eL_n0 + eL_n1))
+        c[n0] += wf * iaLo * f_ + pen;
+        c[lA] -= wf * iaLo * k_;
+        c[lB] -= wf * iaLo * k_ + pen;
+    } else {
+        c[n0] += bnd;
+    }
+    if (hi) {
+        // q_n0 -= sv's high part; q_n1 += sv's high part - wf u1 + pen (e_n1 - eH_n0)
+        c[hA] -= sH;
+        c[n1] += pen - wf * b1;
+        c[ob] -= wf * b0;
+        c[hB] += sH - wf * bH - pen;
+    } else {
+        c[n1] += bnd;
+    }
+}
+
+// One thread per cell: the cell's stencil coefficients from 1/A_FF (its own
+// and its low neighbours') and the geometry.
+template <int NN>
+__global__ void __launch_bounds__(BLOCK)
+stencil_kernel(Geo G, const double *__restrict__ iaF, double *__restrict__ Sc) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= G.ncell) return;
+    const Cell C = cell_of(G, k);
+    constexpr int NS = Stencil<NN>::n;
+    double c[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) c[i] = 0.0;
+    double ia[NN];
+    ldc<NN>(iaF, k, ia);
+    if constexpr (NN == 4) {
+        const double iaL0 = C.L ? iaF[(size_t)(k - 1) * NN + 1] : 0.0;
+        const double iaL1 = C.L ? iaF[(size_t)(k - 1) * NN + 3] : 0.0;
+        const double iaB0 = C.B ? iaF[(size_t)(k - G.nx) * NN + 2] : 0.0;
+        const double iaB1 = C.B ? iaF[(size_t)(k - G.nx) * NN + 3] : 0.0;
+        axis_coefs(G.kx, G.fx, G.lx, G.wfx, G.px, G.bx, ia[0], ia[1], C.L, C.R, iaL0, c, 0, 1,
+                   4, 6, 16, 18, 12, 13);
+        axis_coefs(G.kx, G.fx, G.lx, G.wfx, G.px, G.bx, ia[2], ia[3], C.L, C.R, iaL1, c, 2, 3,
+                   9, 11, 24, 26, 22, 23);
+        axis_coefs(G.ky, G.fy, G.ly, G.wfy, G.py, G.by, ia[0], ia[2], C.B, C.T, iaB0, c, 0, 2,
+                   5, 8, 17, 25, 14, 15);
+        axis_coefs(G.ky, G.fy, G.ly, G.wfy, G.py, G.by, ia[1], ia[3], C.B, C.T, iaB1, c, 1, 3,
+                   7, 10, 21, 27, 19, 20);
+    } else {
+        const double iaL = C.L ? iaF[(size_t)(k - 1) * NN + 1] : 0.0;
+        axis_coefs(G.kx, G.fx, G.lx, G.wfx, G.px, G.bx, ia[0], ia[1], C.L, C.R, iaL, c, 0, 1, 2,
+                   3, 6, 7, 4, 5);
+    }
+    double2 *o = reinterpret_cast<double2 *>(Sc + (size_t)k * NS);
+#pragma unroll
+    for (int i = 0; i < NS / 2; ++i) o[i] = make_double2(c[2 * i], c[2 * i + 1]);
+}
+
+// q = S e on the nodes of cell C from the assembled stencil (the operator of
+// schur_cell_t up to rounding); e receives the cell's own values.
 template <int NN, class Acc>
 __device__ __forceinline__ void schur_cell(const Geo &G, const Cell &C, const Acc &acc,
-                                           const double (&aE)[NN], const double *__restrict__ iaF,
+                                           const double (&aE)[NN], const double *__restrict__ Sc,
                                            double (&q)[NN], double (&e)[NN]) {
-    schur_cell_t<double, NN>(G, C, acc, aE, IaD<NN>{iaF}, q, e);
+    constexpr int NS = Stencil<NN>::n;
+    double c[NS];
+    const double2 *cp = reinterpret_cast<const double2 *>(Sc + (size_t)C.k * NS);
+#pragma unroll
+    for (int i = 0; i < NS / 2; ++i) {
+        const double2 t = __ldg(cp + i);
+        c[2 * i] = t.x;
+        c[2 * i + 1] = t.y;
+    }
+    acc.get(C.k, e);
+    if constexpr (NN == 4) {
+        double eL[4] = {0.0, 0.0, 0.0, 0.0}, eB[4] = {0.0, 0.0, 0.0, 0.0};
+        double eR0 = 0.0, eR2 = 0.0, eT0 = 0.0, eT1 = 0.0;
+        if (C.L) acc.get(C.k - 1, eL);
+        if (C.B) acc.get(C.k - G.nx, eB);
+        if (C.R) {
+            eR0 = acc.get1(C.k + 1, 0);
+            eR2 = acc.get1(C.k + 1, 2);
+        }
+        if (C.T) {
+            eT0 = acc.get1(C.k + G.nx, 0);
+            eT1 = acc.get1(C.k + G.nx, 1);
+        }
+        q[0] = fma(aE[0] + c[0], e[0],
+                   fma(c[4], e[1],
+                       fma(c[5], e[2],
+                           fma(c[12], eL[0],
+                               fma(c[13], eL[1],
+                                   fma(c[14], eB[0],
+                                       fma(c[15], eB[2], fma(c[16], eR0, c[17] * eT0))))))));
+        q[1] = fma(aE[1] + c[1], e[1],
+                   fma(c[6], e[0],
+                       fma(c[7], e[3],
+                           fma(c[18], eR0, fma(c[19], eB[1], fma(c[20], eB[3], c[21] * eT1))))));
+        q[2] = fma(aE[2] + c[2], e[2],
+                   fma(c[8], e[0],
+                       fma(c[9], e[3],
+                           fma(c[22], eL[2], fma(c[23], eL[3], fma(c[24], eR2, c[25] * eT0))))));
+        q[3] = fma(aE[3] + c[3], e[3],
+                   fma(c[10], e[1], fma(c[11], e[2], fma(c[26], eR2, c[27] * eT1))));
+    } else {
+        double eL[2] = {0.0, 0.0}, eR0 = 0.0;
+        if (C.L) acc.get(C.k - 1, eL);
+        if (C.R) eR0 = acc.get1(C.k + 1, 0);
+        q[0] = fma(aE[0] + c[0], e[0],
+                   fma(c[2], e[1], fma(c[4], eL[0], fma(c[5], eL[1], c[6] * eR0))));
+        q[1] = fma(aE[1] + c[1], e[1], fma(c[3], e[0], c[7] * eR0));
+    }
 }
 
 // The geometry coefficients in FP32 (the inner solves of the mixed-precision
@@ -268,6 +413,9 @@ template <int NN> struct VecFD {
         ldf<NN>(v, k, t);
 #pragma unroll
         for (int i = 0; i < NN; ++i) o[i] = (double)t[i];
+    }
+    __device__ __forceinline__ double get1(int k, int n) const {
+        return (double)__ldcg(v + (size_t)k * NN + n);
     }
 };
 // the inner solve's search direction p = u + beta p_old of cell k, on the fly
@@ -332,44 +480,6 @@ __device__ __forceinline__ void fe_cell(const Geo &G, const Cell &C, const Acc &
             ay[n1] = G.fy * (C.T ? eT[n0] : e[n1]) - G.ky * s;
         }
     }
-}
-
-// diag(S) = diag(A_EE) + (c/3) sum_j (A_EF)_tj^2 / (A_FF)_jj, using
-// A_FE = -(c/3) A_EF^T; the A_EF coefficients of a node are m/h on both
-// nodes of its row (sign of the node's side), plus wf on the right node of
-// the row when the right face is interior and -wf on the left neighbour's
-// right node when the left face is interior.
-template <int NN>
-__device__ __forceinline__ void diag_cell(const Geo &G, const Cell &C, const double (&aE)[NN],
-                                          const double *__restrict__ iaF, double (&d)[NN]) {
-    double ia[NN], sq[NN];
-    ldc<NN>(iaF, C.k, ia);
-    const double lx2 = G.lx * G.lx;
-#pragma unroll
-    for (int b = 0; b < NN / 2; ++b) {
-        const int n0 = 2 * b, n1 = 2 * b + 1;
-        d[n0] = aE[n0] + (C.L ? G.px : G.bx);
-        d[n1] = aE[n1] + (C.R ? G.px : G.bx);
-        sq[n0] = lx2 * (ia[n0] + ia[n1]) +
-                 (C.L ? G.wfx * G.wfx * iaF[(size_t)(C.k - 1) * NN + n1] : 0.0);
-        const double c1 = C.R ? G.wfx - G.lx : -G.lx;
-        sq[n1] = lx2 * ia[n0] + c1 * c1 * ia[n1];
-    }
-    if constexpr (NN == 4) {
-        const double ly2 = G.ly * G.ly;
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            const int n0 = a, n1 = a + 2;
-            d[n0] += C.B ? G.py : G.by;
-            d[n1] += C.T ? G.py : G.by;
-            sq[n0] += ly2 * (ia[n0] + ia[n1]) +
-                      (C.B ? G.wfy * G.wfy * iaF[(size_t)(C.k - G.nx) * NN + n1] : 0.0);
-            const double c1 = C.T ? G.wfy - G.ly : -G.ly;
-            sq[n1] += ly2 * ia[n0] + c1 * c1 * ia[n1];
-        }
-    }
-#pragma unroll
-    for (int n = 0; n < NN; ++n) d[n] += G.c3 * sq[n];
 }
 
 // ---------------------------------------------------------------------------
@@ -686,45 +796,68 @@ __device__ bool grid_barrier(const GridBar &b, unsigned &target) {
 // sums the nb per-block partials in a fixed order (every thread gets them).
 // bid / nb: the block's index among the blocks that solve its problem and
 // their number (the whole grid for one problem; a share of it in the batched
-// launch).
+// launch).  FP64 instructions issue at a small fraction of the FP32 rate on
+// this GPU and the conjugate-gradient phases are bound by them, so both sums
+// run in one warp (after a shared-memory transpose) rather than in every warp
+// of the block: the block's threads only store and load.
 template <int K>
 __device__ void block_partials(double (&v)[K], double *part, int bid) {
-    __shared__ double sh[BLOCK / 32][K];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ double sh[K][BLOCK];
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
-    if (lane == 0)
-        for (int k = 0; k < K; ++k) sh[wid][k] = v[k];
+    for (int k = 0; k < K; ++k) sh[k][threadIdx.x] = v[k];
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+#pragma unroll
         for (int k = 0; k < K; ++k) {
-            double t = 0.0;
-            for (int w = 0; w < BLOCK / 32; ++w) t += sh[w][k];
-            part[(size_t)bid * K + k] = t;
+            double t = sh[k][lane];
+#pragma unroll
+            for (int w = 1; w < BLOCK / 32; ++w) t += sh[k][w * 32 + lane];
+            t = warp_sum(t);
+            if (lane == 0) part[(size_t)bid * K + k] = t;
         }
     }
 }
+
+// The grid totals of K values, then M scalars derived from them by
+// f(totals, out) in one thread (divisions and square roots taken once per
+// block instead of once per thread); every thread gets totals and scalars.
+template <int K, int M, class F>
+__device__ void grid_totals_f(double (&v)[K], const double *part, int nb, double (&o)[M], F f) {
+    __shared__ double tot[K + M];
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double t[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double a = 0.0;
+            for (int b = lane; b < nb; b += 32) a += __ldcg(part + (size_t)b * K + k);
+            t[k] = warp_sum(a);
+        }
+        if (lane == 0) {
+            double ov[M];
+            f(t, ov);
+#pragma unroll
+            for (int k = 0; k < K; ++k) tot[k] = t[k];
+#pragma unroll
+            for (int m = 0; m < M; ++m) tot[K + m] = ov[m];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = tot[k];
+#pragma unroll
+    for (int m = 0; m < M; ++m) o[m] = tot[K + m];
+    __syncthreads();
+}
+struct NoScalars {
+    template <int K>
+    __device__ void operator()(const double (&)[K], double (&o)[1]) const { o[0] = 0.0; }
+};
 template <int K>
 __device__ void grid_totals(double (&v)[K], const double *part, int nb) {
-    __shared__ double sh[BLOCK / 32][K];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double t = 0.0;
-        for (int b = threadIdx.x; b < nb; b += BLOCK) t += __ldcg(part + (size_t)b * K + k);
-        v[k] = warp_sum(t);
-    }
-    __syncthreads();
-    if (lane == 0)
-        for (int k = 0; k < K; ++k) sh[wid][k] = v[k];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double t = 0.0;
-        for (int w = 0; w < BLOCK / 32; ++w) t += sh[w][k];
-        v[k] = t;
-    }
-    __syncthreads();
+    double none[1];
+    grid_totals_f<K, 1>(v, part, nb, none, NoScalars{});
 }
 
 // ---------------------------------------------------------------------------
@@ -761,6 +894,7 @@ struct NewtonArgs {
     double a_rad, dt;
     double *T, *E, *F;
     const double *Tstar, *cv, *Estar, *jin2, *R0, *iaF, *ub, *bF;
+    const double *Sc;  // the assembled stencil of S (stencil_kernel)
     double *aE, *idiag, *x, *p;
     double *r[2], *w[2], *s[2];  // double-buffered by iteration parity
     double *partA, *partB, *partC, *partD;
@@ -797,6 +931,15 @@ struct NextU {
             ldc_cg<NN>(s, k, sv);
 #pragma unroll
             for (int i = 0; i < NN; ++i) o[i] = fma(-alpha, fma(beta, sv[i], wv[i]), rv[i]) * dv[i];
+        }
+    }
+    __device__ __forceinline__ double get1(int k, int n) const {
+        const size_t i = (size_t)k * NN + n;
+        const double rv = __ldcg(r + i), dv = __ldcg(idg + i);
+        if constexpr (START) {
+            return rv * dv;
+        } else {
+            return fma(-alpha, fma(beta, __ldcg(s + i), __ldcg(w + i)), rv) * dv;
         }
     }
 };
@@ -857,15 +1000,14 @@ __device__ __forceinline__ void newton_setup_cell(const NewtonArgs &A, int k, do
             }
         }
     }
-    double efu[NN], dg[NN], q[NN], e[NN], rv[NN], idg[NN], zv[NN];
+    double efu[NN], q[NN], e[NN], rv[NN], idg[NN], zv[NN];
     ef_cell<NN>(G, C, A.ub, efu);
-    diag_cell<NN>(G, C, aE, A.iaF, dg);
-    schur_cell<NN>(G, C, VecCG<NN>{A.E}, aE, A.iaF, q, e);
+    schur_cell<NN>(G, C, VecCG<NN>{A.E}, aE, A.Sc, q, e);
 #pragma unroll
     for (int n = 0; n < NN; ++n) {
         const double rhs = bE[n] - efu[n];
         rv[n] = rhs - q[n];
-        idg[n] = 1.0 / dg[n];
+        idg[n] = 1.0 / (aE[n] + __ldg(A.Sc + (size_t)k * Stencil<NN>::n + n));  // 1 / diag(S)
         v[0] += rhs * rhs;
         if constexpr (!SINGLE) {
             zv[n] = rv[n] * idg[n];
@@ -895,6 +1037,10 @@ struct DirCG {
         ldc_cg<NN>(p, k, b);
 #pragma unroll
         for (int i = 0; i < NN; ++i) o[i] = fma(beta, b[i], a[i]);
+    }
+    __device__ __forceinline__ double get1(int k, int n) const {
+        const size_t i = (size_t)k * NN + n;
+        return fma(beta, __ldcg(p + i), __ldcg(u + i));
     }
 };
 
@@ -973,7 +1119,7 @@ __device__ __forceinline__ int cg_textbook(const NewtonArgs &A, const int bid, c
             const Cell C = cell_of(G, k);
             double aEv[NN], qv[NN], pv[NN];
             ldc<NN>(A.aE, k, aEv);
-            schur_cell<NN>(G, C, DirCG<NN>{ub, po, beta}, aEv, A.iaF, qv, pv);
+            schur_cell<NN>(G, C, DirCG<NN>{ub, po, beta}, aEv, A.Sc, qv, pv);
             stc<NN>(pn, k, pv);
             stc<NN>(qb, k, qv);
 #pragma unroll
@@ -981,9 +1127,14 @@ __device__ __forceinline__ int cg_textbook(const NewtonArgs &A, const int bid, c
         }
         block_partials<1>(v1, A.partB, bid);
         if (!grid_barrier(A.bar, bar_target)) return DONE_TIMEOUT;
-        grid_totals<1>(v1, A.partB, nb);
-        if (!(v1[0] > 0.0) || !isfinite(v1[0]) || !isfinite(rz)) return DONE_BREAKDOWN;
-        const double alpha = rz / v1[0];
+        double o1[2];  // (curvature positive and finite, alpha)
+        grid_totals_f<1, 2>(v1, A.partB, nb, o1, [rz](const double (&t)[1], double (&o)[2]) {
+            const bool ok = t[0] > 0.0 && isfinite(t[0]) && isfinite(rz);
+            o[0] = ok ? 1.0 : 0.0;
+            o[1] = ok ? rz / t[0] : 0.0;
+        });
+        if (o1[0] == 0.0) return DONE_BREAKDOWN;
+        const double alpha = o1[1];
         double v2[2] = {0.0, 0.0};
         for (int k = k0; k < G.ncell; k += stride) {
             double pv[NN], qv[NN], dv[NN], xv[NN], rv[NN], zv[NN];
@@ -1006,11 +1157,16 @@ __device__ __forceinline__ int cg_textbook(const NewtonArgs &A, const int bid, c
         }
         block_partials<2>(v2, A.partC, bid);
         if (!grid_barrier(A.bar, bar_target)) return DONE_TIMEOUT;
-        grid_totals<2>(v2, A.partC, nb);
+        double o2[2];  // (converged, beta)
+        grid_totals_f<2, 2>(v2, A.partC, nb, o2,
+                            [rz, stop](const double (&t)[2], double (&o)[2]) {
+                                o[0] = sqrt(t[0]) <= stop ? 1.0 : 0.0;
+                                o[1] = t[1] / rz;
+                            });
         ++iters;
-        if (sqrt(v2[0]) <= stop) return DONE_CONVERGED;
+        if (o2[0] != 0.0) return DONE_CONVERGED;
         if (iters >= A.max_pcg) return DONE_CAPPED;
-        beta = v2[1] / rz;
+        beta = o2[1];
         rz = v2[1];
     }
 }
@@ -1131,7 +1287,7 @@ __device__ __forceinline__ int mixed_cg(const NewtonArgs &A, const int bid, cons
             const Cell C = cell_of(G, k);
             double aEv[NN], se[NN], ed[NN], xv[NN], rv[NN];
             ldc<NN>(A.aE, k, aEv);
-            schur_cell<NN>(G, C, VecFD<NN>{e}, aEv, A.iaF, se, ed);
+            schur_cell<NN>(G, C, VecFD<NN>{e}, aEv, A.Sc, se, ed);
             ldc<NN>(A.x, k, xv);
             ldc<NN>(A.r[0], k, rv);
             float fd[NN], fr[NN], fu[NN], z[NN];
@@ -1167,6 +1323,25 @@ __device__ __forceinline__ int mixed_cg(const NewtonArgs &A, const int bid, cons
         rr32 = v3[2];
     }
 }
+
+// The scalars of an iteration of the single-reduction conjugate gradients
+// from the sums t = (gamma = r.u, delta = w.u, r.r) of the last reduction and
+// the previous iteration's gamma and alpha: (converged, step defined, alpha,
+// beta), taken in one thread.
+struct SingleScalars {
+    double stop, gam_old, alpha_old;
+    bool first;
+    __device__ void operator()(const double (&t)[3], double (&o)[4]) const {
+        const double gam = t[0], del = t[1];
+        const double beta = first ? 0.0 : gam / gam_old;
+        const double den = first ? del : del - beta * gam / alpha_old;
+        const bool ok = den > 0.0 && isfinite(den) && isfinite(gam);
+        o[0] = sqrt(t[2]) <= stop ? 1.0 : 0.0;
+        o[1] = ok ? 1.0 : 0.0;
+        o[2] = ok ? gam / den : 0.0;
+        o[3] = beta;
+    }
+};
 
 // The Newton iteration of one problem on its nb blocks (bid: this block's
 // index among them).  MIXED: the linear solves by mixed-precision conjugate
@@ -1236,7 +1411,7 @@ __device__ __forceinline__ void lo_newton_body(const NewtonArgs &A, const int bi
                     const Cell C = cell_of(G, k);
                     double aEv[NN], wv[NN], uv[NN], rv[NN];
                     ldc<NN>(A.aE, k, aEv);
-                    schur_cell<NN>(G, C, nu, aEv, A.iaF, wv, uv);
+                    schur_cell<NN>(G, C, nu, aEv, A.Sc, wv, uv);
                     ldc<NN>(A.r[0], k, rv);
                     stc<NN>(A.w[0], k, wv);
                     stc<NN>(A.s[1], k, zero);
@@ -1251,18 +1426,18 @@ __device__ __forceinline__ void lo_newton_body(const NewtonArgs &A, const int bi
             }
             block_partials<3>(v3, A.partB, bid);
             if (!grid_barrier(A.bar, bar_target)) { status = LO_TIMEOUT; break; }
-            grid_totals<3>(v3, A.partB, nb);
+            // sc: the next iteration's (converged, den ok, alpha, beta)
+            double sc[4];
+            grid_totals_f<3, 4>(v3, A.partB, nb, sc, SingleScalars{stop, 0.0, 0.0, true});
             // conjugate gradients on S E = b from x = E, one reduction per
             // iteration; iteration i reads r_i, w_i (buffers i % 2) and s_{i-1}
             // (buffer (i + 1) % 2) and writes s_i, r_{i+1}, w_{i+1}
-            double gam = v3[0], del = v3[1], rr = v3[2], gam_old = 0.0, alpha_old = 0.0;
+            double gam = v3[0];
             while (true) {
-                if (sqrt(rr) <= stop) { done = DONE_CONVERGED; break; }
+                if (sc[0] != 0.0) { done = DONE_CONVERGED; break; }
                 if (iters >= A.max_pcg) { done = DONE_CAPPED; break; }
-                const double beta = iters == 0 ? 0.0 : gam / gam_old;
-                const double den = iters == 0 ? del : del - beta * gam / alpha_old;
-                if (!(den > 0.0) || !isfinite(den) || !isfinite(gam)) { done = DONE_BREAKDOWN; break; }
-                const double alpha = gam / den;
+                if (sc[1] == 0.0) { done = DONE_BREAKDOWN; break; }
+                const double alpha = sc[2], beta = sc[3];
                 const int cur = iters & 1, nxt = cur ^ 1;
                 const NextU<NN, false> nu{A.r[cur], A.w[cur], A.s[nxt], A.idiag, alpha, beta};
                 double v[3] = {0.0, 0.0, 0.0};
@@ -1292,7 +1467,7 @@ __device__ __forceinline__ void lo_newton_body(const NewtonArgs &A, const int bi
                     stc<NN>(A.r[nxt], k, rv);
                     double aEv[NN], wn[NN], un[NN];
                     ldc<NN>(A.aE, k, aEv);
-                    schur_cell<NN>(G, C, nu, aEv, A.iaF, wn, un);
+                    schur_cell<NN>(G, C, nu, aEv, A.Sc, wn, un);
                     stc<NN>(A.w[nxt], k, wn);
 #pragma unroll
                     for (int n = 0; n < NN; ++n) v[1] += wn[n] * un[n];
@@ -1300,13 +1475,9 @@ __device__ __forceinline__ void lo_newton_body(const NewtonArgs &A, const int bi
                 double *part = cur ? A.partB : A.partC;
                 block_partials<3>(v, part, bid);
                 if (!grid_barrier(A.bar, bar_target)) { done = DONE_TIMEOUT; break; }
-                grid_totals<3>(v, part, nb);
+                grid_totals_f<3, 4>(v, part, nb, sc, SingleScalars{stop, gam, alpha, false});
                 ++iters;
-                gam_old = gam;
-                alpha_old = alpha;
                 gam = v[0];
-                del = v[1];
-                rr = v[2];
             }
         } else {
             // textbook form (start x = E, p = u)
@@ -1434,6 +1605,7 @@ struct sm_lo_state {
     smk::lo::Scalars *h_sc = nullptr;  // pinned mirror
     int coop_grid[3] = {0, 0, 0};  // blocks of the cooperative launch per PCG form (0: not sized)
     float *fbuf = nullptr;         // the mixed-precision solves' FP32 vectors (10 per node)
+    double *Sc = nullptr;          // the assembled stencil of S, Stencil<NN>::n per cell
     int nsm = 0;                // SMs of the device (0: not queried yet)
 };
 
@@ -1544,6 +1716,10 @@ sm_status lo_ensure(sm_problem *p) {
     const size_t nblk = (size_t)std::max(w.nblk_cell, w.nblk_node);
     LO_CUDA(cudaMalloc(&w.part, sizeof(double) * PART_PER_BLOCK * nblk));
     LO_CUDA(cudaMalloc(&w.fbuf, sizeof(float) * (size_t)N * 10));
+    const size_t nsc = (size_t)p->ncell * (p->nn == 4 ? smk::lo::Stencil<4>::n
+                                                      : smk::lo::Stencil<2>::n);
+    LO_CUDA(cudaMalloc(&w.Sc, sizeof(double) * nsc));
+    p->workspace_bytes += sizeof(double) * nsc;
     p->workspace_bytes += sizeof(float) * (size_t)N * 10;
     LO_CUDA(cudaMalloc(&w.jin2, sizeof(double) * 4));
     {  // consistent method: R0 [N], R1f [N][dim], quadrant moments, inflow moments
@@ -1677,6 +1853,7 @@ smk::lo::NewtonArgs newton_args(sm_problem *p, sm_lo_state &w, const Geo &G, con
     A.jin2 = w.jin2;
     A.R0 = R0;
     A.iaF = w.iaF;
+    A.Sc = w.Sc;
     A.ub = w.ub;
     A.bF = w.bF;
     A.aE = w.aE;
@@ -1769,7 +1946,9 @@ sm_status lo_launch(sm_problem *p, const double *clo, const double *Tstar, const
     smk::lo::prepare_kernel<<<w.nblk_node, BLOCK, 0, s>>>(G, clo, p->nc, 1.0 / (G.c * dt),
                                                           w.Fstar, R1f, w.iaF, w.bF, w.ub, w.sc);
     LO_CUDA(cudaGetLastError());
-    p->launches++;
+    smk::lo::stencil_kernel<NN><<<w.nblk_cell, BLOCK, 0, s>>>(G, w.iaF, w.Sc);
+    LO_CUDA(cudaGetLastError());
+    p->launches += 2;
     LO_TRY(launch_newton<NN>(p, w, G, clo, T, E, F, Tstar, cv, R0, prm));
     p->launches++;
     return SM_OK;
@@ -1926,7 +2105,12 @@ sm_status batch_lo_launch(sm_batch *b, const std::vector<int> &members,
         smk::lo::prepare_kernel<<<w.nblk_node, BLOCK, 0, s>>>(
             G, clo[m], p->nc, 1.0 / (G.c * p->desc.dt), w.Fstar, nullptr, w.iaF, w.bF, w.ub, w.sc);
         LO_CUDA(cudaGetLastError());
-        p->launches++;
+        if (p->nn == 4)
+            smk::lo::stencil_kernel<4><<<w.nblk_cell, BLOCK, 0, s>>>(G, w.iaF, w.Sc);
+        else
+            smk::lo::stencil_kernel<2><<<w.nblk_cell, BLOCK, 0, s>>>(G, w.iaF, w.Sc);
+        LO_CUDA(cudaGetLastError());
+        p->launches += 2;
         L.h_args[i] = newton_args(p, w, G, clo[m], T[m], E[m], F[m], w.Tstar, cv[m], nullptr, prm,
                                   (int)nb[i]);
         form[i] = pcg_form(p, nsm) == 1 ? 1 : 0;  // the batched launch runs the FP64 forms
@@ -1960,7 +2144,8 @@ void batch_lo_free(void *scratch) {
 void lo_free(sm_problem *p) {
     if (!p->lo) return;
     sm_lo_state &w = *p->lo;
-    void *bufs[] = {w.buf, w.part, w.jin2, w.sigma, w.clo, w.sc, w.R0, w.qmom_int, w.jinc, w.fbuf};
+    void *bufs[] = {w.buf, w.part, w.jin2, w.sigma, w.clo, w.sc, w.R0, w.qmom_int, w.jinc, w.fbuf,
+                    w.Sc};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (w.h_sc) cudaFreeHost(w.h_sc);
@@ -2040,7 +2225,6 @@ sm_status sm_step(sm_problem *p, const double *scale_dev, const double *cv_dev, 
     LO_TRY(check_lo_problem(p));
     sm_lo_state &w = *p->lo;
     cudaStream_t s = p->stream;
-    const int N = w.N;
     double *clo = closures_dev ? closures_dev : w.clo;
     const bool consistent = prm.method == SM_METHOD_CONSISTENT;
     const bool refine = prm.refine != 0;
