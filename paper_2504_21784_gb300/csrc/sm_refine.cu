@@ -267,18 +267,21 @@ __global__ void __launch_bounds__(256) update_kernel(float2 *__restrict__ I,
 // Moments of the iterate, per node: one warp per (quadrant, direction block,
 // cell); each lane sums its direction's intensities over all groups of the
 // direction block as pairs, plain and sigma-weighted (sigma_g from the
-// records), the sums (joined into FP64) pass through shared memory, and each
-// lane forms one of the 36 moments (4 nodes x {phi, F, P} and sigma-weighted
-// {phi, F}) as the FP64 dot product of the 32 lanes' sums with their
-// weights; partial moments per (quadrant, direction block) go to
+// records), the sums pass through shared memory as pairs, and each lane
+// forms one of the 36 moments (4 nodes x {phi, F, P} and sigma-weighted
+// {phi, F}) as the compensated dot product (Acc) of the 32 lanes' sums with
+// the pairs of their weights (wpair) -- on the FP32 pipes: in FP64 these dot
+// products bounded the kernel where a direction block holds few groups (the
+// gray problems); partial moments per (quadrant, direction block) go to
 // part[qd][cell][36] for the fixed-order reduction.  Padding lanes have zero
 // weights and padding groups zero intensity.
 constexpr int MOM_WARPS = 4;
 __global__ void __launch_bounds__(MOM_WARPS * 32)
 moments_kernel(const float2 *__restrict__ I, const LaneConst *__restrict__ lanes,
-               const float2 *__restrict__ rec, int ncell, int NQ, int DB, int NGB, int NWT,
-               int GW, int LG, int Gp, double *__restrict__ part) {
-    __shared__ double sh[MOM_WARPS][8][33];
+               const float2 *__restrict__ wpair, const float2 *__restrict__ rec, int ncell,
+               int NQ, int DB, int NGB, int NWT, int GW, int LG, int Gp,
+               double *__restrict__ part) {
+    __shared__ float2 sh[MOM_WARPS][8][33];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const long long wglob = (long long)blockIdx.x * MOM_WARPS + wi;
     if (wglob >= (long long)NQ * DB * ncell) return;
@@ -305,16 +308,17 @@ moments_kernel(const float2 *__restrict__ I, const LaneConst *__restrict__ lanes
     }
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
-        sh[wi][n][lane] = (double)s[n].s + (double)s[n].c;
-        sh[wi][4 + n][lane] = (double)ss[n].s + (double)ss[n].c;
+        sh[wi][n][lane] = two_sum(s[n].s, s[n].c);
+        sh[wi][4 + n][lane] = two_sum(ss[n].s, ss[n].c);
     }
     __syncwarp();
+    const float2 *wq = wpair + (size_t)qd * 32 * 6;
     for (int m = lane; m < 36; m += 32) {
         const int n = m / 9, k = m - 9 * n;
         const int row = k < 6 ? n : 4 + n, wrow = k < 6 ? k : k - 6;
-        double acc = 0.0;
-        for (int j = 0; j < 32; ++j) acc = fma(lanes[qd * 32 + j].wm[wrow], sh[wi][row][j], acc);
-        part[((size_t)qd * ncell + cell) * 36 + m] = acc;
+        Acc a;
+        for (int j = 0; j < 32; ++j) acc_mul(a, wq[j * 6 + wrow], sh[wi][row][j]);
+        part[((size_t)qd * ncell + cell) * 36 + m] = (double)a.s + (double)a.c;
     }
 }
 
@@ -370,6 +374,10 @@ __global__ void tables_kernel(const LaneConst *__restrict__ lanes, int nlanes,
     if (i < nlanes) {
         mueta[2 * i] = df_split(lanes[i].mu);
         mueta[2 * i + 1] = df_split(lanes[i].eta);
+        // the moment weights of the lane as pairs, after the mu / eta table
+        float2 *wp = mueta + 2 * (size_t)nlanes + 6 * (size_t)i;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) wp[k] = df_split(lanes[i].wm[k]);
     }
     if (i < ninflow) inflow_df[i] = df_split(inflow[i]);
 }
@@ -385,7 +393,7 @@ struct sm_refine_state {
     bool fresh = true;                 // no outer iteration of this step has run yet
     bool met = false;                  // the last solve's corrections met the tolerance
     float *inflow0 = nullptr;          // [4][Gp] zero inflow
-    float2 *mueta = nullptr;           // [NQ*DB*32][2]
+    float2 *mueta = nullptr;           // [NQ*DB*32][2] mu, eta; then [NQ*DB*32][6] weights
     float2 *inflow_df = nullptr;       // [4][Gp]
     double *part = nullptr;            // [NQ*DB][cell][36] partial moments of the iterate
     unsigned int *maxes = nullptr;     // max |d|, max |I| of the last update (FP32 bits)
@@ -429,7 +437,7 @@ sm_status refine_ensure(sm_problem *p) {
         cudaMalloc(&R.rec32, nrec * 8 * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&R.rec_dq, nrec * 8 * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&R.inflow0, (size_t)4 * p->Gp * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&R.mueta, (size_t)nlanes * 2 * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&R.mueta, (size_t)nlanes * 8 * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&R.inflow_df, (size_t)4 * p->Gp * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&R.part, npart * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&R.maxes, 2 * sizeof(unsigned int)) != cudaSuccess ||
@@ -471,7 +479,7 @@ sm_status refine_ensure(sm_problem *p) {
         return SM_ERR_UNSUPPORTED;
     }
     R.NS = (p->nx + R.W - 1) / R.W;
-    p->workspace_bytes += ie * 16 + nrec * 112 + (size_t)20 * p->Gp + (size_t)nlanes * 16 +
+    p->workspace_bytes += ie * 16 + nrec * 112 + (size_t)20 * p->Gp + (size_t)nlanes * 64 +
                           npart * 8 + 8;
     return SM_OK;
 }
@@ -628,8 +636,8 @@ sm_status refine_solve(sm_problem *p, void *I, double *mom) {
     }
     const long long warps = (long long)p->NQ * p->DB * p->ncell;
     moments_kernel<<<(unsigned)((warps + MOM_WARPS - 1) / MOM_WARPS), MOM_WARPS * 32, 0, s>>>(
-        Iv, p->d_lanes, R.rec_df, p->ncell, p->NQ, p->DB, p->NGB, p->NWT, p->GW, p->LG, p->Gp,
-        R.part);
+        Iv, p->d_lanes, R.mueta + 2 * (size_t)p->NQ * p->DB * 32, R.rec_df, p->ncell, p->NQ,
+        p->DB, p->NGB, p->NWT, p->GW, p->LG, p->Gp, R.part);
     if (cudaGetLastError() != cudaSuccess ||
         launch_reduce_prec(64, p, R.part, p->NQ * p->DB, mom, nullptr, s) != cudaSuccess)
         return cuda_fail("FP64 defect correction: moments launch failed");
