@@ -714,6 +714,31 @@ def metric2_summary(sm_res: dict) -> dict:
     return out
 
 
+def summary_text(line: dict) -> str:
+    """The line's secondary results as one flat string (the last key), for
+    readers that keep only the top level of the record."""
+    parts = [f"pass {line['value'] / 1e9:.1f} G updates/s"]
+    if "roofline" in line:
+        parts[0] += f", sweep {line['roofline']['frac']:.3f} of HBM"
+    if "e2e" in line:
+        parts[0] += f", e2e {line['e2e']['value'] / 1e9:.1f} G"
+    for name, r in line.get("metric2", {}).items():
+        parts.append(f"{name.split('_')[0]} s/step FP32 {r['fp32_s_per_step'] * 1e3:.2f} ms, "
+                     f"FP64 {r['fp64_s_per_step'] * 1e3:.2f} ms, FP32+FP64-correction "
+                     f"{r['fp32_refined_s_per_step'] * 1e3:.2f} ms (T vs FP64 "
+                     f"{r['refined_vs_fp64_T_rel']:.1e}; FP32 alone {r['fp32_vs_fp64_T_rel']:.1e})")
+    b = line.get("batched")
+    if b:
+        parts.append(f"batched {b['value'] / 1e9:.1f} G updates/s ({b['roofline']['frac']:.3f} of "
+                     f"HBM, {b['batched_speedup']:.2f}x one-by-one), batched step "
+                     f"{b['step']['s_per_step']:.3f} s")
+    for key in ("adjoint", "adjoint_warm"):
+        a = line.get(key)
+        if a and "fd_max_rel_err" in a:
+            parts.append(f"{key} FD {a['fd_cells']} cells max rel err {a['fd_max_rel_err']:.1e}")
+    return "; ".join(parts)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -875,6 +900,7 @@ def main():
         line["cpu_baseline"] = cpu_baseline(cfg)
     if "step_metric" in line:
         line["metric2"] = metric2_summary(line["step_metric"])
+    line["summary"] = summary_text(line)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
