@@ -46,6 +46,9 @@ def parse():
                     help="W,S,E,T: strip width, prefetch rows, fused emission warps and tail "
                          "strips of the main line, set instead of autotuning (profiling runs "
                          "that must not spend launches on the autotuner)")
+    ap.add_argument("--groups-per-warp", type=int, default=0,
+                    help="(d,g) slots per lane of the main line's problem (0: the library's "
+                         "automatic choice; a profiling case otherwise)")
     ap.add_argument("--workload", default="multigroup2d",
                     choices=["multigroup2d", "adjoint2d", "graychannel2d"],
                     help="problem of the main line: the 256^2 x 128 x 64 multigroup workload "
@@ -764,11 +767,13 @@ def main():
         torch.cuda.synchronize()
 
     cfg = workload(args)
-    custom = bool(args.nx or args.groups or args.workload != "multigroup2d")
+    custom = bool(args.nx or args.groups or args.workload != "multigroup2d" or
+                  args.groups_per_warp)
     prec = args.precision
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        prob = sm.Problem.from_config(cfg, prec, stream=stream)
+        prob = sm.Problem.from_config(cfg, prec, stream=stream,
+                                      groups_per_warp=args.groups_per_warp)
         T = torch.from_numpy(W.temperature_wave(cfg)).cuda()
         scale = torch.from_numpy(W.scale_field(cfg)).cuda()
         sigma = prob.opacity(T, scale)
