@@ -313,8 +313,9 @@ sm_status sm_loworder_newton(sm_problem *p, const double *closures_dev, const do
  * arithmetic (each value a pair of FP32 numbers, about 48 significant bits,
  * on the FP32 pipes), so the FP32 sweeps give the FP64 sweep's intensity to
  * about 1e-14 and the step the FP64 step's result; during the step I_next
- * holds the iterate as such pairs (its contents are unspecified if the step
- * fails) and is converted to FP64 at its end.  stats->refine_corrections
+ * and a library buffer of the same size hold the iterate as such pairs in
+ * turn (I_next's contents are unspecified if the step fails), and I_next
+ * receives it in FP64 at the step's end.  stats->refine_corrections
  * counts the corrections.  Synchronizes after each correction.
  * With params->method = SM_METHOD_CONSISTENT (2D) the sweeps also form
  * per-quadrant moments (in the buffer registered with

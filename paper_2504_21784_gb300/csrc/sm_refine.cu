@@ -13,9 +13,12 @@
 //   2. an FP32 sweep of the correction, M d = r + (upwind face terms of d)
 //      with zero inflow (the sweep kernel with q = 0 and r in place of I^k,
 //      1/(c dt) -> 1);
-//   3. I += d,
+//   3. I += d (for the correction that ends the outer iteration, inside the
+//      moments kernel, which reads the iterate anyway and writes I + d to a
+//      second iterate buffer),
 // until a correction is below 1e-8 of the iterate (at most MAX_CORR per outer
-// iteration).  From the second outer iteration of a step on, the iterate
+// iteration; max |d| from a pass over d alone).  From the second outer
+// iteration of a step on, the iterate
 // already solves the previous records' equations to that tolerance and only
 // the emission has changed (the opacities are frozen for the step), so the
 // first correction sweeps the change of q itself and skips the residual.  A
@@ -139,6 +142,10 @@ struct RefineArgs {
 // slot, lane): four nodes, each a compensated sum of its source and products
 // of pairs.  The quadrant is a template parameter so that the
 // upwind/downwind roles of the nodes are compile-time register indices.
+// The residual of one packed element (warp task wg of quadrant Q, cell,
+// slot, lane): four nodes, each a compensated sum of its source and products
+// of pairs.  The quadrant is a template parameter so that the
+// upwind/downwind roles of the nodes are compile-time register indices.
 template <int Q>
 __device__ __forceinline__ void residual_elem(const RefineArgs &R, const size_t e, const int lane,
                                               const int slot, const int cell, const int wt) {
@@ -232,36 +239,45 @@ __global__ void __launch_bounds__(256) residual_kernel(const RefineArgs R) {
     }
 }
 
-// I += d (the iterate as pairs, the FP32 correction in the same packed
-// layout, one element of four nodes per thread), with max |d| and max |I|
-// after the update: non-negative FP32 numbers order like their bit patterns,
-// so the maxima are integer atomics on the bits.
-__global__ void __launch_bounds__(256) update_kernel(float2 *__restrict__ I,
-                                                     const float *__restrict__ d, size_t n_elems,
-                                                     unsigned int *__restrict__ maxes) {
-    unsigned md = 0, mi = 0;
+// I_out = I + d (the iterate as pairs, the FP32 correction in the same
+// packed layout, one element of four nodes per thread; I_out may be I), with
+// max |I_out| in *imax: non-negative FP32 numbers order like their bit
+// patterns, so the maximum is an integer atomic on the bits.
+__global__ void __launch_bounds__(256) update_kernel(const float2 *I, const float *__restrict__ d,
+                                                     float2 *I_out, size_t n_elems,
+                                                     unsigned int *__restrict__ imax) {
+    unsigned mi = 0;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_elems;
          e += (size_t)gridDim.x * blockDim.x) {
         const float4 dv = reinterpret_cast<const float4 *>(d)[e];
-        float4 *ip = reinterpret_cast<float4 *>(I + e * 4);
+        const float4 *ip = reinterpret_cast<const float4 *>(I + e * 4);
         const float4 a = ip[0], b = ip[1];
         const float2 n0 = df_add_f(make_float2(a.x, a.y), dv.x);
         const float2 n1 = df_add_f(make_float2(a.z, a.w), dv.y);
         const float2 n2 = df_add_f(make_float2(b.x, b.y), dv.z);
         const float2 n3 = df_add_f(make_float2(b.z, b.w), dv.w);
-        ip[0] = make_float4(n0.x, n0.y, n1.x, n1.y);
-        ip[1] = make_float4(n2.x, n2.y, n3.x, n3.y);
-        md = max(md, max(max(__float_as_uint(fabsf(dv.x)), __float_as_uint(fabsf(dv.y))),
-                         max(__float_as_uint(fabsf(dv.z)), __float_as_uint(fabsf(dv.w)))));
+        float4 *op = reinterpret_cast<float4 *>(I_out + e * 4);
+        op[0] = make_float4(n0.x, n0.y, n1.x, n1.y);
+        op[1] = make_float4(n2.x, n2.y, n3.x, n3.y);
         mi = max(mi, max(max(__float_as_uint(fabsf(n0.x)), __float_as_uint(fabsf(n1.x))),
                          max(__float_as_uint(fabsf(n2.x)), __float_as_uint(fabsf(n3.x)))));
     }
-    md = __reduce_max_sync(0xffffffffu, md);
     mi = __reduce_max_sync(0xffffffffu, mi);
-    if ((threadIdx.x & 31) == 0) {
-        atomicMax(maxes + 0, md);
-        atomicMax(maxes + 1, mi);
+    if ((threadIdx.x & 31) == 0 && mi) atomicMax(imax, mi);
+}
+
+// max |d| of the correction (FP32 bits; NaN above every finite value)
+__global__ void __launch_bounds__(256) dmax_kernel(const float4 *__restrict__ d, size_t n,
+                                                   unsigned int *__restrict__ dmax) {
+    unsigned m = 0u;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float4 v = d[i];
+        m = max(m, max(max(__float_as_uint(fabsf(v.x)), __float_as_uint(fabsf(v.y))),
+                       max(__float_as_uint(fabsf(v.z)), __float_as_uint(fabsf(v.w)))));
     }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(dmax, m);
 }
 
 // Moments of the iterate, per node: one warp per (quadrant, direction block,
@@ -277,10 +293,11 @@ __global__ void __launch_bounds__(256) update_kernel(float2 *__restrict__ I,
 // weights and padding groups zero intensity.
 constexpr int MOM_WARPS = 4;
 __global__ void __launch_bounds__(MOM_WARPS * 32)
-moments_kernel(const float2 *__restrict__ I, const LaneConst *__restrict__ lanes,
-               const float2 *__restrict__ wpair, const float2 *__restrict__ rec, int ncell,
-               int NQ, int DB, int NGB, int NWT, int GW, int LG, int Gp,
-               double *__restrict__ part) {
+moments_kernel(const float2 *__restrict__ I, const float *__restrict__ dI,
+               float2 *__restrict__ I_new, unsigned int *__restrict__ imax,
+               const LaneConst *__restrict__ lanes, const float2 *__restrict__ wpair,
+               const float2 *__restrict__ rec, int ncell, int NQ, int DB, int NGB, int NWT,
+               int GW, int LG, int Gp, double *__restrict__ part) {
     __shared__ float2 sh[MOM_WARPS][8][33];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const long long wglob = (long long)blockIdx.x * MOM_WARPS + wi;
@@ -289,22 +306,42 @@ moments_kernel(const float2 *__restrict__ I, const LaneConst *__restrict__ lanes
     const int q = qd / DB, db = qd - q * DB;
     const LaneConst &L = lanes[qd * 32 + lane];
     Acc s[4], ss[4];
+    unsigned im = 0u;
     for (int gb = 0; gb < NGB; ++gb) {
         const int wt = db * NGB + gb;
         const size_t e0 = (((size_t)q * NWT + wt) * ncell + cell) * GW;
         for (int gw = 0; gw < GW; ++gw) {
             const int g = gb * GW * LG + gw * LG + L.g_lo;
             const float2 sg = rec[((size_t)cell * Gp + g) * 6 + 5];
-            const float4 *ip = reinterpret_cast<const float4 *>(I + ((e0 + gw) * 32 + lane) * 4);
+            const size_t e = (e0 + gw) * 32 + lane;
+            const float4 *ip = reinterpret_cast<const float4 *>(I + e * 4);
             const float4 a = ip[0], b = ip[1];
-            const float2 v[4] = {make_float2(a.x, a.y), make_float2(a.z, a.w),
-                                 make_float2(b.x, b.y), make_float2(b.z, b.w)};
+            float2 v[4] = {make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
+                           make_float2(b.z, b.w)};
+            if (dI) {
+                // the pending correction: I + dI (update_kernel's operations),
+                // written to the other iterate buffer
+                const float4 dv = reinterpret_cast<const float4 *>(dI)[e];
+                v[0] = df_add_f(v[0], dv.x);
+                v[1] = df_add_f(v[1], dv.y);
+                v[2] = df_add_f(v[2], dv.z);
+                v[3] = df_add_f(v[3], dv.w);
+                float4 *op = reinterpret_cast<float4 *>(I_new + e * 4);
+                op[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+                op[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+                im = max(im, max(max(__float_as_uint(fabsf(v[0].x)), __float_as_uint(fabsf(v[1].x))),
+                                 max(__float_as_uint(fabsf(v[2].x)), __float_as_uint(fabsf(v[3].x)))));
+            }
 #pragma unroll
             for (int n = 0; n < 4; ++n) {
                 acc_add(s[n], v[n]);
                 acc_mul(ss[n], sg, v[n]);
             }
         }
+    }
+    if (dI) {
+        im = __reduce_max_sync(0xffffffffu, im);
+        if (lane == 0 && im) atomicMax(imax, im);
     }
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
@@ -353,15 +390,26 @@ __global__ void records_kernel(const double *__restrict__ rec, float2 *__restric
 
 // FP64 values to pairs (n values), and back (in place: each thread reads its
 // two FP32 numbers before it writes the FP64 number over them).
-__global__ void split_kernel(const double *__restrict__ x, float2 *__restrict__ y, size_t n) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x)
-        y[i] = df_split(x[i]);
-}
-__global__ void join_kernel(void *xy, size_t n) {
+// y = pairs of x, and the bits of max |x| (high parts) into *xmax
+__global__ void split_kernel(const double *__restrict__ x, float2 *__restrict__ y, size_t n,
+                             unsigned int *__restrict__ xmax) {
+    unsigned m = 0u;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
-        const float2 v = static_cast<const float2 *>(xy)[i];
+        const float2 v = df_split(x[i]);
+        y[i] = v;
+        m = max(m, __float_as_uint(fabsf(v.x)));
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(xmax, m);
+}
+// the pairs of xy (or of src, when given) joined into FP64 in xy; in place
+// each thread reads its pair before writing its double over it
+__global__ void join_kernel(void *xy, const float2 *src, size_t n) {
+    const float2 *in = src ? src : static_cast<const float2 *>(xy);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float2 v = in[i];
         static_cast<double *>(xy)[i] = df_join(v);
     }
 }
@@ -396,7 +444,11 @@ struct sm_refine_state {
     float2 *mueta = nullptr;           // [NQ*DB*32][2] mu, eta; then [NQ*DB*32][6] weights
     float2 *inflow_df = nullptr;       // [4][Gp]
     double *part = nullptr;            // [NQ*DB][cell][36] partial moments of the iterate
-    unsigned int *maxes = nullptr;     // max |d|, max |I| of the last update (FP32 bits)
+    float2 *alt = nullptr;             // the second iterate buffer (pairs)
+    float2 *home = nullptr;            // the caller's buffer, the first (pairs during the step)
+    const float2 *cur = nullptr;       // the iterate: ik at the step's start, then home / alt
+    unsigned int *maxes = nullptr;     // max |d| of the last correction sweep, max |I| of
+                                       // the iterate (FP32 bits)
     unsigned int *h_maxes = nullptr;   // pinned mirror
     int W = 0, S = 0, NS = 0;          // tiling of the FP32 correction sweep
     int resident = 0;                  // its CTAs that fit
@@ -411,7 +463,7 @@ void refine_free(sm_problem *p) {
     for (void *b : {(void *)R.r, (void *)R.d, (void *)R.ik, (void *)R.rec_df, (void *)R.rec32,
                     (void *)R.rec_dq,
                     (void *)R.inflow0, (void *)R.mueta, (void *)R.inflow_df, (void *)R.part,
-                    (void *)R.maxes})
+                    (void *)R.maxes, (void *)R.alt})
         if (b) cudaFree(b);
     if (R.h_maxes) cudaFreeHost(R.h_maxes);
     delete p->refine;
@@ -433,6 +485,7 @@ sm_status refine_ensure(sm_problem *p) {
     if (cudaMalloc(&R.r, ie * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&R.d, ie * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&R.ik, ie * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&R.alt, ie * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&R.rec_df, nrec * 6 * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&R.rec32, nrec * 8 * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&R.rec_dq, nrec * 8 * sizeof(float)) != cudaSuccess ||
@@ -479,7 +532,7 @@ sm_status refine_ensure(sm_problem *p) {
         return SM_ERR_UNSUPPORTED;
     }
     R.NS = (p->nx + R.W - 1) / R.W;
-    p->workspace_bytes += ie * 16 + nrec * 112 + (size_t)20 * p->Gp + (size_t)nlanes * 64 +
+    p->workspace_bytes += ie * 24 + nrec * 112 + (size_t)20 * p->Gp + (size_t)nlanes * 64 +
                           npart * 8 + 8;
     return SM_OK;
 }
@@ -489,12 +542,16 @@ sm_status refine_ensure(sm_problem *p) {
 sm_status refine_begin(sm_problem *p, const double *I_k, void *I) {
     sm_refine_state &R = *p->refine;
     R.fresh = true;
+    R.home = static_cast<float2 *>(I);
+    R.cur = R.ik;  // the first update writes the iterate into the caller's buffer
     const size_t nv = (size_t)p->NQ * p->NWT * p->ncell * p->GW * 32 * 4;
     const unsigned blocks = (unsigned)std::min<size_t>((nv + 255) / 256, 152 * 16);
-    split_kernel<<<blocks, 256, 0, p->stream>>>(I_k, R.ik, nv);
-    if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(I, R.ik, nv * sizeof(float2), cudaMemcpyDeviceToDevice, p->stream) !=
-            cudaSuccess) {
+    if (cudaMemsetAsync(R.maxes, 0, 2 * sizeof(unsigned int), p->stream) != cudaSuccess) {
+        set_last_error("FP64 defect correction: split launch failed");
+        return SM_ERR_CUDA;
+    }
+    split_kernel<<<blocks, 256, 0, p->stream>>>(I_k, R.ik, nv, R.maxes + 1);
+    if (cudaGetLastError() != cudaSuccess) {
         set_last_error("FP64 defect correction: split launch failed");
         return SM_ERR_CUDA;
     }
@@ -502,16 +559,20 @@ sm_status refine_begin(sm_problem *p, const double *I_k, void *I) {
     return SM_OK;
 }
 
-// End of a refined step: the iterate joined back into FP64, in place.
+// End of a refined step: the iterate joined back into FP64 in the caller's
+// buffer (in place when it is there).
 sm_status refine_end(sm_problem *p, void *I) {
+    sm_refine_state &R = *p->refine;
     const size_t nv = (size_t)p->NQ * p->NWT * p->ncell * p->GW * 32 * 4;
     const unsigned blocks = (unsigned)std::min<size_t>((nv + 255) / 256, 152 * 16);
-    join_kernel<<<blocks, 256, 0, p->stream>>>(I, nv);
+    const float2 *src = R.cur == static_cast<const float2 *>(I) ? nullptr : R.cur;
+    join_kernel<<<blocks, 256, 0, p->stream>>>(I, src, nv);
     if (cudaGetLastError() != cudaSuccess) {
         set_last_error("FP64 defect correction: join launch failed");
         return SM_ERR_CUDA;
     }
     p->launches++;
+    R.cur = static_cast<const float2 *>(I);
     return SM_OK;
 }
 
@@ -565,7 +626,7 @@ sm_status refine_solve(sm_problem *p, void *I, double *mom) {
     R.fresh = false;
     if (cudaGetLastError() != cudaSuccess) return cuda_fail("FP64 defect correction: records launch failed");
     p->launches++;
-    float2 *Iv = static_cast<float2 *>(I);
+    (void)I;  // the iterate is R.cur; the caller's buffer is R.home
     RefineArgs A;
     A.nx = p->nx;
     A.ny = p->ny;
@@ -586,12 +647,32 @@ sm_status refine_solve(sm_problem *p, void *I, double *mom) {
     A.rec = R.rec_df;
     A.inflow = R.inflow_df;
     A.I_k = R.ik;
-    A.I = Iv;
     A.r = R.r;
     A.n_elems = ie / 4;
+    const unsigned ublocks =
+        (unsigned)std::max<size_t>(1, std::min<size_t>((ie / 4 + 255) / 256, 152 * 8));
+    // The correction that meets the tolerance is added to the iterate by the
+    // moments kernel (which reads the iterate anyway), writing the other
+    // iterate buffer; the others by update_kernel, in place (out of place into
+    // the caller's buffer while the iterate is still I^k's pairs).  So the
+    // stopping test reads max |d| from a pass over d alone, and max |I| of the
+    // iterate before the correction (split, update or moments kernel).
+    bool pending = false;
     for (int c = 0; c < MAX_CORR; ++c) {
         const bool dq = from_dq && c == 0;
+        if (pending) {
+            float2 *out = R.cur == R.ik ? R.home : const_cast<float2 *>(R.cur);
+            if (cudaMemsetAsync(R.maxes + 1, 0, sizeof(unsigned int), s) != cudaSuccess)
+                return cuda_fail("FP64 defect correction: update launch failed");
+            update_kernel<<<ublocks, 256, 0, s>>>(R.cur, R.d, out, ie / 4, R.maxes + 1);
+            if (cudaGetLastError() != cudaSuccess)
+                return cuda_fail("FP64 defect correction: update launch failed");
+            p->launches++;
+            R.cur = out;
+            pending = false;
+        }
         if (!dq) {
+            A.I = R.cur;
             residual_kernel<<<(unsigned)((A.n_elems + 255) / 256), 256, 0, s>>>(A);
             if (cudaGetLastError() != cudaSuccess)
                 return cuda_fail("FP64 defect correction: residual launch failed");
@@ -611,16 +692,17 @@ sm_status refine_solve(sm_problem *p, void *I, double *mom) {
         a.n_tasks = R.NS * p->NQ * p->NWT;
         a.publish = publish_rows(a.n_tasks, R.resident);
         if (cudaMemsetAsync(p->d_ctrl, 0, 2 * sizeof(unsigned int), s) != cudaSuccess ||
-            launch_sweep2d_prec(32, p, a, std::min(a.n_tasks, R.resident), s) != cudaSuccess ||
-            cudaMemsetAsync(R.maxes, 0, 2 * sizeof(unsigned int), s) != cudaSuccess)
+            cudaMemsetAsync(R.maxes, 0, sizeof(unsigned int), s) != cudaSuccess ||
+            launch_sweep2d_prec(32, p, a, std::min(a.n_tasks, R.resident), s) != cudaSuccess)
             return cuda_fail("FP64 defect correction: correction sweep launch failed");
-        update_kernel<<<(unsigned)std::max<size_t>(1, std::min<size_t>((ie / 4 + 255) / 256, 152 * 8)),
-                        256, 0, s>>>(Iv, R.d, ie / 4, R.maxes);
+        dmax_kernel<<<ublocks, 256, 0, s>>>(reinterpret_cast<const float4 *>(R.d), ie / 4,
+                                            R.maxes);
         if (cudaGetLastError() != cudaSuccess ||
             cudaMemcpyAsync(R.h_maxes, R.maxes, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost,
                             s) != cudaSuccess)
-            return cuda_fail("FP64 defect correction: update launch failed");
+            return cuda_fail("FP64 defect correction: correction sweep launch failed");
         p->launches += 2;
+        pending = true;
         ++R.corrections;
         const sm_status st = sm_synchronize(p);  // also reports a wavefront timeout
         if (st != SM_OK) return st;
@@ -631,17 +713,26 @@ sm_status refine_solve(sm_problem *p, void *I, double *mom) {
             set_last_error("FP64 defect correction: the correction is not finite");
             return SM_ERR_NONPHYSICAL;
         }
+        // max |I| of the iterate before this correction: the test's scale
+        // (the correction is tiny next to I whenever the test can pass)
         R.met = (double)dmax <= CORR_TOL * (double)imax;
         if (R.met) break;
     }
+    // the last correction's update with the moments of the updated iterate,
+    // into the iterate buffer that is not being read
+    float2 *out = R.cur == R.home ? R.alt : R.home;
+    if (pending && cudaMemsetAsync(R.maxes + 1, 0, sizeof(unsigned int), s) != cudaSuccess)
+        return cuda_fail("FP64 defect correction: moments launch failed");
     const long long warps = (long long)p->NQ * p->DB * p->ncell;
     moments_kernel<<<(unsigned)((warps + MOM_WARPS - 1) / MOM_WARPS), MOM_WARPS * 32, 0, s>>>(
-        Iv, p->d_lanes, R.mueta + 2 * (size_t)p->NQ * p->DB * 32, R.rec_df, p->ncell, p->NQ,
-        p->DB, p->NGB, p->NWT, p->GW, p->LG, p->Gp, R.part);
+        R.cur, pending ? R.d : nullptr, out, R.maxes + 1, p->d_lanes,
+        R.mueta + 2 * (size_t)p->NQ * p->DB * 32, R.rec_df, p->ncell, p->NQ, p->DB, p->NGB,
+        p->NWT, p->GW, p->LG, p->Gp, R.part);
     if (cudaGetLastError() != cudaSuccess ||
         launch_reduce_prec(64, p, R.part, p->NQ * p->DB, mom, nullptr, s) != cudaSuccess)
         return cuda_fail("FP64 defect correction: moments launch failed");
     p->launches += 2;
+    if (pending) R.cur = out;
     return SM_OK;
 }
 
