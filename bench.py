@@ -269,17 +269,18 @@ def cpu_baseline(cfg, budget_s: float = 6.0, passes: int = 3):
 
 
 def converged_steps(sm, W, cfg, prec: int, n_steps: int, stream, autotune: bool = True,
-                    method: int = 0, refine: bool = False):
+                    method: int = 0, refine: bool = False, groups_per_warp: int = 0):
     """Seconds per converged time step (Algorithm 1 through sm_step) from the
     equilibrium initial state T = T0, I = B_g(T0)/4pi (whose moments are
     phi = a c T0^4, F = 0), with the paper's iteration controls.  One
     warm-up step (allocates the low-order workspace), then n_steps timed
     steps of the same evolution.  sm_step synchronizes internally, so the
     host clock brackets the device work.  refine: the FP32 sweeps with FP64
-    defect correction (an FP64-state problem, sm_step_params.refine = 1)."""
+    defect correction (an FP64-state problem, sm_step_params.refine = 1).
+    groups_per_warp: the problem's slots per lane (0: the library's rule)."""
     import torch
     with torch.cuda.stream(stream):
-        prob = sm.Problem.from_config(cfg, prec, stream=stream)
+        prob = sm.Problem.from_config(cfg, prec, stream=stream, groups_per_warp=groups_per_warp)
         nc, nn = cfg.n_cells, cfg.n_nodes
         T = torch.full((nc, nn), cfg.T0, dtype=torch.float64, device="cuda")
         scale = torch.from_numpy(W.scale_field(cfg)).cuda()
@@ -430,7 +431,10 @@ def step_metric(sm, W, cfgs, n_steps: int, stream):
         r32, T32 = converged_steps(sm, W, cfg, 32, n_steps, stream)
         r64, T64 = converged_steps(sm, W, cfg, 64, n_steps, stream)
         c32, Tc32 = converged_steps(sm, W, cfg, 32, n_steps, stream, method=sm.METHOD_CONSISTENT)
-        rr, Trr = converged_steps(sm, W, cfg, 64, n_steps, stream, refine=True)
+        # every sweep of the refined path is an FP32 correction sweep, so its
+        # FP64-state problem takes the FP32 path's slots per lane
+        rr, Trr = converged_steps(sm, W, cfg, 64, n_steps, stream, refine=True,
+                                  groups_per_warp=r32["tiling"]["groups_per_warp"])
         res[cfg.name] = {"fp32": r32, "fp64": r64,
                          "fp64_over_fp32_time": r64["s_per_step"] / r32["s_per_step"],
                          "fp32_vs_fp64_T_rel": float(np.abs(T32 - T64).max() / np.abs(T64).max()),

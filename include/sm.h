@@ -316,7 +316,11 @@ sm_status sm_loworder_newton(sm_problem *p, const double *closures_dev, const do
  * and a library buffer of the same size hold the iterate as such pairs in
  * turn (I_next's contents are unspecified if the step fails), and I_next
  * receives it in FP64 at the step's end.  stats->refine_corrections
- * counts the corrections.  Synchronizes after each correction.
+ * counts the corrections.  Synchronizes after each correction.  All of
+ * the refined path's sweeps are FP32 sweeps with the problem's slots per
+ * lane, whose automatic value for precision 64 is capped at 4: a problem
+ * made for refined steps runs faster with groups_per_warp set to what the
+ * FP32 rule gives (8 where the groups fill it).
  * With params->method = SM_METHOD_CONSISTENT (2D) the sweeps also form
  * per-quadrant moments (in the buffer registered with
  * sm_set_quadrant_moments, else in the library's own) and the low-order
