@@ -895,6 +895,7 @@ struct NewtonArgs {
     double *T, *E, *F;
     const double *Tstar, *cv, *Estar, *jin2, *R0, *iaF, *ub, *bF;
     const double *Sc;  // the assembled stencil of S (stencil_kernel)
+    double inv_dt, inv_cdt;  // 1/dt, 1/(c dt): FP64 division is slow on this GPU
     double *aE, *idiag, *x, *p;
     double *r[2], *w[2], *s[2];  // double-buffered by iteration parity
     double *partA, *partB, *partC, *partD;
@@ -959,7 +960,7 @@ __device__ __forceinline__ void newton_setup_cell(const NewtonArgs &A, int k, do
     ldc<NN>(A.Tstar, k, Ts);
     ldc<NN>(A.cv, k, cvv);
     ldc<NN>(A.Estar, k, Es);
-    const double inv_cdt = 1.0 / (G.c * A.dt);
+    const double inv_cdt = A.inv_cdt;
 #pragma unroll
     for (int n = 0; n < NN; ++n) {
         const double *cl = A.clo + ((size_t)k * NN + n) * A.nc;
@@ -967,7 +968,7 @@ __device__ __forceinline__ void newton_setup_cell(const NewtonArgs &A, int k, do
         const double Tn = T0[n];
         const double B0 = A.a_rad * G.c * (Tn * Tn * Tn * Tn);
         const double dB = 4.0 * A.a_rad * G.c * (Tn * Tn * Tn);
-        const double cv_dt = cvv[n] / A.dt;
+        const double cv_dt = cvv[n] * A.inv_dt;
         const double den = cv_dt + sP * dB;
         const double rden = den > 0.0 ? 1.0 / den : 0.0;
         const double nu = sP * dB * rden;                     // pseudo-fission coefficient
@@ -977,7 +978,7 @@ __device__ __forceinline__ void newton_setup_cell(const NewtonArgs &A, int k, do
         // (optically thick, nu -> 1) the printed differences cancel catastrophically
         // and the Newton iterates would inherit their rounding
         aE[n] = G.m * G.c * (sE * omnu + inv_cdt);
-        bE[n] = G.m * (sP * B0 * omnu + nu * cv_dt * (Ts[n] - Tn) + Es[n] / A.dt);
+        bE[n] = G.m * (sP * B0 * omnu + nu * cv_dt * (Ts[n] - Tn) + Es[n] * A.inv_dt);
     }
     if (A.R0) {
         // consistent method: face and boundary corrections (the inflow included)
@@ -1073,7 +1074,7 @@ __device__ __forceinline__ void newton_finish_cell(const NewtonArgs &A, int k, d
         if constexpr (D == 2) A.F[nd * D + 1] = (A.bF[nd * D + 1] - ay[n]) * ia[n];
         const double *cl = A.clo + nd * A.nc;
         const double sE = cl[NN == 4 ? 6 : 3], sP = cl[NN == 4 ? 8 : 5];
-        const double cv_dt = cvv[n] / A.dt;
+        const double cv_dt = cvv[n] * A.inv_dt;
         const double k4 = sP * A.a_rad * G.c;
         const double rhs = G.c * sE * e[n] + cv_dt * Ts[n];
         double y = Told[n];
@@ -1844,6 +1845,8 @@ smk::lo::NewtonArgs newton_args(sm_problem *p, sm_lo_state &w, const Geo &G, con
     A.nc = p->nc;
     A.a_rad = p->desc.a;
     A.dt = p->desc.dt;
+    A.inv_dt = 1.0 / p->desc.dt;
+    A.inv_cdt = 1.0 / (G.c * p->desc.dt);
     A.T = T;
     A.E = E;
     A.F = F;
