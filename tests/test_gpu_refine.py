@@ -115,6 +115,53 @@ def test_refined_steps_match_oracle_with_paper_controls(gpu_lib):
     prob.close()
 
 
+@pytest.mark.parametrize("gw", [0, 8])
+def test_refined_step_keeps_an_exact_equilibrium(gpu_lib, gw):
+    """A uniform medium at T0 with I = B_g(T0)/4pi and Planck inflow at T0 on
+    every side is a fixed point of the discrete step, so the first correction
+    of the step (from I^k itself) already meets the tolerance: the iterate's
+    update then comes only from the moments kernel, out of I^k's pairs into the
+    caller's buffer.  T, E and the intensity stay at equilibrium to round-off,
+    and the refined step agrees with the FP64-sweep step.  gw: the problem's
+    slots per lane (0: the library's rule for precision 64, 8: the FP32 rule)."""
+    import dataclasses
+    import torch
+    sm = gpu_lib
+    T0 = 0.5
+    cfg = dataclasses.replace(config(2, 13, 10, 8, 2, 4, T_bdr=(T0, T0, T0, T0)), T0=T0)
+    nc, nn = cfg.n_cells, cfg.n_nodes
+    res = {}
+    for refine in (1, 0):
+        prob = sm.Problem.from_config(cfg, 64, groups_per_warp=gw)
+        T = torch.full((nc, nn), T0, dtype=torch.float64, device="cuda")
+        scale = torch.ones(nc, dtype=torch.float64, device="cuda")
+        cv = torch.full((nc, nn), cfg.cv, dtype=torch.float64, device="cuda")
+        ones = torch.ones((cfg.n_groups, nc), dtype=torch.float64, device="cuda")
+        b = prob.emission(T, ones)  # unit opacity: B_g(T0)/4pi per node
+        Ip = prob.pack(b.unsqueeze(0).expand(cfg.n_dir, -1, -1, -1).contiguous())
+        In = prob.empty_intensity()
+        mom = prob.new_moments()
+        mom.zero_()
+        mom[..., 0] = cfg.a * cfg.c * T0 ** 4
+        E, F = prob.new_nodal(), prob.new_flux()
+        E.fill_(cfg.a * T0 ** 4)
+        st = prob.step(scale, cv, T, E, F, mom, Ip, In,
+                       params=sm.step_params(refine=refine, eps_inner=1e-13, pcg_rtol=1e-15,
+                                             elim_rtol=1e-15, max_elim=80))
+        assert st["converged"] == 1
+        if refine:
+            assert 1 <= st["refine_corrections"] <= 4 * st["outer_iters"]
+        Ig = prob.unpack(In).cpu().numpy()
+        Ieq = b.cpu().numpy()
+        res[refine] = (T.cpu().numpy(), E.cpu().numpy(), Ig)
+        assert np.abs(res[refine][0] - T0).max() < 1e-13 * T0
+        assert np.abs(res[refine][1] - cfg.a * T0 ** 4).max() < 1e-12 * cfg.a * T0 ** 4
+        assert max(_field(Ig[d], Ieq) for d in range(cfg.n_dir)) < 1e-12
+        prob.close()
+    assert _field(res[1][0], res[0][0]) < 1e-13
+    assert max(_field(res[1][2][d], res[0][2][d]) for d in range(cfg.n_dir)) < 1e-12
+
+
 def test_refine_refuses_fp32_state_and_the_consistent_method(gpu_lib):
     import torch
     sm = gpu_lib
