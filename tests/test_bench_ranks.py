@@ -61,3 +61,24 @@ def test_reference_arm_prints_on_rank_zero_only():
                         "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
                        env=env, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_summary_repeats_the_nested_results_as_one_flat_string():
+    """The line's last key restates the step, batched and adjoint results,
+    read from the nested objects (here a line as bench.py builds it)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    line = {"value": 1.52e11, "roofline": {"frac": 0.8}, "e2e": {"value": 1.36e11},
+            "metric2": {"multigroup2d_256x256x128x64": {
+                "fp32_s_per_step": 0.0293, "fp64_s_per_step": 0.471,
+                "fp32_refined_s_per_step": 0.277, "refined_vs_fp64_T_rel": 1e-14,
+                "fp32_vs_fp64_T_rel": 5.5e-8}},
+            "batched": {"value": 1.076e11, "roofline": {"frac": 0.573}, "batched_speedup": 2.06,
+                        "step": {"s_per_step": 0.548}},
+            "adjoint_warm": {"fd_cells": 32, "fd_max_rel_err": 8.0e-7}}
+    s = bench.summary_text(line)
+    for part in ("152.0 G", "0.800 of HBM", "e2e 136.0 G", "FP32 29.30 ms", "FP64 471.00 ms",
+                 "277.00 ms", "1.0e-14", "batched 107.6 G", "0.548 s", "32 cells",
+                 "8.0e-07"):
+        assert part in s, (part, s)
+    assert bench.summary_text({"value": 1e9}) == "pass 1.0 G updates/s"
