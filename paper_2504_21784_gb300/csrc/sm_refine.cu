@@ -679,7 +679,7 @@ sm_status refine_solve(sm_problem *p, void *I, double *mom) {
             p->launches++;
         }
         // the FP32 correction sweep: source r (or the change of q), no
-        // emission, zero inflow, its own tiling (moments not reduced)
+        // emission, zero inflow, its own tiling, no moment stage
         ++p->epoch;
         SweepArgs a = make_sweep_args(p, dq ? nullptr : R.r, R.d);
         a.src = dq ? R.rec_dq : R.rec32;
@@ -689,6 +689,7 @@ sm_status refine_solve(sm_problem *p, void *I, double *mom) {
         a.S = R.S;
         a.NS = R.NS;
         a.strip_x0 = nullptr;  // uniform strips of R.W columns
+        a.mom_acc = nullptr;   // no moments: those of the iterate are taken after
         a.n_tasks = R.NS * p->NQ * p->NWT;
         a.publish = publish_rows(a.n_tasks, R.resident);
         if (cudaMemsetAsync(p->d_ctrl, 0, 2 * sizeof(unsigned int), s) != cudaSuccess ||

@@ -379,7 +379,7 @@ __device__ bool emit_wait_strip(const EmitArgs &E, RT *src, unsigned int *ctrl, 
 // cell column of the strip from the upwind to the downwind edge.  The
 // quadrant is a template parameter so that the upwind/downwind roles of the
 // four nodes are compile-time register indices.
-template <typename RT, int GW, int Q, class Args>
+template <typename RT, int GW, int Q, bool MOM, class Args>
 __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &Lay, const int task,
                                              unsigned char *smem_raw, uint64_t *bars,
                                              uint64_t *ring_bars, uint32_t &ring_p,
@@ -618,44 +618,47 @@ __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &La
                 st_release(myflag, ep | (unsigned long long)(jj + 1));
             }
         }
-        // (e) moments of this cell: transpose through shared memory (this
-        // row's stage, read by every lane by now), then lane m forms moment
-        // m = n*9 + k as a dot product over the 32 lanes
-        RT *Mb = reinterpret_cast<RT *>(wbase + (size_t)st * stg);  // [8][MROW]
-        __syncwarp();
+        // (e) moments of this cell (MOM; the defect correction's sweeps take
+        // the moments of the iterate instead): transpose through shared
+        // memory (this row's stage, read by every lane by now), then lane m
+        // forms moment m = n*9 + k as a dot product over the 32 lanes
+        if constexpr (MOM) {
+            RT *Mb = reinterpret_cast<RT *>(wbase + (size_t)st * stg);  // [8][MROW]
+            __syncwarp();
 #pragma unroll
-        for (int n = 0; n < 4; ++n) {
-            Mb[n * MROW + lane] = s4[n];
-            Mb[(4 + n) * MROW + lane] = ss4[n];
-        }
-        __syncwarp();
-        // four partial sums per dot product: dependent chains of 8, not 32
-        RT d1p[4] = {0, 0, 0, 0};
+            for (int n = 0; n < 4; ++n) {
+                Mb[n * MROW + lane] = s4[n];
+                Mb[(4 + n) * MROW + lane] = ss4[n];
+            }
+            __syncwarp();
+            // four partial sums per dot product: dependent chains of 8, not 32
+            RT d1p[4] = {0, 0, 0, 0};
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            RT a[4], b[4];
-            lds4(Mb + vrow1 * MROW + 4 * i, a);
-            lds4(Wt + wrow1 * MROW + 4 * i, b);
+            for (int i = 0; i < 8; ++i) {
+                RT a[4], b[4];
+                lds4(Mb + vrow1 * MROW + 4 * i, a);
+                lds4(Wt + wrow1 * MROW + 4 * i, b);
 #pragma unroll
-            for (int t = 0; t < 4; ++t) d1p[t] = fma(a[t], b[t], d1p[t]);
+                for (int t = 0; t < 4; ++t) d1p[t] = fma(a[t], b[t], d1p[t]);
+            }
+            const RT d1 = (d1p[0] + d1p[1]) + (d1p[2] + d1p[3]);
+            RT d2;
+            {
+                RT c[4], e4[4];
+                lds4(Mb + vrow2 * MROW + c2, c);
+                lds4(Wt + wrow2 * MROW + c2, e4);
+                d2 = fma(c[3], e4[3], fma(c[2], e4[2], fma(c[1], e4[1], c[0] * e4[0])));
+                d2 += __shfl_xor_sync(0xffffffffu, d2, 1);
+                d2 += __shfl_xor_sync(0xffffffffu, d2, 2);
+                d2 += __shfl_xor_sync(0xffffffffu, d2, 4);
+            }
+            // this warp task's share of the cell's moments: a slot of its own
+            // (no atomics), summed over the warp tasks in a fixed order by the
+            // reduction, so that the moments do not depend on the schedule
+            RT *ac = acc + ((size_t)wg * A.ncell + cell) * 36;
+            ac[m1] = d1;
+            if ((lane & 7) == 0) ac[m2] = d2;
         }
-        const RT d1 = (d1p[0] + d1p[1]) + (d1p[2] + d1p[3]);
-        RT d2;
-        {
-            RT c[4], e4[4];
-            lds4(Mb + vrow2 * MROW + c2, c);
-            lds4(Wt + wrow2 * MROW + c2, e4);
-            d2 = fma(c[3], e4[3], fma(c[2], e4[2], fma(c[1], e4[1], c[0] * e4[0])));
-            d2 += __shfl_xor_sync(0xffffffffu, d2, 1);
-            d2 += __shfl_xor_sync(0xffffffffu, d2, 2);
-            d2 += __shfl_xor_sync(0xffffffffu, d2, 4);
-        }
-        // this warp task's share of the cell's moments: a slot of its own
-        // (no atomics), summed over the warp tasks in a fixed order by the
-        // reduction, so that the moments do not depend on the schedule
-        RT *ac = acc + ((size_t)wg * A.ncell + cell) * 36;
-        ac[m1] = d1;
-        if ((lane & 7) == 0) ac[m2] = d2;
         // the stage is free: prefetch row jj + S into it (the proxy fence
         // orders this warp's reads and writes of it before the copy)
         __syncwarp();
@@ -679,7 +682,7 @@ __device__ __forceinline__ void sweep2d_task_q(const Args &A, const Layout2D &La
     }
 }
 
-template <typename RT, int GW, class Args>
+template <typename RT, int GW, bool MOM = true, class Args>
 __device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay, const int task,
                                              unsigned char *smem_raw, uint64_t *bars,
                                              uint64_t *ring_bars, uint32_t &ring_p,
@@ -691,19 +694,19 @@ __device__ __forceinline__ void sweep2d_task(const Args &A, const Layout2D &Lay,
     const int q = (task % NWG) / A.NWT;
     switch (q) {
         case 0:
-            sweep2d_task_q<RT, GW, 0>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c,
+            sweep2d_task_q<RT, GW, 0, MOM>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c,
                                       s_abort, phase, epoch, E, s_edges);
             break;
         case 1:
-            sweep2d_task_q<RT, GW, 1>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c,
+            sweep2d_task_q<RT, GW, 1, MOM>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c,
                                       s_abort, phase, epoch, E, s_edges);
             break;
         case 2:
-            sweep2d_task_q<RT, GW, 2>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c,
+            sweep2d_task_q<RT, GW, 2, MOM>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c,
                                       s_abort, phase, epoch, E, s_edges);
             break;
         default:
-            sweep2d_task_q<RT, GW, 3>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c,
+            sweep2d_task_q<RT, GW, 3, MOM>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c,
                                       s_abort, phase, epoch, E, s_edges);
             break;
     }
@@ -716,7 +719,7 @@ __device__ __forceinline__ void sweep_warps_sync(int nthreads) {
 
 // W sweep warps (one per cell column of the strip), plus E.warps fused
 // emission warps when E.warps > 0 (EmitArgs).
-template <typename RT, int GW>
+template <typename RT, int GW, bool MOM = true>
 __global__ void __launch_bounds__(512) sweep2d_kernel(const __grid_constant__ SweepArgs A,
                                                       const __grid_constant__ EmitArgs E) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -756,8 +759,8 @@ __global__ void __launch_bounds__(512) sweep2d_kernel(const __grid_constant__ Sw
         sweep_warps_sync(W * 32);
         const int task = s_task;
         if (task >= A.n_tasks || s_abort) return;
-        sweep2d_task<RT, GW>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c, &s_abort,
-                             phase, A.epoch, Ep, s_edges);
+        sweep2d_task<RT, GW, MOM>(A, Lay, task, smem_raw, bars, ring_bars, ring_p, ring_c,
+                                  &s_abort, phase, A.epoch, Ep, s_edges);
     }
 }
 
@@ -946,6 +949,17 @@ static const void *kernel2d_ptr(int GW) {
     }
 }
 
+// The FP32 kernel without the moment stage (the defect correction's sweeps,
+// SweepArgs::mom_acc NULL).
+static const void *kernel2d_nomom_ptr(int GW) {
+    switch (GW) {
+        case 1: return (const void *)sweep2d_kernel<float, 1, false>;
+        case 2: return (const void *)sweep2d_kernel<float, 2, false>;
+        case 4: return (const void *)sweep2d_kernel<float, 4, false>;
+        default: return (const void *)sweep2d_kernel<float, 8, false>;
+    }
+}
+
 // Dynamic shared memory of a 2D sweep CTA: the sweep layout, plus the group
 // edges in FP32 for fused emission warps.
 static size_t sweep2d_smem_total(int prec, int W, int GW, int S, int GSLOT, int emit_warps,
@@ -963,6 +977,8 @@ int sweep2d_max_resident_prec(int prec, const sm_problem *p, int W, int S, size_
     const void *k = (prec == 32) ? kernel2d_ptr<float>(p->GW) : kernel2d_ptr<double>(p->GW);
     int nsm = 0;
     if (!allow_dynamic_smem(k, smem, &nsm)) return 0;
+    // the FP32 kernel without moments runs with the same tiling: same limit
+    if (prec == 32 && !allow_dynamic_smem(kernel2d_nomom_ptr(p->GW), smem, &nsm)) return 0;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, W * 32, smem) != cudaSuccess)
         return 0;
@@ -974,7 +990,9 @@ cudaError_t launch_sweep2d_prec(int prec, const sm_problem *p, const SweepArgs &
     EmitArgs none;
     memset(&none, 0, sizeof(none));
     const size_t smem = sweep2d_smem_bytes(prec, a.W, a.GW, a.S, a.GW * a.LG);
-    const void *k = (prec == 32) ? kernel2d_ptr<float>(a.GW) : kernel2d_ptr<double>(a.GW);
+    const void *k = (prec == 32) ? (a.mom_acc ? kernel2d_ptr<float>(a.GW)
+                                              : kernel2d_nomom_ptr(a.GW))
+                                 : kernel2d_ptr<double>(a.GW);
     SweepArgs args = a;
     void *params[] = {&args, &none};
     return cudaLaunchKernel(k, dim3(grid), dim3(a.W * 32), params, smem, s);
