@@ -13,17 +13,19 @@
 //
 // Unknowns are nodal (cell corners): E_n and F_n = (F_x, F_y).  With the
 // interior faces oriented +x / +y, s = +1, so F^.n takes the low-side F and
-// P^ n the high-side E.  The lumped A_FF = m sigma~_F is diagonal, which lets
-// S = A_EE - A_EF A_FF^-1 A_FE be applied matrix-free as a stencil over a
-// cell and its four face neighbours.
+// P^ n the high-side E.  The lumped A_FF = m sigma~_F is diagonal, which makes
+// S = A_EE - A_EF A_FF^-1 A_FE a stencil over a cell and its four face
+// neighbours; its coefficients are assembled once per low-order solve (only
+// aE on its diagonal changes between Newton iterations).
 //
 // GB300 runs FP64 at about 1/64 of its FP32 rate (roughly two FP64 FMAs per
 // clock per SM), so these kernels are bound by FP64 instruction count, not by
 // memory: the whole working set of a 256x256 mesh is a few MB and stays in
 // L2.  The design therefore minimises FP64 work: one thread per cell (the
 // four nodes of a cell share their stencil loads and partial sums, read as
-// double2 vectors), geometry folded into per-problem coefficients, 1/A_FF and
+// double2 vectors), the stencil of S assembled once per solve, 1/A_FF and
 // 1/diag(S) precomputed so that conjugate-gradient iterations divide nothing,
+// block and grid sums taken by one warp per block,
 // and the pointwise temperature Newton step taken with an FP32 reciprocal of
 // its derivative (a quasi-Newton step: the root is unchanged).  PCG scalars
 // never leave the device: grid-wide sums are deterministic fixed-order sums
