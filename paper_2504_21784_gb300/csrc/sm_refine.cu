@@ -225,11 +225,17 @@ __global__ void __launch_bounds__(256) residual_kernel(const RefineArgs R) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= R.n_elems) return;
     const int lane = (int)(e & 31);
-    size_t rest = e >> 5;
-    const int slot = (int)(rest % R.GW);
-    rest /= R.GW;
-    const int cell = (int)(rest % R.ncell);
-    const int wg = (int)(rest / R.ncell);
+    // the (warp task, cell, slot) of the element in 32-bit unsigned
+    // arithmetic: e / 32 counts 512-byte blocks of the packed FP32 residual,
+    // so it stays below 2^32 on any device; a 64-bit division costs several
+    // times the instructions, and this kernel is bound by instruction issue
+    const unsigned rest = (unsigned)(e >> 5);
+    const unsigned gw = (unsigned)R.GW, nc = (unsigned)R.ncell;
+    const unsigned r1 = rest / gw;
+    const int slot = (int)(rest - r1 * gw);
+    const unsigned wgu = r1 / nc;
+    const int cell = (int)(r1 - wgu * nc);
+    const int wg = (int)wgu;
     const int q = wg / R.NWT, wt = wg - q * R.NWT;
     switch (q) {
         case 0: residual_elem<0>(R, e, lane, slot, cell, wt); break;
